@@ -1,0 +1,196 @@
+/*
+ * wskpn — weight-sharing kernel-prediction Monte Carlo denoiser on one
+ * NVIDIA B300 (sm_103a).  C ABI of libwskpn.so.
+ *
+ * The method (Fan, Wang, Huo, Bao, "Real-time Monte Carlo Denoising with
+ * Weight Sharing Kernel Prediction Network", EGSR 2021):
+ *   Sec. 5.1  input assembly: gamma tone-mapped radiance, albedo, normal and
+ *             depth scaled to [0,1] -> 10 channels;
+ *   Sec. 4.1  ImportanceNet: KSxKS conv blocks with ReLU, then an output conv
+ *             giving M importance maps I_i (Eq. 2) and M fusion logits;
+ *   Eq. 3-4   per-pixel kernels w_p(q) = softmax over the k_i x k_i window
+ *             Omega_p of I_i(q), applied to all colour channels;
+ *   Eq. 5     fusion of the M filtered images with per-pixel softmax weights
+ *             alpha_i; the filter runs on irradiance r / (a + eps) and the
+ *             result is multiplied back by (a + eps) (Sec. 4.2).
+ *
+ * Conventions for every entry point below:
+ *   - Images are float32, planar [C][H][W] (x fastest), in DEVICE memory
+ *     unless a parameter says "host".  A batch of B frames of one size is
+ *     either B separate wskpn_frame pointer sets or one contiguous
+ *     [B][C][H][W] tensor, as stated per call.
+ *   - The caller owns every buffer it passes; the library never frees or
+ *     retains caller pointers beyond the call (asynchronous calls read them
+ *     until the enqueued work completes on `stream`).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Compute calls are asynchronous: they enqueue kernels and
+ *     return; the caller synchronises the stream before reading results.
+ *   - A context belongs to the CUDA device that was current at
+ *     wskpn_create; call it with that device current.
+ *   - Every call returns a wskpn_status and never aborts or traps.  On
+ *     failure wskpn_last_error() describes the cause; nothing is enqueued
+ *     when argument validation fails.
+ *   - All floating-point work of the denoiser runs in CUDA kernels of this
+ *     library; there is no CPU fallback.
+ */
+#ifndef WSKPN_H
+#define WSKPN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WSKPN_OK = 0,
+    WSKPN_EINVAL = 1,       /* bad argument (null pointer, size, config) */
+    WSKPN_ENOMEM = 2,       /* device or host allocation failed */
+    WSKPN_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+    WSKPN_EUNSUPPORTED = 4, /* valid request this build cannot run */
+    WSKPN_EBUSY = 5,        /* serving: admission refused, queue full */
+    WSKPN_ETIMEOUT = 6,     /* a bounded wait ran out */
+    WSKPN_ENUMERIC = 7      /* non-finite values detected */
+} wskpn_status;
+
+typedef enum {
+    WSKPN_FP32 = 0, /* convolutions in FP32 FFMA (SIMT) */
+    WSKPN_BF16 = 1, /* convolutions on tcgen05 tensor cores, BF16 in, FP32 accumulate */
+    WSKPN_FP8 = 2   /* convolutions on tcgen05, e4m3 in, FP32 accumulate, per-channel scales */
+} wskpn_precision;
+
+#define WSKPN_MAX_LAYERS 8
+#define WSKPN_MAX_KERNELS 8
+#define WSKPN_MAX_BATCH 16
+
+/* Network and runtime configuration (Sec. 4.1, Sec. 5.3).
+ * widths[0] must be 10 (the Sec. 5.1 input channels) and widths[n_layers]
+ * must be 2 * n_kernels; every conv layer but the last has a ReLU.
+ * ksizes are odd filtering window sizes (paper: k_b = 3, k_s = 2, M = 6 ->
+ * 3,5,...,13).  max_batch/max_h/max_w size the context's workspaces. */
+typedef struct {
+    int n_layers;
+    int widths[WSKPN_MAX_LAYERS + 1];
+    int conv_ks;        /* 3 or 5 */
+    int n_kernels;      /* M */
+    int ksizes[WSKPN_MAX_KERNELS];
+    wskpn_precision prec;
+    float albedo_eps;   /* eps in y = r / (a + eps) */
+    float gamma;        /* tone-map exponent 1/gamma */
+    float depth_near, depth_far;
+    int max_batch, max_h, max_w;
+} wskpn_config;
+
+/* One frame's input buffers, float32 planar: radiance [3][H][W],
+ * albedo [3][H][W], normal [3][H][W], depth [1][H][W]. */
+typedef struct {
+    const float* radiance;
+    const float* albedo;
+    const float* normal;
+    const float* depth;
+} wskpn_frame;
+
+typedef struct wskpn_ctx wskpn_ctx;
+
+/* Library version string (static storage). */
+const char* wskpn_version(void);
+
+/* Fills *cfg with the paper's 3-block configuration (widths 10-32-48-64-12,
+ * 5x5 convs, M = 6 sizes 3..13, eps 1e-2, gamma 2.2, depth range [1, 10],
+ * BF16, max 1 x 1080 x 1920).  Returns WSKPN_EINVAL if cfg is NULL. */
+wskpn_status wskpn_config_default(wskpn_config* cfg);
+
+/* Number of float32 values in the weight blob for cfg: per layer
+ * W[Cout][Cin][KS][KS] followed by b[Cout], layers in order.  0 if cfg is
+ * invalid. */
+size_t wskpn_n_weights(const wskpn_config* cfg);
+
+/* Creates a context on the current CUDA device: validates cfg, copies the
+ * host weight blob (n_weights floats, layout as wskpn_n_weights), packs it
+ * for the configured precision and allocates workspaces for
+ * max_batch x max_h x max_w.  *out receives the context (NULL on failure).
+ * Errors: EINVAL (cfg/weights), ENOMEM, ECUDA, EUNSUPPORTED. */
+wskpn_status wskpn_create(const wskpn_config* cfg, const float* host_weights, size_t n_weights,
+                          wskpn_ctx** out);
+
+/* Frees the context and all its device memory (synchronises its device).
+ * NULL is ignored. */
+void wskpn_destroy(wskpn_ctx* ctx);
+
+/* Last error message of ctx (or of the calling thread when ctx is NULL). */
+const char* wskpn_last_error(const wskpn_ctx* ctx);
+
+/* Replaces the weights from a host blob (same layout as wskpn_create) or a
+ * device blob; re-packs them for the configured precision, stream-ordered.
+ * The FP8 activation scales are kept. */
+wskpn_status wskpn_set_weights(wskpn_ctx* ctx, const float* weights, size_t n, int on_device,
+                               void* stream);
+
+/* Copies the context's FP32 master weights to a device buffer of
+ * wskpn_n_weights floats (stream-ordered). */
+wskpn_status wskpn_get_weights(wskpn_ctx* ctx, float* dev_out, size_t n, void* stream);
+
+/* D_Theta(r, f): denoises `batch` frames of size h x w (Eq. 1-5).
+ * frames: host array of `batch` wskpn_frame (device pointers).
+ * out:    device float32 [batch][3][h][w].
+ * Errors: EINVAL (null pointers, batch < 1 or > max_batch, h or w < 1 or
+ * beyond max_h/max_w), ECUDA. */
+wskpn_status wskpn_denoise(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
+                           float* out, void* stream);
+
+/* wskpn_denoise from HOST buffers, synchronous: copies each frame's inputs
+ * (host float32 planar, pinned memory recommended) into context-owned
+ * device staging buffers, denoises, copies the result to host_out
+ * ([batch][3][h][w] float32) and waits for `stream` before returning.  The
+ * staging buffers (52 bytes per pixel of max_batch x max_h x max_w) are
+ * allocated by the first call.  Errors as wskpn_denoise, plus ENOMEM. */
+wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h,
+                                int w, float* host_out, void* stream);
+
+/* ImportanceNet only (Sec. 5.1 + Sec. 4.1): writes the network output
+ * z [batch][2M][h][w] (channels 0..M-1 importance maps for ksizes[0..M-1],
+ * M..2M-1 fusion logits) to device memory.  Errors as wskpn_denoise. */
+wskpn_status wskpn_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
+                          float* z_out, void* stream);
+
+/* Sec. 5.1 input assembly alone: x0 [batch][10][h][w] float32 planar:
+ * clamp(r,0,1)^(1/gamma), albedo, 0.5 n + 0.5, (d - near)/(far - near). */
+wskpn_status wskpn_prep(const wskpn_frame* frames, int batch, int h, int w, float gamma,
+                        float depth_near, float depth_far, float* x0_out, void* stream);
+
+/* Reconstruction (Eq. 3-5 with Sec. 4.2 demodulation), stateless:
+ *   z        device [batch][2M][h][w]: importance maps then fusion logits;
+ *   radiance device [batch][3][h][w]; albedo device [batch][3][h][w];
+ *   ksizes   host array of M odd sizes (1..13), M in 1..8;
+ *   out      device [batch][3][h][w];
+ *   fallbacks optional device uint32 counter, incremented once per
+ *            (pixel, size) whose window sum needed the per-window-max path.
+ * Windows are clipped to the image.  Errors: EINVAL, ECUDA. */
+wskpn_status wskpn_decode_fuse_fwd(const float* z, const float* radiance, const float* albedo,
+                                   int batch, int h, int w, int M, const int* ksizes, float eps,
+                                   float* out, unsigned int* fallbacks, void* stream);
+
+/* Numeric fallback counter of ctx (pixels x sizes that took the slow exact
+ * softmax path since creation); synchronises the context's device. */
+wskpn_status wskpn_numeric_fallbacks(wskpn_ctx* ctx, uint64_t* count);
+
+/* Per-stage device timing (the paper reports prediction and reconstruction
+ * time separately, Sec. 6.2, Table "time").  While enabled, every
+ * wskpn_denoise / wskpn_logits call records CUDA events on its own stream
+ * at each stage boundary.  Stages: 0 = input assembly (Sec. 5.1),
+ * 1..n_layers = conv layers (Sec. 4.1), n_layers + 1 = reconstruction
+ * (Eq. 3-5).  Errors: EINVAL (ctx NULL). */
+wskpn_status wskpn_profile_enable(wskpn_ctx* ctx, int enable);
+
+/* Waits for every call recorded since the last read, writes the summed
+ * milliseconds of each stage to ms[0 .. min(cap, n_layers + 2) - 1], the
+ * stage count (n_layers + 2) to *n_stages and the number of recorded calls
+ * to *calls, then clears the record.  Stages a call did not run add 0. */
+wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stages, int* calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WSKPN_H */

@@ -1,0 +1,97 @@
+"""ctypes declarations of libwskpn.so (include/wskpn.h).  Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libwskpn.so")
+
+MAX_LAYERS = 8
+MAX_KERNELS = 8
+MAX_BATCH = 16
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EBUSY, ETIMEOUT, ENUMERIC = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EBUSY", "ETIMEOUT", "ENUMERIC"]
+FP32, BF16, FP8 = 0, 1, 2
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("n_layers", ctypes.c_int),
+        ("widths", ctypes.c_int * (MAX_LAYERS + 1)),
+        ("conv_ks", ctypes.c_int),
+        ("n_kernels", ctypes.c_int),
+        ("ksizes", ctypes.c_int * MAX_KERNELS),
+        ("prec", ctypes.c_int),
+        ("albedo_eps", ctypes.c_float),
+        ("gamma", ctypes.c_float),
+        ("depth_near", ctypes.c_float),
+        ("depth_far", ctypes.c_float),
+        ("max_batch", ctypes.c_int),
+        ("max_h", ctypes.c_int),
+        ("max_w", ctypes.c_int),
+    ]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("radiance", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
+                ("normal", ctypes.c_void_p), ("depth", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_SZ = ctypes.c_size_t
+_FR = ctypes.POINTER(Frame)
+
+# name -> (argtypes, restype): the exported C ABI, in header order
+SIGNATURES = {
+    "wskpn_version": ([], ctypes.c_char_p),
+    "wskpn_config_default": ([ctypes.POINTER(Config)], _I),
+    "wskpn_n_weights": ([ctypes.POINTER(Config)], _SZ),
+    "wskpn_create": ([ctypes.POINTER(Config), _P, _SZ, ctypes.POINTER(_P)], _I),
+    "wskpn_destroy": ([_P], None),
+    "wskpn_last_error": ([_P], ctypes.c_char_p),
+    "wskpn_set_weights": ([_P, _P, _SZ, _I, _P], _I),
+    "wskpn_get_weights": ([_P, _P, _SZ, _P], _I),
+    "wskpn_denoise": ([_P, _FR, _I, _I, _I, _P, _P], _I),
+    "wskpn_denoise_host": ([_P, _FR, _I, _I, _I, _P, _P], _I),
+    "wskpn_logits": ([_P, _FR, _I, _I, _I, _P, _P], _I),
+    "wskpn_prep": ([_FR, _I, _I, _I, _F, _F, _F, _P, _P], _I),
+    "wskpn_decode_fuse_fwd": ([_P, _P, _P, _I, _I, _I, _I, ctypes.POINTER(_I), _F, _P, _P, _P], _I),
+    "wskpn_numeric_fallbacks": ([_P, ctypes.POINTER(ctypes.c_uint64)], _I),
+    "wskpn_profile_enable": ([_P, _I], _I),
+    "wskpn_profile_read": ([_P, ctypes.POINTER(_F), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+}
+
+_lib = None
+
+
+class WskpnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"wskpn {name}: {msg}")
+
+
+def load() -> ctypes.CDLL:
+    """Loads the in-tree libwskpn.so; raises ImportError when it is missing
+    (there is no fallback implementation)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2202_05977_b300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def check(status: int, ctx=None) -> None:
+    if status != OK:
+        msg = load().wskpn_last_error(ctx)
+        raise WskpnError(status, msg.decode() if msg else "")

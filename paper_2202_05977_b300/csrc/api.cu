@@ -1,0 +1,419 @@
+// C ABI of libwskpn: context lifetime, weight packing, workspaces and the
+// per-frame denoise pipeline (Sec. 5.1 prep -> Sec. 4.1 convs -> Eq. 3-5
+// reconstruction), all enqueued on the caller's stream.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace wskpn {
+
+static thread_local std::string g_thread_err;
+void set_thread_error(const std::string& msg) { g_thread_err = msg; }
+const std::string& thread_error() { return g_thread_err; }
+
+// kernels (other translation units)
+wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear,
+                         float dfar, void* const* out, int layout, cudaStream_t st, std::string& err);
+wskpn_status launch_conv_simt(const float* const* in, float* const* out, int B, int H, int W,
+                              int Cin, int Cout, int KS, const float* w_packed,
+                              const float* bias_padded, int relu, cudaStream_t st, std::string& err);
+wskpn_status launch_pack_simt(const float* w, const float* b, int Cin, int Cout, int KS, float* wp,
+                              float* bp, cudaStream_t st, std::string& err);
+int simt_coutp(int cout);
+wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r,
+                                    const float* const* a, float* const* out, int B, int H, int W,
+                                    int M, const int* ks, float eps, unsigned int* fallbacks,
+                                    cudaStream_t st, std::string& err);
+
+void prof_begin(wskpn_ctx* ctx, cudaStream_t st) {
+    if (!ctx->prof) return;
+    const size_t n = ctx->cfg.n_layers + 3;
+    if (ctx->prof_used == ctx->prof_sets.size()) {
+        std::vector<cudaEvent_t> ev(n);
+        for (auto& e : ev) cudaEventCreate(&e);
+        ctx->prof_sets.push_back(ev);
+    }
+    ctx->prof_cur = (int)ctx->prof_used++;
+    auto& ev = ctx->prof_sets[ctx->prof_cur];
+    for (size_t i = 0; i < n; ++i) cudaEventRecord(ev[i], st);  // stages not run read as 0 ms
+}
+
+void prof_mark(wskpn_ctx* ctx, int boundary, cudaStream_t st) {
+    if (!ctx->prof || ctx->prof_cur < 0) return;
+    auto& ev = ctx->prof_sets[ctx->prof_cur];
+    for (size_t i = boundary; i < ev.size(); ++i) cudaEventRecord(ev[i], st);
+}
+
+void prof_end(wskpn_ctx* ctx) { ctx->prof_cur = -1; }
+
+std::string validate_config(const wskpn_config* c) {
+    if (!c) return "config is NULL";
+    if (c->n_layers < 1 || c->n_layers > WSKPN_MAX_LAYERS) return "n_layers out of range [1, 8]";
+    if (c->widths[0] != 10) return "widths[0] must be 10 (Sec. 5.1 input channels)";
+    for (int l = 1; l <= c->n_layers; ++l)
+        if (c->widths[l] < 1 || c->widths[l] > 64) return "layer widths must be in [1, 64]";
+    if (c->conv_ks != 3 && c->conv_ks != 5) return "conv_ks must be 3 or 5";
+    if (c->n_kernels < 1 || c->n_kernels > WSKPN_MAX_KERNELS) return "n_kernels out of range [1, 8]";
+    if (c->widths[c->n_layers] != 2 * c->n_kernels) return "last width must be 2 * n_kernels";
+    for (int i = 0; i < c->n_kernels; ++i)
+        if (c->ksizes[i] < 1 || c->ksizes[i] > 13 || (c->ksizes[i] & 1) == 0)
+            return "ksizes must be odd and in [1, 13]";
+    if (!(c->albedo_eps > 0.f)) return "albedo_eps must be > 0";
+    if (!(c->gamma > 0.f)) return "gamma must be > 0";
+    if (!(c->depth_far > c->depth_near)) return "depth_far must exceed depth_near";
+    if (c->max_batch < 1 || c->max_batch > 64) return "max_batch out of range [1, 64]";
+    if (c->max_h < 1 || c->max_w < 1 || (long)c->max_h * c->max_w > (1L << 26))
+        return "max_h/max_w out of range";
+    if (c->prec != WSKPN_FP32 && c->prec != WSKPN_BF16 && c->prec != WSKPN_FP8) return "unknown precision";
+    return "";
+}
+
+size_t n_weights_of(const wskpn_config* c) {
+    size_t n = 0;
+    for (int l = 1; l <= c->n_layers; ++l)
+        n += (size_t)c->widths[l] * c->widths[l - 1] * c->conv_ks * c->conv_ks + c->widths[l];
+    return n;
+}
+
+wskpn_status ctx_repack(wskpn_ctx* ctx, cudaStream_t st) {
+    const wskpn_config& c = ctx->cfg;
+    for (int l = 0; l < c.n_layers; ++l) {
+        Layer& L = ctx->layers[l];
+        wskpn_status s = launch_pack_simt(ctx->d_master + L.woff, ctx->d_master + L.boff, L.cin, L.cout,
+                                          c.conv_ks, L.w32, L.b32, st, ctx->err);
+        if (s) return s;
+        if (c.prec != WSKPN_FP32) {
+            s = tc_pack_layer(ctx, l, st);
+            if (s) return s;
+        }
+    }
+    return WSKPN_OK;
+}
+
+static wskpn_status check_frames(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w) {
+    if (!frames) {
+        ctx->err = "frames is NULL";
+        return WSKPN_EINVAL;
+    }
+    if (batch < 1 || batch > ctx->cfg.max_batch) {
+        ctx->err = "batch out of range [1, max_batch]";
+        return WSKPN_EINVAL;
+    }
+    if (h < 1 || w < 1 || h > ctx->cfg.max_h || w > ctx->cfg.max_w || (size_t)batch * h * w > ctx->ws_pixels) {
+        ctx->err = "frame size exceeds the context's max_h/max_w/max_batch";
+        return WSKPN_EINVAL;
+    }
+    for (int b = 0; b < batch; ++b)
+        if (!frames[b].radiance || !frames[b].albedo || !frames[b].normal || !frames[b].depth) {
+            ctx->err = "a frame buffer pointer is NULL";
+            return WSKPN_EINVAL;
+        }
+    return WSKPN_OK;
+}
+
+// FP32 plain path: prep -> SIMT convs -> z (planar FP32 [B][2M][H][W]).
+static wskpn_status logits_fp32(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
+                                float* z, cudaStream_t st) {
+    const wskpn_config& c = ctx->cfg;
+    const size_t HW = (size_t)H * W;
+    std::vector<void*> x0(B);
+    for (int b = 0; b < B; ++b) x0[b] = ctx->d_actA + (size_t)b * c.widths[0] * HW;
+    wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), 0, st, ctx->err);
+    if (s) return s;
+    prof_mark(ctx, 1, st);
+    std::vector<const float*> in(B);
+    std::vector<float*> out(B);
+    for (int l = 1; l <= c.n_layers; ++l) {
+        float* src = (l - 1) % 2 == 0 ? ctx->d_actA : ctx->d_actB;
+        float* dst = l == c.n_layers ? z : (l % 2 == 0 ? ctx->d_actA : ctx->d_actB);
+        for (int b = 0; b < B; ++b) {
+            in[b] = src + (size_t)b * c.widths[l - 1] * HW;
+            out[b] = dst + (size_t)b * c.widths[l] * HW;
+        }
+        const Layer& L = ctx->layers[l - 1];
+        s = launch_conv_simt(in.data(), out.data(), B, H, W, L.cin, L.cout, c.conv_ks, L.w32, L.b32,
+                             l < c.n_layers, st, ctx->err);
+        if (s) return s;
+        prof_mark(ctx, 1 + l, st);
+    }
+    return WSKPN_OK;
+}
+
+wskpn_status ctx_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
+                        cudaStream_t st) {
+    if (ctx->cfg.prec == WSKPN_FP32) return logits_fp32(ctx, frames, B, H, W, z, st);
+    return tc_logits(ctx, frames, B, H, W, z, st);
+}
+
+}  // namespace wskpn
+
+using namespace wskpn;
+
+extern "C" {
+
+const char* wskpn_version(void) { return "wskpn 0.1 (sm_103a)"; }
+
+wskpn_status wskpn_config_default(wskpn_config* cfg) {
+    if (!cfg) {
+        set_thread_error("cfg is NULL");
+        return WSKPN_EINVAL;
+    }
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->n_layers = 4;
+    const int widths[5] = {10, 32, 48, 64, 12};
+    for (int i = 0; i < 5; ++i) cfg->widths[i] = widths[i];
+    cfg->conv_ks = 5;
+    cfg->n_kernels = 6;
+    for (int i = 0; i < 6; ++i) cfg->ksizes[i] = 3 + 2 * i;
+    cfg->prec = WSKPN_BF16;
+    cfg->albedo_eps = 1e-2f;
+    cfg->gamma = 2.2f;
+    cfg->depth_near = 1.f;
+    cfg->depth_far = 10.f;
+    cfg->max_batch = 1;
+    cfg->max_h = 1080;
+    cfg->max_w = 1920;
+    return WSKPN_OK;
+}
+
+size_t wskpn_n_weights(const wskpn_config* cfg) {
+    if (!validate_config(cfg).empty()) return 0;
+    return n_weights_of(cfg);
+}
+
+wskpn_status wskpn_create(const wskpn_config* cfg, const float* host_weights, size_t n, wskpn_ctx** out) {
+    if (!out) {
+        set_thread_error("out is NULL");
+        return WSKPN_EINVAL;
+    }
+    *out = nullptr;
+    std::string v = validate_config(cfg);
+    if (!v.empty()) {
+        set_thread_error(v);
+        return WSKPN_EINVAL;
+    }
+    if (!host_weights || n != n_weights_of(cfg)) {
+        set_thread_error("weights NULL or wrong count (see wskpn_n_weights)");
+        return WSKPN_EINVAL;
+    }
+    wskpn_ctx* ctx = new wskpn_ctx();
+    ctx->cfg = *cfg;
+    ctx->nw = n;
+    wskpn_status s = ctx_init(ctx, host_weights);
+    if (s) {
+        set_thread_error(ctx->err);
+        wskpn_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return WSKPN_OK;
+}
+
+void wskpn_destroy(wskpn_ctx* ctx) {
+    if (!ctx) return;
+    ctx_free(ctx);
+    delete ctx;
+}
+
+const char* wskpn_last_error(const wskpn_ctx* ctx) { return ctx ? ctx->err.c_str() : thread_error().c_str(); }
+
+wskpn_status wskpn_set_weights(wskpn_ctx* ctx, const float* weights, size_t n, int on_device, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    if (!weights || n != ctx->nw) {
+        ctx->err = "weights NULL or wrong count";
+        return WSKPN_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    WSKPN_CUDA_TRY(cudaMemcpyAsync(ctx->d_master, weights, n * sizeof(float),
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+                   ctx->err);
+    if (!on_device) WSKPN_CUDA_TRY(cudaStreamSynchronize(st), ctx->err);  // host buffer may go away
+    return ctx_repack(ctx, st);
+}
+
+wskpn_status wskpn_get_weights(wskpn_ctx* ctx, float* dev_out, size_t n, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    if (!dev_out || n != ctx->nw) {
+        ctx->err = "dev_out NULL or wrong count";
+        return WSKPN_EINVAL;
+    }
+    WSKPN_CUDA_TRY(cudaMemcpyAsync(dev_out, ctx->d_master, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   (cudaStream_t)stream),
+                   ctx->err);
+    return WSKPN_OK;
+}
+
+wskpn_status wskpn_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w, float* z_out,
+                          void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    wskpn_status s = check_frames(ctx, frames, batch, h, w);
+    if (s) return s;
+    if (!z_out) {
+        ctx->err = "z_out is NULL";
+        return WSKPN_EINVAL;
+    }
+    prof_begin(ctx, (cudaStream_t)stream);
+    s = ctx_logits(ctx, frames, batch, h, w, z_out, (cudaStream_t)stream);
+    prof_end(ctx);
+    return s;
+}
+
+wskpn_status wskpn_denoise(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w, float* out,
+                           void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    wskpn_status s = check_frames(ctx, frames, batch, h, w);
+    if (s) return s;
+    if (!out) {
+        ctx->err = "out is NULL";
+        return WSKPN_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const wskpn_config& c = ctx->cfg;
+    prof_begin(ctx, st);
+    s = ctx_logits(ctx, frames, batch, h, w, ctx->d_z, st);
+    if (s) {
+        prof_end(ctx);
+        return s;
+    }
+    const size_t HW = (size_t)h * w;
+    std::vector<const float*> z(batch), r(batch), a(batch);
+    std::vector<float*> o(batch);
+    for (int b = 0; b < batch; ++b) {
+        z[b] = ctx->d_z + (size_t)b * 2 * c.n_kernels * HW;
+        r[b] = frames[b].radiance;
+        a[b] = frames[b].albedo;
+        o[b] = out + (size_t)b * 3 * HW;
+    }
+    s = launch_decode_fuse_fwd(z.data(), r.data(), a.data(), o.data(), batch, h, w, c.n_kernels, c.ksizes,
+                               c.albedo_eps, ctx->d_fallbacks, st, ctx->err);
+    prof_mark(ctx, c.n_layers + 2, st);
+    prof_end(ctx);
+    return s;
+}
+
+wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h, int w,
+                                float* host_out, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    wskpn_status s = check_frames(ctx, host_frames, batch, h, w);
+    if (s) return s;
+    if (!host_out) {
+        ctx->err = "host_out is NULL";
+        return WSKPN_EINVAL;
+    }
+    if (!ctx->d_stage) {
+        cudaError_t e = cudaMalloc((void**)&ctx->d_stage, ctx->ws_pixels * 13 * sizeof(float));
+        if (e != cudaSuccess) {
+            ctx->d_stage = nullptr;
+            ctx->err = std::string("staging cudaMalloc: ") + cudaGetErrorString(e);
+            return WSKPN_ENOMEM;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t HW = (size_t)h * w;
+    std::vector<wskpn_frame> dev(batch);
+    float* p = ctx->d_stage;
+    for (int b = 0; b < batch; ++b) {
+        const float* src[4] = {host_frames[b].radiance, host_frames[b].albedo, host_frames[b].normal,
+                               host_frames[b].depth};
+        const int ch[4] = {3, 3, 3, 1};
+        const float** dst[4] = {&dev[b].radiance, &dev[b].albedo, &dev[b].normal, &dev[b].depth};
+        for (int k = 0; k < 4; ++k) {
+            WSKPN_CUDA_TRY(cudaMemcpyAsync(p, src[k], ch[k] * HW * sizeof(float), cudaMemcpyHostToDevice, st),
+                           ctx->err);
+            *dst[k] = p;
+            p += ch[k] * HW;
+        }
+    }
+    float* dout = p;
+    s = wskpn_denoise(ctx, dev.data(), batch, h, w, dout, stream);
+    if (s) return s;
+    WSKPN_CUDA_TRY(cudaMemcpyAsync(host_out, dout, (size_t)batch * 3 * HW * sizeof(float), cudaMemcpyDeviceToHost,
+                                   st),
+                   ctx->err);
+    WSKPN_CUDA_TRY(cudaStreamSynchronize(st), ctx->err);
+    return WSKPN_OK;
+}
+
+wskpn_status wskpn_prep(const wskpn_frame* frames, int batch, int h, int w, float gamma, float depth_near,
+                        float depth_far, float* x0_out, void* stream) {
+    std::string err;
+    if (!frames || !x0_out || batch < 1 || h < 1 || w < 1 || !(gamma > 0.f) || !(depth_far > depth_near)) {
+        set_thread_error("wskpn_prep: invalid argument");
+        return WSKPN_EINVAL;
+    }
+    std::vector<void*> o(batch);
+    for (int b = 0; b < batch; ++b) o[b] = x0_out + (size_t)b * 10 * h * w;
+    wskpn_status s =
+        launch_prep(frames, batch, h, w, gamma, depth_near, depth_far, o.data(), 0, (cudaStream_t)stream, err);
+    if (s) set_thread_error(err);
+    return s;
+}
+
+wskpn_status wskpn_decode_fuse_fwd(const float* z, const float* radiance, const float* albedo, int batch, int h,
+                                   int w, int M, const int* ksizes, float eps, float* out,
+                                   unsigned int* fallbacks, void* stream) {
+    if (!z || !radiance || !albedo || !out || !ksizes || batch < 1 || h < 1 || w < 1 || M < 1 ||
+        M > WSKPN_MAX_KERNELS || !(eps > 0.f)) {
+        set_thread_error("wskpn_decode_fuse_fwd: invalid argument");
+        return WSKPN_EINVAL;
+    }
+    for (int i = 0; i < M; ++i)
+        if (ksizes[i] < 1 || ksizes[i] > 13 || (ksizes[i] & 1) == 0) {
+            set_thread_error("wskpn_decode_fuse_fwd: ksizes must be odd and in [1, 13]");
+            return WSKPN_EINVAL;
+        }
+    const size_t HW = (size_t)h * w;
+    std::vector<const float*> zz(batch), rr(batch), aa(batch);
+    std::vector<float*> oo(batch);
+    for (int b = 0; b < batch; ++b) {
+        zz[b] = z + (size_t)b * 2 * M * HW;
+        rr[b] = radiance + (size_t)b * 3 * HW;
+        aa[b] = albedo + (size_t)b * 3 * HW;
+        oo[b] = out + (size_t)b * 3 * HW;
+    }
+    std::string err;
+    wskpn_status s = launch_decode_fuse_fwd(zz.data(), rr.data(), aa.data(), oo.data(), batch, h, w, M, ksizes,
+                                            eps, fallbacks, (cudaStream_t)stream, err);
+    if (s) set_thread_error(err);
+    return s;
+}
+
+wskpn_status wskpn_numeric_fallbacks(wskpn_ctx* ctx, uint64_t* count) {
+    if (!ctx || !count) return WSKPN_EINVAL;
+    unsigned int v = 0;
+    WSKPN_CUDA_TRY(cudaDeviceSynchronize(), ctx->err);
+    WSKPN_CUDA_TRY(cudaMemcpy(&v, ctx->d_fallbacks, sizeof(v), cudaMemcpyDeviceToHost), ctx->err);
+    *count = v;
+    return WSKPN_OK;
+}
+
+wskpn_status wskpn_profile_enable(wskpn_ctx* ctx, int enable) {
+    if (!ctx) return WSKPN_EINVAL;
+    ctx->prof = enable != 0;
+    return WSKPN_OK;
+}
+
+wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stages, int* calls) {
+    if (!ctx || (!ms && cap > 0)) return WSKPN_EINVAL;
+    const int n = ctx->cfg.n_layers + 2;
+    std::vector<double> acc(n, 0.0);
+    for (size_t k = 0; k < ctx->prof_used; ++k) {
+        auto& ev = ctx->prof_sets[k];
+        WSKPN_CUDA_TRY(cudaEventSynchronize(ev.back()), ctx->err);
+        for (int i = 0; i < n; ++i) {
+            float t = 0.f;
+            WSKPN_CUDA_TRY(cudaEventElapsedTime(&t, ev[i], ev[i + 1]), ctx->err);
+            acc[i] += t;
+        }
+    }
+    for (int i = 0; i < n && i < cap; ++i) ms[i] = (float)acc[i];
+    if (n_stages) *n_stages = n;
+    if (calls) *calls = (int)ctx->prof_used;
+    ctx->prof_used = 0;
+    return WSKPN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Internal definition of the opaque wskpn_ctx and the helpers shared by the
+// library's translation units.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+struct wskpn_ctx;
+
+namespace wskpn {
+
+struct Layer {
+    int cin, cout;
+    size_t woff, boff;  // offsets of W and b in the FP32 master blob
+    // FP32 SIMT packing
+    float* w32 = nullptr;  // [Cin][KS*KS][COUTP]
+    float* b32 = nullptr;  // [COUTP]
+    // tensor-core packing (BF16 / FP8): the exact shared-memory image of the
+    // layer's B operand, plus per-output-channel epilogue scale and bias
+    void* wtc = nullptr;
+    size_t wtc_bytes = 0;
+    float* ep_scale = nullptr;  // [cout_p]  (FP8: act_scale_in * w_scale[o]; BF16: 1)
+    float* ep_bias = nullptr;   // [cout_p]
+    float* wscale = nullptr;    // [cout_p]  FP8 per-output-channel weight scale
+    int cin_p = 0, cout_p = 0;  // padded channel counts of the tensor-core layout
+};
+
+std::string validate_config(const wskpn_config* c);
+size_t n_weights_of(const wskpn_config* c);
+
+}  // namespace wskpn
+
+struct wskpn_ctx {
+    wskpn_config cfg{};
+    int device = 0;
+    std::string err;
+    size_t nw = 0;
+    float* d_master = nullptr;  // FP32 weight blob
+    wskpn::Layer layers[WSKPN_MAX_LAYERS];
+    size_t ws_pixels = 0;       // max_batch * max_h * max_w
+    float* d_actA = nullptr;    // FP32 planar ping buffer
+    float* d_actB = nullptr;    // FP32 planar pong buffer
+    void* d_tcA = nullptr;      // tensor-core NHWC ping buffer
+    void* d_tcB = nullptr;      // tensor-core NHWC pong buffer
+    float* d_z = nullptr;       // network output [B][2M][H][W]
+    float* d_stage = nullptr;   // host-call staging: 10 input + 3 output planes per pixel
+    unsigned int* d_fallbacks = nullptr;
+    unsigned int* d_status = nullptr;  // device status word of the tensor-core kernels
+    float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
+    // stage profiling: one event set (n_layers + 3 events) per recorded call
+    bool prof = false;
+    std::vector<std::vector<cudaEvent_t>> prof_sets;
+    size_t prof_used = 0;
+    int prof_cur = -1;  // index of the set of the call in flight, -1 = none
+};
+
+namespace wskpn {
+wskpn_status ctx_init(wskpn_ctx* ctx, const float* host_weights);
+void ctx_free(wskpn_ctx* ctx);
+wskpn_status ctx_repack(wskpn_ctx* ctx, cudaStream_t st);
+// stage profiling hooks (no-ops unless profiling is enabled)
+void prof_begin(wskpn_ctx* ctx, cudaStream_t st);
+void prof_mark(wskpn_ctx* ctx, int boundary, cudaStream_t st);  // boundary 1..n_layers+2
+void prof_end(wskpn_ctx* ctx);
+wskpn_status ctx_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
+                        cudaStream_t st);
+// tensor-core path (conv_tc.cu)
+size_t tc_act_bytes_per_pixel(const wskpn_config& c, int which /*0 = A, 1 = B*/);
+wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l);
+wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st);
+wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
+                       cudaStream_t st);
+}  // namespace wskpn

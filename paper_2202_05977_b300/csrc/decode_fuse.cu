@@ -1,0 +1,285 @@
+// Reconstruction phase (Sec. 4.2): kernel construction from importance maps
+// (Eq. 3), filtering (Eq. 4), multi-size fusion (Eq. 5) and albedo
+// re-modulation, fused into one streaming kernel that never materialises the
+// H x W x k^2 kernel map.
+//
+// Per output pixel p and size i (window Omega_i(p) clipped to the image):
+//   R_i(p) = sum_q exp(I_i(q)) y(q) / sum_q exp(I_i(q)),  y = r / (a + eps)
+// i.e. Eq. 3-4 written as the ratio of two window sums N_i / D_i.  The sums
+// are separable box sums, evaluated from a shared-memory tile with a 6-pixel
+// halo.  The exponent is shifted by the maximum of I_i over the tile's
+// window footprint; the shift cancels in N/D for every pixel.  A pixel whose
+// D_i falls below 1e-30 (the footprint's logit range exceeds ~69) is
+// recomputed exactly with its own window maximum and counted.
+#include "common.cuh"
+
+namespace wskpn {
+
+namespace df {
+constexpr int TW = 64;              // tile width (output pixels)
+constexpr int TH = 16;              // tile height
+constexpr int HALO = 6;             // largest half window (k = 13)
+constexpr int RW = TW + 2 * HALO;   // 76
+constexpr int RH = TH + 2 * HALO;   // 28
+constexpr int RP = RW + 1;          // odd row pitch: column-walking lanes hit distinct banks
+constexpr int HP = TW + 1;          // pitch of the horizontal-sum rows
+constexpr int THREADS = 256;
+constexpr int PPT = TW * TH / THREADS;  // output pixels per thread (4)
+constexpr int SMEM_FLOATS = 3 * RH * RP + 4 * RH * RP + 4 * RH * HP;
+constexpr size_t SMEM_BYTES = SMEM_FLOATS * sizeof(float);
+constexpr float DMIN = 1e-30f;
+}  // namespace df
+
+struct DecodeArgs {
+    PtrBatch<const float*> z, r, a;
+    PtrBatch<float*> out;
+    int H, W, M;
+    int ks[WSKPN_MAX_KERNELS];
+    float eps;
+    unsigned int* fallbacks;
+};
+
+// Horizontal window sums of the 4 planes (E, E*y0, E*y1, E*y2) for the rows
+// the vertical pass needs.  One thread walks one (plane, row, half-row) and
+// keeps the 32 + K - 1 inputs in registers.
+template <int K>
+__device__ __forceinline__ void hpass(const float* __restrict__ sE, float* __restrict__ sH, int tid) {
+    constexpr int h = K / 2;
+    constexpr int NR = df::TH + 2 * h;
+    for (int it = tid; it < 4 * 2 * NR; it += df::THREADS) {
+        const int row = it % NR;
+        const int half = (it / NR) & 1;
+        const int ch = it / (2 * NR);
+        const int ry = df::HALO - h + row;
+        const float* src = sE + (ch * df::RH + ry) * df::RP + (df::HALO - h) + half * 32;
+        float* dst = sH + (ch * df::RH + ry) * df::HP + half * 32;
+        float win[32 + K - 1];
+#pragma unroll
+        for (int j = 0; j < 32 + K - 1; ++j) win[j] = src[j];
+#pragma unroll
+        for (int x = 0; x < 32; ++x) {
+            float s = win[x];
+#pragma unroll
+            for (int d = 1; d < K; ++d) s += win[x + d];
+            dst[x] = s;
+        }
+    }
+}
+
+// Vertical window sums of the horizontal sums -> sV[4][TH][TW].
+template <int K>
+__device__ __forceinline__ void vpass(const float* __restrict__ sH, float* __restrict__ sV, int tid) {
+    constexpr int h = K / 2;
+    const int x = tid % df::TW;
+    const int ch = tid / df::TW;  // THREADS == 4 * TW
+    const float* src = sH + (ch * df::RH + (df::HALO - h)) * df::HP + x;
+    float col[df::TH + K - 1];
+#pragma unroll
+    for (int j = 0; j < df::TH + K - 1; ++j) col[j] = src[j * df::HP];
+#pragma unroll
+    for (int y = 0; y < df::TH; ++y) {
+        float s = col[y];
+#pragma unroll
+        for (int d = 1; d < K; ++d) s += col[y + d];
+        sV[(ch * df::TH + y) * df::TW + x] = s;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void box_sums(const float* sE, float* sH, float* sV, int tid) {
+    hpass<K>(sE, sH, tid);
+    __syncthreads();
+    vpass<K>(sH, sV, tid);
+}
+
+// Exact per-window evaluation of Eq. 3-4 for one pixel (slow path).
+__device__ void window_exact(const float* __restrict__ z, const float* __restrict__ r,
+                             const float* __restrict__ a, int H, int W, int k, float eps, int px,
+                             int py, float R[3]) {
+    const int h = k / 2;
+    const size_t HW = (size_t)H * W;
+    const int y0 = max(py - h, 0), y1 = min(py + h, H - 1);
+    const int x0 = max(px - h, 0), x1 = min(px + h, W - 1);
+    float m = -INFINITY;
+    for (int qy = y0; qy <= y1; ++qy)
+        for (int qx = x0; qx <= x1; ++qx) m = fmaxf(m, z[(size_t)qy * W + qx]);
+    float D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
+    for (int qy = y0; qy <= y1; ++qy)
+        for (int qx = x0; qx <= x1; ++qx) {
+            const size_t g = (size_t)qy * W + qx;
+            const float e = expf(z[g] - m);
+            D += e;
+            N0 += e * (r[g] / (a[g] + eps));
+            N1 += e * (r[HW + g] / (a[HW + g] + eps));
+            N2 += e * (r[2 * HW + g] / (a[2 * HW + g] + eps));
+        }
+    R[0] = N0 / D;
+    R[1] = N1 / D;
+    R[2] = N2 / D;
+}
+
+__global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeArgs args) {
+    extern __shared__ float smem[];
+    float* sY = smem;                          // [3][RH][RP]  irradiance y
+    float* sE = sY + 3 * df::RH * df::RP;      // [4][RH][RP]  E, E*y  (reused as sV)
+    float* sH = sE + 4 * df::RH * df::RP;      // [4][RH][HP]  horizontal sums
+    float* sV = sE;                            // [4][TH][TW]
+    __shared__ float red[df::THREADS / 32];
+
+    const int tid = threadIdx.x;
+    const int b = blockIdx.z;
+    const int H = args.H, W = args.W, M = args.M;
+    const size_t HW = (size_t)H * W;
+    const int tx0 = blockIdx.x * df::TW, ty0 = blockIdx.y * df::TH;
+    const float* __restrict__ z = args.z.p[b];
+    const float* __restrict__ r = args.r.p[b];
+    const float* __restrict__ a = args.a.p[b];
+    const float eps = args.eps;
+
+    // Demodulated irradiance on the tile + halo (0 outside the image).
+    for (int i = tid; i < df::RH * df::RW; i += df::THREADS) {
+        const int ry = i / df::RW, rx = i % df::RW;
+        const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const size_t g = (size_t)gy * W + gx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            sY[(c * df::RH + ry) * df::RP + rx] = in ? r[c * HW + g] / (a[c * HW + g] + eps) : 0.f;
+    }
+
+    // Fusion weights alpha_i(p): softmax of the M logits of each own pixel.
+    float alpha[df::PPT][WSKPN_MAX_KERNELS];
+    float acc[df::PPT][3];
+#pragma unroll
+    for (int j = 0; j < df::PPT; ++j) {
+        const int p = tid + j * df::THREADS;
+        const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
+        const bool in = gy < H && gx < W;
+        float m = -INFINITY;
+#pragma unroll
+        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) {
+            alpha[j][i] = (i < M && in) ? z[(size_t)(M + i) * HW + (size_t)gy * W + gx] : -INFINITY;
+            m = fmaxf(m, alpha[j][i]);
+        }
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) {
+            alpha[j][i] = (i < M && in) ? expf(alpha[j][i] - m) : 0.f;
+            s += alpha[j][i];
+        }
+#pragma unroll
+        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) alpha[j][i] = in ? alpha[j][i] / s : 0.f;
+        acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
+    }
+
+    for (int i = 0; i < M; ++i) {
+        const int k = args.ks[i];
+        const int h = k / 2;
+        const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
+        const float* __restrict__ zi = z + (size_t)i * HW;
+        // Footprint of this size's windows: load I_i, find its maximum.
+        float m = -INFINITY;
+        for (int t = tid; t < nr * nc; t += df::THREADS) {
+            const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
+            const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
+            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const float v = in ? zi[(size_t)gy * W + gx] : -INFINITY;
+            sE[ry * df::RP + rx] = v;
+            m = fmaxf(m, v);
+        }
+        m = warp_max(m);
+        if ((tid & 31) == 0) red[tid >> 5] = m;
+        __syncthreads();
+        m = red[0];
+#pragma unroll
+        for (int w = 1; w < df::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+        // E = exp(I - m) and E*y on the footprint (E = 0 outside the image).
+        for (int t = tid; t < nr * nc; t += df::THREADS) {
+            const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
+            const int o = ry * df::RP + rx;
+            const float e = expf(sE[o] - m);
+            sE[o] = e;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                sE[(1 + c) * df::RH * df::RP + o] = e * sY[c * df::RH * df::RP + o];
+        }
+        __syncthreads();
+        switch (k) {
+            case 1: box_sums<1>(sE, sH, sV, tid); break;
+            case 3: box_sums<3>(sE, sH, sV, tid); break;
+            case 5: box_sums<5>(sE, sH, sV, tid); break;
+            case 7: box_sums<7>(sE, sH, sV, tid); break;
+            case 9: box_sums<9>(sE, sH, sV, tid); break;
+            case 11: box_sums<11>(sE, sH, sV, tid); break;
+            default: box_sums<13>(sE, sH, sV, tid); break;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < df::PPT; ++j) {
+            const int p = tid + j * df::THREADS;
+            const int ly = p / df::TW, lx = p % df::TW;
+            const int gy = ty0 + ly, gx = tx0 + lx;
+            if (gy >= H || gx >= W) continue;
+            const float D = sV[ly * df::TW + lx];
+            float R[3];
+            if (D >= df::DMIN) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) R[c] = sV[((1 + c) * df::TH + ly) * df::TW + lx] / D;
+            } else {
+                window_exact(zi, r, a, H, W, k, eps, gx, gy, R);
+                if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
+            }
+            float al = 0.f;
+#pragma unroll
+            for (int q = 0; q < WSKPN_MAX_KERNELS; ++q)
+                if (q == i) al = alpha[j][q];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[j][c] = fmaf(al, R[c], acc[j][c]);
+        }
+        __syncthreads();
+    }
+
+    // Re-modulation and store.
+    float* __restrict__ out = args.out.p[b];
+#pragma unroll
+    for (int j = 0; j < df::PPT; ++j) {
+        const int p = tid + j * df::THREADS;
+        const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
+        if (gy >= H || gx >= W) continue;
+        const size_t g = (size_t)gy * W + gx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c * HW + g] = (a[c * HW + g] + eps) * acc[j][c];
+    }
+}
+
+// Host launcher: z/r/a/out given per frame.
+wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r,
+                                    const float* const* a, float* const* out, int B, int H, int W,
+                                    int M, const int* ks, float eps, unsigned int* fallbacks,
+                                    cudaStream_t st, std::string& err) {
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)df::SMEM_BYTES),
+                   err);
+    for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
+        const int nb = B - b0 < WSKPN_MAX_BATCH ? B - b0 : WSKPN_MAX_BATCH;
+        DecodeArgs args{};
+        for (int j = 0; j < nb; ++j) {
+            args.z.p[j] = z[b0 + j];
+            args.r.p[j] = r[b0 + j];
+            args.a.p[j] = a[b0 + j];
+            args.out.p[j] = out[b0 + j];
+        }
+        args.H = H;
+        args.W = W;
+        args.M = M;
+        for (int i = 0; i < M; ++i) args.ks[i] = ks[i];
+        args.eps = eps;
+        args.fallbacks = fallbacks;
+        dim3 grid(cdiv(W, df::TW), cdiv(H, df::TH), nb);
+        decode_fuse_fwd_kernel<<<grid, df::THREADS, df::SMEM_BYTES, st>>>(args);
+        WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    }
+    return WSKPN_OK;
+}
+
+}  // namespace wskpn

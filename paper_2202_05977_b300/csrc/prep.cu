@@ -1,0 +1,96 @@
+// Input assembly (Sec. 5.1): the ImportanceNet's 10 input channels are the
+// gamma tone-mapped LDR radiance clamp(r,0,1)^(1/gamma), the albedo, the
+// normal linearly scaled from [-1,1] to [0,1] and the depth linearly scaled
+// from [near,far] to [0,1].
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace wskpn {
+
+struct PrepArgs {
+    FrameBatch f;
+    PtrBatch<void*> out;
+    int H, W;
+    float inv_gamma, dnear, dscale;  // dscale = 1 / (far - near)
+};
+
+__device__ __forceinline__ void prep_pixel(const PrepArgs& a, int b, size_t g, size_t HW, float v[10]) {
+    const float* r = a.f.r.p[b];
+    const float* al = a.f.a.p[b];
+    const float* n = a.f.n.p[b];
+    const float* d = a.f.d.p[b];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float t = fminf(fmaxf(r[c * HW + g], 0.f), 1.f);
+        v[c] = powf(t, a.inv_gamma);
+        v[3 + c] = al[c * HW + g];
+        v[6 + c] = 0.5f * n[c * HW + g] + 0.5f;
+    }
+    v[9] = (d[g] - a.dnear) * a.dscale;
+}
+
+// Planar FP32 output [10][H][W] (the FP32 path's layout).
+__global__ void prep_planar_kernel(PrepArgs a) {
+    const int b = blockIdx.y;
+    const size_t HW = (size_t)a.H * a.W;
+    float* out = static_cast<float*>(a.out.p[b]);
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < HW; g += (size_t)gridDim.x * blockDim.x) {
+        float v[10];
+        prep_pixel(a, b, g, HW, v);
+#pragma unroll
+        for (int c = 0; c < 10; ++c) out[c * HW + g] = v[c];
+    }
+}
+
+// Channels-last BF16 output [H][W][16] (channels 10..15 zero): the tensor
+// core path's layout, one 32-byte row per pixel.
+__global__ void prep_nhwc16_bf16_kernel(PrepArgs a) {
+    const int b = blockIdx.y;
+    const size_t HW = (size_t)a.H * a.W;
+    uint4* out = static_cast<uint4*>(a.out.p[b]);
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < HW; g += (size_t)gridDim.x * blockDim.x) {
+        float v[10];
+        prep_pixel(a, b, g, HW, v);
+        __nv_bfloat162 h[8];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+#pragma unroll
+        for (int j = 5; j < 8; ++j) h[j] = __floats2bfloat162_rn(0.f, 0.f);
+        const uint4* hv = reinterpret_cast<const uint4*>(h);
+        out[2 * g] = hv[0];
+        out[2 * g + 1] = hv[1];
+    }
+}
+
+wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear,
+                         float dfar, void* const* out, int layout, cudaStream_t st, std::string& err) {
+    for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
+        const int nb = B - b0 < WSKPN_MAX_BATCH ? B - b0 : WSKPN_MAX_BATCH;
+        PrepArgs a{};
+        for (int j = 0; j < nb; ++j) {
+            a.f.r.p[j] = frames[b0 + j].radiance;
+            a.f.a.p[j] = frames[b0 + j].albedo;
+            a.f.n.p[j] = frames[b0 + j].normal;
+            a.f.d.p[j] = frames[b0 + j].depth;
+            a.out.p[j] = out[b0 + j];
+        }
+        a.H = H;
+        a.W = W;
+        a.inv_gamma = (float)(1.0 / (double)gamma);
+        a.dnear = dnear;
+        a.dscale = (float)(1.0 / ((double)dfar - (double)dnear));
+        const size_t HW = (size_t)H * W;
+        int blocks = (int)((HW + 255) / 256);
+        if (blocks > 148 * 8) blocks = 148 * 8;
+        dim3 grid(blocks, nb);
+        if (layout == 0)
+            prep_planar_kernel<<<grid, 256, 0, st>>>(a);
+        else
+            prep_nhwc16_bf16_kernel<<<grid, 256, 0, st>>>(a);
+        WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    }
+    return WSKPN_OK;
+}
+
+}  // namespace wskpn

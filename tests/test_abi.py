@@ -1,0 +1,72 @@
+"""The C-ABI library loads and exports every symbol include/wskpn.h
+declares; argument validation that needs no GPU.  CPU only."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2202_05977_b300 as wk
+from paper_2202_05977_b300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(wskpn_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding declares exactly the header's functions
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_default_config_and_weight_count():
+    c = wk.default_config()
+    assert c.n_layers == 4 and list(c.widths[:5]) == [10, 32, 48, 64, 12]
+    assert c.conv_ks == 5 and c.n_kernels == 6 and list(c.ksizes[:6]) == [3, 5, 7, 9, 11, 13]
+    assert wk.n_weights(c) == 142556          # 25 * (10*32 + 32*48 + 48*64 + 64*12) + 156
+    assert wk.n_weights(wk.default_config(conv_ks=3)) == 51420
+    assert _lib.load().wskpn_version().startswith(b"wskpn")
+
+
+@pytest.mark.parametrize("field,value", [("conv_ks", 4), ("n_kernels", 0), ("albedo_eps", 0.0),
+                                         ("max_batch", 0), ("n_layers", 9)])
+def test_invalid_config_is_rejected_without_touching_the_gpu(field, value):
+    lib = _lib.load()
+    c = wk.default_config()
+    setattr(c, field, value)
+    assert lib.wskpn_n_weights(ctypes.byref(c)) == 0
+    h = ctypes.c_void_p()
+    w = np.zeros(142556, np.float32)
+    s = lib.wskpn_create(ctypes.byref(c), w.ctypes.data, w.size, ctypes.byref(h))
+    assert s == _lib.EINVAL and not h.value
+    assert lib.wskpn_last_error(None)
+
+
+def test_even_kernel_size_rejected():
+    lib = _lib.load()
+    ks = (ctypes.c_int * 2)(3, 4)
+    s = lib.wskpn_decode_fuse_fwd(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 4, 4, 2,
+                                  ks, 0.01, ctypes.c_void_p(16), None, None)
+    assert s == _lib.EINVAL
+    assert b"odd" in lib.wskpn_last_error(None)
+
+
+def test_null_arguments_rejected():
+    lib = _lib.load()
+    assert lib.wskpn_denoise(None, None, 1, 4, 4, None, None) == _lib.EINVAL
+    assert lib.wskpn_create(None, None, 0, None) == _lib.EINVAL
+    lib.wskpn_destroy(None)
