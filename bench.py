@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the weight-sharing kernel-prediction denoiser on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp8|fp32]
+    python bench.py --impl reference ...      # the FP64 CPU oracle as the reference arm
+
+One step = one full denoise (Sec. 5.1 input assembly, the ImportanceNet
+convolutions, Eq. 3-5 reconstruction) of a synthetic 1920x1080 1-spp frame
+(seed 2, batch 1), inputs resident in HBM.  Prints ONE JSON line.
+
+Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
+launching stream; a 256 MiB buffer (> the 126 MB L2) is rewritten between
+timed steps, outside the events.  Per-stage times come from the library's
+own stage events (wskpn_profile_*), recorded on the same stream.  With N>1
+(torchrun) every rank denoises its own frames (replicas only, no
+collective on the data path); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1080p denoise ms/frame (BF16 vs FP32 plain); p50/p99 frame latency in serving"
+UNIT = "ms/frame"
+H, W, SEED = 1080, 1920, 2
+WIDTHS = (10, 32, 48, 64, 12)
+KS = 5
+KSIZES = (3, 5, 7, 9, 11, 13)
+# algorithmic bytes per pixel of the reconstruction kernel: logits (12 x 4)
+# + radiance (3 x 4) + albedo (3 x 4) read, output (3 x 4) written
+DECODE_BYTES_PER_PX = 84
+FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 148, 2032.0
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures
+# of the current kernels (None until captured for this kernel version)
+TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="wskpn", choices=["wskpn", "reference"])
+    p.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
+    p.add_argument("--no-fp32", action="store_true", help="skip the FP32 plain-path comparison")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "source": "fallback"}
+
+
+def conv_flops(l, h=H, w=W):
+    return 2.0 * WIDTHS[l] * WIDTHS[l + 1] * KS * KS * h * w
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on bounded row bands of the same
+    1080p frame; each step denoises ROWS rows and is scaled to ms/frame."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    rows = 16
+    f = synth.make_frame(H, W, SEED)
+    wb = synth.make_weights(WIDTHS, KS, seed=SEED)
+    times = []
+    for i in range(args.warmup + args.steps):
+        y0 = (H // 2 + 37 * i) % (H - rows)
+        t0 = time.perf_counter()
+        oracle.denoise(f, wb, widths=WIDTHS, ks=KS, ksizes=KSIZES, rect=(0, y0, W, y0 + rows))
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    ms_frame = statistics.mean(times) * 1e3 * H / rows
+    sample = f"{args.steps} bands of {rows} x {W} px (rows near the middle) of the 1920x1080 seed-2 frame, " \
+             f"scaled x{H // rows} to a full frame"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms_frame, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block("fp64 oracle"),
+        "cpu_baseline": {"value": ms_frame, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": ms_frame, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block(precision):
+    return {"workload": "synthetic 1-spp frame 1920x1080, seed 2, batch 1 (BMFR-like stand-in)",
+            "resolution": f"{W}x{H}", "batch": 1, "precision": precision,
+            "network": "ImportanceNet 3 blocks 10-32-48-64 + output conv to 12, 5x5 convs",
+            "kernel_sizes": list(KSIZES), "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def cpu_baseline(budget_s=12.0):
+    import oracle
+    import synth
+    f = synth.make_frame(H, W, SEED)
+    wb = synth.make_weights(WIDTHS, KS, seed=SEED)
+    rows, done, t0 = 16, 0, time.perf_counter()
+    y0 = H // 2
+    while time.perf_counter() - t0 < budget_s and done < H:
+        oracle.denoise(f, wb, widths=WIDTHS, ks=KS, ksizes=KSIZES, rect=(0, y0, W, y0 + rows))
+        done += rows
+        y0 = (y0 + rows) % (H - rows)
+    el = time.perf_counter() - t0
+    return {"value": el * 1e3 * H / done, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} rows x {W} px of the 1920x1080 seed-2 frame ({el:.1f} s), scaled to a full frame"}
+
+
+# --------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2202_05977_b300 as wk
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    f = synth.make_frame(H, W, SEED + 1000 * rank)
+    wb = synth.make_weights(WIDTHS, KS, seed=SEED)
+    keys = ("radiance", "albedo", "normal", "depth")
+    xin = [torch.from_numpy(np.ascontiguousarray(f[k][None])).to(dev) for k in keys]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pk = peaks()
+
+    def time_path(precision, steps, warmup):
+        d = wk.Denoiser(wb, precision=precision, max_hw=(H, W))
+        out = torch.empty((1, 3, H, W), device=dev)
+        for _ in range(warmup):
+            d.denoise(*xin, out=out)
+        torch.cuda.synchronize()
+        barrier()
+        d.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t_wall = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record()
+            d.denoise(*xin, out=out)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        barrier()
+        d.profile(False)
+        stage_ms, calls = d.profile_read()
+        per = [a.elapsed_time(b) for a, b in ev]
+        total = torch.tensor([sum(per)], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(total, op=dist.ReduceOp.MAX)
+        res = {"ms_step": total.item() / steps, "per": per, "stage_ms": [s / max(calls, 1) for s in stage_ms],
+               "wall_s": t_wall, "out": out, "d": d}
+        return res
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = ClockSampler(uuid)
+    clk.start()
+    main_res = time_path(args.precision, args.steps, args.warmup)
+    clocks = clk.stop()
+
+    fp32 = None
+    if not args.no_fp32 and args.precision != "fp32":
+        fp32 = time_path("fp32", max(3, args.steps // 4), 3)
+
+    # roofline of the dominant stage (stage 0 prep, 1..L convs, L+1 reconstruction)
+    st = main_res["stage_ms"]
+    dom = max(range(len(st)), key=lambda i: st[i])
+    if 1 <= dom <= len(WIDTHS) - 1:
+        l = dom - 1
+        flops = conv_flops(l)
+        achieved = flops / (st[dom] * 1e-3) / 1e12
+        if args.precision == "fp32":
+            peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            bound, psrc = "alu", "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz"
+        else:
+            peak = pk["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
+            bound, psrc = "tensor", f"{pk['source']} bf16 burst" + (" x2 (fp8 nominal ratio)" if args.precision == "fp8" else "")
+        kname = f"conv{l + 1} ({WIDTHS[l]}->{WIDTHS[l + 1]})"
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC.get((args.precision, kname)), "kernel": kname, "peak_source": psrc}
+    else:
+        name = "prep" if dom == 0 else "decode_fuse_fwd"
+        byts = (40 + {"fp32": 40, "bf16": 32, "fp8": 32}[args.precision]) * H * W if dom == 0 \
+            else DECODE_BYTES_PER_PX * H * W
+        achieved = byts / (st[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": TRAFFIC.get((args.precision, name)), "kernel": name,
+                "peak_source": pk["source"] + " copy bandwidth"}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        d = main_res["d"]
+        hin = [t.cpu().pin_memory() for t in xin]
+        hout = torch.empty((1, 3, H, W), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            d.denoise_host(*hin, hout)
+        barrier()
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            t0 = time.perf_counter()
+            d.denoise_host(*hin, hout)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        tt = torch.tensor([statistics.mean(ts)], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": tt.item() / world, "unit": UNIT, "h2d_bytes_per_step": 40 * H * W,
+               "d2h_bytes_per_step": 12 * H * W, "per_rank_ms_per_frame": tt.item()}
+
+    if rank == 0:
+        L = len(WIDTHS) - 1
+        stage_names = ["prep"] + [f"conv{l + 1}" for l in range(L)] + ["reconstruct"]
+        line = {
+            "metric": METRIC,
+            "value": main_res["ms_step"] / world,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": main_res["ms_step"],
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": args.precision,
+            "data": "synthetic",
+            "config": config_block(args.precision),
+            "fps": 1e3 * world / main_res["ms_step"],
+            "stages_ms": dict(zip(stage_names, main_res["stage_ms"])),
+            "prediction_ms": sum(main_res["stage_ms"][:L + 1]),
+            "reconstruction_ms": main_res["stage_ms"][L + 1],
+            "p50_step_ms": statistics.median(main_res["per"]),
+            "roofline": roof,
+            "gpu_launches": args.steps * (L + 2),
+            "clocks": clocks,
+        }
+        if fp32 is not None:
+            line["fp32_ms_per_frame"] = fp32["ms_step"] / world
+            line["speedup_vs_fp32"] = fp32["ms_step"] / main_res["ms_step"]
+            line["fp32_stages_ms"] = dict(zip(stage_names, fp32["stage_ms"]))
+        if e2e is not None:
+            line["e2e"] = e2e
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
