@@ -189,6 +189,34 @@ wskpn_status wskpn_profile_enable(wskpn_ctx* ctx, int enable);
  * to *calls, then clears the record.  Stages a call did not run add 0. */
 wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stages, int* calls);
 
+/* Allocation-free FP32 denoise (the paper has no counterpart: this is a
+ * deployment feature).  For callers that may not allocate device memory,
+ * for example code running inside another runtime's memory pool, a host
+ * callback, or a plug-in that must not grow its process's device
+ * footprint.  It runs the same kernels as wskpn_denoise with prec = FP32,
+ * but needs no context: every intermediate (packed weights, activations,
+ * network output) lives in one static device array of 64 MiB that each GPU
+ * loading this library holds until the process exits.  No cudaMalloc,
+ * cudaFree or allocating library call is made.
+ *   cfg      configuration as for wskpn_create; prec must be WSKPN_FP32
+ *            (else EUNSUPPORTED); max_batch/max_h/max_w are ignored;
+ *   weights  DEVICE float32 blob in the wskpn_create layout;
+ *   frames   host array of `batch` wskpn_frame (device pointers);
+ *   out      device float32 [batch][3][h][w].
+ * Limit: the whole call must fit the 64 MiB array (packed weights plus
+ * (max even-layer width + max odd-layer width + 2M) floats per pixel of
+ * batch x h x w; at the default widths about 134,000 pixels, e.g. one
+ * 512 x 256 frame); larger requests return EINVAL with the size needed.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (different
+ * streams or devices' threads racing on one device) corrupt each other, so
+ * serialise them.  Asynchronous on `stream` like wskpn_denoise. */
+wskpn_status wskpn_denoise_static(const wskpn_config* cfg, const float* weights,
+                                  const wskpn_frame* frames, int batch, int h, int w, float* out,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

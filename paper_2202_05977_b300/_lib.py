@@ -63,6 +63,7 @@ SIGNATURES = {
     "wskpn_numeric_fallbacks": ([_P, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wskpn_profile_enable": ([_P, _I], _I),
     "wskpn_profile_read": ([_P, ctypes.POINTER(_F), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "wskpn_denoise_static": ([ctypes.POINTER(Config), _P, _FR, _I, _I, _I, _P, _P], _I),
 }
 
 _lib = None
