@@ -189,6 +189,26 @@ wskpn_status wskpn_profile_enable(wskpn_ctx* ctx, int enable);
  * to *calls, then clears the record.  Stages a call did not run add 0. */
 wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stages, int* calls);
 
+/* Tuning knobs of the tensor-core convolution (for tests and benchmarks).
+ *   WSKPN_TUNE_TC_MODE: how the A operand (input pixels) is staged:
+ *     0 = one TMA box of 128 + KS - 1 pixels per input row and channel
+ *         chunk, shared by the KS horizontal taps through operand
+ *         descriptors shifted by whole pixel rows;
+ *     1 = KS aligned TMA boxes of 128 pixels, one per horizontal tap.
+ *   WSKPN_TUNE_TC_DESC_BASE_OFFSET: 0/1, fill the shared-memory descriptor's
+ *     base-offset field from the operand start address (mode 0).
+ * Errors: EINVAL for an unknown key or value. */
+#define WSKPN_TUNE_TC_MODE 1
+#define WSKPN_TUNE_TC_DESC_BASE_OFFSET 2
+wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
+
+/* Reads and clears the context's device status word after synchronising
+ * the device.  Bits 0..2: a bounded wait inside the tensor-core convolution
+ * expired in its TMA, MMA or epilogue role (the kernel gave up instead of
+ * hanging; its output is invalid).  Returns WSKPN_ETIMEOUT when any bit
+ * was set, WSKPN_OK otherwise. */
+wskpn_status wskpn_device_status(wskpn_ctx* ctx, uint32_t* bits);
+
 /* Allocation-free FP32 denoise (the paper has no counterpart: this is a
  * deployment feature).  For callers that may not allocate device memory,
  * for example code running inside another runtime's memory pool, a host

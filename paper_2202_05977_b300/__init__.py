@@ -162,6 +162,17 @@ class Denoiser:
         self._check(self._lib.wskpn_profile_read(self._h, ms, len(ms), ctypes.byref(n), ctypes.byref(calls)))
         return [ms[i] for i in range(n.value)], calls.value
 
+    def set_tuning(self, key: int, value: int):
+        self._check(self._lib.wskpn_set_tuning(self._h, key, value))
+
+    def device_status(self) -> int:
+        """Reads and clears the device status word (0 = no bounded wait expired)."""
+        v = ctypes.c_uint32()
+        s = self._lib.wskpn_device_status(self._h, ctypes.byref(v))
+        if s not in (_lib.OK, _lib.ETIMEOUT):
+            self._check(s)
+        return int(v.value)
+
     def numeric_fallbacks(self) -> int:
         v = ctypes.c_uint64()
         self._check(self._lib.wskpn_numeric_fallbacks(self._h, ctypes.byref(v)))

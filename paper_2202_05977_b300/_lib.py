@@ -14,6 +14,7 @@ MAX_BATCH = 16
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EBUSY, ETIMEOUT, ENUMERIC = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EBUSY", "ETIMEOUT", "ENUMERIC"]
 FP32, BF16, FP8 = 0, 1, 2
+TUNE_TC_MODE, TUNE_TC_DESC_BASE_OFFSET = 1, 2
 
 
 class Config(ctypes.Structure):
@@ -63,6 +64,8 @@ SIGNATURES = {
     "wskpn_numeric_fallbacks": ([_P, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wskpn_profile_enable": ([_P, _I], _I),
     "wskpn_profile_read": ([_P, ctypes.POINTER(_F), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "wskpn_set_tuning": ([_P, _I, _I], _I),
+    "wskpn_device_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I),
     "wskpn_denoise_static": ([ctypes.POINTER(Config), _P, _FR, _I, _I, _I, _P, _P], _I),
 }
 

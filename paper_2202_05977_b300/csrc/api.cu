@@ -416,4 +416,32 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
     return WSKPN_OK;
 }
 
+wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
+    if (!ctx) return WSKPN_EINVAL;
+    if (key == WSKPN_TUNE_TC_MODE && (value == 0 || value == 1)) {
+        ctx->tc_mode = value;
+        return WSKPN_OK;
+    }
+    if (key == WSKPN_TUNE_TC_DESC_BASE_OFFSET && (value == 0 || value == 1)) {
+        ctx->tc_desc_base_offset = value;
+        return WSKPN_OK;
+    }
+    ctx->err = "wskpn_set_tuning: unknown key or value";
+    return WSKPN_EINVAL;
+}
+
+wskpn_status wskpn_device_status(wskpn_ctx* ctx, uint32_t* bits) {
+    if (!ctx) return WSKPN_EINVAL;
+    unsigned int v = 0;
+    WSKPN_CUDA_TRY(cudaDeviceSynchronize(), ctx->err);
+    WSKPN_CUDA_TRY(cudaMemcpy(&v, ctx->d_status, sizeof(v), cudaMemcpyDeviceToHost), ctx->err);
+    WSKPN_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(v)), ctx->err);
+    if (bits) *bits = v;
+    if (v) {
+        ctx->err = "a bounded wait in the tensor-core convolution expired (status " + std::to_string(v) + ")";
+        return WSKPN_ETIMEOUT;
+    }
+    return WSKPN_OK;
+}
+
 }  // extern "C"

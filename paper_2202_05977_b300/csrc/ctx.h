@@ -49,6 +49,8 @@ struct wskpn_ctx {
     unsigned int* d_fallbacks = nullptr;
     unsigned int* d_status = nullptr;  // device status word of the tensor-core kernels
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
+    int tc_mode = 1;              // tensor-core conv A-operand staging (WSKPN_TUNE_TC_MODE)
+    int tc_desc_base_offset = 0;  // WSKPN_TUNE_TC_DESC_BASE_OFFSET
     // stage profiling: one event set (n_layers + 3 events) per recorded call
     bool prof = false;
     std::vector<std::vector<cudaEvent_t>> prof_sets;
