@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 plain-path comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--tc-mode", type=int, default=None, help="tensor-core A staging mode (0 shifted box, 1 aligned)")
+    p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
     return p.parse_args()
 
 
@@ -215,8 +215,8 @@ def main():
 
     def time_path(precision, steps, warmup):
         d = wk.Denoiser(wb, precision=precision, max_hw=(H, W))
-        if args.tc_mode is not None and precision != "fp32":
-            d.set_tuning(1, args.tc_mode)
+        if args.tc_split is not None and precision == "bf16":
+            d.set_tuning(2, args.tc_split)
         out = torch.empty((1, 3, H, W), device=dev)
         for _ in range(warmup):
             d.denoise(*xin, out=out)

@@ -171,6 +171,55 @@ wskpn_status wskpn_decode_fuse_fwd(const float* z, const float* radiance, const 
                                    int batch, int h, int w, int M, const int* ksizes, float eps,
                                    float* out, unsigned int* fallbacks, void* stream);
 
+/* ---- Differentiation (one training step of Eq. 1) ------------------ */
+
+/* Floats of scratch that wskpn_decode_fuse_bwd needs: (5M + 3) x batch x h
+ * x w (0 for invalid sizes). */
+size_t wskpn_decode_fuse_bwd_scratch_floats(int batch, int h, int w, int M);
+
+/* Backward of wskpn_decode_fuse_fwd (chain rule through Eq. 3-5):
+ *   dout     device [batch][3][h][w], dL/d(out);
+ *   dz       device [batch][2M][h][w] output: dL/dz (importance maps, then
+ *            fusion logits);
+ *   scratch  device buffer of wskpn_decode_fuse_bwd_scratch_floats floats,
+ *            owned by the caller and overwritten;
+ * other arguments as wskpn_decode_fuse_fwd.  Errors: EINVAL, ECUDA. */
+wskpn_status wskpn_decode_fuse_bwd(const float* z, const float* radiance, const float* albedo,
+                                   const float* dout, int batch, int h, int w, int M,
+                                   const int* ksizes, float eps, float* dz, float* scratch,
+                                   unsigned int* fallbacks, void* stream);
+
+/* Forward pass for training: out [batch][3][h][w] as wskpn_denoise, and the
+ * network output z_saved [batch][2M][h][w] (device, caller-owned) that
+ * wskpn_backward needs.  No activation is kept. */
+wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
+                                 float* out, float* z_saved, void* stream);
+
+/* Backward pass: from dout = dL/d(out) [batch][3][h][w] and z_saved,
+ * writes dL/dweights (device, wskpn_n_weights floats, blob layout) and,
+ * if dz_out is not NULL, dL/dz [batch][2M][h][w].  The activations are
+ * recomputed from the frames in FP32 and the convolution gradients run in
+ * FP32; the ReLU derivative at 0 is 0.  The first training call on a
+ * context allocates its training workspaces.  batch <= 16.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
+                            const float* z_saved, const float* dout, float* dz_out, float* dweights,
+                            void* stream);
+
+/* L1 loss over n elements: *loss (device float) = sum |out - target| / n,
+ * and, if dout is not NULL, dout = sign(out - target) / n (sign(0) = 0).
+ * Deterministic (fixed-order reduction).  Errors: EINVAL, ENOMEM, ECUDA. */
+wskpn_status wskpn_l1_loss(wskpn_ctx* ctx, const float* out, const float* target, size_t n,
+                           float* loss, float* dout, void* stream);
+
+/* One Adam step (Kingma & Ba; the optimiser of Sec. 5.3) on the context's
+ * FP32 master weights with gradient dweights (device, wskpn_n_weights
+ * floats); step counts from 1 and drives the bias correction; the moments
+ * live in the context (zero at the first call).  Re-packs the weights for
+ * the configured precision.  Errors: EINVAL, ENOMEM, ECUDA. */
+wskpn_status wskpn_adam_step(wskpn_ctx* ctx, const float* dweights, float lr, float beta1,
+                             float beta2, float eps, int step, void* stream);
+
 /* Numeric fallback counter of ctx (pixels x sizes that took the slow exact
  * softmax path since creation); synchronises the context's device. */
 wskpn_status wskpn_numeric_fallbacks(wskpn_ctx* ctx, uint64_t* count);
@@ -189,17 +238,13 @@ wskpn_status wskpn_profile_enable(wskpn_ctx* ctx, int enable);
  * to *calls, then clears the record.  Stages a call did not run add 0. */
 wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stages, int* calls);
 
-/* Tuning knobs of the tensor-core convolution (for tests and benchmarks).
- *   WSKPN_TUNE_TC_MODE: how the A operand (input pixels) is staged:
- *     0 = one TMA box of 128 + KS - 1 pixels per input row and channel
- *         chunk, shared by the KS horizontal taps through operand
- *         descriptors shifted by whole pixel rows;
- *     1 = KS aligned TMA boxes of 128 pixels, one per horizontal tap.
- *   WSKPN_TUNE_TC_DESC_BASE_OFFSET: 0/1, fill the shared-memory descriptor's
- *     base-offset field from the operand start address (mode 0).
+/* Tuning knob of the tensor-core convolution (for tests and benchmarks).
+ *   WSKPN_TUNE_TC_SPLIT (BF16 only): 1 = store every BF16 activation as a
+ *     hi/lo pair (x = hi + lo, both BF16) and run the K loop over both
+ *     halves against the same BF16 weights, which removes the activation
+ *     rounding error at twice the MMA work (default); 0 = one BF16 value.
  * Errors: EINVAL for an unknown key or value. */
-#define WSKPN_TUNE_TC_MODE 1
-#define WSKPN_TUNE_TC_DESC_BASE_OFFSET 2
+#define WSKPN_TUNE_TC_SPLIT 2
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
 
 /* Reads and clears the context's device status word after synchronising

@@ -274,6 +274,19 @@ def smape_loss(out, target, eps: float = 0.01):
     return float((num / den).sum() / n), g
 
 
+# ------------------------------------------------------------------ Adam
+def adam_step(w, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, Algorithm 1; the optimiser named in
+    Sec. 5.3): biased moments, bias correction by 1 - beta^step, update
+    w - lr * mhat / (sqrt(vhat) + eps).  Returns (w, m, v)."""
+    w, g, m, v = _d(w), _d(g), _d(m), _d(v)
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    return w - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
 # ------------------------------------------------------- one training step
 def forward_train(frame, weights, widths=DEFAULT_WIDTHS, ks: int = 5, ksizes=DEFAULT_KSIZES,
                   eps=DEFAULT_EPS, gamma=DEFAULT_GAMMA, dnear=DEPTH_NEAR, dfar=DEPTH_FAR):

@@ -13,7 +13,7 @@ import ctypes
 from . import _lib
 from ._lib import BF16, FP8, FP32, WskpnError
 
-__all__ = ["Denoiser", "decode_fuse_fwd", "prep", "default_config", "n_weights", "WskpnError",
+__all__ = ["Denoiser", "decode_fuse_fwd", "decode_fuse_bwd", "prep", "default_config", "n_weights", "WskpnError",
            "FP32", "BF16", "FP8", "PRECISIONS"]
 
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8}
@@ -151,6 +151,44 @@ class Denoiser:
         self._check(self._lib.wskpn_get_weights(self._h, _dev_f32(out, "out"), self.nw, _stream(stream)))
         return out
 
+    # ------------------------------------------------------------ training
+    def forward_train(self, radiance, albedo, normal, depth, out=None, z=None, stream=None):
+        """Forward for training: (out [B,3,H,W], z [B,2M,H,W]); z is what backward needs."""
+        import torch
+        fr, B, H, W = _frames(radiance, albedo, normal, depth)
+        if out is None:
+            out = torch.empty((B, 3, H, W), device=radiance.device, dtype=torch.float32)
+        if z is None:
+            z = torch.empty((B, 2 * self.M, H, W), device=radiance.device, dtype=torch.float32)
+        self._check(self._lib.wskpn_forward_train(self._h, fr, B, H, W, _dev_f32(out, "out"), _dev_f32(z, "z"),
+                                                  _stream(stream)))
+        return out, z
+
+    def backward(self, radiance, albedo, normal, depth, z, dout, want_dz=False, stream=None):
+        """(dL/dweights [n_weights], dL/dz or None) from dout = dL/d(out)."""
+        import torch
+        fr, B, H, W = _frames(radiance, albedo, normal, depth)
+        dw = torch.empty(self.nw, device=radiance.device, dtype=torch.float32)
+        dz = torch.empty((B, 2 * self.M, H, W), device=radiance.device, dtype=torch.float32) if want_dz else None
+        self._check(self._lib.wskpn_backward(self._h, fr, B, H, W, _dev_f32(z, "z"), _dev_f32(dout, "dout"),
+                                             _dev_f32(dz, "dz") if dz is not None else None, _dev_f32(dw, "dw"),
+                                             _stream(stream)))
+        return dw, dz
+
+    def l1_loss(self, out, target, want_grad=True, stream=None):
+        """(loss [1] device tensor, dL/d(out) or None), L1 mean over all elements."""
+        import torch
+        loss = torch.empty(1, device=out.device, dtype=torch.float32)
+        g = torch.empty_like(out) if want_grad else None
+        self._check(self._lib.wskpn_l1_loss(self._h, _dev_f32(out, "out"), _dev_f32(target, "target"), out.numel(),
+                                            _dev_f32(loss, "loss"), _dev_f32(g, "dout") if g is not None else None,
+                                            _stream(stream)))
+        return loss, g
+
+    def adam_step(self, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._check(self._lib.wskpn_adam_step(self._h, _dev_f32(grad, "grad"), lr, beta1, beta2, eps, step,
+                                              _stream(stream)))
+
     def profile(self, enable: bool = True):
         """Start/stop recording per-stage CUDA events on each call's stream."""
         self._check(self._lib.wskpn_profile_enable(self._h, int(enable)))
@@ -189,6 +227,26 @@ def prep(radiance, albedo, normal, depth, gamma=2.2, depth_range=(1.0, 10.0), ou
     _lib.check(lib.wskpn_prep(fr, B, H, W, gamma, depth_range[0], depth_range[1], _dev_f32(out, "out"),
                               _stream(stream)))
     return out
+
+
+def decode_fuse_bwd(z, radiance, albedo, dout, ksizes=(3, 5, 7, 9, 11, 13), eps=1e-2, dz=None, scratch=None,
+                    fallbacks=None, stream=None):
+    """dL/dz [B, 2M, H, W] from dL/d(out) for the Eq. 3-5 reconstruction."""
+    import torch
+    lib = _lib.load()
+    B, C, H, W = z.shape
+    M = len(ksizes)
+    if dz is None:
+        dz = torch.empty_like(z)
+    if scratch is None:
+        scratch = torch.empty(int(lib.wskpn_decode_fuse_bwd_scratch_floats(B, H, W, M)), device=z.device,
+                              dtype=torch.float32)
+    ks = (ctypes.c_int * M)(*ksizes)
+    fb = ctypes.c_void_p(fallbacks.data_ptr()) if fallbacks is not None else None
+    _lib.check(lib.wskpn_decode_fuse_bwd(_dev_f32(z, "z"), _dev_f32(radiance, "radiance"), _dev_f32(albedo, "albedo"),
+                                         _dev_f32(dout, "dout"), B, H, W, M, ks, eps, _dev_f32(dz, "dz"),
+                                         _dev_f32(scratch, "scratch"), fb, _stream(stream)))
+    return dz
 
 
 def decode_fuse_fwd(z, radiance, albedo, ksizes=(3, 5, 7, 9, 11, 13), eps=1e-2, out=None,

@@ -14,7 +14,7 @@ MAX_BATCH = 16
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EBUSY, ETIMEOUT, ENUMERIC = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EBUSY", "ETIMEOUT", "ENUMERIC"]
 FP32, BF16, FP8 = 0, 1, 2
-TUNE_TC_MODE, TUNE_TC_DESC_BASE_OFFSET = 1, 2
+TUNE_TC_SPLIT = 2
 
 
 class Config(ctypes.Structure):
@@ -61,6 +61,12 @@ SIGNATURES = {
     "wskpn_logits": ([_P, _FR, _I, _I, _I, _P, _P], _I),
     "wskpn_prep": ([_FR, _I, _I, _I, _F, _F, _F, _P, _P], _I),
     "wskpn_decode_fuse_fwd": ([_P, _P, _P, _I, _I, _I, _I, ctypes.POINTER(_I), _F, _P, _P, _P], _I),
+    "wskpn_decode_fuse_bwd_scratch_floats": ([_I, _I, _I, _I], _SZ),
+    "wskpn_decode_fuse_bwd": ([_P, _P, _P, _P, _I, _I, _I, _I, ctypes.POINTER(_I), _F, _P, _P, _P, _P], _I),
+    "wskpn_forward_train": ([_P, _FR, _I, _I, _I, _P, _P, _P], _I),
+    "wskpn_backward": ([_P, _FR, _I, _I, _I, _P, _P, _P, _P, _P], _I),
+    "wskpn_l1_loss": ([_P, _P, _P, _SZ, _P, _P, _P], _I),
+    "wskpn_adam_step": ([_P, _P, _F, _F, _F, _F, _I, _P], _I),
     "wskpn_numeric_fallbacks": ([_P, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wskpn_profile_enable": ([_P, _I], _I),
     "wskpn_profile_read": ([_P, ctypes.POINTER(_F), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),

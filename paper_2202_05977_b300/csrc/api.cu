@@ -418,12 +418,8 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
 
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
     if (!ctx) return WSKPN_EINVAL;
-    if (key == WSKPN_TUNE_TC_MODE && (value == 0 || value == 1)) {
-        ctx->tc_mode = value;
-        return WSKPN_OK;
-    }
-    if (key == WSKPN_TUNE_TC_DESC_BASE_OFFSET && (value == 0 || value == 1)) {
-        ctx->tc_desc_base_offset = value;
+    if (key == WSKPN_TUNE_TC_SPLIT && (value == 0 || value == 1)) {
+        ctx->tc_split = value;
         return WSKPN_OK;
     }
     ctx->err = "wskpn_set_tuning: unknown key or value";

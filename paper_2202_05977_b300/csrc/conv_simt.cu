@@ -19,9 +19,10 @@ constexpr int TW = 32, TH = 8, THREADS = 256, CC = 8;
 struct ConvSimtArgs {
     PtrBatch<const float*> in;
     PtrBatch<float*> out;
+    PtrBatch<const float*> mask;  // optional [Cout][H][W]: output zeroed where mask <= 0 (ReLU backward)
     const float* w;     // [Cin][KS*KS][COUTP]
     const float* bias;  // [COUTP]
-    int H, W, Cin, Cout, relu;
+    int H, W, Cin, Cout, relu, has_mask;
 };
 
 template <int KS, int CPT>
@@ -107,7 +108,9 @@ __global__ void __launch_bounds__(cs::THREADS, 2) conv_simt_kernel(ConvSimtArgs 
             if (o < a.Cout) {
                 float v = acc[r][j];
                 if (a.relu) v = fmaxf(v, 0.f);
-                out[(size_t)o * HW + (size_t)gy * W + gx] = v;
+                const size_t g = (size_t)o * HW + (size_t)gy * W + gx;
+                if (a.has_mask && !(a.mask.p[b][g] > 0.f)) v = 0.f;
+                out[g] = v;
             }
         }
     }
@@ -129,10 +132,9 @@ static wskpn_status launch_simt_t(const ConvSimtArgs& a, int nb, cudaStream_t st
 // Output channels padded to a multiple of 16 (4 channel groups x CPT, CPT % 4 == 0).
 int simt_coutp(int cout) { return ((cout + 15) / 16) * 16; }
 
-wskpn_status launch_conv_simt(const float* const* in, float* const* out, int B, int H, int W,
-                              int Cin, int Cout, int KS, const float* w_packed,
-                              const float* bias_padded, int relu, cudaStream_t st,
-                              std::string& err) {
+wskpn_status launch_conv_simt_masked(const float* const* in, float* const* out, const float* const* mask, int B,
+                                     int H, int W, int Cin, int Cout, int KS, const float* w_packed,
+                                     const float* bias_padded, int relu, cudaStream_t st, std::string& err) {
     const int cpt = simt_coutp(Cout) / 4;
     for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
         const int nb = B - b0 < WSKPN_MAX_BATCH ? B - b0 : WSKPN_MAX_BATCH;
@@ -140,7 +142,9 @@ wskpn_status launch_conv_simt(const float* const* in, float* const* out, int B, 
         for (int j = 0; j < nb; ++j) {
             a.in.p[j] = in[b0 + j];
             a.out.p[j] = out[b0 + j];
+            a.mask.p[j] = mask ? mask[b0 + j] : nullptr;
         }
+        a.has_mask = mask != nullptr;
         a.w = w_packed;
         a.bias = bias_padded;
         a.H = H;
@@ -158,6 +162,12 @@ wskpn_status launch_conv_simt(const float* const* in, float* const* out, int B, 
         return WSKPN_EUNSUPPORTED;
     }
     return WSKPN_OK;
+}
+
+wskpn_status launch_conv_simt(const float* const* in, float* const* out, int B, int H, int W, int Cin, int Cout,
+                              int KS, const float* w_packed, const float* bias_padded, int relu, cudaStream_t st,
+                              std::string& err) {
+    return launch_conv_simt_masked(in, out, nullptr, B, H, W, Cin, Cout, KS, w_packed, bias_padded, relu, st, err);
 }
 
 // Packs an OIHW FP32 layer ([Cout][Cin][KS][KS] + bias[Cout]) into the SIMT

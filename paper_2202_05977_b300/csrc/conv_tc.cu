@@ -4,16 +4,24 @@
 //
 // GEMM view of one tile: M = 128 consecutive pixels of an image row (TMEM
 // lanes), N = padded output channels, K = KS*KS taps x input channels,
-// consumed 32 bytes (16 BF16 or 32 e4m3 channels) at a time.  A CTA owns
+// consumed 32 bytes (16 BF16 or 32 e4m3 channels) per MMA.  A CTA owns
 // R = 4 output rows x 128 pixels and keeps 4 accumulators (one per output
 // row) in TMEM, double-buffered across tiles so the epilogue of one tile
 // overlaps the MMAs of the next.  Each input row is fetched once per tile
-// and channel chunk and serves every (dy, dx) tap that reads it:
-//   mode 0: one TMA box of 128 + KS - 1 pixels; the KS horizontal taps use
-//           the same box through operand descriptors shifted by dx rows;
-//   mode 1: KS TMA boxes of 128 pixels, one per horizontal tap.
-// The weights of the layer stay resident in shared memory for the whole
-// persistent kernel (pre-swizzled image, one bulk copy per CTA).
+// (one TMA box of 128 + KS - 1 pixels per 32-byte channel chunk) and
+// serves every tap that reads it: the KS horizontal taps through operand
+// descriptors shifted by whole pixel rows, the KS vertical taps by
+// accumulating into the matching output row.  The layer's weights stay
+// resident in shared memory (pre-swizzled image, one bulk copy per CTA).
+//
+// BF16 activations may be stored as hi/lo pairs (x = hi + lo): the K loop
+// then runs over both halves against the same weight chunk, which removes
+// the activation rounding error at twice the MMA work.
+//
+// Issue path: one pipeline item is one input row with all its channel
+// chunks; the MMAs of an item are a compile-time unrolled, branch-free
+// sequence followed by one commit (a branch or commit between MMAs roughly
+// doubles their issue time on this part).
 //
 // Roles: warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs (one
 // thread), warps 2-5 drain TMEM (bias, ReLU, requantise) and store NHWC
@@ -49,15 +57,14 @@ struct TcArgs {
     uint32_t wbytes;
     const float* ep_scale;   // [COUT_P] multiplier of the accumulator
     const float* ep_bias;    // [COUT_P]
-    void* out;               // NHWC [B][H][W][COUT_P] activations, or planar FP32 [B][cout][H][W]
+    void* out;               // NHWC activations, or planar FP32 [B][cout][H][W] for the last layer
     int B, H, W;
-    int ncc;                 // K chunks per tap
     int cout;                // real output channels
     int relu, last;
+    int split_out;           // write BF16 hi/lo pairs: [hi(COUT_P) | lo(COUT_P)]
     float out_qscale;        // FP8 activations: 1 / scale of the output activation
-    int mode;                // see file comment
-    int desc_base_offset;    // fill the descriptor's base-offset field from the start address
     int stages;
+    uint32_t box_stride;     // bytes between the chunk boxes of a stage
     uint32_t stage_bytes;
     int tiles_x, tiles_y, ntiles;
     unsigned int* status;
@@ -121,29 +128,33 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
 // K-major operand, 32-byte swizzle: rows of 32 bytes, 8-row groups 256 B apart.
-__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr, int base_offset_mode) {
+// The swizzle follows the absolute shared-memory address bits (as the TMA
+// writes it), so a start address shifted by whole 32-byte rows addresses
+// the shifted matrix with the base-offset field left at 0.
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
     d |= (uint64_t)(256 >> 4) << 32;     // stride byte offset: 8 rows x 32 B
     d |= (uint64_t)1 << 46;              // descriptor version for tcgen05
-    if (base_offset_mode) d |= (uint64_t)((saddr >> 7) & 7u) << 49;
     d |= (uint64_t)6 << 61;              // 32-byte swizzle
     return d;
 }
-template <bool FP8>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// The accumulate flag is a compile-time constant: a predicate computed at
+// run time costs about twice the issue time of the MMA itself.
+template <bool FP8, bool ACC>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc) {
     if constexpr (FP8) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            "l"(a), "l"(b), "r"(idesc), "n"(ACC ? 1 : 0)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            "l"(a), "l"(b), "r"(idesc), "n"(ACC ? 1 : 0)
             : "memory");
     }
 }
@@ -170,13 +181,62 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
            : 2 * tc::R * COUT_P <= 256 ? 256 : 512;
 }
 
+// All MMAs of input row RI of a tile: output row ro = RI - dy for each
+// vertical tap dy with 0 <= ro < R, every channel chunk and horizontal tap.
+// The first contribution to a row (dy = 0, chunk 0, dx = 0) overwrites the
+// accumulator; everything else accumulates.  Fully unrolled, no branches.
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int RI>
+__device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                          uint32_t box_step) {
+    constexpr uint32_t b_chunk = (COUT_P * tc::ROWB) >> 4;
+    constexpr uint32_t b_tap = NCC_W * b_chunk;
+    constexpr uint32_t a_dx = tc::ROWB >> 4;
+#pragma unroll
+    for (int dy = 0; dy < KS; ++dy) {
+        const int ro = RI - dy;
+        if (ro < 0 || ro >= tc::R) continue;  // resolved at compile time
+        const uint32_t d = dbase + (uint32_t)(ro * COUT_P);
+#pragma unroll
+        for (int cc = 0; cc < NCC_IN; ++cc) {
+            const int ccw = cc % NCC_W;  // the lo half of a split activation reuses the weights
+#pragma unroll
+            for (int dx = 0; dx < KS; ++dx) {
+                const uint64_t a = ad + (uint64_t)(cc * box_step + dx * a_dx);
+                const uint64_t b = bd + (uint64_t)((dy * KS + dx) * b_tap + ccw * b_chunk);
+                if (dy == 0 && cc == 0 && dx == 0)
+                    mma<FP8, false>(d, a, b, idesc);
+                else
+                    mma<FP8, true>(d, a, b, idesc);
+            }
+        }
+    }
+}
+
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
+__device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                           uint32_t box_step) {
+    static_assert(tc::R + KS - 1 <= 8, "rows per tile");
+    switch (ri) {
+        case 0: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 0>(dbase, ad, bd, idesc, box_step); break;
+        case 1: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 1>(dbase, ad, bd, idesc, box_step); break;
+        case 2: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 2>(dbase, ad, bd, idesc, box_step); break;
+        case 3: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 3>(dbase, ad, bd, idesc, box_step); break;
+        case 4: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 4>(dbase, ad, bd, idesc, box_step); break;
+        case 5: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 5>(dbase, ad, bd, idesc, box_step); break;
+        case 6: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 6>(dbase, ad, bd, idesc, box_step); break;
+        default: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 7>(dbase, ad, bd, idesc, box_step); break;
+    }
+}
+
 // ----------------------------------------------------------------- kernel
-template <int KS, int COUT_P, bool FP8>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr int PAD = KS / 2;
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
     constexpr uint32_t NCOL = tmem_cols<COUT_P>();
+    constexpr int ROWS_IN = tc::R + KS - 1;
+    constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB;
     static_assert(COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256, "MMA N");
     static_assert(2 * tc::R * COUT_P <= 512, "TMEM columns");
     constexpr uint32_t IDESC = (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) |
@@ -196,9 +256,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     uint64_t* fin = wbar + 1;
     volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(fin + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(fin + 1) + 1;
+    float* s_scale = reinterpret_cast<float*>(fin + 2);  // [COUT_P]
+    float* s_bias = s_scale + COUT_P;                     // [COUT_P]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
+    for (int i = tid; i < COUT_P; i += tc::THREADS) {
+        s_scale[i] = a.ep_scale[i];
+        s_bias[i] = a.ep_bias[i];
+    }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
@@ -224,7 +289,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    const int rows_in = tc::R + KS - 1;
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
@@ -239,26 +303,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
                 const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
                 const int x0 = tx * tc::BM, y0 = ty * tc::R;
-                for (int ri = 0; ri < rows_in && ok; ++ri)
-                    for (int cc = 0; cc < a.ncc; ++cc, ++it) {
-                        const int s = it % S;
-                        const uint32_t ph = (it / S) & 1u;
-                        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        const uint32_t fb = smem_u32(&full[s]);
-                        const uint32_t dst = smem_u32(sA + (size_t)s * a.stage_bytes);
-                        if (a.mode == 0) {
-                            mbar_expect_tx(fb, (tc::BM + KS - 1) * tc::ROWB);
-                            tma_load_4d(dst, &tmap, cc * CH, x0 - PAD, y0 - PAD + ri, b, fb);
-                        } else {
-                            mbar_expect_tx(fb, KS * tc::BM * tc::ROWB);
-                            for (int dx = 0; dx < KS; ++dx)
-                                tma_load_4d(dst + dx * tc::BM * tc::ROWB, &tmap, cc * CH, x0 - PAD + dx,
-                                            y0 - PAD + ri, b, fb);
-                        }
+                for (int ri = 0; ri < ROWS_IN; ++ri, ++it) {
+                    const int s = it % S;
+                    if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
                     }
+                    const uint32_t fb = smem_u32(&full[s]);
+                    const uint32_t dst = smem_u32(sA + (size_t)s * a.stage_bytes);
+                    mbar_expect_tx(fb, NCC_IN * BOX_BYTES);
+#pragma unroll
+                    for (int cc = 0; cc < NCC_IN; ++cc)
+                        tma_load_4d(dst + cc * a.box_stride, &tmap, cc * CH, x0 - PAD, y0 - PAD + ri, b, fb);
+                }
             }
             if (!ok) {
                 atomicOr(a.status, tc::ST_TIMEOUT_PRODUCER);
@@ -275,7 +332,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag);
-            const uint32_t wbase = smem_u32(sW);
+            // Descriptors are linear in the start address (16-byte units in
+            // the low bits): stages, chunks and taps are offsets from two bases.
+            const uint64_t wdesc0 = sdesc_sw32(smem_u32(sW));
+            const uint64_t adesc0 = sdesc_sw32(smem_u32(sA));
+            const uint32_t a_stage = a.stage_bytes >> 4;
+            const uint32_t box_step = a.box_stride >> 4;
             uint32_t it = 0;
             int lt = 0;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
@@ -286,31 +348,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t dbase = tmem + (uint32_t)(buf * tc::R * COUT_P);
-                for (int ri = 0; ri < rows_in && ok; ++ri)
-                    for (int cc = 0; cc < a.ncc; ++cc, ++it) {
-                        const int s = it % S;
-                        if (!mbar_wait(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t abase = smem_u32(sA + (size_t)s * a.stage_bytes);
-#pragma unroll
-                        for (int dy = 0; dy < KS; ++dy) {
-                            const int ro = ri - dy;
-                            if (ro < 0 || ro >= tc::R) continue;
-#pragma unroll
-                            for (int dx = 0; dx < KS; ++dx) {
-                                const uint32_t aaddr =
-                                    a.mode == 0 ? abase + dx * tc::ROWB : abase + dx * tc::BM * tc::ROWB;
-                                const uint32_t baddr =
-                                    wbase + (uint32_t)(((dy * KS + dx) * a.ncc + cc) * COUT_P * tc::ROWB);
-                                mma<FP8>(dbase + (uint32_t)(ro * COUT_P), sdesc_sw32(aaddr, a.desc_base_offset),
-                                         sdesc_sw32(baddr, 0), IDESC, (dy | cc | dx) != 0);
-                            }
-                        }
-                        mma_commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
+                for (int ri = 0; ri < ROWS_IN; ++ri, ++it) {
+                    const int s = it % S;
+                    if (!mbar_wait(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8>(ri, dbase, adesc0 + (uint64_t)(s * a_stage), wdesc0,
+                                                               IDESC, box_step);
+                    mma_commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
+                }
                 if (ok) mma_commit(smem_u32(&accf[buf]));
             }
             if (!ok) {
@@ -355,7 +403,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int o = c16 * 16 + j;
-                        v[j] = fmaf(v[j], a.ep_scale[o], a.ep_bias[o]);
+                        v[j] = fmaf(v[j], s_scale[o], s_bias[o]);
                         if (a.relu) v[j] = fmaxf(v[j], 0.f);
                     }
                     const size_t pix = ((size_t)b * a.H + y) * a.W + x;
@@ -382,13 +430,29 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + pix * COUT_P + c16 * 16);
                         *dst = make_uint4(w[0], w[1], w[2], w[3]);
                     } else {
+                        const int rowc = a.split_out ? 2 * COUT_P : COUT_P;  // channels per stored pixel
                         __nv_bfloat162 h2[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + (pix * COUT_P + c16 * 16) * 2);
+                        uint4* dst =
+                            reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + (pix * rowc + c16 * 16) * 2);
                         const uint4* src = reinterpret_cast<const uint4*>(h2);
                         dst[0] = src[0];
                         dst[1] = src[1];
+                        if (a.split_out) {
+                            // residual v - bf16(v), itself rounded to BF16
+                            __nv_bfloat162 l2[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float2 hf = __bfloat1622float2(h2[j]);
+                                l2[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+                            }
+                            uint4* dlo = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) +
+                                                                  (pix * rowc + COUT_P + c16 * 16) * 2);
+                            const uint4* slo = reinterpret_cast<const uint4*>(l2);
+                            dlo[0] = slo[0];
+                            dlo[1] = slo[1];
+                        }
                     }
                 }
             }
@@ -430,12 +494,13 @@ static int cout_pad(const wskpn_config& c, int l) {
     return l == c.n_layers - 1 ? (c.widths[l + 1] + 15) / 16 * 16 : chan_pad(c.widths[l + 1], fp8);
 }
 
+// BF16 activations are stored as hi/lo pairs (2 x channels), FP8 as one byte.
 size_t tc_act_bytes_per_pixel(const wskpn_config& c, int which) {
     const bool fp8 = c.prec == WSKPN_FP8;
     size_t m = 0;
     for (int l = 0; l < c.n_layers; ++l)
         if (l % 2 == which) {
-            const size_t b = (size_t)chan_pad(c.widths[l], fp8) * (fp8 ? 1 : 2);
+            const size_t b = (size_t)chan_pad(c.widths[l], fp8) * (fp8 ? 1 : 4);
             m = b > m ? b : m;
         }
     return m;
@@ -525,19 +590,18 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     return WSKPN_OK;
 }
 
-template <int KS, int COUT_P, bool FP8>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
-    WSKPN_CUDA_TRY(cudaFuncSetAttribute(conv_tc_kernel<KS, COUT_P, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem),
-                   err);
-    conv_tc_kernel<KS, COUT_P, FP8><<<grid, tc::THREADS, smem, st>>>(map, a);
+    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8>;
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
+    kern<<<grid, tc::THREADS, smem, st>>>(map, a);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
 
-// One conv layer on the tensor cores.  in: NHWC [B][H][W][cin_p] (BF16 or
-// e4m3); out: NHWC [B][H][W][cout_p] or (last) planar FP32 [B][cout][H][W].
+// One conv layer on the tensor cores.  in: NHWC [B][H][W][cin_p x (1 or 2)]
+// (BF16 or e4m3); out: NHWC activations or (last) planar FP32 [B][cout][H][W].
 static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st) {
     const wskpn_config& c = ctx->cfg;
     const Layer& L = ctx->layers[l];
@@ -547,11 +611,12 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     const int ch = fp8 ? 32 : 16;
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode(ctx->err);
     if (!encode) return WSKPN_EUNSUPPORTED;
-    const int mode = ctx->tc_mode;
+    const int split = fp8 ? 0 : ctx->tc_split;
+    const int cin_row = L.cin_p * (split ? 2 : 1);  // stored channels per input pixel
     CUtensorMap map;
-    cuuint64_t gdim[4] = {(cuuint64_t)L.cin_p, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
-    cuuint64_t gstr[3] = {(cuuint64_t)L.cin_p * eb, (cuuint64_t)W * L.cin_p * eb, (cuuint64_t)H * W * L.cin_p * eb};
-    cuuint32_t box[4] = {(cuuint32_t)ch, (cuuint32_t)(mode == 0 ? tc::BM + KS - 1 : tc::BM), 1, 1};
+    cuuint64_t gdim[4] = {(cuuint64_t)cin_row, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    cuuint64_t gstr[3] = {(cuuint64_t)cin_row * eb, (cuuint64_t)W * cin_row * eb, (cuuint64_t)H * W * cin_row * eb};
+    cuuint32_t box[4] = {(cuuint32_t)ch, (cuuint32_t)(tc::BM + KS - 1), 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult cr = encode(&map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                          const_cast<void*>(in), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -560,6 +625,8 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
         ctx->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
         return WSKPN_ECUDA;
     }
+    const int ncc_w = L.cin_p / ch;
+    const int ncc_in = ncc_w * (split ? 2 : 1);
     TcArgs a{};
     a.wimg = L.wtc;
     a.wbytes = (uint32_t)L.wtc_bytes;
@@ -569,23 +636,21 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     a.B = B;
     a.H = H;
     a.W = W;
-    a.ncc = L.cin_p / ch;
     a.cout = L.cout;
     a.last = l == c.n_layers - 1;
     a.relu = !a.last;
+    a.split_out = split && !a.last;
     a.out_qscale = fp8 && !a.last ? 1.f / ctx->act_scale[l + 1] : 1.f;
-    a.mode = mode;
-    a.desc_base_offset = ctx->tc_desc_base_offset;
-    a.stage_bytes = mode == 0 ? (uint32_t)(((tc::BM + KS - 1) * tc::ROWB + 1023) / 1024 * 1024)
-                              : (uint32_t)(KS * tc::BM * tc::ROWB);
-    const size_t fixed = 1024 + ((L.wtc_bytes + 1023) / 1024 * 1024) + 256;
+    // one box of 128 + KS - 1 rows of 32 B per chunk, 256-byte aligned (swizzle atom)
+    a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB + 255) / 256 * 256);
+    a.stage_bytes = (uint32_t)((ncc_in * a.box_stride + 1023) / 1024 * 1024);
+    const size_t fixed = 1024 + ((L.wtc_bytes + 1023) / 1024 * 1024) + 256 + 2 * 64 * sizeof(float);
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
-        ctx->err = "conv_tc: layer weights do not fit in shared memory";
+        ctx->err = "conv_tc: layer weights and two input stages do not fit in shared memory";
         return WSKPN_EUNSUPPORTED;
     }
-    int stages = (int)((tc::SMEM_MAX - fixed) / a.stage_bytes);
-    const int max_stages = mode == 0 ? 8 : 4;
-    a.stages = stages < max_stages ? stages : max_stages;
+    const int stages = (int)((tc::SMEM_MAX - fixed) / a.stage_bytes);
+    a.stages = stages < 6 ? stages : 6;
     // at least ~120 KB so that exactly one CTA (and one TMEM allocation) lives on an SM
     size_t smem = fixed + (size_t)a.stages * a.stage_bytes;
     if (smem < 120 * 1024) smem = 120 * 1024;
@@ -596,15 +661,22 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
-#define WSKPN_TC_CASE(ks_, n_, f8_)                                                   \
-    if (KS == ks_ && L.cout_p == n_ && fp8 == f8_)                                    \
-        return launch_tc_t<ks_, n_, f8_>(map, a, smem, grid, st, ctx->err);
-    WSKPN_TC_CASE(5, 16, false) WSKPN_TC_CASE(5, 32, false) WSKPN_TC_CASE(5, 48, false) WSKPN_TC_CASE(5, 64, false)
-    WSKPN_TC_CASE(3, 16, false) WSKPN_TC_CASE(3, 32, false) WSKPN_TC_CASE(3, 48, false) WSKPN_TC_CASE(3, 64, false)
-    WSKPN_TC_CASE(5, 16, true) WSKPN_TC_CASE(5, 32, true) WSKPN_TC_CASE(5, 64, true)
-    WSKPN_TC_CASE(3, 16, true) WSKPN_TC_CASE(3, 32, true) WSKPN_TC_CASE(3, 64, true)
+#define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_)                                                  \
+    if (KS == ks_ && L.cout_p == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_)          \
+        return launch_tc_t<ks_, n_, nin_, nw_, f8_>(map, a, smem, grid, st, ctx->err);
+#define WSKPN_TC_BF16(ks_)                                                                                 \
+    WSKPN_TC_CASE(ks_, 32, 1, 1, false) WSKPN_TC_CASE(ks_, 32, 2, 1, false)                                \
+    WSKPN_TC_CASE(ks_, 48, 2, 2, false) WSKPN_TC_CASE(ks_, 48, 4, 2, false)                                \
+    WSKPN_TC_CASE(ks_, 64, 3, 3, false) WSKPN_TC_CASE(ks_, 64, 6, 3, false)                                \
+    WSKPN_TC_CASE(ks_, 16, 4, 4, false) WSKPN_TC_CASE(ks_, 16, 8, 4, false)
+#define WSKPN_TC_FP8(ks_)                                                                                  \
+    WSKPN_TC_CASE(ks_, 32, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 2, 2, true) \
+    WSKPN_TC_CASE(ks_, 16, 2, 2, true)
+    WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3)
+#undef WSKPN_TC_FP8
+#undef WSKPN_TC_BF16
 #undef WSKPN_TC_CASE
-    ctx->err = "conv_tc: unsupported (KS, padded Cout, precision)";
+    ctx->err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M are built";
     return WSKPN_EUNSUPPORTED;
 }
 
@@ -621,9 +693,11 @@ wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, 
     uint8_t* A = static_cast<uint8_t*>(ctx->d_tcA);
     uint8_t* Bf = static_cast<uint8_t*>(ctx->d_tcB);
     std::vector<void*> x0(B);
-    const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * HW;
+    const int split = ctx->tc_split;
+    const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * (split ? 2 : 1) * HW;
     for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * x0_bytes;
-    wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), 1, st, ctx->err);
+    wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), split ? 2 : 1, st,
+                                 ctx->err);
     if (s) return s;
     prof_mark(ctx, 1, st);
     for (int l = 0; l < c.n_layers; ++l) {

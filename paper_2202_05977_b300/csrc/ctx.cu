@@ -76,6 +76,7 @@ wskpn_status ctx_init(wskpn_ctx* ctx, const float* host_weights) {
 
 void ctx_free(wskpn_ctx* ctx) {
     cudaDeviceSynchronize();
+    ctx_free_train(ctx);
     for (int l = 0; l < WSKPN_MAX_LAYERS; ++l) {
         Layer& L = ctx->layers[l];
         cudaFree(L.w32);

@@ -49,8 +49,8 @@ struct wskpn_ctx {
     unsigned int* d_fallbacks = nullptr;
     unsigned int* d_status = nullptr;  // device status word of the tensor-core kernels
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
-    int tc_mode = 1;              // tensor-core conv A-operand staging (WSKPN_TUNE_TC_MODE)
-    int tc_desc_base_offset = 0;  // WSKPN_TUNE_TC_DESC_BASE_OFFSET
+    int tc_split = 1;  // BF16 activations as hi/lo pairs (WSKPN_TUNE_TC_SPLIT)
+    void* train = nullptr;  // training workspaces (train.cu), allocated by the first training call
     // stage profiling: one event set (n_layers + 3 events) per recorded call
     bool prof = false;
     std::vector<std::vector<cudaEvent_t>> prof_sets;
@@ -61,6 +61,7 @@ struct wskpn_ctx {
 namespace wskpn {
 wskpn_status ctx_init(wskpn_ctx* ctx, const float* host_weights);
 void ctx_free(wskpn_ctx* ctx);
+void ctx_free_train(wskpn_ctx* ctx);
 wskpn_status ctx_repack(wskpn_ctx* ctx, cudaStream_t st);
 // stage profiling hooks (no-ops unless profiling is enabled)
 void prof_begin(wskpn_ctx* ctx, cudaStream_t st);

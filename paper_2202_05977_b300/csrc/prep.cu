@@ -15,7 +15,7 @@ struct PrepArgs {
     float inv_gamma, dnear, dscale;  // dscale = 1 / (far - near)
 };
 
-__device__ __forceinline__ void prep_pixel(const PrepArgs& a, int b, size_t g, size_t HW, float v[10]) {
+__device__ __forceinline__ void prep_pixel(const PrepArgs& a, int b, size_t g, size_t HW, float* v) {
     const float* r = a.f.r.p[b];
     const float* al = a.f.a.p[b];
     const float* n = a.f.n.p[b];
@@ -63,6 +63,33 @@ __global__ void prep_nhwc16_bf16_kernel(PrepArgs a) {
     }
 }
 
+// Channels-last BF16 hi/lo output [H][W][32]: channels 0..15 = bf16(v),
+// 16..31 = bf16(v - bf16(v)) (the split-BF16 activation format).
+__global__ void prep_nhwc16_bf16x2_kernel(PrepArgs a) {
+    const int b = blockIdx.y;
+    const size_t HW = (size_t)a.H * a.W;
+    uint4* out = static_cast<uint4*>(a.out.p[b]);
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < HW; g += (size_t)gridDim.x * blockDim.x) {
+        float v[16];
+        prep_pixel(a, b, g, HW, v);
+#pragma unroll
+        for (int j = 10; j < 16; ++j) v[j] = 0.f;
+        __nv_bfloat162 h[8], l[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            const float2 hf = __bfloat1622float2(h[j]);
+            l[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+        }
+        const uint4* hv = reinterpret_cast<const uint4*>(h);
+        const uint4* lv = reinterpret_cast<const uint4*>(l);
+        out[4 * g] = hv[0];
+        out[4 * g + 1] = hv[1];
+        out[4 * g + 2] = lv[0];
+        out[4 * g + 3] = lv[1];
+    }
+}
+
 wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear,
                          float dfar, void* const* out, int layout, cudaStream_t st, std::string& err) {
     for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
@@ -86,8 +113,10 @@ wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float g
         dim3 grid(blocks, nb);
         if (layout == 0)
             prep_planar_kernel<<<grid, 256, 0, st>>>(a);
-        else
+        else if (layout == 1)
             prep_nhwc16_bf16_kernel<<<grid, 256, 0, st>>>(a);
+        else
+            prep_nhwc16_bf16x2_kernel<<<grid, 256, 0, st>>>(a);
         WSKPN_CUDA_TRY(cudaGetLastError(), err);
     }
     return WSKPN_OK;

@@ -1,0 +1,358 @@
+// Training step (Eq. 1): forward with the network output kept, L1 loss,
+// backward through the reconstruction (Eq. 3-5) and the convolutions with
+// the activations recomputed from the inputs (not stored between forward
+// and backward), and one Adam update of the weights.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ctx.h"
+
+namespace wskpn {
+
+wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
+                         void* const* out, int layout, cudaStream_t st, std::string& err);
+wskpn_status launch_conv_simt(const float* const* in, float* const* out, int B, int H, int W, int Cin, int Cout,
+                              int KS, const float* w_packed, const float* bias_padded, int relu, cudaStream_t st,
+                              std::string& err);
+wskpn_status launch_conv_simt_masked(const float* const* in, float* const* out, const float* const* mask, int B,
+                                     int H, int W, int Cin, int Cout, int KS, const float* w_packed,
+                                     const float* bias_padded, int relu, cudaStream_t st, std::string& err);
+wskpn_status launch_pack_simt_transposed(const float* w, int Cin, int Cout, int KS, float* wp, float* bp,
+                                         cudaStream_t st, std::string& err);
+int simt_coutp(int cout);
+size_t wgrad_part_floats(int Cin, int KS, int G);
+wskpn_status launch_wgrad(const float* const* x, const float* const* gy, int B, int H, int W, int Cin, int Cout,
+                          int KS, int G, float* part, float* dw, float* db, cudaStream_t st, std::string& err);
+wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r, const float* const* a,
+                                    float* const* out, int B, int H, int W, int M, const int* ks, float eps,
+                                    unsigned int* fallbacks, cudaStream_t st, std::string& err);
+wskpn_status launch_decode_fuse_bwd(const float* const* z, const float* const* r, const float* const* a,
+                                    const float* const* G, float* const* dz, float* const* scratch, int B, int H,
+                                    int W, int M, const int* ks, float eps, unsigned int* fallbacks,
+                                    cudaStream_t st, std::string& err);
+
+namespace {
+constexpr int kWgradGroups = 256;
+constexpr int kLossBlocks = 1024;
+}
+
+struct TrainWs {
+    size_t px = 0;
+    float* acts = nullptr;      // x_0 .. x_{L-1}, planar FP32, layer after layer
+    size_t act_off[WSKPN_MAX_LAYERS] = {};
+    float* gA = nullptr;        // gradient ping-pong [B][maxw][H][W]
+    float* gB = nullptr;
+    float* dz = nullptr;        // [B][2M][H][W]
+    float* dscratch = nullptr;  // reconstruction-backward scratch [B][5M+3][H][W]
+    float* part = nullptr;      // wgrad partial sums
+    float* wT[WSKPN_MAX_LAYERS] = {};  // transposed + flipped packed weights
+    float* bT[WSKPN_MAX_LAYERS] = {};
+    float* loss_part = nullptr;
+    float* m = nullptr;         // Adam moments
+    float* v = nullptr;
+};
+
+static void free_train(TrainWs* t) {
+    if (!t) return;
+    cudaFree(t->acts);
+    cudaFree(t->gA);
+    cudaFree(t->gB);
+    cudaFree(t->dz);
+    cudaFree(t->dscratch);
+    cudaFree(t->part);
+    for (int l = 0; l < WSKPN_MAX_LAYERS; ++l) {
+        cudaFree(t->wT[l]);
+        cudaFree(t->bT[l]);
+    }
+    cudaFree(t->loss_part);
+    cudaFree(t->m);
+    cudaFree(t->v);
+    delete t;
+}
+
+void ctx_free_train(wskpn_ctx* ctx) {
+    free_train(static_cast<TrainWs*>(ctx->train));
+    ctx->train = nullptr;
+}
+
+#define WSKPN_TRY_ALLOC(ptr, bytes)                                                               \
+    do {                                                                                          \
+        if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                                 \
+            ctx->err = std::string("training workspace allocation failed: ") + #ptr;             \
+            return WSKPN_ENOMEM;                                                                  \
+        }                                                                                         \
+    } while (0)
+
+static wskpn_status ensure_train(wskpn_ctx* ctx) {
+    if (ctx->train) return WSKPN_OK;
+    const wskpn_config& c = ctx->cfg;
+    TrainWs* t = new TrainWs();
+    ctx->train = t;
+    t->px = ctx->ws_pixels;
+    const int L = c.n_layers, M = c.n_kernels, KS = c.conv_ks;
+    size_t off = 0;
+    int maxw = 0, maxcin = 0;
+    for (int l = 0; l < L; ++l) {
+        t->act_off[l] = off;
+        off += (size_t)c.widths[l] * t->px;
+    }
+    for (int l = 1; l <= L; ++l) maxw = std::max(maxw, c.widths[l]);
+    for (int l = 0; l < L; ++l) maxcin = std::max(maxcin, c.widths[l]);
+    WSKPN_TRY_ALLOC(t->acts, off * sizeof(float));
+    WSKPN_TRY_ALLOC(t->gA, (size_t)maxw * t->px * sizeof(float));
+    WSKPN_TRY_ALLOC(t->gB, (size_t)maxw * t->px * sizeof(float));
+    WSKPN_TRY_ALLOC(t->dz, (size_t)2 * M * t->px * sizeof(float));
+    WSKPN_TRY_ALLOC(t->dscratch, (size_t)(5 * M + 3) * t->px * sizeof(float));
+    WSKPN_TRY_ALLOC(t->part, wgrad_part_floats(maxcin, KS, kWgradGroups) * sizeof(float));
+    for (int l = 1; l < L; ++l) {  // layer 0 needs no input gradient
+        const int cin = c.widths[l], cout = c.widths[l + 1];
+        WSKPN_TRY_ALLOC(t->wT[l], (size_t)cout * KS * KS * simt_coutp(cin) * sizeof(float));
+        WSKPN_TRY_ALLOC(t->bT[l], (size_t)simt_coutp(cin) * sizeof(float));
+    }
+    WSKPN_TRY_ALLOC(t->loss_part, kLossBlocks * sizeof(float));
+    return WSKPN_OK;
+}
+
+// ------------------------------------------------------------------ loss
+// L1: loss = sum |o - t| / n,  dout = sign(o - t) / n (sign(0) = 0).
+__global__ void l1_loss_kernel(const float* __restrict__ o, const float* __restrict__ t, size_t n,
+                               float* __restrict__ part, float* __restrict__ grad) {
+    float s = 0.f;
+    const float inv = 1.f / (float)n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = o[i] - t[i];
+        s += fabsf(d);
+        if (grad) grad[i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+    }
+    __shared__ float red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+        part[blockIdx.x] = b;
+    }
+}
+
+__global__ void sum_partials_kernel(const float* __restrict__ part, int n, double scale, float* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        out[0] = (float)(s * scale);
+    }
+}
+
+// ------------------------------------------------------------------ Adam
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+}  // namespace wskpn
+
+using namespace wskpn;
+
+extern "C" {
+
+size_t wskpn_decode_fuse_bwd_scratch_floats(int batch, int h, int w, int M) {
+    if (batch < 1 || h < 1 || w < 1 || M < 1 || M > WSKPN_MAX_KERNELS) return 0;
+    return (size_t)(5 * M + 3) * batch * h * w;
+}
+
+wskpn_status wskpn_decode_fuse_bwd(const float* z, const float* radiance, const float* albedo, const float* dout,
+                                   int batch, int h, int w, int M, const int* ksizes, float eps, float* dz,
+                                   float* scratch, unsigned int* fallbacks, void* stream) {
+    if (!z || !radiance || !albedo || !dout || !dz || !scratch || !ksizes || batch < 1 || h < 1 || w < 1 || M < 1 ||
+        M > WSKPN_MAX_KERNELS || !(eps > 0.f)) {
+        set_thread_error("wskpn_decode_fuse_bwd: invalid argument");
+        return WSKPN_EINVAL;
+    }
+    for (int i = 0; i < M; ++i)
+        if (ksizes[i] < 1 || ksizes[i] > 13 || (ksizes[i] & 1) == 0) {
+            set_thread_error("wskpn_decode_fuse_bwd: ksizes must be odd and in [1, 13]");
+            return WSKPN_EINVAL;
+        }
+    const size_t HW = (size_t)h * w;
+    std::vector<const float*> zz(batch), rr(batch), aa(batch), gg(batch);
+    std::vector<float*> dd(batch), ss(batch);
+    for (int b = 0; b < batch; ++b) {
+        zz[b] = z + (size_t)b * 2 * M * HW;
+        rr[b] = radiance + (size_t)b * 3 * HW;
+        aa[b] = albedo + (size_t)b * 3 * HW;
+        gg[b] = dout + (size_t)b * 3 * HW;
+        dd[b] = dz + (size_t)b * 2 * M * HW;
+        ss[b] = scratch + (size_t)b * (5 * M + 3) * HW;
+    }
+    std::string err;
+    wskpn_status s = launch_decode_fuse_bwd(zz.data(), rr.data(), aa.data(), gg.data(), dd.data(), ss.data(), batch,
+                                            h, w, M, ksizes, eps, fallbacks, (cudaStream_t)stream, err);
+    if (s) set_thread_error(err);
+    return s;
+}
+
+wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w, float* out,
+                                 float* z_saved, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    if (!z_saved || !out) {
+        ctx->err = "wskpn_forward_train: out or z_saved is NULL";
+        return WSKPN_EINVAL;
+    }
+    wskpn_status s = wskpn_logits(ctx, frames, batch, h, w, z_saved, stream);
+    if (s) return s;
+    const wskpn_config& c = ctx->cfg;
+    const size_t HW = (size_t)h * w;
+    std::vector<const float*> z(batch), r(batch), a(batch);
+    std::vector<float*> o(batch);
+    for (int b = 0; b < batch; ++b) {
+        z[b] = z_saved + (size_t)b * 2 * c.n_kernels * HW;
+        r[b] = frames[b].radiance;
+        a[b] = frames[b].albedo;
+        o[b] = out + (size_t)b * 3 * HW;
+    }
+    return launch_decode_fuse_fwd(z.data(), r.data(), a.data(), o.data(), batch, h, w, c.n_kernels, c.ksizes,
+                                  c.albedo_eps, ctx->d_fallbacks, (cudaStream_t)stream, ctx->err);
+}
+
+wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
+                            const float* z_saved, const float* dout, float* dz_out, float* dweights, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    if (!frames || !z_saved || !dout || !dweights) {
+        ctx->err = "wskpn_backward: NULL argument";
+        return WSKPN_EINVAL;
+    }
+    if (batch < 1 || batch > ctx->cfg.max_batch || batch > WSKPN_MAX_BATCH || h < 1 || w < 1 ||
+        h > ctx->cfg.max_h || w > ctx->cfg.max_w || (size_t)batch * h * w > ctx->ws_pixels) {
+        ctx->err = "wskpn_backward: batch or size out of range (batch <= 16 and <= max_batch)";
+        return WSKPN_EINVAL;
+    }
+    wskpn_status s = ensure_train(ctx);
+    if (s) return s;
+    TrainWs* t = static_cast<TrainWs*>(ctx->train);
+    const wskpn_config& c = ctx->cfg;
+    const int L = c.n_layers, M = c.n_kernels, KS = c.conv_ks;
+    const size_t HW = (size_t)h * w;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* dz = dz_out ? dz_out : t->dz;
+
+    // 1. reconstruction backward
+    {
+        std::vector<const float*> zz(batch), rr(batch), aa(batch), gg(batch);
+        std::vector<float*> dd(batch), ss(batch);
+        for (int b = 0; b < batch; ++b) {
+            zz[b] = z_saved + (size_t)b * 2 * M * HW;
+            rr[b] = frames[b].radiance;
+            aa[b] = frames[b].albedo;
+            gg[b] = dout + (size_t)b * 3 * HW;
+            dd[b] = dz + (size_t)b * 2 * M * HW;
+            ss[b] = t->dscratch + (size_t)b * (5 * M + 3) * HW;
+        }
+        s = launch_decode_fuse_bwd(zz.data(), rr.data(), aa.data(), gg.data(), dd.data(), ss.data(), batch, h, w, M,
+                                   c.ksizes, c.albedo_eps, ctx->d_fallbacks, st, ctx->err);
+        if (s) return s;
+    }
+    // 2. recompute x_0 .. x_{L-1} (FP32)
+    auto act = [&](int l, int b) { return t->acts + t->act_off[l] + (size_t)b * c.widths[l] * HW; };
+    {
+        std::vector<void*> x0(batch);
+        for (int b = 0; b < batch; ++b) x0[b] = act(0, b);
+        s = launch_prep(frames, batch, h, w, c.gamma, c.depth_near, c.depth_far, x0.data(), 0, st, ctx->err);
+        if (s) return s;
+        std::vector<const float*> in(batch);
+        std::vector<float*> o(batch);
+        for (int l = 1; l < L; ++l) {
+            for (int b = 0; b < batch; ++b) {
+                in[b] = act(l - 1, b);
+                o[b] = act(l, b);
+            }
+            const Layer& Ly = ctx->layers[l - 1];
+            s = launch_conv_simt(in.data(), o.data(), batch, h, w, Ly.cin, Ly.cout, KS, Ly.w32, Ly.b32, 1, st,
+                                 ctx->err);
+            if (s) return s;
+        }
+    }
+    // 3. layer by layer: weight gradient, then the masked input gradient
+    std::vector<const float*> gy(batch), xs(batch), mask(batch);
+    std::vector<float*> gx(batch);
+    for (int b = 0; b < batch; ++b) gy[b] = dz + (size_t)b * 2 * M * HW;
+    float* gbuf[2] = {t->gA, t->gB};
+    for (int l = L - 1; l >= 0; --l) {
+        const Layer& Ly = ctx->layers[l];
+        for (int b = 0; b < batch; ++b) xs[b] = act(l, b);
+        const int nchunks = (Ly.cin + 7) / 8;
+        int G = kWgradGroups / nchunks;
+        const int ntiles = ((w + 31) / 32) * ((h + 7) / 8) * batch;
+        G = std::max(1, std::min(G, ntiles));
+        s = launch_wgrad(xs.data(), gy.data(), batch, h, w, Ly.cin, Ly.cout, KS, G, t->part, dweights + Ly.woff,
+                         dweights + Ly.boff, st, ctx->err);
+        if (s) return s;
+        if (l == 0) break;
+        s = launch_pack_simt_transposed(ctx->d_master + Ly.woff, Ly.cin, Ly.cout, KS, t->wT[l], t->bT[l], st,
+                                        ctx->err);
+        if (s) return s;
+        float* dst = gbuf[l % 2];
+        for (int b = 0; b < batch; ++b) {
+            gx[b] = dst + (size_t)b * Ly.cin * HW;
+            mask[b] = xs[b];
+        }
+        s = launch_conv_simt_masked(gy.data(), gx.data(), mask.data(), batch, h, w, Ly.cout, Ly.cin, KS, t->wT[l],
+                                    t->bT[l], 0, st, ctx->err);
+        if (s) return s;
+        for (int b = 0; b < batch; ++b) gy[b] = gx[b];
+    }
+    return WSKPN_OK;
+}
+
+wskpn_status wskpn_l1_loss(wskpn_ctx* ctx, const float* out, const float* target, size_t n, float* loss,
+                           float* dout, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    if (!out || !target || !loss || n == 0) {
+        ctx->err = "wskpn_l1_loss: invalid argument";
+        return WSKPN_EINVAL;
+    }
+    wskpn_status s = ensure_train(ctx);
+    if (s) return s;
+    TrainWs* t = static_cast<TrainWs*>(ctx->train);
+    cudaStream_t st = (cudaStream_t)stream;
+    l1_loss_kernel<<<kLossBlocks, 256, 0, st>>>(out, target, n, t->loss_part, dout);
+    WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
+    sum_partials_kernel<<<1, 32, 0, st>>>(t->loss_part, kLossBlocks, 1.0 / (double)n, loss);
+    WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
+    return WSKPN_OK;
+}
+
+wskpn_status wskpn_adam_step(wskpn_ctx* ctx, const float* dweights, float lr, float beta1, float beta2, float eps,
+                             int step, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    if (!dweights || step < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+        !(eps > 0.f)) {
+        ctx->err = "wskpn_adam_step: invalid argument";
+        return WSKPN_EINVAL;
+    }
+    wskpn_status s = ensure_train(ctx);
+    if (s) return s;
+    TrainWs* t = static_cast<TrainWs*>(ctx->train);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!t->m) {
+        WSKPN_TRY_ALLOC(t->m, ctx->nw * sizeof(float));
+        WSKPN_TRY_ALLOC(t->v, ctx->nw * sizeof(float));
+        WSKPN_CUDA_TRY(cudaMemsetAsync(t->m, 0, ctx->nw * sizeof(float), st), ctx->err);
+        WSKPN_CUDA_TRY(cudaMemsetAsync(t->v, 0, ctx->nw * sizeof(float), st), ctx->err);
+    }
+    const float c1 = (float)(1.0 - std::pow((double)beta1, step));
+    const float c2 = (float)(1.0 - std::pow((double)beta2, step));
+    adam_kernel<<<148, 256, 0, st>>>(ctx->d_master, dweights, t->m, t->v, ctx->nw, lr, beta1, beta2, eps, c1, c2);
+    WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
+    return ctx_repack(ctx, st);
+}
+
+}  // extern "C"

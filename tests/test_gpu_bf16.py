@@ -1,0 +1,113 @@
+"""GPU parity of the tensor-core (tcgen05, BF16 operands, FP32 accumulate)
+path against the FP64 oracle, through the C ABI.  Tolerance: max relative
+error 1e-2 per output element (|gpu - ref| / max(|ref|, 1e-6)); the decode,
+normalisation and fusion stay in FP32."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._util import args, rel_err, sample_pixels, stack_frames, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_BF16 = 1e-2
+SPLIT = 2  # wskpn_set_tuning key WSKPN_TUNE_TC_SPLIT
+
+
+@pytest.fixture(scope="module")
+def wk():
+    import paper_2202_05977_b300 as wk
+    return wk
+
+
+def _den(wk, wb, **kw):
+    return wk.Denoiser(wb, precision="bf16", **kw)
+
+
+def test_bf16_denoise_64_matches_oracle(wk):
+    f = synth.make_frame(64, 64, 0)
+    wb = synth.make_weights(seed=0)
+    d = _den(wk, wb, max_hw=(64, 64))
+    out = d.denoise(*args(to_dev(stack_frames([f])))).cpu().numpy()[0]
+    assert d.device_status() == 0
+    mx, mean = rel_err(out, oracle.denoise(f, wb))
+    print(f"bf16 64x64: max rel {mx:.3e} mean {mean:.3e}")
+    assert mx < TOL_BF16
+
+
+def test_bf16_single_value_activations_64(wk):
+    # WSKPN_TUNE_TC_SPLIT = 0: plain BF16 activations (no hi/lo pair)
+    f = synth.make_frame(64, 64, 0)
+    wb = synth.make_weights(seed=0)
+    d = _den(wk, wb, max_hw=(64, 64))
+    d.set_tuning(SPLIT, 0)
+    out = d.denoise(*args(to_dev(stack_frames([f])))).cpu().numpy()[0]
+    assert d.device_status() == 0
+    mx, _ = rel_err(out, oracle.denoise(f, wb))
+    assert mx < TOL_BF16
+
+
+def test_bf16_split_is_more_accurate_than_single(wk):
+    f = synth.make_frame(70, 300, 3)
+    wb = synth.make_weights(seed=3)
+    dev = to_dev(stack_frames([f]))
+    ref = oracle.logits(f, wb)
+    errs = []
+    for split in (1, 0):
+        d = _den(wk, wb, max_hw=(70, 300))
+        d.set_tuning(SPLIT, split)
+        errs.append(np.abs(d.logits(*args(dev)).cpu().numpy()[0] - ref).max())
+        assert d.device_status() == 0
+    assert errs[0] < errs[1]
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 45, 67), (1, 1, 1), (1, 13, 13), (1, 14, 200), (3, 19, 33),
+                                   (1, 130, 257)])
+def test_bf16_denoise_ragged_matches_oracle(wk, B, H, W):
+    frames = [synth.make_frame(H, W, 50 + b) for b in range(B)]
+    wb = synth.make_weights(seed=5)
+    d = _den(wk, wb, max_hw=(H, W), max_batch=B)
+    out = d.denoise(*args(to_dev(stack_frames(frames)))).cpu().numpy()
+    assert d.device_status() == 0
+    for b in range(B):
+        mx, _ = rel_err(out[b], oracle.denoise(frames[b], wb))
+        assert mx < TOL_BF16, (b, mx)
+
+
+def test_bf16_logits_close_to_oracle(wk):
+    f = synth.make_frame(96, 160, 6)
+    wb = synth.make_weights(seed=6)
+    d = _den(wk, wb, max_hw=(96, 160))
+    z = d.logits(*args(to_dev(stack_frames([f])))).cpu().numpy()[0]
+    ref = oracle.logits(f, wb)
+    assert np.abs(z - ref).max() < 1e-2 * max(1.0, np.abs(ref).max())
+
+
+def test_bf16_1080p_sampled_matches_oracle(wk):
+    """Precision form, 1920x1080, seed 2: sampled pixels against the oracle,
+    every pixel against the FP32 path (itself within 2e-6 of the oracle)."""
+    H, W = 1080, 1920
+    f = synth.make_frame(H, W, 2)
+    wb = synth.make_weights(seed=2)
+    dev = to_dev(stack_frames([f]))
+    out = _den(wk, wb, max_hw=(H, W)).denoise(*args(dev)).cpu().numpy()[0]
+    pix = sample_pixels(H, W, 40, seed=2)
+    ref = oracle.denoise_pixels(f, wb, pix)
+    mx, mean = rel_err(np.stack([out[:, y, x] for x, y in pix]), ref)
+    full = wk.Denoiser(wb, precision="fp32", max_hw=(H, W)).denoise(*args(dev)).cpu().numpy()[0]
+    fmx, fmean = rel_err(out, full)
+    print(f"bf16 1080p: sampled vs oracle max {mx:.3e} mean {mean:.3e}; all px vs fp32 max {fmx:.3e} mean {fmean:.3e}")
+    assert mx < TOL_BF16
+    assert fmx < TOL_BF16
+
+
+def test_bf16_batch_invariance(wk):
+    frames = [synth.make_frame(48, 80, 60 + b) for b in range(3)]
+    wb = synth.make_weights(seed=7)
+    d = _den(wk, wb, max_hw=(48, 80), max_batch=3)
+    dev = to_dev(stack_frames(frames))
+    both = d.denoise(*args(dev)).cpu().numpy()
+    for b in range(3):
+        one = d.denoise(*(dev[k][b:b + 1].contiguous() for k in ("radiance", "albedo", "normal", "depth")))
+        np.testing.assert_array_equal(one.cpu().numpy()[0], both[b])

@@ -1,0 +1,158 @@
+"""Differentiation form on the GPU through the C ABI: the reconstruction
+backward kernel, the full training backward, the L1 loss and Adam, against
+the FP64 oracle (whose gradients are pinned to finite differences).
+Tolerance for FP32 gradients: per tensor max |gpu - ref| <= 2e-4 max |ref|."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._util import KSIZES, args, stack_frames, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 2e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+@pytest.fixture(scope="module")
+def wk():
+    import paper_2202_05977_b300 as wk
+    return wk
+
+
+def _close(gpu, ref, tol=TOL_GRAD):
+    gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
+    return float(np.abs(gpu - ref).max() / max(np.abs(ref).max(), 1e-30)) < tol
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 45, 67), (2, 33, 90), (1, 1, 1), (1, 14, 200), (1, 70, 20)])
+def test_decode_fuse_bwd_matches_oracle(torch, wk, B, H, W):
+    g = np.random.default_rng(B * 100 + H)
+    frames = [synth.make_frame(H, W, 200 + b) for b in range(B)]
+    dev = to_dev(stack_frames(frames))
+    z = (g.standard_normal((B, 12, H, W)) * 1.5).astype(np.float32)
+    G = g.standard_normal((B, 3, H, W)).astype(np.float32)
+    fb = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dz = wk.decode_fuse_bwd(torch.from_numpy(z).cuda(), dev["radiance"], dev["albedo"], torch.from_numpy(G).cuda(),
+                            KSIZES, 1e-2, fallbacks=fb).cpu().numpy()
+    for b in range(B):
+        ref = oracle.reconstruct_bwd(z[b], frames[b]["radiance"], frames[b]["albedo"], G[b])
+        for c in range(12):
+            assert _close(dz[b, c], ref[c]), (b, c)
+    assert int(fb.item()) == 0
+
+
+def test_decode_fuse_bwd_wide_range_takes_exact_path(torch, wk):
+    H, W = 40, 70
+    f = synth.make_frame(H, W, 77)
+    g = np.random.default_rng(77)
+    z = g.standard_normal((1, 12, H, W)).astype(np.float32)
+    z[0, :6, 20, 30] = 95.0
+    z[0, :6, :, :10] -= 40.0
+    G = g.standard_normal((1, 3, H, W)).astype(np.float32)
+    dev = to_dev(stack_frames([f]))
+    fb = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dz = wk.decode_fuse_bwd(torch.from_numpy(z).cuda(), dev["radiance"], dev["albedo"], torch.from_numpy(G).cuda(),
+                            KSIZES, 1e-2, fallbacks=fb).cpu().numpy()
+    ref = oracle.reconstruct_bwd(z[0], f["radiance"], f["albedo"], G[0])
+    for c in range(12):
+        assert _close(dz[0, c], ref[c], 1e-3), c
+    assert int(fb.item()) > 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_training_backward_matches_oracle(torch, wk, prec):
+    """dL/dTheta for a random cotangent dL/dout, B = 2 frames of 24 x 40."""
+    B, H, W = 2, 24, 40
+    frames = [synth.make_frame(H, W, 300 + b) for b in range(B)]
+    wb = synth.make_weights(seed=9)
+    d = wk.Denoiser(wb, precision=prec, max_batch=B, max_hw=(H, W))
+    dev = to_dev(stack_frames(frames))
+    out, z = d.forward_train(*args(dev))
+    G = np.random.default_rng(9).standard_normal((B, 3, H, W)).astype(np.float32)
+    dw, dz = d.backward(*args(dev), z, torch.from_numpy(G).cuda(), want_dz=True)
+    ref = np.zeros(wb.size)
+    for b in range(B):
+        o, acts = oracle.forward_train(frames[b], wb)
+        gb, _ = oracle.backward_train(frames[b], wb, acts, G[b])
+        ref += gb
+    dw = dw.cpu().numpy()
+    tol = TOL_GRAD if prec == "fp32" else 2e-2  # bf16: the saved z (hence dz) carries BF16 rounding
+    off = 0
+    for (ws, bs) in synth.weight_shapes():
+        n = int(np.prod(ws)) + bs[0]
+        assert _close(dw[off:off + n], ref[off:off + n], tol), (ws, off)
+        off += n
+    assert np.isfinite(dz.cpu().numpy()).all()
+
+
+def test_l1_loss_and_gradient(torch, wk):
+    g = np.random.default_rng(5)
+    o = g.lognormal(0, 1, (2, 3, 17, 29)).astype(np.float32)
+    t = g.lognormal(0, 1, (2, 3, 17, 29)).astype(np.float32)
+    d = wk.Denoiser(synth.make_weights(seed=0), precision="fp32", max_hw=(8, 8))
+    loss, grad = d.l1_loss(torch.from_numpy(o).cuda(), torch.from_numpy(t).cuda())
+    L, G = oracle.l1_loss(o, t)
+    assert abs(loss.item() - L) <= 1e-6 * L
+    np.testing.assert_allclose(grad.cpu().numpy(), G, rtol=1e-6)
+
+
+def test_adam_steps_match_oracle(torch, wk):
+    wb = synth.make_weights(seed=3)
+    d = wk.Denoiser(wb, precision="fp32", max_hw=(8, 8))
+    w, m, v = wb.astype(np.float64), np.zeros(wb.size), np.zeros(wb.size)
+    for step in range(1, 4):
+        g = np.random.default_rng(step).standard_normal(wb.size).astype(np.float32) * 1e-2
+        d.adam_step(torch.from_numpy(g).cuda(), step, lr=1e-3)
+        w, m, v = oracle.adam_step(w, g, m, v, step, lr=1e-3)
+    got = d.get_weights().cpu().numpy()
+    assert np.abs(got - w).max() < 1e-6
+
+
+def test_autograd_decode_fuse_matches_kernel_and_fd(torch, wk):
+    from paper_2202_05977_b300.autograd import decode_fuse
+    H, W = 30, 50
+    f = synth.make_frame(H, W, 8)
+    dev = to_dev(stack_frames([f]))
+    g = np.random.default_rng(8)
+    z = torch.from_numpy(g.standard_normal((1, 12, H, W)).astype(np.float32)).cuda().requires_grad_()
+    G = torch.from_numpy(g.standard_normal((1, 3, H, W)).astype(np.float32)).cuda()
+    (decode_fuse(z, dev["radiance"], dev["albedo"]) * G).sum().backward()
+    ref = wk.decode_fuse_bwd(z.detach(), dev["radiance"], dev["albedo"], G)
+    assert torch.equal(z.grad, ref)
+    # directional derivative, central difference in FP32
+    v = torch.from_numpy(g.standard_normal((1, 12, H, W)).astype(np.float32)).cuda()
+    h = 1e-2
+    fp = (wk.decode_fuse_fwd(z.detach() + h * v, dev["radiance"], dev["albedo"]) * G).sum().item()
+    fm = (wk.decode_fuse_fwd(z.detach() - h * v, dev["radiance"], dev["albedo"]) * G).sum().item()
+    fd = (fp - fm) / (2 * h)
+    an = (z.grad * v).sum().item()
+    assert abs(fd - an) <= 1e-2 * abs(an) + 1e-3
+
+
+def test_training_step_256_crops(torch, wk):
+    """Differentiation form: 16 crops of 256 x 256, BF16 forward, L1 against
+    the mean of 256 noise draws, backward, Adam; the loss is finite and one
+    small step along -grad lowers it."""
+    B, H, W = 16, 256, 256
+    b = synth.make_batch(B, H, W, seed=5)
+    target = synth.make_target(b["clean"], seed=5, draws=256)
+    wb = synth.make_weights(seed=5)
+    d = wk.Denoiser(wb, precision="bf16", max_batch=B, max_hw=(H, W))
+    dev = to_dev(b)
+    tg = torch.from_numpy(target).cuda()
+    out, z = d.forward_train(*args(dev))
+    loss0, dout = d.l1_loss(out, tg)
+    dw, _ = d.backward(*args(dev), z, dout)
+    assert np.isfinite(dw.cpu().numpy()).all() and np.isfinite(loss0.item())
+    d.adam_step(dw, 1, lr=1e-4)
+    out1, _ = d.forward_train(*args(dev))
+    loss1, _ = d.l1_loss(out1, tg, want_grad=False)
+    assert loss1.item() < loss0.item()
+    assert d.device_status() == 0

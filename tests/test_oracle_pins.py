@@ -308,3 +308,21 @@ def test_golden_tiny_frame():
     f = synth.make_frame(6, 8, 42)
     out = oracle.denoise(f, synth.make_weights(seed=42))
     np.testing.assert_allclose(out, ref, rtol=1e-12)
+
+
+def test_adam_first_step_is_signed_lr_and_matches_torch():
+    # First step: mhat = g, vhat = g^2, so every weight moves by lr * g / (|g| + eps).
+    g = _rng(30).standard_normal(50)
+    w0 = _rng(31).standard_normal(50)
+    w1, m, v = oracle.adam_step(w0, g, np.zeros(50), np.zeros(50), 1, lr=1e-3, eps=1e-8)
+    np.testing.assert_allclose(w0 - w1, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    # several steps against torch.optim.Adam (library routine, float64)
+    wt = torch.tensor(w0, requires_grad=True)
+    opt = torch.optim.Adam([wt], lr=1e-2, betas=(0.9, 0.99), eps=1e-8)
+    w, m, v = w0.copy(), np.zeros(50), np.zeros(50)
+    for step in range(1, 6):
+        gs = _rng(40 + step).standard_normal(50)
+        wt.grad = torch.tensor(gs)
+        opt.step()
+        w, m, v = oracle.adam_step(w, gs, m, v, step, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-8)
+    np.testing.assert_allclose(w, wt.detach().numpy(), rtol=1e-12, atol=1e-14)
