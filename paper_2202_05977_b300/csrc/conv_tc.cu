@@ -175,56 +175,69 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+}
+
 template <int COUT_P>
 __host__ __device__ constexpr uint32_t tmem_cols() {
     return 2 * tc::R * COUT_P <= 32 ? 32 : 2 * tc::R * COUT_P <= 64 ? 64 : 2 * tc::R * COUT_P <= 128 ? 128
            : 2 * tc::R * COUT_P <= 256 ? 256 : 512;
 }
 
-// All MMAs of input row RI of a tile: output row ro = RI - dy for each
-// vertical tap dy with 0 <= ro < R, every channel chunk and horizontal tap.
-// The first contribution to a row (dy = 0, chunk 0, dx = 0) overwrites the
-// accumulator; everything else accumulates.  Fully unrolled, no branches.
+// All MMAs of input row RI of a tile.  Input row RI feeds output rows
+// ro = RI - dy for the vertical taps dy in [DY0, DY1] (those with
+// 0 <= ro < R).  For each channel chunk and horizontal tap dx, ONE MMA
+// covers all of them: the weight image stores the KS vertical taps of a
+// (dx, chunk) pair as consecutive N blocks, and the accumulators of the R
+// output rows sit in TMEM in descending row order (row ro at column block
+// R - 1 - ro), so N = (DY1 - DY0 + 1) x COUT_P columns are contiguous.
+// Accumulators are zeroed by the epilogue, so every MMA accumulates.
+// Fully unrolled, no branches.
 template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int RI>
-__device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                          uint32_t box_step) {
-    constexpr uint32_t b_chunk = (COUT_P * tc::ROWB) >> 4;
-    constexpr uint32_t b_tap = NCC_W * b_chunk;
+__device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
+    constexpr int DY0 = RI - (tc::R - 1) > 0 ? RI - (tc::R - 1) : 0;
+    constexpr int DY1 = RI < KS - 1 ? RI : KS - 1;
+    constexpr int NB = DY1 - DY0 + 1;  // output rows fed by this input row
+    if constexpr (NB <= 0) {
+        return;  // row beyond R + KS - 1 (only instantiated for KS = 3)
+    } else {
+    constexpr int N = NB * COUT_P;
+    static_assert(N % 16 == 0 && N <= 256, "MMA N");
+    constexpr uint32_t IDESC = (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(N >> 3) << 17) |
+                               ((uint32_t)(tc::BM >> 4) << 24);
+    constexpr uint32_t b_blk = (COUT_P * tc::ROWB) >> 4;  // one (dx, chunk, dy) block, 16-byte units
     constexpr uint32_t a_dx = tc::ROWB >> 4;
+    const uint32_t d = dbase + (uint32_t)((tc::R - 1 - (RI - DY0)) * COUT_P);
 #pragma unroll
-    for (int dy = 0; dy < KS; ++dy) {
-        const int ro = RI - dy;
-        if (ro < 0 || ro >= tc::R) continue;  // resolved at compile time
-        const uint32_t d = dbase + (uint32_t)(ro * COUT_P);
+    for (int cc = 0; cc < NCC_IN; ++cc) {
+        const int ccw = cc % NCC_W;  // the lo half of a split activation reuses the weights
 #pragma unroll
-        for (int cc = 0; cc < NCC_IN; ++cc) {
-            const int ccw = cc % NCC_W;  // the lo half of a split activation reuses the weights
-#pragma unroll
-            for (int dx = 0; dx < KS; ++dx) {
-                const uint64_t a = ad + (uint64_t)(cc * box_step + dx * a_dx);
-                const uint64_t b = bd + (uint64_t)((dy * KS + dx) * b_tap + ccw * b_chunk);
-                if (dy == 0 && cc == 0 && dx == 0)
-                    mma<FP8, false>(d, a, b, idesc);
-                else
-                    mma<FP8, true>(d, a, b, idesc);
-            }
+        for (int dx = 0; dx < KS; ++dx) {
+            const uint64_t a = ad + (uint64_t)(cc * box_step + dx * a_dx);
+            const uint64_t b = bd + (uint64_t)(((dx * NCC_W + ccw) * KS + DY0) * b_blk);
+            mma<FP8, true>(d, a, b, IDESC);
         }
+    }
     }
 }
 
 template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
-__device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                           uint32_t box_step) {
+__device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
     static_assert(tc::R + KS - 1 <= 8, "rows per tile");
     switch (ri) {
-        case 0: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 0>(dbase, ad, bd, idesc, box_step); break;
-        case 1: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 1>(dbase, ad, bd, idesc, box_step); break;
-        case 2: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 2>(dbase, ad, bd, idesc, box_step); break;
-        case 3: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 3>(dbase, ad, bd, idesc, box_step); break;
-        case 4: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 4>(dbase, ad, bd, idesc, box_step); break;
-        case 5: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 5>(dbase, ad, bd, idesc, box_step); break;
-        case 6: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 6>(dbase, ad, bd, idesc, box_step); break;
-        default: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 7>(dbase, ad, bd, idesc, box_step); break;
+        case 0: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 0>(dbase, ad, bd, box_step); break;
+        case 1: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 1>(dbase, ad, bd, box_step); break;
+        case 2: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 2>(dbase, ad, bd, box_step); break;
+        case 3: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 3>(dbase, ad, bd, box_step); break;
+        case 4: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 4>(dbase, ad, bd, box_step); break;
+        case 5: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 5>(dbase, ad, bd, box_step); break;
+        case 6: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 6>(dbase, ad, bd, box_step); break;
+        default: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 7>(dbase, ad, bd, box_step); break;
     }
 }
 
@@ -239,8 +252,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB;
     static_assert(COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256, "MMA N");
     static_assert(2 * tc::R * COUT_P <= 512, "TMEM columns");
-    constexpr uint32_t IDESC = (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) |
-                               ((uint32_t)(COUT_P >> 3) << 17) | ((uint32_t)(tc::BM >> 4) << 24);
 
     extern __shared__ __align__(1024) uint8_t dsmem[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
@@ -288,6 +299,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
+    if (warp >= 2) {
+        // accumulators start at zero: every MMA accumulates
+        const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;
+#pragma unroll 1
+        for (int c = 0; c < 2 * tc::R * COUT_P; c += 16) tmem_zero16(tmem + lb + (uint32_t)c);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -356,7 +377,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     }
                     tc_fence_after();
                     issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8>(ri, dbase, adesc0 + (uint64_t)(s * a_stage), wdesc0,
-                                                               IDESC, box_step);
+                                                               box_step);
                     mma_commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
                 }
                 if (ok) mma_commit(smem_u32(&accf[buf]));
@@ -394,11 +415,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             for (int r = 0; r < tc::R; ++r) {
                 const int y = ty * tc::R + r;
                 const bool valid = x < a.W && y < a.H;
-                const uint32_t col = (uint32_t)(buf * tc::R * COUT_P + r * COUT_P);
+                const uint32_t col = (uint32_t)(buf * tc::R * COUT_P + (tc::R - 1 - r) * COUT_P);
 #pragma unroll
                 for (int c16 = 0; c16 < COUT_P / 16; ++c16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + col + c16 * 16, v);
+                    tmem_zero16(tmem + lane_base + col + c16 * 16);  // ready for the buffer's next tile
                     if (!valid) continue;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -456,6 +478,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     }
                 }
             }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
@@ -525,9 +548,11 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
     return WSKPN_OK;
 }
 
-// Builds the shared-memory image of a layer's B operand: chunk (tap, cc)
-// holds COUT_P rows of 32 bytes (K-major), 32-byte swizzled like the TMA
-// writes A: byte o of a chunk goes to o ^ (((o >> 7) & 1) << 4).
+// Builds the shared-memory image of a layer's B operand: block
+// ((dx * ncc + cc) * KS + dy) holds the COUT_P rows of 32 bytes (K-major) of
+// tap (dy, dx) and channel chunk cc, so the KS vertical taps of one
+// (dx, cc) pair are consecutive N blocks.  32-byte swizzled like the TMA
+// writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).
 __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restrict__ bias, int Cin, int Cout,
                                int KS, int cout_p, int ncc, int fp8, const float* __restrict__ wscale,
                                float act_in_scale, uint8_t* __restrict__ img, float* __restrict__ ep_scale,
@@ -538,9 +563,9 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restr
         const int k = i % ch;
         const int n = (i / ch) % cout_p;
         const int chunk = i / (ch * cout_p);
-        const int cc = chunk % ncc, t = chunk / ncc;
+        const int dy = chunk % KS, cc = (chunk / KS) % ncc, dx = chunk / (KS * ncc);
         const int cin = cc * ch + k;
-        const float v = (n < Cout && cin < Cin) ? w[((size_t)n * Cin + cin) * KS * KS + t] : 0.f;
+        const float v = (n < Cout && cin < Cin) ? w[((size_t)n * Cin + cin) * KS * KS + dy * KS + dx] : 0.f;
         const uint32_t o = (uint32_t)(n * 32 + k * (fp8 ? 1 : 2));
         const uint32_t phys = (uint32_t)chunk * cout_p * 32 + (o ^ (((o >> 7) & 1u) << 4));
         if (fp8) {

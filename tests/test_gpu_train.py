@@ -26,9 +26,13 @@ def wk():
     return wk
 
 
-def _close(gpu, ref, tol=TOL_GRAD):
+def _close(gpu, ref, tol=TOL_GRAD, scale=None):
+    """max |gpu - ref| <= tol * max(max |ref|, scale); `scale` is the size of
+    the whole gradient, so channels whose exact gradient vanishes (rounding
+    noise only) are judged against it."""
     gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
-    return float(np.abs(gpu - ref).max() / max(np.abs(ref).max(), 1e-30)) < tol
+    den = max(np.abs(ref).max(), scale or 0.0, 1e-30)
+    return float(np.abs(gpu - ref).max() / den) < tol
 
 
 @pytest.mark.parametrize("B,H,W", [(1, 45, 67), (2, 33, 90), (1, 1, 1), (1, 14, 200), (1, 70, 20)])
@@ -43,8 +47,9 @@ def test_decode_fuse_bwd_matches_oracle(torch, wk, B, H, W):
                             KSIZES, 1e-2, fallbacks=fb).cpu().numpy()
     for b in range(B):
         ref = oracle.reconstruct_bwd(z[b], frames[b]["radiance"], frames[b]["albedo"], G[b])
+        scale = 1e-3 * np.abs(ref).max()
         for c in range(12):
-            assert _close(dz[b, c], ref[c]), (b, c)
+            assert _close(dz[b, c], ref[c], scale=scale), (b, c)
     assert int(fb.item()) == 0
 
 
