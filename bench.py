@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 plain-path comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=4096)
+    p.add_argument("--serve-rate", type=float, default=240.0)
     p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
     return p.parse_args()
 
@@ -163,6 +166,64 @@ def config_block(precision):
             "resolution": f"{W}x{H}", "batch": 1, "precision": precision,
             "network": "ImportanceNet 3 blocks 10-32-48-64 + output conv to 12, 5x5 convs",
             "kernel_sizes": list(KSIZES), "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def serving_run(wk_serving, synth, torch, np, n_req, rate, wb, dev):
+    """Serving form: n_req requests, Poisson arrivals at `rate`/s from 8
+    client streams, sizes uniform over 720p / 1080p / 1440p, BF16."""
+    sizes = [(720, 1280), (1080, 1920), (1440, 2560)]
+    keys = ("radiance", "albedo", "normal", "depth")
+    frames = []
+    for i, (h, w) in enumerate(sizes):
+        f = synth.make_frame(h, w, 11 + i)
+        frames.append([torch.from_numpy(np.ascontiguousarray(f[k][None])).to(dev) for k in keys])
+    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=4, max_batch=4, mem_budget=8 << 30,
+                            batch_window_us=200)
+    n_streams = 8
+    outs = {(s, r): torch.empty((1, 3, *sizes[r]), device=dev) for s in range(n_streams) for r in range(3)}
+    busy = {}
+    g = np.random.default_rng(240)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
+    res = g.integers(0, 3, n_req)
+    # warm the graphs of every size once
+    for r in range(3):
+        t = srv.submit(0, *frames[r], outs[(0, r)])
+        srv.wait(t, 60000)
+    srv.stop()
+    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=4, max_batch=4, mem_budget=8 << 30,
+                            batch_window_us=200)
+    for r in range(3):  # capture outside the measured stream
+        t = srv.submit(0, *frames[r], outs[(0, r)])
+        srv.wait(t, 60000)
+    stats0 = srv.stats()
+    t0 = time.perf_counter()
+    tickets = []
+    late = 0
+    for i in range(n_req):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        sid, r = i % n_streams, int(res[i])
+        prev = busy.get((sid, r))
+        if prev is not None and srv.wait(prev, 0) != 0:
+            late += 1
+            srv.wait(prev, -1)
+        t = srv.submit(sid, *frames[r], outs[(sid, r)])
+        busy[(sid, r)] = t
+        tickets.append(t)
+    for t in busy.values():
+        srv.wait(t, -1)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.stop()
+    done = st["completed"] - stats0["completed"]
+    return {"requests": n_req, "rate_per_s": rate, "streams": n_streams,
+            "sizes": ["1280x720", "1920x1080", "2560x1440"], "precision": "bf16",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "fps": done / wall, "mean_batch": st["mean_batch"], "batches": st["batches"],
+            "graph_launches": st["graph_launches"], "rejected": st["rejected"], "failed": st["failed"],
+            "mem_peak_gib": st["mem_peak"] / 2 ** 30, "client_waits_for_own_buffer": late,
+            "note": "latency submit->delivery incl. the warm-up requests of each size (3 of the total)"}
 
 
 def cpu_baseline(budget_s=12.0):
@@ -334,6 +395,9 @@ def main():
             line["fp32_stages_ms"] = dict(zip(stage_names, fp32["stage_ms"]))
         if e2e is not None:
             line["e2e"] = e2e
+        if not args.no_serving:
+            import paper_2202_05977_b300.serving as wk_serving
+            line["serving"] = serving_run(wk_serving, synth, torch, np, args.serve_requests, args.serve_rate, wb, dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -220,6 +220,73 @@ wskpn_status wskpn_l1_loss(wskpn_ctx* ctx, const float* out, const float* target
 wskpn_status wskpn_adam_step(wskpn_ctx* ctx, const float* dweights, float lr, float beta1,
                              float beta2, float eps, int step, void* stream);
 
+/* ---- Serving: continuous batching of frame-denoise requests --------- */
+
+typedef struct wskpn_server wskpn_server;
+
+typedef struct {
+    int n_workers;        /* GPU batches in flight at once, one CUDA stream and
+                             one context each (default 4) */
+    int max_batch;        /* frames of one size per batch (default 4, <= 16) */
+    int max_queue;        /* queued requests beyond which submit returns
+                             EBUSY (default 8192) */
+    size_t mem_budget;    /* bytes of device memory that admitted requests may
+                             occupy at once (their footprint: workspace and
+                             staging per pixel); 0 = 8 GiB */
+    int use_graphs;       /* 1 = replay one captured CUDA graph per
+                             (worker, h, w, batch) (default 1) */
+    int batch_window_us;  /* how long the oldest request may wait for
+                             companions of its size (default 200) */
+} wskpn_serve_config;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, failed;
+    uint64_t batches, graph_launches, graph_captures;
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> delivery latency */
+    double fps;                              /* completed / (last delivery - first submit) */
+    double mean_batch;
+    size_t mem_in_use, mem_peak;             /* admitted footprint, bytes */
+} wskpn_serve_stats;
+
+/* Fills the defaults above. */
+wskpn_status wskpn_serve_config_default(wskpn_serve_config* scfg);
+
+/* Starts a server: cfg/weights as wskpn_create (cfg's max_h/max_w bound
+ * the request sizes; its max_batch is replaced by scfg->max_batch), one
+ * context, CUDA stream and staging slots per worker on the current device,
+ * and a scheduler thread.  Requests of equal size are batched; requests
+ * that arrive while others run are admitted as workers and memory budget
+ * free up, and their batches run concurrently on the workers' streams.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+wskpn_status wskpn_serve_start(const wskpn_config* cfg, const float* host_weights, size_t n_weights,
+                               const wskpn_serve_config* scfg, wskpn_server** out);
+
+/* Queues one frame (device pointers, planar float32) of size h x w for
+ * stream `stream_id` (any integer naming a client stream); the result is
+ * written to `out` (device [3][h][w]).  The caller keeps the frame and out
+ * buffers alive and unmodified until the ticket is delivered.  Results are
+ * delivered in submission order per stream.  Errors: EINVAL (size beyond
+ * the server's limits, NULL pointers), EBUSY (queue full or the request's
+ * footprint alone exceeds the budget). */
+wskpn_status wskpn_serve_submit(wskpn_server* srv, int stream_id, const wskpn_frame* frame, int h, int w,
+                                float* out, uint64_t* ticket);
+
+/* Waits up to timeout_ms (0 = poll, < 0 = no limit) for a ticket.  Returns
+ * OK when delivered, ETIMEOUT when the limit ran out, EINVAL for an unknown
+ * ticket, or the request's own failure status. */
+wskpn_status wskpn_serve_wait(wskpn_server* srv, uint64_t ticket, int timeout_ms);
+
+/* Pauses (1) or resumes (0) admission of queued requests (batches already
+ * on the GPU finish).  Used to drain or to build a queue deterministically. */
+wskpn_status wskpn_serve_pause(wskpn_server* srv, int paused);
+
+/* Snapshot of the counters and latency percentiles so far. */
+wskpn_status wskpn_serve_stats_get(wskpn_server* srv, wskpn_serve_stats* st);
+
+/* Finishes queued and running work, stops the scheduler and frees the
+ * server.  NULL is ignored. */
+void wskpn_serve_stop(wskpn_server* srv);
+
 /* Numeric fallback counter of ctx (pixels x sizes that took the slow exact
  * softmax path since creation); synchronises the context's device. */
 wskpn_status wskpn_numeric_fallbacks(wskpn_ctx* ctx, uint64_t* count);

@@ -40,6 +40,19 @@ class Frame(ctypes.Structure):
                 ("normal", ctypes.c_void_p), ("depth", ctypes.c_void_p)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("n_workers", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_queue", ctypes.c_int),
+                ("mem_budget", ctypes.c_size_t), ("use_graphs", ctypes.c_int), ("batch_window_us", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("graph_captures", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("fps", ctypes.c_double),
+                ("mean_batch", ctypes.c_double), ("mem_in_use", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _F = ctypes.c_float
@@ -67,6 +80,13 @@ SIGNATURES = {
     "wskpn_backward": ([_P, _FR, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "wskpn_l1_loss": ([_P, _P, _P, _SZ, _P, _P, _P], _I),
     "wskpn_adam_step": ([_P, _P, _F, _F, _F, _F, _I, _P], _I),
+    "wskpn_serve_config_default": ([ctypes.POINTER(ServeConfig)], _I),
+    "wskpn_serve_start": ([ctypes.POINTER(Config), _P, _SZ, ctypes.POINTER(ServeConfig), ctypes.POINTER(_P)], _I),
+    "wskpn_serve_submit": ([_P, _I, _FR, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
+    "wskpn_serve_wait": ([_P, ctypes.c_uint64, _I], _I),
+    "wskpn_serve_pause": ([_P, _I], _I),
+    "wskpn_serve_stats_get": ([_P, ctypes.POINTER(ServeStats)], _I),
+    "wskpn_serve_stop": ([_P], None),
     "wskpn_numeric_fallbacks": ([_P, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wskpn_profile_enable": ([_P, _I], _I),
     "wskpn_profile_read": ([_P, ctypes.POINTER(_F), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),

@@ -1,0 +1,111 @@
+"""Serving loop (continuous batching, admission by footprint, graph
+replay) through the C ABI: every result equals the same frame denoised
+alone, per-stream delivery order, refusals and bounded waits."""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+from tests._util import args, stack_frames, to_dev
+
+pytestmark = pytest.mark.gpu
+
+OK, EBUSY, ETIMEOUT = 0, 5, 6
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def _frames(sizes, seed0):
+    return [to_dev(stack_frames([synth.make_frame(h, w, seed0 + i)])) for i, (h, w) in enumerate(sizes)]
+
+
+def test_mixed_sizes_equal_solo_results(torch):
+    import paper_2202_05977_b300 as wk
+    from paper_2202_05977_b300.serving import Server
+    wb = synth.make_weights(seed=11)
+    sizes = [(72, 128), (90, 160), (72, 128), (45, 67), (90, 160), (72, 128)] * 3
+    frames = _frames(sizes, 500)
+    srv = Server(wb, "bf16", max_hw=(96, 176), n_workers=3, max_batch=3, batch_window_us=500)
+    outs = [torch.full((1, 3, h, w), float("nan"), device="cuda") for (h, w) in sizes]
+    tickets = [None] * len(sizes)
+
+    def client(sid):  # three client streams submitting concurrently
+        for i in range(sid, len(sizes), 3):
+            tickets[i] = srv.submit(sid, *args(frames[i]), outs[i])
+
+    th = [threading.Thread(target=client, args=(s,)) for s in range(3)]
+    [t.start() for t in th]
+    [t.join() for t in th]
+    for t in tickets:
+        assert srv.wait(t, 20000) == OK
+    st = srv.stats()
+    srv.stop()
+    assert st["completed"] == len(sizes) and st["failed"] == 0
+    assert st["graph_launches"] > 0 and st["p99_ms"] >= st["p50_ms"] > 0
+    solo = {}
+    for i, (h, w) in enumerate(sizes):
+        if (h, w) not in solo:
+            solo[(h, w)] = wk.Denoiser(wb, "bf16", max_hw=(h, w))
+        ref = solo[(h, w)].denoise(*args(frames[i]))
+        assert torch.equal(outs[i], ref), i
+
+
+def test_delivery_in_order_per_stream_and_bounded_wait(torch):
+    from paper_2202_05977_b300.serving import Server
+    wb = synth.make_weights(seed=12)
+    big, small = _frames([(96, 176)], 600)[0], _frames([(16, 16)], 601)[0]
+    srv = Server(wb, "bf16", max_hw=(96, 176), n_workers=2, max_batch=1, batch_window_us=0)
+    srv.pause(True)
+    o1 = torch.empty((1, 3, 96, 176), device="cuda")
+    o2 = torch.empty((1, 3, 16, 16), device="cuda")
+    t1 = srv.submit(7, *args(big), o1)
+    t2 = srv.submit(7, *args(small), o2)
+    assert srv.wait(t2, 50) == ETIMEOUT      # paused: nothing runs, the wait gives up
+    srv.pause(False)
+    assert srv.wait(t2, 20000) == OK          # t2 is delivered only after t1 (same stream)
+    assert srv.wait(t1, 0) == OK
+    srv.stop()
+
+
+def test_admission_refusals(torch):
+    from paper_2202_05977_b300.serving import Server
+    wb = synth.make_weights(seed=13)
+    fr = _frames([(64, 64)], 700)[0]
+    out = torch.empty((1, 3, 64, 64), device="cuda")
+    # footprint of one 64x64 request is far above a 1 KiB budget
+    srv = Server(wb, "bf16", max_hw=(64, 64), n_workers=1, max_batch=1, mem_budget=1024)
+    st, _ = srv.try_submit(0, *args(fr), out)
+    assert st == EBUSY
+    srv.stop()
+    # queue limit
+    srv = Server(wb, "bf16", max_hw=(64, 64), n_workers=1, max_batch=1, max_queue=2)
+    srv.pause(True)
+    outs = [torch.empty((1, 3, 64, 64), device="cuda") for _ in range(3)]
+    t = [srv.try_submit(0, *args(fr), outs[i]) for i in range(3)]
+    assert [s for s, _ in t] == [OK, OK, EBUSY]
+    srv.pause(False)
+    assert all(srv.wait(tk, 20000) == OK for s, tk in t if s == OK)
+    assert srv.stats()["rejected"] == 1
+    srv.stop()
+
+
+def test_budget_limits_concurrency_but_everything_completes(torch):
+    from paper_2202_05977_b300.serving import Server
+    wb = synth.make_weights(seed=14)
+    frames = _frames([(64, 96)] * 6, 800)
+    # budget fits about two requests at a time
+    probe = Server(wb, "bf16", max_hw=(64, 96), n_workers=1, max_batch=1)
+    probe.stop()
+    per_req = 64 * 96 * 600
+    srv = Server(wb, "bf16", max_hw=(64, 96), n_workers=4, max_batch=1, mem_budget=2 * per_req, batch_window_us=0)
+    outs = [torch.empty((1, 3, 64, 96), device="cuda") for _ in frames]
+    tk = [srv.submit(i, *args(f), o) for i, (f, o) in enumerate(zip(frames, outs))]
+    assert all(srv.wait(t, 20000) == OK for t in tk)
+    st = srv.stats()
+    assert st["mem_peak"] <= 2 * per_req and st["completed"] == 6
+    srv.stop()
