@@ -171,6 +171,19 @@ wskpn_status wskpn_decode_fuse_fwd(const float* z, const float* radiance, const 
                                    int batch, int h, int w, int M, const int* ksizes, float eps,
                                    float* out, unsigned int* fallbacks, void* stream);
 
+/* FP8 contexts: sets the static per-layer activation scales.  Runs the
+ * FP32 network on the given frames (device, as wskpn_denoise), takes the
+ * maximum of each layer's input over all pixels and channels, and sets
+ * scale_l = margin * max_l / 448 (the largest finite e4m3 value), so that
+ * x / scale_l is stored in e4m3 with satfinite.  Weights carry their own
+ * per-output-channel scales (max |W[o]| / 448).  margin >= 1.  Must be
+ * called before the first denoise of an FP8 context (which otherwise
+ * returns EUNSUPPORTED); allocates and frees temporary device buffers;
+ * synchronises `stream`.  batch <= 16.  Errors: EINVAL (not FP8, bad
+ * arguments), ENOMEM, ECUDA. */
+wskpn_status wskpn_calibrate(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
+                             float margin, void* stream);
+
 /* ---- Differentiation (one training step of Eq. 1) ------------------ */
 
 /* Floats of scratch that wskpn_decode_fuse_bwd needs: (5M + 3) x batch x h

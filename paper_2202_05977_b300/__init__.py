@@ -151,6 +151,11 @@ class Denoiser:
         self._check(self._lib.wskpn_get_weights(self._h, _dev_f32(out, "out"), self.nw, _stream(stream)))
         return out
 
+    def calibrate(self, radiance, albedo, normal, depth, margin=2.0, stream=None):
+        """FP8 only: set the per-layer activation scales from these frames."""
+        fr, B, H, W = _frames(radiance, albedo, normal, depth)
+        self._check(self._lib.wskpn_calibrate(self._h, fr, B, H, W, float(margin), _stream(stream)))
+
     # ------------------------------------------------------------ training
     def forward_train(self, radiance, albedo, normal, depth, out=None, z=None, stream=None):
         """Forward for training: (out [B,3,H,W], z [B,2M,H,W]); z is what backward needs."""

@@ -74,6 +74,7 @@ SIGNATURES = {
     "wskpn_logits": ([_P, _FR, _I, _I, _I, _P, _P], _I),
     "wskpn_prep": ([_FR, _I, _I, _I, _F, _F, _F, _P, _P], _I),
     "wskpn_decode_fuse_fwd": ([_P, _P, _P, _I, _I, _I, _I, ctypes.POINTER(_I), _F, _P, _P, _P], _I),
+    "wskpn_calibrate": ([_P, _FR, _I, _I, _I, _F, _P], _I),
     "wskpn_decode_fuse_bwd_scratch_floats": ([_I, _I, _I, _I], _SZ),
     "wskpn_decode_fuse_bwd": ([_P, _P, _P, _P, _I, _I, _I, _I, ctypes.POINTER(_I), _F, _P, _P, _P, _P], _I),
     "wskpn_forward_train": ([_P, _FR, _I, _I, _I, _P, _P, _P], _I),

@@ -35,6 +35,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -708,12 +709,38 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
 wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
                          void* const* out, int layout, cudaStream_t st, std::string& err);
 
-wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z, cudaStream_t st) {
+wskpn_status launch_prep_fp8(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
+                             void* const* out, float act_scale, cudaStream_t st, std::string& err);
+
+static wskpn_status tc_logits_fp8(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
+                                  cudaStream_t st) {
     const wskpn_config& c = ctx->cfg;
-    if (c.prec == WSKPN_FP8) {
-        ctx->err = "FP8 convolutions are not enabled in this build";
+    if (!ctx->fp8_calibrated) {
+        ctx->err = "FP8 context is not calibrated: call wskpn_calibrate first";
         return WSKPN_EUNSUPPORTED;
     }
+    const size_t HW = (size_t)H * W;
+    uint8_t* A = static_cast<uint8_t*>(ctx->d_tcA);
+    uint8_t* Bf = static_cast<uint8_t*>(ctx->d_tcB);
+    std::vector<void*> x0(B);
+    for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * ctx->layers[0].cin_p * HW;
+    wskpn_status s = launch_prep_fp8(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(),
+                                     ctx->act_scale[0], st, ctx->err);
+    if (s) return s;
+    prof_mark(ctx, 1, st);
+    for (int l = 0; l < c.n_layers; ++l) {
+        const void* in = l % 2 == 0 ? (const void*)A : (const void*)Bf;
+        void* out = l == c.n_layers - 1 ? (void*)z : ((l + 1) % 2 == 0 ? (void*)A : (void*)Bf);
+        s = conv_tc(ctx, l, in, out, B, H, W, st);
+        if (s) return s;
+        prof_mark(ctx, 2 + l, st);
+    }
+    return WSKPN_OK;
+}
+
+wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z, cudaStream_t st) {
+    const wskpn_config& c = ctx->cfg;
+    if (c.prec == WSKPN_FP8) return tc_logits_fp8(ctx, frames, B, H, W, z, st);
     const size_t HW = (size_t)H * W;
     uint8_t* A = static_cast<uint8_t*>(ctx->d_tcA);
     uint8_t* Bf = static_cast<uint8_t*>(ctx->d_tcB);
@@ -735,4 +762,85 @@ wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, 
     return WSKPN_OK;
 }
 
+// max over n non-negative floats (ReLU outputs, [0,1] inputs) by their bit patterns
+__global__ void amax_nonneg_kernel(const float* __restrict__ x, size_t n, unsigned int* __restrict__ out) {
+    unsigned int m = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fmaxf(x[i], 0.f)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+wskpn_status launch_conv_simt(const float* const* in, float* const* out, int B, int H, int W, int Cin, int Cout,
+                              int KS, const float* w_packed, const float* bias_padded, int relu, cudaStream_t st,
+                              std::string& err);
+
 }  // namespace wskpn
+
+using namespace wskpn;
+
+extern "C" wskpn_status wskpn_calibrate(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
+                                        float margin, void* stream) {
+    if (!ctx) return WSKPN_EINVAL;
+    const wskpn_config& c = ctx->cfg;
+    if (c.prec != WSKPN_FP8) {
+        ctx->err = "wskpn_calibrate: only FP8 contexts have activation scales";
+        return WSKPN_EINVAL;
+    }
+    if (!frames || batch < 1 || batch > WSKPN_MAX_BATCH || h < 1 || w < 1 || !(margin >= 1.f)) {
+        ctx->err = "wskpn_calibrate: invalid argument";
+        return WSKPN_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t HW = (size_t)h * w;
+    int maxw = 0;
+    for (int l = 0; l < c.n_layers; ++l) maxw = maxw > c.widths[l] ? maxw : c.widths[l];
+    float* buf[2] = {nullptr, nullptr};
+    unsigned int* d_amax = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(buf[0]);
+        cudaFree(buf[1]);
+        cudaFree(d_amax);
+    };
+    if (cudaMalloc(&buf[0], (size_t)batch * maxw * HW * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&buf[1], (size_t)batch * maxw * HW * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&d_amax, WSKPN_MAX_LAYERS * sizeof(unsigned int)) != cudaSuccess) {
+        cleanup();
+        ctx->err = "wskpn_calibrate: temporary allocation failed";
+        return WSKPN_ENOMEM;
+    }
+    wskpn_status s = WSKPN_OK;
+    cudaMemsetAsync(d_amax, 0, WSKPN_MAX_LAYERS * sizeof(unsigned int), st);
+    std::vector<void*> x0(batch);
+    for (int b = 0; b < batch; ++b) x0[b] = buf[0] + (size_t)b * c.widths[0] * HW;
+    s = launch_prep(frames, batch, h, w, c.gamma, c.depth_near, c.depth_far, x0.data(), 0, st, ctx->err);
+    std::vector<const float*> in(batch);
+    std::vector<float*> out(batch);
+    for (int l = 0; l < c.n_layers && !s; ++l) {
+        amax_nonneg_kernel<<<148, 256, 0, st>>>(buf[l % 2], (size_t)batch * c.widths[l] * HW, d_amax + l);
+        if (l == c.n_layers - 1) break;
+        for (int b = 0; b < batch; ++b) {
+            in[b] = buf[l % 2] + (size_t)b * c.widths[l] * HW;
+            out[b] = buf[(l + 1) % 2] + (size_t)b * c.widths[l + 1] * HW;
+        }
+        const Layer& L = ctx->layers[l];
+        s = launch_conv_simt(in.data(), out.data(), batch, h, w, L.cin, L.cout, c.conv_ks, L.w32, L.b32, 1, st,
+                             ctx->err);
+    }
+    unsigned int h_amax[WSKPN_MAX_LAYERS] = {};
+    if (!s && (cudaMemcpyAsync(h_amax, d_amax, sizeof(h_amax), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+               cudaStreamSynchronize(st) != cudaSuccess)) {
+        ctx->err = "wskpn_calibrate: CUDA error";
+        s = WSKPN_ECUDA;
+    }
+    cleanup();
+    if (s) return s;
+    for (int l = 0; l < c.n_layers; ++l) {
+        float m;
+        std::memcpy(&m, &h_amax[l], sizeof(m));
+        ctx->act_scale[l] = m > 0.f ? m * margin / 448.f : 1.f;
+    }
+    ctx->fp8_calibrated = true;
+    return ctx_repack(ctx, st);
+}

@@ -3,6 +3,7 @@
 // normal linearly scaled from [-1,1] to [0,1] and the depth linearly scaled
 // from [near,far] to [0,1].
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 
@@ -13,6 +14,7 @@ struct PrepArgs {
     PtrBatch<void*> out;
     int H, W;
     float inv_gamma, dnear, dscale;  // dscale = 1 / (far - near)
+    float qscale;                    // e4m3 layout: 1 / activation scale
 };
 
 __device__ __forceinline__ void prep_pixel(const PrepArgs& a, int b, size_t g, size_t HW, float* v) {
@@ -90,6 +92,36 @@ __global__ void prep_nhwc16_bf16x2_kernel(PrepArgs a) {
     }
 }
 
+// Channels-last e4m3 output [H][W][32] (channels 10..31 zero), values
+// divided by the layer-0 activation scale (FP8 tensor-core path).
+__global__ void prep_nhwc32_fp8_kernel(PrepArgs a) {
+    const int b = blockIdx.y;
+    const size_t HW = (size_t)a.H * a.W;
+    uint4* out = static_cast<uint4*>(a.out.p[b]);
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < HW; g += (size_t)gridDim.x * blockDim.x) {
+        float v[16];
+        prep_pixel(a, b, g, HW, v);
+#pragma unroll
+        for (int j = 10; j < 16; ++j) v[j] = 0.f;
+        uint32_t wds[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_fp8x2_storage_t lo =
+                __nv_cvt_float2_to_fp8x2(make_float2(v[4 * j] * a.qscale, v[4 * j + 1] * a.qscale), __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[4 * j + 2] * a.qscale, v[4 * j + 3] * a.qscale), __NV_SATFINITE, __NV_E4M3);
+            wds[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        out[2 * g] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+        out[2 * g + 1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+static thread_local float g_prep_qscale = 1.f;
+
+wskpn_status launch_prep_fp8(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
+                             void* const* out, float act_scale, cudaStream_t st, std::string& err);
+
 wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear,
                          float dfar, void* const* out, int layout, cudaStream_t st, std::string& err) {
     for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
@@ -107,6 +139,7 @@ wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float g
         a.inv_gamma = (float)(1.0 / (double)gamma);
         a.dnear = dnear;
         a.dscale = (float)(1.0 / ((double)dfar - (double)dnear));
+        a.qscale = g_prep_qscale;
         const size_t HW = (size_t)H * W;
         int blocks = (int)((HW + 255) / 256);
         if (blocks > 148 * 8) blocks = 148 * 8;
@@ -115,11 +148,22 @@ wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float g
             prep_planar_kernel<<<grid, 256, 0, st>>>(a);
         else if (layout == 1)
             prep_nhwc16_bf16_kernel<<<grid, 256, 0, st>>>(a);
-        else
+        else if (layout == 2)
             prep_nhwc16_bf16x2_kernel<<<grid, 256, 0, st>>>(a);
+        else
+            prep_nhwc32_fp8_kernel<<<grid, 256, 0, st>>>(a);
         WSKPN_CUDA_TRY(cudaGetLastError(), err);
     }
     return WSKPN_OK;
+}
+
+// layout 3: e4m3 NHWC32 with values / act_scale
+wskpn_status launch_prep_fp8(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
+                             void* const* out, float act_scale, cudaStream_t st, std::string& err) {
+    g_prep_qscale = 1.f / act_scale;
+    const wskpn_status s = launch_prep(frames, B, H, W, gamma, dnear, dfar, out, 3, st, err);
+    g_prep_qscale = 1.f;
+    return s;
 }
 
 }  // namespace wskpn
