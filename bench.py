@@ -278,6 +278,9 @@ def main():
         d = wk.Denoiser(wb, precision=precision, max_hw=(H, W))
         if args.tc_split is not None and precision == "bf16":
             d.set_tuning(2, args.tc_split)
+        if precision == "fp8":  # static activation scales from a different frame (seed 3)
+            cal = synth.make_frame(H, W, SEED + 1)
+            d.calibrate(*[torch.from_numpy(np.ascontiguousarray(cal[k][None])).to(dev) for k in keys])
         out = torch.empty((1, 3, H, W), device=dev)
         for _ in range(warmup):
             d.denoise(*xin, out=out)

@@ -141,6 +141,24 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
     d |= (uint64_t)6 << 61;              // 32-byte swizzle
     return d;
 }
+
+// K-major operand with rows of RB = 32, 64 or 128 bytes and the matching
+// swizzle (32B, 64B, 128B); one MMA reads 32 bytes of each row, selected by
+// adding the byte offset within the row to the start address.
+template <int RB>
+__device__ __forceinline__ uint64_t sdesc_rows(uint32_t saddr) {
+    constexpr uint64_t layout = RB == 128 ? 2 : (RB == 64 ? 4 : 6);
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((8 * RB) >> 4) << 32;  // 8-row groups
+    d |= (uint64_t)1 << 46;
+    d |= layout << 61;
+    return d;
+}
+
+// Channel chunks per TMA box: the widest of 4, 2, 1 that divides the chunk count.
+__host__ __device__ constexpr int chunks_per_box(int ncc_in) { return ncc_in % 4 == 0 ? 4 : (ncc_in % 2 == 0 ? 2 : 1); }
 // The accumulate flag is a compile-time constant: a predicate computed at
 // run time costs about twice the issue time of the MMA itself.
 template <bool FP8, bool ACC>
@@ -212,14 +230,15 @@ __device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t 
     constexpr uint32_t IDESC = (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(N >> 3) << 17) |
                                ((uint32_t)(tc::BM >> 4) << 24);
     constexpr uint32_t b_blk = (COUT_P * tc::ROWB) >> 4;  // one (dx, chunk, dy) block, 16-byte units
-    constexpr uint32_t a_dx = tc::ROWB >> 4;
+    constexpr int CPB = chunks_per_box(NCC_IN);
+    constexpr uint32_t a_dx = (CPB * tc::ROWB) >> 4;       // one pixel row of a box
     const uint32_t d = dbase + (uint32_t)((tc::R - 1 - (RI - DY0)) * COUT_P);
 #pragma unroll
     for (int cc = 0; cc < NCC_IN; ++cc) {
         const int ccw = cc % NCC_W;  // the lo half of a split activation reuses the weights
 #pragma unroll
         for (int dx = 0; dx < KS; ++dx) {
-            const uint64_t a = ad + (uint64_t)(cc * box_step + dx * a_dx);
+            const uint64_t a = ad + (uint64_t)((cc / CPB) * box_step + (cc % CPB) * (tc::ROWB >> 4) + dx * a_dx);
             const uint64_t b = bd + (uint64_t)(((dx * NCC_W + ccw) * KS + DY0) * b_blk);
             mma<FP8, true>(d, a, b, IDESC);
         }
@@ -250,7 +269,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
     constexpr uint32_t NCOL = tmem_cols<COUT_P>();
     constexpr int ROWS_IN = tc::R + KS - 1;
-    constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB;
+    constexpr int CPB = chunks_per_box(NCC_IN);
+    constexpr int NBOX = NCC_IN / CPB;
+    constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB * CPB;
     static_assert(COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256, "MMA N");
     static_assert(2 * tc::R * COUT_P <= 512, "TMEM columns");
 
@@ -333,10 +354,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     }
                     const uint32_t fb = smem_u32(&full[s]);
                     const uint32_t dst = smem_u32(sA + (size_t)s * a.stage_bytes);
-                    mbar_expect_tx(fb, NCC_IN * BOX_BYTES);
+                    mbar_expect_tx(fb, NBOX * BOX_BYTES);
 #pragma unroll
-                    for (int cc = 0; cc < NCC_IN; ++cc)
-                        tma_load_4d(dst + cc * a.box_stride, &tmap, cc * CH, x0 - PAD, y0 - PAD + ri, b, fb);
+                    for (int bx = 0; bx < NBOX; ++bx)
+                        tma_load_4d(dst + bx * a.box_stride, &tmap, bx * CPB * CH, x0 - PAD, y0 - PAD + ri, b, fb);
                 }
             }
             if (!ok) {
@@ -357,7 +378,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             // Descriptors are linear in the start address (16-byte units in
             // the low bits): stages, chunks and taps are offsets from two bases.
             const uint64_t wdesc0 = sdesc_sw32(smem_u32(sW));
-            const uint64_t adesc0 = sdesc_sw32(smem_u32(sA));
+            const uint64_t adesc0 = sdesc_rows<CPB * tc::ROWB>(smem_u32(sA));
             const uint32_t a_stage = a.stage_bytes >> 4;
             const uint32_t box_step = a.box_stride >> 4;
             uint32_t it = 0;
@@ -642,17 +663,19 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     CUtensorMap map;
     cuuint64_t gdim[4] = {(cuuint64_t)cin_row, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
     cuuint64_t gstr[3] = {(cuuint64_t)cin_row * eb, (cuuint64_t)W * cin_row * eb, (cuuint64_t)H * W * cin_row * eb};
-    cuuint32_t box[4] = {(cuuint32_t)ch, (cuuint32_t)(tc::BM + KS - 1), 1, 1};
+    const int ncc_w = L.cin_p / ch;
+    const int ncc_in = ncc_w * (split ? 2 : 1);
+    const int cpb = chunks_per_box(ncc_in);
+    cuuint32_t box[4] = {(cuuint32_t)(ch * cpb), (cuuint32_t)(tc::BM + KS - 1), 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult cr = encode(&map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                          const_cast<void*>(in), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         cpb == 4 ? CU_TENSOR_MAP_SWIZZLE_128B : (cpb == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
         ctx->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
         return WSKPN_ECUDA;
     }
-    const int ncc_w = L.cin_p / ch;
-    const int ncc_in = ncc_w * (split ? 2 : 1);
     TcArgs a{};
     a.wimg = L.wtc;
     a.wbytes = (uint32_t)L.wtc_bytes;
@@ -667,9 +690,9 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     a.relu = !a.last;
     a.split_out = split && !a.last;
     a.out_qscale = fp8 && !a.last ? 1.f / ctx->act_scale[l + 1] : 1.f;
-    // one box of 128 + KS - 1 rows of 32 B per chunk, 256-byte aligned (swizzle atom)
-    a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB + 255) / 256 * 256);
-    a.stage_bytes = (uint32_t)((ncc_in * a.box_stride + 1023) / 1024 * 1024);
+    // boxes of 128 + KS - 1 rows of cpb x 32 B, each 1024-byte aligned (128B-swizzle atom)
+    a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024);
+    a.stage_bytes = (uint32_t)((ncc_in / cpb) * a.box_stride);
     const size_t fixed = 1024 + ((L.wtc_bytes + 1023) / 1024 * 1024) + 256 + 2 * 64 * sizeof(float);
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
         ctx->err = "conv_tc: layer weights and two input stages do not fit in shared memory";

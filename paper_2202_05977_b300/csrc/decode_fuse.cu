@@ -118,6 +118,63 @@ __device__ void window_exact(const float* __restrict__ z, const float* __restric
     R[2] = N2 / D;
 }
 
+// Every load of a thread is issued before any is used (one memory latency
+// per phase instead of one per loop iteration).
+constexpr int REGION_PER_THREAD = (df::RH * df::RW + df::THREADS - 1) / df::THREADS;  // 9
+
+__device__ __forceinline__ void load_irradiance(float* __restrict__ sY, const float* __restrict__ r,
+                                                const float* __restrict__ a, int H, int W, int tx0, int ty0,
+                                                float eps, int tid) {
+    const size_t HW = (size_t)H * W;
+    float rv[REGION_PER_THREAD][3], av[REGION_PER_THREAD][3];
+#pragma unroll
+    for (int j = 0; j < REGION_PER_THREAD; ++j) {
+        const int i = tid + j * df::THREADS;
+        const int ry = i / df::RW, rx = i % df::RW;
+        const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
+        const bool in = i < df::RH * df::RW && gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const size_t g = in ? (size_t)gy * W + gx : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rv[j][c] = in ? __ldg(r + c * HW + g) : 0.f;
+            av[j][c] = in ? __ldg(a + c * HW + g) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < REGION_PER_THREAD; ++j) {
+        const int i = tid + j * df::THREADS;
+        if (i >= df::RH * df::RW) continue;
+        const int ry = i / df::RW, rx = i % df::RW;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sY[(c * df::RH + ry) * df::RP + rx] = rv[j][c] / (av[j][c] + eps);
+    }
+}
+
+// Importance map I_i on the footprint of windows of half-size h into
+// sE plane 0; returns this thread's maximum (-inf outside the image).
+__device__ __forceinline__ float load_importance(float* __restrict__ sE, const float* __restrict__ zi, int H, int W,
+                                                 int tx0, int ty0, int h, int tid) {
+    const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
+    float v[REGION_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < REGION_PER_THREAD; ++j) {
+        const int t = tid + j * df::THREADS;
+        const int gy = ty0 - h + t / nc, gx = tx0 - h + t % nc;
+        const bool in = t < nr * nc && gy >= 0 && gy < H && gx >= 0 && gx < W;
+        v[j] = in ? __ldg(zi + (size_t)gy * W + gx) : -INFINITY;
+    }
+    float m = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < REGION_PER_THREAD; ++j) {
+        const int t = tid + j * df::THREADS;
+        if (t >= nr * nc) continue;
+        const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
+        sE[ry * df::RP + rx] = v[j];
+        m = fmaxf(m, v[j]);
+    }
+    return m;
+}
+
 __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeArgs args) {
     extern __shared__ float smem[];
     float* sY = smem;                          // [3][RH][RP]  irradiance y
@@ -137,15 +194,7 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeA
     const float eps = args.eps;
 
     // Demodulated irradiance on the tile + halo (0 outside the image).
-    for (int i = tid; i < df::RH * df::RW; i += df::THREADS) {
-        const int ry = i / df::RW, rx = i % df::RW;
-        const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const size_t g = (size_t)gy * W + gx;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            sY[(c * df::RH + ry) * df::RP + rx] = in ? r[c * HW + g] / (a[c * HW + g] + eps) : 0.f;
-    }
+    load_irradiance(sY, r, a, H, W, tx0, ty0, eps, tid);
 
     // Fusion weights alpha_i(p): softmax of the M logits of each own pixel.
     float alpha[df::PPT][WSKPN_MAX_KERNELS];
@@ -178,15 +227,7 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeA
         const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
         const float* __restrict__ zi = z + (size_t)i * HW;
         // Footprint of this size's windows: load I_i, find its maximum.
-        float m = -INFINITY;
-        for (int t = tid; t < nr * nc; t += df::THREADS) {
-            const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
-            const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
-            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-            const float v = in ? zi[(size_t)gy * W + gx] : -INFINITY;
-            sE[ry * df::RP + rx] = v;
-            m = fmaxf(m, v);
-        }
+        float m = load_importance(sE, zi, H, W, tx0, ty0, h, tid);
         m = warp_max(m);
         if ((tid & 31) == 0) red[tid >> 5] = m;
         __syncthreads();
@@ -223,8 +264,9 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeA
             const float D = sV[ly * df::TW + lx];
             float R[3];
             if (D >= df::DMIN) {
+                const float invD = 1.f / D;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) R[c] = sV[((1 + c) * df::TH + ly) * df::TW + lx] / D;
+                for (int c = 0; c < 3; ++c) R[c] = sV[((1 + c) * df::TH + ly) * df::TW + lx] * invD;
             } else {
                 window_exact(zi, r, a, H, W, k, eps, gx, gy, R);
                 if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
@@ -334,15 +376,7 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd1_kernel(Decode
     float* __restrict__ dz = args.dz.p[b];
     const float eps = args.eps;
 
-    for (int i = tid; i < df::RH * df::RW; i += df::THREADS) {
-        const int ry = i / df::RW, rx = i % df::RW;
-        const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const size_t g = (size_t)gy * W + gx;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            sY[(c * df::RH + ry) * df::RP + rx] = in ? r[c * HW + g] / (a[c * HW + g] + eps) : 0.f;
-    }
+    load_irradiance(sY, r, a, H, W, tx0, ty0, eps, tid);
 
     float alpha[df::PPT][WSKPN_MAX_KERNELS];
     float dal[df::PPT][WSKPN_MAX_KERNELS];
@@ -384,15 +418,7 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd1_kernel(Decode
         const int h = k / 2;
         const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
         const float* __restrict__ zi = z + (size_t)i * HW;
-        float m = -INFINITY;
-        for (int t = tid; t < nr * nc; t += df::THREADS) {
-            const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
-            const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
-            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-            const float v = in ? zi[(size_t)gy * W + gx] : -INFINITY;
-            sE[ry * df::RP + rx] = v;
-            m = fmaxf(m, v);
-        }
+        float m = load_importance(sE, zi, H, W, tx0, ty0, h, tid);
         m = warp_max(m);
         if ((tid & 31) == 0) red[tid >> 5] = m;
         __syncthreads();
