@@ -40,24 +40,26 @@ struct DecodeArgs {
 };
 
 // Horizontal window sums of the 4 planes (E, E*y0, E*y1, E*y2) for the rows
-// the vertical pass needs.  One thread walks one (plane, row, half-row) and
-// keeps the 32 + K - 1 inputs in registers.
+// the vertical pass needs.  One thread walks one (plane, row, 16-pixel
+// segment) and keeps the 16 + K - 1 inputs in registers.
 template <int K>
 __device__ __forceinline__ void hpass(const float* __restrict__ sE, float* __restrict__ sH, int tid) {
     constexpr int h = K / 2;
     constexpr int NR = df::TH + 2 * h;
-    for (int it = tid; it < 4 * 2 * NR; it += df::THREADS) {
+    constexpr int SEG = 16;                 // outputs per item
+    constexpr int NSEG = df::TW / SEG;      // 4
+    for (int it = tid; it < 4 * NSEG * NR; it += df::THREADS) {
         const int row = it % NR;
-        const int half = (it / NR) & 1;
-        const int ch = it / (2 * NR);
+        const int seg = (it / NR) % NSEG;
+        const int ch = it / (NSEG * NR);
         const int ry = df::HALO - h + row;
-        const float* src = sE + (ch * df::RH + ry) * df::RP + (df::HALO - h) + half * 32;
-        float* dst = sH + (ch * df::RH + ry) * df::HP + half * 32;
-        float win[32 + K - 1];
+        const float* src = sE + (ch * df::RH + ry) * df::RP + (df::HALO - h) + seg * SEG;
+        float* dst = sH + (ch * df::RH + ry) * df::HP + seg * SEG;
+        float win[SEG + K - 1];
 #pragma unroll
-        for (int j = 0; j < 32 + K - 1; ++j) win[j] = src[j];
+        for (int j = 0; j < SEG + K - 1; ++j) win[j] = src[j];
 #pragma unroll
-        for (int x = 0; x < 32; ++x) {
+        for (int x = 0; x < SEG; ++x) {
             float s = win[x];
 #pragma unroll
             for (int d = 1; d < K; ++d) s += win[x + d];
@@ -93,7 +95,7 @@ __device__ __forceinline__ void box_sums(const float* sE, float* sH, float* sV, 
 }
 
 // Exact per-window evaluation of Eq. 3-4 for one pixel (slow path).
-__device__ void window_exact(const float* __restrict__ z, const float* __restrict__ r,
+__device__ __noinline__ void window_exact(const float* __restrict__ z, const float* __restrict__ r,
                              const float* __restrict__ a, int H, int W, int k, float eps, int px,
                              int py, float R[3]) {
     const int h = k / 2;
@@ -150,29 +152,59 @@ __device__ __forceinline__ void load_irradiance(float* __restrict__ sY, const fl
     }
 }
 
-// Importance map I_i on the footprint of windows of half-size h into
-// sE plane 0; returns this thread's maximum (-inf outside the image).
-__device__ __forceinline__ float load_importance(float* __restrict__ sE, const float* __restrict__ zi, int H, int W,
-                                                 int tx0, int ty0, int h, int tid) {
-    const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
-    float v[REGION_PER_THREAD];
+// For one window size K (compile-time, so all index arithmetic divides by
+// constants): load I_i on the footprint of the tile's windows, shift by its
+// maximum m, form E = exp(I - m) and E*y in smem (E = 0 outside the image)
+// and take the K x K window sums into sV.  Returns m.
+template <int K>
+__device__ __noinline__ float size_sums(float* __restrict__ sE, float* __restrict__ sH, float* __restrict__ sV,
+                                           const float* __restrict__ sY, float* __restrict__ red,
+                                           const float* __restrict__ zi, int H, int W, int tx0, int ty0, int tid) {
+    constexpr int h = K / 2, NR = df::TH + 2 * h, NC = df::TW + 2 * h, NT = NR * NC;
+    constexpr int PER = (NT + df::THREADS - 1) / df::THREADS;
+    float v[PER];
 #pragma unroll
-    for (int j = 0; j < REGION_PER_THREAD; ++j) {
+    for (int j = 0; j < PER; ++j) {
         const int t = tid + j * df::THREADS;
-        const int gy = ty0 - h + t / nc, gx = tx0 - h + t % nc;
-        const bool in = t < nr * nc && gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const int gy = ty0 - h + t / NC, gx = tx0 - h + t % NC;
+        const bool in = t < NT && gy >= 0 && gy < H && gx >= 0 && gx < W;
         v[j] = in ? __ldg(zi + (size_t)gy * W + gx) : -INFINITY;
     }
     float m = -INFINITY;
 #pragma unroll
-    for (int j = 0; j < REGION_PER_THREAD; ++j) {
+    for (int j = 0; j < PER; ++j) m = fmaxf(m, v[j]);
+    m = warp_max(m);
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    m = red[0];
+#pragma unroll
+    for (int w = 1; w < df::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
         const int t = tid + j * df::THREADS;
-        if (t >= nr * nc) continue;
-        const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
-        sE[ry * df::RP + rx] = v[j];
-        m = fmaxf(m, v[j]);
+        if (PER * df::THREADS > NT && t >= NT) continue;
+        const int o = (df::HALO - h + t / NC) * df::RP + (df::HALO - h + t % NC);
+        const float e = expf(v[j] - m);
+        sE[o] = e;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sE[(1 + c) * df::RH * df::RP + o] = e * sY[c * df::RH * df::RP + o];
     }
+    __syncthreads();
+    box_sums<K>(sE, sH, sV, tid);
     return m;
+}
+
+__device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float* sV, const float* sY, float* red,
+                                             const float* zi, int H, int W, int tx0, int ty0, int tid) {
+    switch (k) {
+        case 1: return size_sums<1>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
+        case 3: return size_sums<3>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
+        case 5: return size_sums<5>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
+        case 7: return size_sums<7>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
+        case 9: return size_sums<9>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
+        case 11: return size_sums<11>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
+        default: return size_sums<13>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
+    }
 }
 
 __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeArgs args) {
@@ -196,64 +228,30 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeA
     // Demodulated irradiance on the tile + halo (0 outside the image).
     load_irradiance(sY, r, a, H, W, tx0, ty0, eps, tid);
 
-    // Fusion weights alpha_i(p): softmax of the M logits of each own pixel.
-    float alpha[df::PPT][WSKPN_MAX_KERNELS];
+    // Fusion weights alpha_i(p) = exp(l_i - lmax) / sum_j exp(l_j - lmax)
+    // over the M logits of each own pixel; only lmax and 1/sum are kept.
+    float lmax[df::PPT], linv[df::PPT];
     float acc[df::PPT][3];
 #pragma unroll
     for (int j = 0; j < df::PPT; ++j) {
         const int p = tid + j * df::THREADS;
         const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
         const bool in = gy < H && gx < W;
+        const size_t g = in ? (size_t)gy * W + gx : 0;
         float m = -INFINITY;
-#pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) {
-            alpha[j][i] = (i < M && in) ? z[(size_t)(M + i) * HW + (size_t)gy * W + gx] : -INFINITY;
-            m = fmaxf(m, alpha[j][i]);
-        }
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) {
-            alpha[j][i] = (i < M && in) ? expf(alpha[j][i] - m) : 0.f;
-            s += alpha[j][i];
-        }
-#pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) alpha[j][i] = in ? alpha[j][i] / s : 0.f;
+        for (int i = 0; i < M; ++i) m = fmaxf(m, in ? __ldg(z + (size_t)(M + i) * HW + g) : 0.f);
+        float sum = 0.f;
+        for (int i = 0; i < M; ++i) sum += in ? expf(__ldg(z + (size_t)(M + i) * HW + g) - m) : 1.f;
+        lmax[j] = m;
+        linv[j] = 1.f / sum;
         acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
     }
 
     for (int i = 0; i < M; ++i) {
         const int k = args.ks[i];
-        const int h = k / 2;
-        const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
         const float* __restrict__ zi = z + (size_t)i * HW;
-        // Footprint of this size's windows: load I_i, find its maximum.
-        float m = load_importance(sE, zi, H, W, tx0, ty0, h, tid);
-        m = warp_max(m);
-        if ((tid & 31) == 0) red[tid >> 5] = m;
-        __syncthreads();
-        m = red[0];
-#pragma unroll
-        for (int w = 1; w < df::THREADS / 32; ++w) m = fmaxf(m, red[w]);
-        // E = exp(I - m) and E*y on the footprint (E = 0 outside the image).
-        for (int t = tid; t < nr * nc; t += df::THREADS) {
-            const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
-            const int o = ry * df::RP + rx;
-            const float e = expf(sE[o] - m);
-            sE[o] = e;
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                sE[(1 + c) * df::RH * df::RP + o] = e * sY[c * df::RH * df::RP + o];
-        }
-        __syncthreads();
-        switch (k) {
-            case 1: box_sums<1>(sE, sH, sV, tid); break;
-            case 3: box_sums<3>(sE, sH, sV, tid); break;
-            case 5: box_sums<5>(sE, sH, sV, tid); break;
-            case 7: box_sums<7>(sE, sH, sV, tid); break;
-            case 9: box_sums<9>(sE, sH, sV, tid); break;
-            case 11: box_sums<11>(sE, sH, sV, tid); break;
-            default: box_sums<13>(sE, sH, sV, tid); break;
-        }
+        // E_i = exp(I_i - m) and E_i * y on the footprint, then window sums
+        size_sums_k(k, sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < df::PPT; ++j) {
@@ -271,10 +269,7 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeA
                 window_exact(zi, r, a, H, W, k, eps, gx, gy, R);
                 if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
             }
-            float al = 0.f;
-#pragma unroll
-            for (int q = 0; q < WSKPN_MAX_KERNELS; ++q)
-                if (q == i) al = alpha[j][q];
+            const float al = expf(__ldg(z + (size_t)(M + i) * HW + (size_t)gy * W + gx) - lmax[j]) * linv[j];
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[j][c] = fmaf(al, R[c], acc[j][c]);
         }
@@ -416,33 +411,8 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd1_kernel(Decode
     for (int i = 0; i < M; ++i) {
         const int k = args.ks[i];
         const int h = k / 2;
-        const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
         const float* __restrict__ zi = z + (size_t)i * HW;
-        float m = load_importance(sE, zi, H, W, tx0, ty0, h, tid);
-        m = warp_max(m);
-        if ((tid & 31) == 0) red[tid >> 5] = m;
-        __syncthreads();
-        m = red[0];
-#pragma unroll
-        for (int w = 1; w < df::THREADS / 32; ++w) m = fmaxf(m, red[w]);
-        for (int t = tid; t < nr * nc; t += df::THREADS) {
-            const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
-            const int o = ry * df::RP + rx;
-            const float e = expf(sE[o] - m);
-            sE[o] = e;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sE[(1 + c) * df::RH * df::RP + o] = e * sY[c * df::RH * df::RP + o];
-        }
-        __syncthreads();
-        switch (k) {
-            case 1: box_sums<1>(sE, sH, sV, tid); break;
-            case 3: box_sums<3>(sE, sH, sV, tid); break;
-            case 5: box_sums<5>(sE, sH, sV, tid); break;
-            case 7: box_sums<7>(sE, sH, sV, tid); break;
-            case 9: box_sums<9>(sE, sH, sV, tid); break;
-            case 11: box_sums<11>(sE, sH, sV, tid); break;
-            default: box_sums<13>(sE, sH, sV, tid); break;
-        }
+        const float m = size_sums_k(k, sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < df::PPT; ++j) {
