@@ -233,6 +233,23 @@ wskpn_status wskpn_l1_loss(wskpn_ctx* ctx, const float* out, const float* target
 wskpn_status wskpn_adam_step(wskpn_ctx* ctx, const float* dweights, float lr, float beta1,
                              float beta2, float eps, int step, void* stream);
 
+/* ---- RepVGG re-parameterisation (Sec. 4.1) -------------------------- */
+
+/* Folds one training-time block (5x5, 3x3 and 1x1 conv branches, plus the
+ * identity when `identity` is set, which needs cin == cout) into the single
+ * 5x5 conv used at inference: W = w5 + pad(w3) + pad(w1) (+ centre 1 on the
+ * diagonal), b = b5 + b3 + b1.  Device float32, layouts [cout][cin][k][k]
+ * and [cout]; w_out [cout][cin][5][5], b_out [cout].  Errors: EINVAL, ECUDA. */
+wskpn_status wskpn_repvgg_fold(const float* w5, const float* b5, const float* w3, const float* b3,
+                               const float* w1, const float* b1, int cin, int cout, int identity,
+                               float* w_out, float* b_out, void* stream);
+
+/* Gradient of the fold: from dL/dW [cout][cin][5][5] writes dL/dw5 (same
+ * shape), dL/dw3 [cout][cin][3][3] and dL/dw1 [cout][cin][1][1] (any may be
+ * NULL); every branch bias receives dL/db unchanged.  Errors: EINVAL, ECUDA. */
+wskpn_status wskpn_repvgg_fold_grad(const float* gW, int cin, int cout, float* g5, float* g3, float* g1,
+                                    void* stream);
+
 /* ---- Serving: continuous batching of frame-denoise requests --------- */
 
 typedef struct wskpn_server wskpn_server;

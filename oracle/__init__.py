@@ -274,6 +274,33 @@ def smape_loss(out, target, eps: float = 0.01):
     return float((num / den).sum() / n), g
 
 
+# ---------------------------------------------------------------- RepVGG
+def repvgg_fold(w5, b5, w3, b3, w1, b1, identity: bool):
+    """Sec. 4.1: a training-time block sums a 5x5, a 3x3 and a 1x1 conv
+    branch (all zero-padded to 'same' size) and, when Cin == Cout, the input
+    itself; being linear, it equals one 5x5 conv whose kernel is the sum of
+    the branch kernels zero-padded to 5x5 (plus a centre 1 on the diagonal
+    for the identity) and whose bias is the sum of the biases.
+    w5 [Co,Ci,5,5], w3 [Co,Ci,3,3], w1 [Co,Ci,1,1].  Returns (W [Co,Ci,5,5], b [Co])."""
+    w5, w3, w1 = _d(w5), _d(w3), _d(w1)
+    co, ci = w5.shape[:2]
+    W = w5.copy()
+    W[:, :, 1:4, 1:4] += w3
+    W[:, :, 2, 2] += w1[:, :, 0, 0]
+    if identity:
+        assert co == ci
+        for c in range(co):
+            W[c, c, 2, 2] += 1.0
+    return W, _d(b5) + _d(b3) + _d(b1)
+
+
+def repvgg_fold_grad(gW):
+    """Gradient of the fold: (dL/dw5, dL/dw3, dL/dw1) from dL/dW [Co,Ci,5,5];
+    each bias receives dL/db unchanged."""
+    gW = _d(gW)
+    return gW.copy(), gW[:, :, 1:4, 1:4].copy(), gW[:, :, 2:3, 2:3].copy()
+
+
 # ------------------------------------------------------------------ Adam
 def adam_step(w, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba, Algorithm 1; the optimiser named in

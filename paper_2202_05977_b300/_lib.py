@@ -81,6 +81,8 @@ SIGNATURES = {
     "wskpn_backward": ([_P, _FR, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "wskpn_l1_loss": ([_P, _P, _P, _SZ, _P, _P, _P], _I),
     "wskpn_adam_step": ([_P, _P, _F, _F, _F, _F, _I, _P], _I),
+    "wskpn_repvgg_fold": ([_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P], _I),
+    "wskpn_repvgg_fold_grad": ([_P, _I, _I, _P, _P, _P, _P], _I),
     "wskpn_serve_config_default": ([ctypes.POINTER(ServeConfig)], _I),
     "wskpn_serve_start": ([ctypes.POINTER(Config), _P, _SZ, ctypes.POINTER(ServeConfig), ctypes.POINTER(_P)], _I),
     "wskpn_serve_submit": ([_P, _I, _FR, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)], _I),

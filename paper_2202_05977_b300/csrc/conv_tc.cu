@@ -101,13 +101,18 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 // Bounded wait: false when the limit expired or another role aborted.
+// SLEEP_NS > 0 parks the thread between polls, so a waiting warp does not
+// take issue slots from the MMA-issuing warp on the same sub-partition.
+template <int SLEEP_NS>
 __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int* abort_flag) {
     if (mbar_try_wait(a, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
 #pragma unroll 1
-        for (int i = 0; i < 32; ++i)
+        for (int i = 0; i < 8; ++i) {
             if (mbar_try_wait(a, parity)) return true;
+            if (SLEEP_NS > 0) __nanosleep(SLEEP_NS);
+        }
         if (*abort_flag) return false;
         if (gtimer() - t0 > tc::WAIT_NS) return false;
     }
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const int x0 = tx * tc::BM, y0 = ty * tc::R;
                 for (int ri = 0; ri < ROWS_IN; ++ri, ++it) {
                     const int s = it % S;
-                    if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag)) {
+                    if (!mbar_wait<64>(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -368,13 +373,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const uint32_t n_in_flight = it < (uint32_t)S ? it : (uint32_t)S;
             for (uint32_t k = 0; k < n_in_flight; ++k) {
                 const uint32_t j = it - 1 - k;
-                mbar_wait(smem_u32(&full[j % S]), (j / S) & 1u, abort_flag);
+                mbar_wait<64>(smem_u32(&full[j % S]), (j / S) & 1u, abort_flag);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag);
+            bool ok = mbar_wait<0>(smem_u32(wbar), 0, abort_flag);
             // Descriptors are linear in the start address (16-byte units in
             // the low bits): stages, chunks and taps are offsets from two bases.
             const uint64_t wdesc0 = sdesc_sw32(smem_u32(sW));
@@ -385,7 +390,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             int lt = 0;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
                 const int buf = lt & 1;
-                if (!mbar_wait(smem_u32(&acce[buf]), ((lt >> 1) & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait<0>(smem_u32(&acce[buf]), ((lt >> 1) & 1) ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -393,7 +398,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const uint32_t dbase = tmem + (uint32_t)(buf * tc::R * COUT_P);
                 for (int ri = 0; ri < ROWS_IN; ++ri, ++it) {
                     const int s = it % S;
-                    if (!mbar_wait(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
+                    if (!mbar_wait<0>(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             }
             // Every issued MMA must complete before TMEM is released.
             mma_commit(smem_u32(fin));
-            mbar_wait(smem_u32(fin), 0, abort_flag);
+            mbar_wait<0>(smem_u32(fin), 0, abort_flag);
         }
     } else {
         // ------------------------------------------------ epilogue warps 2..5
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
             const int buf = lt & 1;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag);
+            if (lane == 0) ok = mbar_wait<256>(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 if (lane == 0) {

@@ -326,3 +326,30 @@ def test_adam_first_step_is_signed_lr_and_matches_torch():
         opt.step()
         w, m, v = oracle.adam_step(w, gs, m, v, step, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-8)
     np.testing.assert_allclose(w, wt.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("ci,co,identity", [(6, 5, False), (4, 4, True)])
+def test_repvgg_fold_equals_multi_branch_block(ci, co, identity):
+    # Sec. 4.1: the converted single 5x5 conv computes the same as the sum of
+    # the 5x5, 3x3, 1x1 branches (+ identity) -- torch float64 convs per branch.
+    g = _rng(50 + ci)
+    w5, w3, w1 = g.standard_normal((co, ci, 5, 5)), g.standard_normal((co, ci, 3, 3)), g.standard_normal((co, ci, 1, 1))
+    b5, b3, b1 = g.standard_normal(co), g.standard_normal(co), g.standard_normal(co)
+    x = torch.from_numpy(g.standard_normal((1, ci, 9, 11)))
+    ref = (F.conv2d(x, torch.from_numpy(w5), torch.from_numpy(b5), padding=2)
+           + F.conv2d(x, torch.from_numpy(w3), torch.from_numpy(b3), padding=1)
+           + F.conv2d(x, torch.from_numpy(w1), torch.from_numpy(b1)))
+    if identity:
+        ref = ref + x
+    W, b = oracle.repvgg_fold(w5, b5, w3, b3, w1, b1, identity)
+    np.testing.assert_allclose(oracle.conv2d(x[0].numpy(), W, b, relu=False), ref[0].numpy(), rtol=1e-12, atol=1e-12)
+    # the fold's gradient maps dL/dW back to the branches (torch autograd through the block)
+    w5t, w3t, w1t = (torch.from_numpy(t).requires_grad_() for t in (w5, w3, w1))
+    gy = torch.from_numpy(g.standard_normal(ref.shape))
+    (F.conv2d(x, w5t, padding=2) + F.conv2d(x, w3t, padding=1) + F.conv2d(x, w1t)).mul(gy).sum().backward()
+    Wt = torch.from_numpy(W).requires_grad_()
+    F.conv2d(x, Wt, padding=2).mul(gy).sum().backward()
+    g5, g3, g1 = oracle.repvgg_fold_grad(Wt.grad.numpy())
+    np.testing.assert_allclose(g5, w5t.grad.numpy(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g3, w3t.grad.numpy(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g1, w1t.grad.numpy(), rtol=1e-12, atol=1e-12)
