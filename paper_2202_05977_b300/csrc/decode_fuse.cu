@@ -207,85 +207,312 @@ __device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float*
     }
 }
 
-__global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_fwd_kernel(DecodeArgs args) {
-    extern __shared__ float smem[];
-    float* sY = smem;                          // [3][RH][RP]  irradiance y
-    float* sE = sY + 3 * df::RH * df::RP;      // [4][RH][RP]  E, E*y  (reused as sV)
-    float* sH = sE + 4 * df::RH * df::RP;      // [4][RH][HP]  horizontal sums
-    float* sV = sE;                            // [4][TH][TW]
-    __shared__ float red[df::THREADS / 32];
+// ---------------------------------------------------------------- forward
+// The forward kernel keeps the same tile (64 x 16 outputs, 6-pixel halo) but
+// organises each size's work for instruction economy:
+//  * the horizontal pass forms E and E*y on the fly from the E and y planes
+//    and handles the four planes as two packed pairs (D, N0) and (N1, N2)
+//    with paired FP32 adds;
+//  * a K-wide window sum is built from sums of 2, 4 and 8 neighbours taken
+//    once per row segment and combined by the binary digits of K (all
+//    terms positive, so no cancellation);
+//  * the vertical pass of one column produces D and N directly for the
+//    thread's own 4 pixels, which accumulate alpha_i R_i in registers;
+//  * alpha (Eq. 5) is computed once per pixel into shared memory.
+namespace dfw {
+constexpr int TW = 64;                  // tile width (output pixels)
+constexpr int TH = 16;                  // tile height
+constexpr int HALO = 6;                 // largest half window (k = 13)
+constexpr int RW = TW + 2 * HALO;       // 76: region pitch in floats (76 / 4 odd: row-strided 16-byte accesses are conflict-free)
+constexpr int RH = TH + 2 * HALO;       // 28
+constexpr int SEG = 8;                  // horizontal-pass outputs per item
+constexpr int NSEG = TW / SEG;          // 8
+constexpr int HP2 = TW + 2;             // pitch of the packed horizontal-sum rows in float2 (132 floats, 132 / 4 odd)
+constexpr int THREADS = 256;
+constexpr int RPT = TH * TW / THREADS;  // 4 output pixels per thread, one column
+static_assert(THREADS / TW * RPT == TH, "vertical-pass mapping");
+static_assert(RH * NSEG <= THREADS, "one horizontal item per thread");
+constexpr int MAXK = WSKPN_MAX_KERNELS;
+// shared memory in floats: y [3][RH][RW] | E [RH][RW] | hsum [2][RH][HP2] float2 | alpha [MAXK][TH][TW] |
+// acc [RPT * 3][THREADS]
+constexpr int OFF_Y = 0;
+constexpr int OFF_E = OFF_Y + 3 * RH * RW;
+constexpr int OFF_H = OFF_E + RH * RW;
+constexpr int OFF_A = OFF_H + 2 * RH * HP2 * 2;
+constexpr int OFF_ACC = OFF_A + MAXK * TH * TW;
+constexpr int SMEM_FLOATS = OFF_ACC + RPT * 3 * THREADS;
+constexpr size_t SMEM_BYTES = SMEM_FLOATS * sizeof(float);
+static_assert(OFF_E % 4 == 0 && OFF_H % 4 == 0 && OFF_A % 4 == 0, "16-byte aligned planes");
+}  // namespace dfw
+
+// s[x] = sum_{d < K} w[x + d], x < NOUT, for two planes at once.  Sums of 2,
+// 4 and 8 consecutive inputs are formed once and the window is assembled
+// from the binary digits of K (K <= 15); values no output needs are never
+// computed (the arrays are fully unrolled).
+template <int K, int NOUT>
+__device__ __forceinline__ void box_sum2(const float2 (&w)[NOUT + K - 1], float2 (&s)[NOUT]) {
+    constexpr int N1 = NOUT + K - 1;
+    constexpr int B8 = K & 8, B4 = K & 4, B2 = K & 2, B1 = K & 1;
+    constexpr int O4 = B8, O2 = B8 + B4, O1 = B8 + B4 + B2;
+    static_assert(K >= 1 && K <= 15, "window");
+    float2 p2[N1 > 1 ? N1 - 1 : 1], p4[N1 > 3 ? N1 - 3 : 1], p8[N1 > 7 ? N1 - 7 : 1];
+#pragma unroll
+    for (int j = 0; j + 1 < N1; ++j) p2[j] = __fadd2_rn(w[j], w[j + 1]);
+#pragma unroll
+    for (int j = 0; j + 3 < N1; ++j) p4[j] = __fadd2_rn(p2[j], p2[j + 2]);
+#pragma unroll
+    for (int j = 0; j + 7 < N1; ++j) p8[j] = __fadd2_rn(p4[j], p4[j + 4]);
+#pragma unroll
+    for (int x = 0; x < NOUT; ++x) {
+        float2 t = make_float2(0.f, 0.f);
+        if constexpr (B8 != 0) t = p8[x];
+        if constexpr (B4 != 0) {
+            if constexpr (O4 != 0) t = __fadd2_rn(t, p4[x + O4]);
+            else t = p4[x];
+        }
+        if constexpr (B2 != 0) {
+            if constexpr (O2 != 0) t = __fadd2_rn(t, p2[x + O2]);
+            else t = p2[x];
+        }
+        if constexpr (B1 != 0) {
+            if constexpr (O1 != 0) t = __fadd2_rn(t, w[x + O1]);
+            else t = w[x];
+        }
+        s[x] = t;
+    }
+}
+
+// Horizontal window sums of (E, E y0) and (E y1, E y2) for the NR footprint
+// rows of size K: one thread per (row, 8-pixel segment).  Inputs are read
+// as 16-byte vectors from the aligned column at or before the footprint's
+// first column; rows of consecutive threads are one region pitch apart.
+template <int K>
+__device__ __forceinline__ void fwd_hpass(const float* __restrict__ sE, const float* __restrict__ sY,
+                                          float2* __restrict__ sH, int tid) {
+    constexpr int h = K / 2, NR = dfw::TH + 2 * h;
+    constexpr int C0 = dfw::HALO - h;
+    constexpr int A0 = C0 & ~3;
+    constexpr int OFF = C0 - A0;
+    constexpr int NIN = dfw::SEG + K - 1;
+    constexpr int NV = (OFF + NIN + 3) / 4;
+    static_assert(A0 + (dfw::NSEG - 1) * dfw::SEG + 4 * NV <= dfw::RW, "aligned row reads stay in the region");
+    if (tid >= NR * dfw::NSEG) return;
+    const int row = tid % NR, seg = tid / NR;
+    const int base = (dfw::HALO - h + row) * dfw::RW + seg * dfw::SEG + A0;
+    float e[4 * NV], y[4 * NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const float4 t = *reinterpret_cast<const float4*>(sE + base + 4 * v);
+        e[4 * v] = t.x; e[4 * v + 1] = t.y; e[4 * v + 2] = t.z; e[4 * v + 3] = t.w;
+    }
+    float2 w[NIN], s01[dfw::SEG], s23[dfw::SEG];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const float4 t = *reinterpret_cast<const float4*>(sY + base + 4 * v);
+        y[4 * v] = t.x; y[4 * v + 1] = t.y; y[4 * v + 2] = t.z; y[4 * v + 3] = t.w;
+    }
+#pragma unroll
+    for (int j = 0; j < NIN; ++j) w[j] = make_float2(e[OFF + j], e[OFF + j] * y[OFF + j]);
+    box_sum2<K, dfw::SEG>(w, s01);
+    float y2[4 * NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const float4 t = *reinterpret_cast<const float4*>(sY + dfw::RH * dfw::RW + base + 4 * v);
+        const float4 u = *reinterpret_cast<const float4*>(sY + 2 * dfw::RH * dfw::RW + base + 4 * v);
+        y[4 * v] = t.x; y[4 * v + 1] = t.y; y[4 * v + 2] = t.z; y[4 * v + 3] = t.w;
+        y2[4 * v] = u.x; y2[4 * v + 1] = u.y; y2[4 * v + 2] = u.z; y2[4 * v + 3] = u.w;
+    }
+#pragma unroll
+    for (int j = 0; j < NIN; ++j)
+        w[j] = __fmul2_rn(make_float2(e[OFF + j], e[OFF + j]), make_float2(y[OFF + j], y2[OFF + j]));
+    box_sum2<K, dfw::SEG>(w, s23);
+    float2* d01 = sH + row * dfw::HP2 + seg * dfw::SEG;
+    float2* d23 = d01 + dfw::RH * dfw::HP2;
+#pragma unroll
+    for (int x = 0; x < dfw::SEG; x += 2) {
+        *reinterpret_cast<float4*>(d01 + x) = make_float4(s01[x].x, s01[x].y, s01[x + 1].x, s01[x + 1].y);
+        *reinterpret_cast<float4*>(d23 + x) = make_float4(s23[x].x, s23[x].y, s23[x + 1].x, s23[x + 1].y);
+    }
+}
+
+// One window size K: footprint logits and their maximum, E = exp(I_i - m)
+// (0 outside the image), horizontal then vertical window sums, and
+// acc += alpha_i R_i for the thread's own pixels (column x, rows
+// RPT * rg ...), kept in shared memory [RPT * 3][THREADS] so that each size
+// is a separate function with its own register allocation.  Three block
+// barriers; the next size's first barrier orders this size's reads of E and
+// the sums before they are overwritten.
+template <int K>
+__device__ __noinline__ void fwd_size(float* __restrict__ sE, float2* __restrict__ sH,
+                                         const float* __restrict__ sY, const float* __restrict__ sAl,
+                                         float* __restrict__ red, const float* __restrict__ zi,
+                                         const float* __restrict__ r, const float* __restrict__ a, int H, int W,
+                                         int tx0, int ty0, int tid, float eps, unsigned int* fallbacks,
+                                         float* __restrict__ sAcc) {
+    constexpr int h = K / 2, NR = dfw::TH + 2 * h, NC = dfw::TW + 2 * h, NT = NR * NC;
+    constexpr int PER = (NT + dfw::THREADS - 1) / dfw::THREADS;
+    float v[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int t = tid + j * dfw::THREADS;
+        const int gy = ty0 - h + t / NC, gx = tx0 - h + t % NC;
+        const bool in = t < NT && gy >= 0 && gy < H && gx >= 0 && gx < W;
+        v[j] = in ? __ldg(zi + (size_t)gy * W + gx) : -INFINITY;
+    }
+    float m = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) m = fmaxf(m, v[j]);
+    m = warp_max(m);
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    m = red[0];
+#pragma unroll
+    for (int w = 1; w < dfw::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int t = tid + j * dfw::THREADS;
+        if (PER * dfw::THREADS > NT && t >= NT) continue;
+        sE[(dfw::HALO - h + t / NC) * dfw::RW + (dfw::HALO - h + t % NC)] = expf(v[j] - m);
+    }
+    __syncthreads();
+    fwd_hpass<K>(sE, sY, sH, tid);
+    __syncthreads();
+
+    const int x = tid % dfw::TW, rg = tid / dfw::TW;
+    constexpr int NIN = dfw::RPT + K - 1;
+    float2 c[NIN], s01[dfw::RPT], s23[dfw::RPT];
+#pragma unroll
+    for (int j = 0; j < NIN; ++j) c[j] = sH[(rg * dfw::RPT + j) * dfw::HP2 + x];
+    box_sum2<K, dfw::RPT>(c, s01);
+#pragma unroll
+    for (int j = 0; j < NIN; ++j) c[j] = sH[(dfw::RH + rg * dfw::RPT + j) * dfw::HP2 + x];
+    box_sum2<K, dfw::RPT>(c, s23);
+    const int gx = tx0 + x;
+#pragma unroll
+    for (int j = 0; j < dfw::RPT; ++j) {
+        const int ly = rg * dfw::RPT + j, gy = ty0 + ly;
+        if (gy >= H || gx >= W) continue;
+        float R[3];
+        const float D = s01[j].x;
+        if (D >= df::DMIN) {
+            const float invD = 1.f / D;
+            R[0] = s01[j].y * invD;
+            R[1] = s23[j].x * invD;
+            R[2] = s23[j].y * invD;
+        } else {
+            window_exact(zi, r, a, H, W, K, eps, gx, gy, R);
+            if (fallbacks) atomicAdd(fallbacks, 1u);
+        }
+        const float al = sAl[ly * dfw::TW + x];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float* p = sAcc + (j * 3 + ch) * dfw::THREADS + tid;
+            *p = fmaf(al, R[ch], *p);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(DecodeArgs args) {
+    extern __shared__ float4 dsm4[];
+    float* smem = reinterpret_cast<float*>(dsm4);
+    float* sY = smem + dfw::OFF_Y;
+    float* sE = smem + dfw::OFF_E;
+    float2* sH = reinterpret_cast<float2*>(smem + dfw::OFF_H);
+    float* sAl = smem + dfw::OFF_A;
+    float* sAcc = smem + dfw::OFF_ACC;
+    __shared__ float red[dfw::THREADS / 32];
 
     const int tid = threadIdx.x;
     const int b = blockIdx.z;
     const int H = args.H, W = args.W, M = args.M;
     const size_t HW = (size_t)H * W;
-    const int tx0 = blockIdx.x * df::TW, ty0 = blockIdx.y * df::TH;
+    const int tx0 = blockIdx.x * dfw::TW, ty0 = blockIdx.y * dfw::TH;
     const float* __restrict__ z = args.z.p[b];
     const float* __restrict__ r = args.r.p[b];
     const float* __restrict__ a = args.a.p[b];
     const float eps = args.eps;
 
-    // Demodulated irradiance on the tile + halo (0 outside the image).
-    load_irradiance(sY, r, a, H, W, tx0, ty0, eps, tid);
-
-    // Fusion weights alpha_i(p) = exp(l_i - lmax) / sum_j exp(l_j - lmax)
-    // over the M logits of each own pixel; only lmax and 1/sum are kept.
-    float lmax[df::PPT], linv[df::PPT];
-    float acc[df::PPT][3];
+    // Demodulated irradiance y = r / (a + eps) on tile + halo (0 outside the image);
+    // every load of the phase is issued before any is used.
+    {
+        constexpr int NREG = dfw::RH * dfw::RW;
+        constexpr int PER = (NREG + dfw::THREADS - 1) / dfw::THREADS;
+        float rv[PER][3], av[PER][3];
 #pragma unroll
-    for (int j = 0; j < df::PPT; ++j) {
-        const int p = tid + j * df::THREADS;
-        const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
-        const bool in = gy < H && gx < W;
-        const size_t g = in ? (size_t)gy * W + gx : 0;
-        float m = -INFINITY;
-        for (int i = 0; i < M; ++i) m = fmaxf(m, in ? __ldg(z + (size_t)(M + i) * HW + g) : 0.f);
-        float sum = 0.f;
-        for (int i = 0; i < M; ++i) sum += in ? expf(__ldg(z + (size_t)(M + i) * HW + g) - m) : 1.f;
-        lmax[j] = m;
-        linv[j] = 1.f / sum;
-        acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
+        for (int j = 0; j < PER; ++j) {
+            const int t = tid + j * dfw::THREADS;
+            const int gy = ty0 - dfw::HALO + t / dfw::RW, gx = tx0 - dfw::HALO + t % dfw::RW;
+            const bool in = t < NREG && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const size_t g = in ? (size_t)gy * W + gx : 0;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                rv[j][ch] = in ? __ldg(r + ch * HW + g) : 0.f;
+                av[j][ch] = in ? __ldg(a + ch * HW + g) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int t = tid + j * dfw::THREADS;
+            if (PER * dfw::THREADS > NREG && t >= NREG) continue;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) sY[ch * NREG + t] = rv[j][ch] / (av[j][ch] + eps);
+        }
     }
 
-    for (int i = 0; i < M; ++i) {
-        const int k = args.ks[i];
-        const float* __restrict__ zi = z + (size_t)i * HW;
-        // E_i = exp(I_i - m) and E_i * y on the footprint, then window sums
-        size_sums_k(k, sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        __syncthreads();
+    // Fusion weights alpha_i(p) = softmax_i of the M fusion logits (Eq. 5),
+    // once per own pixel, into shared memory [i][TH][TW].
+    const int x = tid % dfw::TW, rg = tid / dfw::TW;
+    const int gx = tx0 + x;
 #pragma unroll
-        for (int j = 0; j < df::PPT; ++j) {
-            const int p = tid + j * df::THREADS;
-            const int ly = p / df::TW, lx = p % df::TW;
-            const int gy = ty0 + ly, gx = tx0 + lx;
-            if (gy >= H || gx >= W) continue;
-            const float D = sV[ly * df::TW + lx];
-            float R[3];
-            if (D >= df::DMIN) {
-                const float invD = 1.f / D;
+    for (int j = 0; j < dfw::RPT; ++j) {
+        const int ly = rg * dfw::RPT + j, gy = ty0 + ly;
+        if (gy >= H || gx >= W) continue;
+        const size_t g = (size_t)gy * W + gx;
+        float l[dfw::MAXK];
+        float m = -INFINITY;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) R[c] = sV[((1 + c) * df::TH + ly) * df::TW + lx] * invD;
-            } else {
-                window_exact(zi, r, a, H, W, k, eps, gx, gy, R);
-                if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
-            }
-            const float al = expf(__ldg(z + (size_t)(M + i) * HW + (size_t)gy * W + gx) - lmax[j]) * linv[j];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc[j][c] = fmaf(al, R[c], acc[j][c]);
+        for (int i = 0; i < dfw::MAXK; ++i) {
+            l[i] = i < M ? __ldg(z + (size_t)(M + i) * HW + g) : -INFINITY;
+            m = fmaxf(m, l[i]);
         }
-        __syncthreads();
+        float sum = 0.f;
+#pragma unroll
+        for (int i = 0; i < dfw::MAXK; ++i) {
+            l[i] = i < M ? expf(l[i] - m) : 0.f;
+            sum += l[i];
+        }
+        const float inv = 1.f / sum;
+#pragma unroll
+        for (int i = 0; i < dfw::MAXK; ++i)
+            if (i < M) sAl[(i * dfw::TH + ly) * dfw::TW + x] = l[i] * inv;
+    }
+#pragma unroll
+    for (int j = 0; j < dfw::RPT * 3; ++j) sAcc[j * dfw::THREADS + tid] = 0.f;
+    __syncthreads();
+
+    for (int i = 0; i < M; ++i) {
+        const float* __restrict__ zi = z + (size_t)i * HW;
+        const float* __restrict__ al = sAl + i * dfw::TH * dfw::TW;
+#define WSKPN_FWD_SIZE(K_) \
+    case K_: fwd_size<K_>(sE, sH, sY, al, red, zi, r, a, H, W, tx0, ty0, tid, eps, args.fallbacks, sAcc); break;
+        switch (args.ks[i]) {
+            WSKPN_FWD_SIZE(1) WSKPN_FWD_SIZE(3) WSKPN_FWD_SIZE(5) WSKPN_FWD_SIZE(7) WSKPN_FWD_SIZE(9)
+            WSKPN_FWD_SIZE(11)
+            default: fwd_size<13>(sE, sH, sY, al, red, zi, r, a, H, W, tx0, ty0, tid, eps, args.fallbacks, sAcc);
+        }
+#undef WSKPN_FWD_SIZE
     }
 
     // Re-modulation and store.
     float* __restrict__ out = args.out.p[b];
 #pragma unroll
-    for (int j = 0; j < df::PPT; ++j) {
-        const int p = tid + j * df::THREADS;
-        const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
+    for (int j = 0; j < dfw::RPT; ++j) {
+        const int gy = ty0 + rg * dfw::RPT + j;
         if (gy >= H || gx >= W) continue;
         const size_t g = (size_t)gy * W + gx;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) out[c * HW + g] = (a[c * HW + g] + eps) * acc[j][c];
+        for (int ch = 0; ch < 3; ++ch)
+            out[ch * HW + g] = (__ldg(a + ch * HW + g) + eps) * sAcc[(j * 3 + ch) * dfw::THREADS + tid];
     }
 }
 
@@ -295,7 +522,7 @@ wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r
                                     int M, const int* ks, float eps, unsigned int* fallbacks,
                                     cudaStream_t st, std::string& err) {
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)df::SMEM_BYTES),
+                                        (int)dfw::SMEM_BYTES),
                    err);
     for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
         const int nb = B - b0 < WSKPN_MAX_BATCH ? B - b0 : WSKPN_MAX_BATCH;
@@ -312,8 +539,8 @@ wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r
         for (int i = 0; i < M; ++i) args.ks[i] = ks[i];
         args.eps = eps;
         args.fallbacks = fallbacks;
-        dim3 grid(cdiv(W, df::TW), cdiv(H, df::TH), nb);
-        decode_fuse_fwd_kernel<<<grid, df::THREADS, df::SMEM_BYTES, st>>>(args);
+        dim3 grid(cdiv(W, dfw::TW), cdiv(H, dfw::TH), nb);
+        decode_fuse_fwd_kernel<<<grid, dfw::THREADS, dfw::SMEM_BYTES, st>>>(args);
         WSKPN_CUDA_TRY(cudaGetLastError(), err);
     }
     return WSKPN_OK;

@@ -37,7 +37,7 @@ def test_folded_network_denoises_like_the_branch_network():
     blob = []
     for l in range(4):
         ci, co = widths[l], widths[l + 1]
-        br = [g.standard_normal(s).astype(np.float32) * sc for s, sc in
+        br = [(g.standard_normal(s) * sc).astype(np.float32) for s, sc in
               (((co, ci, 5, 5), 0.3 / np.sqrt(25 * ci)), ((co,), 0.05), ((co, ci, 3, 3), 0.3 / np.sqrt(9 * ci)),
                ((co,), 0.05), ((co, ci, 1, 1), 0.3 / np.sqrt(ci)), ((co,), 0.05))]
         W, b = repvgg.fold(*(torch.from_numpy(x).cuda() for x in br))
