@@ -5,8 +5,9 @@
 // GEMM view of one tile: M = 128 consecutive pixels of an image row (TMEM
 // lanes), N = padded output channels, K = KS*KS taps x input channels,
 // consumed 32 bytes (16 BF16 or 32 e4m3 channels) per MMA.  A CTA owns
-// R = 4 output rows x 128 pixels and keeps 4 accumulators (one per output
-// row) in TMEM, double-buffered across tiles so the epilogue of one tile
+// R output rows x 128 pixels (R = 8 for layers with at most 32 output
+// channels, else 4) and keeps R accumulators (one per output row) in TMEM,
+// double-buffered across tiles so the epilogue of one tile
 // overlaps the MMAs of the next.  Each input row is fetched once per tile
 // (one TMA box of 128 + KS - 1 pixels per 32-byte channel chunk) and
 // serves every tap that reads it: the KS horizontal taps through operand
@@ -45,7 +46,10 @@ namespace wskpn {
 
 namespace tc {
 constexpr int BM = 128;            // pixels per tile row = MMA M = TMEM lanes
-constexpr int R = 4;               // output rows per tile
+// Output rows per tile: 8 when two buffers of 8 row accumulators fit in
+// TMEM (COUT_P <= 32), else 4.  More rows per tile means fewer MMAs per
+// output row, since an input row's MMA serves up to min(R, KS) output rows.
+__host__ __device__ constexpr int rows_per_tile(int cout_p) { return cout_p <= 32 ? 8 : 4; }
 constexpr int THREADS = 192;
 constexpr int ROWB = 32;           // bytes of one pixel row of one K chunk
 constexpr uint32_t SMEM_MAX = 232448;
@@ -101,18 +105,13 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 // Bounded wait: false when the limit expired or another role aborted.
-// SLEEP_NS > 0 parks the thread between polls, so a waiting warp does not
-// take issue slots from the MMA-issuing warp on the same sub-partition.
-template <int SLEEP_NS>
 __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int* abort_flag) {
     if (mbar_try_wait(a, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
 #pragma unroll 1
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 8; ++i)
             if (mbar_try_wait(a, parity)) return true;
-            if (SLEEP_NS > 0) __nanosleep(SLEEP_NS);
-        }
         if (*abort_flag) return false;
         if (gtimer() - t0 > tc::WAIT_NS) return false;
     }
@@ -207,10 +206,10 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
         : "memory");
 }
 
-template <int COUT_P>
+template <int COUT_P, int R>
 __host__ __device__ constexpr uint32_t tmem_cols() {
-    return 2 * tc::R * COUT_P <= 32 ? 32 : 2 * tc::R * COUT_P <= 64 ? 64 : 2 * tc::R * COUT_P <= 128 ? 128
-           : 2 * tc::R * COUT_P <= 256 ? 256 : 512;
+    return 2 * R * COUT_P <= 32 ? 32 : 2 * R * COUT_P <= 64 ? 64 : 2 * R * COUT_P <= 128 ? 128
+           : 2 * R * COUT_P <= 256 ? 256 : 512;
 }
 
 // All MMAs of input row RI of a tile.  Input row RI feeds output rows
@@ -222,13 +221,13 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
 // R - 1 - ro), so N = (DY1 - DY0 + 1) x COUT_P columns are contiguous.
 // Accumulators are zeroed by the epilogue, so every MMA accumulates.
 // Fully unrolled, no branches.
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int RI>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int RI>
 __device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
-    constexpr int DY0 = RI - (tc::R - 1) > 0 ? RI - (tc::R - 1) : 0;
+    constexpr int DY0 = RI - (R - 1) > 0 ? RI - (R - 1) : 0;
     constexpr int DY1 = RI < KS - 1 ? RI : KS - 1;
     constexpr int NB = DY1 - DY0 + 1;  // output rows fed by this input row
     if constexpr (NB <= 0) {
-        return;  // row beyond R + KS - 1 (only instantiated for KS = 3)
+        return;  // row beyond R + KS - 1 (instantiated by the switch below, never reached)
     } else {
     constexpr int N = NB * COUT_P;
     static_assert(N % 16 == 0 && N <= 256, "MMA N");
@@ -237,7 +236,7 @@ __device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t 
     constexpr uint32_t b_blk = (COUT_P * tc::ROWB) >> 4;  // one (dx, chunk, dy) block, 16-byte units
     constexpr int CPB = chunks_per_box(NCC_IN);
     constexpr uint32_t a_dx = (CPB * tc::ROWB) >> 4;       // one pixel row of a box
-    const uint32_t d = dbase + (uint32_t)((tc::R - 1 - (RI - DY0)) * COUT_P);
+    const uint32_t d = dbase + (uint32_t)((R - 1 - (RI - DY0)) * COUT_P);
 #pragma unroll
     for (int cc = 0; cc < NCC_IN; ++cc) {
         const int ccw = cc % NCC_W;  // the lo half of a split activation reuses the weights
@@ -251,34 +250,32 @@ __device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t 
     }
 }
 
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R>
 __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
-    static_assert(tc::R + KS - 1 <= 8, "rows per tile");
+    static_assert(R + KS - 1 <= 12, "rows per tile");
+#define WSKPN_ROW(i_) \
+    case i_: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, R, i_>(dbase, ad, bd, box_step); break;
     switch (ri) {
-        case 0: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 0>(dbase, ad, bd, box_step); break;
-        case 1: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 1>(dbase, ad, bd, box_step); break;
-        case 2: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 2>(dbase, ad, bd, box_step); break;
-        case 3: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 3>(dbase, ad, bd, box_step); break;
-        case 4: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 4>(dbase, ad, bd, box_step); break;
-        case 5: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 5>(dbase, ad, bd, box_step); break;
-        case 6: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 6>(dbase, ad, bd, box_step); break;
-        default: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, 7>(dbase, ad, bd, box_step); break;
+        WSKPN_ROW(0) WSKPN_ROW(1) WSKPN_ROW(2) WSKPN_ROW(3) WSKPN_ROW(4) WSKPN_ROW(5)
+        WSKPN_ROW(6) WSKPN_ROW(7) WSKPN_ROW(8) WSKPN_ROW(9) WSKPN_ROW(10)
+        default: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, R, 11>(dbase, ad, bd, box_step); break;
     }
+#undef WSKPN_ROW
 }
 
 // ----------------------------------------------------------------- kernel
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr int PAD = KS / 2;
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
-    constexpr uint32_t NCOL = tmem_cols<COUT_P>();
-    constexpr int ROWS_IN = tc::R + KS - 1;
+    constexpr uint32_t NCOL = tmem_cols<COUT_P, R>();
+    constexpr int ROWS_IN = R + KS - 1;
     constexpr int CPB = chunks_per_box(NCC_IN);
     constexpr int NBOX = NCC_IN / CPB;
     constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB * CPB;
     static_assert(COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256, "MMA N");
-    static_assert(2 * tc::R * COUT_P <= 512, "TMEM columns");
+    static_assert(2 * R * COUT_P <= 512, "TMEM columns");
 
     extern __shared__ __align__(1024) uint8_t dsmem[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
@@ -330,7 +327,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         // accumulators start at zero: every MMA accumulates
         const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll 1
-        for (int c = 0; c < 2 * tc::R * COUT_P; c += 16) tmem_zero16(tmem + lb + (uint32_t)c);
+        for (int c = 0; c < 2 * R * COUT_P; c += 16) tmem_zero16(tmem + lb + (uint32_t)c);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
     }
@@ -350,10 +347,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
                 const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
-                const int x0 = tx * tc::BM, y0 = ty * tc::R;
+                const int x0 = tx * tc::BM, y0 = ty * R;
                 for (int ri = 0; ri < ROWS_IN; ++ri, ++it) {
                     const int s = it % S;
-                    if (!mbar_wait<64>(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -373,13 +370,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const uint32_t n_in_flight = it < (uint32_t)S ? it : (uint32_t)S;
             for (uint32_t k = 0; k < n_in_flight; ++k) {
                 const uint32_t j = it - 1 - k;
-                mbar_wait<64>(smem_u32(&full[j % S]), (j / S) & 1u, abort_flag);
+                mbar_wait(smem_u32(&full[j % S]), (j / S) & 1u, abort_flag);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            bool ok = mbar_wait<0>(smem_u32(wbar), 0, abort_flag);
+            bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag);
             // Descriptors are linear in the start address (16-byte units in
             // the low bits): stages, chunks and taps are offsets from two bases.
             const uint64_t wdesc0 = sdesc_sw32(smem_u32(sW));
@@ -390,20 +387,20 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             int lt = 0;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
                 const int buf = lt & 1;
-                if (!mbar_wait<0>(smem_u32(&acce[buf]), ((lt >> 1) & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait(smem_u32(&acce[buf]), ((lt >> 1) & 1) ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dbase = tmem + (uint32_t)(buf * tc::R * COUT_P);
+                const uint32_t dbase = tmem + (uint32_t)(buf * R * COUT_P);
                 for (int ri = 0; ri < ROWS_IN; ++ri, ++it) {
                     const int s = it % S;
-                    if (!mbar_wait<0>(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8>(ri, dbase, adesc0 + (uint64_t)(s * a_stage), wdesc0,
+                    issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8, R>(ri, dbase, adesc0 + (uint64_t)(s * a_stage), wdesc0,
                                                                box_step);
                     mma_commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
                 }
@@ -415,7 +412,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             }
             // Every issued MMA must complete before TMEM is released.
             mma_commit(smem_u32(fin));
-            mbar_wait<0>(smem_u32(fin), 0, abort_flag);
+            mbar_wait(smem_u32(fin), 0, abort_flag);
         }
     } else {
         // ------------------------------------------------ epilogue warps 2..5
@@ -426,7 +423,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
             const int buf = lt & 1;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait<256>(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag);
+            if (lane == 0) ok = mbar_wait(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 if (lane == 0) {
@@ -439,10 +436,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
             const int x = tx * tc::BM + p;
 #pragma unroll 1
-            for (int r = 0; r < tc::R; ++r) {
-                const int y = ty * tc::R + r;
+            for (int r = 0; r < R; ++r) {
+                const int y = ty * R + r;
                 const bool valid = x < a.W && y < a.H;
-                const uint32_t col = (uint32_t)(buf * tc::R * COUT_P + (tc::R - 1 - r) * COUT_P);
+                const uint32_t col = (uint32_t)(buf * R * COUT_P + (R - 1 - r) * COUT_P);
 #pragma unroll
                 for (int c16 = 0; c16 < COUT_P / 16; ++c16) {
                     float v[16];
@@ -645,7 +642,7 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
 template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
-    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8>;
+    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, tc::rows_per_tile(COUT_P)>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     kern<<<grid, tc::THREADS, smem, st>>>(map, a);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
@@ -709,7 +706,7 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     size_t smem = fixed + (size_t)a.stages * a.stage_bytes;
     if (smem < 120 * 1024) smem = 120 * 1024;
     a.tiles_x = cdiv(W, tc::BM);
-    a.tiles_y = cdiv(H, tc::R);
+    a.tiles_y = cdiv(H, tc::rows_per_tile(L.cout_p));
     a.ntiles = a.tiles_x * a.tiles_y * B;
     a.status = ctx->d_status;
     int nsm = 148;
