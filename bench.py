@@ -39,9 +39,19 @@ KSIZES = (3, 5, 7, 9, 11, 13)
 # + radiance (3 x 4) + albedo (3 x 4) read, output (3 x 4) written
 DECODE_BYTES_PER_PX = 84
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 148, 2032.0
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures
-# of the current kernels (None until captured for this kernel version)
-TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the current kernels at 1920x1080 (profiles/conv_tc_bf16_1080p.md and
+# profiles/decode_fuse_fwd_1080p.md); a kernel absent here has no capture of
+# its current version
+TRAFFIC = {
+    ("bf16", "conv1 (10->32)"): 344.2e6,
+    ("bf16", "conv2 (32->48)"): 609.9e6,
+    ("bf16", "conv3 (48->64)"): 876.1e6,
+    ("bf16", "conv4 (64->12)"): 616.5e6,
+    ("bf16", "decode_fuse_fwd"): 165.7e6,
+    ("fp32", "decode_fuse_fwd"): 165.7e6,
+    ("fp8", "decode_fuse_fwd"): 165.7e6,
+}
 
 
 def parse():
@@ -55,6 +65,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="skip the 720p / 1440p runs")
     p.add_argument("--serve-requests", type=int, default=4096)
     p.add_argument("--serve-rate", type=float, default=240.0)
     p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
@@ -76,6 +87,34 @@ def peaks():
 
 def conv_flops(l, h=H, w=W):
     return 2.0 * WIDTHS[l] * WIDTHS[l + 1] * KS * KS * h * w
+
+
+def stage_rooflines(stage_ms, precision, pk, h=H, w=W):
+    """Achieved throughput and fraction of the measured peak for every stage
+    (algorithmic FLOPs for the convolutions, algorithmic bytes for the
+    streaming kernels), from the stage times of one denoise."""
+    L = len(WIDTHS) - 1
+    out = {}
+    prep_bytes = (40 + {"fp32": 40, "bf16": 64, "fp8": 32}[precision]) * h * w
+    for i, ms in enumerate(stage_ms):
+        if ms <= 0:
+            continue
+        if i == 0 or i == L + 1:
+            byts = prep_bytes if i == 0 else DECODE_BYTES_PER_PX * h * w
+            gbs = byts / (ms * 1e-3) / 1e9
+            out["prep" if i == 0 else "reconstruct"] = {
+                "bound": "hbm", "achieved": gbs, "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                "traffic": TRAFFIC.get((precision, "decode_fuse_fwd")) if i == L + 1 and (h, w) == (H, W) else None}
+        else:
+            tf = conv_flops(i - 1, h, w) / (ms * 1e-3) / 1e12
+            if precision == "fp32":
+                peak, bound = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12, "alu"
+            else:
+                peak, bound = pk["bf16_tflops"] * (2.0 if precision == "fp8" else 1.0), "tensor"
+            kname = f"conv{i} ({WIDTHS[i - 1]}->{WIDTHS[i]})"
+            out[f"conv{i}"] = {"bound": bound, "achieved": tf, "unit": "TFLOP/s", "frac": tf / peak,
+                               "traffic": TRAFFIC.get((precision, kname)) if (h, w) == (H, W) else None}
+    return out
 
 
 # ------------------------------------------------------------------ clocks
@@ -274,16 +313,18 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     pk = peaks()
 
-    def time_path(precision, steps, warmup):
-        d = wk.Denoiser(wb, precision=precision, max_hw=(H, W))
+    def time_path(precision, steps, warmup, hw=(H, W), frame=None):
+        h, w = hw
+        xs = xin if frame is None else frame
+        d = wk.Denoiser(wb, precision=precision, max_hw=(h, w))
         if args.tc_split is not None and precision == "bf16":
             d.set_tuning(2, args.tc_split)
         if precision == "fp8":  # static activation scales from a different frame (seed 3)
-            cal = synth.make_frame(H, W, SEED + 1)
+            cal = synth.make_frame(h, w, SEED + 1)
             d.calibrate(*[torch.from_numpy(np.ascontiguousarray(cal[k][None])).to(dev) for k in keys])
-        out = torch.empty((1, 3, H, W), device=dev)
+        out = torch.empty((1, 3, h, w), device=dev)
         for _ in range(warmup):
-            d.denoise(*xin, out=out)
+            d.denoise(*xs, out=out)
         torch.cuda.synchronize()
         barrier()
         d.profile(True)
@@ -292,7 +333,7 @@ def main():
         for i in range(steps):
             flush.fill_(float(i))
             ev[i][0].record()
-            d.denoise(*xin, out=out)
+            d.denoise(*xs, out=out)
             ev[i][1].record()
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -321,6 +362,18 @@ def main():
     if not args.no_fp32 and args.precision != "fp32":
         fp32 = time_path("fp32", max(3, args.steps // 4), 3)
 
+    # the same path at 720p and 1440p (seeds 1 and 3), for ms/frame, frames/s
+    # and the per-stage roofline fractions at each resolution
+    sweep = {}
+    if not args.no_sweep:
+        for (h, w), sd in (((720, 1280), 1), ((1440, 2560), 3)):
+            fr = synth.make_frame(h, w, sd + 1000 * rank)
+            xs = [torch.from_numpy(np.ascontiguousarray(fr[k][None])).to(dev) for k in keys]
+            r = time_path(args.precision, max(5, args.steps // 2), 3, (h, w), xs)
+            sweep[f"{w}x{h}"] = {"ms_per_frame": r["ms_step"], "fps": 1e3 / r["ms_step"],
+                                 "stage_rooflines": stage_rooflines(r["stage_ms"], args.precision, pk, h, w)}
+            del r
+
     # roofline of the dominant stage (stage 0 prep, 1..L convs, L+1 reconstruction)
     st = main_res["stage_ms"]
     dom = max(range(len(st)), key=lambda i: st[i])
@@ -339,7 +392,7 @@ def main():
                 "traffic": TRAFFIC.get((args.precision, kname)), "kernel": kname, "peak_source": psrc}
     else:
         name = "prep" if dom == 0 else "decode_fuse_fwd"
-        byts = (40 + {"fp32": 40, "bf16": 32, "fp8": 32}[args.precision]) * H * W if dom == 0 \
+        byts = (40 + {"fp32": 40, "bf16": 64, "fp8": 32}[args.precision]) * H * W if dom == 0 \
             else DECODE_BYTES_PER_PX * H * W
         achieved = byts / (st[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -389,9 +442,14 @@ def main():
             "reconstruction_ms": main_res["stage_ms"][L + 1],
             "p50_step_ms": statistics.median(main_res["per"]),
             "roofline": roof,
+            "stage_rooflines": stage_rooflines(main_res["stage_ms"], args.precision, pk),
             "gpu_launches": args.steps * (L + 2),
             "clocks": clocks,
         }
+        if sweep:
+            sweep["1920x1080"] = {"ms_per_frame": main_res["ms_step"], "fps": 1e3 / main_res["ms_step"],
+                                  "stage_rooflines": line["stage_rooflines"]}
+            line["resolutions"] = sweep
         if fp32 is not None:
             line["fp32_ms_per_frame"] = fp32["ms_step"] / world
             line["speedup_vs_fp32"] = fp32["ms_step"] / main_res["ms_step"]
