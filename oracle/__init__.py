@@ -19,6 +19,8 @@ What it computes (paper sections / equations):
   * ``reconstruct_bwd`` / ``conv2d_bwd`` / ``train_grads``: the chain rule of
                         the above for one training step (Eq. 1), with the L1
                         loss or SMAPE (Eq. 6).
+  * ``temporal.accumulate`` Sec. 4.3 temporal accumulation before denoising
+                        (reprojection, geometry consistency, blend); numpy.
 
 Parity status of each function is stated in the tests that pin it; the whole
 denoiser's agreement with the paper's *trained* network is unpinned (no

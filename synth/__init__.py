@@ -32,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "Frame", "make_frame", "make_batch", "make_target", "make_weights",
-    "weight_shapes", "n_weights", "DEPTH_NEAR", "DEPTH_FAR",
+    "weight_shapes", "n_weights", "make_sequence", "DEPTH_NEAR", "DEPTH_FAR",
 ]
 
 DEPTH_NEAR = 1.0
@@ -55,7 +55,7 @@ def _rng(seed: int, stream: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64([int(seed), int(stream)]))
 
 
-def _geometry(H: int, W: int, seed: int):
+def _geometry(H: int, W: int, seed: int, origin=(0.0, 1.0, 0.0), with_position: bool = False):
     g = _rng(seed, 1)
     n_sph = 6
     cx = g.uniform(-3.0, 3.0, n_sph)
@@ -70,7 +70,7 @@ def _geometry(H: int, W: int, seed: int):
     dx, dy = np.meshgrid(xs, ys)                      # [H, W]
     d = np.stack([dx, dy, np.ones_like(dx)], axis=0)  # [3, H, W]
     d /= np.linalg.norm(d, axis=0, keepdims=True)
-    o = np.array([0.0, 1.0, 0.0])
+    o = np.asarray(origin, dtype=np.float64)
 
     t_best = np.full((H, W), np.inf)
     nrm = np.zeros((3, H, W))
@@ -102,6 +102,9 @@ def _geometry(H: int, W: int, seed: int):
     zcam = np.where(np.isfinite(t_best), t_best * d[2], DEPTH_FAR)
     depth = np.clip(zcam, DEPTH_NEAR, DEPTH_FAR)[None]
     nrm /= np.maximum(np.linalg.norm(nrm, axis=0, keepdims=True), 1e-12)
+    if with_position:
+        pos = o[:, None, None] + d * np.where(np.isfinite(t_best), t_best, 0.0)[None]
+        return nrm, depth, pos
     return nrm, depth
 
 
@@ -184,3 +187,54 @@ def make_weights(widths=(10, 32, 48, 64, 12), ks: int = 5, seed: int = 0) -> np.
         parts.append(g.standard_normal(ws).ravel() * np.sqrt(2.0 / fan_in))
         parts.append(g.uniform(-1.0, 1.0, bs) / np.sqrt(fan_in))
     return np.concatenate(parts).astype(np.float32)
+
+
+def _project(pos: np.ndarray, origin, H: int, W: int) -> np.ndarray:
+    """Continuous pixel coordinates (x, y) of world points [3, H, W] in the
+    camera at `origin` (same orientation and field of view as make_frame;
+    pixel centres at integer coordinates)."""
+    th = np.tan(np.deg2rad(60.0) / 2)
+    d = pos - np.asarray(origin, dtype=np.float64)[:, None, None]
+    z = np.maximum(d[2], 1e-9)
+    xn = d[0] / (z * th * (W / H))
+    yn = d[1] / (z * th)
+    return np.stack([(xn + 1.0) * 0.5 * W - 0.5, (1.0 - yn) * 0.5 * H - 0.5])
+
+
+def make_sequence(H: int, W: int, T: int, seed: int, velocity=(0.04, 0.0, 0.03)) -> list:
+    """T consecutive 1-spp frames of one static scene seen from a camera that
+    moves by `velocity` (world units) per frame.  Besides the make_frame
+    buffers every frame has the world position of the first hit
+    position[3,H,W] and the motion vector motion[2,H,W] = (x, y) offset from
+    the pixel to where the same surface point projects in the previous
+    frame's camera (0 for the first frame).  Albedo is attached to the
+    surfaces (uniform [0,1]^3 per cell of a 0.5-unit world grid, hashed into
+    a seeded table), so the noise-free radiance of a point is the same in
+    every frame; radiance noise is drawn per frame as in make_frame."""
+    table = _rng(seed, 6).uniform(0.0, 1.0, (4096, 3))
+    frames = []
+    for t in range(T):
+        origin = (velocity[0] * t, 1.0 + velocity[1] * t, velocity[2] * t)
+        nrm, depth, pos = _geometry(H, W, seed, origin, with_position=True)
+        cell = np.floor(pos / 0.5).astype(np.int64)
+        h = (cell[0] * 73856093) ^ (cell[1] * 19349663) ^ (cell[2] * 83492791)
+        alb = np.transpose(table[np.mod(h, 4096)], (2, 0, 1))
+        shade = 0.1 + sum(np.maximum(np.einsum("chw,c->hw", nrm, l), 0.0) for l in _LIGHTS)
+        clean = alb * shade[None]
+        g = _rng(seed * 1000 + t, 7)
+        noise = np.exp(g.standard_normal((3, H, W)))
+        fire = g.uniform(0.0, 1.0, (H, W)) < 0.02
+        rad = clean * noise * np.where(fire, 50.0, 1.0)[None]
+        if t == 0:
+            motion = np.zeros((2, H, W))
+        else:
+            prev = (velocity[0] * (t - 1), 1.0 + velocity[1] * (t - 1), velocity[2] * (t - 1))
+            q = _project(pos, prev, H, W)
+            px = np.arange(W, dtype=np.float64)[None, :]
+            py = np.arange(H, dtype=np.float64)[:, None]
+            motion = np.stack([q[0] - px, q[1] - py])
+        frames.append(Frame(
+            radiance=rad.astype(np.float32), albedo=alb.astype(np.float32), normal=nrm.astype(np.float32),
+            depth=depth.astype(np.float32), clean=clean.astype(np.float32), position=pos.astype(np.float32),
+            motion=motion.astype(np.float32)))
+    return frames
