@@ -250,6 +250,51 @@ wskpn_status wskpn_repvgg_fold(const float* w5, const float* b5, const float* w3
 wskpn_status wskpn_repvgg_fold_grad(const float* gW, int cin, int cout, float* g5, float* g3, float* g1,
                                     void* stream);
 
+/* ---- Temporal accumulation before denoising (Sec. 4.3) -------------- */
+
+/* Per pixel p, the previous frame's accumulated radiance is reprojected to
+ * q = p + motion(p) (bilinear over the 4 pixels around q, pixel centres at
+ * integer coordinates); a tap is kept when it lies in the image, has
+ * history, |P_prev - P|^2 < tau_pos^2 and n_prev . n > tau_normal.  With
+ * kept weight W > min_weight: A_prev and the history length are the
+ * renormalised kept averages, h = h_prev + 1, alpha = max(1/h, alpha_min),
+ * A = A_prev + alpha (c - A_prev); otherwise A = c, h = 1.  The paper gives
+ * the steps, not the constants; the defaults are readings. */
+typedef struct wskpn_temporal wskpn_temporal;
+
+typedef struct {
+    float alpha_min;   /* blend floor; 1/alpha_min frames of running mean (0.2) */
+    float tau_pos;     /* world-position distance threshold (0.1) */
+    float tau_normal;  /* minimum dot product of the shading normals (0.9) */
+    float min_weight;  /* minimum kept bilinear weight (1e-3) */
+} wskpn_temporal_config;
+
+void wskpn_temporal_config_default(wskpn_temporal_config* cfg);
+
+/* History of one stream of h x w frames, owned by the library (two device
+ * copies of 10 float planes: accumulated radiance, world position, normal,
+ * history length), starting empty.  cfg may be NULL (defaults).
+ * Errors: EINVAL (size, config), ENOMEM, ECUDA. */
+wskpn_status wskpn_temporal_create(const wskpn_temporal_config* cfg, int h, int w, wskpn_temporal** out);
+
+/* One frame: device float32 planar radiance [3][h][w], world position
+ * [3][h][w], shading normal [3][h][w] and motion [2][h][w] ((x, y) offset
+ * from each pixel to its position in the previous frame); writes the
+ * accumulated radiance [3][h][w] (caller-owned, may not alias the inputs)
+ * and advances the history.  Calls on one object must be ordered on the
+ * GPU (same stream, or synchronised).  Errors: EINVAL, ECUDA. */
+wskpn_status wskpn_temporal_step(wskpn_temporal* t, const float* radiance, const float* position,
+                                 const float* normal, const float* motion, float* accumulated, void* stream);
+
+/* Copies the current history length plane [h][w] (0 = none) to `history`
+ * (device).  Errors: EINVAL, ECUDA. */
+wskpn_status wskpn_temporal_history(const wskpn_temporal* t, float* history, void* stream);
+
+/* Forgets the history (the next step restarts every pixel).  Errors: EINVAL, ECUDA. */
+wskpn_status wskpn_temporal_reset(wskpn_temporal* t, void* stream);
+
+void wskpn_temporal_destroy(wskpn_temporal* t);
+
 /* ---- Serving: continuous batching of frame-denoise requests --------- */
 
 typedef struct wskpn_server wskpn_server;
@@ -267,6 +312,9 @@ typedef struct {
                              (worker, h, w, batch) (default 1) */
     int batch_window_us;  /* how long the oldest request may wait for
                              companions of its size (default 200) */
+    wskpn_temporal_config temporal;  /* constants of the per-stream temporal
+                             accumulation (wskpn_serve_submit_temporal);
+                             default wskpn_temporal_config_default */
 } wskpn_serve_config;
 
 typedef struct {
@@ -276,6 +324,9 @@ typedef struct {
     double fps;                              /* completed / (last delivery - first submit) */
     double mean_batch;
     size_t mem_in_use, mem_peak;             /* admitted footprint, bytes */
+    uint64_t temporal_frames;                /* frames accumulated with their stream's history */
+    uint64_t temporal_streams;               /* streams holding a temporal history */
+    size_t temporal_bytes;                   /* device bytes of those histories */
 } wskpn_serve_stats;
 
 /* Fills the defaults above. */
@@ -300,6 +351,19 @@ wskpn_status wskpn_serve_start(const wskpn_config* cfg, const float* host_weight
  * footprint alone exceeds the budget). */
 wskpn_status wskpn_serve_submit(wskpn_server* srv, int stream_id, const wskpn_frame* frame, int h, int w,
                                 float* out, uint64_t* ticket);
+
+/* As wskpn_serve_submit, with temporal accumulation (Sec. 4.3) before the
+ * denoise: the frame's radiance is blended with the reprojected history of
+ * stream `stream_id` (kept by the server on the device, created on the
+ * stream's first temporal frame and restarted when its size changes or
+ * reset_history is set).  position [3][h][w] is the world position of each
+ * pixel, motion [2][h][w] its (x, y) offset to the previous frame; the
+ * constants are scfg->temporal.  Frames of one temporal stream run one at a
+ * time in submission order; frames of different streams batch together.
+ * Errors: as wskpn_serve_submit. */
+wskpn_status wskpn_serve_submit_temporal(wskpn_server* srv, int stream_id, const wskpn_frame* frame,
+                                         const float* position, const float* motion, int reset_history, int h,
+                                         int w, float* out, uint64_t* ticket);
 
 /* Waits up to timeout_ms (0 = poll, < 0 = no limit) for a ticket.  Returns
  * OK when delivered, ETIMEOUT when the limit ran out, EINVAL for an unknown

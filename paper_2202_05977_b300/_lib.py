@@ -40,9 +40,15 @@ class Frame(ctypes.Structure):
                 ("normal", ctypes.c_void_p), ("depth", ctypes.c_void_p)]
 
 
+class TemporalConfig(ctypes.Structure):
+    _fields_ = [("alpha_min", ctypes.c_float), ("tau_pos", ctypes.c_float), ("tau_normal", ctypes.c_float),
+                ("min_weight", ctypes.c_float)]
+
+
 class ServeConfig(ctypes.Structure):
     _fields_ = [("n_workers", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_queue", ctypes.c_int),
-                ("mem_budget", ctypes.c_size_t), ("use_graphs", ctypes.c_int), ("batch_window_us", ctypes.c_int)]
+                ("mem_budget", ctypes.c_size_t), ("use_graphs", ctypes.c_int), ("batch_window_us", ctypes.c_int),
+                ("temporal", TemporalConfig)]
 
 
 class ServeStats(ctypes.Structure):
@@ -50,7 +56,9 @@ class ServeStats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
                 ("graph_captures", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("fps", ctypes.c_double),
-                ("mean_batch", ctypes.c_double), ("mem_in_use", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t)]
+                ("mean_batch", ctypes.c_double), ("mem_in_use", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t),
+                ("temporal_frames", ctypes.c_uint64), ("temporal_streams", ctypes.c_uint64),
+                ("temporal_bytes", ctypes.c_size_t)]
 
 
 _P = ctypes.c_void_p
@@ -83,9 +91,16 @@ SIGNATURES = {
     "wskpn_adam_step": ([_P, _P, _F, _F, _F, _F, _I, _P], _I),
     "wskpn_repvgg_fold": ([_P, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P], _I),
     "wskpn_repvgg_fold_grad": ([_P, _I, _I, _P, _P, _P, _P], _I),
+    "wskpn_temporal_config_default": ([_P], None),
+    "wskpn_temporal_create": ([_P, _I, _I, _P], _I),
+    "wskpn_temporal_step": ([_P, _P, _P, _P, _P, _P, _P], _I),
+    "wskpn_temporal_history": ([_P, _P, _P], _I),
+    "wskpn_temporal_reset": ([_P, _P], _I),
+    "wskpn_temporal_destroy": ([_P], None),
     "wskpn_serve_config_default": ([ctypes.POINTER(ServeConfig)], _I),
     "wskpn_serve_start": ([ctypes.POINTER(Config), _P, _SZ, ctypes.POINTER(ServeConfig), ctypes.POINTER(_P)], _I),
     "wskpn_serve_submit": ([_P, _I, _FR, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
+    "wskpn_serve_submit_temporal": ([_P, _I, _FR, _P, _P, _I, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wskpn_serve_wait": ([_P, ctypes.c_uint64, _I], _I),
     "wskpn_serve_pause": ([_P, _I], _I),
     "wskpn_serve_stats_get": ([_P, ctypes.POINTER(ServeStats)], _I),

@@ -77,3 +77,23 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st);
 wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                        cudaStream_t st);
 }  // namespace wskpn
+
+// Temporal accumulation history of one stream (temporal.cu): planes
+// [A0 A1 A2 | P0 P1 P2 | n0 n1 n2 | h] of H x W floats, two copies; state[cur]
+// holds the latest frame's state.
+struct wskpn_temporal {
+    wskpn_temporal_config cfg;
+    int h = 0, w = 0;
+    float* state[2] = {nullptr, nullptr};
+    int cur = 0;
+};
+
+namespace wskpn {
+constexpr int TEMPORAL_PLANES = 10;
+bool temporal_config_valid(const wskpn_temporal_config& c);
+// Batched step: frame j reads prev[j] (10 planes) and writes next[j] and out[j] (3 planes).
+wskpn_status launch_temporal(const wskpn_temporal_config& cfg, const float* const* c, const float* const* P,
+                             const float* const* n, const float* const* m, const float* const* prev,
+                             float* const* next, float* const* out, int B, int H, int W, cudaStream_t st,
+                             std::string& err);
+}  // namespace wskpn

@@ -20,6 +20,7 @@
 #include <thread>
 #include <tuple>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "ctx.h"
@@ -34,6 +35,9 @@ struct Request {
     wskpn_frame frame{};
     int h = 0, w = 0;
     float* out = nullptr;
+    const float* position = nullptr;  // temporal requests: world position [3][h][w]
+    const float* motion = nullptr;    // and motion [2][h][w]
+    int temporal = 0, reset = 0;
     size_t footprint = 0;
     Clock::time_point t_submit, t_done;
     int state = 0;  // 0 queued, 1 running, 2 complete, 3 delivered
@@ -51,6 +55,13 @@ struct Worker {
     bool busy = false;
 };
 
+// Temporal history of one client stream; `running` while one of its frames
+// is on the GPU (the next frame reads the state that frame writes).
+struct TStream {
+    wskpn_temporal* t = nullptr;
+    bool running = false;
+};
+
 }  // namespace wskpn
 
 struct wskpn_server {
@@ -65,13 +76,14 @@ struct wskpn_server {
     std::deque<wskpn::Request*> queue;
     std::unordered_map<uint64_t, wskpn::Request*> reqs;
     std::unordered_map<int, std::deque<wskpn::Request*>> pending;  // per stream, submission order
+    std::unordered_map<int, wskpn::TStream> tstreams;              // temporal histories per stream
     uint64_t next_ticket = 1;
     size_t mem_in_use = 0, mem_peak = 0;
     bool paused = false, stopping = false;
     std::thread sched;
     // statistics
     uint64_t submitted = 0, completed = 0, rejected = 0, failed = 0, batches = 0, graph_launches = 0,
-             graph_captures = 0, batched_frames = 0;
+             graph_captures = 0, batched_frames = 0, temporal_frames = 0;
     std::vector<double> lat_ms;
     bool any_submit = false;
     wskpn::Clock::time_point t_first, t_last;
@@ -107,12 +119,53 @@ static wskpn_status dispatch(wskpn_server* s, Worker& wk) {
         const int ch[4] = {3, 3, 3, 1};
         size_t off = 0;
         for (int k = 0; k < 4; ++k) {
-            WSKPN_CUDA_TRY(cudaMemcpyAsync(base + off, src[k], ch[k] * px * sizeof(float), cudaMemcpyDeviceToDevice,
-                                           wk.stream),
-                           s->err);
+            if (k > 0 || !r->temporal)  // a temporal frame's radiance slot is written by the accumulation
+                WSKPN_CUDA_TRY(cudaMemcpyAsync(base + off, src[k], ch[k] * px * sizeof(float),
+                                               cudaMemcpyDeviceToDevice, wk.stream),
+                               s->err);
             off += ch[k] * px;
         }
         slots[j] = {base, base + 3 * px, base + 6 * px, base + 9 * px};
+    }
+    // temporal accumulation of the batch's temporal frames, written straight
+    // into their radiance slots (the stream's previous frame has completed)
+    {
+        std::vector<const float*> tc, tP, tn, tm, tprev;
+        std::vector<float*> tnext, tout;
+        for (int j = 0; j < B; ++j) {
+            Request* r = wk.batch[j];
+            if (!r->temporal) continue;
+            TStream& ts = s->tstreams[r->stream_id];
+            if (ts.t && (ts.t->h != h || ts.t->w != w)) {
+                wskpn_temporal_destroy(ts.t);
+                ts.t = nullptr;
+            }
+            if (!ts.t) {
+                if (wskpn_temporal_create(&s->scfg.temporal, h, w, &ts.t) != WSKPN_OK) {
+                    s->err = "temporal history allocation failed";
+                    return WSKPN_ENOMEM;
+                }
+            } else if (r->reset) {
+                WSKPN_CUDA_TRY(cudaMemsetAsync(ts.t->state[ts.t->cur], 0, TEMPORAL_PLANES * px * sizeof(float),
+                                               wk.stream),
+                               s->err);
+            }
+            tc.push_back(r->frame.radiance);
+            tP.push_back(r->position);
+            tn.push_back(r->frame.normal);
+            tm.push_back(r->motion);
+            tprev.push_back(ts.t->state[ts.t->cur]);
+            tnext.push_back(ts.t->state[ts.t->cur ^ 1]);
+            tout.push_back(const_cast<float*>(slots[j].radiance));
+            ts.t->cur ^= 1;
+        }
+        if (!tc.empty()) {
+            const wskpn_status ts = launch_temporal(s->scfg.temporal, tc.data(), tP.data(), tn.data(), tm.data(),
+                                                    tprev.data(), tnext.data(), tout.data(), (int)tc.size(), h, w,
+                                                    wk.stream, s->err);
+            if (ts) return ts;
+            s->temporal_frames += tc.size();
+        }
     }
     wskpn_status st = WSKPN_OK;
     if (s->scfg.use_graphs) {
@@ -193,6 +246,7 @@ static void scheduler(wskpn_server* s) {
                 r->t_done = now;
                 if (q != cudaSuccess) r->status = WSKPN_ECUDA;
                 s->mem_in_use -= r->footprint;
+                if (r->temporal) s->tstreams[r->stream_id].running = false;
             }
             wk.batch.clear();
             wk.busy = false;
@@ -203,7 +257,21 @@ static void scheduler(wskpn_server* s) {
         if (!s->paused) {
             for (auto& wk : s->workers) {
                 if (wk.busy || s->queue.empty()) continue;
-                Request* head = s->queue.front();
+                // the oldest request that may run now: a temporal stream runs one
+                // frame at a time, in submission order
+                Request* head = nullptr;
+                {
+                    std::unordered_set<int> blocked;
+                    for (Request* r : s->queue) {
+                        if (r->temporal && (blocked.count(r->stream_id) || s->tstreams[r->stream_id].running)) {
+                            blocked.insert(r->stream_id);
+                            continue;
+                        }
+                        head = r;
+                        break;
+                    }
+                }
+                if (!head) break;
                 if (s->mem_in_use + head->footprint > s->scfg.mem_budget) break;  // wait for memory
                 const double age_us =
                     std::chrono::duration<double, std::micro>(Clock::now() - head->t_submit).count();
@@ -212,9 +280,15 @@ static void scheduler(wskpn_server* s) {
                     if (r->h == head->h && r->w == head->w) ++same;
                 if (same < s->scfg.max_batch && age_us < s->scfg.batch_window_us && !s->stopping) break;
                 size_t mem = s->mem_in_use;
+                std::unordered_set<int> tblocked;  // temporal streams that may not join this batch
                 for (auto it = s->queue.begin(); it != s->queue.end() && (int)wk.batch.size() < s->scfg.max_batch;) {
                     Request* r = *it;
-                    if (r->h == head->h && r->w == head->w && mem + r->footprint <= s->scfg.mem_budget) {
+                    bool ok = r->h == head->h && r->w == head->w && mem + r->footprint <= s->scfg.mem_budget;
+                    if (r->temporal) {
+                        if (tblocked.count(r->stream_id) || s->tstreams[r->stream_id].running) ok = false;
+                        tblocked.insert(r->stream_id);  // one frame per stream per batch, and none after a skip
+                    }
+                    if (ok) {
                         mem += r->footprint;
                         r->state = 1;
                         wk.batch.push_back(r);
@@ -225,6 +299,8 @@ static void scheduler(wskpn_server* s) {
                 }
                 s->mem_in_use = mem;
                 s->mem_peak = std::max(s->mem_peak, mem);
+                for (Request* r : wk.batch)
+                    if (r->temporal) s->tstreams[r->stream_id].running = true;
                 const wskpn_status st = dispatch(s, wk);
                 ++s->batches;
                 s->batched_frames += wk.batch.size();
@@ -235,6 +311,7 @@ static void scheduler(wskpn_server* s) {
                         r->status = st;
                         r->t_done = now;
                         s->mem_in_use -= r->footprint;
+                        if (r->temporal) s->tstreams[r->stream_id].running = false;
                     }
                     wk.batch.clear();
                 } else {
@@ -269,6 +346,7 @@ wskpn_status wskpn_serve_config_default(wskpn_serve_config* c) {
     c->mem_budget = (size_t)8 << 30;
     c->use_graphs = 1;
     c->batch_window_us = 200;
+    wskpn_temporal_config_default(&c->temporal);
     return WSKPN_OK;
 }
 
@@ -284,7 +362,7 @@ wskpn_status wskpn_serve_start(const wskpn_config* cfg, const float* host_weight
     if (scfg_in) scfg = *scfg_in;
     if (scfg.mem_budget == 0) scfg.mem_budget = (size_t)8 << 30;
     if (scfg.n_workers < 1 || scfg.n_workers > 32 || scfg.max_batch < 1 || scfg.max_batch > WSKPN_MAX_BATCH ||
-        scfg.max_queue < 1 || scfg.batch_window_us < 0) {
+        scfg.max_queue < 1 || scfg.batch_window_us < 0 || !temporal_config_valid(scfg.temporal)) {
         set_thread_error("wskpn_serve_start: serve config out of range");
         return WSKPN_EINVAL;
     }
@@ -318,16 +396,21 @@ wskpn_status wskpn_serve_start(const wskpn_config* cfg, const float* host_weight
     return WSKPN_OK;
 }
 
-wskpn_status wskpn_serve_submit(wskpn_server* s, int stream_id, const wskpn_frame* frame, int h, int w, float* out,
-                                uint64_t* ticket) {
+static wskpn_status submit(wskpn_server* s, int stream_id, const wskpn_frame* frame, const float* position,
+                           const float* motion, int temporal, int reset, int h, int w, float* out,
+                           uint64_t* ticket) {
     if (!s) return WSKPN_EINVAL;
     if (!frame || !out || !frame->radiance || !frame->albedo || !frame->normal || !frame->depth || h < 1 || w < 1 ||
-        h > s->cfg.max_h || w > s->cfg.max_w) {
+        h > s->cfg.max_h || w > s->cfg.max_w || (temporal && (!position || !motion))) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->err = "wskpn_serve_submit: invalid frame, output or size";
         return WSKPN_EINVAL;
     }
     Request* r = new Request();
+    r->position = position;
+    r->motion = motion;
+    r->temporal = temporal;
+    r->reset = reset;
     r->stream_id = stream_id;
     r->frame = *frame;
     r->h = h;
@@ -359,6 +442,17 @@ wskpn_status wskpn_serve_submit(wskpn_server* s, int stream_id, const wskpn_fram
     }
     s->cv_sched.notify_one();
     return WSKPN_OK;
+}
+
+wskpn_status wskpn_serve_submit(wskpn_server* s, int stream_id, const wskpn_frame* frame, int h, int w, float* out,
+                                uint64_t* ticket) {
+    return submit(s, stream_id, frame, nullptr, nullptr, 0, 0, h, w, out, ticket);
+}
+
+wskpn_status wskpn_serve_submit_temporal(wskpn_server* s, int stream_id, const wskpn_frame* frame,
+                                         const float* position, const float* motion, int reset_history, int h,
+                                         int w, float* out, uint64_t* ticket) {
+    return submit(s, stream_id, frame, position, motion, 1, reset_history != 0, h, w, out, ticket);
 }
 
 wskpn_status wskpn_serve_wait(wskpn_server* s, uint64_t ticket, int timeout_ms) {
@@ -405,6 +499,12 @@ wskpn_status wskpn_serve_stats_get(wskpn_server* s, wskpn_serve_stats* st) {
     st->mem_in_use = s->mem_in_use;
     st->mem_peak = s->mem_peak;
     st->mean_batch = s->batches ? (double)s->batched_frames / s->batches : 0.0;
+    st->temporal_frames = s->temporal_frames;
+    for (const auto& kv : s->tstreams)
+        if (kv.second.t) {
+            ++st->temporal_streams;
+            st->temporal_bytes += 2 * TEMPORAL_PLANES * sizeof(float) * (size_t)kv.second.t->h * kv.second.t->w;
+        }
     if (!s->lat_ms.empty()) {
         std::vector<double> v = s->lat_ms;
         std::sort(v.begin(), v.end());
@@ -439,6 +539,7 @@ void wskpn_serve_stop(wskpn_server* s) {
         cudaFree(wk.slot_out);
         wskpn_destroy(wk.ctx);
     }
+    for (auto& kv : s->tstreams) wskpn_temporal_destroy(kv.second.t);
     for (auto& kv : s->reqs) delete kv.second;
     delete s;
 }

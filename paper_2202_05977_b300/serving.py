@@ -13,13 +13,16 @@ class Server:
     """Continuous-batching denoise server on the current CUDA device."""
 
     def __init__(self, weights, precision="bf16", max_hw=(1440, 2560), n_workers=4, max_batch=4,
-                 max_queue=8192, mem_budget=8 << 30, use_graphs=True, batch_window_us=200, **cfg_kw):
+                 max_queue=8192, mem_budget=8 << 30, use_graphs=True, batch_window_us=200, temporal=None,
+                 **cfg_kw):
         self._lib = _lib.load()
         cfg = default_config(precision, max_batch=max_batch, max_hw=max_hw, **cfg_kw)
         sc = _lib.ServeConfig()
         _lib.check(self._lib.wskpn_serve_config_default(ctypes.byref(sc)))
         sc.n_workers, sc.max_batch, sc.max_queue = n_workers, max_batch, max_queue
         sc.mem_budget, sc.use_graphs, sc.batch_window_us = mem_budget, int(use_graphs), batch_window_us
+        for k, v in (temporal or {}).items():  # alpha_min, tau_pos, tau_normal, min_weight
+            setattr(sc.temporal, k, float(v))
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
         h = ctypes.c_void_p()
         _lib.check(self._lib.wskpn_serve_start(ctypes.byref(cfg), w.ctypes.data, w.size, ctypes.byref(sc),
@@ -36,6 +39,25 @@ class Server:
         t = ctypes.c_uint64()
         s = self._lib.wskpn_serve_submit(self._h, int(stream_id), fr, H, W, ctypes.c_void_p(out.data_ptr()),
                                          ctypes.byref(t))
+        if s != _lib.OK:
+            raise _lib.WskpnError(s, "submit refused")
+        return t.value
+
+    def submit_temporal(self, stream_id, radiance, albedo, normal, depth, position, motion, out, reset=False):
+        """Queue one frame with temporal accumulation (Sec. 4.3) against the
+        history the server keeps for `stream_id`; position [3,H,W] and motion
+        [2,H,W] float32 device tensors -> ticket."""
+        sq = lambda t: t if t.dim() == 4 else t.unsqueeze(0)
+        fr, B, H, W = _frames(sq(radiance), sq(albedo), sq(normal), sq(depth))
+        if B != 1:
+            raise ValueError("one frame per request")
+        for name, t, c in (("position", position, 3), ("motion", motion, 2)):
+            if tuple(t.shape[-3:]) != (c, H, W) or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError(f"{name} must be a contiguous CUDA tensor [{c},{H},{W}]")
+        t = ctypes.c_uint64()
+        s = self._lib.wskpn_serve_submit_temporal(self._h, int(stream_id), fr, ctypes.c_void_p(position.data_ptr()),
+                                                  ctypes.c_void_p(motion.data_ptr()), int(bool(reset)), H, W,
+                                                  ctypes.c_void_p(out.data_ptr()), ctypes.byref(t))
         if s != _lib.OK:
             raise _lib.WskpnError(s, "submit refused")
         return t.value

@@ -70,3 +70,17 @@ def test_null_arguments_rejected():
     assert lib.wskpn_denoise(None, None, 1, 4, 4, None, None) == _lib.EINVAL
     assert lib.wskpn_create(None, None, 0, None) == _lib.EINVAL
     lib.wskpn_destroy(None)
+
+
+def test_temporal_arguments_rejected_without_touching_the_gpu():
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    assert lib.wskpn_temporal_create(None, 0, 16, ctypes.byref(out)) == _lib.EINVAL
+    cfg = _lib.TemporalConfig()
+    lib.wskpn_temporal_config_default(ctypes.byref(cfg))
+    assert (cfg.alpha_min, cfg.tau_normal) == (pytest.approx(0.2), pytest.approx(0.9))
+    cfg.alpha_min = 0.0
+    assert lib.wskpn_temporal_create(ctypes.byref(cfg), 8, 8, ctypes.byref(out)) == _lib.EINVAL
+    assert b"alpha_min" in lib.wskpn_last_error(None)
+    assert lib.wskpn_temporal_step(None, None, None, None, None, None, None) == _lib.EINVAL
+    lib.wskpn_temporal_destroy(None)

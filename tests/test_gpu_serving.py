@@ -109,3 +109,44 @@ def test_budget_limits_concurrency_but_everything_completes(torch):
     st = srv.stats()
     assert st["mem_peak"] <= 2 * per_req and st["completed"] == 6
     srv.stop()
+
+
+def test_temporal_streams_equal_sequential_library_calls(torch):
+    # per-stream temporal histories in the server: frames of three streams
+    # (two sizes) submitted together batch across streams, run one at a time
+    # per stream, and equal TemporalAccumulator + Denoiser called in order
+    import paper_2202_05977_b300 as wk
+    from paper_2202_05977_b300.serving import Server
+    from paper_2202_05977_b300.temporal import TemporalAccumulator
+    wb = synth.make_weights(seed=13)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    streams = {0: synth.make_sequence(40, 56, 4, seed=21), 1: synth.make_sequence(48, 64, 4, seed=22),
+               2: synth.make_sequence(40, 56, 4, seed=23)}
+    data = {s: [{k: dev(f[k]) for k in ("radiance", "albedo", "normal", "depth", "position", "motion")}
+                for f in seq] for s, seq in streams.items()}
+    srv = Server(wb, "bf16", max_hw=(48, 64), n_workers=3, max_batch=4, batch_window_us=500)
+    srv.pause(True)
+    outs, tickets = {}, []
+    for t in range(4):
+        for s in streams:
+            f = data[s][t]
+            o = torch.full((1, 3, *f["radiance"].shape[1:]), float("nan"), device="cuda")
+            outs[(s, t)] = o
+            tickets.append(srv.submit_temporal(s, f["radiance"], f["albedo"], f["normal"], f["depth"],
+                                               f["position"], f["motion"], o, reset=(s == 2 and t == 2)))
+    srv.pause(False)
+    for tk in tickets:
+        assert srv.wait(tk, 20000) == OK
+    st = srv.stats()
+    srv.stop()
+    assert st["temporal_frames"] == 12 and st["temporal_streams"] == 3 and st["failed"] == 0
+    for s, seq in data.items():
+        h, w = seq[0]["radiance"].shape[1:]
+        ta = TemporalAccumulator(h, w)
+        d = wk.Denoiser(wb, "bf16", max_hw=(h, w))
+        for t, f in enumerate(seq):
+            if s == 2 and t == 2:
+                ta.reset()
+            acc = ta.step(f["radiance"], f["position"], f["normal"], f["motion"])
+            ref = d.denoise(acc[None], f["albedo"][None], f["normal"][None], f["depth"][None])
+            assert torch.equal(outs[(s, t)], ref), (s, t)
