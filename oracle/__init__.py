@@ -21,6 +21,9 @@ What it computes (paper sections / equations):
                         loss or SMAPE (Eq. 6).
   * ``temporal.accumulate`` Sec. 4.3 temporal accumulation before denoising
                         (reprojection, geometry consistency, blend); numpy.
+  * ``multires``        the multi-resolution variant: U-Net logits at 3
+                        levels, per-level Eq. 3-5 with kernels 3 and 5, and
+                        the Eq. 7 combination; numpy over the C routines.
 
 Parity status of each function is stated in the tests that pin it; the whole
 denoiser's agreement with the paper's *trained* network is unpinned (no

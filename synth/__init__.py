@@ -32,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "Frame", "make_frame", "make_batch", "make_target", "make_weights",
-    "weight_shapes", "n_weights", "make_sequence", "DEPTH_NEAR", "DEPTH_FAR",
+    "weight_shapes", "n_weights", "make_sequence", "make_weights_for", "DEPTH_NEAR", "DEPTH_FAR",
 ]
 
 DEPTH_NEAR = 1.0
@@ -174,6 +174,19 @@ def weight_shapes(widths=(10, 32, 48, 64, 12), ks: int = 5):
 
 def n_weights(widths=(10, 32, 48, 64, 12), ks: int = 5) -> int:
     return sum(int(np.prod(w)) + int(np.prod(b)) for w, b in weight_shapes(widths, ks))
+
+
+def make_weights_for(shapes, seed: int = 0) -> np.ndarray:
+    """Random-init weights for an arbitrary list of conv layers given as
+    [((Cout, Cin, k, k), (Cout,)), ...], one flat float32 blob in that order,
+    with the same He-normal / uniform recipe as make_weights."""
+    g = _rng(seed, 8)
+    parts = []
+    for ws, bs in shapes:
+        fan_in = ws[1] * ws[2] * ws[3]
+        parts.append(g.standard_normal(ws).ravel() * np.sqrt(2.0 / fan_in))
+        parts.append(g.uniform(-1.0, 1.0, bs) / np.sqrt(fan_in))
+    return np.concatenate(parts).astype(np.float32)
 
 
 def make_weights(widths=(10, 32, 48, 64, 12), ks: int = 5, seed: int = 0) -> np.ndarray:
