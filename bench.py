@@ -66,6 +66,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the 720p / 1440p runs")
+    p.add_argument("--no-variants", action="store_true", help="skip the 6-block network timing")
     p.add_argument("--serve-requests", type=int, default=4096)
     p.add_argument("--serve-rate", type=float, default=240.0)
     p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
@@ -313,10 +314,10 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     pk = peaks()
 
-    def time_path(precision, steps, warmup, hw=(H, W), frame=None):
+    def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None):
         h, w = hw
         xs = xin if frame is None else frame
-        d = wk.Denoiser(wb, precision=precision, max_hw=(h, w))
+        d = wk.Denoiser(wb if weights is None else weights, precision=precision, max_hw=(h, w), widths=widths)
         if args.tc_split is not None and precision == "bf16":
             d.set_tuning(2, args.tc_split)
         if precision == "fp8":  # static activation scales from a different frame (seed 3)
@@ -373,6 +374,27 @@ def main():
             sweep[f"{w}x{h}"] = {"ms_per_frame": r["ms_step"], "fps": 1e3 / r["ms_step"],
                                  "stage_rooflines": stage_rooflines(r["stage_ms"], args.precision, pk, h, w)}
             del r
+
+    # the paper's 6-block quality variant of ImportanceNet (Sec. 4.1), widths
+    # 10-32-48-64-64-64-64 + output conv to 12, at 720p (the paper's timing
+    # resolution) and 1080p
+    variants = {}
+    if not args.no_variants and args.precision != "fp8":
+        w6 = (10, 32, 48, 64, 64, 64, 64, 12)
+        wb6 = synth.make_weights(w6, KS, seed=SEED)
+        f720 = synth.make_frame(720, 1280, 1 + 1000 * rank)
+        x720 = [torch.from_numpy(np.ascontiguousarray(f720[k][None])).to(dev) for k in keys]
+        six = {}
+        for (h, w), xs in (((720, 1280), x720), ((H, W), None)):
+            r = time_path(args.precision, max(5, args.steps // 2), 3, (h, w), xs, w6, wb6)
+            six[f"{w}x{h}"] = {"ms_per_frame": r["ms_step"], "fps": 1e3 / r["ms_step"],
+                               "prediction_ms": sum(r["stage_ms"][:-1]), "reconstruction_ms": r["stage_ms"][-1]}
+            del r
+        if not args.no_fp32 and args.precision != "fp32":
+            r = time_path("fp32", 3, 2, (720, 1280), x720, w6, wb6)
+            six["1280x720"]["fp32_ms_per_frame"] = r["ms_step"]
+            del r
+        variants["six_blocks"] = six
 
     # roofline of the dominant stage (stage 0 prep, 1..L convs, L+1 reconstruction)
     st = main_res["stage_ms"]
@@ -450,6 +472,8 @@ def main():
             sweep["1920x1080"] = {"ms_per_frame": main_res["ms_step"], "fps": 1e3 / main_res["ms_step"],
                                   "stage_rooflines": line["stage_rooflines"]}
             line["resolutions"] = sweep
+        if variants:
+            line["variants"] = variants
         if fp32 is not None:
             line["fp32_ms_per_frame"] = fp32["ms_step"] / world
             line["speedup_vs_fp32"] = fp32["ms_step"] / main_res["ms_step"]

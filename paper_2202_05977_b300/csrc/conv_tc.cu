@@ -64,7 +64,9 @@ struct TcArgs {
     const float* ep_bias;    // [COUT_P]
     void* out;               // NHWC activations, or planar FP32 [B][cout][H][W] for the last layer
     int B, H, W;
-    int cout;                // real output channels
+    int cout;                // real output channels of the layer
+    int out_cp;              // padded output channels per stored pixel (all groups)
+    int out_c0;              // first output channel of this group
     int relu, last;
     int split_out;           // write BF16 hi/lo pairs: [hi(COUT_P) | lo(COUT_P)]
     float out_qscale;        // FP8 activations: 1 / scale of the output activation
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         const size_t HW = (size_t)a.H * a.W;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const int o = c16 * 16 + j;
+                            const int o = a.out_c0 + c16 * 16 + j;
                             if (o < a.cout) z[((size_t)b * a.cout + o) * HW + (size_t)y * a.W + x] = v[j];
                         }
                     } else if constexpr (FP8) {
@@ -473,15 +475,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                                 __NV_SATFINITE, __NV_E4M3);
                             w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
                         }
-                        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + pix * COUT_P + c16 * 16);
+                        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + pix * a.out_cp + a.out_c0 +
+                                                              c16 * 16);
                         *dst = make_uint4(w[0], w[1], w[2], w[3]);
                     } else {
-                        const int rowc = a.split_out ? 2 * COUT_P : COUT_P;  // channels per stored pixel
+                        const int rowc = a.split_out ? 2 * a.out_cp : a.out_cp;  // channels per stored pixel
                         __nv_bfloat162 h2[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
                         uint4* dst =
-                            reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + (pix * rowc + c16 * 16) * 2);
+                            reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + (pix * rowc + a.out_c0 + c16 * 16) * 2);
                         const uint4* src = reinterpret_cast<const uint4*>(h2);
                         dst[0] = src[0];
                         dst[1] = src[1];
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                                 l2[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
                             }
                             uint4* dlo = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) +
-                                                                  (pix * rowc + COUT_P + c16 * 16) * 2);
+                                                                  (pix * rowc + a.out_cp + a.out_c0 + c16 * 16) * 2);
                             const uint4* slo = reinterpret_cast<const uint4*>(l2);
                             dlo[0] = slo[0];
                             dlo[1] = slo[1];
@@ -565,6 +568,23 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
     }
     const int ncc = L.cin_p / (fp8 ? 32 : 16);
     L.wtc_bytes = (size_t)c.conv_ks * c.conv_ks * ncc * L.cout_p * tc::ROWB;
+    // Output-channel groups: the smallest power-of-two count whose weight image
+    // leaves room for two input stages (hi/lo activations assumed), each group
+    // a multiple of 16 channels.
+    L.groups = 1;
+    while (true) {
+        const size_t wg = L.wtc_bytes / L.groups;
+        const int ncc_in = fp8 ? ncc : 2 * ncc;
+        const int cpb = chunks_per_box(ncc_in);
+        const size_t box = ((size_t)(tc::BM + c.conv_ks - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024;
+        const size_t fixed = 1024 + (wg + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
+        if (fixed + 2 * (ncc_in / cpb) * box <= tc::SMEM_MAX) break;
+        if (L.cout_p / (2 * L.groups) < 16 || (L.cout_p / (2 * L.groups)) % 16) {
+            ctx->err = "conv_tc: layer weights do not fit in shared memory";
+            return WSKPN_EUNSUPPORTED;
+        }
+        L.groups *= 2;
+    }
     WSKPN_CUDA_TRY(cudaMalloc(&L.wtc, L.wtc_bytes), ctx->err);
     WSKPN_CUDA_TRY(cudaMalloc(&L.ep_scale, L.cout_p * sizeof(float)), ctx->err);
     WSKPN_CUDA_TRY(cudaMalloc(&L.ep_bias, L.cout_p * sizeof(float)), ctx->err);
@@ -572,26 +592,31 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
     return WSKPN_OK;
 }
 
-// Builds the shared-memory image of a layer's B operand: block
-// ((dx * ncc + cc) * KS + dy) holds the COUT_P rows of 32 bytes (K-major) of
-// tap (dy, dx) and channel chunk cc, so the KS vertical taps of one
-// (dx, cc) pair are consecutive N blocks.  32-byte swizzled like the TMA
+// Builds the shared-memory image of a layer's B operand, one image per
+// output-channel group of cg = cout_p / groups channels: block
+// ((dx * ncc + cc) * KS + dy) of a group holds its cg rows of 32 bytes
+// (K-major) of tap (dy, dx) and channel chunk cc, so the KS vertical taps of
+// one (dx, cc) pair are consecutive N blocks.  32-byte swizzled like the TMA
 // writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).
 __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restrict__ bias, int Cin, int Cout,
-                               int KS, int cout_p, int ncc, int fp8, const float* __restrict__ wscale,
+                               int KS, int cout_p, int groups, int ncc, int fp8, const float* __restrict__ wscale,
                                float act_in_scale, uint8_t* __restrict__ img, float* __restrict__ ep_scale,
                                float* __restrict__ ep_bias) {
     const int ch = fp8 ? 32 : 16;
+    const int cg = cout_p / groups;
     const int n_el = KS * KS * ncc * cout_p * ch;
+    const size_t group_bytes = (size_t)KS * KS * ncc * cg * 32;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += gridDim.x * blockDim.x) {
         const int k = i % ch;
-        const int n = (i / ch) % cout_p;
-        const int chunk = i / (ch * cout_p);
+        const int nl = (i / ch) % cg;
+        const int chunk = (i / (ch * cg)) % (KS * KS * ncc);
+        const int g = i / (ch * cg * KS * KS * ncc);
+        const int n = g * cg + nl;
         const int dy = chunk % KS, cc = (chunk / KS) % ncc, dx = chunk / (KS * ncc);
         const int cin = cc * ch + k;
         const float v = (n < Cout && cin < Cin) ? w[((size_t)n * Cin + cin) * KS * KS + dy * KS + dx] : 0.f;
-        const uint32_t o = (uint32_t)(n * 32 + k * (fp8 ? 1 : 2));
-        const uint32_t phys = (uint32_t)chunk * cout_p * 32 + (o ^ (((o >> 7) & 1u) << 4));
+        const uint32_t o = (uint32_t)(nl * 32 + k * (fp8 ? 1 : 2));
+        const size_t phys = g * group_bytes + (size_t)chunk * cg * 32 + (o ^ (((o >> 7) & 1u) << 4));
         if (fp8) {
             img[phys] = (uint8_t)__nv_cvt_float_to_fp8(v / wscale[n], __NV_SATFINITE, __NV_E4M3);
         } else {
@@ -633,7 +658,7 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
         wscale_kernel<<<L.cout_p, 128, 0, st>>>(w, L.cin, L.cout, c.conv_ks, L.cout_p, L.wscale);
         WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     }
-    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, ncc, fp8, L.wscale,
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, L.wscale,
                                         ctx->act_scale[l], static_cast<uint8_t*>(L.wtc), L.ep_scale, L.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     return WSKPN_OK;
@@ -678,16 +703,16 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
         ctx->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
         return WSKPN_ECUDA;
     }
+    const int G = L.groups, cg = L.cout_p / G;
+    const size_t group_bytes = L.wtc_bytes / G;
     TcArgs a{};
-    a.wimg = L.wtc;
-    a.wbytes = (uint32_t)L.wtc_bytes;
-    a.ep_scale = L.ep_scale;
-    a.ep_bias = L.ep_bias;
+    a.wbytes = (uint32_t)group_bytes;
     a.out = out;
     a.B = B;
     a.H = H;
     a.W = W;
     a.cout = L.cout;
+    a.out_cp = L.cout_p;
     a.last = l == c.n_layers - 1;
     a.relu = !a.last;
     a.split_out = split && !a.last;
@@ -695,7 +720,7 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     // boxes of 128 + KS - 1 rows of cpb x 32 B, each 1024-byte aligned (128B-swizzle atom)
     a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024);
     a.stage_bytes = (uint32_t)((ncc_in / cpb) * a.box_stride);
-    const size_t fixed = 1024 + ((L.wtc_bytes + 1023) / 1024 * 1024) + 256 + 2 * 64 * sizeof(float);
+    const size_t fixed = 1024 + ((group_bytes + 1023) / 1024 * 1024) + 256 + 2 * 64 * sizeof(float);
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
         ctx->err = "conv_tc: layer weights and two input stages do not fit in shared memory";
         return WSKPN_EUNSUPPORTED;
@@ -706,20 +731,22 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     size_t smem = fixed + (size_t)a.stages * a.stage_bytes;
     if (smem < 120 * 1024) smem = 120 * 1024;
     a.tiles_x = cdiv(W, tc::BM);
-    a.tiles_y = cdiv(H, tc::rows_per_tile(L.cout_p));
+    a.tiles_y = cdiv(H, tc::rows_per_tile(cg));
     a.ntiles = a.tiles_x * a.tiles_y * B;
     a.status = ctx->d_status;
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
+    wskpn_status (*launch)(const CUtensorMap&, const TcArgs&, size_t, int, cudaStream_t, std::string&) = nullptr;
 #define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_)                                                  \
-    if (KS == ks_ && L.cout_p == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_)          \
-        return launch_tc_t<ks_, n_, nin_, nw_, f8_>(map, a, smem, grid, st, ctx->err);
+    if (!launch && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_)     \
+        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_>;
 #define WSKPN_TC_BF16(ks_)                                                                                 \
     WSKPN_TC_CASE(ks_, 32, 1, 1, false) WSKPN_TC_CASE(ks_, 32, 2, 1, false)                                \
     WSKPN_TC_CASE(ks_, 48, 2, 2, false) WSKPN_TC_CASE(ks_, 48, 4, 2, false)                                \
     WSKPN_TC_CASE(ks_, 64, 3, 3, false) WSKPN_TC_CASE(ks_, 64, 6, 3, false)                                \
-    WSKPN_TC_CASE(ks_, 16, 4, 4, false) WSKPN_TC_CASE(ks_, 16, 8, 4, false)
+    WSKPN_TC_CASE(ks_, 16, 4, 4, false) WSKPN_TC_CASE(ks_, 16, 8, 4, false)                                \
+    WSKPN_TC_CASE(ks_, 32, 4, 4, false) WSKPN_TC_CASE(ks_, 32, 8, 4, false)
 #define WSKPN_TC_FP8(ks_)                                                                                  \
     WSKPN_TC_CASE(ks_, 32, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 2, 2, true) \
     WSKPN_TC_CASE(ks_, 16, 2, 2, true)
@@ -727,8 +754,20 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
 #undef WSKPN_TC_FP8
 #undef WSKPN_TC_BF16
 #undef WSKPN_TC_CASE
-    ctx->err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M are built";
-    return WSKPN_EUNSUPPORTED;
+    if (!launch) {
+        ctx->err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M "
+                   "and 64-64 are built";
+        return WSKPN_EUNSUPPORTED;
+    }
+    for (int g = 0; g < G; ++g) {  // each group reads the whole input and writes its channels
+        a.wimg = static_cast<const uint8_t*>(L.wtc) + g * group_bytes;
+        a.ep_scale = L.ep_scale + g * cg;
+        a.ep_bias = L.ep_bias + g * cg;
+        a.out_c0 = g * cg;
+        const wskpn_status s = launch(map, a, smem, grid, st, ctx->err);
+        if (s) return s;
+    }
+    return WSKPN_OK;
 }
 
 wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
