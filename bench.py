@@ -395,6 +395,34 @@ def main():
             six["1280x720"]["fp32_ms_per_frame"] = r["ms_step"]
             del r
         variants["six_blocks"] = six
+    if not args.no_variants:
+        # the multi-resolution variant (U-Net, 3 levels, kernels 3 and 5, Eq. 7), FP32
+        from paper_2202_05977_b300.multires import MultiResDenoiser
+        from paper_2202_05977_b300.multires import n_weights as mr_n
+        g = np.random.default_rng(SEED)
+        wmr = (g.standard_normal(mr_n()) * 0.05).astype(np.float32)
+        mres = {}
+        for (h, w), sd in (((720, 1280), 1), ((H, W), SEED)):
+            fr = synth.make_frame(h, w, sd + 1000 * rank)
+            xs = [torch.from_numpy(np.ascontiguousarray(fr[k][None])).to(dev) for k in keys]
+            dm = MultiResDenoiser(wmr, max_hw=(h, w))
+            o = torch.empty((1, 3, h, w), device=dev)
+            for _ in range(3):
+                dm.denoise(*xs, out=o)
+            torch.cuda.synchronize()
+            n_it = max(5, args.steps // 2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for i in range(n_it):
+                flush.fill_(float(i))
+                e0.record()
+                dm.denoise(*xs, out=o)
+                e1.record()
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            mres[f"{w}x{h}"] = {"ms_per_frame": tot / n_it, "fps": 1e3 * n_it / tot, "precision": "fp32"}
+            dm.close()
+        variants["multires_unet"] = mres
 
     # roofline of the dominant stage (stage 0 prep, 1..L convs, L+1 reconstruction)
     st = main_res["stage_ms"]

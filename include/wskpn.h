@@ -295,6 +295,48 @@ wskpn_status wskpn_temporal_reset(wskpn_temporal* t, void* stream);
 
 void wskpn_temporal_destroy(wskpn_temporal* t);
 
+/* ---- Multi-resolution variant (Sec. 5.3 "Implementation", Eq. 7) ----- */
+
+/* The paper's network for high-spp input: a U-Net of 3x3 convolutions
+ * predicts, at full, half and quarter resolution, importance maps for
+ * kernel sizes 3 and 5, their fusion logits and (full and half) a blending
+ * logit; each level filters the demodulated irradiance averaged down to its
+ * resolution (Eq. 3-5), and the levels combine from the coarsest as
+ * o = i^f - alpha U D i^f + alpha U o^c (Eq. 7, D = 2x2 box average,
+ * U = nearest upsampling, alpha = sigmoid of the blending logit); the
+ * output is (a + eps) o.  Layers (weight-blob order, each W[cout][cin][3][3]
+ * then b[cout]): 10-32, 32-32, 32-48, 48-48, 48-64, 64-64, head 64-4,
+ * 112-48 (upsampled 64 + skip 48), head 48-5, 80-32 (upsampled 48 + skip
+ * 32), head 32-5.  The architecture is a reading: the paper defers it to a
+ * supplement.  FP32. */
+typedef struct wskpn_mr wskpn_mr;
+
+typedef struct {
+    int max_h, max_w;                /* largest frame (workspaces sized for it) */
+    float albedo_eps, gamma, depth_near, depth_far;  /* as wskpn_config */
+} wskpn_mr_config;
+
+void wskpn_mr_config_default(wskpn_mr_config* cfg);
+size_t wskpn_mr_n_weights(void);
+
+/* Copies the FP32 weights (wskpn_mr_n_weights() floats, host) to the device
+ * and allocates the workspaces.  cfg may be NULL (defaults: 1080 x 1920).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+wskpn_status wskpn_mr_create(const wskpn_mr_config* cfg, const float* host_weights, size_t n, wskpn_mr** out);
+
+/* Denoises one frame (device planar float32 buffers as wskpn_denoise) into
+ * out [3][h][w] (device).  Calls on one object must not overlap on the GPU.
+ * Errors: EINVAL (size beyond the config, NULL pointers), ECUDA. */
+wskpn_status wskpn_mr_denoise(wskpn_mr* m, const wskpn_frame* frame, int h, int w, float* out, void* stream);
+
+/* The U-Net outputs of one frame: z0 [5][h][w], z1 [5][h1][w1],
+ * z2 [4][h2][w2] (h1 = ceil(h/2), h2 = ceil(h1/2), same for w); device. */
+wskpn_status wskpn_mr_logits(wskpn_mr* m, const wskpn_frame* frame, int h, int w, float* z0, float* z1, float* z2,
+                             void* stream);
+
+const char* wskpn_mr_last_error(const wskpn_mr* m);
+void wskpn_mr_destroy(wskpn_mr* m);
+
 /* ---- Serving: continuous batching of frame-denoise requests --------- */
 
 typedef struct wskpn_server wskpn_server;

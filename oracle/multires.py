@@ -147,6 +147,26 @@ def reconstruct(zs, rad, alb, eps=DEFAULT_EPS, ksizes=KSIZES):
     return (alb + eps) * o
 
 
+def term_scale(zs, rad, alb, eps=DEFAULT_EPS, ksizes=KSIZES):
+    """Per-element magnitude of the three terms Eq. 7 sums at the finest level,
+    (a + eps)(|i_0| + alpha_0 |U D i_0| + alpha_0 |U o_1|): the scale that the
+    rounding error of any evaluation of the combination is proportional to
+    (the combination can cancel to values far below its terms)."""
+    rad, alb = _d(rad), _d(alb)
+    M = len(ksizes)
+    y = rad / (alb + eps)
+    ys = [y]
+    for _ in range(len(zs) - 1):
+        ys.append(downsample(ys[-1]))
+    i_levels = [filter_level(z[:2 * M], yl, ksizes) for z, yl in zip(zs, ys)]
+    o1 = combine(i_levels[1:], [z[2 * M] for z in zs[1:-1]])
+    _, H, W = i_levels[0].shape
+    alpha = 1.0 / (1.0 + np.exp(-_d(zs[0][2 * M])))
+    t = (np.abs(i_levels[0]) + alpha[None] * np.abs(upsample(downsample(i_levels[0]), H, W))
+         + alpha[None] * np.abs(upsample(o1, H, W)))
+    return (alb + eps) * t
+
+
 def denoise(frame, weights, eps=DEFAULT_EPS):
     """The whole multi-resolution denoiser on one frame: [3, H, W] float64."""
     return reconstruct(logits(frame, weights), frame["radiance"], frame["albedo"], eps)

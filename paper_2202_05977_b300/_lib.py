@@ -45,6 +45,11 @@ class TemporalConfig(ctypes.Structure):
                 ("min_weight", ctypes.c_float)]
 
 
+class MrConfig(ctypes.Structure):
+    _fields_ = [("max_h", ctypes.c_int), ("max_w", ctypes.c_int), ("albedo_eps", ctypes.c_float),
+                ("gamma", ctypes.c_float), ("depth_near", ctypes.c_float), ("depth_far", ctypes.c_float)]
+
+
 class ServeConfig(ctypes.Structure):
     _fields_ = [("n_workers", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_queue", ctypes.c_int),
                 ("mem_budget", ctypes.c_size_t), ("use_graphs", ctypes.c_int), ("batch_window_us", ctypes.c_int),
@@ -97,6 +102,13 @@ SIGNATURES = {
     "wskpn_temporal_history": ([_P, _P, _P], _I),
     "wskpn_temporal_reset": ([_P, _P], _I),
     "wskpn_temporal_destroy": ([_P], None),
+    "wskpn_mr_config_default": ([_P], None),
+    "wskpn_mr_n_weights": ([], _SZ),
+    "wskpn_mr_create": ([_P, _P, _SZ, _P], _I),
+    "wskpn_mr_denoise": ([_P, _FR, _I, _I, _P, _P], _I),
+    "wskpn_mr_logits": ([_P, _FR, _I, _I, _P, _P, _P, _P], _I),
+    "wskpn_mr_last_error": ([_P], ctypes.c_char_p),
+    "wskpn_mr_destroy": ([_P], None),
     "wskpn_serve_config_default": ([ctypes.POINTER(ServeConfig)], _I),
     "wskpn_serve_start": ([ctypes.POINTER(Config), _P, _SZ, ctypes.POINTER(ServeConfig), ctypes.POINTER(_P)], _I),
     "wskpn_serve_submit": ([_P, _I, _FR, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)], _I),

@@ -111,9 +111,9 @@ __device__ __noinline__ void window_exact(const float* __restrict__ z, const flo
             const size_t g = (size_t)qy * W + qx;
             const float e = expf(z[g] - m);
             D += e;
-            N0 += e * (r[g] / (a[g] + eps));
-            N1 += e * (r[HW + g] / (a[HW + g] + eps));
-            N2 += e * (r[2 * HW + g] / (a[2 * HW + g] + eps));
+            N0 += e * (a ? r[g] / (a[g] + eps) : r[g]);
+            N1 += e * (a ? r[HW + g] / (a[HW + g] + eps) : r[HW + g]);
+            N2 += e * (a ? r[2 * HW + g] / (a[2 * HW + g] + eps) : r[2 * HW + g]);
         }
     R[0] = N0 / D;
     R[1] = N1 / D;
@@ -208,6 +208,9 @@ __device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float*
 }
 
 // ---------------------------------------------------------------- forward
+// With a NULL albedo the kernel takes r as the irradiance itself and writes
+// the fused filtered irradiance (no demodulation, no re-modulation): the
+// per-level filtering of the multi-resolution variant.
 // The forward kernel keeps the same tile (64 x 16 outputs, 6-pixel halo) but
 // organises each size's work for instruction economy:
 //  * the horizontal pass forms E and E*y on the fly from the E and y planes
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(Decode
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 rv[j][ch] = in ? __ldg(r + ch * HW + g) : 0.f;
-                av[j][ch] = in ? __ldg(a + ch * HW + g) : 0.f;
+                av[j][ch] = in && a ? __ldg(a + ch * HW + g) : 1.f - eps;
             }
         }
 #pragma unroll
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(Decode
             const int t = tid + j * dfw::THREADS;
             if (PER * dfw::THREADS > NREG && t >= NREG) continue;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) sY[ch * NREG + t] = rv[j][ch] / (av[j][ch] + eps);
+            for (int ch = 0; ch < 3; ++ch) sY[ch * NREG + t] = a ? rv[j][ch] / (av[j][ch] + eps) : rv[j][ch];
         }
     }
 
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(Decode
         const size_t g = (size_t)gy * W + gx;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch)
-            out[ch * HW + g] = (__ldg(a + ch * HW + g) + eps) * sAcc[(j * 3 + ch) * dfw::THREADS + tid];
+            out[ch * HW + g] = (a ? __ldg(a + ch * HW + g) + eps : 1.f) * sAcc[(j * 3 + ch) * dfw::THREADS + tid];
     }
 }
 

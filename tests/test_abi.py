@@ -84,3 +84,18 @@ def test_temporal_arguments_rejected_without_touching_the_gpu():
     assert b"alpha_min" in lib.wskpn_last_error(None)
     assert lib.wskpn_temporal_step(None, None, None, None, None, None, None) == _lib.EINVAL
     lib.wskpn_temporal_destroy(None)
+
+
+def test_multires_arguments_rejected_without_touching_the_gpu():
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    w = np.zeros(10, np.float32)
+    assert lib.wskpn_mr_create(None, w.ctypes.data, w.size, ctypes.byref(out)) == _lib.EINVAL
+    assert b"weights" in lib.wskpn_last_error(None)
+    cfg = _lib.MrConfig()
+    lib.wskpn_mr_config_default(ctypes.byref(cfg))
+    assert (cfg.max_h, cfg.max_w) == (1080, 1920)
+    cfg.max_h = 0
+    assert lib.wskpn_mr_create(ctypes.byref(cfg), w.ctypes.data, w.size, ctypes.byref(out)) == _lib.EINVAL
+    assert lib.wskpn_mr_n_weights() == 188_878
+    lib.wskpn_mr_destroy(None)

@@ -1,0 +1,64 @@
+"""Multi-resolution variant (U-Net, 3 levels, Eq. 7) on the GPU against the
+FP64 oracle: the U-Net outputs at every level and the denoised frame."""
+import numpy as np
+import pytest
+
+from oracle import multires as omr
+import synth
+from _util import args, rel_err, stack_frames, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(H, W, seed):
+    from paper_2202_05977_b300.multires import MultiResDenoiser
+    f = synth.make_frame(H, W, seed)
+    wb = synth.make_weights_for(omr.weight_shapes(), seed=seed)
+    return f, wb, MultiResDenoiser(wb, max_hw=(H, W)), args(to_dev(stack_frames([f])))
+
+
+@pytest.mark.parametrize("H,W,seed", [(64, 96, 80), (37, 53, 81), (5, 3, 82)])
+def test_unet_levels_match_oracle(H, W, seed):
+    f, wb, d, a = _setup(H, W, seed)
+    zs = [z.cpu().numpy() for z in d.logits(*a)]
+    refs = omr.logits(f, wb)
+    for l, (z, ref) in enumerate(zip(zs, refs)):
+        assert z.shape == ref.shape
+        assert np.abs(z - ref).max() < 1e-5 * max(1.0, np.abs(ref).max()), l
+
+
+def _err(out, f, wb):
+    """|gpu - ref| relative to max(|ref|, the magnitude of Eq. 7's terms):
+    the combination can cancel to values far below its terms, where any
+    float32 evaluation has an error of ~1e-7 of the terms."""
+    zs = omr.logits(f, wb)
+    ref = omr.reconstruct(zs, f["radiance"], f["albedo"])
+    scale = np.maximum(np.abs(ref), omr.term_scale(zs, f["radiance"], f["albedo"]))
+    e = np.abs(out - ref) / scale
+    return float(e.max()), float(e.mean()), rel_err(out, ref)[1]
+
+
+@pytest.mark.parametrize("H,W,seed", [(64, 96, 80), (37, 53, 81), (130, 257, 83), (5, 3, 82)])
+def test_multires_denoise_matches_oracle(H, W, seed):
+    f, wb, d, a = _setup(H, W, seed)
+    out = d.denoise(*a).cpu().numpy()[0]
+    mx, mean, mean_rel = _err(out, f, wb)
+    print(f"multires {H}x{W}: max err / term scale {mx:.3e}, mean {mean:.3e}; mean rel {mean_rel:.3e}")
+    assert mx < 1e-5 and mean_rel < 1e-5
+
+
+def test_multires_constant_irradiance_passes_through():
+    import torch
+    f, wb, d, _ = _setup(48, 72, 84)
+    c = np.array([0.4, 0.9, 1.3], np.float32)[:, None, None]
+    f["radiance"] = ((f["albedo"] + np.float32(0.01)) * c).astype(np.float32)
+    out = d.denoise(*args(to_dev(stack_frames([f])))).cpu().numpy()[0]
+    assert rel_err(out, f["radiance"])[0] < 1e-5
+
+
+def test_multires_256x384_matches_oracle():
+    f, wb, d, a = _setup(256, 384, 85)
+    out = d.denoise(*a).cpu().numpy()[0]
+    mx, mean, mean_rel = _err(out, f, wb)
+    print(f"multires 256x384: max err / term scale {mx:.3e}, mean {mean:.3e}; mean rel {mean_rel:.3e}")
+    assert mx < 1e-5 and mean_rel < 1e-5

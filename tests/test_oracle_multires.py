@@ -105,3 +105,12 @@ def test_multires_denoiser_passes_a_constant_irradiance_through():
 
 def test_n_weights_matches_the_layer_list():
     assert mr.n_weights() == synth.make_weights_for(mr.weight_shapes()).size == 188_878  # 2912+9248+13872+20784+27712+36928+2308+48432+2165+23072+1445
+
+
+def test_term_scale_bounds_the_output():
+    f = synth.make_frame(21, 30, 7)
+    wb = synth.make_weights_for(mr.weight_shapes(), seed=7)
+    zs = mr.logits(f, wb)
+    out = mr.reconstruct(zs, f["radiance"], f["albedo"])
+    sc = mr.term_scale(zs, f["radiance"], f["albedo"])
+    assert np.all(np.abs(out) <= sc * (1 + 1e-12))
