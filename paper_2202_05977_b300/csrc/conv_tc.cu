@@ -5,8 +5,8 @@
 // GEMM view of one tile: M = 128 consecutive pixels of an image row (TMEM
 // lanes), N = padded output channels, K = KS*KS taps x input channels,
 // consumed 32 bytes (16 BF16 or 32 e4m3 channels) per MMA.  A CTA owns
-// R output rows x 128 pixels (R = 8 for layers with at most 32 output
-// channels, else 4) and keeps R accumulators (one per output row) in TMEM,
+// R output rows x 128 pixels (R = 8, 5, 4 for at most 32, 48, 64 output
+// channels) and keeps R accumulators (one per output row) in TMEM,
 // double-buffered across tiles so the epilogue of one tile
 // overlaps the MMAs of the next.  Each input row is fetched once per tile
 // (one TMA box of 128 + KS - 1 pixels per 32-byte channel chunk) and
@@ -46,10 +46,15 @@ namespace wskpn {
 
 namespace tc {
 constexpr int BM = 128;            // pixels per tile row = MMA M = TMEM lanes
-// Output rows per tile: 8 when two buffers of 8 row accumulators fit in
-// TMEM (COUT_P <= 32), else 4.  More rows per tile means fewer MMAs per
-// output row, since an input row's MMA serves up to min(R, KS) output rows.
-__host__ __device__ constexpr int rows_per_tile(int cout_p) { return cout_p <= 32 ? 8 : 4; }
+// Output rows per tile: as many as two buffers of R row accumulators allow
+// in TMEM (2 R COUT_P <= 512 columns), at most 8.  More rows per tile means
+// fewer MMAs per output row, since an input row's MMA serves up to
+// min(R, KS) output rows, and fewer re-fetched halo rows.  Beyond 8 rows the
+// unrolled MMA sequences of all input rows outgrow the instruction cache
+// (16 rows for 16 channels measured 0.58 ms against 0.39 ms with 8).
+__host__ __device__ constexpr int rows_per_tile(int cout_p) {
+    return cout_p <= 32 ? 8 : cout_p <= 48 ? 5 : 4;
+}
 constexpr int THREADS = 192;
 constexpr int ROWB = 32;           // bytes of one pixel row of one K chunk
 constexpr uint32_t SMEM_MAX = 232448;
@@ -437,11 +442,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             tc_fence_after();
             const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
             const int x = tx * tc::BM + p;
+            // bytes per stored pixel of an NHWC output (BF16 hi/lo pairs double it)
+            const size_t pix_bytes = FP8 ? (size_t)a.out_cp : (size_t)a.out_cp * 2 * (a.split_out ? 2 : 1);
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const int y = ty * R + r;
                 const bool valid = x < a.W && y < a.H;
                 const uint32_t col = (uint32_t)(buf * R * COUT_P + (R - 1 - r) * COUT_P);
+                const size_t pix = ((size_t)b * a.H + y) * a.W + x;
+                // this group's first channel of the pixel (hi half for BF16)
+                uint8_t* const pbase = static_cast<uint8_t*>(a.out) + pix * pix_bytes + (size_t)a.out_c0 * (FP8 ? 1 : 2);
 #pragma unroll
                 for (int c16 = 0; c16 < COUT_P / 16; ++c16) {
                     float v[16];
@@ -454,15 +464,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         v[j] = fmaf(v[j], s_scale[o], s_bias[o]);
                         if (a.relu) v[j] = fmaxf(v[j], 0.f);
                     }
-                    const size_t pix = ((size_t)b * a.H + y) * a.W + x;
                     if (a.last) {
-                        float* z = static_cast<float*>(a.out);
                         const size_t HW = (size_t)a.H * a.W;
+                        const int o0 = a.out_c0 + c16 * 16;  // first of these 16 output channels
+                        float* z = static_cast<float*>(a.out) + ((size_t)b * a.cout + o0) * HW + (size_t)y * a.W + x;
+                        const int nvalid = a.cout - o0;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int o = a.out_c0 + c16 * 16 + j;
-                            if (o < a.cout) z[((size_t)b * a.cout + o) * HW + (size_t)y * a.W + x] = v[j];
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            if (j < nvalid) z[(size_t)j * HW] = v[j];
                     } else if constexpr (FP8) {
                         uint32_t w[4];
 #pragma unroll
@@ -475,16 +484,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                                 __NV_SATFINITE, __NV_E4M3);
                             w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
                         }
-                        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + pix * a.out_cp + a.out_c0 +
-                                                              c16 * 16);
-                        *dst = make_uint4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<uint4*>(pbase + c16 * 16) = make_uint4(w[0], w[1], w[2], w[3]);
                     } else {
-                        const int rowc = a.split_out ? 2 * a.out_cp : a.out_cp;  // channels per stored pixel
                         __nv_bfloat162 h2[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        uint4* dst =
-                            reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) + (pix * rowc + a.out_c0 + c16 * 16) * 2);
+                        uint4* dst = reinterpret_cast<uint4*>(pbase + c16 * 32);
                         const uint4* src = reinterpret_cast<const uint4*>(h2);
                         dst[0] = src[0];
                         dst[1] = src[1];
@@ -496,8 +501,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                                 const float2 hf = __bfloat1622float2(h2[j]);
                                 l2[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
                             }
-                            uint4* dlo = reinterpret_cast<uint4*>(static_cast<uint8_t*>(a.out) +
-                                                                  (pix * rowc + a.out_cp + a.out_c0 + c16 * 16) * 2);
+                            uint4* dlo = reinterpret_cast<uint4*>(pbase + (size_t)a.out_cp * 2 + c16 * 32);
                             const uint4* slo = reinterpret_cast<const uint4*>(l2);
                             dlo[0] = slo[0];
                             dlo[1] = slo[1];

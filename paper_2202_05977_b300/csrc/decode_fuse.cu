@@ -415,6 +415,7 @@ __device__ __noinline__ void fwd_size(float* __restrict__ sE, float2* __restrict
     }
 }
 
+template <bool DEMOD>
 __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(DecodeArgs args) {
     extern __shared__ float4 dsm4[];
     float* smem = reinterpret_cast<float*>(dsm4);
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(Decode
     const int tx0 = blockIdx.x * dfw::TW, ty0 = blockIdx.y * dfw::TH;
     const float* __restrict__ z = args.z.p[b];
     const float* __restrict__ r = args.r.p[b];
-    const float* __restrict__ a = args.a.p[b];
+    const float* __restrict__ a = DEMOD ? args.a.p[b] : nullptr;
     const float eps = args.eps;
 
     // Demodulated irradiance y = r / (a + eps) on tile + halo (0 outside the image);
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(Decode
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 rv[j][ch] = in ? __ldg(r + ch * HW + g) : 0.f;
-                av[j][ch] = in && a ? __ldg(a + ch * HW + g) : 1.f - eps;
+                av[j][ch] = in && DEMOD ? __ldg(a + ch * HW + g) : 1.f - eps;
             }
         }
 #pragma unroll
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(Decode
             const int t = tid + j * dfw::THREADS;
             if (PER * dfw::THREADS > NREG && t >= NREG) continue;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) sY[ch * NREG + t] = a ? rv[j][ch] / (av[j][ch] + eps) : rv[j][ch];
+            for (int ch = 0; ch < 3; ++ch) sY[ch * NREG + t] = DEMOD ? rv[j][ch] / (av[j][ch] + eps) : rv[j][ch];
         }
     }
 
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(Decode
         const size_t g = (size_t)gy * W + gx;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch)
-            out[ch * HW + g] = (a ? __ldg(a + ch * HW + g) + eps : 1.f) * sAcc[(j * 3 + ch) * dfw::THREADS + tid];
+            out[ch * HW + g] = (DEMOD ? __ldg(a + ch * HW + g) + eps : 1.f) * sAcc[(j * 3 + ch) * dfw::THREADS + tid];
     }
 }
 
@@ -524,7 +525,10 @@ wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r
                                     const float* const* a, float* const* out, int B, int H, int W,
                                     int M, const int* ks, float eps, unsigned int* fallbacks,
                                     cudaStream_t st, std::string& err) {
-    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)dfw::SMEM_BYTES),
+                   err);
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)dfw::SMEM_BYTES),
                    err);
     for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
@@ -543,7 +547,10 @@ wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r
         args.eps = eps;
         args.fallbacks = fallbacks;
         dim3 grid(cdiv(W, dfw::TW), cdiv(H, dfw::TH), nb);
-        decode_fuse_fwd_kernel<<<grid, dfw::THREADS, dfw::SMEM_BYTES, st>>>(args);
+        if (a[b0])  // every frame of a call either has an albedo or none
+            decode_fuse_fwd_kernel<true><<<grid, dfw::THREADS, dfw::SMEM_BYTES, st>>>(args);
+        else
+            decode_fuse_fwd_kernel<false><<<grid, dfw::THREADS, dfw::SMEM_BYTES, st>>>(args);
         WSKPN_CUDA_TRY(cudaGetLastError(), err);
     }
     return WSKPN_OK;
