@@ -48,9 +48,6 @@ TRAFFIC = {
     ("bf16", "conv2 (32->48)"): 609.6e6,
     ("bf16", "conv3 (48->64)"): 875.6e6,
     ("bf16", "conv4 (64->12)"): 616.5e6,
-    ("bf16", "decode_fuse_fwd"): 165.4e6,
-    ("fp32", "decode_fuse_fwd"): 165.4e6,
-    ("fp8", "decode_fuse_fwd"): 165.4e6,
 }
 
 

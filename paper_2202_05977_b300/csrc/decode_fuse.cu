@@ -211,8 +211,10 @@ __device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float*
 // With a NULL albedo the kernel takes r as the irradiance itself and writes
 // the fused filtered irradiance (no demodulation, no re-modulation): the
 // per-level filtering of the multi-resolution variant.
-// The forward kernel keeps the same tile (64 x 16 outputs, 6-pixel halo) but
-// organises each size's work for instruction economy:
+// The forward kernel uses 64 x 32 output tiles (6-pixel halo, 512 threads,
+// one CTA per SM: the halo overhead of a tile is 1.6x its area for the
+// largest window instead of 2.1x with 64 x 16) and organises each size's
+// work for instruction economy:
 //  * the horizontal pass forms E and E*y on the fly from the E and y planes
 //    and handles the four planes as two packed pairs (D, N0) and (N1, N2)
 //    with paired FP32 adds;
@@ -224,14 +226,14 @@ __device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float*
 //  * alpha (Eq. 5) is computed once per pixel into shared memory.
 namespace dfw {
 constexpr int TW = 64;                  // tile width (output pixels)
-constexpr int TH = 16;                  // tile height
+constexpr int TH = 32;                  // tile height
 constexpr int HALO = 6;                 // largest half window (k = 13)
 constexpr int RW = TW + 2 * HALO;       // 76: region pitch in floats (76 / 4 odd: row-strided 16-byte accesses are conflict-free)
-constexpr int RH = TH + 2 * HALO;       // 28
+constexpr int RH = TH + 2 * HALO;       // 44
 constexpr int SEG = 8;                  // horizontal-pass outputs per item
 constexpr int NSEG = TW / SEG;          // 8
 constexpr int HP2 = TW + 2;             // pitch of the packed horizontal-sum rows in float2 (132 floats, 132 / 4 odd)
-constexpr int THREADS = 256;
+constexpr int THREADS = 512;
 constexpr int RPT = TH * TW / THREADS;  // 4 output pixels per thread, one column
 static_assert(THREADS / TW * RPT == TH, "vertical-pass mapping");
 static_assert(RH * NSEG <= THREADS, "one horizontal item per thread");
@@ -416,7 +418,7 @@ __device__ __noinline__ void fwd_size(float* __restrict__ sE, float2* __restrict
 }
 
 template <bool DEMOD>
-__global__ void __launch_bounds__(dfw::THREADS, 2) decode_fuse_fwd_kernel(DecodeArgs args) {
+__global__ void __launch_bounds__(dfw::THREADS, 1) decode_fuse_fwd_kernel(DecodeArgs args) {
     extern __shared__ float4 dsm4[];
     float* smem = reinterpret_cast<float*>(dsm4);
     float* sY = smem + dfw::OFF_Y;
