@@ -402,23 +402,27 @@ def main():
         for (h, w), sd in (((720, 1280), 1), ((H, W), SEED)):
             fr = synth.make_frame(h, w, sd + 1000 * rank)
             xs = [torch.from_numpy(np.ascontiguousarray(fr[k][None])).to(dev) for k in keys]
-            dm = MultiResDenoiser(wmr, max_hw=(h, w))
-            o = torch.empty((1, 3, h, w), device=dev)
-            for _ in range(3):
-                dm.denoise(*xs, out=o)
-            torch.cuda.synchronize()
-            n_it = max(5, args.steps // 2)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            tot = 0.0
-            for i in range(n_it):
-                flush.fill_(float(i))
-                e0.record()
-                dm.denoise(*xs, out=o)
-                e1.record()
+            entry = {}
+            for prec in ("bf16", "fp32"):
+                dm = MultiResDenoiser(wmr, max_hw=(h, w), precision=prec)
+                o = torch.empty((1, 3, h, w), device=dev)
+                for _ in range(3):
+                    dm.denoise(*xs, out=o)
                 torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
-            mres[f"{w}x{h}"] = {"ms_per_frame": tot / n_it, "fps": 1e3 * n_it / tot, "precision": "fp32"}
-            dm.close()
+                n_it = max(5, args.steps // 2)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                tot = 0.0
+                for i in range(n_it):
+                    flush.fill_(float(i))
+                    e0.record()
+                    dm.denoise(*xs, out=o)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    tot += e0.elapsed_time(e1)
+                entry[f"{prec}_ms_per_frame"] = tot / n_it
+                dm.close()
+            entry["fps_bf16"] = 1e3 / entry["bf16_ms_per_frame"]
+            mres[f"{w}x{h}"] = entry
         variants["multires_unet"] = mres
 
     # roofline of the dominant stage (stage 0 prep, 1..L convs, L+1 reconstruction)

@@ -308,12 +308,14 @@ void wskpn_temporal_destroy(wskpn_temporal* t);
  * then b[cout]): 10-32, 32-32, 32-48, 48-48, 48-64, 64-64, head 64-4,
  * 112-48 (upsampled 64 + skip 48), head 48-5, 80-32 (upsampled 48 + skip
  * 32), head 32-5.  The architecture is a reading: the paper defers it to a
- * supplement.  FP32. */
+ * supplement.  The decode, Eq. 7 and re-modulation are FP32 in every mode. */
 typedef struct wskpn_mr wskpn_mr;
 
 typedef struct {
     int max_h, max_w;                /* largest frame (workspaces sized for it) */
     float albedo_eps, gamma, depth_near, depth_far;  /* as wskpn_config */
+    wskpn_precision prec;            /* WSKPN_FP32 (SIMT convolutions) or WSKPN_BF16
+                                        (tcgen05, hi/lo activations); default FP32 */
 } wskpn_mr_config;
 
 void wskpn_mr_config_default(wskpn_mr_config* cfg);

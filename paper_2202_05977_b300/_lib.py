@@ -47,7 +47,8 @@ class TemporalConfig(ctypes.Structure):
 
 class MrConfig(ctypes.Structure):
     _fields_ = [("max_h", ctypes.c_int), ("max_w", ctypes.c_int), ("albedo_eps", ctypes.c_float),
-                ("gamma", ctypes.c_float), ("depth_near", ctypes.c_float), ("depth_far", ctypes.c_float)]
+                ("gamma", ctypes.c_float), ("depth_near", ctypes.c_float), ("depth_far", ctypes.c_float),
+                ("prec", ctypes.c_int)]
 
 
 class ServeConfig(ctypes.Structure):

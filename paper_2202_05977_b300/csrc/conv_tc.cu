@@ -560,6 +560,34 @@ size_t tc_act_bytes_per_pixel(const wskpn_config& c, int which) {
     return m;
 }
 
+// Output-channel groups and device buffers of a tensor-core layer whose
+// cin_p / cout_p are set: the smallest power-of-two group count whose weight
+// image leaves room for two input stages (hi/lo activations assumed for
+// BF16), each group a multiple of 16 channels.
+wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, std::string& err) {
+    const int ncc = L.cin_p / (fp8 ? 32 : 16);
+    L.wtc_bytes = (size_t)KS * KS * ncc * L.cout_p * tc::ROWB;
+    L.groups = 1;
+    while (true) {
+        const size_t wg = L.wtc_bytes / L.groups;
+        const int ncc_in = fp8 ? ncc : 2 * ncc;
+        const int cpb = chunks_per_box(ncc_in);
+        const size_t box = ((size_t)(tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024;
+        const size_t fixed = 1024 + (wg + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
+        if (fixed + 2 * (ncc_in / cpb) * box <= tc::SMEM_MAX) break;
+        if (L.cout_p / (2 * L.groups) < 16 || (L.cout_p / (2 * L.groups)) % 16) {
+            err = "conv_tc: layer weights do not fit in shared memory";
+            return WSKPN_EUNSUPPORTED;
+        }
+        L.groups *= 2;
+    }
+    WSKPN_CUDA_TRY(cudaMalloc(&L.wtc, L.wtc_bytes), err);
+    WSKPN_CUDA_TRY(cudaMalloc(&L.ep_scale, L.cout_p * sizeof(float)), err);
+    WSKPN_CUDA_TRY(cudaMalloc(&L.ep_bias, L.cout_p * sizeof(float)), err);
+    WSKPN_CUDA_TRY(cudaMalloc(&L.wscale, L.cout_p * sizeof(float)), err);
+    return WSKPN_OK;
+}
+
 wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
     const wskpn_config& c = ctx->cfg;
     Layer& L = ctx->layers[l];
@@ -570,30 +598,7 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
         ctx->err = "tensor-core path supports at most 64 output channels per layer";
         return WSKPN_EUNSUPPORTED;
     }
-    const int ncc = L.cin_p / (fp8 ? 32 : 16);
-    L.wtc_bytes = (size_t)c.conv_ks * c.conv_ks * ncc * L.cout_p * tc::ROWB;
-    // Output-channel groups: the smallest power-of-two count whose weight image
-    // leaves room for two input stages (hi/lo activations assumed), each group
-    // a multiple of 16 channels.
-    L.groups = 1;
-    while (true) {
-        const size_t wg = L.wtc_bytes / L.groups;
-        const int ncc_in = fp8 ? ncc : 2 * ncc;
-        const int cpb = chunks_per_box(ncc_in);
-        const size_t box = ((size_t)(tc::BM + c.conv_ks - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024;
-        const size_t fixed = 1024 + (wg + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
-        if (fixed + 2 * (ncc_in / cpb) * box <= tc::SMEM_MAX) break;
-        if (L.cout_p / (2 * L.groups) < 16 || (L.cout_p / (2 * L.groups)) % 16) {
-            ctx->err = "conv_tc: layer weights do not fit in shared memory";
-            return WSKPN_EUNSUPPORTED;
-        }
-        L.groups *= 2;
-    }
-    WSKPN_CUDA_TRY(cudaMalloc(&L.wtc, L.wtc_bytes), ctx->err);
-    WSKPN_CUDA_TRY(cudaMalloc(&L.ep_scale, L.cout_p * sizeof(float)), ctx->err);
-    WSKPN_CUDA_TRY(cudaMalloc(&L.ep_bias, L.cout_p * sizeof(float)), ctx->err);
-    WSKPN_CUDA_TRY(cudaMalloc(&L.wscale, L.cout_p * sizeof(float)), ctx->err);
-    return WSKPN_OK;
+    return tc_layer_alloc(L, c.conv_ks, fp8, ctx->err);
 }
 
 // Builds the shared-memory image of a layer's B operand, one image per
@@ -678,18 +683,32 @@ static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t 
     return WSKPN_OK;
 }
 
-// One conv layer on the tensor cores.  in: NHWC [B][H][W][cin_p x (1 or 2)]
-// (BF16 or e4m3); out: NHWC activations or (last) planar FP32 [B][cout][H][W].
-static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st) {
-    const wskpn_config& c = ctx->cfg;
-    const Layer& L = ctx->layers[l];
-    const bool fp8 = c.prec == WSKPN_FP8;
-    const int KS = c.conv_ks;
+// One conv layer on the tensor cores, independent of a context.
+// in: NHWC [B][H][W][cin_p x (split_in ? 2 : 1)] (BF16 or e4m3); out: NHWC
+// with out_cp channels per stored pixel (x 2 when split_out), this layer's
+// channels starting at out_c0, or (last) planar FP32 [B][cout][H][W].
+struct TcRun {
+    const Layer* L;
+    int KS;
+    bool fp8;
+    int split_in, split_out;
+    int last, relu;
+    int out_cp, out_c0;
+    float out_qscale;
+    unsigned int* status;
+    int device;
+};
+
+static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int H, int W, cudaStream_t st,
+                           std::string& err) {
+    const Layer& L = *r.L;
+    const bool fp8 = r.fp8;
+    const int KS = r.KS;
     const int eb = fp8 ? 1 : 2;
     const int ch = fp8 ? 32 : 16;
-    PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode(ctx->err);
+    PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode(err);
     if (!encode) return WSKPN_EUNSUPPORTED;
-    const int split = fp8 ? 0 : ctx->tc_split;
+    const int split = fp8 ? 0 : r.split_in;
     const int cin_row = L.cin_p * (split ? 2 : 1);  // stored channels per input pixel
     CUtensorMap map;
     cuuint64_t gdim[4] = {(cuuint64_t)cin_row, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
@@ -704,7 +723,7 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
                          cpb == 4 ? CU_TENSOR_MAP_SWIZZLE_128B : (cpb == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
-        ctx->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
+        err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
         return WSKPN_ECUDA;
     }
     const int G = L.groups, cg = L.cout_p / G;
@@ -716,17 +735,17 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     a.H = H;
     a.W = W;
     a.cout = L.cout;
-    a.out_cp = L.cout_p;
-    a.last = l == c.n_layers - 1;
-    a.relu = !a.last;
-    a.split_out = split && !a.last;
-    a.out_qscale = fp8 && !a.last ? 1.f / ctx->act_scale[l + 1] : 1.f;
+    a.out_cp = r.out_cp;
+    a.last = r.last;
+    a.relu = r.relu;
+    a.split_out = r.split_out && !r.last && !fp8;
+    a.out_qscale = r.out_qscale;
     // boxes of 128 + KS - 1 rows of cpb x 32 B, each 1024-byte aligned (128B-swizzle atom)
     a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024);
     a.stage_bytes = (uint32_t)((ncc_in / cpb) * a.box_stride);
     const size_t fixed = 1024 + ((group_bytes + 1023) / 1024 * 1024) + 256 + 2 * 64 * sizeof(float);
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
-        ctx->err = "conv_tc: layer weights and two input stages do not fit in shared memory";
+        err = "conv_tc: layer weights and two input stages do not fit in shared memory";
         return WSKPN_EUNSUPPORTED;
     }
     const int stages = (int)((tc::SMEM_MAX - fixed) / a.stage_bytes);
@@ -737,9 +756,9 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     a.tiles_x = cdiv(W, tc::BM);
     a.tiles_y = cdiv(H, tc::rows_per_tile(cg));
     a.ntiles = a.tiles_x * a.tiles_y * B;
-    a.status = ctx->d_status;
+    a.status = r.status;
     int nsm = 148;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, r.device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
     wskpn_status (*launch)(const CUtensorMap&, const TcArgs&, size_t, int, cudaStream_t, std::string&) = nullptr;
 #define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_)                                                  \
@@ -754,24 +773,94 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
 #define WSKPN_TC_FP8(ks_)                                                                                  \
     WSKPN_TC_CASE(ks_, 32, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 2, 2, true) \
     WSKPN_TC_CASE(ks_, 16, 2, 2, true)
-    WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3)
+// the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
+// 112-48, 80-32 and the heads 48-5, 32-5
+#define WSKPN_TC_UNET                                                                                      \
+    WSKPN_TC_CASE(3, 32, 4, 2, false) WSKPN_TC_CASE(3, 48, 6, 3, false) WSKPN_TC_CASE(3, 64, 8, 4, false)  \
+    WSKPN_TC_CASE(3, 48, 14, 7, false) WSKPN_TC_CASE(3, 32, 10, 5, false) WSKPN_TC_CASE(3, 16, 6, 3, false) \
+    WSKPN_TC_CASE(3, 16, 4, 2, false)
+    WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3) WSKPN_TC_UNET
+#undef WSKPN_TC_UNET
 #undef WSKPN_TC_FP8
 #undef WSKPN_TC_BF16
 #undef WSKPN_TC_CASE
     if (!launch) {
-        ctx->err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M "
-                   "and 64-64 are built";
+        err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M, "
+              "64-64 and the multi-resolution U-Net are built";
         return WSKPN_EUNSUPPORTED;
     }
     for (int g = 0; g < G; ++g) {  // each group reads the whole input and writes its channels
         a.wimg = static_cast<const uint8_t*>(L.wtc) + g * group_bytes;
         a.ep_scale = L.ep_scale + g * cg;
         a.ep_bias = L.ep_bias + g * cg;
-        a.out_c0 = g * cg;
-        const wskpn_status s = launch(map, a, smem, grid, st, ctx->err);
+        a.out_c0 = r.out_c0 + g * cg;
+        const wskpn_status s = launch(map, a, smem, grid, st, err);
         if (s) return s;
     }
     return WSKPN_OK;
+}
+
+// One layer of a context's ImportanceNet.
+static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st) {
+    const wskpn_config& c = ctx->cfg;
+    const bool fp8 = c.prec == WSKPN_FP8;
+    TcRun r{};
+    r.L = &ctx->layers[l];
+    r.KS = c.conv_ks;
+    r.fp8 = fp8;
+    r.split_in = r.split_out = fp8 ? 0 : ctx->tc_split;
+    r.last = l == c.n_layers - 1;
+    r.relu = !r.last;
+    r.out_cp = ctx->layers[l].cout_p;
+    r.out_c0 = 0;
+    r.out_qscale = fp8 && !r.last ? 1.f / ctx->act_scale[l + 1] : 1.f;
+    r.status = ctx->d_status;
+    r.device = ctx->device;
+    return tc_run(r, in, out, B, H, W, st, ctx->err);
+}
+
+// A BF16 layer (hi/lo activations) outside a context: weight image, groups,
+// epilogue bias; w [cout][cin][KS][KS] and b [cout] on the device.
+wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, cudaStream_t st, std::string& err) {
+    L.cin_p = chan_pad(L.cin, false);
+    L.cout_p = (L.cout + 15) / 16 * 16;
+    if (L.cout_p > 64) {
+        err = "tensor-core path supports at most 64 output channels per layer";
+        return WSKPN_EUNSUPPORTED;
+    }
+    wskpn_status s = tc_layer_alloc(L, KS, false, err);
+    if (s) return s;
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, KS, L.cout_p, L.groups, L.cin_p / 16, 0, L.wscale, 1.f,
+                                        static_cast<uint8_t*>(L.wtc), L.ep_scale, L.ep_bias);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    return WSKPN_OK;
+}
+
+void tc_layer_free(Layer& L) {
+    cudaFree(L.wtc);
+    cudaFree(L.ep_scale);
+    cudaFree(L.ep_bias);
+    cudaFree(L.wscale);
+    L.wtc = nullptr;
+    L.ep_scale = L.ep_bias = L.wscale = nullptr;
+}
+
+wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int out_cp, int out_c0, int last,
+                          int relu, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
+                          std::string& err) {
+    TcRun r{};
+    r.L = &L;
+    r.KS = KS;
+    r.fp8 = false;
+    r.split_in = r.split_out = 1;
+    r.last = last;
+    r.relu = relu;
+    r.out_cp = out_cp;
+    r.out_c0 = out_c0;
+    r.out_qscale = 1.f;
+    r.status = status;
+    r.device = device;
+    return tc_run(r, in, out, B, H, W, st, err);
 }
 
 wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,

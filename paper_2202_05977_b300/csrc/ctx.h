@@ -77,6 +77,13 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l);
 wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st);
 wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                        cudaStream_t st);
+wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, std::string& err);
+// BF16 tensor-core layers outside a context (hi/lo activations in and out)
+wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, cudaStream_t st, std::string& err);
+void tc_layer_free(Layer& L);
+wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int out_cp, int out_c0, int last,
+                          int relu, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
+                          std::string& err);
 }  // namespace wskpn
 
 // Temporal accumulation history of one stream (temporal.cu): planes

@@ -1,5 +1,5 @@
 // Multi-resolution variant of the denoiser (the paper's configuration for
-// high-spp input, Sec. 5.3 "Implementation", Eq. 7), FP32.
+// high-spp input, Sec. 5.3 "Implementation", Eq. 7), U-Net in FP32 or BF16.
 //
 // A U-Net of 3x3 convolutions predicts, at 3 resolutions, importance maps for
 // kernel sizes 3 and 5, their fusion logits and (levels 0 and 1) a blending
@@ -14,9 +14,13 @@
 // the levels combine from the coarsest with Eq. 7:
 //   o_l = i_l - alpha_l U D i_l + alpha_l U o_{l+1},   out = (a + eps) o_0.
 //
-// Layout: planar FP32 [C][h][w] per level.  Concatenations cost nothing: the
-// skip activation E0b (E1b) is written straight after the planes the
-// upsampling of D1 (E2b) fills, so [U D1, E0b] is one contiguous input.
+// FP32: planar [C][h][w] per level, SIMT convolutions.  BF16: channels-last
+// hi/lo activations [pixel][hi(C) | lo(C)] and tcgen05 convolutions, FP32
+// network outputs.  Concatenations cost nothing in either layout: the skip
+// activation E0b (E1b) is written straight into its channels (planes) of
+// the buffer the upsampling of D1 (E2b) fills, so [U D1, E0b] is one input.
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include "ctx.h"
@@ -113,6 +117,49 @@ __global__ void combine_kernel(const float* __restrict__ i_f, const float* __res
     }
 }
 
+// BF16 hi/lo NHWC: D over channels [c0, c0 + C) of pixels [hi(in_cp) | lo(in_cp)]
+// -> [hi(C) | lo(C)] at ceil halves; the mean of hi + lo is split again.
+__global__ void pool_nhwc_kernel(const __nv_bfloat16* __restrict__ x, int in_cp, int c0, int C, int h, int w,
+                                 __nv_bfloat16* __restrict__ y) {
+    const int h2 = (h + 1) / 2, w2 = (w + 1) / 2;
+    const size_t n = (size_t)C * h2 * w2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int X = (int)(q % w2), Y = (int)(q / w2);
+        const int x0 = 2 * X, y0 = 2 * Y;
+        float s = 0.f;
+        int cnt = 0;
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                if (x0 + dx >= w || y0 + dy >= h) continue;
+                const __nv_bfloat16* p = x + ((size_t)(y0 + dy) * w + x0 + dx) * 2 * in_cp + c0 + c;
+                s += __bfloat162float(p[0]) + __bfloat162float(p[in_cp]);
+                ++cnt;
+            }
+        const float v = s / (float)cnt;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        y[q * 2 * C + c] = hi;
+        y[q * 2 * C + C + c] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+// BF16 hi/lo NHWC: U of [hi(C) | lo(C)] at ceil halves into channels
+// [c0, c0 + C) of pixels [hi(out_cp) | lo(out_cp)] at (h, w).
+__global__ void up_nhwc_kernel(const __nv_bfloat16* __restrict__ x, int C, int h, int w, int out_cp, int c0,
+                               __nv_bfloat16* __restrict__ y) {
+    const int w2 = (w + 1) / 2;
+    const size_t n = (size_t)C * h * w;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int X = (int)(q % w), Y = (int)(q / w);
+        const size_t src = ((size_t)(Y / 2) * w2 + X / 2) * 2 * C;
+        y[q * 2 * out_cp + c0 + c] = x[src + c];
+        y[q * 2 * out_cp + out_cp + c0 + c] = x[src + C + c];
+    }
+}
+
 inline int grid_for(size_t n) {
     const size_t g = (n + 255) / 256;
     return (int)(g < 148 * 16 ? (g > 0 ? g : 1) : 148 * 16);
@@ -126,8 +173,14 @@ struct wskpn_mr {
     wskpn_mr_config cfg{};
     int device = 0;
     float* d_master = nullptr;  // FP32 weight blob
-    float* w32[mr::NL] = {};    // SIMT packing per layer
+    float* w32[mr::NL] = {};    // SIMT packing per layer (FP32)
     float* b32[mr::NL] = {};
+    wskpn::Layer tcL[mr::NL];   // tensor-core layers (BF16)
+    // BF16 activations, hi/lo NHWC: x0 [16], t0 [32], c0 [48 + 32], p1 [32],
+    // t1 [48], c1 [64 + 48], p2 [48], t2 [64], e2 [64]
+    __nv_bfloat16 *bx0 = nullptr, *bt0 = nullptr, *bc0 = nullptr, *bp1 = nullptr, *bt1 = nullptr,
+                  *bc1 = nullptr, *bp2 = nullptr, *bt2 = nullptr, *be2 = nullptr;
+    unsigned int* d_status = nullptr;
     // workspaces, sized for max_h x max_w (levels: l1 = ceil halves, l2 = ceil quarters)
     float* x0 = nullptr;   // [10] level 0
     float* t0 = nullptr;   // [32] E0 / D0 scratch, level 0
@@ -156,6 +209,7 @@ extern "C" void wskpn_mr_config_default(wskpn_mr_config* c) {
     c->gamma = 2.2f;
     c->depth_near = 1.f;
     c->depth_far = 10.f;
+    c->prec = WSKPN_FP32;
 }
 
 extern "C" size_t wskpn_mr_n_weights(void) { return mr::n_weights(); }
@@ -170,7 +224,11 @@ extern "C" void wskpn_mr_destroy(wskpn_mr* m) {
     float* bufs[] = {m->x0, m->t0, m->c0, m->z0, m->p1, m->t1, m->c1, m->z1, m->p2, m->t2, m->e2, m->z2,
                      m->y[0], m->y[1], m->y[2], m->iv[0], m->iv[1], m->iv[2], m->o1};
     for (float* b : bufs) cudaFree(b);
+    __nv_bfloat16* hbufs[] = {m->bx0, m->bt0, m->bc0, m->bp1, m->bt1, m->bc1, m->bp2, m->bt2, m->be2};
+    for (auto* b : hbufs) cudaFree(b);
+    for (auto& L : m->tcL) tc_layer_free(L);
     cudaFree(m->d_fallbacks);
+    cudaFree(m->d_status);
     delete m;
 }
 
@@ -185,7 +243,8 @@ extern "C" wskpn_status wskpn_mr_create(const wskpn_mr_config* cfg_in, const flo
     wskpn_mr_config_default(&cfg);
     if (cfg_in) cfg = *cfg_in;
     if (cfg.max_h < 1 || cfg.max_w < 1 || (long)cfg.max_h * cfg.max_w > (1L << 26) || !(cfg.albedo_eps > 0.f) ||
-        !(cfg.gamma > 0.f) || !(cfg.depth_far > cfg.depth_near)) {
+        !(cfg.gamma > 0.f) || !(cfg.depth_far > cfg.depth_near) ||
+        (cfg.prec != WSKPN_FP32 && cfg.prec != WSKPN_BF16)) {
         set_thread_error("wskpn_mr_create: config out of range");
         return WSKPN_EINVAL;
     }
@@ -200,15 +259,25 @@ extern "C" wskpn_status wskpn_mr_create(const wskpn_mr_config* cfg_in, const flo
     const size_t h1 = (cfg.max_h + 1) / 2, w1 = (cfg.max_w + 1) / 2;
     const size_t P1 = h1 * w1, P2 = ((h1 + 1) / 2) * ((w1 + 1) / 2);
     auto alloc = [&](float** p, size_t floats) { return cudaMalloc(p, floats * sizeof(float)) == cudaSuccess; };
-    bool ok = alloc(&m->d_master, n) && alloc(&m->x0, 10 * P0) && alloc(&m->t0, 32 * P0) &&
-              alloc(&m->c0, 80 * P0) && alloc(&m->z0, 5 * P0) && alloc(&m->p1, 32 * P1) && alloc(&m->t1, 48 * P1) &&
-              alloc(&m->c1, 112 * P1) && alloc(&m->z1, 5 * P1) && alloc(&m->p2, 48 * P2) && alloc(&m->t2, 64 * P2) &&
-              alloc(&m->e2, 64 * P2) && alloc(&m->z2, 4 * P2) && alloc(&m->y[0], 3 * P0) && alloc(&m->y[1], 3 * P1) &&
-              alloc(&m->y[2], 3 * P2) && alloc(&m->iv[0], 3 * P0) && alloc(&m->iv[1], 3 * P1) &&
-              alloc(&m->iv[2], 3 * P2) && alloc(&m->o1, 3 * P1) &&
-              cudaMalloc(&m->d_fallbacks, sizeof(unsigned int)) == cudaSuccess;
+    auto halloc = [&](__nv_bfloat16** p, size_t ch, size_t px) {
+        return cudaMalloc(p, ch * 2 * px * sizeof(__nv_bfloat16)) == cudaSuccess;
+    };
+    const bool bf16 = cfg.prec == WSKPN_BF16;
+    bool ok = alloc(&m->d_master, n) && alloc(&m->z0, 5 * P0) && alloc(&m->z1, 5 * P1) && alloc(&m->z2, 4 * P2) &&
+              alloc(&m->y[0], 3 * P0) && alloc(&m->y[1], 3 * P1) && alloc(&m->y[2], 3 * P2) &&
+              alloc(&m->iv[0], 3 * P0) && alloc(&m->iv[1], 3 * P1) && alloc(&m->iv[2], 3 * P2) &&
+              alloc(&m->o1, 3 * P1) && cudaMalloc(&m->d_fallbacks, sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc(&m->d_status, sizeof(unsigned int)) == cudaSuccess;
+    if (ok && !bf16)
+        ok = alloc(&m->x0, 10 * P0) && alloc(&m->t0, 32 * P0) && alloc(&m->c0, 80 * P0) && alloc(&m->p1, 32 * P1) &&
+             alloc(&m->t1, 48 * P1) && alloc(&m->c1, 112 * P1) && alloc(&m->p2, 48 * P2) && alloc(&m->t2, 64 * P2) &&
+             alloc(&m->e2, 64 * P2);
+    if (ok && bf16)
+        ok = halloc(&m->bx0, 16, P0) && halloc(&m->bt0, 32, P0) && halloc(&m->bc0, 80, P0) &&
+             halloc(&m->bp1, 32, P1) && halloc(&m->bt1, 48, P1) && halloc(&m->bc1, 112, P1) &&
+             halloc(&m->bp2, 48, P2) && halloc(&m->bt2, 64, P2) && halloc(&m->be2, 64, P2);
     size_t off = 0;
-    for (int l = 0; ok && l < mr::NL; ++l) {
+    for (int l = 0; ok && !bf16 && l < mr::NL; ++l) {
         const auto& L = mr::LAYERS[l];
         const int coutp = simt_coutp(L.cout);
         ok = alloc(&m->w32[l], (size_t)L.cin * mr::KS * mr::KS * coutp) && alloc(&m->b32[l], coutp);
@@ -222,13 +291,20 @@ extern "C" wskpn_status wskpn_mr_create(const wskpn_mr_config* cfg_in, const flo
     std::string err;
     wskpn_status s = WSKPN_OK;
     if (cudaMemcpy(m->d_master, host_weights, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(m->d_fallbacks, 0, sizeof(unsigned int)) != cudaSuccess)
+        cudaMemset(m->d_fallbacks, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(m->d_status, 0, sizeof(unsigned int)) != cudaSuccess)
         s = WSKPN_ECUDA;
     for (int l = 0; !s && l < mr::NL; ++l) {
         const auto& L = mr::LAYERS[l];
         const size_t nw = (size_t)L.cout * L.cin * mr::KS * mr::KS;
-        s = launch_pack_simt(m->d_master + off, m->d_master + off + nw, L.cin, L.cout, mr::KS, m->w32[l], m->b32[l],
-                             nullptr, err);
+        if (bf16) {
+            m->tcL[l].cin = L.cin;
+            m->tcL[l].cout = L.cout;
+            s = tc_layer_create(m->tcL[l], mr::KS, m->d_master + off, m->d_master + off + nw, nullptr, err);
+        } else {
+            s = launch_pack_simt(m->d_master + off, m->d_master + off + nw, L.cin, L.cout, mr::KS, m->w32[l],
+                                 m->b32[l], nullptr, err);
+        }
         off += nw + L.cout;
     }
     if (!s && cudaDeviceSynchronize() != cudaSuccess) s = WSKPN_ECUDA;
@@ -247,8 +323,52 @@ wskpn_status mr_conv(wskpn_mr* m, int l, const float* in, float* out, int h, int
     return launch_conv_simt(&in, &out, 1, h, w, L.cin, L.cout, mr::KS, m->w32[l], m->b32[l], L.relu, st, m->err);
 }
 
+wskpn_status mr_tc(wskpn_mr* m, int l, const void* in, void* out, int out_cp, int out_c0, int h, int w,
+                   cudaStream_t st) {
+    const bool head = l == mr::H2 || l == mr::H1 || l == mr::H0;
+    return tc_layer_run(m->tcL[l], mr::KS, in, out, out_cp, out_c0, head, mr::LAYERS[l].relu, 1, h, w, m->d_status,
+                        m->device, st, m->err);
+}
+
+// BF16 U-Net on the tensor cores (hi/lo activations), same outputs as mr_forward.
+wskpn_status mr_forward_bf16(wskpn_mr* m, const wskpn_frame* f, int h, int w, cudaStream_t st) {
+    const int h1 = (h + 1) / 2, w1 = (w + 1) / 2, h2 = (h1 + 1) / 2, w2 = (w1 + 1) / 2;
+    const size_t P0 = (size_t)h * w, P1 = (size_t)h1 * w1, P2 = (size_t)h2 * w2;
+    void* x0 = m->bx0;
+    wskpn_status s = launch_prep(f, 1, h, w, m->cfg.gamma, m->cfg.depth_near, m->cfg.depth_far, &x0, 2, st, m->err);
+    if (!s) s = mr_tc(m, mr::E0, m->bx0, m->bt0, 32, 0, h, w, st);
+    if (!s) s = mr_tc(m, mr::E0B, m->bt0, m->bc0, 80, 48, h, w, st);  // skip into channels 48..79
+    if (!s) {
+        mr::pool_nhwc_kernel<<<mr::grid_for(32 * P1), 256, 0, st>>>(m->bc0, 80, 48, 32, h, w, m->bp1);
+        s = mr_tc(m, mr::E1, m->bp1, m->bt1, 48, 0, h1, w1, st);
+    }
+    if (!s) s = mr_tc(m, mr::E1B, m->bt1, m->bc1, 112, 64, h1, w1, st);  // skip into channels 64..111
+    if (!s) {
+        mr::pool_nhwc_kernel<<<mr::grid_for(48 * P2), 256, 0, st>>>(m->bc1, 112, 64, 48, h1, w1, m->bp2);
+        s = mr_tc(m, mr::E2, m->bp2, m->bt2, 64, 0, h2, w2, st);
+    }
+    if (!s) s = mr_tc(m, mr::E2B, m->bt2, m->be2, 64, 0, h2, w2, st);
+    if (!s) s = mr_tc(m, mr::H2, m->be2, m->z2, 16, 0, h2, w2, st);
+    if (!s) {
+        mr::up_nhwc_kernel<<<mr::grid_for(64 * P1), 256, 0, st>>>(m->be2, 64, h1, w1, 112, 0, m->bc1);
+        s = mr_tc(m, mr::D1, m->bc1, m->bt1, 48, 0, h1, w1, st);
+    }
+    if (!s) s = mr_tc(m, mr::H1, m->bt1, m->z1, 16, 0, h1, w1, st);
+    if (!s) {
+        mr::up_nhwc_kernel<<<mr::grid_for(48 * P0), 256, 0, st>>>(m->bt1, 48, h, w, 80, 0, m->bc0);
+        s = mr_tc(m, mr::D0, m->bc0, m->bt0, 32, 0, h, w, st);
+    }
+    if (!s) s = mr_tc(m, mr::H0, m->bt0, m->z0, 16, 0, h, w, st);
+    if (!s && cudaGetLastError() != cudaSuccess) {
+        m->err = "multires forward: kernel launch failed";
+        s = WSKPN_ECUDA;
+    }
+    return s;
+}
+
 // U-Net outputs for one frame into m->z0 [5][h][w], m->z1 [5][h1][w1], m->z2 [4][h2][w2].
 wskpn_status mr_forward(wskpn_mr* m, const wskpn_frame* f, int h, int w, cudaStream_t st) {
+    if (m->cfg.prec == WSKPN_BF16) return mr_forward_bf16(m, f, h, w, st);
     const int h1 = (h + 1) / 2, w1 = (w + 1) / 2, h2 = (h1 + 1) / 2, w2 = (w1 + 1) / 2;
     const size_t P0 = (size_t)h * w, P1 = (size_t)h1 * w1;
     void* x0 = m->x0;

@@ -12,15 +12,18 @@ def n_weights() -> int:
 
 
 class MultiResDenoiser:
-    """U-Net + 3-level reconstruction with kernels 3 and 5 per level, FP32."""
+    """U-Net + 3-level reconstruction with kernels 3 and 5 per level; the
+    U-Net in FP32 (SIMT) or BF16 (tensor cores, hi/lo activations)."""
 
-    def __init__(self, weights, max_hw=(1080, 1920), albedo_eps=1e-2, gamma=2.2, depth_near=1.0, depth_far=10.0):
+    def __init__(self, weights, max_hw=(1080, 1920), precision="fp32", albedo_eps=1e-2, gamma=2.2, depth_near=1.0,
+                 depth_far=10.0):
         import numpy as np
         self._lib = _lib.load()
         cfg = _lib.MrConfig()
         self._lib.wskpn_mr_config_default(ctypes.byref(cfg))
         cfg.max_h, cfg.max_w = int(max_hw[0]), int(max_hw[1])
         cfg.albedo_eps, cfg.gamma, cfg.depth_near, cfg.depth_far = albedo_eps, gamma, depth_near, depth_far
+        cfg.prec = {"fp32": _lib.FP32, "bf16": _lib.BF16}[precision]
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
         h = ctypes.c_void_p()
         _lib.check(self._lib.wskpn_mr_create(ctypes.byref(cfg), w.ctypes.data, w.size, ctypes.byref(h)))

@@ -62,3 +62,39 @@ def test_multires_256x384_matches_oracle():
     mx, mean, mean_rel = _err(out, f, wb)
     print(f"multires 256x384: max err / term scale {mx:.3e}, mean {mean:.3e}; mean rel {mean_rel:.3e}")
     assert mx < 1e-5 and mean_rel < 1e-5
+
+
+def _setup_bf16(H, W, seed):
+    from paper_2202_05977_b300.multires import MultiResDenoiser
+    f = synth.make_frame(H, W, seed)
+    wb = synth.make_weights_for(omr.weight_shapes(), seed=seed)
+    return f, wb, MultiResDenoiser(wb, max_hw=(H, W), precision="bf16"), args(to_dev(stack_frames([f])))
+
+
+@pytest.mark.parametrize("H,W,seed", [(64, 96, 90), (37, 53, 91), (5, 3, 92)])
+def test_multires_bf16_unet_levels_close_to_oracle(H, W, seed):
+    f, wb, d, a = _setup_bf16(H, W, seed)
+    for l, (z, ref) in enumerate(zip((z.cpu().numpy() for z in d.logits(*a)), omr.logits(f, wb))):
+        assert np.abs(z - ref).max() < 1e-2 * max(1.0, np.abs(ref).max()), l
+
+
+@pytest.mark.parametrize("H,W,seed", [(64, 96, 90), (130, 257, 93), (256, 384, 94)])
+def test_multires_bf16_denoise_close_to_oracle(H, W, seed):
+    f, wb, d, a = _setup_bf16(H, W, seed)
+    out = d.denoise(*a).cpu().numpy()[0]
+    mx, mean, mean_rel = _err(out, f, wb)
+    print(f"multires bf16 {H}x{W}: max err / term scale {mx:.3e}, mean {mean:.3e}; mean rel {mean_rel:.3e}")
+    assert mx < 1e-2 and mean_rel < 1e-3
+
+
+def test_multires_bf16_1080p_agrees_with_fp32_path():
+    from paper_2202_05977_b300.multires import MultiResDenoiser
+    f = synth.make_frame(1080, 1920, 2)
+    wb = synth.make_weights_for(omr.weight_shapes(), seed=2)
+    a = args(to_dev(stack_frames([f])))
+    o16 = MultiResDenoiser(wb, max_hw=(1080, 1920), precision="bf16").denoise(*a).cpu().numpy()[0]
+    o32 = MultiResDenoiser(wb, max_hw=(1080, 1920), precision="fp32").denoise(*a).cpu().numpy()[0]
+    assert np.all(np.isfinite(o16))
+    e = np.abs(o16 - o32) / np.maximum(np.abs(o32), 1e-6)
+    print(f"multires bf16 vs fp32 1080p: median rel {np.median(e):.3e} mean {e.mean():.3e}")
+    assert np.median(e) < 1e-3
