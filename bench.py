@@ -83,6 +83,29 @@ def peaks():
                 "source": "fallback"}
 
 
+# ------------------------------------------------------- replicas (N > 1)
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank denoises its own frame (replicas only: no data is exchanged)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The slowest rank's value (the job ends when it does)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_metrics(ms_per_step_max: float, world: int) -> dict:
+    """Whole-job numbers from the slowest rank's ms per step, with one frame
+    per rank and step: ms per frame of the job and frames per second."""
+    return {"ms_per_step": ms_per_step_max, "ms_per_frame": ms_per_step_max / world,
+            "fps": 1e3 * world / ms_per_step_max}
+
+
 def conv_flops(l, h=H, w=W):
     return 2.0 * WIDTHS[l] * WIDTHS[l + 1] * KS * KS * h * w
 
@@ -304,7 +327,7 @@ def main():
             dist.barrier()
 
     dev = torch.device("cuda", local)
-    f = synth.make_frame(H, W, SEED + 1000 * rank)
+    f = synth.make_frame(H, W, replica_seed(SEED, rank))
     wb = synth.make_weights(WIDTHS, KS, seed=SEED)
     keys = ("radiance", "albedo", "normal", "depth")
     xin = [torch.from_numpy(np.ascontiguousarray(f[k][None])).to(dev) for k in keys]
@@ -339,10 +362,8 @@ def main():
         d.profile(False)
         stage_ms, calls = d.profile_read()
         per = [a.elapsed_time(b) for a, b in ev]
-        total = torch.tensor([sum(per)], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(total, op=dist.ReduceOp.MAX)
-        res = {"ms_step": total.item() / steps, "per": per, "stage_ms": [s / max(calls, 1) for s in stage_ms],
+        total = max_over_ranks(sum(per), dist if world > 1 else None, dev)
+        res = {"ms_step": total / steps, "per": per, "stage_ms": [s / max(calls, 1) for s in stage_ms],
                "wall_s": t_wall, "out": out, "d": d}
         return res
 
@@ -365,7 +386,7 @@ def main():
     sweep = {}
     if not args.no_sweep:
         for (h, w), sd in (((720, 1280), 1), ((1440, 2560), 3)):
-            fr = synth.make_frame(h, w, sd + 1000 * rank)
+            fr = synth.make_frame(h, w, replica_seed(sd, rank))
             xs = [torch.from_numpy(np.ascontiguousarray(fr[k][None])).to(dev) for k in keys]
             r = time_path(args.precision, max(5, args.steps // 2), 3, (h, w), xs)
             sweep[f"{w}x{h}"] = {"ms_per_frame": r["ms_step"], "fps": 1e3 / r["ms_step"],
@@ -379,7 +400,7 @@ def main():
     if not args.no_variants and args.precision != "fp8":
         w6 = (10, 32, 48, 64, 64, 64, 64, 12)
         wb6 = synth.make_weights(w6, KS, seed=SEED)
-        f720 = synth.make_frame(720, 1280, 1 + 1000 * rank)
+        f720 = synth.make_frame(720, 1280, replica_seed(1, rank))
         x720 = [torch.from_numpy(np.ascontiguousarray(f720[k][None])).to(dev) for k in keys]
         six = {}
         for (h, w), xs in (((720, 1280), x720), ((H, W), None)):
@@ -400,7 +421,7 @@ def main():
         wmr = (g.standard_normal(mr_n()) * 0.05).astype(np.float32)
         mres = {}
         for (h, w), sd in (((720, 1280), 1), ((H, W), SEED)):
-            fr = synth.make_frame(h, w, sd + 1000 * rank)
+            fr = synth.make_frame(h, w, replica_seed(sd, rank))
             xs = [torch.from_numpy(np.ascontiguousarray(fr[k][None])).to(dev) for k in keys]
             entry = {}
             for prec in ("bf16", "fp32"):
@@ -464,18 +485,16 @@ def main():
             t0 = time.perf_counter()
             d.denoise_host(*hin, hout)
             ts.append((time.perf_counter() - t0) * 1e3)
-        tt = torch.tensor([statistics.mean(ts)], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": tt.item() / world, "unit": UNIT, "h2d_bytes_per_step": 40 * H * W,
-               "d2h_bytes_per_step": 12 * H * W, "per_rank_ms_per_frame": tt.item()}
+        tt = max_over_ranks(statistics.mean(ts), dist if world > 1 else None, dev)
+        e2e = {"value": job_metrics(tt, world)["ms_per_frame"], "unit": UNIT, "h2d_bytes_per_step": 40 * H * W,
+               "d2h_bytes_per_step": 12 * H * W, "per_rank_ms_per_frame": tt}
 
     if rank == 0:
         L = len(WIDTHS) - 1
         stage_names = ["prep"] + [f"conv{l + 1}" for l in range(L)] + ["reconstruct"]
         line = {
             "metric": METRIC,
-            "value": main_res["ms_step"] / world,
+            "value": job_metrics(main_res["ms_step"], world)["ms_per_frame"],
             "unit": UNIT,
             "n_gpus": world,
             "steps": args.steps,
@@ -487,7 +506,7 @@ def main():
             "dtype": args.precision,
             "data": "synthetic",
             "config": config_block(args.precision),
-            "fps": 1e3 * world / main_res["ms_step"],
+            "fps": job_metrics(main_res["ms_step"], world)["fps"],
             "stages_ms": dict(zip(stage_names, main_res["stage_ms"])),
             "prediction_ms": sum(main_res["stage_ms"][:L + 1]),
             "reconstruction_ms": main_res["stage_ms"][L + 1],
