@@ -443,13 +443,19 @@ wskpn_status wskpn_profile_enable(wskpn_ctx* ctx, int enable);
  * to *calls, then clears the record.  Stages a call did not run add 0. */
 wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stages, int* calls);
 
-/* Tuning knob of the tensor-core convolution (for tests and benchmarks).
+/* Tuning knobs (for tests and benchmarks).
  *   WSKPN_TUNE_TC_SPLIT (BF16 only): 1 = store every BF16 activation as a
  *     hi/lo pair (x = hi + lo, both BF16) and run the K loop over both
  *     halves against the same BF16 weights, which removes the activation
  *     rounding error at twice the MMA work (default); 0 = one BF16 value.
+ *   WSKPN_TUNE_TRAIN_RECOMPUTE (BF16 only): how wskpn_backward recomputes
+ *     the activations: 1 = with the context's own tensor-core convolutions,
+ *     as the forward computed them (default; needs TC_SPLIT = 1); 0 = in
+ *     FP32 with the FP32 weights (the ReLU masks are then those of the FP32
+ *     network, which brings the gradient closer to the FP32/FP64 one).
  * Errors: EINVAL for an unknown key or value. */
 #define WSKPN_TUNE_TC_SPLIT 2
+#define WSKPN_TUNE_TRAIN_RECOMPUTE 3
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
 
 /* Reads and clears the context's device status word after synchronising

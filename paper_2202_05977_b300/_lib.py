@@ -15,6 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EBUSY, ETIMEOUT, ENUMERIC = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EBUSY", "ETIMEOUT", "ENUMERIC"]
 FP32, BF16, FP8 = 0, 1, 2
 TUNE_TC_SPLIT = 2
+TUNE_TRAIN_RECOMPUTE = 3
 
 
 class Config(ctypes.Structure):

@@ -919,6 +919,56 @@ wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, 
     return WSKPN_OK;
 }
 
+// BF16 hi/lo NHWC [B][HW][hi(cp) | lo(cp)] -> planar FP32 out[b] [C][HW], x = hi + lo.
+__global__ void hilo_to_planar_kernel(const __nv_bfloat16* __restrict__ in, int cp, int C, size_t HW, int B,
+                                      PtrBatch<float*> out) {
+    const size_t n = (size_t)B * C * HW;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = i % HW;
+        const int c = (int)((i / HW) % C), b = (int)(i / (HW * C));
+        const __nv_bfloat16* px = in + ((size_t)b * HW + p) * 2 * cp;
+        out.p[b][(size_t)c * HW + p] = __bfloat162float(px[c]) + __bfloat162float(px[cp + c]);
+    }
+}
+
+// The activations x_1 .. x_{L-1} of a BF16 context recomputed on the tensor
+// cores exactly as its forward computes them (hi/lo activations), returned
+// as planar FP32 acts[l - 1][b] [C_l][H][W] for the gradient kernels.
+wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
+                               const std::vector<std::vector<float*>>& acts, cudaStream_t st) {
+    const wskpn_config& c = ctx->cfg;
+    if (c.prec != WSKPN_BF16 || B > WSKPN_MAX_BATCH) {
+        ctx->err = "tc_recompute_acts: BF16 contexts only, at most 16 frames";
+        return WSKPN_EUNSUPPORTED;
+    }
+    const size_t HW = (size_t)H * W;
+    uint8_t* A = static_cast<uint8_t*>(ctx->d_tcA);
+    uint8_t* Bf = static_cast<uint8_t*>(ctx->d_tcB);
+    const int split = ctx->tc_split;
+    std::vector<void*> x0(B);
+    const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * (split ? 2 : 1) * HW;
+    for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * x0_bytes;
+    wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), split ? 2 : 1, st,
+                                 ctx->err);
+    for (int l = 0; !s && l + 1 < c.n_layers; ++l) {
+        const void* in = l % 2 == 0 ? (const void*)A : (const void*)Bf;
+        void* out = (l + 1) % 2 == 0 ? (void*)A : (void*)Bf;
+        s = conv_tc(ctx, l, in, out, B, H, W, st);
+        if (s) break;
+        if (!split) {
+            ctx->err = "tc_recompute_acts: needs hi/lo activations";
+            return WSKPN_EUNSUPPORTED;
+        }
+        PtrBatch<float*> o{};
+        for (int b = 0; b < B; ++b) o.p[b] = acts[l][b];
+        const Layer& L = ctx->layers[l];
+        hilo_to_planar_kernel<<<148 * 8, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(out), L.cout_p, L.cout, HW,
+                                                       B, o);
+        WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
+    }
+    return s;
+}
+
 // max over n non-negative floats (ReLU outputs, [0,1] inputs) by their bit patterns
 __global__ void amax_nonneg_kernel(const float* __restrict__ x, size_t n, unsigned int* __restrict__ out) {
     unsigned int m = 0;

@@ -52,6 +52,7 @@ struct wskpn_ctx {
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
     bool fp8_calibrated = false;
     int tc_split = 1;  // BF16 activations as hi/lo pairs (WSKPN_TUNE_TC_SPLIT)
+    int train_tc_recompute = 1;  // backward recomputes on the tensor cores (WSKPN_TUNE_TRAIN_RECOMPUTE)
     void* train = nullptr;  // training workspaces (train.cu), allocated by the first training call
     // stage profiling: one event set (n_layers + 3 events) per recorded call
     bool prof = false;
@@ -78,6 +79,8 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st);
 wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                        cudaStream_t st);
 wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, std::string& err);
+wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
+                               const std::vector<std::vector<float*>>& acts, cudaStream_t st);
 // BF16 tensor-core layers outside a context (hi/lo activations in and out)
 wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, cudaStream_t st, std::string& err);
 void tc_layer_free(Layer& L);

@@ -260,7 +260,8 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
                                    c.ksizes, c.albedo_eps, ctx->d_fallbacks, st, ctx->err);
         if (s) return s;
     }
-    // 2. recompute x_0 .. x_{L-1} (FP32)
+    // 2. recompute x_0 .. x_{L-1}: with the context's own convolutions for BF16
+    //    (tensor cores, hi/lo activations, as the forward), else FP32
     auto act = [&](int l, int b) { return t->acts + t->act_off[l] + (size_t)b * c.widths[l] * HW; };
     {
         std::vector<void*> x0(batch);
@@ -269,7 +270,16 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         if (s) return s;
         std::vector<const float*> in(batch);
         std::vector<float*> o(batch);
-        for (int l = 1; l < L; ++l) {
+        const bool on_tc = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute &&
+                           batch <= WSKPN_MAX_BATCH;
+        if (on_tc) {
+            std::vector<std::vector<float*>> acts(L > 1 ? L - 1 : 0, std::vector<float*>(batch));
+            for (int l = 1; l < L; ++l)
+                for (int b = 0; b < batch; ++b) acts[l - 1][b] = act(l, b);
+            s = tc_recompute_acts(ctx, frames, batch, h, w, acts, st);
+            if (s) return s;
+        }
+        for (int l = 1; l < L && !on_tc; ++l) {
             for (int b = 0; b < batch; ++b) {
                 in[b] = act(l - 1, b);
                 o[b] = act(l, b);

@@ -76,11 +76,15 @@ def test_decode_fuse_bwd_wide_range_takes_exact_path(torch, wk):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_training_backward_matches_oracle(torch, wk, prec):
-    """dL/dTheta for a random cotangent dL/dout, B = 2 frames of 24 x 40."""
+    """dL/dTheta for a random cotangent dL/dout, B = 2 frames of 24 x 40
+    (BF16: activations recomputed in FP32, TUNE_TRAIN_RECOMPUTE = 0)."""
     B, H, W = 2, 24, 40
     frames = [synth.make_frame(H, W, 300 + b) for b in range(B)]
     wb = synth.make_weights(seed=9)
     d = wk.Denoiser(wb, precision=prec, max_batch=B, max_hw=(H, W))
+    if prec == "bf16":
+        from paper_2202_05977_b300 import _lib
+        d.set_tuning(_lib.TUNE_TRAIN_RECOMPUTE, 0)
     dev = to_dev(stack_frames(frames))
     out, z = d.forward_train(*args(dev))
     G = np.random.default_rng(9).standard_normal((B, 3, H, W)).astype(np.float32)
@@ -98,6 +102,38 @@ def test_training_backward_matches_oracle(torch, wk, prec):
         assert _close(dw[off:off + n], ref[off:off + n], tol), (ws, off)
         off += n
     assert np.isfinite(dz.cpu().numpy()).all()
+
+
+def test_training_backward_bf16_tensor_core_recompute(torch, wk):
+    """BF16 convolutions with recomputed activations (the default): the
+    activations come from the BF16-weight network, so a few ReLU masks
+    differ from the FP64 network's; the gradient keeps its direction
+    (cosine > 0.99 per layer) and stays within 15 % in L2 (measured 6-10 %
+    for the first three layers, 0.4-0.7 % for the last)."""
+    B, H, W = 2, 64, 96
+    frames = [synth.make_frame(H, W, 310 + b) for b in range(B)]
+    wb = synth.make_weights(seed=10)
+    d = wk.Denoiser(wb, precision="bf16", max_batch=B, max_hw=(H, W))
+    dev = to_dev(stack_frames(frames))
+    out, z = d.forward_train(*args(dev))
+    G = np.random.default_rng(10).standard_normal((B, 3, H, W)).astype(np.float32)
+    dw, _ = d.backward(*args(dev), z, torch.from_numpy(G).cuda())
+    ref = np.zeros(wb.size)
+    for b in range(B):
+        o, acts = oracle.forward_train(frames[b], wb)
+        gb, _ = oracle.backward_train(frames[b], wb, acts, G[b])
+        ref += gb
+    dw = dw.cpu().numpy().astype(np.float64)
+    off = 0
+    for (ws, bs) in synth.weight_shapes():
+        n = int(np.prod(ws)) + bs[0]
+        a, r = dw[off:off + n], ref[off:off + n]
+        rel = np.linalg.norm(a - r) / np.linalg.norm(r)
+        cos = a @ r / np.linalg.norm(a) / np.linalg.norm(r)
+        print(f"bf16 tc recompute {ws}: L2 rel {rel:.3e} cos {cos:.6f}")
+        assert rel < 0.15 and cos > 0.99, ws
+        off += n
+    assert d.device_status() == 0
 
 
 def test_l1_loss_and_gradient(torch, wk):
