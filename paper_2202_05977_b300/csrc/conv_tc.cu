@@ -182,11 +182,15 @@ __host__ __device__ constexpr uint32_t tc_row_bytes(int KS, int ncc_in) {
 __host__ __device__ constexpr size_t tc_fixed_bytes(int KS, int cout_g, int ncc_w) {
     return 1024 + ((size_t)KS * KS * ncc_w * cout_g * 32 + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
 }
-// Input rows per pipeline stage: two when two such stages fit (halves the
-// barrier waits and commits per MMA; measured 12-13% faster on the layers
-// with at most 48 output channels), else one.
+// Input rows per pipeline stage: the most of 4, 3, 2 for which two such
+// stages fit (one barrier wait and one commit per stage instead of per row:
+// conv1 0.158 -> 0.130, conv2 0.269 -> 0.232, conv4 0.381 -> 0.341 ms at
+// 1080p), else one.
 __host__ __device__ constexpr int tc_rows_per_item(int KS, int cout_g, int ncc_in, int ncc_w) {
-    return tc_fixed_bytes(KS, cout_g, ncc_w) + 4 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 2 : 1;
+    return tc_fixed_bytes(KS, cout_g, ncc_w) + 8 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448   ? 4
+           : tc_fixed_bytes(KS, cout_g, ncc_w) + 6 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 3
+           : tc_fixed_bytes(KS, cout_g, ncc_w) + 4 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 2
+                                                                                                  : 1;
 }
 // The accumulate flag is a compile-time constant: a predicate computed at
 // run time costs about twice the issue time of the MMA itself.
