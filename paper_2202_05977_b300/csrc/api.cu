@@ -1,6 +1,7 @@
 // C ABI of libwskpn: context lifetime, weight packing, workspaces and the
 // per-frame denoise pipeline (Sec. 5.1 prep -> Sec. 4.1 convs -> Eq. 3-5
 // reconstruction), all enqueued on the caller's stream.
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -294,6 +295,92 @@ wskpn_status wskpn_denoise(wskpn_ctx* ctx, const wskpn_frame* frames, int batch,
     return s;
 }
 
+// Banded host call.  Output rows [y0, y1) of a frame depend only on input
+// rows within the receptive field: conv_ks / 2 per layer plus the largest
+// window's half, so each band is denoised as a sub-image of its rows plus
+// that halo (recomputed per band) and only its central rows are kept.  Band
+// j + 1's upload (one copy stream) and band j - 1's download (another)
+// overlap band j's compute on the caller's stream.
+static int band_halo(const wskpn_config& c) {
+    int kmax = 1;
+    for (int i = 0; i < c.n_kernels; ++i) kmax = std::max(kmax, c.ksizes[i]);
+    return c.n_layers * (c.conv_ks / 2) + kmax / 2;
+}
+
+static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, int batch, int h, int w,
+                                        float* host_out, int nb, cudaStream_t st) {
+    const int halo = band_halo(ctx->cfg);
+    const int bh = (h + nb - 1) / nb;
+    const int ext = std::min(h, bh + 2 * halo);  // rows of an extended band
+    const size_t need = (size_t)13 * ext * w;
+    if (!ctx->up_stream) {
+        WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking), ctx->err);
+        WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking), ctx->err);
+        ctx->band_events.resize(6);
+        for (auto& e : ctx->band_events)
+            WSKPN_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), ctx->err);
+    }
+    if (ctx->band_floats < need) {
+        cudaFree(ctx->d_band[0]);
+        cudaFree(ctx->d_band[1]);
+        ctx->d_band[0] = ctx->d_band[1] = nullptr;
+        ctx->band_floats = 0;
+        WSKPN_CUDA_TRY(cudaMalloc(&ctx->d_band[0], need * sizeof(float)), ctx->err);
+        WSKPN_CUDA_TRY(cudaMalloc(&ctx->d_band[1], need * sizeof(float)), ctx->err);
+        ctx->band_floats = need;
+    }
+    // events per slot: [0..1] uploaded, [2..3] computed, [4..5] downloaded
+    cudaEvent_t* ev = ctx->band_events.data();
+    const int ch[4] = {3, 3, 3, 1};
+    const size_t HW = (size_t)h * w;
+    int job = 0;
+    for (int b = 0; b < batch; ++b) {
+        const float* src[4] = {hf[b].radiance, hf[b].albedo, hf[b].normal, hf[b].depth};
+        for (int k = 0; k < nb; ++k, ++job) {
+            const int slot = job & 1;
+            const int y0 = k * bh, y1 = std::min(h, y0 + bh);
+            if (y0 >= y1) break;
+            const int e0 = std::max(0, y0 - halo), e1 = std::min(h, y1 + halo), eh = e1 - e0;
+            const size_t ePX = (size_t)eh * w;
+            float* base = ctx->d_band[slot];
+            // the slot's previous band must be computed before its inputs are replaced
+            if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, ev[2 + slot], 0), ctx->err);
+            wskpn_frame f{};
+            const float** dst[4] = {&f.radiance, &f.albedo, &f.normal, &f.depth};
+            float* p = base;
+            for (int q = 0; q < 4; ++q) {
+                *dst[q] = p;
+                for (int c = 0; c < ch[q]; ++c) {
+                    WSKPN_CUDA_TRY(cudaMemcpyAsync(p, src[q] + c * HW + (size_t)e0 * w, ePX * sizeof(float),
+                                                   cudaMemcpyHostToDevice, ctx->up_stream),
+                                   ctx->err);
+                    p += ePX;
+                }
+            }
+            float* dout = p;
+            WSKPN_CUDA_TRY(cudaEventRecord(ev[slot], ctx->up_stream), ctx->err);
+            // compute after the upload, and after the slot's previous download
+            WSKPN_CUDA_TRY(cudaStreamWaitEvent(st, ev[slot], 0), ctx->err);
+            if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(st, ev[4 + slot], 0), ctx->err);
+            wskpn_status s = wskpn_denoise(ctx, &f, 1, eh, w, dout, st);
+            if (s) return s;
+            WSKPN_CUDA_TRY(cudaEventRecord(ev[2 + slot], st), ctx->err);
+            // download the central rows
+            WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->down_stream, ev[2 + slot], 0), ctx->err);
+            for (int c = 0; c < 3; ++c)
+                WSKPN_CUDA_TRY(cudaMemcpyAsync(host_out + ((size_t)b * 3 + c) * HW + (size_t)y0 * w,
+                                               dout + c * ePX + (size_t)(y0 - e0) * w,
+                                               (size_t)(y1 - y0) * w * sizeof(float), cudaMemcpyDeviceToHost,
+                                               ctx->down_stream),
+                               ctx->err);
+            WSKPN_CUDA_TRY(cudaEventRecord(ev[4 + slot], ctx->down_stream), ctx->err);
+        }
+    }
+    WSKPN_CUDA_TRY(cudaStreamSynchronize(ctx->down_stream), ctx->err);
+    WSKPN_CUDA_TRY(cudaStreamSynchronize(st), ctx->err);
+    return WSKPN_OK;
+}
+
 wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h, int w,
                                 float* host_out, void* stream) {
     if (!ctx) return WSKPN_EINVAL;
@@ -303,6 +390,11 @@ wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, 
         ctx->err = "host_out is NULL";
         return WSKPN_EINVAL;
     }
+    // Frames of at least 480 rows go through the banded pipeline (one band
+    // per ~240 rows, at most 8): the recomputed halos cost less than the
+    // copies they let overlap.  Smaller frames: one upload, denoise, download.
+    const int nb = std::min(8, h / 240);
+    if (nb >= 2) return denoise_host_banded(ctx, host_frames, batch, h, w, host_out, nb, (cudaStream_t)stream);
     if (!ctx->d_stage) {
         cudaError_t e = cudaMalloc((void**)&ctx->d_stage, ctx->ws_pixels * 13 * sizeof(float));
         if (e != cudaSuccess) {

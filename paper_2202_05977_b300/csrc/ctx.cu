@@ -93,6 +93,11 @@ void ctx_free(wskpn_ctx* ctx) {
     cudaFree(ctx->d_tcB);
     cudaFree(ctx->d_z);
     cudaFree(ctx->d_stage);
+    cudaFree(ctx->d_band[0]);
+    cudaFree(ctx->d_band[1]);
+    for (cudaEvent_t e : ctx->band_events) cudaEventDestroy(e);
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+    if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
     cudaFree(ctx->d_fallbacks);
     for (auto& set : ctx->prof_sets)
         for (auto e : set) cudaEventDestroy(e);

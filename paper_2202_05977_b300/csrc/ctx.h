@@ -47,6 +47,12 @@ struct wskpn_ctx {
     void* d_tcB = nullptr;      // tensor-core NHWC pong buffer
     float* d_z = nullptr;       // network output [B][2M][H][W]
     float* d_stage = nullptr;   // host-call staging: 10 input + 3 output planes per pixel
+    // banded host calls: two copy streams (upload, download) and the staging
+    // of two bands in flight
+    cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    float* d_band[2] = {nullptr, nullptr};  // [10 + 3][band_rows][max_w]
+    size_t band_floats = 0;
+    std::vector<cudaEvent_t> band_events;   // 4 per band slot ring (uploaded, computed, downloaded)
     unsigned int* d_fallbacks = nullptr;
     unsigned int* d_status = nullptr;  // device status word of the tensor-core kernels
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
