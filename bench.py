@@ -86,6 +86,24 @@ def peaks():
                 "source": "fallback"}
 
 
+def host_upload_bytes(h: int, w: int, n_layers: int = len(WIDTHS) - 1, ks: int = KS,
+                      kmax: int = max(KSIZES)) -> int:
+    """Bytes wskpn_denoise_host uploads for one frame: frames of 480+ rows go
+    in bands of ceil(h / nb) rows (nb = min(8, h // 240)), each with a halo
+    of n_layers * ks // 2 + kmax // 2 rows, so the halo rows travel twice."""
+    nb = min(8, h // 240)
+    if nb < 2:
+        return 40 * h * w
+    halo = n_layers * (ks // 2) + kmax // 2
+    bh = -(-h // nb)
+    rows = 0
+    for k in range(nb):
+        y0, y1 = k * bh, min(h, (k + 1) * bh)
+        if y0 < y1:
+            rows += min(h, y1 + halo) - max(0, y0 - halo)
+    return 40 * rows * w
+
+
 # ------------------------------------------------------- replicas (N > 1)
 def replica_seed(seed: int, rank: int) -> int:
     """Each rank denoises its own frame (replicas only: no data is exchanged)."""
@@ -489,7 +507,8 @@ def main():
             d.denoise_host(*hin, hout)
             ts.append((time.perf_counter() - t0) * 1e3)
         tt = max_over_ranks(statistics.mean(ts), dist if world > 1 else None, dev)
-        e2e = {"value": job_metrics(tt, world)["ms_per_frame"], "unit": UNIT, "h2d_bytes_per_step": 40 * H * W,
+        e2e = {"value": job_metrics(tt, world)["ms_per_frame"], "unit": UNIT,
+               "h2d_bytes_per_step": host_upload_bytes(H, W),
                "d2h_bytes_per_step": 12 * H * W, "per_rank_ms_per_frame": tt}
 
     if rank == 0:
