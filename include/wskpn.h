@@ -48,7 +48,7 @@ typedef enum {
     WSKPN_EINVAL = 1,       /* bad argument (null pointer, size, config) */
     WSKPN_ENOMEM = 2,       /* device or host allocation failed */
     WSKPN_ECUDA = 3,        /* a CUDA runtime/driver call failed */
-    WSKPN_EUNSUPPORTED = 4, /* valid request this build cannot run */
+    WSKPN_EUNSUPPORTED = 4, /* valid request the library has no kernel for */
     WSKPN_EBUSY = 5,        /* serving: admission refused, queue full */
     WSKPN_ETIMEOUT = 6,     /* a bounded wait ran out */
     WSKPN_ENUMERIC = 7      /* non-finite values detected */

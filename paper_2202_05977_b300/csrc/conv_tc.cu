@@ -563,7 +563,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string& err) {
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !p) {
-            err = "cuTensorMapEncodeTiled is not available from the driver";
+            err = "cuTensorMapEncodeTiled is not available from the CUDA driver";
             return nullptr;
         }
         fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
