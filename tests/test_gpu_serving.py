@@ -150,3 +150,30 @@ def test_temporal_streams_equal_sequential_library_calls(torch):
             acc = ta.step(f["radiance"], f["position"], f["normal"], f["motion"])
             ref = d.denoise(acc[None], f["albedo"][None], f["normal"][None], f["depth"][None])
             assert torch.equal(outs[(s, t)], ref), (s, t)
+
+
+def test_temporal_stream_restarts_when_its_size_changes(torch):
+    # a stream whose frames change size gets a fresh history at the new size
+    import paper_2202_05977_b300 as wk
+    from paper_2202_05977_b300.serving import Server
+    from paper_2202_05977_b300.temporal import TemporalAccumulator
+    wb = synth.make_weights(seed=14)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    small = synth.make_sequence(40, 56, 2, seed=31)
+    large = synth.make_sequence(48, 64, 2, seed=32)
+    seq = [{k: dev(f[k]) for k in ("radiance", "albedo", "normal", "depth", "position", "motion")}
+           for f in small + large]
+    srv = Server(wb, "bf16", max_hw=(48, 64), n_workers=2, max_batch=2)
+    outs = []
+    for f in seq:
+        o = torch.empty((1, 3, *f["radiance"].shape[1:]), device="cuda")
+        t = srv.submit_temporal(5, f["radiance"], f["albedo"], f["normal"], f["depth"], f["position"], f["motion"], o)
+        assert srv.wait(t, 20000) == OK
+        outs.append(o)
+    srv.stop()
+    for part, frames in ((outs[:2], seq[:2]), (outs[2:], seq[2:])):
+        h, w = frames[0]["radiance"].shape[1:]
+        ta, d = TemporalAccumulator(h, w), wk.Denoiser(wb, "bf16", max_hw=(h, w))
+        for o, f in zip(part, frames):
+            acc = ta.step(f["radiance"], f["position"], f["normal"], f["motion"])
+            assert torch.equal(o, d.denoise(acc[None], f["albedo"][None], f["normal"][None], f["depth"][None]))
