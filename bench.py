@@ -544,6 +544,10 @@ def main():
             line["resolutions"] = sweep
         if variants:
             line["variants"] = variants
+        # the paper's own timings (1280x720, RTX 2080 Ti, precision not stated):
+        # context only, another machine and resolution
+        line["paper_context"] = {"hardware": "RTX 2080 Ti", "resolution": "1280x720",
+                                 "ms_per_frame": {"3_blocks": 6.58, "6_blocks": 12.89, "multires": 22.70}}
         if fp32 is not None:
             line["fp32_ms_per_frame"] = fp32["ms_step"] / world
             line["speedup_vs_fp32"] = fp32["ms_step"] / main_res["ms_step"]
