@@ -533,6 +533,8 @@ def main():
             "prediction_ms": sum(main_res["stage_ms"][:L + 1]),
             "reconstruction_ms": main_res["stage_ms"][L + 1],
             "p50_step_ms": statistics.median(main_res["per"]),
+            "p99_step_ms": sorted(main_res["per"])[min(len(main_res["per"]) - 1,
+                                                      int(round(0.99 * (len(main_res["per"]) - 1))))],
             "roofline": roof,
             "stage_rooflines": stage_rooflines(main_res["stage_ms"], args.precision, pk),
             "gpu_launches": args.steps * (L + 2),
