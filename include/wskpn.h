@@ -142,9 +142,16 @@ wskpn_status wskpn_denoise(wskpn_ctx* ctx, const wskpn_frame* frames, int batch,
 /* wskpn_denoise from HOST buffers, synchronous: copies each frame's inputs
  * (host float32 planar, pinned memory recommended) into context-owned
  * device staging buffers, denoises, copies the result to host_out
- * ([batch][3][h][w] float32) and waits for `stream` before returning.  The
- * staging buffers (52 bytes per pixel of max_batch x max_h x max_w) are
- * allocated by the first call.  Errors as wskpn_denoise, plus ENOMEM. */
+ * ([batch][3][h][w] float32) and waits before returning.  Frames of 480
+ * rows or more are processed as horizontal bands of about 240 rows, each
+ * with the receptive-field halo (conv_ks / 2 rows per layer plus the largest
+ * window's half) recomputed, on `stream`, while two context-owned copy
+ * streams upload the next band and download the previous one; the result
+ * equals wskpn_denoise up to the reconstruction's per-tile exponent shift
+ * (float32 rounding).  Staging (52 bytes per pixel of max_batch x max_h x
+ * max_w for unbanded calls, 13 floats per pixel of two extended bands for
+ * banded ones) is allocated on first use.  Errors as wskpn_denoise, plus
+ * ENOMEM. */
 wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h,
                                 int w, float* host_out, void* stream);
 
