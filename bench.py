@@ -466,6 +466,35 @@ def main():
             entry["fps_bf16"] = 1e3 / entry["bf16_ms_per_frame"]
             mres[f"{w}x{h}"] = entry
         variants["multires_unet"] = mres
+        # temporal accumulation (Sec. 4.3) on a 1080p moving-camera pair: one
+        # step reads the frame (radiance, position, normal, motion: 44 B/px)
+        # and the previous state (40 B/px) and writes the state and the
+        # accumulated radiance (52 B/px)
+        from paper_2202_05977_b300.temporal import TemporalAccumulator
+        seq = synth.make_sequence(H, W, 2, seed=replica_seed(SEED, rank))
+        tin = [{k: torch.from_numpy(np.ascontiguousarray(f[k])).to(dev)
+                for k in ("radiance", "position", "normal", "motion")} for f in seq]
+        ta = TemporalAccumulator(H, W)
+        acc = torch.empty((3, H, W), device=dev)
+        for f in tin:
+            ta.step(f["radiance"], f["position"], f["normal"], f["motion"], out=acc)
+        torch.cuda.synchronize()
+        n_it = max(10, args.steps)
+        tot = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(n_it):
+            flush.fill_(float(i))
+            f = tin[1]
+            e0.record()
+            ta.step(f["radiance"], f["position"], f["normal"], f["motion"], out=acc)
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / n_it
+        variants["temporal_accumulation"] = {"resolution": f"{W}x{H}", "ms_per_frame": ms,
+                                             "achieved_gbs": 136 * H * W / (ms * 1e-3) / 1e9,
+                                             "frac_hbm": 136 * H * W / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+        ta.close()
 
     # roofline of the dominant stage (stage 0 prep, 1..L convs, L+1 reconstruction)
     st = main_res["stage_ms"]
