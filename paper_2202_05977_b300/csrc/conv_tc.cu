@@ -19,10 +19,13 @@
 // then runs over both halves against the same weight chunk, which removes
 // the activation rounding error at twice the MMA work.
 //
-// Issue path: one pipeline item is one input row with all its channel
-// chunks; the MMAs of an item are a compile-time unrolled, branch-free
-// sequence followed by one commit (a branch or commit between MMAs roughly
-// doubles their issue time on this part).
+// Issue path: one pipeline stage holds up to four input rows with all
+// their channel chunks (as many as let two stages fit next to the weights);
+// the MMAs of a row are a compile-time unrolled, branch-free sequence, and
+// a stage ends with one commit (a branch or commit between MMAs roughly
+// doubles their issue time on this part, and every stage costs the MMA
+// thread a barrier wait).  Layers whose weight image leaves no room for two
+// stages run as output-channel groups, each a pass over the input.
 //
 // Roles: warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs (one
 // thread), warps 2-5 drain TMEM (bias, ReLU, requantise) and store NHWC
