@@ -11,6 +11,11 @@
 // device; requests arriving meanwhile are admitted as workers and budget
 // free up (continuous batching).  Completions are polled with events and
 // delivered in submission order per stream; latency is submit -> delivery.
+// Temporal requests (Sec. 4.3) carry world position and motion; the server
+// keeps each stream's accumulation history on the device, runs one frame of
+// a temporal stream at a time in submission order, and writes the
+// accumulated radiance straight into the batch's radiance slot before the
+// denoise.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
