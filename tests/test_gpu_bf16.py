@@ -111,3 +111,29 @@ def test_bf16_batch_invariance(wk):
     for b in range(3):
         one = d.denoise(*(dev[k][b:b + 1].contiguous() for k in ("radiance", "albedo", "normal", "depth")))
         np.testing.assert_array_equal(one.cpu().numpy()[0], both[b])
+
+
+def test_bf16_denoises_1080p_faster_than_fp32(wk):
+    """The precision form's speed target: at 1920x1080 the BF16 tensor-core
+    path is faster than the FP32 plain path (measured ~10x; asserted 3x)."""
+    import torch
+    H, W = 1080, 1920
+    dev = to_dev(stack_frames([synth.make_frame(H, W, 2)]))
+    wb = synth.make_weights(seed=2)
+
+    def ms(prec):
+        d = wk.Denoiser(wb, precision=prec, max_hw=(H, W))
+        out = torch.empty((1, 3, H, W), device="cuda")
+        for _ in range(2):
+            d.denoise(*args(dev), out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            d.denoise(*args(dev), out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 3
+
+    t16, t32 = ms("bf16"), ms("fp32")
+    print(f"1080p: bf16 {t16:.3f} ms, fp32 {t32:.3f} ms")
+    assert t16 * 3 < t32
