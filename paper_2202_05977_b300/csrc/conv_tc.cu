@@ -5,8 +5,8 @@
 // GEMM view of one tile: M = 128 consecutive pixels of an image row (TMEM
 // lanes), N = padded output channels, K = KS*KS taps x input channels,
 // consumed 32 bytes (16 BF16 or 32 e4m3 channels) per MMA.  A CTA owns
-// R output rows x 128 pixels (R = 8, 5, 4 for at most 32, 48, 64 output
-// channels) and keeps R accumulators (one per output row) in TMEM,
+// R output rows x 128 pixels (R = 16, 8, 5, 4 for at most 16, 32, 48, 64
+// output channels) and keeps R accumulators (one per output row) in TMEM,
 // double-buffered across tiles so the epilogue of one tile
 // overlaps the MMAs of the next.  Each input row is fetched once per tile
 // (one TMA box of 128 + KS - 1 pixels per 32-byte channel chunk) and
@@ -50,13 +50,11 @@ namespace wskpn {
 namespace tc {
 constexpr int BM = 128;            // pixels per tile row = MMA M = TMEM lanes
 // Output rows per tile: as many as two buffers of R row accumulators allow
-// in TMEM (2 R COUT_P <= 512 columns), at most 8.  More rows per tile means
+// in TMEM (2 R COUT_P <= 512 columns), at most 16.  More rows per tile means
 // fewer MMAs per output row, since an input row's MMA serves up to
-// min(R, KS) output rows, and fewer re-fetched halo rows.  Beyond 8 rows the
-// unrolled MMA sequences of all input rows outgrow the instruction cache
-// (16 rows for 16 channels measured 0.58 ms against 0.39 ms with 8).
+// min(R, KS) output rows, and fewer re-fetched halo rows.
 __host__ __device__ constexpr int rows_per_tile(int cout_p) {
-    return cout_p <= 32 ? 8 : cout_p <= 48 ? 5 : 4;
+    return cout_p <= 16 ? 16 : cout_p <= 32 ? 8 : cout_p <= 48 ? 5 : 4;
 }
 constexpr int THREADS = 192;
 constexpr int ROWB = 32;           // bytes of one pixel row of one K chunk
@@ -244,55 +242,41 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
            : 2 * R * COUT_P <= 256 ? 256 : 512;
 }
 
-// All MMAs of input row RI of a tile.  Input row RI feeds output rows
-// ro = RI - dy for the vertical taps dy in [DY0, DY1] (those with
+// All MMAs of input row ri of a tile.  Input row ri feeds output rows
+// ro = ri - dy for the vertical taps dy in [dy0, dy1] (those with
 // 0 <= ro < R).  For each channel chunk and horizontal tap dx, ONE MMA
 // covers all of them: the weight image stores the KS vertical taps of a
 // (dx, chunk) pair as consecutive N blocks, and the accumulators of the R
 // output rows sit in TMEM in descending row order (row ro at column block
-// R - 1 - ro), so N = (DY1 - DY0 + 1) x COUT_P columns are contiguous.
-// Accumulators are zeroed by the epilogue, so every MMA accumulates.
-// Fully unrolled, no branches.
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int RI>
-__device__ __forceinline__ void issue_row(uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
-    constexpr int DY0 = RI - (R - 1) > 0 ? RI - (R - 1) : 0;
-    constexpr int DY1 = RI < KS - 1 ? RI : KS - 1;
-    constexpr int NB = DY1 - DY0 + 1;  // output rows fed by this input row
-    if constexpr (NB <= 0) {
-        return;  // row beyond R + KS - 1 (instantiated by the switch below, never reached)
-    } else {
-    constexpr int N = NB * COUT_P;
-    static_assert(N % 16 == 0 && N <= 256, "MMA N");
-    constexpr uint32_t IDESC = (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(N >> 3) << 17) |
-                               ((uint32_t)(tc::BM >> 4) << 24);
+// R - 1 - ro), so N = (dy1 - dy0 + 1) x COUT_P columns are contiguous.
+// Accumulators are zeroed by the epilogue, so every MMA accumulates.  The
+// row's tap range (hence N, the accumulator column and the weight offset)
+// is computed at run time; the NCC_IN x KS MMAs themselves are an unrolled,
+// branch-free sequence, so one body serves every row of any tile height.
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R>
+__device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
+    static_assert(COUT_P % 16 == 0 && COUT_P * (R < KS ? R : KS) <= 256, "MMA N");
+    const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
+    const int dy1 = ri < KS - 1 ? ri : KS - 1;
+    const int nb = dy1 - dy0 + 1;  // output rows fed by this input row
+    if (nb <= 0) return;           // rows past R + KS - 1 loaded to fill a stage
+    constexpr uint32_t IDESC0 = (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(tc::BM >> 4) << 24);
+    const uint32_t idesc = IDESC0 | ((uint32_t)((nb * COUT_P) >> 3) << 17);
     constexpr uint32_t b_blk = (COUT_P * tc::ROWB) >> 4;  // one (dx, chunk, dy) block, 16-byte units
     constexpr int CPB = chunks_per_box(NCC_IN);
     constexpr uint32_t a_dx = (CPB * tc::ROWB) >> 4;       // one pixel row of a box
-    const uint32_t d = dbase + (uint32_t)((R - 1 - (RI - DY0)) * COUT_P);
+    const uint32_t d = dbase + (uint32_t)((R - 1 - (ri - dy0)) * COUT_P);
+    const uint64_t b0 = bd + (uint64_t)(dy0 * b_blk);
 #pragma unroll
     for (int cc = 0; cc < NCC_IN; ++cc) {
         const int ccw = cc % NCC_W;  // the lo half of a split activation reuses the weights
 #pragma unroll
         for (int dx = 0; dx < KS; ++dx) {
             const uint64_t a = ad + (uint64_t)((cc / CPB) * box_step + (cc % CPB) * (tc::ROWB >> 4) + dx * a_dx);
-            const uint64_t b = bd + (uint64_t)(((dx * NCC_W + ccw) * KS + DY0) * b_blk);
-            mma<FP8, true>(d, a, b, IDESC);
+            const uint64_t b = b0 + (uint64_t)((dx * NCC_W + ccw) * KS * b_blk);
+            mma<FP8, true>(d, a, b, idesc);
         }
     }
-    }
-}
-
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R>
-__device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
-    static_assert(R + KS - 1 <= 12, "rows per tile");
-#define WSKPN_ROW(i_) \
-    case i_: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, R, i_>(dbase, ad, bd, box_step); break;
-    switch (ri) {
-        WSKPN_ROW(0) WSKPN_ROW(1) WSKPN_ROW(2) WSKPN_ROW(3) WSKPN_ROW(4) WSKPN_ROW(5)
-        WSKPN_ROW(6) WSKPN_ROW(7) WSKPN_ROW(8) WSKPN_ROW(9) WSKPN_ROW(10)
-        default: issue_row<KS, COUT_P, NCC_IN, NCC_W, FP8, R, 11>(dbase, ad, bd, box_step); break;
-    }
-#undef WSKPN_ROW
 }
 
 // ----------------------------------------------------------------- kernel
