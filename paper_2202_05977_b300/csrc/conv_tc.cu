@@ -44,6 +44,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "tma.cuh"
 
 namespace wskpn {
 
@@ -59,7 +60,6 @@ __host__ __device__ constexpr int rows_per_tile(int cout_p) {
 constexpr int THREADS = 192;
 constexpr int ROWB = 32;           // bytes of one pixel row of one K chunk
 constexpr uint32_t SMEM_MAX = 232448;  // also the limit tc_rows_per_item tests against
-constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr unsigned ST_TIMEOUT_PRODUCER = 1u, ST_TIMEOUT_MMA = 2u, ST_TIMEOUT_EPILOGUE = 4u;
 }  // namespace tc
 
@@ -85,59 +85,6 @@ struct TcArgs {
 };
 
 // ------------------------------------------------------------- primitives
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait: false when the limit expired or another role aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int* abort_flag) {
-    if (mbar_try_wait(a, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (true) {
-#pragma unroll 1
-        for (int i = 0; i < 8; ++i)
-            if (mbar_try_wait(a, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > tc::WAIT_NS) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
-        : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
-}
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
@@ -540,7 +487,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 }
 
 // ------------------------------------------------------------ host side
-static PFN_cuTensorMapEncodeTiled_v12000 get_encode(std::string& err) {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(std::string& err) {
     static std::mutex mu;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     std::lock_guard<std::mutex> lock(mu);
@@ -722,7 +669,7 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     const int KS = r.KS;
     const int eb = fp8 ? 1 : 2;
     const int ch = fp8 ? 32 : 16;
-    PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode(err);
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder(err);
     if (!encode) return WSKPN_EUNSUPPORTED;
     const int split = fp8 ? 0 : r.split_in;
     const int cin_row = L.cin_p * (split ? 2 : 1);  // stored channels per input pixel
