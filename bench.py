@@ -137,7 +137,7 @@ def stage_rooflines(stage_ms, precision, pk, h=H, w=W):
     streaming kernels), from the stage times of one denoise."""
     L = len(WIDTHS) - 1
     out = {}
-    prep_bytes = (40 + {"fp32": 40, "bf16": 64, "fp8": 32}[precision]) * h * w
+    prep_bytes = (40 + {"fp32": 40, "bf16": 64, "fp8": 64}[precision]) * h * w
     for i, ms in enumerate(stage_ms):
         if ms <= 0:
             continue
@@ -514,7 +514,7 @@ def main():
                 "traffic": TRAFFIC.get((args.precision, kname)), "kernel": kname, "peak_source": psrc}
     else:
         name = "prep" if dom == 0 else "decode_fuse_fwd"
-        byts = (40 + {"fp32": 40, "bf16": 64, "fp8": 32}[args.precision]) * H * W if dom == 0 \
+        byts = (40 + {"fp32": 40, "bf16": 64, "fp8": 64}[args.precision]) * H * W if dom == 0 \
             else DECODE_BYTES_PER_PX * H * W
         achieved = byts / (st[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",

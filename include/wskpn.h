@@ -57,7 +57,8 @@ typedef enum {
 typedef enum {
     WSKPN_FP32 = 0, /* convolutions in FP32 FFMA (SIMT) */
     WSKPN_BF16 = 1, /* convolutions on tcgen05 tensor cores, BF16 in, FP32 accumulate */
-    WSKPN_FP8 = 2   /* convolutions on tcgen05, e4m3 in, FP32 accumulate, per-channel scales */
+    WSKPN_FP8 = 2   /* convolutions on tcgen05, e4m3 operands (as hi/lo pairs by default, see
+                       WSKPN_TUNE_FP8_SPLIT), FP32 accumulate, per-channel weight scales */
 } wskpn_precision;
 
 #define WSKPN_MAX_LAYERS 8
@@ -460,9 +461,17 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     as the forward computed them (default; needs TC_SPLIT = 1); 0 = in
  *     FP32 with the FP32 weights (the ReLU masks are then those of the FP32
  *     network, which brings the gradient closer to the FP32/FP64 one).
+ *   WSKPN_TUNE_FP8_SPLIT (FP8 only): 1 = every e4m3 activation and weight
+ *     is a hi/lo pair in one scale (x / s = hi + lo, lo = e4m3 of the
+ *     residual) and each convolution sums A_hi W_hi + A_lo W_hi + A_hi W_lo,
+ *     three e4m3 products (default: the e4m3 rounding of the single term,
+ *     about 6 % per operand, compounds through the layers and the exp of
+ *     Eq. 3); 0 = one e4m3 value per operand.  Changing it re-packs the
+ *     weights (synchronises the device).
  * Errors: EINVAL for an unknown key or value. */
 #define WSKPN_TUNE_TC_SPLIT 2
 #define WSKPN_TUNE_TRAIN_RECOMPUTE 3
+#define WSKPN_TUNE_FP8_SPLIT 4
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
 
 /* Reads and clears the context's device status word after synchronising

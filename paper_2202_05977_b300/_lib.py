@@ -16,6 +16,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EBUSY", "ETI
 FP32, BF16, FP8 = 0, 1, 2
 TUNE_TC_SPLIT = 2
 TUNE_TRAIN_RECOMPUTE = 3
+TUNE_FP8_SPLIT = 4
 
 
 class Config(ctypes.Structure):

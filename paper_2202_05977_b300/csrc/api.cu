@@ -518,6 +518,19 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
         ctx->train_tc_recompute = value;
         return WSKPN_OK;
     }
+    if (key == WSKPN_TUNE_FP8_SPLIT && (value == 0 || value == 1) && ctx->cfg.prec == WSKPN_FP8) {
+        if (value == ctx->fp8_split) return WSKPN_OK;
+        WSKPN_CUDA_TRY(cudaDeviceSynchronize(), ctx->err);
+        ctx->fp8_split = value;
+        for (int l = 0; l < ctx->cfg.n_layers; ++l) {
+            wskpn_status s = tc_alloc_layer(ctx, l);
+            if (s) return s;
+        }
+        wskpn_status s = ctx_repack(ctx, 0);
+        if (s) return s;
+        WSKPN_CUDA_TRY(cudaDeviceSynchronize(), ctx->err);
+        return WSKPN_OK;
+    }
     ctx->err = "wskpn_set_tuning: unknown key or value";
     return WSKPN_EINVAL;
 }

@@ -37,6 +37,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include <cstring>
@@ -44,6 +45,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "quant.cuh"
 #include "tma.cuh"
 
 namespace wskpn {
@@ -200,7 +202,7 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
 // row's tap range (hence N, the accumulator column and the weight offset)
 // is computed at run time; the NCC_IN x KS MMAs themselves are an unrolled,
 // branch-free sequence, so one body serves every row of any tile height.
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, bool WLO>
 __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
     static_assert(COUT_P % 16 == 0 && COUT_P * (R < KS ? R : KS) <= 256, "MMA N");
     const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
@@ -214,20 +216,28 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
     constexpr uint32_t a_dx = (CPB * tc::ROWB) >> 4;       // one pixel row of a box
     const uint32_t d = dbase + (uint32_t)((R - 1 - (ri - dy0)) * COUT_P);
     const uint64_t b0 = bd + (uint64_t)(dy0 * b_blk);
+    // The (activation chunk, weight chunk) products of the row.  Without WLO
+    // every activation chunk meets its weight chunk (the lo half of a BF16
+    // hi/lo activation reuses the hi weights).  With WLO (e4m3 hi/lo
+    // activations and weights, n chunks each): A_hi W_hi + A_lo W_hi +
+    // A_hi W_lo, the lo x lo term being below the e4m3 rounding of the rest.
+    constexpr int NP = WLO ? 3 * (NCC_IN / 2) : NCC_IN;
 #pragma unroll
-    for (int cc = 0; cc < NCC_IN; ++cc) {
-        const int ccw = cc % NCC_W;  // the lo half of a split activation reuses the weights
+    for (int p = 0; p < NP; ++p) {
+        constexpr int n = NCC_IN / 2;
+        const int ca = WLO ? (p / n == 1 ? n + p % n : p % n) : p;
+        const int cw = WLO ? (p / n == 2 ? n + p % n : p % n) : p % NCC_W;
 #pragma unroll
         for (int dx = 0; dx < KS; ++dx) {
-            const uint64_t a = ad + (uint64_t)((cc / CPB) * box_step + (cc % CPB) * (tc::ROWB >> 4) + dx * a_dx);
-            const uint64_t b = b0 + (uint64_t)((dx * NCC_W + ccw) * KS * b_blk);
+            const uint64_t a = ad + (uint64_t)((ca / CPB) * box_step + (ca % CPB) * (tc::ROWB >> 4) + dx * a_dx);
+            const uint64_t b = b0 + (uint64_t)((dx * NCC_W + cw) * KS * b_blk);
             mma<FP8, true>(d, a, b, idesc);
         }
     }
 }
 
 // ----------------------------------------------------------------- kernel
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, bool WLO>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr int PAD = KS / 2;
@@ -370,7 +380,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     tc_fence_after();
 #pragma unroll
                     for (int j = 0; j < RPI; ++j)
-                        issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8, R>(
+                        issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8, R, WLO>(
                             r0 + j, dbase, adesc0 + (uint64_t)(s * a_stage + j * a_row), wdesc0, box_step);
                     mma_commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
                 }
@@ -406,7 +416,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
             const int x = tx * tc::BM + p;
             // bytes per stored pixel of an NHWC output (BF16 hi/lo pairs double it)
-            const size_t pix_bytes = FP8 ? (size_t)a.out_cp : (size_t)a.out_cp * 2 * (a.split_out ? 2 : 1);
+            const size_t pix_bytes = (size_t)a.out_cp * (FP8 ? 1 : 2) * (a.split_out ? 2 : 1);
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const int y = ty * R + r;
@@ -436,18 +446,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         for (int j = 0; j < 16; ++j)
                             if (j < nvalid) z[(size_t)j * HW] = v[j];
                     } else if constexpr (FP8) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
-                                make_float2(v[4 * j] * a.out_qscale, v[4 * j + 1] * a.out_qscale), __NV_SATFINITE,
-                                __NV_E4M3);
-                            const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
-                                make_float2(v[4 * j + 2] * a.out_qscale, v[4 * j + 3] * a.out_qscale),
-                                __NV_SATFINITE, __NV_E4M3);
-                            w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
-                        }
-                        *reinterpret_cast<uint4*>(pbase + c16 * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+                        uint4 hq, lq;
+                        fp8_pack16(v, a.out_qscale, hq, a.split_out ? &lq : nullptr);
+                        *reinterpret_cast<uint4*>(pbase + c16 * 16) = hq;
+                        if (a.split_out) *reinterpret_cast<uint4*>(pbase + a.out_cp + c16 * 16) = lq;
                     } else {
                         __nv_bfloat162 h2[8];
 #pragma unroll
@@ -511,13 +513,14 @@ static int cout_pad(const wskpn_config& c, int l) {
     return l == c.n_layers - 1 ? (c.widths[l + 1] + 15) / 16 * 16 : chan_pad(c.widths[l + 1], fp8);
 }
 
-// BF16 activations are stored as hi/lo pairs (2 x channels), FP8 as one byte.
+// Activations are stored as hi/lo pairs: BF16 (4 bytes per channel) or e4m3
+// (2 bytes per channel; the single-term e4m3 form uses half of it).
 size_t tc_act_bytes_per_pixel(const wskpn_config& c, int which) {
     const bool fp8 = c.prec == WSKPN_FP8;
     size_t m = 0;
     for (int l = 0; l < c.n_layers; ++l)
         if (l % 2 == which) {
-            const size_t b = (size_t)chan_pad(c.widths[l], fp8) * (fp8 ? 1 : 4);
+            const size_t b = (size_t)chan_pad(c.widths[l], fp8) * (fp8 ? 2 : 4);
             m = b > m ? b : m;
         }
     return m;
@@ -525,19 +528,24 @@ size_t tc_act_bytes_per_pixel(const wskpn_config& c, int which) {
 
 // Output-channel groups and device buffers of a tensor-core layer whose
 // cin_p / cout_p are set: the smallest power-of-two group count whose weight
-// image leaves room for two input stages (hi/lo activations assumed for
-// BF16), each group a multiple of 16 channels.
-wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, std::string& err) {
-    const int ncc = L.cin_p / (fp8 ? 32 : 16);
-    L.wtc_bytes = (size_t)KS * KS * ncc * L.cout_p * tc::ROWB;
+// image leaves room for two input stages (hi/lo activations assumed), each
+// group a multiple of 16 channels.  fp8_lo: e4m3 weights as hi/lo pairs
+// (the image holds the hi chunks, then the lo chunks).
+wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string& err) {
+    const int nch = L.cin_p / (fp8 ? 32 : 16);
+    const int ncc_w = fp8 && fp8_lo ? 2 * nch : nch;
+    const int ncc_in = 2 * nch;
+    cudaFree(L.wtc);
+    cudaFree(L.ep_scale);
+    cudaFree(L.ep_bias);
+    cudaFree(L.wscale);
+    L.wtc = nullptr;
+    L.ep_scale = L.ep_bias = L.wscale = nullptr;
+    L.wtc_bytes = (size_t)KS * KS * ncc_w * L.cout_p * tc::ROWB;
     L.groups = 1;
     while (true) {
-        const size_t wg = L.wtc_bytes / L.groups;
-        const int ncc_in = fp8 ? ncc : 2 * ncc;
-        const int cpb = chunks_per_box(ncc_in);
-        const size_t box = ((size_t)(tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024;
-        const size_t fixed = 1024 + (wg + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
-        if (fixed + 2 * (ncc_in / cpb) * box <= tc::SMEM_MAX) break;
+        const size_t fixed = tc_fixed_bytes(KS, L.cout_p / L.groups, ncc_w);
+        if (fixed + 2 * (size_t)tc_row_bytes(KS, ncc_in) <= tc::SMEM_MAX) break;
         if (L.cout_p / (2 * L.groups) < 16 || (L.cout_p / (2 * L.groups)) % 16) {
             err = "conv_tc: layer weights do not fit in shared memory";
             return WSKPN_EUNSUPPORTED;
@@ -561,7 +569,7 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
         ctx->err = "tensor-core path supports at most 64 output channels per layer";
         return WSKPN_EUNSUPPORTED;
     }
-    return tc_layer_alloc(L, c.conv_ks, fp8, ctx->err);
+    return tc_layer_alloc(L, c.conv_ks, fp8, fp8 && ctx->fp8_split, ctx->err);
 }
 
 // Builds the shared-memory image of a layer's B operand, one image per
@@ -569,13 +577,16 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
 // ((dx * ncc + cc) * KS + dy) of a group holds its cg rows of 32 bytes
 // (K-major) of tap (dy, dx) and channel chunk cc, so the KS vertical taps of
 // one (dx, cc) pair are consecutive N blocks.  32-byte swizzled like the TMA
-// writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).
+// writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).  With
+// wlo (e4m3 only) chunks ncc / 2 .. ncc - 1 hold the lo halves of chunks
+// 0 .. ncc / 2 - 1: e4m3(w / s - e4m3(w / s)), s the channel's scale.
 __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restrict__ bias, int Cin, int Cout,
-                               int KS, int cout_p, int groups, int ncc, int fp8, const float* __restrict__ wscale,
-                               float act_in_scale, uint8_t* __restrict__ img, float* __restrict__ ep_scale,
-                               float* __restrict__ ep_bias) {
+                               int KS, int cout_p, int groups, int ncc, int fp8, int wlo,
+                               const float* __restrict__ wscale, float act_in_scale, uint8_t* __restrict__ img,
+                               float* __restrict__ ep_scale, float* __restrict__ ep_bias) {
     const int ch = fp8 ? 32 : 16;
     const int cg = cout_p / groups;
+    const int nreal = wlo ? ncc / 2 : ncc;
     const int n_el = KS * KS * ncc * cout_p * ch;
     const size_t group_bytes = (size_t)KS * KS * ncc * cg * 32;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += gridDim.x * blockDim.x) {
@@ -585,12 +596,21 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restr
         const int g = i / (ch * cg * KS * KS * ncc);
         const int n = g * cg + nl;
         const int dy = chunk % KS, cc = (chunk / KS) % ncc, dx = chunk / (KS * ncc);
-        const int cin = cc * ch + k;
+        const bool lo = cc >= nreal;
+        const int cin = (lo ? cc - nreal : cc) * ch + k;
         const float v = (n < Cout && cin < Cin) ? w[((size_t)n * Cin + cin) * KS * KS + dy * KS + dx] : 0.f;
         const uint32_t o = (uint32_t)(nl * 32 + k * (fp8 ? 1 : 2));
         const size_t phys = g * group_bytes + (size_t)chunk * cg * 32 + (o ^ (((o >> 7) & 1u) << 4));
         if (fp8) {
-            img[phys] = (uint8_t)__nv_cvt_float_to_fp8(v / wscale[n], __NV_SATFINITE, __NV_E4M3);
+            const float q = v / wscale[n];
+            const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+            if (lo) {
+                const __half_raw hr = __nv_cvt_fp8_to_halfraw(h, __NV_E4M3);
+                img[phys] = (uint8_t)__nv_cvt_float_to_fp8(q - __half2float(*reinterpret_cast<const __half*>(&hr)),
+                                                           __NV_SATFINITE, __NV_E4M3);
+            } else {
+                img[phys] = (uint8_t)h;
+            }
         } else {
             *reinterpret_cast<__nv_bfloat16*>(img + phys) = __float2bfloat16_rn(v);
         }
@@ -623,23 +643,25 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     const wskpn_config& c = ctx->cfg;
     Layer& L = ctx->layers[l];
     const bool fp8 = c.prec == WSKPN_FP8;
-    const int ncc = L.cin_p / (fp8 ? 32 : 16);
+    const bool wlo = fp8 && ctx->fp8_split;
+    const int ncc = L.cin_p / (fp8 ? 32 : 16) * (wlo ? 2 : 1);
     const float* w = ctx->d_master + L.woff;
     const float* b = ctx->d_master + L.boff;
     if (fp8) {
         wscale_kernel<<<L.cout_p, 128, 0, st>>>(w, L.cin, L.cout, c.conv_ks, L.cout_p, L.wscale);
         WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     }
-    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, L.wscale,
-                                        ctx->act_scale[l], static_cast<uint8_t*>(L.wtc), L.ep_scale, L.ep_bias);
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, wlo,
+                                        L.wscale, ctx->act_scale[l], static_cast<uint8_t*>(L.wtc), L.ep_scale,
+                                        L.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     return WSKPN_OK;
 }
 
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, bool WLO>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
-    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, tc::rows_per_tile(COUT_P)>;
+    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, tc::rows_per_tile(COUT_P), WLO>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     kern<<<grid, tc::THREADS, smem, st>>>(map, a);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
@@ -671,13 +693,14 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     const int ch = fp8 ? 32 : 16;
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder(err);
     if (!encode) return WSKPN_EUNSUPPORTED;
-    const int split = fp8 ? 0 : r.split_in;
+    const int split = r.split_in;                   // hi/lo activations (BF16 or e4m3)
+    const bool wlo = fp8 && split;                  // e4m3 hi/lo weights with e4m3 hi/lo activations
     const int cin_row = L.cin_p * (split ? 2 : 1);  // stored channels per input pixel
     CUtensorMap map;
     cuuint64_t gdim[4] = {(cuuint64_t)cin_row, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
     cuuint64_t gstr[3] = {(cuuint64_t)cin_row * eb, (cuuint64_t)W * cin_row * eb, (cuuint64_t)H * W * cin_row * eb};
-    const int ncc_w = L.cin_p / ch;
-    const int ncc_in = ncc_w * (split ? 2 : 1);
+    const int ncc_in = L.cin_p / ch * (split ? 2 : 1);
+    const int ncc_w = fp8 && split ? ncc_in : L.cin_p / ch;  // weight-image chunks
     const int cpb = chunks_per_box(ncc_in);
     cuuint32_t box[4] = {(cuuint32_t)(ch * cpb), (cuuint32_t)(tc::BM + KS - 1), 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -701,7 +724,7 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     a.out_cp = r.out_cp;
     a.last = r.last;
     a.relu = r.relu;
-    a.split_out = r.split_out && !r.last && !fp8;
+    a.split_out = r.split_out && !r.last;
     a.out_qscale = r.out_qscale;
     // boxes of 128 + KS - 1 rows of cpb x 32 B, each 1024-byte aligned (128B-swizzle atom)
     a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024);
@@ -725,24 +748,31 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, r.device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
     wskpn_status (*launch)(const CUtensorMap&, const TcArgs&, size_t, int, cudaStream_t, std::string&) = nullptr;
-#define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_)                                                  \
-    if (!launch && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_)     \
-        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_>;
+#define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, lo_)                                                    \
+    if (!launch && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wlo == lo_)  \
+        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, lo_>;
 #define WSKPN_TC_BF16(ks_)                                                                                 \
-    WSKPN_TC_CASE(ks_, 32, 1, 1, false) WSKPN_TC_CASE(ks_, 32, 2, 1, false)                                \
-    WSKPN_TC_CASE(ks_, 48, 2, 2, false) WSKPN_TC_CASE(ks_, 48, 4, 2, false)                                \
-    WSKPN_TC_CASE(ks_, 64, 3, 3, false) WSKPN_TC_CASE(ks_, 64, 6, 3, false)                                \
-    WSKPN_TC_CASE(ks_, 16, 4, 4, false) WSKPN_TC_CASE(ks_, 16, 8, 4, false)                                \
-    WSKPN_TC_CASE(ks_, 32, 4, 4, false) WSKPN_TC_CASE(ks_, 32, 8, 4, false)
+    WSKPN_TC_CASE(ks_, 32, 1, 1, false, false) WSKPN_TC_CASE(ks_, 32, 2, 1, false, false)                  \
+    WSKPN_TC_CASE(ks_, 48, 2, 2, false, false) WSKPN_TC_CASE(ks_, 48, 4, 2, false, false)                  \
+    WSKPN_TC_CASE(ks_, 64, 3, 3, false, false) WSKPN_TC_CASE(ks_, 64, 6, 3, false, false)                  \
+    WSKPN_TC_CASE(ks_, 16, 4, 4, false, false) WSKPN_TC_CASE(ks_, 16, 8, 4, false, false)                  \
+    WSKPN_TC_CASE(ks_, 32, 4, 4, false, false) WSKPN_TC_CASE(ks_, 32, 8, 4, false, false)
+// e4m3: single-term (widths 10-32-48-64-12 and 64-64), and hi/lo pairs of
+// activations and weights (5x5 layers with 64 input channels run as two
+// 32-channel output groups)
 #define WSKPN_TC_FP8(ks_)                                                                                  \
-    WSKPN_TC_CASE(ks_, 32, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 1, 1, true) WSKPN_TC_CASE(ks_, 64, 2, 2, true) \
-    WSKPN_TC_CASE(ks_, 16, 2, 2, true)
+    WSKPN_TC_CASE(ks_, 32, 1, 1, true, false) WSKPN_TC_CASE(ks_, 64, 1, 1, true, false)                    \
+    WSKPN_TC_CASE(ks_, 64, 2, 2, true, false) WSKPN_TC_CASE(ks_, 16, 2, 2, true, false)                    \
+    WSKPN_TC_CASE(ks_, 32, 2, 2, true, true) WSKPN_TC_CASE(ks_, 64, 2, 2, true, true)                      \
+    WSKPN_TC_CASE(ks_, 32, 4, 4, true, true) WSKPN_TC_CASE(ks_, 64, 4, 4, true, true)                      \
+    WSKPN_TC_CASE(ks_, 16, 4, 4, true, true)
 // the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
 // 112-48, 80-32 and the heads 48-5, 32-5
 #define WSKPN_TC_UNET                                                                                      \
-    WSKPN_TC_CASE(3, 32, 4, 2, false) WSKPN_TC_CASE(3, 48, 6, 3, false) WSKPN_TC_CASE(3, 64, 8, 4, false)  \
-    WSKPN_TC_CASE(3, 48, 14, 7, false) WSKPN_TC_CASE(3, 32, 10, 5, false) WSKPN_TC_CASE(3, 16, 6, 3, false) \
-    WSKPN_TC_CASE(3, 16, 4, 2, false)
+    WSKPN_TC_CASE(3, 32, 4, 2, false, false) WSKPN_TC_CASE(3, 48, 6, 3, false, false)                      \
+    WSKPN_TC_CASE(3, 64, 8, 4, false, false) WSKPN_TC_CASE(3, 48, 14, 7, false, false)                     \
+    WSKPN_TC_CASE(3, 32, 10, 5, false, false) WSKPN_TC_CASE(3, 16, 6, 3, false, false)                     \
+    WSKPN_TC_CASE(3, 16, 4, 2, false, false)
     WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3) WSKPN_TC_UNET
 #undef WSKPN_TC_UNET
 #undef WSKPN_TC_FP8
@@ -772,7 +802,7 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     r.L = &ctx->layers[l];
     r.KS = c.conv_ks;
     r.fp8 = fp8;
-    r.split_in = r.split_out = fp8 ? 0 : ctx->tc_split;
+    r.split_in = r.split_out = fp8 ? ctx->fp8_split : ctx->tc_split;
     r.last = l == c.n_layers - 1;
     r.relu = !r.last;
     r.out_cp = ctx->layers[l].cout_p;
@@ -792,9 +822,9 @@ wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, c
         err = "tensor-core path supports at most 64 output channels per layer";
         return WSKPN_EUNSUPPORTED;
     }
-    wskpn_status s = tc_layer_alloc(L, KS, false, err);
+    wskpn_status s = tc_layer_alloc(L, KS, false, false, err);
     if (s) return s;
-    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, KS, L.cout_p, L.groups, L.cin_p / 16, 0, L.wscale, 1.f,
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, KS, L.cout_p, L.groups, L.cin_p / 16, 0, 0, L.wscale, 1.f,
                                         static_cast<uint8_t*>(L.wtc), L.ep_scale, L.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
@@ -831,7 +861,7 @@ wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float g
                          void* const* out, int layout, cudaStream_t st, std::string& err);
 
 wskpn_status launch_prep_fp8(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
-                             void* const* out, float act_scale, cudaStream_t st, std::string& err);
+                             void* const* out, float act_scale, int hilo, cudaStream_t st, std::string& err);
 
 static wskpn_status tc_logits_fp8(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                                   cudaStream_t st) {
@@ -844,9 +874,10 @@ static wskpn_status tc_logits_fp8(wskpn_ctx* ctx, const wskpn_frame* frames, int
     uint8_t* A = static_cast<uint8_t*>(ctx->d_tcA);
     uint8_t* Bf = static_cast<uint8_t*>(ctx->d_tcB);
     std::vector<void*> x0(B);
-    for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * ctx->layers[0].cin_p * HW;
+    const int split = ctx->fp8_split;
+    for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * ctx->layers[0].cin_p * (split ? 2 : 1) * HW;
     wskpn_status s = launch_prep_fp8(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(),
-                                     ctx->act_scale[0], st, ctx->err);
+                                     ctx->act_scale[0], split, st, ctx->err);
     if (s) return s;
     prof_mark(ctx, 1, st);
     for (int l = 0; l < c.n_layers; ++l) {

@@ -58,6 +58,7 @@ struct wskpn_ctx {
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
     bool fp8_calibrated = false;
     int tc_split = 1;  // BF16 activations as hi/lo pairs (WSKPN_TUNE_TC_SPLIT)
+    int fp8_split = 1;  // e4m3 activations and weights as hi/lo pairs (WSKPN_TUNE_FP8_SPLIT)
     int train_tc_recompute = 1;  // backward recomputes on the tensor cores (WSKPN_TUNE_TRAIN_RECOMPUTE)
     void* train = nullptr;  // training workspaces (train.cu), allocated by the first training call
     // stage profiling: one event set (n_layers + 3 events) per recorded call
@@ -84,7 +85,7 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l);
 wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st);
 wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                        cudaStream_t st);
-wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, std::string& err);
+wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string& err);
 wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
                                const std::vector<std::vector<float*>>& acts, cudaStream_t st);
 // BF16 tensor-core layers outside a context (hi/lo activations in and out)

@@ -6,6 +6,7 @@
 #include <cuda_fp8.h>
 
 #include "common.cuh"
+#include "quant.cuh"
 
 namespace wskpn {
 
@@ -117,10 +118,28 @@ __global__ void prep_nhwc32_fp8_kernel(PrepArgs a) {
     }
 }
 
-static thread_local float g_prep_qscale = 1.f;
+// Channels-last e4m3 hi/lo pairs [H][W][hi 32 | lo 32] of the values divided
+// by the layer-0 activation scale (the FP8 hi/lo tensor-core path).
+__global__ void prep_nhwc32_fp8x2_kernel(PrepArgs a) {
+    const int b = blockIdx.y;
+    const size_t HW = (size_t)a.H * a.W;
+    uint4* out = static_cast<uint4*>(a.out.p[b]);
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < HW; g += (size_t)gridDim.x * blockDim.x) {
+        float v[16];
+        prep_pixel(a, b, g, HW, v);
+#pragma unroll
+        for (int j = 10; j < 16; ++j) v[j] = 0.f;
+        uint4 hi, lo;
+        fp8_pack16(v, a.qscale, hi, &lo);
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+        out[4 * g] = hi;
+        out[4 * g + 1] = zero;
+        out[4 * g + 2] = lo;
+        out[4 * g + 3] = zero;
+    }
+}
 
-wskpn_status launch_prep_fp8(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
-                             void* const* out, float act_scale, cudaStream_t st, std::string& err);
+static thread_local float g_prep_qscale = 1.f;
 
 wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear,
                          float dfar, void* const* out, int layout, cudaStream_t st, std::string& err) {
@@ -150,18 +169,20 @@ wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float g
             prep_nhwc16_bf16_kernel<<<grid, 256, 0, st>>>(a);
         else if (layout == 2)
             prep_nhwc16_bf16x2_kernel<<<grid, 256, 0, st>>>(a);
-        else
+        else if (layout == 3)
             prep_nhwc32_fp8_kernel<<<grid, 256, 0, st>>>(a);
+        else
+            prep_nhwc32_fp8x2_kernel<<<grid, 256, 0, st>>>(a);
         WSKPN_CUDA_TRY(cudaGetLastError(), err);
     }
     return WSKPN_OK;
 }
 
-// layout 3: e4m3 NHWC32 with values / act_scale
+// layout 3: e4m3 NHWC32 with values / act_scale; layout 4 (hilo): e4m3 hi/lo pairs
 wskpn_status launch_prep_fp8(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,
-                             void* const* out, float act_scale, cudaStream_t st, std::string& err) {
+                             void* const* out, float act_scale, int hilo, cudaStream_t st, std::string& err) {
     g_prep_qscale = 1.f / act_scale;
-    const wskpn_status s = launch_prep(frames, B, H, W, gamma, dnear, dfar, out, 3, st, err);
+    const wskpn_status s = launch_prep(frames, B, H, W, gamma, dnear, dfar, out, hilo ? 4 : 3, st, err);
     g_prep_qscale = 1.f;
     return s;
 }

@@ -1,8 +1,10 @@
 """FP8 (e4m3) tensor-core convolutions with per-output-channel weight
 scales and calibrated per-layer activation scales; reconstruction in FP32.
-The per-pixel error against the FP64 oracle is measured and reported; the
-bounds asserted here are what single-term e4m3 reaches (max about 0.15 in
-emulation, mean about 1e-2), above the 3e-2 per-pixel target."""
+Default form: activations and weights as e4m3 hi/lo pairs (three e4m3
+products per convolution), held to the 3e-2 per-pixel maximum relative
+error against the FP64 oracle.  The single-term form (one e4m3 value per
+operand, WSKPN_TUNE_FP8_SPLIT = 0) is held to what it reaches (max about
+0.15 in emulation, mean about 1e-2)."""
 import numpy as np
 import pytest
 
@@ -11,6 +13,8 @@ import synth
 from tests._util import args, rel_err, sample_pixels, stack_frames, to_dev
 
 pytestmark = pytest.mark.gpu
+
+TOL_FP8 = 3e-2
 
 
 @pytest.fixture(scope="module")
@@ -36,9 +40,19 @@ def test_fp8_denoise_error_vs_oracle(wk, H, W):
     d.calibrate(*args(dev))
     out = d.denoise(*args(dev)).cpu().numpy()[0]
     assert d.device_status() == 0
-    mx, mean = rel_err(out, oracle.denoise(f, wb))
-    print(f"fp8 {H}x{W}: max rel {mx:.3e} mean {mean:.3e}")
-    assert np.isfinite(out).all() and mean < 3e-2 and mx < 0.5
+    ref = oracle.denoise(f, wb)
+    mx, mean = rel_err(out, ref)
+    print(f"fp8 hi/lo {H}x{W}: max rel {mx:.3e} mean {mean:.3e}")
+    assert np.isfinite(out).all() and mx < TOL_FP8
+    # the single-term form, then back: the repacked weights give the same result
+    d.set_tuning(wk._lib.TUNE_FP8_SPLIT, 0)
+    out1 = d.denoise(*args(dev)).cpu().numpy()[0]
+    mx1, mean1 = rel_err(out1, ref)
+    print(f"fp8 single {H}x{W}: max rel {mx1:.3e} mean {mean1:.3e}")
+    assert np.isfinite(out1).all() and mean1 < 3e-2 and mx1 < 0.5 and mean1 > mean
+    d.set_tuning(wk._lib.TUNE_FP8_SPLIT, 1)
+    assert np.array_equal(d.denoise(*args(dev)).cpu().numpy()[0], out)
+    assert d.device_status() == 0
 
 
 def test_fp8_1080p_error(wk):
@@ -58,4 +72,5 @@ def test_fp8_1080p_error(wk):
     full = wk.Denoiser(wb, precision="fp32", max_hw=(H, W)).denoise(*args(dev)).cpu().numpy()[0]
     fmx, fmean = rel_err(out, full)
     print(f"fp8 1080p: sampled vs oracle max {mx:.3e} mean {mean:.3e}; all px vs fp32 max {fmx:.3e} mean {fmean:.3e}")
-    assert np.isfinite(out).all() and fmean < 3e-2 and fmx < 1.0
+    # the FP32 path is within 2e-6 of the oracle (tests/test_gpu_fp32.py)
+    assert np.isfinite(out).all() and mx < TOL_FP8 and fmx < TOL_FP8
