@@ -74,6 +74,7 @@ struct TcArgs {
     int B, H, W;
     int cout;                // real output channels of the layer
     int out_cp;              // padded output channels per stored pixel (all groups)
+    int zero_c0, zero_n;     // storage channels [zero_c0, zero_c0 + zero_n) this launch writes as zeros
     int out_c0;              // first output channel of this group
     int relu, last;
     int split_out;           // write BF16 hi/lo pairs: [hi(COUT_P) | lo(COUT_P)]
@@ -473,6 +474,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         }
                     }
                 }
+                if (a.zero_n && valid) {  // storage padding past the layer's channels
+                    constexpr int EB = FP8 ? 1 : 2;
+                    uint8_t* const zb = static_cast<uint8_t*>(a.out) + pix * pix_bytes + (size_t)a.zero_c0 * EB;
+                    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+                    for (int zc = 0; zc < a.zero_n * EB; zc += 16) {
+                        *reinterpret_cast<uint4*>(zb + zc) = zero;
+                        if (a.split_out) *reinterpret_cast<uint4*>(zb + (size_t)a.out_cp * EB + zc) = zero;
+                    }
+                }
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
@@ -508,10 +518,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(std::string& err) {
 }
 
 static int chan_pad(int c, bool fp8) { return fp8 ? (c + 31) / 32 * 32 : (c + 15) / 16 * 16; }
-static int cout_pad(const wskpn_config& c, int l) {
-    const bool fp8 = c.prec == WSKPN_FP8;
-    return l == c.n_layers - 1 ? (c.widths[l + 1] + 15) / 16 * 16 : chan_pad(c.widths[l + 1], fp8);
-}
+// Output channels of a layer's MMAs (N per vertical tap): a multiple of 16.
+// Its stored pixels may be wider (e4m3 activations are stored in 32-channel
+// chunks); the epilogue writes the padding as zeros.
+static int cout_pad(const wskpn_config& c, int l) { return (c.widths[l + 1] + 15) / 16 * 16; }
 
 // Activations are stored as hi/lo pairs: BF16 (4 bytes per channel) or e4m3
 // (2 bytes per channel; the single-term e4m3 form uses half of it).
@@ -679,6 +689,7 @@ struct TcRun {
     int split_in, split_out;
     int last, relu;
     int out_cp, out_c0;
+    int zero_pad;  // write storage channels past the layer's own (up to out_cp) as zeros
     float out_qscale;
     unsigned int* status;
     int device;
@@ -761,9 +772,9 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
 // activations and weights (5x5 layers with 64 input channels run as two
 // 32-channel output groups)
 #define WSKPN_TC_FP8(ks_)                                                                                  \
-    WSKPN_TC_CASE(ks_, 32, 1, 1, true, false) WSKPN_TC_CASE(ks_, 64, 1, 1, true, false)                    \
+    WSKPN_TC_CASE(ks_, 32, 1, 1, true, false) WSKPN_TC_CASE(ks_, 48, 1, 1, true, false)                    \
     WSKPN_TC_CASE(ks_, 64, 2, 2, true, false) WSKPN_TC_CASE(ks_, 16, 2, 2, true, false)                    \
-    WSKPN_TC_CASE(ks_, 32, 2, 2, true, true) WSKPN_TC_CASE(ks_, 64, 2, 2, true, true)                      \
+    WSKPN_TC_CASE(ks_, 32, 2, 2, true, true) WSKPN_TC_CASE(ks_, 48, 2, 2, true, true)                      \
     WSKPN_TC_CASE(ks_, 32, 4, 4, true, true) WSKPN_TC_CASE(ks_, 64, 4, 4, true, true)                      \
     WSKPN_TC_CASE(ks_, 16, 4, 4, true, true)
 // the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
@@ -788,6 +799,9 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
         a.ep_scale = L.ep_scale + g * cg;
         a.ep_bias = L.ep_bias + g * cg;
         a.out_c0 = r.out_c0 + g * cg;
+        const int end = r.out_c0 + L.cout_p;
+        a.zero_c0 = end;
+        a.zero_n = r.zero_pad && g == G - 1 && r.out_cp > end ? r.out_cp - end : 0;
         const wskpn_status s = launch(map, a, smem, grid, st, err);
         if (s) return s;
     }
@@ -805,7 +819,8 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     r.split_in = r.split_out = fp8 ? ctx->fp8_split : ctx->tc_split;
     r.last = l == c.n_layers - 1;
     r.relu = !r.last;
-    r.out_cp = ctx->layers[l].cout_p;
+    r.out_cp = r.last ? ctx->layers[l].cout_p : ctx->layers[l + 1].cin_p;  // stored channels per pixel
+    r.zero_pad = 1;
     r.out_c0 = 0;
     r.out_qscale = fp8 && !r.last ? 1.f / ctx->act_scale[l + 1] : 1.f;
     r.status = ctx->d_status;
