@@ -75,6 +75,8 @@ struct TcArgs {
     int cout;                // real output channels of the layer
     int out_cp;              // padded output channels per stored pixel (all groups)
     int zero_c0, zero_n;     // storage channels [zero_c0, zero_c0 + zero_n) this launch writes as zeros
+    int dup_src, dup_dst;    // e4m3 hi/lo: the hi bytes of channels [dup_src, dup_src + 16) are also
+                             // written at dup_dst (the next layer's trailing half chunk); -1: none
     int out_c0;              // first output channel of this group
     int relu, last;
     int split_out;           // write BF16 hi/lo pairs: [hi(COUT_P) | lo(COUT_P)]
@@ -203,7 +205,7 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
 // row's tap range (hence N, the accumulator column and the weight offset)
 // is computed at run time; the NCC_IN x KS MMAs themselves are an unrolled,
 // branch-free sequence, so one body serves every row of any tile height.
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, bool WLO>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM>
 __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
     static_assert(COUT_P % 16 == 0 && COUT_P * (R < KS ? R : KS) <= 256, "MMA N");
     const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
@@ -217,17 +219,33 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
     constexpr uint32_t a_dx = (CPB * tc::ROWB) >> 4;       // one pixel row of a box
     const uint32_t d = dbase + (uint32_t)((R - 1 - (ri - dy0)) * COUT_P);
     const uint64_t b0 = bd + (uint64_t)(dy0 * b_blk);
-    // The (activation chunk, weight chunk) products of the row.  Without WLO
+    // The (activation chunk, weight chunk) products of the row.  WM = 0:
     // every activation chunk meets its weight chunk (the lo half of a BF16
-    // hi/lo activation reuses the hi weights).  With WLO (e4m3 hi/lo
-    // activations and weights, n chunks each): A_hi W_hi + A_lo W_hi +
-    // A_hi W_lo, the lo x lo term being below the e4m3 rounding of the rest.
-    constexpr int NP = WLO ? 3 * (NCC_IN / 2) : NCC_IN;
+    // hi/lo activation reuses the hi weights).  WM = 1 (e4m3 hi/lo
+    // activations and weights, NF chunks each): A_hi W_hi + A_lo W_hi +
+    // A_hi W_lo per chunk, the lo x lo term being below the e4m3 rounding of
+    // the rest.  WM = 2: the same for NF full chunks plus a trailing chunk of
+    // at most 16 channels t, whose activation chunks are [A_hi(t) | A_hi(t)]
+    // and [A_lo(t) | 0] and whose one weight chunk is [W_hi(t) | W_lo(t)]: two
+    // MMAs give A_hi W_hi + A_hi W_lo + A_lo W_hi of the tail.  Weight chunks:
+    // W_hi of the full chunks, their W_lo, then the tail chunk.
+    constexpr int nA = NCC_IN / 2;                  // activation chunks per half (hi or lo)
+    constexpr int NF = WM == 2 ? nA - 1 : nA;       // full chunks
+    constexpr int NP = WM == 0 ? NCC_IN : 3 * NF + (WM == 2 ? 2 : 0);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        constexpr int n = NCC_IN / 2;
-        const int ca = WLO ? (p / n == 1 ? n + p % n : p % n) : p;
-        const int cw = WLO ? (p / n == 2 ? n + p % n : p % n) : p % NCC_W;
+        int ca, cw;
+        if (WM == 0) {
+            ca = p;
+            cw = p % NCC_W;
+        } else if (p < 3 * NF) {
+            const int c = NF > 0 ? p % NF : 0, kind = NF > 0 ? p / NF : 0;
+            ca = kind == 1 ? nA + c : c;
+            cw = kind == 2 ? NF + c : c;
+        } else {
+            ca = p == 3 * NF ? NF : nA + NF;
+            cw = 2 * NF;
+        }
 #pragma unroll
         for (int dx = 0; dx < KS; ++dx) {
             const uint64_t a = ad + (uint64_t)((ca / CPB) * box_step + (ca % CPB) * (tc::ROWB >> 4) + dx * a_dx);
@@ -238,7 +256,7 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
 }
 
 // ----------------------------------------------------------------- kernel
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, bool WLO>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr int PAD = KS / 2;
@@ -381,7 +399,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     tc_fence_after();
 #pragma unroll
                     for (int j = 0; j < RPI; ++j)
-                        issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8, R, WLO>(
+                        issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8, R, WM>(
                             r0 + j, dbase, adesc0 + (uint64_t)(s * a_stage + j * a_row), wdesc0, box_step);
                     mma_commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
                 }
@@ -451,6 +469,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         fp8_pack16(v, a.out_qscale, hq, a.split_out ? &lq : nullptr);
                         *reinterpret_cast<uint4*>(pbase + c16 * 16) = hq;
                         if (a.split_out) *reinterpret_cast<uint4*>(pbase + a.out_cp + c16 * 16) = lq;
+                        if (a.out_c0 + c16 * 16 == a.dup_src)
+                            *reinterpret_cast<uint4*>(pbase + (a.dup_dst - a.out_c0)) = hq;
                     } else {
                         __nv_bfloat162 h2[8];
 #pragma unroll
@@ -479,7 +499,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     uint8_t* const zb = static_cast<uint8_t*>(a.out) + pix * pix_bytes + (size_t)a.zero_c0 * EB;
                     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
                     for (int zc = 0; zc < a.zero_n * EB; zc += 16) {
-                        *reinterpret_cast<uint4*>(zb + zc) = zero;
+                        if (a.dup_src < 0) *reinterpret_cast<uint4*>(zb + zc) = zero;  // else the tail copy
                         if (a.split_out) *reinterpret_cast<uint4*>(zb + (size_t)a.out_cp * EB + zc) = zero;
                     }
                 }
@@ -518,6 +538,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(std::string& err) {
 }
 
 static int chan_pad(int c, bool fp8) { return fp8 ? (c + 31) / 32 * 32 : (c + 15) / 16 * 16; }
+// e4m3 hi/lo weight mode of a layer with cin input channels: 2 when the
+// last 32-channel chunk holds at most 16 channels (trailing half chunk,
+// stored twice in the hi half of the activations), else 1.
+static int fp8_weight_mode(int cin) { return cin % 32 != 0 && cin % 32 <= 16 ? 2 : 1; }
 // Output channels of a layer's MMAs (N per vertical tap): a multiple of 16.
 // Its stored pixels may be wider (e4m3 activations are stored in 32-channel
 // chunks); the epilogue writes the padding as zeros.
@@ -540,11 +564,12 @@ size_t tc_act_bytes_per_pixel(const wskpn_config& c, int which) {
 // cin_p / cout_p are set: the smallest power-of-two group count whose weight
 // image leaves room for two input stages (hi/lo activations assumed), each
 // group a multiple of 16 channels.  fp8_lo: e4m3 weights as hi/lo pairs
-// (the image holds the hi chunks, then the lo chunks).
+// (weight mode fp8_weight_mode(cin), the chunk counts of fp8_chunks).
 wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string& err) {
     const int nch = L.cin_p / (fp8 ? 32 : 16);
-    const int ncc_w = fp8 && fp8_lo ? 2 * nch : nch;
+    const int wm = fp8 && fp8_lo ? fp8_weight_mode(L.cin) : 0;
     const int ncc_in = 2 * nch;
+    const int ncc_w = wm == 1 ? ncc_in : wm == 2 ? ncc_in - 1 : nch;
     cudaFree(L.wtc);
     cudaFree(L.ep_scale);
     cudaFree(L.ep_bias);
@@ -587,16 +612,18 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
 // ((dx * ncc + cc) * KS + dy) of a group holds its cg rows of 32 bytes
 // (K-major) of tap (dy, dx) and channel chunk cc, so the KS vertical taps of
 // one (dx, cc) pair are consecutive N blocks.  32-byte swizzled like the TMA
-// writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).  With
-// wlo (e4m3 only) chunks ncc / 2 .. ncc - 1 hold the lo halves of chunks
-// 0 .. ncc / 2 - 1: e4m3(w / s - e4m3(w / s)), s the channel's scale.
+// writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).  e4m3
+// weight modes (lo = e4m3(w / s - e4m3(w / s)), s the channel's scale):
+// wm 1: chunks nf .. 2 nf - 1 hold the lo halves of chunks 0 .. nf - 1;
+// wm 2: the same for nf = (ncc - 1) / 2 full chunks, then one chunk with
+// the hi (bytes 0..15) and lo (16..31) of the at most 16 trailing channels.
 __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restrict__ bias, int Cin, int Cout,
-                               int KS, int cout_p, int groups, int ncc, int fp8, int wlo,
+                               int KS, int cout_p, int groups, int ncc, int fp8, int wm,
                                const float* __restrict__ wscale, float act_in_scale, uint8_t* __restrict__ img,
                                float* __restrict__ ep_scale, float* __restrict__ ep_bias) {
     const int ch = fp8 ? 32 : 16;
     const int cg = cout_p / groups;
-    const int nreal = wlo ? ncc / 2 : ncc;
+    const int nf = wm == 1 ? ncc / 2 : wm == 2 ? (ncc - 1) / 2 : ncc;
     const int n_el = KS * KS * ncc * cout_p * ch;
     const size_t group_bytes = (size_t)KS * KS * ncc * cg * 32;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += gridDim.x * blockDim.x) {
@@ -606,8 +633,15 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restr
         const int g = i / (ch * cg * KS * KS * ncc);
         const int n = g * cg + nl;
         const int dy = chunk % KS, cc = (chunk / KS) % ncc, dx = chunk / (KS * ncc);
-        const bool lo = cc >= nreal;
-        const int cin = (lo ? cc - nreal : cc) * ch + k;
+        bool lo;
+        int cin;
+        if (wm == 2 && cc == 2 * nf) {  // trailing half chunk: hi | lo
+            lo = k >= 16;
+            cin = nf * ch + (k & 15);
+        } else {
+            lo = wm != 0 && cc >= nf;
+            cin = (lo ? cc - nf : cc) * ch + k;
+        }
         const float v = (n < Cout && cin < Cin) ? w[((size_t)n * Cin + cin) * KS * KS + dy * KS + dx] : 0.f;
         const uint32_t o = (uint32_t)(nl * 32 + k * (fp8 ? 1 : 2));
         const size_t phys = g * group_bytes + (size_t)chunk * cg * 32 + (o ^ (((o >> 7) & 1u) << 4));
@@ -653,25 +687,26 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     const wskpn_config& c = ctx->cfg;
     Layer& L = ctx->layers[l];
     const bool fp8 = c.prec == WSKPN_FP8;
-    const bool wlo = fp8 && ctx->fp8_split;
-    const int ncc = L.cin_p / (fp8 ? 32 : 16) * (wlo ? 2 : 1);
+    const int wm = fp8 && ctx->fp8_split ? fp8_weight_mode(L.cin) : 0;
+    const int nch = L.cin_p / (fp8 ? 32 : 16);
+    const int ncc = wm == 1 ? 2 * nch : wm == 2 ? 2 * nch - 1 : nch;
     const float* w = ctx->d_master + L.woff;
     const float* b = ctx->d_master + L.boff;
     if (fp8) {
         wscale_kernel<<<L.cout_p, 128, 0, st>>>(w, L.cin, L.cout, c.conv_ks, L.cout_p, L.wscale);
         WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     }
-    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, wlo,
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, wm,
                                         L.wscale, ctx->act_scale[l], static_cast<uint8_t*>(L.wtc), L.ep_scale,
                                         L.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     return WSKPN_OK;
 }
 
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, bool WLO>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
-    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, tc::rows_per_tile(COUT_P), WLO>;
+    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, tc::rows_per_tile(COUT_P), WM>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     kern<<<grid, tc::THREADS, smem, st>>>(map, a);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
@@ -690,6 +725,7 @@ struct TcRun {
     int last, relu;
     int out_cp, out_c0;
     int zero_pad;  // write storage channels past the layer's own (up to out_cp) as zeros
+    int dup_src = -1, dup_dst = -1;  // e4m3 hi/lo trailing half chunk of the next layer (TcArgs)
     float out_qscale;
     unsigned int* status;
     int device;
@@ -705,13 +741,13 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder(err);
     if (!encode) return WSKPN_EUNSUPPORTED;
     const int split = r.split_in;                   // hi/lo activations (BF16 or e4m3)
-    const bool wlo = fp8 && split;                  // e4m3 hi/lo weights with e4m3 hi/lo activations
+    const int wm = fp8 && split ? fp8_weight_mode(L.cin) : 0;  // e4m3 hi/lo weights with hi/lo activations
     const int cin_row = L.cin_p * (split ? 2 : 1);  // stored channels per input pixel
     CUtensorMap map;
     cuuint64_t gdim[4] = {(cuuint64_t)cin_row, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
     cuuint64_t gstr[3] = {(cuuint64_t)cin_row * eb, (cuuint64_t)W * cin_row * eb, (cuuint64_t)H * W * cin_row * eb};
     const int ncc_in = L.cin_p / ch * (split ? 2 : 1);
-    const int ncc_w = fp8 && split ? ncc_in : L.cin_p / ch;  // weight-image chunks
+    const int ncc_w = wm == 1 ? ncc_in : wm == 2 ? ncc_in - 1 : L.cin_p / ch;  // weight-image chunks
     const int cpb = chunks_per_box(ncc_in);
     cuuint32_t box[4] = {(cuuint32_t)(ch * cpb), (cuuint32_t)(tc::BM + KS - 1), 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -759,31 +795,31 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, r.device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
     wskpn_status (*launch)(const CUtensorMap&, const TcArgs&, size_t, int, cudaStream_t, std::string&) = nullptr;
-#define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, lo_)                                                    \
-    if (!launch && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wlo == lo_)  \
-        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, lo_>;
+#define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
+    if (!launch && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_)    \
+        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_>;
 #define WSKPN_TC_BF16(ks_)                                                                                 \
-    WSKPN_TC_CASE(ks_, 32, 1, 1, false, false) WSKPN_TC_CASE(ks_, 32, 2, 1, false, false)                  \
-    WSKPN_TC_CASE(ks_, 48, 2, 2, false, false) WSKPN_TC_CASE(ks_, 48, 4, 2, false, false)                  \
-    WSKPN_TC_CASE(ks_, 64, 3, 3, false, false) WSKPN_TC_CASE(ks_, 64, 6, 3, false, false)                  \
-    WSKPN_TC_CASE(ks_, 16, 4, 4, false, false) WSKPN_TC_CASE(ks_, 16, 8, 4, false, false)                  \
-    WSKPN_TC_CASE(ks_, 32, 4, 4, false, false) WSKPN_TC_CASE(ks_, 32, 8, 4, false, false)
+    WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 64, 3, 3, false, 0) WSKPN_TC_CASE(ks_, 64, 6, 3, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 16, 4, 4, false, 0) WSKPN_TC_CASE(ks_, 16, 8, 4, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 32, 4, 4, false, 0) WSKPN_TC_CASE(ks_, 32, 8, 4, false, 0)
 // e4m3: single-term (widths 10-32-48-64-12 and 64-64), and hi/lo pairs of
-// activations and weights (5x5 layers with 64 input channels run as two
-// 32-channel output groups)
+// activations and weights (10 and 48 input channels with a trailing half
+// chunk; 5x5 64-64 layers as two 32-channel output groups)
 #define WSKPN_TC_FP8(ks_)                                                                                  \
-    WSKPN_TC_CASE(ks_, 32, 1, 1, true, false) WSKPN_TC_CASE(ks_, 48, 1, 1, true, false)                    \
-    WSKPN_TC_CASE(ks_, 64, 2, 2, true, false) WSKPN_TC_CASE(ks_, 16, 2, 2, true, false)                    \
-    WSKPN_TC_CASE(ks_, 32, 2, 2, true, true) WSKPN_TC_CASE(ks_, 48, 2, 2, true, true)                      \
-    WSKPN_TC_CASE(ks_, 32, 4, 4, true, true) WSKPN_TC_CASE(ks_, 64, 4, 4, true, true)                      \
-    WSKPN_TC_CASE(ks_, 16, 4, 4, true, true)
+    WSKPN_TC_CASE(ks_, 32, 1, 1, true, 0) WSKPN_TC_CASE(ks_, 48, 1, 1, true, 0)                            \
+    WSKPN_TC_CASE(ks_, 64, 2, 2, true, 0) WSKPN_TC_CASE(ks_, 16, 2, 2, true, 0)                            \
+    WSKPN_TC_CASE(ks_, 32, 2, 1, true, 2) WSKPN_TC_CASE(ks_, 48, 2, 2, true, 1)                            \
+    WSKPN_TC_CASE(ks_, 64, 4, 3, true, 2) WSKPN_TC_CASE(ks_, 16, 4, 4, true, 1)                            \
+    WSKPN_TC_CASE(ks_, 32, 4, 4, true, 1) WSKPN_TC_CASE(ks_, 64, 4, 4, true, 1)
 // the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
 // 112-48, 80-32 and the heads 48-5, 32-5
 #define WSKPN_TC_UNET                                                                                      \
-    WSKPN_TC_CASE(3, 32, 4, 2, false, false) WSKPN_TC_CASE(3, 48, 6, 3, false, false)                      \
-    WSKPN_TC_CASE(3, 64, 8, 4, false, false) WSKPN_TC_CASE(3, 48, 14, 7, false, false)                     \
-    WSKPN_TC_CASE(3, 32, 10, 5, false, false) WSKPN_TC_CASE(3, 16, 6, 3, false, false)                     \
-    WSKPN_TC_CASE(3, 16, 4, 2, false, false)
+    WSKPN_TC_CASE(3, 32, 4, 2, false, 0) WSKPN_TC_CASE(3, 48, 6, 3, false, 0)                              \
+    WSKPN_TC_CASE(3, 64, 8, 4, false, 0) WSKPN_TC_CASE(3, 48, 14, 7, false, 0)                             \
+    WSKPN_TC_CASE(3, 32, 10, 5, false, 0) WSKPN_TC_CASE(3, 16, 6, 3, false, 0)                             \
+    WSKPN_TC_CASE(3, 16, 4, 2, false, 0)
     WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3) WSKPN_TC_UNET
 #undef WSKPN_TC_UNET
 #undef WSKPN_TC_FP8
@@ -802,6 +838,8 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
         const int end = r.out_c0 + L.cout_p;
         a.zero_c0 = end;
         a.zero_n = r.zero_pad && g == G - 1 && r.out_cp > end ? r.out_cp - end : 0;
+        a.dup_src = r.dup_src;
+        a.dup_dst = r.dup_dst;
         const wskpn_status s = launch(map, a, smem, grid, st, err);
         if (s) return s;
     }
@@ -821,6 +859,10 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     r.relu = !r.last;
     r.out_cp = r.last ? ctx->layers[l].cout_p : ctx->layers[l + 1].cin_p;  // stored channels per pixel
     r.zero_pad = 1;
+    if (fp8 && ctx->fp8_split && !r.last && fp8_weight_mode(ctx->layers[l + 1].cin) == 2) {
+        r.dup_src = ctx->layers[l + 1].cin / 32 * 32;  // the next layer's trailing half chunk
+        r.dup_dst = r.dup_src + 16;
+    }
     r.out_c0 = 0;
     r.out_qscale = fp8 && !r.last ? 1.f / ctx->act_scale[l + 1] : 1.f;
     r.status = ctx->d_status;

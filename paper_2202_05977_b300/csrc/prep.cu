@@ -118,8 +118,10 @@ __global__ void prep_nhwc32_fp8_kernel(PrepArgs a) {
     }
 }
 
-// Channels-last e4m3 hi/lo pairs [H][W][hi 32 | lo 32] of the values divided
-// by the layer-0 activation scale (the FP8 hi/lo tensor-core path).
+// Channels-last e4m3 hi/lo pairs of the values divided by the layer-0
+// activation scale (the FP8 hi/lo tensor-core path): per pixel
+// [hi(16) | hi(16) again | lo(16) | 0 (16)], the 10 channels (6 zeros after
+// them) being the first layer's trailing half chunk.
 __global__ void prep_nhwc32_fp8x2_kernel(PrepArgs a) {
     const int b = blockIdx.y;
     const size_t HW = (size_t)a.H * a.W;
@@ -133,7 +135,7 @@ __global__ void prep_nhwc32_fp8x2_kernel(PrepArgs a) {
         fp8_pack16(v, a.qscale, hi, &lo);
         const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
         out[4 * g] = hi;
-        out[4 * g + 1] = zero;
+        out[4 * g + 1] = hi;
         out[4 * g + 2] = lo;
         out[4 * g + 3] = zero;
     }
