@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--impl", default="wskpn", choices=["wskpn", "reference"])
     p.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 plain-path comparison")
+    p.add_argument("--no-fp8", action="store_true", help="skip the FP8 form's timing and error (BF16 runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serving", action="store_true")
@@ -402,6 +403,25 @@ def main():
     if not args.no_fp32 and args.precision != "fp32":
         fp32 = time_path("fp32", max(3, args.steps // 4), 3)
 
+    # the precision form: the same frame through the BF16 and FP8 forms, each
+    # output against the FP32 path's (which is within 2e-6 of the FP64
+    # oracle), per element |x - ref| / max(|ref|, 1e-6)
+    precision_form = None
+    if fp32 is not None and args.precision == "bf16":
+        def err_vs_fp32(out):
+            ref = fp32["out"]
+            e = (out - ref).abs() / ref.abs().clamp_min(1e-6)
+            return {"max_rel_err_vs_fp32": float(e.max()), "mean_rel_err_vs_fp32": float(e.mean())}
+        precision_form = {"bf16": {"ms_per_frame": main_res["ms_step"], **err_vs_fp32(main_res["out"])}}
+        if not args.no_fp8:
+            r8 = time_path("fp8", max(5, args.steps // 2), 3)
+            precision_form["fp8"] = {"ms_per_frame": r8["ms_step"], "form": "e4m3 hi/lo activations and weights",
+                                     "calibration": f"static scales from the seed-{SEED + 1} frame",
+                                     "stages_ms": dict(zip(["prep"] + [f"conv{i + 1}" for i in range(len(WIDTHS) - 1)]
+                                                           + ["reconstruct"], r8["stage_ms"])),
+                                     **err_vs_fp32(r8["out"])}
+            del r8
+
     # the same path at 720p and 1440p (seeds 1 and 3), for ms/frame, frames/s
     # and the per-stage roofline fractions at each resolution
     sweep = {}
@@ -579,6 +599,8 @@ def main():
         # context only, another machine and resolution
         line["paper_context"] = {"hardware": "RTX 2080 Ti", "resolution": "1280x720",
                                  "ms_per_frame": {"3_blocks": 6.58, "6_blocks": 12.89, "multires": 22.70}}
+        if precision_form is not None:
+            line["precision_form"] = precision_form
         if fp32 is not None:
             line["fp32_ms_per_frame"] = fp32["ms_step"] / world
             line["speedup_vs_fp32"] = fp32["ms_step"] / main_res["ms_step"]
