@@ -288,6 +288,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     float* s_bias = s_scale + COUT_P;                     // [COUT_P]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // Every CTA of this persistent grid is resident from the start, so the
+    // next kernel on the stream may launch now: its CTAs take an SM as this
+    // grid's CTAs leave and set up (weights, barriers, TMEM) while it drains.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     for (int i = tid; i < COUT_P; i += tc::THREADS) {
         s_scale[i] = a.ep_scale[i];
         s_bias[i] = a.ep_bias[i];
@@ -336,6 +340,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const uint32_t n = a.wbytes - off < 32768u ? a.wbytes - off : 32768u;
                 bulk_load(smem_u32(sW + off), static_cast<const uint8_t*>(a.wimg) + off, n, wb);
             }
+            // the activations are the previous kernel's output: wait for that
+            // grid to complete (returns at once without a programmatic
+            // dependency).  Everything else this CTA reads or writes in global
+            // memory follows from these loads.
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             uint32_t it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
@@ -708,8 +717,19 @@ static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t 
                                 std::string& err) {
     auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, tc::rows_per_tile(COUT_P), WM>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
-    kern<<<grid, tc::THREADS, smem, st>>>(map, a);
-    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    // programmatic dependent launch: set-up overlaps the previous kernel's
+    // tail; the TMA producer waits for that kernel before reading activations
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tc::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    WSKPN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, map, a), err);
     return WSKPN_OK;
 }
 
