@@ -356,10 +356,11 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     pk = peaks()
 
-    def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None):
+    def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS):
         h, w = hw
         xs = xin if frame is None else frame
-        d = wk.Denoiser(wb if weights is None else weights, precision=precision, max_hw=(h, w), widths=widths)
+        d = wk.Denoiser(wb if weights is None else weights, precision=precision, max_hw=(h, w), widths=widths,
+                        conv_ks=ks)
         if args.tc_split is not None and precision == "bf16":
             d.set_tuning(2, args.tc_split)
         if precision == "fp8":  # static activation scales from a different frame (seed 3)
@@ -462,6 +463,15 @@ def main():
             six["1280x720"]["fp32_ms_per_frame"] = r["ms_step"]
             del r
         variants["six_blocks"] = six
+        # the 3x3 form of the same network (the configuration text's kernel
+        # size; Sec. 4.1's 5x5 is the primary form) at 1080p
+        wb3 = synth.make_weights(WIDTHS, 3, seed=SEED)
+        c3 = {}
+        for prec in ("bf16", "fp8"):
+            r = time_path(prec, max(5, args.steps // 2), 3, (H, W), None, WIDTHS, wb3, 3)
+            c3[f"{prec}_ms_per_frame"] = r["ms_step"]
+            del r
+        variants["conv3x3_1920x1080"] = c3
     if not args.no_variants:
         # the multi-resolution variant (U-Net, 3 levels, kernels 3 and 5, Eq. 7), FP32
         from paper_2202_05977_b300.multires import MultiResDenoiser
