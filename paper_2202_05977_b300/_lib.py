@@ -17,6 +17,8 @@ FP32, BF16, FP8 = 0, 1, 2
 TUNE_TC_SPLIT = 2
 TUNE_TRAIN_RECOMPUTE = 3
 TUNE_FP8_SPLIT = 4
+TUNE_HOST_BANDS = 5
+TUNE_HOST_FIRST_BAND = 6
 
 
 class Config(ctypes.Structure):

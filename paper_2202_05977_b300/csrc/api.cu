@@ -310,7 +310,17 @@ static int band_halo(const wskpn_config& c) {
 static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, int batch, int h, int w,
                                         float* host_out, int nb, cudaStream_t st) {
     const int halo = band_halo(ctx->cfg);
-    const int bh = (h + nb - 1) / nb;
+    // band k covers rows [yb[k], yb[k + 1]); the first may be shorter, so
+    // that the first computation starts sooner
+    std::vector<int> yb(nb + 1, h);
+    {
+        const double w0 = ctx->host_first_pct / 100.0, unit = h / (w0 + nb - 1);
+        yb[0] = 0;
+        yb[1] = std::max(1, std::min(h, (int)(w0 * unit + 0.5)));
+        for (int k = 2; k < nb; ++k) yb[k] = std::min(h, yb[1] + (int)((k - 1) * (h - yb[1]) / (double)(nb - 1) + 0.5));
+    }
+    int bh = 0;
+    for (int k = 0; k < nb; ++k) bh = std::max(bh, yb[k + 1] - yb[k]);
     const int ext = std::min(h, bh + 2 * halo);  // rows of an extended band
     const size_t need = (size_t)13 * ext * w;
     if (!ctx->up_stream) {
@@ -338,7 +348,7 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
         const float* src[4] = {hf[b].radiance, hf[b].albedo, hf[b].normal, hf[b].depth};
         for (int k = 0; k < nb; ++k, ++job) {
             const int slot = job & 1;
-            const int y0 = k * bh, y1 = std::min(h, y0 + bh);
+            const int y0 = yb[k], y1 = yb[k + 1];
             if (y0 >= y1) break;
             const int e0 = std::max(0, y0 - halo), e1 = std::min(h, y1 + halo), eh = e1 - e0;
             const size_t ePX = (size_t)eh * w;
@@ -393,7 +403,7 @@ wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, 
     // Frames of at least 480 rows go through the banded pipeline (one band
     // per ~240 rows, at most 8): the recomputed halos cost less than the
     // copies they let overlap.  Smaller frames: one upload, denoise, download.
-    const int nb = std::min(8, h / 240);
+    const int nb = ctx->host_bands > 0 ? std::min(ctx->host_bands, h) : std::min(8, h / 240);
     if (nb >= 2) return denoise_host_banded(ctx, host_frames, batch, h, w, host_out, nb, (cudaStream_t)stream);
     if (!ctx->d_stage) {
         cudaError_t e = cudaMalloc((void**)&ctx->d_stage, ctx->ws_pixels * 13 * sizeof(float));
@@ -516,6 +526,14 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
     }
     if (key == WSKPN_TUNE_TRAIN_RECOMPUTE && (value == 0 || value == 1)) {
         ctx->train_tc_recompute = value;
+        return WSKPN_OK;
+    }
+    if (key == WSKPN_TUNE_HOST_BANDS && value >= 0 && value <= 64) {
+        ctx->host_bands = value;
+        return WSKPN_OK;
+    }
+    if (key == WSKPN_TUNE_HOST_FIRST_BAND && value >= 10 && value <= 100) {
+        ctx->host_first_pct = value;
         return WSKPN_OK;
     }
     if (key == WSKPN_TUNE_FP8_SPLIT && (value == 0 || value == 1) && ctx->cfg.prec == WSKPN_FP8) {

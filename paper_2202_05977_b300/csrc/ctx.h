@@ -60,6 +60,8 @@ struct wskpn_ctx {
     int tc_split = 1;  // BF16 activations as hi/lo pairs (WSKPN_TUNE_TC_SPLIT)
     int fp8_split = 1;  // e4m3 activations and weights as hi/lo pairs (WSKPN_TUNE_FP8_SPLIT)
     int train_tc_recompute = 1;  // backward recomputes on the tensor cores (WSKPN_TUNE_TRAIN_RECOMPUTE)
+    int host_bands = 0;         // bands of the host-buffer pipeline, 0 = automatic (WSKPN_TUNE_HOST_BANDS)
+    int host_first_pct = 100;   // first band's height in % of the others (WSKPN_TUNE_HOST_FIRST_BAND)
     void* train = nullptr;  // training workspaces (train.cu), allocated by the first training call
     // stage profiling: one event set (n_layers + 3 events) per recorded call
     bool prof = false;
