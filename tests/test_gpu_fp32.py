@@ -188,3 +188,25 @@ def test_banded_host_call_matches_device_call(torch, wk, prec, B, H, W):
     d.denoise_host(*host, out)
     mx, _ = rel_err(out.numpy(), ref)
     assert mx < 1e-5, mx
+
+
+@pytest.mark.parametrize("bands,first", [(3, 40), (7, 100), (2, 70)])
+def test_banded_host_call_with_tuned_bands(torch, wk, bands, first):
+    """WSKPN_TUNE_HOST_BANDS / WSKPN_TUNE_HOST_FIRST_BAND change only how the
+    host pipeline splits the frame, not its result."""
+    from paper_2202_05977_b300 import _lib
+    H, W = 530, 160
+    f = synth.make_frame(H, W, 44)
+    wb = synth.make_weights(seed=4)
+    d = wk.Denoiser(wb, precision="fp32", max_hw=(H, W))
+    st = stack_frames([f])
+    ref = d.denoise(*args(to_dev(st))).cpu().numpy()
+    d.set_tuning(_lib.TUNE_HOST_BANDS, bands)
+    d.set_tuning(_lib.TUNE_HOST_FIRST_BAND, first)
+    host = [torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in ("radiance", "albedo", "normal", "depth")]
+    out = torch.full((1, 3, H, W), float("nan"), dtype=torch.float32).pin_memory()
+    d.denoise_host(*host, out)
+    mx, _ = rel_err(out.numpy(), ref)
+    assert mx < 1e-5, mx
+    with pytest.raises(wk.WskpnError):
+        d.set_tuning(_lib.TUNE_HOST_FIRST_BAND, 5)
