@@ -135,6 +135,15 @@ __host__ __device__ constexpr uint32_t tc_row_bytes(int KS, int ncc_in) {
 __host__ __device__ constexpr size_t tc_fixed_bytes(int KS, int cout_g, int ncc_w) {
     return 1024 + ((size_t)KS * KS * ncc_w * cout_g * 32 + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
 }
+// Folded horizontal taps (XF, the last layer with 16 output channels): the
+// epilogue warps exchange the partial sums of their edge pixels through
+// shared memory, [2 rows][4 warps][KS - 1 lanes][KS - 1 taps][16] floats,
+// plus 2 x 4 flags.
+__host__ __device__ constexpr size_t tc_xf_bytes(int KS) {
+    return (size_t)2 * 4 * (KS - 1) * (KS - 1) * 16 * sizeof(float) + 64;
+}
+// Output rows per tile of the folded form: N = (vertical taps) x KS x 16 <= 256.
+__host__ __device__ constexpr int xf_rows_per_tile(int KS) { return 256 / (KS * 16); }
 // Input rows per pipeline stage: the most of 4, 3, 2 for which two such
 // stages fit (one barrier wait and one commit per stage instead of per row:
 // conv1 0.158 -> 0.130, conv2 0.269 -> 0.232, conv4 0.381 -> 0.341 ms at
@@ -205,8 +214,34 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
 // row's tap range (hence N, the accumulator column and the weight offset)
 // is computed at run time; the NCC_IN x KS MMAs themselves are an unrolled,
 // branch-free sequence, so one body serves every row of any tile height.
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF>
 __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
+    if constexpr (XF) {
+        // Folded horizontal taps: one MMA per channel chunk covers the input
+        // row's vertical taps dy0..dy1 and all KS horizontal taps, N = nb x KS x
+        // COUT_P columns ordered (dy, dx, channel); accumulator row slots hold
+        // KS x COUT_P columns, and the epilogue adds the dx-shifted partial sums.
+        // The A operand is the unshifted row window (input pixels x0 - PAD ..).
+        constexpr int NCB = KS * COUT_P;
+        static_assert(NCB * (R < KS ? R : KS) <= 256, "MMA N");
+        const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
+        const int dy1 = ri < KS - 1 ? ri : KS - 1;
+        const int nb = dy1 - dy0 + 1;
+        if (nb <= 0) return;
+        constexpr uint32_t IDESC0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tc::BM >> 4) << 24);
+        const uint32_t idesc = IDESC0 | ((uint32_t)((nb * NCB) >> 3) << 17);
+        constexpr uint32_t b_blk = (COUT_P * tc::ROWB) >> 4;  // one (dy, dx) block of a chunk, 16-byte units
+        constexpr int CPB = chunks_per_box(NCC_IN);
+        const uint32_t d = dbase + (uint32_t)((R - 1 - (ri - dy0)) * NCB);
+#pragma unroll
+        for (int cc = 0; cc < NCC_IN; ++cc) {
+            const int ccw = cc % NCC_W;
+            const uint64_t a = ad + (uint64_t)((cc / CPB) * box_step + (cc % CPB) * (tc::ROWB >> 4));
+            const uint64_t b = bd + (uint64_t)((ccw * KS + dy0) * KS * b_blk);
+            mma<false, true>(d, a, b, idesc);
+        }
+        return;
+    }
     static_assert(COUT_P % 16 == 0 && COUT_P * (R < KS ? R : KS) <= 256, "MMA N");
     const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
     const int dy1 = ri < KS - 1 ? ri : KS - 1;
@@ -256,19 +291,22 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
 }
 
 // ----------------------------------------------------------------- kernel
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr int PAD = KS / 2;
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
-    constexpr uint32_t NCOL = tmem_cols<COUT_P, R>();
+    constexpr int NCB = XF ? KS * COUT_P : COUT_P;        // TMEM columns of one output row's accumulators
+    constexpr int TPX = XF ? tc::BM - (KS - 1) : tc::BM;  // output pixels per tile row
+    static_assert(!XF || (!FP8 && WM == 0 && COUT_P == 16), "folded taps: BF16, 16 output channels");
+    constexpr uint32_t NCOL = tmem_cols<NCB, R>();
     constexpr int ROWS_IN = R + KS - 1;
     constexpr int CPB = chunks_per_box(NCC_IN);
     constexpr int NBOX = NCC_IN / CPB;
     constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB * CPB;
     constexpr int RPI = tc_rows_per_item(KS, COUT_P, NCC_IN, NCC_W);
     static_assert(COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256, "MMA N");
-    static_assert(2 * R * COUT_P <= 512, "TMEM columns");
+    static_assert(2 * R * NCB <= 512, "TMEM columns");
 
     extern __shared__ __align__(1024) uint8_t dsmem[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
@@ -286,6 +324,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(fin + 1) + 1;
     float* s_scale = reinterpret_cast<float*>(fin + 2);  // [COUT_P]
     float* s_bias = s_scale + COUT_P;                     // [COUT_P]
+    // XF: edge partial sums and the epilogue warps' tile flags, after the 2 x 64 floats
+    float* const sEdge = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(fin + 2) + 2 * 64 * sizeof(float) + 15) & ~uintptr_t(15));
+    volatile int* const sOk = reinterpret_cast<volatile int*>(sEdge + 2 * 4 * (KS - 1) * (KS - 1) * 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // Every CTA of this persistent grid is resident from the start, so the
@@ -349,7 +391,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
                 const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
-                const int x0 = tx * tc::BM, y0 = ty * R;
+                const int x0 = tx * TPX, y0 = ty * R;
                 for (int r0 = 0; r0 < ROWS_IN; r0 += RPI, ++it) {
                     const int s = it % S;
                     if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag)) {
@@ -398,7 +440,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dbase = tmem + (uint32_t)(buf * R * COUT_P);
+                const uint32_t dbase = tmem + (uint32_t)(buf * R * NCB);
                 for (int r0 = 0; r0 < ROWS_IN; r0 += RPI, ++it) {
                     const int s = it % S;
                     if (!mbar_wait(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
@@ -408,7 +450,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     tc_fence_after();
 #pragma unroll
                     for (int j = 0; j < RPI; ++j)
-                        issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8, R, WM>(
+                        issue_item<KS, COUT_P, NCC_IN, NCC_W, FP8, R, WM, XF>(
                             r0 + j, dbase, adesc0 + (uint64_t)(s * a_stage + j * a_row), wdesc0, box_step);
                     mma_commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
                 }
@@ -427,12 +469,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int q = warp & 3;  // TMEM lane quarter this warp may access
         const int p = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        int lt = 0;
+        int lt = 0, rowc = 0;
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
             const int buf = lt & 1;
             int ok = 1;
             if (lane == 0) ok = mbar_wait(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
+            if constexpr (XF) {
+                // the rows below hold barriers of the 4 epilogue warps: all of
+                // them take this tile or all give up
+                if (lane == 0) sOk[(lt & 1) * 4 + q] = ok;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                ok = sOk[(lt & 1) * 4] & sOk[(lt & 1) * 4 + 1] & sOk[(lt & 1) * 4 + 2] & sOk[(lt & 1) * 4 + 3];
+            }
             if (!ok) {
                 if (lane == 0) {
                     atomicOr(a.status, tc::ST_TIMEOUT_EPILOGUE);
@@ -442,14 +491,59 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             }
             tc_fence_after();
             const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
-            const int x = tx * tc::BM + p;
+            const int x = tx * TPX + p;
             // bytes per stored pixel of an NHWC output (BF16 hi/lo pairs double it)
             const size_t pix_bytes = (size_t)a.out_cp * (FP8 ? 1 : 2) * (a.split_out ? 2 : 1);
+            if constexpr (XF) {
+                // output pixel p = sum over dx of the accumulator of TMEM lane
+                // (window pixel) p + dx, block dx; lanes p + dx beyond this warp
+                // come from the next warp's first KS - 1 lanes via shared memory
+#pragma unroll 1
+                for (int r = 0; r < R; ++r, ++rowc) {
+                    const int y = ty * R + r;
+                    const uint32_t col = (uint32_t)(buf * R * NCB + (R - 1 - r) * NCB);
+                    float v[KS][16];
+#pragma unroll
+                    for (int dx = 0; dx < KS; ++dx) {
+                        tmem_ld16(tmem + lane_base + col + dx * 16, v[dx]);
+                        tmem_zero16(tmem + lane_base + col + dx * 16);
+                    }
+                    float* const eb = sEdge + (rowc & 1) * (4 * (KS - 1) * (KS - 1) * 16);
+                    if (lane < KS - 1) {
+#pragma unroll
+                        for (int dx = 1; dx < KS; ++dx)
+#pragma unroll
+                            for (int o = 0; o < 16; ++o)
+                                eb[((q * (KS - 1) + lane) * (KS - 1) + dx - 1) * 16 + o] = v[dx][o];
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    float acc[16];
+#pragma unroll
+                    for (int o = 0; o < 16; ++o) acc[o] = v[0][o];
+#pragma unroll
+                    for (int dx = 1; dx < KS; ++dx) {
+                        const int src = lane + dx - 32;  // >= 0: lane src of the next warp
+#pragma unroll
+                        for (int o = 0; o < 16; ++o) {
+                            float sv = __shfl_down_sync(0xffffffffu, v[dx][o], dx);
+                            if (src >= 0) sv = q < 3 ? eb[(((q + 1) * (KS - 1) + src) * (KS - 1) + dx - 1) * 16 + o] : 0.f;
+                            acc[o] += sv;
+                        }
+                    }
+                    if (p < TPX && x < a.W && y < a.H) {
+                        const size_t HW = (size_t)a.H * a.W;
+                        float* z = static_cast<float*>(a.out) + (size_t)b * a.cout * HW + (size_t)y * a.W + x;
+#pragma unroll
+                        for (int o = 0; o < 16; ++o)
+                            if (o < a.cout) z[(size_t)o * HW] = fmaf(acc[o], s_scale[o], s_bias[o]);
+                    }
+                }
+            } else
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const int y = ty * R + r;
                 const bool valid = x < a.W && y < a.H;
-                const uint32_t col = (uint32_t)(buf * R * COUT_P + (R - 1 - r) * COUT_P);
+                const uint32_t col = (uint32_t)(buf * R * NCB + (R - 1 - r) * NCB);
                 const size_t pix = ((size_t)b * a.H + y) * a.W + x;
                 // this group's first channel of the pixel (hi half for BF16)
                 uint8_t* const pbase = static_cast<uint8_t*>(a.out) + pix * pix_bytes + (size_t)a.out_c0 * (FP8 ? 1 : 2);
@@ -621,13 +715,15 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
 // ((dx * ncc + cc) * KS + dy) of a group holds its cg rows of 32 bytes
 // (K-major) of tap (dy, dx) and channel chunk cc, so the KS vertical taps of
 // one (dx, cc) pair are consecutive N blocks.  32-byte swizzled like the TMA
-// writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).  e4m3
+// writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).  With xf
+// (folded horizontal taps) the blocks of a chunk are ordered (dy, dx)
+// instead: block ((cc * KS + dy) * KS + dx).  e4m3
 // weight modes (lo = e4m3(w / s - e4m3(w / s)), s the channel's scale):
 // wm 1: chunks nf .. 2 nf - 1 hold the lo halves of chunks 0 .. nf - 1;
 // wm 2: the same for nf = (ncc - 1) / 2 full chunks, then one chunk with
 // the hi (bytes 0..15) and lo (16..31) of the at most 16 trailing channels.
 __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restrict__ bias, int Cin, int Cout,
-                               int KS, int cout_p, int groups, int ncc, int fp8, int wm,
+                               int KS, int cout_p, int groups, int ncc, int fp8, int wm, int xf,
                                const float* __restrict__ wscale, float act_in_scale, uint8_t* __restrict__ img,
                                float* __restrict__ ep_scale, float* __restrict__ ep_bias) {
     const int ch = fp8 ? 32 : 16;
@@ -641,7 +737,10 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restr
         const int chunk = (i / (ch * cg)) % (KS * KS * ncc);
         const int g = i / (ch * cg * KS * KS * ncc);
         const int n = g * cg + nl;
-        const int dy = chunk % KS, cc = (chunk / KS) % ncc, dx = chunk / (KS * ncc);
+        // block order (dx, cc, dy), or (cc, dy, dx) for folded horizontal taps
+        const int dy = xf ? (chunk / KS) % KS : chunk % KS;
+        const int cc = xf ? chunk / (KS * KS) : (chunk / KS) % ncc;
+        const int dx = xf ? chunk % KS : chunk / (KS * ncc);
         bool lo;
         int cin;
         if (wm == 2 && cc == 2 * nf) {  // trailing half chunk: hi | lo
@@ -701,21 +800,26 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     const int ncc = wm == 1 ? 2 * nch : wm == 2 ? 2 * nch - 1 : nch;
     const float* w = ctx->d_master + L.woff;
     const float* b = ctx->d_master + L.boff;
+    // the last layer of a BF16 context with 64 input and 16 output channels
+    // runs with folded horizontal taps (fewer, wider MMAs; see issue_item)
+    L.xfold = !fp8 && l == c.n_layers - 1 && L.cin_p == 64 && L.cout_p == 16 && L.groups == 1 &&
+              (c.conv_ks == 5 || c.conv_ks == 3);
     if (fp8) {
         wscale_kernel<<<L.cout_p, 128, 0, st>>>(w, L.cin, L.cout, c.conv_ks, L.cout_p, L.wscale);
         WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     }
-    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, wm,
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, wm, L.xfold,
                                         L.wscale, ctx->act_scale[l], static_cast<uint8_t*>(L.wtc), L.ep_scale,
                                         L.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     return WSKPN_OK;
 }
 
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
-    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, tc::rows_per_tile(COUT_P), WM>;
+    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, XF ? xf_rows_per_tile(KS) : tc::rows_per_tile(COUT_P),
+                               WM, XF>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     // programmatic dependent launch: set-up overlaps the previous kernel's
     // tail; the TMA producer waits for that kernel before reading activations
@@ -796,7 +900,12 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     // boxes of 128 + KS - 1 rows of cpb x 32 B, each 1024-byte aligned (128B-swizzle atom)
     a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024);
     a.row_bytes = tc_row_bytes(KS, ncc_in);
-    const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w);
+    const bool xf = L.xfold != 0;  // folded horizontal taps (the image was packed for them)
+    if (xf && !(r.last && !fp8 && cg == 16 && wm == 0)) {
+        err = "conv_tc: folded-tap weights outside the BF16 last layer";
+        return WSKPN_EINVAL;
+    }
+    const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w) + (xf ? tc_xf_bytes(KS) : 0);
     a.stage_bytes = tc_rows_per_item(KS, cg, ncc_in, ncc_w) * a.row_bytes;  // the kernel's own RPI
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
         err = "conv_tc: layer weights and two input stages do not fit in shared memory";
@@ -807,8 +916,8 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     // at least ~120 KB so that exactly one CTA (and one TMEM allocation) lives on an SM
     size_t smem = fixed + (size_t)a.stages * a.stage_bytes;
     if (smem < 120 * 1024) smem = 120 * 1024;
-    a.tiles_x = cdiv(W, tc::BM);
-    a.tiles_y = cdiv(H, tc::rows_per_tile(cg));
+    a.tiles_x = cdiv(W, xf ? tc::BM - (KS - 1) : tc::BM);
+    a.tiles_y = cdiv(H, xf ? xf_rows_per_tile(KS) : tc::rows_per_tile(cg));
     a.ntiles = a.tiles_x * a.tiles_y * B;
     a.status = r.status;
     int nsm = 148;
@@ -816,8 +925,14 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
     wskpn_status (*launch)(const CUtensorMap&, const TcArgs&, size_t, int, cudaStream_t, std::string&) = nullptr;
 #define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
-    if (!launch && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_)    \
-        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_>;
+    if (!launch && !xf && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
+        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_, false>;
+    // the BF16 last layer 64 -> 16 with folded horizontal taps
+    // (hi/lo activations, or single BF16 values when the split is tuned off)
+    if (xf && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
+    if (xf && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
+    if (xf && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
+    if (xf && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
 #define WSKPN_TC_BF16(ks_)                                                                                 \
     WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
     WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
@@ -901,7 +1016,8 @@ wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, c
     }
     wskpn_status s = tc_layer_alloc(L, KS, false, false, err);
     if (s) return s;
-    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, KS, L.cout_p, L.groups, L.cin_p / 16, 0, 0, L.wscale, 1.f,
+    L.xfold = 0;
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, KS, L.cout_p, L.groups, L.cin_p / 16, 0, 0, 0, L.wscale, 1.f,
                                         static_cast<uint8_t*>(L.wtc), L.ep_scale, L.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;

@@ -26,6 +26,7 @@ struct Layer {
     float* wscale = nullptr;    // [cout_p]  FP8 per-output-channel weight scale
     int cin_p = 0, cout_p = 0;  // padded channel counts of the tensor-core layout
     int groups = 1;             // output-channel groups run as separate passes (weights too large for one)
+    int xfold = 0;              // image packed for folded horizontal taps (BF16 last layer, 16 outputs)
 };
 
 std::string validate_config(const wskpn_config* c);
