@@ -137,10 +137,10 @@ __host__ __device__ constexpr size_t tc_fixed_bytes(int KS, int cout_g, int ncc_
 }
 // Folded horizontal taps (XF, the last layer with 16 output channels): the
 // epilogue warps exchange the partial sums of their edge pixels through
-// shared memory, [2 rows][4 warps][KS - 1 lanes][KS - 1 taps][16] floats,
-// plus 2 x 4 flags.
+// shared memory, [2 rows][4 warps][KS - 1 lanes][KS - 1 taps][16 (+1 pad)]
+// floats, plus 2 x 4 flags.
 __host__ __device__ constexpr size_t tc_xf_bytes(int KS) {
-    return (size_t)2 * 4 * (KS - 1) * (KS - 1) * 16 * sizeof(float) + 64;
+    return (size_t)2 * 4 * (KS - 1) * (KS - 1) * 17 * sizeof(float) + 64;
 }
 // Output rows per tile of the folded form: N = (vertical taps) x KS x 16 <= 256.
 __host__ __device__ constexpr int xf_rows_per_tile(int KS) { return 256 / (KS * 16); }
@@ -187,6 +187,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tcgen05.ld of 16 columns without waiting; tmem_wait16 waits for the loads in
+// flight and ties these registers to the wait (so nothing reads them before)
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
@@ -327,7 +346,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     // XF: edge partial sums and the epilogue warps' tile flags, after the 2 x 64 floats
     float* const sEdge = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(fin + 2) + 2 * 64 * sizeof(float) + 15) & ~uintptr_t(15));
-    volatile int* const sOk = reinterpret_cast<volatile int*>(sEdge + 2 * 4 * (KS - 1) * (KS - 1) * 16);
+    volatile int* const sOk = reinterpret_cast<volatile int*>(sEdge + 2 * 4 * (KS - 1) * (KS - 1) * 17);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // Every CTA of this persistent grid is resident from the start, so the
@@ -502,19 +521,25 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 for (int r = 0; r < R; ++r, ++rowc) {
                     const int y = ty * R + r;
                     const uint32_t col = (uint32_t)(buf * R * NCB + (R - 1 - r) * NCB);
+                    uint32_t u[KS][16];
+#pragma unroll
+                    for (int dx = 0; dx < KS; ++dx) tmem_ld16_async(tmem + lane_base + col + dx * 16, u[dx]);
+#pragma unroll
+                    for (int dx = 0; dx < KS; ++dx) tmem_wait16(u[dx]);
+#pragma unroll
+                    for (int dx = 0; dx < KS; ++dx) tmem_zero16(tmem + lane_base + col + dx * 16);
                     float v[KS][16];
 #pragma unroll
-                    for (int dx = 0; dx < KS; ++dx) {
-                        tmem_ld16(tmem + lane_base + col + dx * 16, v[dx]);
-                        tmem_zero16(tmem + lane_base + col + dx * 16);
-                    }
-                    float* const eb = sEdge + (rowc & 1) * (4 * (KS - 1) * (KS - 1) * 16);
+                    for (int dx = 0; dx < KS; ++dx)
+#pragma unroll
+                        for (int o = 0; o < 16; ++o) v[dx][o] = __uint_as_float(u[dx][o]);
+                    float* const eb = sEdge + (rowc & 1) * (4 * (KS - 1) * (KS - 1) * 17);
                     if (lane < KS - 1) {
 #pragma unroll
                         for (int dx = 1; dx < KS; ++dx)
 #pragma unroll
                             for (int o = 0; o < 16; ++o)
-                                eb[((q * (KS - 1) + lane) * (KS - 1) + dx - 1) * 16 + o] = v[dx][o];
+                                eb[((q * (KS - 1) + lane) * (KS - 1) + dx - 1) * 17 + o] = v[dx][o];
                     }
                     asm volatile("bar.sync 1, 128;" ::: "memory");
                     float acc[16];
@@ -526,7 +551,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                         for (int o = 0; o < 16; ++o) {
                             float sv = __shfl_down_sync(0xffffffffu, v[dx][o], dx);
-                            if (src >= 0) sv = q < 3 ? eb[(((q + 1) * (KS - 1) + src) * (KS - 1) + dx - 1) * 16 + o] : 0.f;
+                            if (src >= 0) sv = q < 3 ? eb[(((q + 1) * (KS - 1) + src) * (KS - 1) + dx - 1) * 17 + o] : 0.f;
                             acc[o] += sv;
                         }
                     }
