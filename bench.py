@@ -44,13 +44,13 @@ FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 148, 2032.0
 # profiles/decode_fuse_fwd_1080p.md); a kernel absent here has no capture of
 # its current version
 TRAFFIC = {
-    ("bf16", "conv1 (10->32)"): 344.3e6,
-    ("bf16", "conv2 (32->48)"): 610.6e6,
-    ("bf16", "conv3 (48->64)"): 876.1e6,
-    ("bf16", "conv4 (64->12)"): 645.3e6,
-    ("bf16", "decode_fuse_fwd"): 165.9e6,
-    ("fp32", "decode_fuse_fwd"): 165.9e6,
-    ("fp8", "decode_fuse_fwd"): 165.9e6,
+    ("bf16", "conv1 (10->32)"): 344.2e6,
+    ("bf16", "conv2 (32->48)"): 610.4e6,
+    ("bf16", "conv3 (48->64)"): 876.0e6,
+    ("bf16", "conv4 (64->12)"): 620.2e6,
+    ("bf16", "decode_fuse_fwd"): 165.0e6,
+    ("fp32", "decode_fuse_fwd"): 165.0e6,
+    ("fp8", "decode_fuse_fwd"): 165.0e6,
 }
 
 
