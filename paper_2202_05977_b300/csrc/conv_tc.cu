@@ -236,28 +236,44 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
 template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF>
 __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, uint64_t bd, uint32_t box_step) {
     if constexpr (XF) {
-        // Folded horizontal taps: one MMA per channel chunk covers the input
-        // row's vertical taps dy0..dy1 and all KS horizontal taps, N = nb x KS x
-        // COUT_P columns ordered (dy, dx, channel); accumulator row slots hold
-        // KS x COUT_P columns, and the epilogue adds the dx-shifted partial sums.
-        // The A operand is the unshifted row window (input pixels x0 - PAD ..).
+        // Folded horizontal taps: one MMA per (activation chunk, weight chunk)
+        // product covers the input row's vertical taps dy0..dy1 and all KS
+        // horizontal taps, N = nb x KS x COUT_P columns ordered (dy, dx,
+        // channel); accumulator row slots hold KS x COUT_P columns, and the
+        // epilogue adds the dx-shifted partial sums.  The A operand is the
+        // unshifted row window (input pixels x0 - PAD ..).  Products as below.
         constexpr int NCB = KS * COUT_P;
         static_assert(NCB * (R < KS ? R : KS) <= 256, "MMA N");
         const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
         const int dy1 = ri < KS - 1 ? ri : KS - 1;
         const int nb = dy1 - dy0 + 1;
         if (nb <= 0) return;
-        constexpr uint32_t IDESC0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(tc::BM >> 4) << 24);
+        constexpr uint32_t IDESC0 =
+            (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(tc::BM >> 4) << 24);
         const uint32_t idesc = IDESC0 | ((uint32_t)((nb * NCB) >> 3) << 17);
         constexpr uint32_t b_blk = (COUT_P * tc::ROWB) >> 4;  // one (dy, dx) block of a chunk, 16-byte units
         constexpr int CPB = chunks_per_box(NCC_IN);
         const uint32_t d = dbase + (uint32_t)((R - 1 - (ri - dy0)) * NCB);
+        constexpr int nA = NCC_IN / 2;
+        constexpr int NF = WM == 2 ? nA - 1 : nA;
+        constexpr int NP = WM == 0 ? NCC_IN : 3 * NF + (WM == 2 ? 2 : 0);
 #pragma unroll
-        for (int cc = 0; cc < NCC_IN; ++cc) {
-            const int ccw = cc % NCC_W;
-            const uint64_t a = ad + (uint64_t)((cc / CPB) * box_step + (cc % CPB) * (tc::ROWB >> 4));
-            const uint64_t b = bd + (uint64_t)((ccw * KS + dy0) * KS * b_blk);
-            mma<false, true>(d, a, b, idesc);
+        for (int p = 0; p < NP; ++p) {
+            int ca, cw;
+            if (WM == 0) {
+                ca = p;
+                cw = p % NCC_W;
+            } else if (p < 3 * NF) {
+                const int c = NF > 0 ? p % NF : 0, kind = NF > 0 ? p / NF : 0;
+                ca = kind == 1 ? nA + c : c;
+                cw = kind == 2 ? NF + c : c;
+            } else {
+                ca = p == 3 * NF ? NF : nA + NF;
+                cw = 2 * NF;
+            }
+            const uint64_t a = ad + (uint64_t)((ca / CPB) * box_step + (ca % CPB) * (tc::ROWB >> 4));
+            const uint64_t b = bd + (uint64_t)((cw * KS + dy0) * KS * b_blk);
+            mma<FP8, true>(d, a, b, idesc);
         }
         return;
     }
@@ -317,7 +333,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
     constexpr int NCB = XF ? KS * COUT_P : COUT_P;        // TMEM columns of one output row's accumulators
     constexpr int TPX = XF ? tc::BM - (KS - 1) : tc::BM;  // output pixels per tile row
-    static_assert(!XF || (!FP8 && WM == 0 && COUT_P == 16), "folded taps: BF16, 16 output channels");
+    static_assert(!XF || COUT_P == 16, "folded taps: 16 output channels");
     constexpr uint32_t NCOL = tmem_cols<NCB, R>();
     constexpr int ROWS_IN = R + KS - 1;
     constexpr int CPB = chunks_per_box(NCC_IN);
@@ -825,9 +841,9 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     const int ncc = wm == 1 ? 2 * nch : wm == 2 ? 2 * nch - 1 : nch;
     const float* w = ctx->d_master + L.woff;
     const float* b = ctx->d_master + L.boff;
-    // the last layer of a BF16 context with 64 input and 16 output channels
+    // the last layer of a tensor-core context with 64 input and 16 output channels
     // runs with folded horizontal taps (fewer, wider MMAs; see issue_item)
-    L.xfold = !fp8 && l == c.n_layers - 1 && L.cin_p == 64 && L.cout_p == 16 && L.groups == 1 &&
+    L.xfold = l == c.n_layers - 1 && L.cin_p == 64 && L.cout_p == 16 && L.groups == 1 &&
               (c.conv_ks == 5 || c.conv_ks == 3);
     if (fp8) {
         wscale_kernel<<<L.cout_p, 128, 0, st>>>(w, L.cin, L.cout, c.conv_ks, L.cout_p, L.wscale);
@@ -926,8 +942,8 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024);
     a.row_bytes = tc_row_bytes(KS, ncc_in);
     const bool xf = L.xfold != 0;  // folded horizontal taps (the image was packed for them)
-    if (xf && !(r.last && !fp8 && cg == 16 && wm == 0)) {
-        err = "conv_tc: folded-tap weights outside the BF16 last layer";
+    if (xf && !(r.last && cg == 16)) {
+        err = "conv_tc: folded-tap weights outside the last layer";
         return WSKPN_EINVAL;
     }
     const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w) + (xf ? tc_xf_bytes(KS) : 0);
@@ -954,10 +970,15 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
         launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_, false>;
     // the BF16 last layer 64 -> 16 with folded horizontal taps
     // (hi/lo activations, or single BF16 values when the split is tuned off)
-    if (xf && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
-    if (xf && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
-    if (xf && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
-    if (xf && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
+    if (xf && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
+    if (xf && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
+    if (xf && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
+    if (xf && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
+    // e4m3 hi/lo (three products per chunk) and single-term
+    if (xf && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
+    if (xf && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
+    if (xf && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
+    if (xf && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
 #define WSKPN_TC_BF16(ks_)                                                                                 \
     WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
     WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
