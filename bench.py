@@ -259,8 +259,8 @@ def serving_run(wk_serving, synth, torch, np, n_req, rate, wb, dev):
     for i, (h, w) in enumerate(sizes):
         f = synth.make_frame(h, w, 11 + i)
         frames.append([torch.from_numpy(np.ascontiguousarray(f[k][None])).to(dev) for k in keys])
-    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=4, max_batch=4, mem_budget=8 << 30,
-                            batch_window_us=200)
+    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=2, max_batch=4, mem_budget=8 << 30,
+                            batch_window_us=0)
     n_streams = 8
     outs = {(s, r): torch.empty((1, 3, *sizes[r]), device=dev) for s in range(n_streams) for r in range(3)}
     busy = {}
@@ -272,8 +272,8 @@ def serving_run(wk_serving, synth, torch, np, n_req, rate, wb, dev):
         t = srv.submit(0, *frames[r], outs[(0, r)])
         srv.wait(t, 60000)
     srv.stop()
-    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=4, max_batch=4, mem_budget=8 << 30,
-                            batch_window_us=200)
+    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=2, max_batch=4, mem_budget=8 << 30,
+                            batch_window_us=0)
     for r in range(3):  # capture outside the measured stream
         t = srv.submit(0, *frames[r], outs[(0, r)])
         srv.wait(t, 60000)
