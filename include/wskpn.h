@@ -471,14 +471,17 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *   WSKPN_TUNE_HOST_BANDS: bands of the wskpn_denoise_host pipeline; 0 =
  *     automatic (one per ~240 rows, at most 8, none below 480 rows), 1 = no
  *     banding, n = n bands.
- *   WSKPN_TUNE_HOST_FIRST_BAND: height of the pipeline's first band in % of
- *     the others (10 .. 100, default 100).
+ *   WSKPN_TUNE_HOST_FIRST_BAND, WSKPN_TUNE_HOST_LAST_BAND: height of the
+ *     pipeline's first / last band in % of the others (10 .. 100; defaults
+ *     100 and 70: a shorter last band leaves less work after the last
+ *     upload).
  * Errors: EINVAL for an unknown key or value. */
 #define WSKPN_TUNE_TC_SPLIT 2
 #define WSKPN_TUNE_TRAIN_RECOMPUTE 3
 #define WSKPN_TUNE_FP8_SPLIT 4
 #define WSKPN_TUNE_HOST_BANDS 5
 #define WSKPN_TUNE_HOST_FIRST_BAND 6
+#define WSKPN_TUNE_HOST_LAST_BAND 7
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
 
 /* Reads and clears the context's device status word after synchronising

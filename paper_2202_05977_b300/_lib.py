@@ -19,6 +19,7 @@ TUNE_TRAIN_RECOMPUTE = 3
 TUNE_FP8_SPLIT = 4
 TUNE_HOST_BANDS = 5
 TUNE_HOST_FIRST_BAND = 6
+TUNE_HOST_LAST_BAND = 7
 
 
 class Config(ctypes.Structure):

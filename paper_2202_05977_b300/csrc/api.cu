@@ -307,17 +307,50 @@ static int band_halo(const wskpn_config& c) {
     return c.n_layers * (c.conv_ks / 2) + kmax / 2;
 }
 
+// The network's workspaces (activations, logits) for a call of `px` pixels,
+// moved to the second half of the context's buffers while the object lives:
+// two band calls of at most ws_pixels / 2 pixels each can then be in flight
+// on two streams (kernels take the buffer addresses at launch).
+struct WorkspaceShift {
+    wskpn_ctx* c;
+    void *ta, *tb;
+    float *fa, *fb, *z;
+    WorkspaceShift(wskpn_ctx* ctx, bool shift, size_t px) : c(ctx) {
+        ta = c->d_tcA, tb = c->d_tcB, fa = c->d_actA, fb = c->d_actB, z = c->d_z;
+        if (!shift) return;
+        const wskpn_config& cfg = c->cfg;
+        auto up = [](size_t b) { return (b + 255) / 256 * 256; };  // keep 256-byte alignment
+        if (c->d_tcA) c->d_tcA = static_cast<uint8_t*>(ta) + up(px * tc_act_bytes_per_pixel(cfg, 0));
+        if (c->d_tcB) c->d_tcB = static_cast<uint8_t*>(tb) + up(px * tc_act_bytes_per_pixel(cfg, 1));
+        int wa = 0, wb = 0;
+        for (int l = 0; l < cfg.n_layers; ++l) (l % 2 == 0 ? wa : wb) = std::max(l % 2 == 0 ? wa : wb, cfg.widths[l]);
+        if (c->d_actA) c->d_actA = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(fa) + up(px * wa * 4));
+        if (c->d_actB) c->d_actB = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(fb) + up(px * wb * 4));
+        c->d_z = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(z) + up(px * cfg.widths[cfg.n_layers] * 4));
+    }
+    ~WorkspaceShift() { c->d_tcA = ta, c->d_tcB = tb, c->d_actA = fa, c->d_actB = fb, c->d_z = z; }
+};
+
 static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, int batch, int h, int w,
                                         float* host_out, int nb, cudaStream_t st) {
     const int halo = band_halo(ctx->cfg);
-    // band k covers rows [yb[k], yb[k + 1]); the first may be shorter, so
-    // that the first computation starts sooner
+    // band k covers rows [yb[k], yb[k + 1]); the first may be shorter (the
+    // first computation starts sooner) and the last (less work after the
+    // last upload)
     std::vector<int> yb(nb + 1, h);
     {
-        const double w0 = ctx->host_first_pct / 100.0, unit = h / (w0 + nb - 1);
+        double wgt[64];
+        double tot = 0.0;
+        for (int k = 0; k < nb; ++k) {
+            wgt[k] = nb == 1 ? 1.0 : k == 0 ? ctx->host_first_pct / 100.0 : k == nb - 1 ? ctx->host_last_pct / 100.0 : 1.0;
+            tot += wgt[k];
+        }
+        double acc = 0.0;
         yb[0] = 0;
-        yb[1] = std::max(1, std::min(h, (int)(w0 * unit + 0.5)));
-        for (int k = 2; k < nb; ++k) yb[k] = std::min(h, yb[1] + (int)((k - 1) * (h - yb[1]) / (double)(nb - 1) + 0.5));
+        for (int k = 1; k < nb; ++k) {
+            acc += wgt[k - 1];
+            yb[k] = std::max(yb[k - 1] + 1, std::min(h - (nb - k), (int)(h * acc / tot + 0.5)));
+        }
     }
     int bh = 0;
     for (int k = 0; k < nb; ++k) bh = std::max(bh, yb[k + 1] - yb[k]);
@@ -329,6 +362,17 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
         ctx->band_events.resize(6);
         for (auto& e : ctx->band_events)
             WSKPN_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), ctx->err);
+    }
+    // consecutive bands compute on two streams (one's tail overlaps the
+    // next one's start) when two band workspaces fit in the context's
+    // buffers; not while per-stage profiling records events on one stream
+    const size_t band_px = (size_t)ext * w;
+    const bool two = !ctx->prof && 2 * (band_px + 256) <= ctx->ws_pixels;
+    if (two && !ctx->band_stream)
+        WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->band_stream, cudaStreamNonBlocking), ctx->err);
+    if (two) {  // the second stream starts after what the caller queued before
+        WSKPN_CUDA_TRY(cudaEventRecord(ctx->band_events[0], st), ctx->err);
+        WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->band_stream, ctx->band_events[0], 0), ctx->err);
     }
     if (ctx->band_floats < need) {
         cudaFree(ctx->d_band[0]);
@@ -369,12 +413,18 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
             }
             float* dout = p;
             WSKPN_CUDA_TRY(cudaEventRecord(ev[slot], ctx->up_stream), ctx->err);
-            // compute after the upload, and after the slot's previous download
-            WSKPN_CUDA_TRY(cudaStreamWaitEvent(st, ev[slot], 0), ctx->err);
-            if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(st, ev[4 + slot], 0), ctx->err);
-            wskpn_status s = wskpn_denoise(ctx, &f, 1, eh, w, dout, st);
-            if (s) return s;
-            WSKPN_CUDA_TRY(cudaEventRecord(ev[2 + slot], st), ctx->err);
+            // compute after the upload, and after the slot's previous download;
+            // with two compute streams, slot 1's jobs use the second stream and
+            // the second half of the workspaces
+            cudaStream_t cs = two && slot ? ctx->band_stream : st;
+            WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[slot], 0), ctx->err);
+            if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[4 + slot], 0), ctx->err);
+            {
+                WorkspaceShift shift(ctx, two && slot, band_px);
+                wskpn_status s = wskpn_denoise(ctx, &f, 1, eh, w, dout, cs);
+                if (s) return s;
+            }
+            WSKPN_CUDA_TRY(cudaEventRecord(ev[2 + slot], cs), ctx->err);
             // download the central rows
             WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->down_stream, ev[2 + slot], 0), ctx->err);
             for (int c = 0; c < 3; ++c)
@@ -388,6 +438,7 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
     }
     WSKPN_CUDA_TRY(cudaStreamSynchronize(ctx->down_stream), ctx->err);
     WSKPN_CUDA_TRY(cudaStreamSynchronize(st), ctx->err);
+    if (two) WSKPN_CUDA_TRY(cudaStreamSynchronize(ctx->band_stream), ctx->err);
     return WSKPN_OK;
 }
 
@@ -534,6 +585,10 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
     }
     if (key == WSKPN_TUNE_HOST_FIRST_BAND && value >= 10 && value <= 100) {
         ctx->host_first_pct = value;
+        return WSKPN_OK;
+    }
+    if (key == WSKPN_TUNE_HOST_LAST_BAND && value >= 10 && value <= 100) {
+        ctx->host_last_pct = value;
         return WSKPN_OK;
     }
     if (key == WSKPN_TUNE_FP8_SPLIT && (value == 0 || value == 1) && ctx->cfg.prec == WSKPN_FP8) {

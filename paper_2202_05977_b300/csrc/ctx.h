@@ -51,6 +51,7 @@ struct wskpn_ctx {
     // banded host calls: two copy streams (upload, download) and the staging
     // of two bands in flight
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    cudaStream_t band_stream = nullptr;  // second compute stream of the host-buffer pipeline
     float* d_band[2] = {nullptr, nullptr};  // [10 + 3][band_rows][max_w]
     size_t band_floats = 0;
     std::vector<cudaEvent_t> band_events;   // 4 per band slot ring (uploaded, computed, downloaded)
@@ -63,6 +64,7 @@ struct wskpn_ctx {
     int train_tc_recompute = 1;  // backward recomputes on the tensor cores (WSKPN_TUNE_TRAIN_RECOMPUTE)
     int host_bands = 0;         // bands of the host-buffer pipeline, 0 = automatic (WSKPN_TUNE_HOST_BANDS)
     int host_first_pct = 100;   // first band's height in % of the others (WSKPN_TUNE_HOST_FIRST_BAND)
+    int host_last_pct = 70;     // last band's height in % of the others (WSKPN_TUNE_HOST_LAST_BAND)
     void* train = nullptr;  // training workspaces (train.cu), allocated by the first training call
     // stage profiling: one event set (n_layers + 3 events) per recorded call
     bool prof = false;
