@@ -47,11 +47,13 @@ struct WgradArgs {
     int B, H, W, Cin, Cout, tiles_x, tiles_y, ntiles, G;
 };
 
-// Grid (G, Cin chunks).  Lane = output channel (o and o + 32), warp w owns
-// KS of the CC x KS (channel, dy) pairs; each thread keeps 2 x KS x KS
-// partial sums and slides a KS-wide window of x along each tile row.
-template <int KS>
+// Grid (G, Cin chunks).  Lane = output channel (o, and o + 32 when NO = 64
+// output channels are kept; NO = 32 serves layers of at most 32), warp w
+// owns KS of the CC x KS (channel, dy) pairs; each thread keeps NO / 32 x KS
+// x KS partial sums and slides a KS-wide window of x along each tile row.
+template <int KS, int NO>
 __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
+    constexpr int U = NO / 32;  // output channels per lane
     constexpr int PAD = KS / 2, IW = wg::TW + KS - 1, IH = wg::TH + KS - 1;
     constexpr int COMBOS = wg::CC * KS;           // (c, dy) pairs per chunk
     constexpr int CPW = COMBOS / (wg::THREADS / 32);  // pairs per warp
@@ -63,10 +65,12 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
     const int g = blockIdx.x, c0 = blockIdx.y * wg::CC;
     const int H = a.H, W = a.W;
     const size_t HW = (size_t)H * W;
-    float acc[2][CPW][KS];
-    float dbacc[2] = {0.f, 0.f};
+    float acc[U][CPW][KS];
+    float dbacc[U];
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int u = 0; u < U; ++u) dbacc[u] = 0.f;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int k = 0; k < CPW; ++k)
 #pragma unroll
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
             const bool in = c0 + c < a.Cin && gy >= 0 && gy < H && gx >= 0 && gx < W;
             sx[c][iy][ix] = in ? xb[(size_t)(c0 + c) * HW + (size_t)gy * W + gx] : 0.f;
         }
-        for (int i = tid; i < wg::TH * wg::TW * wg::MAXO; i += wg::THREADS) {
+        for (int i = tid; i < wg::TH * wg::TW * NO; i += wg::THREADS) {
             const int o = i / (wg::TH * wg::TW), p = i % (wg::TH * wg::TW);
             const int gy = y0 + p / wg::TW, gx = x0 + p % wg::TW;
             const bool in = o < a.Cout && gy < H && gx < W;
@@ -101,11 +105,12 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
             }
 #pragma unroll
             for (int px = 0; px < wg::TW; ++px) {
-                const float g0 = sg[py * wg::TW + px][lane], g1 = sg[py * wg::TW + px][lane + 32];
-                if (blockIdx.y == 0 && warp == 0) {
-                    dbacc[0] += g0;
-                    dbacc[1] += g1;
-                }
+                float gv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) gv[u] = sg[py * wg::TW + px][lane + 32 * u];
+                if (blockIdx.y == 0 && warp == 0)
+#pragma unroll
+                    for (int u = 0; u < U; ++u) dbacc[u] += gv[u];
 #pragma unroll
                 for (int k = 0; k < CPW; ++k) {
                     const int combo = warp * CPW + k, c = combo / KS, dy = combo % KS;
@@ -113,8 +118,8 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
 #pragma unroll
                     for (int d = 0; d < KS; ++d) {
                         const float xv = win[k][(px + d) % KS];
-                        acc[0][k][d] = fmaf(g0, xv, acc[0][k][d]);
-                        acc[1][k][d] = fmaf(g1, xv, acc[1][k][d]);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) acc[u][k][d] = fmaf(gv[u], xv, acc[u][k][d]);
                     }
                 }
             }
@@ -129,13 +134,13 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
 #pragma unroll
         for (int d = 0; d < KS; ++d)
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-                part[((size_t)c * KS * KS + dy * KS + d) * wg::MAXO + lane + 32 * u] = acc[u][k][d];
+            for (int u = 0; u < 2; ++u)  // channels this kernel does not keep are zero
+                part[((size_t)c * KS * KS + dy * KS + d) * wg::MAXO + lane + 32 * u] = u < U ? acc[u][k][d] : 0.f;
     }
     if (blockIdx.y == 0 && warp == 0) {
         float* pdb = a.part + (size_t)a.G * cpad * KS * KS * wg::MAXO + (size_t)g * wg::MAXO;
         pdb[lane] = dbacc[0];
-        pdb[lane + 32] = dbacc[1];
+        pdb[lane + 32] = U > 1 ? dbacc[U - 1] : 0.f;
     }
 }
 
@@ -187,13 +192,11 @@ wskpn_status launch_wgrad(const float* const* x, const float* const* gy, int B, 
     const int nchunks = cdiv(Cin, wg::CC);
     dim3 grid(G, nchunks);
     const size_t smem = (size_t)(wg::CC * (wg::TH + KS - 1) * (wg::TW + KS - 1) + wg::TH * wg::TW * wg::MAXO) * sizeof(float);
-    if (KS == 5) {
-        WSKPN_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
-        wgrad_kernel<5><<<grid, wg::THREADS, smem, st>>>(a);
-    } else {
-        WSKPN_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
-        wgrad_kernel<3><<<grid, wg::THREADS, smem, st>>>(a);
-    }
+    // layers of at most 32 output channels keep one channel per lane
+    void (*kern)(WgradArgs) = KS == 5 ? (Cout <= 32 ? wgrad_kernel<5, 32> : wgrad_kernel<5, 64>)
+                                      : (Cout <= 32 ? wgrad_kernel<3, 32> : wgrad_kernel<3, 64>);
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
+    kern<<<grid, wg::THREADS, smem, st>>>(a);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     wgrad_reduce_kernel<<<148, 256, 0, st>>>(part, G, nchunks * wg::CC, Cin, Cout, KS * KS, dw, db);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
