@@ -51,18 +51,25 @@ struct WgradArgs {
 // output channels are kept; NO = 32 serves layers of at most 32), warp w
 // owns KS of the CC x KS (channel, dy) pairs; each thread keeps NO / 32 x KS
 // x KS partial sums and slides a KS-wide window of x along each tile row.
+// NO = 16 (at most 16 output channels): each half-warp is one set of 16
+// channels and owns its own pairs, and a chunk holds 2 CC input channels.
 template <int KS, int NO>
 __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
-    constexpr int U = NO / 32;  // output channels per lane
+    constexpr bool HALF = NO == 16;
+    constexpr int U = HALF ? 1 : NO / 32;        // output channels per lane
+    constexpr int CCT = HALF ? 2 * wg::CC : wg::CC;  // input channels per chunk
     constexpr int PAD = KS / 2, IW = wg::TW + KS - 1, IH = wg::TH + KS - 1;
-    constexpr int COMBOS = wg::CC * KS;           // (c, dy) pairs per chunk
-    constexpr int CPW = COMBOS / (wg::THREADS / 32);  // pairs per warp
-    static_assert(COMBOS % (wg::THREADS / 32) == 0, "pairs per warp");
+    constexpr int COMBOS = CCT * KS;             // (c, dy) pairs per chunk
+    constexpr int GROUPS = (wg::THREADS / 32) * (HALF ? 2 : 1);  // warps, or half-warps
+    constexpr int CPW = COMBOS / GROUPS;         // pairs per warp (half-warp)
+    static_assert(COMBOS % GROUPS == 0, "pairs per warp");
     extern __shared__ float wg_smem[];
-    float (*sx)[IH][IW] = reinterpret_cast<float (*)[IH][IW]>(wg_smem);                       // [CC][IH][IW]
-    float (*sg)[wg::MAXO] = reinterpret_cast<float (*)[wg::MAXO]>(wg_smem + wg::CC * IH * IW);  // [TH*TW][MAXO]
+    float (*sx)[IH][IW] = reinterpret_cast<float (*)[IH][IW]>(wg_smem);                    // [CCT][IH][IW]
+    float (*sg)[wg::MAXO] = reinterpret_cast<float (*)[wg::MAXO]>(wg_smem + CCT * IH * IW);  // [TH*TW][MAXO]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = blockIdx.x, c0 = blockIdx.y * wg::CC;
+    const int grp = HALF ? warp * 2 + (lane >> 4) : warp;  // owner of pairs grp * CPW ..
+    const int ol = HALF ? lane & 15 : lane;                // this lane's output channel
+    const int g = blockIdx.x, c0 = blockIdx.y * CCT;
     const int H = a.H, W = a.W;
     const size_t HW = (size_t)H * W;
     float acc[U][CPW][KS];
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
         const float* __restrict__ xb = a.x.p[b];
         const float* __restrict__ gb = a.gy.p[b];
         __syncthreads();
-        for (int i = tid; i < wg::CC * IH * IW; i += wg::THREADS) {
+        for (int i = tid; i < CCT * IH * IW; i += wg::THREADS) {
             const int c = i / (IH * IW), rem = i % (IH * IW), iy = rem / IW, ix = rem % IW;
             const int gy = y0 + iy - PAD, gx = x0 + ix - PAD;
             const bool in = c0 + c < a.Cin && gy >= 0 && gy < H && gx >= 0 && gx < W;
@@ -99,7 +106,7 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
             float win[CPW][KS];
 #pragma unroll
             for (int k = 0; k < CPW; ++k) {
-                const int combo = warp * CPW + k, c = combo / KS, dy = combo % KS;
+                const int combo = grp * CPW + k, c = combo / KS, dy = combo % KS;
 #pragma unroll
                 for (int d = 0; d < KS - 1; ++d) win[k][d] = sx[c][py + dy][d];
             }
@@ -107,13 +114,13 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
             for (int px = 0; px < wg::TW; ++px) {
                 float gv[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) gv[u] = sg[py * wg::TW + px][lane + 32 * u];
-                if (blockIdx.y == 0 && warp == 0)
+                for (int u = 0; u < U; ++u) gv[u] = sg[py * wg::TW + px][ol + 32 * u];
+                if (blockIdx.y == 0 && grp == 0)
 #pragma unroll
                     for (int u = 0; u < U; ++u) dbacc[u] += gv[u];
 #pragma unroll
                 for (int k = 0; k < CPW; ++k) {
-                    const int combo = warp * CPW + k, c = combo / KS, dy = combo % KS;
+                    const int combo = grp * CPW + k, c = combo / KS, dy = combo % KS;
                     win[k][(px + KS - 1) % KS] = sx[c][py + dy][px + KS - 1];
 #pragma unroll
                     for (int d = 0; d < KS; ++d) {
@@ -126,21 +133,21 @@ __global__ void __launch_bounds__(wg::THREADS) wgrad_kernel(WgradArgs a) {
         }
     }
     // partial [g][c][dy*KS+dx][o]
-    const int cpad = gridDim.y * wg::CC;
+    // (entries of channels o >= NO are never read: the layer has fewer)
+    const int cpad = gridDim.y * CCT;
     float* part = a.part + (size_t)g * cpad * KS * KS * wg::MAXO;
 #pragma unroll
     for (int k = 0; k < CPW; ++k) {
-        const int combo = warp * CPW + k, c = c0 + combo / KS, dy = combo % KS;
+        const int combo = grp * CPW + k, c = c0 + combo / KS, dy = combo % KS;
 #pragma unroll
         for (int d = 0; d < KS; ++d)
 #pragma unroll
-            for (int u = 0; u < 2; ++u)  // channels this kernel does not keep are zero
-                part[((size_t)c * KS * KS + dy * KS + d) * wg::MAXO + lane + 32 * u] = u < U ? acc[u][k][d] : 0.f;
+            for (int u = 0; u < U; ++u) part[((size_t)c * KS * KS + dy * KS + d) * wg::MAXO + ol + 32 * u] = acc[u][k][d];
     }
-    if (blockIdx.y == 0 && warp == 0) {
+    if (blockIdx.y == 0 && grp == 0) {
         float* pdb = a.part + (size_t)a.G * cpad * KS * KS * wg::MAXO + (size_t)g * wg::MAXO;
-        pdb[lane] = dbacc[0];
-        pdb[lane + 32] = U > 1 ? dbacc[U - 1] : 0.f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) pdb[ol + 32 * u] = dbacc[u];
     }
 }
 
@@ -164,7 +171,7 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, int G, int c
 }
 
 size_t wgrad_part_floats(int Cin, int KS, int G) {
-    const int cpad = (Cin + wg::CC - 1) / wg::CC * wg::CC;
+    const int cpad = (Cin + 2 * wg::CC - 1) / (2 * wg::CC) * (2 * wg::CC);  // chunks of CC or 2 CC channels
     return (size_t)G * cpad * KS * KS * wg::MAXO + (size_t)G * wg::MAXO;
 }
 
@@ -189,16 +196,18 @@ wskpn_status launch_wgrad(const float* const* x, const float* const* gy, int B, 
     a.tiles_y = cdiv(H, wg::TH);
     a.ntiles = a.tiles_x * a.tiles_y * B;
     a.G = G;
-    const int nchunks = cdiv(Cin, wg::CC);
+    // layers of at most 16 / 32 output channels keep them on half-warps / one per lane
+    const int no = Cout <= 16 ? 16 : Cout <= 32 ? 32 : 64;
+    const int cct = no == 16 ? 2 * wg::CC : wg::CC;  // input channels per chunk
+    const int nchunks = cdiv(Cin, cct);
     dim3 grid(G, nchunks);
-    const size_t smem = (size_t)(wg::CC * (wg::TH + KS - 1) * (wg::TW + KS - 1) + wg::TH * wg::TW * wg::MAXO) * sizeof(float);
-    // layers of at most 32 output channels keep one channel per lane
-    void (*kern)(WgradArgs) = KS == 5 ? (Cout <= 32 ? wgrad_kernel<5, 32> : wgrad_kernel<5, 64>)
-                                      : (Cout <= 32 ? wgrad_kernel<3, 32> : wgrad_kernel<3, 64>);
+    const size_t smem = (size_t)(cct * (wg::TH + KS - 1) * (wg::TW + KS - 1) + wg::TH * wg::TW * wg::MAXO) * sizeof(float);
+    void (*kern)(WgradArgs) = KS == 5 ? (no == 16 ? wgrad_kernel<5, 16> : no == 32 ? wgrad_kernel<5, 32> : wgrad_kernel<5, 64>)
+                                      : (no == 16 ? wgrad_kernel<3, 16> : no == 32 ? wgrad_kernel<3, 32> : wgrad_kernel<3, 64>);
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     kern<<<grid, wg::THREADS, smem, st>>>(a);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
-    wgrad_reduce_kernel<<<148, 256, 0, st>>>(part, G, nchunks * wg::CC, Cin, Cout, KS * KS, dw, db);
+    wgrad_reduce_kernel<<<148, 256, 0, st>>>(part, G, nchunks * cct, Cin, Cout, KS * KS, dw, db);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
