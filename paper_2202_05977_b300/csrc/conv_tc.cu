@@ -357,11 +357,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     uint64_t* fin = wbar + 1;
     volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(fin + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(fin + 1) + 1;
-    float* s_scale = reinterpret_cast<float*>(fin + 2);  // [COUT_P]
+    // [COUT_P], 16-byte aligned for vector loads (the barriers end 8 bytes past a 16-byte boundary)
+    float* s_scale = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(fin + 2) + 15) & ~uintptr_t(15));
     float* s_bias = s_scale + COUT_P;                     // [COUT_P]
     // XF: edge partial sums and the epilogue warps' tile flags, after the 2 x 64 floats
     float* const sEdge = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(fin + 2) + 2 * 64 * sizeof(float) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(s_scale) + 2 * 64 * sizeof(float) + 15) & ~uintptr_t(15));
     volatile int* const sOk = reinterpret_cast<volatile int*>(sEdge + 2 * 4 * (KS - 1) * (KS - 1) * 17);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -574,9 +575,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     if (p < TPX && x < a.W && y < a.H) {
                         const size_t HW = (size_t)a.H * a.W;
                         float* z = static_cast<float*>(a.out) + (size_t)b * a.cout * HW + (size_t)y * a.W + x;
+                        const float4* s4 = reinterpret_cast<const float4*>(s_scale);
+                        const float4* b4 = reinterpret_cast<const float4*>(s_bias);
 #pragma unroll
-                        for (int o = 0; o < 16; ++o)
-                            if (o < a.cout) z[(size_t)o * HW] = fmaf(acc[o], s_scale[o], s_bias[o]);
+                        for (int j4 = 0; j4 < 4; ++j4) {
+                            const float4 ss = s4[j4], bb = b4[j4];
+                            const float sj[4] = {ss.x, ss.y, ss.z, ss.w}, bj[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (4 * j4 + k < a.cout) z[(size_t)(4 * j4 + k) * HW] = fmaf(acc[4 * j4 + k], sj[k], bj[k]);
+                        }
                     }
                 }
             } else
@@ -594,11 +602,27 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     tmem_ld16(tmem + lane_base + col + c16 * 16, v);
                     tmem_zero16(tmem + lane_base + col + c16 * 16);  // ready for the buffer's next tile
                     if (!valid) continue;
+                    {
+                        // BF16 accumulators need no rescale (the scale is 1)
+                        const float4* b4 = reinterpret_cast<const float4*>(s_bias + c16 * 16);
+                        const float4* s4 = reinterpret_cast<const float4*>(s_scale + c16 * 16);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int o = c16 * 16 + j;
-                        v[j] = fmaf(v[j], s_scale[o], s_bias[o]);
-                        if (a.relu) v[j] = fmaxf(v[j], 0.f);
+                        for (int j4 = 0; j4 < 4; ++j4) {
+                            const float4 bb = b4[j4];
+                            const float bj[4] = {bb.x, bb.y, bb.z, bb.w};
+                            if constexpr (FP8) {
+                                const float4 ss = s4[j4];
+                                const float sj[4] = {ss.x, ss.y, ss.z, ss.w};
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) v[4 * j4 + k] = fmaf(v[4 * j4 + k], sj[k], bj[k]);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) v[4 * j4 + k] += bj[k];
+                            }
+                        }
+                        if (a.relu)
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
                     }
                     if (a.last) {
                         const size_t HW = (size_t)a.H * a.W;
