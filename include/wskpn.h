@@ -457,10 +457,15 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     halves against the same BF16 weights, which removes the activation
  *     rounding error at twice the MMA work (default); 0 = one BF16 value.
  *   WSKPN_TUNE_TRAIN_RECOMPUTE (BF16 only): how wskpn_backward recomputes
- *     the activations: 1 = with the context's own tensor-core convolutions,
- *     as the forward computed them (default; needs TC_SPLIT = 1); 0 = in
- *     FP32 with the FP32 weights (the ReLU masks are then those of the FP32
+ *     the activations and forms the input gradients: 1 = activations with
+ *     the context's own tensor-core convolutions, as the forward computed
+ *     them, and each layer's input gradient as a tensor-core convolution of
+ *     the gradient (BF16 hi/lo pairs) with the transposed, flipped BF16
+ *     weights (default; needs TC_SPLIT = 1); 2 = the same activations, input
+ *     gradients in FP32 SIMT with the FP32 weights; 0 = everything in FP32
+ *     with the FP32 weights (the ReLU masks are then those of the FP32
  *     network, which brings the gradient closer to the FP32/FP64 one).
+ *     Weight gradients are FP32 SIMT in every mode.
  *   WSKPN_TUNE_FP8_SPLIT (FP8 only): 1 = every e4m3 activation and weight
  *     is a hi/lo pair in one scale (x / s = hi + lo, lo = e4m3 of the
  *     residual) and each convolution sums A_hi W_hi + A_lo W_hi + A_hi W_lo,

@@ -575,7 +575,7 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
         ctx->tc_split = value;
         return WSKPN_OK;
     }
-    if (key == WSKPN_TUNE_TRAIN_RECOMPUTE && (value == 0 || value == 1)) {
+    if (key == WSKPN_TUNE_TRAIN_RECOMPUTE && value >= 0 && value <= 2) {
         ctx->train_tc_recompute = value;
         return WSKPN_OK;
     }

@@ -902,6 +902,65 @@ static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t 
     return WSKPN_OK;
 }
 
+using TcLaunch = wskpn_status (*)(const CUtensorMap&, const TcArgs&, size_t, int, cudaStream_t, std::string&);
+
+// The kernel instantiation for a layer shape: KS, output channels of one
+// group, input chunks per row (hi/lo included), weight-image chunks,
+// precision, e4m3 weight mode, folded taps.  nullptr when none is built.
+static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8, int wm, bool xf) {
+    TcLaunch launch = nullptr;
+#define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
+    if (!launch && !xf && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
+        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_, false>;
+    // the BF16 last layer 64 -> 16 with folded horizontal taps
+    // (hi/lo activations, or single BF16 values when the split is tuned off)
+    if (xf && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
+    if (xf && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
+    if (xf && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
+    if (xf && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
+    // e4m3 hi/lo (three products per chunk) and single-term
+    if (xf && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
+    if (xf && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
+    if (xf && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
+    if (xf && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
+#define WSKPN_TC_BF16(ks_)                                                                                 \
+    WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 64, 3, 3, false, 0) WSKPN_TC_CASE(ks_, 64, 6, 3, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 16, 4, 4, false, 0) WSKPN_TC_CASE(ks_, 16, 8, 4, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 32, 4, 4, false, 0) WSKPN_TC_CASE(ks_, 32, 8, 4, false, 0)
+// e4m3: single-term (widths 10-32-48-64-12 and 64-64), and hi/lo pairs of
+// activations and weights (10 and 48 input channels with a trailing half
+// chunk; 5x5 64-64 layers as two 32-channel output groups)
+#define WSKPN_TC_FP8(ks_)                                                                                  \
+    WSKPN_TC_CASE(ks_, 32, 1, 1, true, 0) WSKPN_TC_CASE(ks_, 48, 1, 1, true, 0)                            \
+    WSKPN_TC_CASE(ks_, 64, 2, 2, true, 0) WSKPN_TC_CASE(ks_, 16, 2, 2, true, 0)                            \
+    WSKPN_TC_CASE(ks_, 32, 2, 1, true, 2) WSKPN_TC_CASE(ks_, 48, 2, 2, true, 1)                            \
+    WSKPN_TC_CASE(ks_, 64, 4, 3, true, 2) WSKPN_TC_CASE(ks_, 16, 4, 4, true, 1)                            \
+    WSKPN_TC_CASE(ks_, 32, 4, 4, true, 1) WSKPN_TC_CASE(ks_, 64, 4, 4, true, 1)
+// input gradients of the training step (hi/lo gradients, weights transposed
+// and flipped): 12 -> 64, 64 -> 48, 48 -> 32 (64 -> 64 runs as two 32-channel
+// groups, a forward case above)
+#define WSKPN_TC_DGRAD(ks_)                                                                                \
+    WSKPN_TC_CASE(ks_, 64, 2, 1, false, 0) WSKPN_TC_CASE(ks_, 48, 8, 4, false, 0)                          \
+    WSKPN_TC_CASE(ks_, 32, 6, 3, false, 0)
+// the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
+// 112-48, 80-32 and the heads 48-5, 32-5
+#define WSKPN_TC_UNET                                                                                      \
+    WSKPN_TC_CASE(3, 32, 4, 2, false, 0) WSKPN_TC_CASE(3, 48, 6, 3, false, 0)                              \
+    WSKPN_TC_CASE(3, 64, 8, 4, false, 0) WSKPN_TC_CASE(3, 48, 14, 7, false, 0)                             \
+    WSKPN_TC_CASE(3, 32, 10, 5, false, 0) WSKPN_TC_CASE(3, 16, 6, 3, false, 0)                             \
+    WSKPN_TC_CASE(3, 16, 4, 2, false, 0)
+    WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3) WSKPN_TC_UNET
+    WSKPN_TC_DGRAD(5) WSKPN_TC_DGRAD(3)
+#undef WSKPN_TC_DGRAD
+#undef WSKPN_TC_UNET
+#undef WSKPN_TC_FP8
+#undef WSKPN_TC_BF16
+#undef WSKPN_TC_CASE
+    return launch;
+}
+
 // One conv layer on the tensor cores, independent of a context.
 // in: NHWC [B][H][W][cin_p x (split_in ? 2 : 1)] (BF16 or e4m3); out: NHWC
 // with out_cp channels per stored pixel (x 2 when split_out), this layer's
@@ -988,48 +1047,7 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, r.device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
-    wskpn_status (*launch)(const CUtensorMap&, const TcArgs&, size_t, int, cudaStream_t, std::string&) = nullptr;
-#define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
-    if (!launch && !xf && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
-        launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_, false>;
-    // the BF16 last layer 64 -> 16 with folded horizontal taps
-    // (hi/lo activations, or single BF16 values when the split is tuned off)
-    if (xf && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
-    if (xf && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
-    if (xf && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
-    if (xf && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
-    // e4m3 hi/lo (three products per chunk) and single-term
-    if (xf && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
-    if (xf && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
-    if (xf && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
-    if (xf && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
-#define WSKPN_TC_BF16(ks_)                                                                                 \
-    WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
-    WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
-    WSKPN_TC_CASE(ks_, 64, 3, 3, false, 0) WSKPN_TC_CASE(ks_, 64, 6, 3, false, 0)                          \
-    WSKPN_TC_CASE(ks_, 16, 4, 4, false, 0) WSKPN_TC_CASE(ks_, 16, 8, 4, false, 0)                          \
-    WSKPN_TC_CASE(ks_, 32, 4, 4, false, 0) WSKPN_TC_CASE(ks_, 32, 8, 4, false, 0)
-// e4m3: single-term (widths 10-32-48-64-12 and 64-64), and hi/lo pairs of
-// activations and weights (10 and 48 input channels with a trailing half
-// chunk; 5x5 64-64 layers as two 32-channel output groups)
-#define WSKPN_TC_FP8(ks_)                                                                                  \
-    WSKPN_TC_CASE(ks_, 32, 1, 1, true, 0) WSKPN_TC_CASE(ks_, 48, 1, 1, true, 0)                            \
-    WSKPN_TC_CASE(ks_, 64, 2, 2, true, 0) WSKPN_TC_CASE(ks_, 16, 2, 2, true, 0)                            \
-    WSKPN_TC_CASE(ks_, 32, 2, 1, true, 2) WSKPN_TC_CASE(ks_, 48, 2, 2, true, 1)                            \
-    WSKPN_TC_CASE(ks_, 64, 4, 3, true, 2) WSKPN_TC_CASE(ks_, 16, 4, 4, true, 1)                            \
-    WSKPN_TC_CASE(ks_, 32, 4, 4, true, 1) WSKPN_TC_CASE(ks_, 64, 4, 4, true, 1)
-// the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
-// 112-48, 80-32 and the heads 48-5, 32-5
-#define WSKPN_TC_UNET                                                                                      \
-    WSKPN_TC_CASE(3, 32, 4, 2, false, 0) WSKPN_TC_CASE(3, 48, 6, 3, false, 0)                              \
-    WSKPN_TC_CASE(3, 64, 8, 4, false, 0) WSKPN_TC_CASE(3, 48, 14, 7, false, 0)                             \
-    WSKPN_TC_CASE(3, 32, 10, 5, false, 0) WSKPN_TC_CASE(3, 16, 6, 3, false, 0)                             \
-    WSKPN_TC_CASE(3, 16, 4, 2, false, 0)
-    WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3) WSKPN_TC_UNET
-#undef WSKPN_TC_UNET
-#undef WSKPN_TC_FP8
-#undef WSKPN_TC_BF16
-#undef WSKPN_TC_CASE
+    const TcLaunch launch = select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf);
     if (!launch) {
         err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M, "
               "64-64 and the multi-resolution U-Net are built";
@@ -1089,6 +1107,55 @@ wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, c
     L.xfold = 0;
     pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, KS, L.cout_p, L.groups, L.cin_p / 16, 0, 0, 0, L.wscale, 1.f,
                                         static_cast<uint8_t*>(L.wtc), L.ep_scale, L.ep_bias);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    return WSKPN_OK;
+}
+
+// Input gradient of a layer y = b + W * x (KS x KS cross-correlation, zero
+// padding KS / 2): dL/dx[c](q) = sum_{o,t} W[o][c][t] dL/dy[o](q - t + pad),
+// itself a KS x KS cross-correlation of dL/dy with cin and cout exchanged,
+// every kernel flipped and no bias: wt[c][o][t] = w[o][c][KS*KS - 1 - t].
+__global__ void transpose_flip_kernel(const float* __restrict__ w, int Cin, int Cout, int KK, float* __restrict__ wt) {
+    const int n = Cin * Cout * KK;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int t = i % KK, o = (i / KK) % Cout, c = i / (KK * Cout);
+        wt[i] = w[((size_t)o * Cin + c) * KK + (KK - 1 - t)];
+    }
+}
+
+// The tensor-core layer (BF16, hi/lo inputs) of the input gradient of a
+// forward layer with cin -> cout channels: Lt.cin = cout, Lt.cout = cin.
+// EUNSUPPORTED when no kernel is built for its shape (the caller then takes
+// the FP32 path).
+wskpn_status tc_dgrad_layer_alloc(Layer& Lt, int KS, int cin, int cout, std::string& err) {
+    Lt.cin = cout;
+    Lt.cout = cin;
+    Lt.cin_p = chan_pad(Lt.cin, false);
+    Lt.cout_p = (Lt.cout + 15) / 16 * 16;
+    Lt.xfold = 0;
+    if (Lt.cout_p > 64) {
+        err = "tensor-core input gradient: at most 64 channels";
+        return WSKPN_EUNSUPPORTED;
+    }
+    const wskpn_status s = tc_layer_alloc(Lt, KS, false, false, err);
+    if (s) return s;
+    const int ncc = Lt.cin_p / 16;
+    if (!select_tc_kernel(KS, Lt.cout_p / Lt.groups, 2 * ncc, ncc, false, 0, false)) {
+        err = "tensor-core input gradient: no kernel for this layer shape";
+        return WSKPN_EUNSUPPORTED;
+    }
+    return WSKPN_OK;
+}
+
+// Packs Lt's weight image from the forward layer's FP32 weights w (OIHW
+// [cout][cin][KS][KS] of the forward layer); wt: scratch of
+// cin * cout * KS * KS floats; zero_bias: Lt.cout_p zeros.
+wskpn_status tc_dgrad_layer_pack(Layer& Lt, int KS, const float* w, float* wt, const float* zero_bias,
+                                 cudaStream_t st, std::string& err) {
+    transpose_flip_kernel<<<148, 256, 0, st>>>(w, Lt.cout, Lt.cin, KS * KS, wt);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    pack_tc_kernel<<<148, 256, 0, st>>>(wt, zero_bias, Lt.cin, Lt.cout, KS, Lt.cout_p, Lt.groups, Lt.cin_p / 16, 0, 0,
+                                        0, Lt.wscale, 1.f, static_cast<uint8_t*>(Lt.wtc), Lt.ep_scale, Lt.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }

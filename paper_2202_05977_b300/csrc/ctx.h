@@ -61,7 +61,7 @@ struct wskpn_ctx {
     bool fp8_calibrated = false;
     int tc_split = 1;  // BF16 activations as hi/lo pairs (WSKPN_TUNE_TC_SPLIT)
     int fp8_split = 1;  // e4m3 activations and weights as hi/lo pairs (WSKPN_TUNE_FP8_SPLIT)
-    int train_tc_recompute = 1;  // backward recomputes on the tensor cores (WSKPN_TUNE_TRAIN_RECOMPUTE)
+    int train_tc_recompute = 1;  // backward on the tensor cores: 1 recompute + input gradients, 2 recompute only (WSKPN_TUNE_TRAIN_RECOMPUTE)
     int host_bands = 0;         // bands of the host-buffer pipeline, 0 = automatic (WSKPN_TUNE_HOST_BANDS)
     int host_first_pct = 100;   // first band's height in % of the others (WSKPN_TUNE_HOST_FIRST_BAND)
     int host_last_pct = 70;     // last band's height in % of the others (WSKPN_TUNE_HOST_LAST_BAND)
@@ -96,6 +96,9 @@ wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B,
 // BF16 tensor-core layers outside a context (hi/lo activations in and out)
 wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, cudaStream_t st, std::string& err);
 void tc_layer_free(Layer& L);
+wskpn_status tc_dgrad_layer_alloc(Layer& Lt, int KS, int cin, int cout, std::string& err);
+wskpn_status tc_dgrad_layer_pack(Layer& Lt, int KS, const float* w, float* wt, const float* zero_bias,
+                                 cudaStream_t st, std::string& err);
 wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int out_cp, int out_c0, int last,
                           int relu, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
                           std::string& err);

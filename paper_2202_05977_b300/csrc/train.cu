@@ -6,6 +6,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "ctx.h"
 
 namespace wskpn {
@@ -51,6 +53,12 @@ struct TrainWs {
     float* loss_part = nullptr;
     float* m = nullptr;         // Adam moments
     float* v = nullptr;
+    // BF16 contexts: input gradients on the tensor cores
+    Layer lt[WSKPN_MAX_LAYERS];         // layer l's input-gradient conv (weights transposed, flipped)
+    bool lt_ok[WSKPN_MAX_LAYERS] = {};  // a kernel exists for lt[l]'s shape
+    float* wt = nullptr;                // transposed weights of one layer (packing scratch)
+    float* zero_bias = nullptr;         // [64] zeros
+    void* gpack = nullptr;              // gradient as NHWC BF16 hi/lo [B][H][W][2 cp]
 };
 
 static void free_train(TrainWs* t) {
@@ -68,6 +76,10 @@ static void free_train(TrainWs* t) {
     cudaFree(t->loss_part);
     cudaFree(t->m);
     cudaFree(t->v);
+    for (int l = 0; l < WSKPN_MAX_LAYERS; ++l) tc_layer_free(t->lt[l]);
+    cudaFree(t->wt);
+    cudaFree(t->zero_bias);
+    cudaFree(t->gpack);
     delete t;
 }
 
@@ -111,6 +123,80 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
         WSKPN_TRY_ALLOC(t->bT[l], (size_t)simt_coutp(cin) * sizeof(float));
     }
     WSKPN_TRY_ALLOC(t->loss_part, kLossBlocks * sizeof(float));
+    if (c.prec == WSKPN_BF16) {
+        // input gradients of layers 1 .. L-1 as BF16 tensor-core convolutions
+        size_t wmax = 0, gcp = 0;
+        for (int l = 1; l < L; ++l) {
+            std::string e;
+            t->lt_ok[l] = tc_dgrad_layer_alloc(t->lt[l], KS, c.widths[l], c.widths[l + 1], e) == WSKPN_OK;
+            if (!t->lt_ok[l]) continue;
+            wmax = std::max(wmax, (size_t)c.widths[l] * c.widths[l + 1] * KS * KS);
+            gcp = std::max(gcp, (size_t)t->lt[l].cin_p);
+        }
+        if (wmax) {
+            WSKPN_TRY_ALLOC(t->wt, wmax * sizeof(float));
+            WSKPN_TRY_ALLOC(t->zero_bias, 64 * sizeof(float));
+            WSKPN_TRY_ALLOC(t->gpack, gcp * 2 * sizeof(uint16_t) * t->px);
+            if (cudaMemset(t->zero_bias, 0, 64 * sizeof(float)) != cudaSuccess) {
+                ctx->err = "training workspace: cudaMemset failed";
+                return WSKPN_ECUDA;
+            }
+        }
+    }
+    return WSKPN_OK;
+}
+
+// Gradient planes g (planar FP32 [C][HW] per frame).  With a mask (the
+// layer's input activation, same shape) g is first multiplied in place by
+// the ReLU derivative (mask > 0).  With nhwc, the planes are also written as
+// channels-last BF16 hi/lo pairs [HW][hi(cp) | lo(cp)] per frame (channels
+// C .. cp - 1 zero, lo = bf16(g - bf16(g))): the input of a tensor-core
+// input-gradient convolution.
+__global__ void grad_mask_pack_kernel(PtrBatch<float*> g, PtrBatch<const float*> mask, int C, int cp, size_t HW,
+                                      uint4* __restrict__ nhwc) {
+    const int b = blockIdx.y;
+    float* __restrict__ gb = g.p[b];
+    const float* __restrict__ mb = mask.p[b];
+    const int cend = nhwc ? cp : C;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < HW; p += (size_t)gridDim.x * blockDim.x) {
+        uint4* dst = nhwc ? nhwc + ((size_t)b * HW + p) * (size_t)(cp / 4) : nullptr;  // 2 cp BF16 = cp / 4 uint4
+        for (int c0 = 0; c0 < cend; c0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + j;
+                v[j] = c < C ? gb[(size_t)c * HW + p] : 0.f;
+                if (mb && c < C) {
+                    if (!(mb[(size_t)c * HW + p] > 0.f)) v[j] = 0.f;
+                    gb[(size_t)c * HW + p] = v[j];
+                }
+            }
+            if (dst) {
+                __nv_bfloat162 h[4], l[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                    const float2 hf = __bfloat1622float2(h[j]);
+                    l[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+                }
+                dst[c0 / 8] = *reinterpret_cast<const uint4*>(h);
+                dst[cp / 8 + c0 / 8] = *reinterpret_cast<const uint4*>(l);
+            }
+        }
+    }
+}
+
+static wskpn_status launch_grad_mask_pack(float* const* g, const float* const* mask, int B, int C, int cp, size_t HW,
+                                          void* nhwc, cudaStream_t st, std::string& err) {
+    PtrBatch<float*> gp{};
+    PtrBatch<const float*> mp{};
+    for (int b = 0; b < B; ++b) {
+        gp.p[b] = g[b];
+        mp.p[b] = mask ? mask[b] : nullptr;
+    }
+    const size_t blocks = std::min<size_t>((HW + 255) / 256, 148 * 8);
+    grad_mask_pack_kernel<<<dim3((unsigned)blocks, B), 256, 0, st>>>(gp, mp, C, cp, HW, static_cast<uint4*>(nhwc));
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
 
@@ -291,10 +377,16 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         }
     }
     // 3. layer by layer: weight gradient, then the masked input gradient
+    //    (BF16 with the tensor-core recompute: as a tensor-core convolution of
+    //    the hi/lo gradient with the transposed, flipped BF16 weights, then the
+    //    ReLU mask; else FP32 SIMT with the mask fused)
+    const bool tc_dgrad = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute == 1 &&
+                          batch <= WSKPN_MAX_BATCH;
     std::vector<const float*> gy(batch), xs(batch), mask(batch);
     std::vector<float*> gx(batch);
     for (int b = 0; b < batch; ++b) gy[b] = dz + (size_t)b * 2 * M * HW;
     float* gbuf[2] = {t->gA, t->gB};
+    bool packed = false;  // t->gpack holds gy as NHWC hi/lo
     for (int l = L - 1; l >= 0; --l) {
         const Layer& Ly = ctx->layers[l];
         for (int b = 0; b < batch; ++b) xs[b] = act(l, b);
@@ -306,17 +398,38 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
                          dweights + Ly.boff, st, ctx->err);
         if (s) return s;
         if (l == 0) break;
-        s = launch_pack_simt_transposed(ctx->d_master + Ly.woff, Ly.cin, Ly.cout, KS, t->wT[l], t->bT[l], st,
-                                        ctx->err);
-        if (s) return s;
         float* dst = gbuf[l % 2];
         for (int b = 0; b < batch; ++b) {
             gx[b] = dst + (size_t)b * Ly.cin * HW;
             mask[b] = xs[b];
         }
-        s = launch_conv_simt_masked(gy.data(), gx.data(), mask.data(), batch, h, w, Ly.cout, Ly.cin, KS, t->wT[l],
-                                    t->bT[l], 0, st, ctx->err);
-        if (s) return s;
+        if (tc_dgrad && t->lt_ok[l]) {
+            Layer& Lt = t->lt[l];
+            if (!packed) {  // gy (already masked) -> NHWC hi/lo
+                s = launch_grad_mask_pack(const_cast<float* const*>(gy.data()), nullptr, batch, Ly.cout, Lt.cin_p, HW,
+                                          t->gpack, st, ctx->err);
+                if (s) return s;
+            }
+            s = tc_dgrad_layer_pack(Lt, KS, ctx->d_master + Ly.woff, t->wt, t->zero_bias, st, ctx->err);
+            if (s) return s;
+            s = tc_layer_run(Lt, KS, t->gpack, dst, Lt.cout_p, 0, 1, 0, batch, h, w, ctx->d_status, ctx->device, st,
+                             ctx->err);
+            if (s) return s;
+            // mask in place; pack for the next layer's input gradient when that one runs on the tensor cores too
+            const bool next_tc = l - 1 >= 1 && t->lt_ok[l - 1];
+            s = launch_grad_mask_pack(gx.data(), mask.data(), batch, Ly.cin, next_tc ? t->lt[l - 1].cin_p : 0, HW,
+                                      next_tc ? t->gpack : nullptr, st, ctx->err);
+            if (s) return s;
+            packed = next_tc;
+        } else {
+            s = launch_pack_simt_transposed(ctx->d_master + Ly.woff, Ly.cin, Ly.cout, KS, t->wT[l], t->bT[l], st,
+                                            ctx->err);
+            if (s) return s;
+            s = launch_conv_simt_masked(gy.data(), gx.data(), mask.data(), batch, h, w, Ly.cout, Ly.cin, KS,
+                                        t->wT[l], t->bT[l], 0, st, ctx->err);
+            if (s) return s;
+            packed = false;
+        }
         for (int b = 0; b < batch; ++b) gy[b] = gx[b];
     }
     return WSKPN_OK;
