@@ -26,6 +26,10 @@ int simt_coutp(int cout);
 size_t wgrad_part_floats(int Cin, int KS, int G);
 wskpn_status launch_wgrad(const float* const* x, const float* const* gy, int B, int H, int W, int Cin, int Cout,
                           int KS, int G, float* part, float* dw, float* db, cudaStream_t st, std::string& err);
+bool wgrad_tc_supported(int KS, int Cin, int Cout, int B, int H, int W, int nsm, size_t* part_floats);
+wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gcp_stride, const float* const* gy,
+                             int B, int H, int W, int Cin, int Cout, int KS, float* part, size_t part_cap, float* dw,
+                             float* db, unsigned int* status, int device, cudaStream_t st, std::string& err);
 wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r, const float* const* a,
                                     float* const* out, int B, int H, int W, int M, const int* ks, float eps,
                                     unsigned int* fallbacks, cudaStream_t st, std::string& err);
@@ -53,12 +57,16 @@ struct TrainWs {
     float* loss_part = nullptr;
     float* m = nullptr;         // Adam moments
     float* v = nullptr;
-    // BF16 contexts: input gradients on the tensor cores
+    // BF16 contexts: input and weight gradients on the tensor cores
     Layer lt[WSKPN_MAX_LAYERS];         // layer l's input-gradient conv (weights transposed, flipped)
     bool lt_ok[WSKPN_MAX_LAYERS] = {};  // a kernel exists for lt[l]'s shape
+    bool wg_ok[WSKPN_MAX_LAYERS] = {};  // layer l's weight gradient has a tensor-core kernel
     float* wt = nullptr;                // transposed weights of one layer (packing scratch)
     float* zero_bias = nullptr;         // [64] zeros
     void* gpack = nullptr;              // gradient as NHWC BF16 hi/lo [B][H][W][2 cp]
+    void* xpack = nullptr;              // layer input as NHWC BF16 [B][H][W][cp]
+    float* wg_part = nullptr;           // tensor-core weight-gradient partial sums
+    size_t wg_part_floats = 0;
 };
 
 static void free_train(TrainWs* t) {
@@ -80,6 +88,8 @@ static void free_train(TrainWs* t) {
     cudaFree(t->wt);
     cudaFree(t->zero_bias);
     cudaFree(t->gpack);
+    cudaFree(t->xpack);
+    cudaFree(t->wg_part);
     delete t;
 }
 
@@ -124,42 +134,59 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
     }
     WSKPN_TRY_ALLOC(t->loss_part, kLossBlocks * sizeof(float));
     if (c.prec == WSKPN_BF16) {
-        // input gradients of layers 1 .. L-1 as BF16 tensor-core convolutions
-        size_t wmax = 0, gcp = 0;
-        for (int l = 1; l < L; ++l) {
+        // input gradients of layers 1 .. L-1 as BF16 tensor-core convolutions,
+        // weight gradients of every layer as tensor-core GEMMs over the pixels
+        int nsm = 148;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        size_t wmax = 0, gcp = 0, xcp = 0;
+        for (int l = 0; l < L; ++l) {
+            const int cin = c.widths[l], cout = c.widths[l + 1];
+            size_t pf = 0;
+            t->wg_ok[l] = wgrad_tc_supported(KS, cin, cout, c.max_batch, c.max_h, c.max_w, nsm, &pf);
+            if (t->wg_ok[l]) {
+                t->wg_part_floats = std::max(t->wg_part_floats, pf);
+                xcp = std::max(xcp, (size_t)(cin + 15) / 16 * 16);
+                gcp = std::max(gcp, (size_t)(cout + 15) / 16 * 16);
+            }
+            if (l == 0) continue;
             std::string e;
-            t->lt_ok[l] = tc_dgrad_layer_alloc(t->lt[l], KS, c.widths[l], c.widths[l + 1], e) == WSKPN_OK;
+            t->lt_ok[l] = tc_dgrad_layer_alloc(t->lt[l], KS, cin, cout, e) == WSKPN_OK;
             if (!t->lt_ok[l]) continue;
-            wmax = std::max(wmax, (size_t)c.widths[l] * c.widths[l + 1] * KS * KS);
+            wmax = std::max(wmax, (size_t)cin * cout * KS * KS);
             gcp = std::max(gcp, (size_t)t->lt[l].cin_p);
         }
         if (wmax) {
             WSKPN_TRY_ALLOC(t->wt, wmax * sizeof(float));
             WSKPN_TRY_ALLOC(t->zero_bias, 64 * sizeof(float));
-            WSKPN_TRY_ALLOC(t->gpack, gcp * 2 * sizeof(uint16_t) * t->px);
             if (cudaMemset(t->zero_bias, 0, 64 * sizeof(float)) != cudaSuccess) {
                 ctx->err = "training workspace: cudaMemset failed";
                 return WSKPN_ECUDA;
             }
         }
+        if (gcp) WSKPN_TRY_ALLOC(t->gpack, gcp * 2 * sizeof(uint16_t) * t->px);
+        if (xcp) WSKPN_TRY_ALLOC(t->xpack, xcp * sizeof(uint16_t) * t->px);
+        if (t->wg_part_floats) WSKPN_TRY_ALLOC(t->wg_part, t->wg_part_floats * sizeof(float));
     }
     return WSKPN_OK;
 }
 
 // Gradient planes g (planar FP32 [C][HW] per frame).  With a mask (the
 // layer's input activation, same shape) g is first multiplied in place by
-// the ReLU derivative (mask > 0).  With nhwc, the planes are also written as
-// channels-last BF16 hi/lo pairs [HW][hi(cp) | lo(cp)] per frame (channels
-// C .. cp - 1 zero, lo = bf16(g - bf16(g))): the input of a tensor-core
-// input-gradient convolution.
+// the ReLU derivative (mask > 0).  With nhwc, the planes are also written
+// channels-last per frame, channels C .. cp - 1 zero: as BF16 hi/lo pairs
+// [HW][hi(cp) | lo(cp)] (lo = bf16(g - bf16(g)); the input of a tensor-core
+// input-gradient convolution, whose hi half feeds the weight gradient), or
+// with hilo = 0 as single BF16 values [HW][cp] (a layer input for the
+// weight gradient).
 __global__ void grad_mask_pack_kernel(PtrBatch<float*> g, PtrBatch<const float*> mask, int C, int cp, size_t HW,
-                                      uint4* __restrict__ nhwc) {
+                                      int hilo, uint4* __restrict__ nhwc) {
     const int b = blockIdx.y;
     float* __restrict__ gb = g.p[b];
     const float* __restrict__ mb = mask.p[b];
     const int cend = nhwc ? cp : C;
+    const size_t pix_u4 = (size_t)cp / 8 * (hilo ? 2 : 1);  // uint4 (8 BF16) per stored pixel
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < HW; p += (size_t)gridDim.x * blockDim.x) {
-        uint4* dst = nhwc ? nhwc + ((size_t)b * HW + p) * (size_t)(cp / 4) : nullptr;  // 2 cp BF16 = cp / 4 uint4
+        uint4* dst = nhwc ? nhwc + ((size_t)b * HW + p) * pix_u4 : nullptr;
         for (int c0 = 0; c0 < cend; c0 += 8) {
             float v[8];
 #pragma unroll
@@ -180,14 +207,14 @@ __global__ void grad_mask_pack_kernel(PtrBatch<float*> g, PtrBatch<const float*>
                     l[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
                 }
                 dst[c0 / 8] = *reinterpret_cast<const uint4*>(h);
-                dst[cp / 8 + c0 / 8] = *reinterpret_cast<const uint4*>(l);
+                if (hilo) dst[cp / 8 + c0 / 8] = *reinterpret_cast<const uint4*>(l);
             }
         }
     }
 }
 
 static wskpn_status launch_grad_mask_pack(float* const* g, const float* const* mask, int B, int C, int cp, size_t HW,
-                                          void* nhwc, cudaStream_t st, std::string& err) {
+                                          void* nhwc, cudaStream_t st, std::string& err, int hilo = 1) {
     PtrBatch<float*> gp{};
     PtrBatch<const float*> mp{};
     for (int b = 0; b < B; ++b) {
@@ -195,7 +222,8 @@ static wskpn_status launch_grad_mask_pack(float* const* g, const float* const* m
         mp.p[b] = mask ? mask[b] : nullptr;
     }
     const size_t blocks = std::min<size_t>((HW + 255) / 256, 148 * 8);
-    grad_mask_pack_kernel<<<dim3((unsigned)blocks, B), 256, 0, st>>>(gp, mp, C, cp, HW, static_cast<uint4*>(nhwc));
+    grad_mask_pack_kernel<<<dim3((unsigned)blocks, B), 256, 0, st>>>(gp, mp, C, cp, HW, hilo,
+                                                                      static_cast<uint4*>(nhwc));
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
@@ -376,51 +404,78 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
             if (s) return s;
         }
     }
-    // 3. layer by layer: weight gradient, then the masked input gradient
-    //    (BF16 with the tensor-core recompute: as a tensor-core convolution of
-    //    the hi/lo gradient with the transposed, flipped BF16 weights, then the
-    //    ReLU mask; else FP32 SIMT with the mask fused)
-    const bool tc_dgrad = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute == 1 &&
-                          batch <= WSKPN_MAX_BATCH;
+    // 3. layer by layer: weight gradient, then the masked input gradient.
+    //    BF16 with the tensor-core recompute: the gradient is packed as NHWC
+    //    BF16 hi/lo pairs; the weight gradient is a tensor-core GEMM over the
+    //    pixels (hi half), the input gradient a tensor-core convolution with
+    //    the transposed, flipped BF16 weights followed by the ReLU mask.
+    //    Otherwise FP32 SIMT (mask fused into the input-gradient conv).
+    const bool tc_bwd = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute == 1 &&
+                        batch <= WSKPN_MAX_BATCH;
+    auto tc_wg = [&](int l) { return tc_bwd && t->wg_ok[l]; };
+    auto tc_dg = [&](int l) { return tc_bwd && l >= 1 && t->lt_ok[l]; };
+    auto gcp = [&](int l) { return (c.widths[l + 1] + 15) / 16 * 16; };  // padded gradient channels of layer l
     std::vector<const float*> gy(batch), xs(batch), mask(batch);
-    std::vector<float*> gx(batch);
+    std::vector<float*> gx(batch), xsw(batch);
     for (int b = 0; b < batch; ++b) gy[b] = dz + (size_t)b * 2 * M * HW;
     float* gbuf[2] = {t->gA, t->gB};
-    bool packed = false;  // t->gpack holds gy as NHWC hi/lo
+    // Transposed weight images first: the input-gradient conv is launched as a
+    // programmatic dependent of the kernel before it and loads its weight
+    // image before waiting for that kernel, so the image must not be written
+    // by the kernel immediately before it.
+    for (int l = 1; l < L; ++l)
+        if (tc_dg(l)) {
+            s = tc_dgrad_layer_pack(t->lt[l], KS, ctx->d_master + ctx->layers[l].woff, t->wt, t->zero_bias, st,
+                                    ctx->err);
+            if (s) return s;
+        }
+    bool packed = false;  // t->gpack holds gy as NHWC hi/lo with gcp(l) channels
     for (int l = L - 1; l >= 0; --l) {
         const Layer& Ly = ctx->layers[l];
-        for (int b = 0; b < batch; ++b) xs[b] = act(l, b);
-        const int nchunks = (Ly.cin + 7) / 8;
-        int G = kWgradGroups / nchunks;
-        const int ntiles = ((w + 31) / 32) * ((h + 7) / 8) * batch;
-        G = std::max(1, std::min(G, ntiles));
-        s = launch_wgrad(xs.data(), gy.data(), batch, h, w, Ly.cin, Ly.cout, KS, G, t->part, dweights + Ly.woff,
-                         dweights + Ly.boff, st, ctx->err);
-        if (s) return s;
+        for (int b = 0; b < batch; ++b) {
+            xs[b] = act(l, b);
+            xsw[b] = act(l, b);
+        }
+        if ((tc_wg(l) || tc_dg(l)) && !packed) {  // gy (already masked) -> NHWC hi/lo
+            s = launch_grad_mask_pack(const_cast<float* const*>(gy.data()), nullptr, batch, Ly.cout, gcp(l), HW,
+                                      t->gpack, st, ctx->err);
+            if (s) return s;
+            packed = true;
+        }
+        if (tc_wg(l)) {
+            const int xcp = (Ly.cin + 15) / 16 * 16;
+            s = launch_grad_mask_pack(xsw.data(), nullptr, batch, Ly.cin, xcp, HW, t->xpack, st, ctx->err, 0);
+            if (s) return s;
+            s = launch_wgrad_tc(t->xpack, xcp, t->gpack, 2 * gcp(l), gy.data(), batch, h, w, Ly.cin, Ly.cout, KS,
+                                t->wg_part, t->wg_part_floats, dweights + Ly.woff, dweights + Ly.boff, ctx->d_status,
+                                ctx->device, st, ctx->err);
+            if (s) return s;
+        } else {
+            const int nchunks = (Ly.cin + 7) / 8;
+            int G = kWgradGroups / nchunks;
+            const int ntiles = ((w + 31) / 32) * ((h + 7) / 8) * batch;
+            G = std::max(1, std::min(G, ntiles));
+            s = launch_wgrad(xs.data(), gy.data(), batch, h, w, Ly.cin, Ly.cout, KS, G, t->part, dweights + Ly.woff,
+                             dweights + Ly.boff, st, ctx->err);
+            if (s) return s;
+        }
         if (l == 0) break;
         float* dst = gbuf[l % 2];
         for (int b = 0; b < batch; ++b) {
             gx[b] = dst + (size_t)b * Ly.cin * HW;
             mask[b] = xs[b];
         }
-        if (tc_dgrad && t->lt_ok[l]) {
+        const bool next_pack = tc_wg(l - 1) || tc_dg(l - 1);
+        if (tc_dg(l)) {
             Layer& Lt = t->lt[l];
-            if (!packed) {  // gy (already masked) -> NHWC hi/lo
-                s = launch_grad_mask_pack(const_cast<float* const*>(gy.data()), nullptr, batch, Ly.cout, Lt.cin_p, HW,
-                                          t->gpack, st, ctx->err);
-                if (s) return s;
-            }
-            s = tc_dgrad_layer_pack(Lt, KS, ctx->d_master + Ly.woff, t->wt, t->zero_bias, st, ctx->err);
-            if (s) return s;
             s = tc_layer_run(Lt, KS, t->gpack, dst, Lt.cout_p, 0, 1, 0, batch, h, w, ctx->d_status, ctx->device, st,
                              ctx->err);
             if (s) return s;
-            // mask in place; pack for the next layer's input gradient when that one runs on the tensor cores too
-            const bool next_tc = l - 1 >= 1 && t->lt_ok[l - 1];
-            s = launch_grad_mask_pack(gx.data(), mask.data(), batch, Ly.cin, next_tc ? t->lt[l - 1].cin_p : 0, HW,
-                                      next_tc ? t->gpack : nullptr, st, ctx->err);
+            // mask in place, and pack for the next layer's tensor-core gradients
+            s = launch_grad_mask_pack(gx.data(), mask.data(), batch, Ly.cin, next_pack ? gcp(l - 1) : 0, HW,
+                                      next_pack ? t->gpack : nullptr, st, ctx->err);
             if (s) return s;
-            packed = next_tc;
+            packed = next_pack;
         } else {
             s = launch_pack_simt_transposed(ctx->d_master + Ly.woff, Ly.cin, Ly.cout, KS, t->wT[l], t->bT[l], st,
                                             ctx->err);

@@ -137,14 +137,16 @@ def test_training_backward_bf16_tensor_core_recompute(torch, wk):
 
 
 @pytest.mark.parametrize("KS,six", [(5, False), (3, False), (5, True)])
-def test_tensor_core_input_gradient_matches_fp32(torch, wk, KS, six):
-    """Input gradients on the tensor cores (default) against the same
-    backward with FP32 SIMT input gradients (TUNE_TRAIN_RECOMPUTE = 2): both
-    recompute the same BF16 activations, so the ReLU masks agree and only
-    the BF16 rounding of the transposed weights separates them.  The last
-    layer's weight gradient needs no input gradient and is bitwise equal;
-    every other layer stays within 1e-2 in L2 and 2e-2 of its largest
-    element (2 frames of 40 x 200: two tile columns, ragged rows)."""
+def test_tensor_core_gradients_match_fp32(torch, wk, KS, six):
+    """Input and weight gradients on the tensor cores (default) against the
+    same backward with FP32 SIMT gradient kernels (TUNE_TRAIN_RECOMPUTE = 2):
+    both recompute the same BF16 activations, so the ReLU masks agree and
+    only BF16 rounding separates them (transposed weights in the input
+    gradients; layer inputs and gradients in the weight gradients, FP32
+    sums).  Every layer's weight gradient stays within 1e-2 in L2 and 2e-2
+    of its largest element (measured 4-6e-3 in L2), the last layer's bias
+    gradient (FP32 sums of the same values) within 1e-4 (2 frames of
+    40 x 200: two tile columns, ragged rows)."""
     from paper_2202_05977_b300 import _lib
     B, H, W = 2, 40, 200
     frames = [synth.make_frame(H, W, 320 + b) for b in range(B)]
@@ -162,15 +164,15 @@ def test_tensor_core_input_gradient_matches_fp32(torch, wk, KS, six):
     shapes = synth.weight_shapes(widths, KS)
     off = 0
     for i, (ws, bs) in enumerate(shapes):
-        n = int(np.prod(ws)) + bs[0]
-        a, r = dw_tc[off:off + n], dw_fp[off:off + n]
-        if i == len(shapes) - 1:
-            assert np.array_equal(a, r), ws
-        else:
-            rel = np.linalg.norm(a - r) / np.linalg.norm(r)
-            print(f"tc input gradient KS={KS} {ws}: L2 rel {rel:.3e}")
-            assert rel < 1e-2 and _close(a, r, 2e-2), ws
-        off += n
+        nw = int(np.prod(ws))
+        a, r = dw_tc[off:off + nw], dw_fp[off:off + nw]
+        rel = np.linalg.norm(a - r) / np.linalg.norm(r)
+        mx = np.abs(a - r).max() / np.abs(r).max()
+        print(f"tc gradients KS={KS} {ws}: L2 rel {rel:.3e}, max {mx:.3e}")
+        assert rel < 1e-2 and mx < 2e-2, ws
+        ab, rb = dw_tc[off + nw:off + nw + bs[0]], dw_fp[off + nw:off + nw + bs[0]]
+        assert _close(ab, rb, 1e-2 if i < len(shapes) - 1 else 1e-4), (ws, "bias")
+        off += nw + bs[0]
     assert d.device_status() == 0
 
 
