@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the 720p / 1440p runs")
     p.add_argument("--no-variants", action="store_true", help="skip the 6-block network timing")
+    p.add_argument("--train-only", action="store_true",
+                   help="time only the training step (16 crops of 256 x 256) and print its line")
     p.add_argument("--serve-requests", type=int, default=4096)
     p.add_argument("--serve-rate", type=float, default=240.0)
     p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
@@ -356,6 +358,46 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     pk = peaks()
 
+    def time_training(steps, warmup):
+        """The differentiation form: one training step on 16 crops of 256 x
+        256 (BF16 forward, L1 loss against the mean of 256 noise draws,
+        hand-written backward with the activations recomputed, Adam)."""
+        tb = synth.make_batch(16, 256, 256, seed=5)
+        ttg = torch.from_numpy(synth.make_target(tb["clean"], seed=5, draws=256)).to(dev)
+        tx = [torch.from_numpy(np.ascontiguousarray(tb[k])).to(dev) for k in keys]
+        dt = wk.Denoiser(wb, precision="bf16", max_batch=16, max_hw=(256, 256))
+        t_it = 1
+
+        def train_step():
+            nonlocal t_it
+            o, zz = dt.forward_train(*tx)
+            _, dout = dt.l1_loss(o, ttg)
+            dw, _ = dt.backward(*tx, zz, dout)
+            dt.adam_step(dw, t_it, lr=1e-4)
+            t_it += 1
+
+        for _ in range(warmup):
+            train_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            train_step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_t = e0.elapsed_time(e1) / steps
+        dt.close()
+        return {"precision": "bf16", "ms_per_step": ms_t, "crops_per_s": 16e3 / ms_t}
+
+    if args.train_only:
+        # the differentiation form alone (for profiling its launches)
+        r = time_training(args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": "training step ms (16 crops of 256 x 256, BF16)", "value": r["ms_per_step"],
+                              "unit": "ms/step", "steps": args.steps, "warmup": args.warmup,
+                              "higher_is_better": False, "crops_per_s": r["crops_per_s"], "data": "synthetic"}))
+        return
+
     def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS):
         h, w = hw
         xs = xin if frame is None else frame
@@ -472,37 +514,7 @@ def main():
             c3[f"{prec}_ms_per_frame"] = r["ms_step"]
             del r
         variants["conv3x3_1920x1080"] = c3
-        # the differentiation form: one training step on 16 crops of 256 x 256
-        # (BF16 forward, L1 loss against the mean of 256 noise draws, hand-
-        # written backward with the activations recomputed, Adam)
-        tb = synth.make_batch(16, 256, 256, seed=5)
-        ttg = torch.from_numpy(synth.make_target(tb["clean"], seed=5, draws=256)).to(dev)
-        tx = [torch.from_numpy(np.ascontiguousarray(tb[k])).to(dev) for k in keys]
-        dt = wk.Denoiser(wb, precision="bf16", max_batch=16, max_hw=(256, 256))
-        t_it = 1
-
-        def train_step():
-            nonlocal t_it
-            o, zz = dt.forward_train(*tx)
-            _, dout = dt.l1_loss(o, ttg)
-            dw, _ = dt.backward(*tx, zz, dout)
-            dt.adam_step(dw, t_it, lr=1e-4)
-            t_it += 1
-
-        for _ in range(3):
-            train_step()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n_t = max(5, args.steps // 4)
-        e0.record()
-        for _ in range(n_t):
-            train_step()
-        e1.record()
-        torch.cuda.synchronize()
-        ms_t = e0.elapsed_time(e1) / n_t
-        variants["training_step_16x256x256"] = {"precision": "bf16", "ms_per_step": ms_t,
-                                                "crops_per_s": 16e3 / ms_t}
-        dt.close()
+        variants["training_step_16x256x256"] = time_training(max(5, args.steps // 4), 3)
     if not args.no_variants:
         # the multi-resolution variant (U-Net, 3 levels, kernels 3 and 5, Eq. 7), FP32
         from paper_2202_05977_b300.multires import MultiResDenoiser

@@ -1294,6 +1294,25 @@ wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B,
     return s;
 }
 
+// The layer inputs x_0 .. x_{L-1} of a BF16 context (hi/lo activations)
+// recomputed on the tensor cores exactly as its forward computes them, kept
+// channels-last: xs[l] = NHWC [B][H][W][hi(cin_p) | lo(cin_p)] of layer l.
+wskpn_status tc_recompute_nhwc(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
+                               const std::vector<void*>& xs, cudaStream_t st) {
+    const wskpn_config& c = ctx->cfg;
+    if (c.prec != WSKPN_BF16 || !ctx->tc_split || B > WSKPN_MAX_BATCH) {
+        ctx->err = "tc_recompute_nhwc: BF16 contexts with hi/lo activations only, at most 16 frames";
+        return WSKPN_EUNSUPPORTED;
+    }
+    const size_t HW = (size_t)H * W;
+    std::vector<void*> x0(B);
+    const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * 2 * HW;
+    for (int b = 0; b < B; ++b) x0[b] = static_cast<uint8_t*>(xs[0]) + (size_t)b * x0_bytes;
+    wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), 2, st, ctx->err);
+    for (int l = 0; !s && l + 1 < c.n_layers; ++l) s = conv_tc(ctx, l, xs[l], xs[l + 1], B, H, W, st);
+    return s;
+}
+
 // max over n non-negative floats (ReLU outputs, [0,1] inputs) by their bit patterns
 __global__ void amax_nonneg_kernel(const float* __restrict__ x, size_t n, unsigned int* __restrict__ out) {
     unsigned int m = 0;

@@ -27,9 +27,9 @@ size_t wgrad_part_floats(int Cin, int KS, int G);
 wskpn_status launch_wgrad(const float* const* x, const float* const* gy, int B, int H, int W, int Cin, int Cout,
                           int KS, int G, float* part, float* dw, float* db, cudaStream_t st, std::string& err);
 bool wgrad_tc_supported(int KS, int Cin, int Cout, int B, int H, int W, int nsm, size_t* part_floats);
-wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gcp_stride, const float* const* gy,
-                             int B, int H, int W, int Cin, int Cout, int KS, float* part, size_t part_cap, float* dw,
-                             float* db, unsigned int* status, int device, cudaStream_t st, std::string& err);
+wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gcp_stride, int B, int H, int W,
+                             int Cin, int Cout, int KS, float* part, size_t part_cap, float* dw, unsigned int* status,
+                             int device, cudaStream_t st, std::string& err);
 wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r, const float* const* a,
                                     float* const* out, int B, int H, int W, int M, const int* ks, float eps,
                                     unsigned int* fallbacks, cudaStream_t st, std::string& err);
@@ -40,6 +40,7 @@ wskpn_status launch_decode_fuse_bwd(const float* const* z, const float* const* r
 
 namespace {
 constexpr int kWgradGroups = 256;
+constexpr int GP_TILE = 64;  // pixels per block of the gradient pack
 constexpr int kLossBlocks = 1024;
 }
 
@@ -64,9 +65,14 @@ struct TrainWs {
     float* wt = nullptr;                // transposed weights of one layer (packing scratch)
     float* zero_bias = nullptr;         // [64] zeros
     void* gpack = nullptr;              // gradient as NHWC BF16 hi/lo [B][H][W][2 cp]
-    void* xpack = nullptr;              // layer input as NHWC BF16 [B][H][W][cp]
+    void* xnhwc = nullptr;              // layer inputs x_0 .. x_{L-1}, NHWC BF16 hi/lo, layer after layer
+    size_t x_off[WSKPN_MAX_LAYERS] = {};  // byte offsets in xnhwc
+    size_t x_bytes = 0;
+    bool all_tc = false;                // every layer has its tensor-core gradient kernels
+    float* bias_part = nullptr;         // per-tile bias-gradient sums [tiles][64]
     float* wg_part = nullptr;           // tensor-core weight-gradient partial sums
     size_t wg_part_floats = 0;
+    size_t acts_floats = 0;             // planar acts (FP32 gradient paths), allocated on first use
 };
 
 static void free_train(TrainWs* t) {
@@ -88,7 +94,8 @@ static void free_train(TrainWs* t) {
     cudaFree(t->wt);
     cudaFree(t->zero_bias);
     cudaFree(t->gpack);
-    cudaFree(t->xpack);
+    cudaFree(t->xnhwc);
+    cudaFree(t->bias_part);
     cudaFree(t->wg_part);
     delete t;
 }
@@ -121,7 +128,7 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
     }
     for (int l = 1; l <= L; ++l) maxw = std::max(maxw, c.widths[l]);
     for (int l = 0; l < L; ++l) maxcin = std::max(maxcin, c.widths[l]);
-    WSKPN_TRY_ALLOC(t->acts, off * sizeof(float));
+    t->acts_floats = off;  // allocated by the first backward that needs planar activations
     WSKPN_TRY_ALLOC(t->gA, (size_t)maxw * t->px * sizeof(float));
     WSKPN_TRY_ALLOC(t->gB, (size_t)maxw * t->px * sizeof(float));
     WSKPN_TRY_ALLOC(t->dz, (size_t)2 * M * t->px * sizeof(float));
@@ -138,92 +145,155 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
         // weight gradients of every layer as tensor-core GEMMs over the pixels
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-        size_t wmax = 0, gcp = 0, xcp = 0;
+        size_t wmax = 0, gcp = 0;
+        t->all_tc = true;
         for (int l = 0; l < L; ++l) {
             const int cin = c.widths[l], cout = c.widths[l + 1];
             size_t pf = 0;
             t->wg_ok[l] = wgrad_tc_supported(KS, cin, cout, c.max_batch, c.max_h, c.max_w, nsm, &pf);
-            if (t->wg_ok[l]) {
-                t->wg_part_floats = std::max(t->wg_part_floats, pf);
-                xcp = std::max(xcp, (size_t)(cin + 15) / 16 * 16);
-                gcp = std::max(gcp, (size_t)(cout + 15) / 16 * 16);
-            }
+            t->all_tc = t->all_tc && t->wg_ok[l];
+            t->wg_part_floats = std::max(t->wg_part_floats, pf);
+            gcp = std::max(gcp, (size_t)(cout + 15) / 16 * 16);
+            t->x_off[l] = t->x_bytes;
+            t->x_bytes += (size_t)(cin + 15) / 16 * 16 * 2 * sizeof(uint16_t) * t->px;
             if (l == 0) continue;
             std::string e;
             t->lt_ok[l] = tc_dgrad_layer_alloc(t->lt[l], KS, cin, cout, e) == WSKPN_OK;
-            if (!t->lt_ok[l]) continue;
+            t->all_tc = t->all_tc && t->lt_ok[l];
             wmax = std::max(wmax, (size_t)cin * cout * KS * KS);
-            gcp = std::max(gcp, (size_t)t->lt[l].cin_p);
         }
-        if (wmax) {
-            WSKPN_TRY_ALLOC(t->wt, wmax * sizeof(float));
+        if (t->all_tc) {
+            WSKPN_TRY_ALLOC(t->wt, std::max<size_t>(wmax, 1) * sizeof(float));
             WSKPN_TRY_ALLOC(t->zero_bias, 64 * sizeof(float));
             if (cudaMemset(t->zero_bias, 0, 64 * sizeof(float)) != cudaSuccess) {
                 ctx->err = "training workspace: cudaMemset failed";
                 return WSKPN_ECUDA;
             }
+            WSKPN_TRY_ALLOC(t->gpack, gcp * 2 * sizeof(uint16_t) * t->px);
+            WSKPN_TRY_ALLOC(t->wg_part, t->wg_part_floats * sizeof(float));
+            // tiles of GP_TILE pixels per frame, for every frame of a call
+            const size_t tiles = (size_t)c.max_batch * (((size_t)c.max_h * c.max_w + GP_TILE - 1) / GP_TILE);
+            WSKPN_TRY_ALLOC(t->bias_part, tiles * 64 * sizeof(float));
         }
-        if (gcp) WSKPN_TRY_ALLOC(t->gpack, gcp * 2 * sizeof(uint16_t) * t->px);
-        if (xcp) WSKPN_TRY_ALLOC(t->xpack, xcp * sizeof(uint16_t) * t->px);
-        if (t->wg_part_floats) WSKPN_TRY_ALLOC(t->wg_part, t->wg_part_floats * sizeof(float));
     }
     return WSKPN_OK;
 }
 
-// Gradient planes g (planar FP32 [C][HW] per frame).  With a mask (the
-// layer's input activation, same shape) g is first multiplied in place by
-// the ReLU derivative (mask > 0).  With nhwc, the planes are also written
-// channels-last per frame, channels C .. cp - 1 zero: as BF16 hi/lo pairs
-// [HW][hi(cp) | lo(cp)] (lo = bf16(g - bf16(g)); the input of a tensor-core
-// input-gradient convolution, whose hi half feeds the weight gradient), or
-// with hilo = 0 as single BF16 values [HW][cp] (a layer input for the
-// weight gradient).
-__global__ void grad_mask_pack_kernel(PtrBatch<float*> g, PtrBatch<const float*> mask, int C, int cp, size_t HW,
-                                      int hilo, uint4* __restrict__ nhwc) {
-    const int b = blockIdx.y;
+// Gradient planes g (planar FP32 [C][HW] per frame, C <= 64), one block per
+// tile of 64 pixels of one frame, transposed through shared memory so that
+// both layouts are read and written in whole runs.  With a mask (the layer's
+// input activation as NHWC BF16 hi/lo pairs [B][HW][hi(mcp) | lo(mcp)], mcp a
+// multiple of 16 and >= C, x = hi + lo) g is multiplied in place by the ReLU
+// derivative (x > 0).  The planes are written channels-last as BF16 hi/lo
+// pairs nhwc [B][HW][hi(cp) | lo(cp)] (channels C .. cp - 1 zero,
+// lo = bf16(g - bf16(g))): the input of a tensor-core input-gradient
+// convolution, whose hi half also feeds the weight gradient.  bias_part
+// [tiles][64] receives each tile's per-channel sum of the (masked) gradient
+// (pixels in a fixed order), from which the bias gradient is added up.
+__device__ __forceinline__ void bf16x8_to_float(const uint4& u, float f[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+__global__ void __launch_bounds__(256) grad_mask_pack_kernel(PtrBatch<float*> g, const uint4* __restrict__ mask,
+                                                             int mcp, int C, int cp, size_t HW,
+                                                             uint4* __restrict__ nhwc, float* __restrict__ bias_part) {
+    __shared__ float sg[64][GP_TILE + 1];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const size_t p0 = (size_t)blockIdx.x * GP_TILE;
     float* __restrict__ gb = g.p[b];
-    const float* __restrict__ mb = mask.p[b];
-    const int cend = nhwc ? cp : C;
-    const size_t pix_u4 = (size_t)cp / 8 * (hilo ? 2 : 1);  // uint4 (8 BF16) per stored pixel
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < HW; p += (size_t)gridDim.x * blockDim.x) {
-        uint4* dst = nhwc ? nhwc + ((size_t)b * HW + p) * pix_u4 : nullptr;
-        for (int c0 = 0; c0 < cend; c0 += 8) {
-            float v[8];
+    // 1. planar -> shared (channel rows of 64 pixels)
+    for (int k = tid; k < cp * GP_TILE; k += 256) {
+        const int c = k / GP_TILE, i = k % GP_TILE;
+        sg[c][i] = c < C && p0 + i < HW ? gb[(size_t)c * HW + p0 + i] : 0.f;
+    }
+    __syncthreads();
+    // 2. per (pixel, 8-channel chunk): mask, then the hi/lo pair as two 16-byte stores
+    const int nq = cp / 8;
+    for (int k = tid; k < GP_TILE * nq; k += 256) {
+        const int i = k / nq, q = k % nq;
+        const size_t p = p0 + i;
+        if (p >= HW) continue;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = sg[q * 8 + j][i];
+        if (mask && q * 8 < C) {
+            const uint4* mpx = mask + ((size_t)b * HW + p) * (size_t)(mcp / 4);  // 2 mcp BF16
+            float mh[8], ml[8];
+            bf16x8_to_float(mpx[q], mh);
+            bf16x8_to_float(mpx[mcp / 8 + q], ml);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int c = c0 + j;
-                v[j] = c < C ? gb[(size_t)c * HW + p] : 0.f;
-                if (mb && c < C) {
-                    if (!(mb[(size_t)c * HW + p] > 0.f)) v[j] = 0.f;
-                    gb[(size_t)c * HW + p] = v[j];
-                }
-            }
-            if (dst) {
-                __nv_bfloat162 h[4], l[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    const float2 hf = __bfloat1622float2(h[j]);
-                    l[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
-                }
-                dst[c0 / 8] = *reinterpret_cast<const uint4*>(h);
-                if (hilo) dst[cp / 8 + c0 / 8] = *reinterpret_cast<const uint4*>(l);
+                if (!(mh[j] + ml[j] > 0.f)) v[j] = 0.f;
+                sg[q * 8 + j][i] = v[j];
             }
         }
+        __nv_bfloat162 h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            const float2 hf = __bfloat1622float2(h[j]);
+            l[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+        }
+        uint4* dst = nhwc + ((size_t)b * HW + p) * (size_t)(cp / 4);  // 2 cp BF16 = cp / 4 uint4
+        dst[q] = *reinterpret_cast<const uint4*>(h);
+        dst[cp / 8 + q] = *reinterpret_cast<const uint4*>(l);
+    }
+    __syncthreads();
+    // 3. masked planes back (planar, whole runs) and per-channel tile sums:
+    //    4 threads per channel, 16 pixels each in order, then 2 shuffle steps
+    if (mask)
+        for (int k = tid; k < C * GP_TILE; k += 256) {
+            const int c = k / GP_TILE, i = k % GP_TILE;
+            if (p0 + i < HW) gb[(size_t)c * HW + p0 + i] = sg[c][i];
+        }
+    {
+        const int c = tid / 4, part = tid % 4;
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < GP_TILE / 4; ++i) s += sg[c][part * (GP_TILE / 4) + i];
+        s += __shfl_down_sync(0xffffffffu, s, 1);
+        s += __shfl_down_sync(0xffffffffu, s, 2);
+        if (part == 0 && c < C) bias_part[((size_t)b * gridDim.x + blockIdx.x) * 64 + c] = s;
     }
 }
 
-static wskpn_status launch_grad_mask_pack(float* const* g, const float* const* mask, int B, int C, int cp, size_t HW,
-                                          void* nhwc, cudaStream_t st, std::string& err, int hilo = 1) {
-    PtrBatch<float*> gp{};
-    PtrBatch<const float*> mp{};
-    for (int b = 0; b < B; ++b) {
-        gp.p[b] = g[b];
-        mp.p[b] = mask ? mask[b] : nullptr;
+// db[o] = sum over the tiles (fixed order: thread t adds tiles t, t + 256,
+// ..., then a fixed tree) of bias_part[tile][o]; one block per channel.
+__global__ void bias_from_tiles_kernel(const float* __restrict__ part, int ntiles, float* __restrict__ db) {
+    const int o = blockIdx.x;
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int k = threadIdx.x; k < ntiles; k += 256) s += part[(size_t)k * 64 + o];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
-    const size_t blocks = std::min<size_t>((HW + 255) / 256, 148 * 8);
-    grad_mask_pack_kernel<<<dim3((unsigned)blocks, B), 256, 0, st>>>(gp, mp, C, cp, HW, hilo,
-                                                                      static_cast<uint4*>(nhwc));
+    if (threadIdx.x == 0) db[o] = red[0];
+}
+
+// Packs (and with a mask, masks) the gradient of a layer with C output
+// channels, then writes its bias gradient db.
+static wskpn_status launch_grad_mask_pack(float* const* g, const void* mask, int mcp, int B, int C, int cp,
+                                          size_t HW, void* nhwc, float* bias_part, float* db, cudaStream_t st,
+                                          std::string& err) {
+    if (C > 64 || cp > 64 || B > WSKPN_MAX_BATCH) {
+        err = "gradient pack: at most 64 channels and 16 frames";
+        return WSKPN_EUNSUPPORTED;
+    }
+    PtrBatch<float*> gp{};
+    for (int b = 0; b < B; ++b) gp.p[b] = g[b];
+    const unsigned tiles = (unsigned)((HW + GP_TILE - 1) / GP_TILE);
+    grad_mask_pack_kernel<<<dim3(tiles, B), 256, 0, st>>>(gp, static_cast<const uint4*>(mask), mcp, C, cp, HW,
+                                                          static_cast<uint4*>(nhwc), bias_part);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    bias_from_tiles_kernel<<<C, 256, 0, st>>>(bias_part, (int)tiles * B, db);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
@@ -250,12 +320,19 @@ __global__ void l1_loss_kernel(const float* __restrict__ o, const float* __restr
     }
 }
 
+// One block of 256 threads: thread t adds partials t, t + 256, ... in FP64,
+// then a fixed-order tree (deterministic).
 __global__ void sum_partials_kernel(const float* __restrict__ part, int n, double scale, float* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += part[i];
-        out[0] = (float)(s * scale);
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[0] = (float)(red[0] * scale);
 }
 
 // ------------------------------------------------------------------ Adam
@@ -375,17 +452,27 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         if (s) return s;
     }
     // 2. recompute x_0 .. x_{L-1}: with the context's own convolutions for BF16
-    //    (tensor cores, hi/lo activations, as the forward), else FP32
+    //    (tensor cores, hi/lo activations, as the forward), else FP32.  With
+    //    every gradient on the tensor cores they stay NHWC hi/lo; otherwise
+    //    planar FP32 for the SIMT gradient kernels.
+    const bool on_tc = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute && batch <= WSKPN_MAX_BATCH;
+    const bool tc_bwd = on_tc && ctx->train_tc_recompute == 1 && t->all_tc;
+    auto xn = [&](int l) { return static_cast<void*>(static_cast<uint8_t*>(t->xnhwc) + t->x_off[l]); };
     auto act = [&](int l, int b) { return t->acts + t->act_off[l] + (size_t)b * c.widths[l] * HW; };
-    {
+    if (tc_bwd) {
+        if (!t->xnhwc) WSKPN_TRY_ALLOC(t->xnhwc, t->x_bytes);
+        std::vector<void*> xs(L);
+        for (int l = 0; l < L; ++l) xs[l] = xn(l);
+        s = tc_recompute_nhwc(ctx, frames, batch, h, w, xs, st);
+        if (s) return s;
+    } else {
+        if (!t->acts) WSKPN_TRY_ALLOC(t->acts, t->acts_floats * sizeof(float));
         std::vector<void*> x0(batch);
         for (int b = 0; b < batch; ++b) x0[b] = act(0, b);
         s = launch_prep(frames, batch, h, w, c.gamma, c.depth_near, c.depth_far, x0.data(), 0, st, ctx->err);
         if (s) return s;
         std::vector<const float*> in(batch);
         std::vector<float*> o(batch);
-        const bool on_tc = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute &&
-                           batch <= WSKPN_MAX_BATCH;
         if (on_tc) {
             std::vector<std::vector<float*>> acts(L > 1 ? L - 1 : 0, std::vector<float*>(batch));
             for (int l = 1; l < L; ++l)
@@ -405,86 +492,72 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         }
     }
     // 3. layer by layer: weight gradient, then the masked input gradient.
-    //    BF16 with the tensor-core recompute: the gradient is packed as NHWC
-    //    BF16 hi/lo pairs; the weight gradient is a tensor-core GEMM over the
-    //    pixels (hi half), the input gradient a tensor-core convolution with
-    //    the transposed, flipped BF16 weights followed by the ReLU mask.
-    //    Otherwise FP32 SIMT (mask fused into the input-gradient conv).
-    const bool tc_bwd = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute == 1 &&
-                        batch <= WSKPN_MAX_BATCH;
-    auto tc_wg = [&](int l) { return tc_bwd && t->wg_ok[l]; };
-    auto tc_dg = [&](int l) { return tc_bwd && l >= 1 && t->lt_ok[l]; };
-    auto gcp = [&](int l) { return (c.widths[l + 1] + 15) / 16 * 16; };  // padded gradient channels of layer l
+    //    Tensor cores: the gradient is packed as NHWC BF16 hi/lo pairs; the
+    //    weight gradient is a GEMM over the pixels of the hi halves of layer
+    //    input and gradient, the input gradient a convolution with the
+    //    transposed, flipped BF16 weights, then the ReLU mask (from the NHWC
+    //    layer input).  Otherwise FP32 SIMT (mask fused into the conv).
+    auto cpad = [&](int ch) { return (ch + 15) / 16 * 16; };
     std::vector<const float*> gy(batch), xs(batch), mask(batch);
-    std::vector<float*> gx(batch), xsw(batch);
+    std::vector<float*> gx(batch);
     for (int b = 0; b < batch; ++b) gy[b] = dz + (size_t)b * 2 * M * HW;
     float* gbuf[2] = {t->gA, t->gB};
-    // Transposed weight images first: the input-gradient conv is launched as a
-    // programmatic dependent of the kernel before it and loads its weight
-    // image before waiting for that kernel, so the image must not be written
-    // by the kernel immediately before it.
-    for (int l = 1; l < L; ++l)
-        if (tc_dg(l)) {
+    if (tc_bwd) {
+        // Transposed weight images first: the input-gradient conv is launched
+        // as a programmatic dependent of the kernel before it and loads its
+        // weight image before waiting for that kernel, so the image must not
+        // be written by the kernel immediately before it.
+        for (int l = 1; l < L; ++l) {
             s = tc_dgrad_layer_pack(t->lt[l], KS, ctx->d_master + ctx->layers[l].woff, t->wt, t->zero_bias, st,
                                     ctx->err);
             if (s) return s;
         }
-    bool packed = false;  // t->gpack holds gy as NHWC hi/lo with gcp(l) channels
+        // dz -> NHWC hi/lo
+        s = launch_grad_mask_pack(const_cast<float* const*>(gy.data()), nullptr, 0, batch, 2 * M, cpad(2 * M), HW,
+                                  t->gpack, t->bias_part, dweights + ctx->layers[L - 1].boff, st, ctx->err);
+        if (s) return s;
+    }
     for (int l = L - 1; l >= 0; --l) {
         const Layer& Ly = ctx->layers[l];
-        for (int b = 0; b < batch; ++b) {
-            xs[b] = act(l, b);
-            xsw[b] = act(l, b);
+        if (tc_bwd) {
+            const int gcp = cpad(Ly.cout), xcp = cpad(Ly.cin);
+            s = launch_wgrad_tc(xn(l), 2 * xcp, t->gpack, 2 * gcp, batch, h, w, Ly.cin, Ly.cout, KS, t->wg_part,
+                                t->wg_part_floats, dweights + Ly.woff, ctx->d_status, ctx->device, st, ctx->err);
+            if (s) return s;
+            if (l == 0) break;
+            float* dst = gbuf[l % 2];
+            for (int b = 0; b < batch; ++b) gx[b] = dst + (size_t)b * Ly.cin * HW;
+            Layer& Lt = t->lt[l];
+            s = tc_layer_run(Lt, KS, t->gpack, dst, Lt.cout_p, 0, 1, 0, batch, h, w, ctx->d_status, ctx->device, st,
+                             ctx->err);
+            if (s) return s;
+            // ReLU mask of x_l in place; NHWC hi/lo for the next layer's gradients
+            s = launch_grad_mask_pack(gx.data(), xn(l), xcp, batch, Ly.cin, xcp, HW, t->gpack, t->bias_part,
+                                      dweights + ctx->layers[l - 1].boff, st, ctx->err);
+            if (s) return s;
+            for (int b = 0; b < batch; ++b) gy[b] = gx[b];
+            continue;
         }
-        if ((tc_wg(l) || tc_dg(l)) && !packed) {  // gy (already masked) -> NHWC hi/lo
-            s = launch_grad_mask_pack(const_cast<float* const*>(gy.data()), nullptr, batch, Ly.cout, gcp(l), HW,
-                                      t->gpack, st, ctx->err);
-            if (s) return s;
-            packed = true;
-        }
-        if (tc_wg(l)) {
-            const int xcp = (Ly.cin + 15) / 16 * 16;
-            s = launch_grad_mask_pack(xsw.data(), nullptr, batch, Ly.cin, xcp, HW, t->xpack, st, ctx->err, 0);
-            if (s) return s;
-            s = launch_wgrad_tc(t->xpack, xcp, t->gpack, 2 * gcp(l), gy.data(), batch, h, w, Ly.cin, Ly.cout, KS,
-                                t->wg_part, t->wg_part_floats, dweights + Ly.woff, dweights + Ly.boff, ctx->d_status,
-                                ctx->device, st, ctx->err);
-            if (s) return s;
-        } else {
-            const int nchunks = (Ly.cin + 7) / 8;
-            int G = kWgradGroups / nchunks;
-            const int ntiles = ((w + 31) / 32) * ((h + 7) / 8) * batch;
-            G = std::max(1, std::min(G, ntiles));
-            s = launch_wgrad(xs.data(), gy.data(), batch, h, w, Ly.cin, Ly.cout, KS, G, t->part, dweights + Ly.woff,
-                             dweights + Ly.boff, st, ctx->err);
-            if (s) return s;
-        }
+        for (int b = 0; b < batch; ++b) xs[b] = act(l, b);
+        const int nchunks = (Ly.cin + 7) / 8;
+        int G = kWgradGroups / nchunks;
+        const int ntiles = ((w + 31) / 32) * ((h + 7) / 8) * batch;
+        G = std::max(1, std::min(G, ntiles));
+        s = launch_wgrad(xs.data(), gy.data(), batch, h, w, Ly.cin, Ly.cout, KS, G, t->part, dweights + Ly.woff,
+                         dweights + Ly.boff, st, ctx->err);
+        if (s) return s;
         if (l == 0) break;
+        s = launch_pack_simt_transposed(ctx->d_master + Ly.woff, Ly.cin, Ly.cout, KS, t->wT[l], t->bT[l], st,
+                                        ctx->err);
+        if (s) return s;
         float* dst = gbuf[l % 2];
         for (int b = 0; b < batch; ++b) {
             gx[b] = dst + (size_t)b * Ly.cin * HW;
             mask[b] = xs[b];
         }
-        const bool next_pack = tc_wg(l - 1) || tc_dg(l - 1);
-        if (tc_dg(l)) {
-            Layer& Lt = t->lt[l];
-            s = tc_layer_run(Lt, KS, t->gpack, dst, Lt.cout_p, 0, 1, 0, batch, h, w, ctx->d_status, ctx->device, st,
-                             ctx->err);
-            if (s) return s;
-            // mask in place, and pack for the next layer's tensor-core gradients
-            s = launch_grad_mask_pack(gx.data(), mask.data(), batch, Ly.cin, next_pack ? gcp(l - 1) : 0, HW,
-                                      next_pack ? t->gpack : nullptr, st, ctx->err);
-            if (s) return s;
-            packed = next_pack;
-        } else {
-            s = launch_pack_simt_transposed(ctx->d_master + Ly.woff, Ly.cin, Ly.cout, KS, t->wT[l], t->bT[l], st,
-                                            ctx->err);
-            if (s) return s;
-            s = launch_conv_simt_masked(gy.data(), gx.data(), mask.data(), batch, h, w, Ly.cout, Ly.cin, KS,
-                                        t->wT[l], t->bT[l], 0, st, ctx->err);
-            if (s) return s;
-            packed = false;
-        }
+        s = launch_conv_simt_masked(gy.data(), gx.data(), mask.data(), batch, h, w, Ly.cout, Ly.cin, KS, t->wT[l],
+                                    t->bT[l], 0, st, ctx->err);
+        if (s) return s;
         for (int b = 0; b < batch; ++b) gy[b] = gx[b];
     }
     return WSKPN_OK;
@@ -503,7 +576,7 @@ wskpn_status wskpn_l1_loss(wskpn_ctx* ctx, const float* out, const float* target
     cudaStream_t st = (cudaStream_t)stream;
     l1_loss_kernel<<<kLossBlocks, 256, 0, st>>>(out, target, n, t->loss_part, dout);
     WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
-    sum_partials_kernel<<<1, 32, 0, st>>>(t->loss_part, kLossBlocks, 1.0 / (double)n, loss);
+    sum_partials_kernel<<<1, 256, 0, st>>>(t->loss_part, kLossBlocks, 1.0 / (double)n, loss);
     WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     return WSKPN_OK;
 }

@@ -3,7 +3,7 @@
 // training step of Eq. 1.  For y = b + W * x (KS x KS cross-correlation,
 // zero padding KS / 2) and the pre-activation gradient gy:
 //   dL/dW[o][c][dy][dx] = sum_{b,y,x} gy[o](y, x) x[c](y + dy - pad, x + dx - pad)
-//   dL/db[o]            = sum_{b,y,x} gy[o](y, x).
+// (the bias gradient, the plain sum of gy, is formed where gy is packed).
 //
 // GEMM view: K = pixels.  A work item is one segment of 128 pixels of one
 // gy row; it meets the KS x rows y + dy - pad.  Both operands are read
@@ -290,25 +290,6 @@ __global__ void wgrad_tc_reduce_kernel(const float* __restrict__ part, int Gk, i
     }
 }
 
-// db[o] = sum over frames and pixels of gy[o]: one block per channel, each
-// thread a fixed strided subset, then a fixed-order tree (deterministic).
-__global__ void bias_grad_kernel(PtrBatch<const float*> gy, int B, size_t HW, float* __restrict__ db) {
-    const int o = blockIdx.x;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) {
-        const float* g = gy.p[b] + (size_t)o * HW;
-        for (size_t p = threadIdx.x; p < HW; p += blockDim.x) s += g[p];
-    }
-    __shared__ float red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) db[o] = red[0];
-}
-
 // Channel chunks per CTA group: the largest divisor of the chunk count whose
 // accumulators fit in TMEM (KS x NCC x CPG <= 512 columns), at most 4.
 static int wgrad_tc_ncc(int KS, int nchunks, int cpg) {
@@ -378,15 +359,15 @@ bool wgrad_tc_supported(int KS, int Cin, int Cout, int B, int H, int W, int nsm,
     return true;
 }
 
-// x: channels-last BF16 [B][H][W][xcp] (xcp >= round16(Cin), channels past
-// Cin zero); gy_nhwc: channels-last BF16 [B][H][W][gcp_stride] whose first
-// round16(Cout) channels are the gradient (e.g. the hi half of a hi/lo
-// pair); gy: the same gradient as planar FP32 per frame (bias gradient).
-// part: at least the partial-sum floats wgrad_tc_supported reports for a
-// grid of nsm CTAs.
-wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gcp_stride, const float* const* gy,
-                             int B, int H, int W, int Cin, int Cout, int KS, float* part, size_t part_cap, float* dw,
-                             float* db, unsigned int* status, int device, cudaStream_t st, std::string& err) {
+// x: channels-last BF16 [B][H][W][xcp] whose first round16(Cin) channels are
+// the layer input (channels past Cin zero; e.g. the hi half of a hi/lo
+// pair); gy_nhwc: the same for the gradient, [B][H][W][gcp_stride] with
+// round16(Cout) gradient channels.  part: at least the partial-sum floats
+// wgrad_tc_supported reports for a grid of nsm CTAs.  Writes dw (OIHW); the
+// bias gradient is formed where the gradient is packed.
+wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gcp_stride, int B, int H, int W,
+                             int Cin, int Cout, int KS, float* part, size_t part_cap, float* dw, unsigned int* status,
+                             int device, cudaStream_t st, std::string& err) {
     if (B > WSKPN_MAX_BATCH) {
         err = "wgrad_tc: batch > 16";
         return WSKPN_EUNSUPPORTED;
@@ -440,10 +421,6 @@ wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gc
     const WgLaunch launch = select_wg(KS, p.cpg, p.ncc);
     WSKPN_CUDA_TRY(launch(xm, gm, a, dim3(p.gk, p.groups), p.smem, st), err);
     wgrad_tc_reduce_kernel<<<148, 256, 0, st>>>(part, p.gk, KS, p.ncc, p.cpg, Cin, Cout, dw);
-    WSKPN_CUDA_TRY(cudaGetLastError(), err);
-    PtrBatch<const float*> g{};
-    for (int b = 0; b < B; ++b) g.p[b] = gy[b];
-    bias_grad_kernel<<<Cout, 256, 0, st>>>(g, B, (size_t)H * W, db);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
