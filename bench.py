@@ -44,20 +44,20 @@ FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 148, 2032.0
 # profiles/decode_fuse_fwd_1080p.md); a kernel absent here has no capture of
 # its current version
 TRAFFIC = {
-    ("bf16", "conv1 (10->32)"): 344.2e6,
-    ("bf16", "conv2 (32->48)"): 610.4e6,
-    ("bf16", "conv3 (48->64)"): 876.0e6,
-    ("bf16", "conv4 (64->12)"): 620.2e6,
-    ("bf16", "decode_fuse_fwd"): 165.0e6,
-    ("fp32", "decode_fuse_fwd"): 165.0e6,
-    ("fp8", "decode_fuse_fwd"): 165.0e6,
+    ("bf16", "conv1 (10->32)"): 344.9e6,
+    ("bf16", "conv2 (32->48)"): 610.0e6,
+    ("bf16", "conv3 (48->64)"): 875.7e6,
+    ("bf16", "conv4 (64->12)"): 620.4e6,
+    ("bf16", "decode_fuse_fwd"): 165.4e6,
+    ("fp32", "decode_fuse_fwd"): 165.4e6,
+    ("fp8", "decode_fuse_fwd"): 165.4e6,
 }
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=300, help="timed steps (the paper averages 300 iterations)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="wskpn", choices=["wskpn", "reference"])
     p.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
@@ -164,6 +164,10 @@ def stage_rooflines(stage_ms, precision, pk, h=H, w=W):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi sampled every 50 ms by a reader thread; only the samples
+    taken between mark_start() and mark_end() (the timed steps) are
+    reported, or the last one before mark_end() when the timed region is
+    shorter than the sampling period."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -172,27 +176,50 @@ class ClockSampler:
     def __init__(self, uuid):
         self.uuid = uuid
         self.proc = None
+        self.lines = []  # (monotonic time, line)
+        self.t0 = self.t1 = None
 
-    def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+    def start(self, wait_s: float = 3.0):
+        import threading
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
         if self.uuid:
             cmd += ["-i", self.uuid]
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append((time.monotonic(), line))
+        threading.Thread(target=reader, daemon=True).start()
+        t = time.monotonic()
+        while not self.lines and time.monotonic() - t < wait_s:  # nvidia-smi is sampling
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if not self.proc:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+        t0 = self.t0 if self.t0 is not None else -1e30
+        t1 = self.t1 if self.t1 is not None else 1e30
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1]
+        if not inside:
+            before = [ln for t, ln in self.lines if t <= t1]
+            inside = before[-1:]
         sm, mx, reasons = [], [], set()
-        for line in out.strip().splitlines():
+        for line in inside:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 7:
                 continue
@@ -207,7 +234,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "reasons": sorted(reasons),
+                "window_ms": (t1 - t0) * 1e3 if self.t0 is not None and self.t1 is not None else None}
 
 
 # -------------------------------------------------------------- reference
@@ -398,7 +426,7 @@ def main():
                               "higher_is_better": False, "crops_per_s": r["crops_per_s"], "data": "synthetic"}))
         return
 
-    def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS):
+    def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS, clk=None):
         h, w = hw
         xs = xin if frame is None else frame
         d = wk.Denoiser(wb if weights is None else weights, precision=precision, max_hw=(h, w), widths=widths,
@@ -418,6 +446,8 @@ def main():
         # during the previous one's tail); the stage split comes from extra
         # steps with the events on
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if clk:
+            clk.mark_start()
         t_wall = time.perf_counter()
         for i in range(steps):
             flush.fill_(float(i))
@@ -426,6 +456,8 @@ def main():
             ev[i][1].record()
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        if clk:
+            clk.mark_end()
         barrier()
         d.profile(True)
         for i in range(max(3, steps // 2)):
@@ -447,7 +479,7 @@ def main():
         pass
     clk = ClockSampler(uuid)
     clk.start()
-    main_res = time_path(args.precision, args.steps, args.warmup)
+    main_res = time_path(args.precision, args.steps, args.warmup, clk=clk)
     clocks = clk.stop()
 
     fp32 = None
