@@ -16,6 +16,8 @@
 //           and discarded);
 //   B = gy: N = the layer's padded output channels, 16-channel chunks in
 //           separate boxes.
+// Where KS x N fits one MMA the vertical taps are folded into N instead: a
+// work item is an x row, B stacks the KS gy rows it meets (see the kernel).
 // One accumulator per (dy, channel chunk) of N columns stays in TMEM for the
 // whole kernel; each CTA walks a fixed set of work items (split K) and
 // writes its sums as partials, which a second kernel adds in a fixed order,
@@ -94,8 +96,15 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
         : "memory");
 }
 
-__host__ __device__ constexpr uint32_t stage_bytes(int KS, int CPG, int NCC) {
-    return (uint32_t)(CPG / 16) * GY_BOX + (uint32_t)(KS * NCC) * X_SLOT;
+// Shared-memory bytes of one stage: the gy boxes (one row, or with folded
+// vertical taps the KS rows an x row meets), then the x boxes (KS rows of NCC
+// chunks, or one row of NCC chunks with folded taps).
+__host__ __device__ constexpr uint32_t gy_part_bytes(int KS, int CPG, bool FOLD) {
+    return (uint32_t)((FOLD ? KS : 1) * (CPG / 16)) * GY_BOX;
+}
+__host__ __device__ constexpr int x_boxes(int KS, int NCC, bool FOLD) { return FOLD ? NCC : KS * NCC; }
+__host__ __device__ constexpr uint32_t stage_bytes(int KS, int CPG, int NCC, bool FOLD) {
+    return gy_part_bytes(KS, CPG, FOLD) + (uint32_t)x_boxes(KS, NCC, FOLD) * X_SLOT;
 }
 __host__ __device__ constexpr uint32_t tmem_alloc_cols(int cols) {
     return cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
@@ -105,14 +114,21 @@ __host__ __device__ constexpr uint32_t tmem_alloc_cols(int cols) {
 struct WgTcArgs {
     float* part;          // [gridDim.y][gridDim.x][KS * NCC][CPG][128] partial sums
     int H, W;
-    int tiles_x, nitems;  // work items: (frame, gy row, 128-pixel segment)
+    int tiles_x, nitems;  // work items: (frame, row, 128-pixel segment)
     int stages;
     unsigned int* status;
 };
 
 // Grid (split-K CTAs, channel-chunk groups); group blockIdx.y takes x chunks
 // blockIdx.y * NCC .. + NCC - 1.
-template <int KS, int CPG, int NCC>
+// Without FOLD a work item is a gy row y meeting the KS x rows y + dy - pad:
+// one MMA (N = CPG) per (dy, chunk, K step), accumulators ordered (dy, chunk).
+// With FOLD (KS x CPG <= 256) a work item is an x row y' meeting the KS gy
+// rows y' - dy + pad: the B operand stacks those rows' gradients along N
+// (N = KS x CPG, the boxes one LBO apart), so one MMA per (chunk, K step)
+// covers every vertical tap and reads its A tile once; accumulators ordered
+// (chunk, dy).  Every (x row, gy row) pair is met exactly once either way.
+template <int KS, int CPG, int NCC, bool FOLD>
 __global__ void __launch_bounds__(wgtc::THREADS, 1)
     wgrad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap gmap,
                     const WgTcArgs a) {
@@ -121,15 +137,24 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
     constexpr int NACC = KS * NCC;              // accumulators (dy, chunk)
     constexpr int NCOL = NACC * CPG;            // TMEM columns used
     constexpr uint32_t ALLOC = tmem_alloc_cols(NCOL);
-    constexpr uint32_t SB = stage_bytes(KS, CPG, NCC);
-    constexpr uint32_t GYB = (uint32_t)(CPG / 16) * GY_BOX;  // gy part of a stage
-    constexpr uint32_t TX = GYB + (uint32_t)NACC * X_BOX;   // bytes a stage's loads deliver
+    constexpr uint32_t SB = stage_bytes(KS, CPG, NCC, FOLD);
+    constexpr uint32_t GYB = gy_part_bytes(KS, CPG, FOLD);  // gy part of a stage
+    constexpr int NXB = x_boxes(KS, NCC, FOLD);
+    constexpr uint32_t TX = GYB + (uint32_t)NXB * X_BOX;    // bytes a stage's loads deliver
+    // folded: DYP vertical taps per MMA (N = DYP x CPG <= 256), the last MMA
+    // of a K step takes the remaining DYL taps
+    constexpr int DYP = FOLD ? (KS * CPG <= 256 ? KS : 256 / CPG) : 1;
+    constexpr int NPART = FOLD ? (KS + DYP - 1) / DYP : 1;
+    constexpr int DYL = KS - (NPART - 1) * DYP;
+    constexpr int N = FOLD ? DYP * CPG : CPG;  // MMA N (all but the last part)
     static_assert(KS <= 8, "horizontal shifts per A operand");
-    static_assert(CPG % 16 == 0 && CPG >= 16 && CPG <= 256, "MMA N");
+    static_assert(N % 16 == 0 && N >= 16 && N <= 256, "MMA N");
     static_assert(NCOL <= 512, "TMEM columns");
-    // kind::f16, D F32, A and B BF16, both MN-major, N = CPG, M = 128
-    constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                               ((uint32_t)(CPG >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    // kind::f16, D F32, A and B BF16, both MN-major, M = 128
+    constexpr uint32_t IDESC0 = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                ((uint32_t)(128 >> 4) << 24);
+    constexpr uint32_t IDESC = IDESC0 | ((uint32_t)(N >> 3) << 17);
+    constexpr uint32_t IDESC_L = IDESC0 | ((uint32_t)((FOLD ? DYL * CPG : CPG) >> 3) << 17);
 
     extern __shared__ __align__(1024) uint8_t dsmem[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
@@ -187,14 +212,27 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
                 const uint32_t fb = smem_u32(&full[s]);
                 const uint32_t dst = smem_u32(sm + (size_t)s * SB);
                 mbar_expect_tx(fb, TX);
+                // rows and pixels outside the image read as zeros
+                if constexpr (FOLD) {
 #pragma unroll
-                for (int j = 0; j < CPG / 16; ++j) tma_load_4d(dst + j * GY_BOX, &gmap, 16 * j, x0, y, b, fb);
+                    for (int dy = 0; dy < KS; ++dy)
 #pragma unroll
-                for (int dy = 0; dy < KS; ++dy)
+                        for (int j = 0; j < CPG / 16; ++j)
+                            tma_load_4d(dst + (dy * (CPG / 16) + j) * GY_BOX, &gmap, 16 * j, x0, y - dy + PAD, b,
+                                        fb);
 #pragma unroll
-                    for (int ci = 0; ci < NCC; ++ci)  // rows and pixels outside the image read as zeros
-                        tma_load_4d(dst + GYB + (dy * NCC + ci) * X_SLOT, &xmap, (chunk0 + ci) * 16, x0 - PAD,
-                                    y + dy - PAD, b, fb);
+                    for (int ci = 0; ci < NCC; ++ci)
+                        tma_load_4d(dst + GYB + ci * X_SLOT, &xmap, (chunk0 + ci) * 16, x0 - PAD, y, b, fb);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < CPG / 16; ++j) tma_load_4d(dst + j * GY_BOX, &gmap, 16 * j, x0, y, b, fb);
+#pragma unroll
+                    for (int dy = 0; dy < KS; ++dy)
+#pragma unroll
+                        for (int ci = 0; ci < NCC; ++ci)
+                            tma_load_4d(dst + GYB + (dy * NCC + ci) * X_SLOT, &xmap, (chunk0 + ci) * 16, x0 - PAD,
+                                        y + dy - PAD, b, fb);
+                }
             }
             if (!ok) {
                 atomicOr(a.status, ST_TIMEOUT);
@@ -224,12 +262,26 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
                 fence_after();
                 const uint64_t as = ad0 + (uint64_t)(s * (SB >> 4));
                 const uint64_t bs = bd0 + (uint64_t)(s * (SB >> 4));
+                // K steps of 16 pixels = 16 rows of 32 bytes
+                if constexpr (FOLD) {
 #pragma unroll
-                for (int k = 0; k < NACC; ++k)
+                    for (int ci = 0; ci < NCC; ++ci)
 #pragma unroll
-                    for (int j = 0; j < TPX / 16; ++j)  // K steps of 16 pixels = 16 rows of 32 bytes
-                        mma_bf16(tmem + (uint32_t)(k * CPG), as + (uint64_t)(k * (X_SLOT >> 4) + j * 32),
-                                 bs + (uint64_t)(j * 32), IDESC);
+                        for (int j = 0; j < TPX / 16; ++j)
+#pragma unroll
+                            for (int pt = 0; pt < NPART; ++pt)
+                                mma_bf16(tmem + (uint32_t)((ci * KS + pt * DYP) * CPG),
+                                         as + (uint64_t)(ci * (X_SLOT >> 4) + j * 32),
+                                         bs + (uint64_t)(pt * DYP * (CPG / 16) * (GY_BOX >> 4) + j * 32),
+                                         pt == NPART - 1 ? IDESC_L : IDESC);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NACC; ++k)
+#pragma unroll
+                        for (int j = 0; j < TPX / 16; ++j)
+                            mma_bf16(tmem + (uint32_t)(k * CPG), as + (uint64_t)(k * (X_SLOT >> 4) + j * 32),
+                                     bs + (uint64_t)(j * 32), IDESC);
+                }
                 commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
             }
             if (!ok) {
@@ -274,16 +326,18 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
 }
 
 // dW[o][c][dy][dx] = sum over the split-K CTAs g (fixed order) of partial
-// [group][g][dy * NCC + ci][o][dx * 16 + c % 16], chunk c / 16 = group * NCC + ci.
-__global__ void wgrad_tc_reduce_kernel(const float* __restrict__ part, int Gk, int KS, int NCC, int CPG, int Cin,
-                                       int Cout, float* __restrict__ dw) {
+// [group][g][k][o][dx * 16 + c % 16], chunk c / 16 = group * NCC + ci and
+// accumulator k = dy * NCC + ci, or ci * KS + dy with folded vertical taps.
+__global__ void wgrad_tc_reduce_kernel(const float* __restrict__ part, int Gk, int KS, int NCC, int CPG, int fold,
+                                       int Cin, int Cout, float* __restrict__ dw) {
     const int KK = KS * KS;
     const int n = Cout * Cin * KK;
     const size_t blk = (size_t)KS * NCC * CPG * 128;  // floats of one CTA's partials
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int dx = i % KS, dy = (i / KS) % KS, c = (i / KK) % Cin, o = i / (KK * Cin);
         const int cc = c / 16, grp = cc / NCC, ci = cc % NCC;
-        const float* p = part + (size_t)grp * Gk * blk + ((size_t)(dy * NCC + ci) * CPG + o) * 128 + dx * 16 + c % 16;
+        const int k = fold ? ci * KS + dy : dy * NCC + ci;
+        const float* p = part + (size_t)grp * Gk * blk + ((size_t)k * CPG + o) * 128 + dx * 16 + c % 16;
         float s = 0.f;
         for (int g = 0; g < Gk; ++g) s += p[(size_t)g * blk];
         dw[i] = s;
@@ -301,22 +355,29 @@ static int wgrad_tc_ncc(int KS, int nchunks, int cpg) {
 using WgLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const WgTcArgs&, dim3, size_t,
                                  cudaStream_t);
 
-template <int KS, int CPG, int NCC>
+template <int KS, int CPG, int NCC, bool FOLD>
 static cudaError_t launch_wg(const CUtensorMap& xm, const CUtensorMap& gm, const WgTcArgs& a, dim3 grid, size_t smem,
                              cudaStream_t st) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(wgrad_tc_kernel<KS, CPG, NCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<KS, CPG, NCC, FOLD>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    wgrad_tc_kernel<KS, CPG, NCC><<<grid, wgtc::THREADS, smem, st>>>(xm, gm, a);
+    wgrad_tc_kernel<KS, CPG, NCC, FOLD><<<grid, wgtc::THREADS, smem, st>>>(xm, gm, a);
     return cudaGetLastError();
 }
 
+// Vertical taps folded into N where KS x CPG fits one MMA (<= 256).  For
+// wider layers (5 x 64) the fold with two MMAs per K step (4 + 1 taps)
+// measured no faster than the unfolded form (278 vs 271 us for 48 -> 64 at
+// 16 x 256^2): each gradient row is then fetched KS times from L2.
+static constexpr bool wg_fold(int KS, int cpg) { return KS * cpg <= 256; }
+
 static WgLaunch select_wg(int KS, int cpg, int ncc) {
 #define WSKPN_WG_CASE(ks_, n_, c_) \
-    if (KS == ks_ && cpg == n_ && ncc == c_) return launch_wg<ks_, n_, c_>;
-    // widths 10-32-48-64-12 (and 64-64): (output channels, x chunks per CTA)
+    if (KS == ks_ && cpg == n_ && ncc == c_) return launch_wg<ks_, n_, c_, wg_fold(ks_, n_)>;
+    // widths 10-32-48-64-12 and 64-64: (output channels, x chunks per CTA)
     WSKPN_WG_CASE(5, 32, 1) WSKPN_WG_CASE(5, 48, 2) WSKPN_WG_CASE(5, 64, 1) WSKPN_WG_CASE(5, 16, 4)
     WSKPN_WG_CASE(3, 32, 1) WSKPN_WG_CASE(3, 48, 2) WSKPN_WG_CASE(3, 64, 1) WSKPN_WG_CASE(3, 16, 4)
+    WSKPN_WG_CASE(3, 64, 2)
 #undef WSKPN_WG_CASE
     return nullptr;
 }
@@ -338,7 +399,7 @@ static bool wgrad_tc_plan(int KS, int Cin, int Cout, int B, int H, int W, int ns
     p.gk = nsm / p.groups;
     if (p.gk < 1) p.gk = 1;
     if (p.gk > nitems) p.gk = nitems;
-    const uint32_t sb = wgtc::stage_bytes(KS, p.cpg, p.ncc);
+    const uint32_t sb = wgtc::stage_bytes(KS, p.cpg, p.ncc, wg_fold(KS, p.cpg));
     const uint32_t fixed = 1024 + 256;  // alignment slack, barriers
     const int s = (int)((wgtc::SMEM_MAX - fixed) / sb);
     if (s < 2) return false;
@@ -420,7 +481,8 @@ wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gc
     a.status = status;
     const WgLaunch launch = select_wg(KS, p.cpg, p.ncc);
     WSKPN_CUDA_TRY(launch(xm, gm, a, dim3(p.gk, p.groups), p.smem, st), err);
-    wgrad_tc_reduce_kernel<<<148, 256, 0, st>>>(part, p.gk, KS, p.ncc, p.cpg, Cin, Cout, dw);
+    wgrad_tc_reduce_kernel<<<148, 256, 0, st>>>(part, p.gk, KS, p.ncc, p.cpg, wg_fold(KS, p.cpg) ? 1 : 0, Cin, Cout,
+                                                dw);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
