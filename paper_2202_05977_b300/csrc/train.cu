@@ -206,15 +206,28 @@ __global__ void __launch_bounds__(256) grad_mask_pack_kernel(PtrBatch<float*> g,
     const int b = blockIdx.y, tid = threadIdx.x;
     const size_t p0 = (size_t)blockIdx.x * GP_TILE;
     float* __restrict__ gb = g.p[b];
-    // 1. planar -> shared (channel rows of 64 pixels)
-    for (int k = tid; k < cp * GP_TILE; k += 256) {
-        const int c = k / GP_TILE, i = k % GP_TILE;
-        sg[c][i] = c < C && p0 + i < HW ? gb[(size_t)c * HW + p0 + i] : 0.f;
+    // 1. planar -> shared (channel rows of 64 pixels); all of a thread's
+    //    loads are issued before any is stored
+    {
+        float v[64 * GP_TILE / 256];
+#pragma unroll
+        for (int u = 0; u < 64 * GP_TILE / 256; ++u) {
+            const int k = tid + 256 * u, c = k / GP_TILE, i = k % GP_TILE;
+            v[u] = c < C && p0 + i < HW ? gb[(size_t)c * HW + p0 + i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 64 * GP_TILE / 256; ++u) {
+            const int k = tid + 256 * u;
+            sg[k / GP_TILE][k % GP_TILE] = v[u];
+        }
     }
     __syncthreads();
     // 2. per (pixel, 8-channel chunk): mask, then the hi/lo pair as two 16-byte stores
     const int nq = cp / 8;
-    for (int k = tid; k < GP_TILE * nq; k += 256) {
+#pragma unroll
+    for (int u = 0; u < 8 * GP_TILE / 256; ++u) {
+        const int k = tid + 256 * u;
+        if (k >= GP_TILE * nq) break;
         const int i = k / nq, q = k % nq;
         const size_t p = p0 + i;
         if (p >= HW) continue;
@@ -247,9 +260,10 @@ __global__ void __launch_bounds__(256) grad_mask_pack_kernel(PtrBatch<float*> g,
     // 3. masked planes back (planar, whole runs) and per-channel tile sums:
     //    4 threads per channel, 16 pixels each in order, then 2 shuffle steps
     if (mask)
-        for (int k = tid; k < C * GP_TILE; k += 256) {
-            const int c = k / GP_TILE, i = k % GP_TILE;
-            if (p0 + i < HW) gb[(size_t)c * HW + p0 + i] = sg[c][i];
+#pragma unroll
+        for (int u = 0; u < 64 * GP_TILE / 256; ++u) {
+            const int k = tid + 256 * u, c = k / GP_TILE, i = k % GP_TILE;
+            if (c < C && p0 + i < HW) gb[(size_t)c * HW + p0 + i] = sg[c][i];
         }
     {
         const int c = tid / 4, part = tid % 4;
