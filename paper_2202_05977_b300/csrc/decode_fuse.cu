@@ -39,6 +39,43 @@ struct DecodeArgs {
     unsigned int* fallbacks;
 };
 
+// s[x] = sum_{d < K} w[x + d], x < NOUT (K <= 15): sums of 2, 4 and 8
+// consecutive inputs are formed once and each window is assembled from the
+// binary digits of K (all terms of one sign, so no cancellation); values no
+// output needs are never computed (the arrays are fully unrolled).
+template <int K, int NOUT>
+__device__ __forceinline__ void box_sum1(const float (&w)[NOUT + K - 1], float (&s)[NOUT]) {
+    constexpr int N1 = NOUT + K - 1;
+    constexpr int B8 = K & 8, B4 = K & 4, B2 = K & 2, B1 = K & 1;
+    constexpr int O4 = B8, O2 = B8 + B4, O1 = B8 + B4 + B2;
+    static_assert(K >= 1 && K <= 15, "window");
+    float p2[N1 > 1 ? N1 - 1 : 1], p4[N1 > 3 ? N1 - 3 : 1], p8[N1 > 7 ? N1 - 7 : 1];
+#pragma unroll
+    for (int j = 0; j + 1 < N1; ++j) p2[j] = w[j] + w[j + 1];
+#pragma unroll
+    for (int j = 0; j + 3 < N1; ++j) p4[j] = p2[j] + p2[j + 2];
+#pragma unroll
+    for (int j = 0; j + 7 < N1; ++j) p8[j] = p4[j] + p4[j + 4];
+#pragma unroll
+    for (int x = 0; x < NOUT; ++x) {
+        float t = 0.f;
+        if constexpr (B8 != 0) t = p8[x];
+        if constexpr (B4 != 0) {
+            if constexpr (O4 != 0) t += p4[x + O4];
+            else t = p4[x];
+        }
+        if constexpr (B2 != 0) {
+            if constexpr (O2 != 0) t += p2[x + O2];
+            else t = p2[x];
+        }
+        if constexpr (B1 != 0) {
+            if constexpr (O1 != 0) t += w[x + O1];
+            else t = w[x];
+        }
+        s[x] = t;
+    }
+}
+
 // Horizontal window sums of the 4 planes (E, E*y0, E*y1, E*y2) for the rows
 // the vertical pass needs.  One thread walks one (plane, row, 16-pixel
 // segment) and keeps the 16 + K - 1 inputs in registers.
@@ -55,16 +92,12 @@ __device__ __forceinline__ void hpass(const float* __restrict__ sE, float* __res
         const int ry = df::HALO - h + row;
         const float* src = sE + (ch * df::RH + ry) * df::RP + (df::HALO - h) + seg * SEG;
         float* dst = sH + (ch * df::RH + ry) * df::HP + seg * SEG;
-        float win[SEG + K - 1];
+        float win[SEG + K - 1], out[SEG];
 #pragma unroll
         for (int j = 0; j < SEG + K - 1; ++j) win[j] = src[j];
+        box_sum1<K, SEG>(win, out);
 #pragma unroll
-        for (int x = 0; x < SEG; ++x) {
-            float s = win[x];
-#pragma unroll
-            for (int d = 1; d < K; ++d) s += win[x + d];
-            dst[x] = s;
-        }
+        for (int x = 0; x < SEG; ++x) dst[x] = out[x];
     }
 }
 
@@ -75,16 +108,12 @@ __device__ __forceinline__ void vpass(const float* __restrict__ sH, float* __res
     const int x = tid % df::TW;
     const int ch = tid / df::TW;  // THREADS == 4 * TW
     const float* src = sH + (ch * df::RH + (df::HALO - h)) * df::HP + x;
-    float col[df::TH + K - 1];
+    float col[df::TH + K - 1], out[df::TH];
 #pragma unroll
     for (int j = 0; j < df::TH + K - 1; ++j) col[j] = src[j * df::HP];
+    box_sum1<K, df::TH>(col, out);
 #pragma unroll
-    for (int y = 0; y < df::TH; ++y) {
-        float s = col[y];
-#pragma unroll
-        for (int d = 1; d < K; ++d) s += col[y + d];
-        sV[(ch * df::TH + y) * df::TW + x] = s;
-    }
+    for (int y = 0; y < df::TH; ++y) sV[(ch * df::TH + y) * df::TW + x] = out[y];
 }
 
 template <int K>
