@@ -328,19 +328,24 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
 // dW[o][c][dy][dx] = sum over the split-K CTAs g (fixed order) of partial
 // [group][g][k][o][dx * 16 + c % 16], chunk c / 16 = group * NCC + ci and
 // accumulator k = dy * NCC + ci, or ci * KS + dy with folded vertical taps.
-__global__ void wgrad_tc_reduce_kernel(const float* __restrict__ part, int Gk, int KS, int NCC, int CPG, int fold,
-                                       int Cin, int Cout, float* __restrict__ dw) {
-    const int KK = KS * KS;
-    const int n = Cout * Cin * KK;
+// Threads walk the partials in their own order (consecutive TMEM lanes), so
+// every read of a CTA's partials is coalesced; the few sums are scattered to
+// dW, and lanes of shifts >= KS or padding channels are skipped.
+__global__ void wgrad_tc_reduce_kernel(const float* __restrict__ part, int Gk, int groups, int KS, int NCC, int CPG,
+                                       int fold, int Cin, int Cout, float* __restrict__ dw) {
     const size_t blk = (size_t)KS * NCC * CPG * 128;  // floats of one CTA's partials
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int dx = i % KS, dy = (i / KS) % KS, c = (i / KK) % Cin, o = i / (KK * Cin);
-        const int cc = c / 16, grp = cc / NCC, ci = cc % NCC;
-        const int k = fold ? ci * KS + dy : dy * NCC + ci;
-        const float* p = part + (size_t)grp * Gk * blk + ((size_t)k * CPG + o) * 128 + dx * 16 + c % 16;
+    const size_t n = (size_t)groups * blk;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int row = (int)(i % 128), o = (int)((i / 128) % CPG), k = (int)((i / (128 * (size_t)CPG)) % (KS * NCC));
+        const int grp = (int)(i / blk);
+        const int dx = row / 16, c16 = row % 16;
+        const int dy = fold ? k % KS : k / NCC, ci = fold ? k / KS : k % NCC;
+        const int c = (grp * NCC + ci) * 16 + c16;
+        if (dx >= KS || c >= Cin || o >= Cout) continue;
+        const float* p = part + (size_t)grp * Gk * blk + (i % blk);
         float s = 0.f;
         for (int g = 0; g < Gk; ++g) s += p[(size_t)g * blk];
-        dw[i] = s;
+        dw[(((size_t)o * Cin + c) * KS + dy) * KS + dx] = s;
     }
 }
 
@@ -481,8 +486,8 @@ wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gc
     a.status = status;
     const WgLaunch launch = select_wg(KS, p.cpg, p.ncc);
     WSKPN_CUDA_TRY(launch(xm, gm, a, dim3(p.gk, p.groups), p.smem, st), err);
-    wgrad_tc_reduce_kernel<<<148, 256, 0, st>>>(part, p.gk, KS, p.ncc, p.cpg, wg_fold(KS, p.cpg) ? 1 : 0, Cin, Cout,
-                                                dw);
+    wgrad_tc_reduce_kernel<<<148 * 4, 256, 0, st>>>(part, p.gk, p.groups, KS, p.ncc, p.cpg,
+                                                    wg_fold(KS, p.cpg) ? 1 : 0, Cin, Cout, dw);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
