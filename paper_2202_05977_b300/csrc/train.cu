@@ -64,7 +64,8 @@ struct TrainWs {
     bool wg_ok[WSKPN_MAX_LAYERS] = {};  // layer l's weight gradient has a tensor-core kernel
     float* wt = nullptr;                // transposed weights of one layer (packing scratch)
     float* zero_bias = nullptr;         // [64] zeros
-    void* gpack = nullptr;              // gradient as NHWC BF16 hi/lo [B][H][W][2 cp]
+    void* gpack = nullptr;              // gradient as NHWC BF16 hi/lo [B][H][W][2 cp], two buffers
+    void* gpack2 = nullptr;
     void* xnhwc = nullptr;              // layer inputs x_0 .. x_{L-1}, NHWC BF16 hi/lo, layer after layer
     size_t x_off[WSKPN_MAX_LAYERS] = {};  // byte offsets in xnhwc
     size_t x_bytes = 0;
@@ -95,6 +96,7 @@ static void free_train(TrainWs* t) {
     cudaFree(t->zero_bias);
     cudaFree(t->gpack);
     cudaFree(t->xnhwc);
+    cudaFree(t->gpack2);
     cudaFree(t->bias_part);
     cudaFree(t->wg_part);
     delete t;
@@ -170,6 +172,7 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
                 return WSKPN_ECUDA;
             }
             WSKPN_TRY_ALLOC(t->gpack, gcp * 2 * sizeof(uint16_t) * t->px);
+            WSKPN_TRY_ALLOC(t->gpack2, gcp * 2 * sizeof(uint16_t) * t->px);
             WSKPN_TRY_ALLOC(t->wg_part, t->wg_part_floats * sizeof(float));
             // tiles of GP_TILE pixels per frame, for every frame of a call
             const size_t tiles = (size_t)c.max_batch * (((size_t)c.max_h * c.max_w + GP_TILE - 1) / GP_TILE);
@@ -276,6 +279,69 @@ __global__ void __launch_bounds__(256) grad_mask_pack_kernel(PtrBatch<float*> g,
     }
 }
 
+// The input gradient of a layer, written by its tensor-core convolution as
+// NHWC BF16 hi/lo pairs g [B][HW][hi(cp) | lo(cp)], times the ReLU derivative
+// of the layer input (mask, NHWC hi/lo with the same cp: x = hi + lo > 0),
+// in place; channels C .. cp - 1 are set to zero.  One block per 64 pixels
+// of one frame; threads walk (pixel, 8-channel chunk) pairs, so every load
+// and store is a whole 16-byte piece of consecutive runs.  bias_part
+// [tiles][64] receives each tile's per-channel sum of the masked gradient
+// (pixels in a fixed order).
+__global__ void __launch_bounds__(256) grad_mask_nhwc_kernel(uint4* __restrict__ g, const uint4* __restrict__ mask,
+                                                             int C, int cp, size_t HW, float* __restrict__ bias_part) {
+    __shared__ float sg[64][GP_TILE + 1];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const size_t p0 = (size_t)blockIdx.x * GP_TILE;
+    const int nq = cp / 8;
+#pragma unroll
+    for (int u = 0; u < 8 * GP_TILE / 256; ++u) {
+        const int k = tid + 256 * u;
+        if (k >= GP_TILE * nq) break;
+        const int i = k / nq, q = k % nq;
+        const size_t p = p0 + i;
+        float v[8];
+        if (p < HW) {
+            const size_t px = ((size_t)b * HW + p) * (size_t)(cp / 4);  // 2 cp BF16 = cp / 4 uint4
+            uint4 gh = g[px + q], gl = g[px + cp / 8 + q];
+            const uint4 mh = mask[px + q], ml = mask[px + cp / 8 + q];
+            float fgh[8], fgl[8], fmh[8], fml[8];
+            bf16x8_to_float(gh, fgh);
+            bf16x8_to_float(gl, fgl);
+            bf16x8_to_float(mh, fmh);
+            bf16x8_to_float(ml, fml);
+            __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&gh);
+            __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&gl);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bool keep = q * 8 + j < C && fmh[j] + fml[j] > 0.f;
+                v[j] = keep ? fgh[j] + fgl[j] : 0.f;
+                if (!keep) {
+                    hh[j] = __float2bfloat16_rn(0.f);
+                    ll[j] = __float2bfloat16_rn(0.f);
+                }
+            }
+            g[px + q] = gh;
+            g[px + cp / 8 + q] = gl;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sg[q * 8 + j][i] = v[j];
+    }
+    __syncthreads();
+    {
+        const int c = tid / 4, part = tid % 4;
+        float s = 0.f;
+        if (c < cp)
+#pragma unroll
+            for (int i = 0; i < GP_TILE / 4; ++i) s += sg[c][part * (GP_TILE / 4) + i];
+        s += __shfl_down_sync(0xffffffffu, s, 1);
+        s += __shfl_down_sync(0xffffffffu, s, 2);
+        if (part == 0 && c < C) bias_part[((size_t)b * gridDim.x + blockIdx.x) * 64 + c] = s;
+    }
+}
+
 // db[o] = sum over the tiles (fixed order: thread t adds tiles t, t + 256,
 // ..., then a fixed tree) of bias_part[tile][o]; one block per channel.
 __global__ void bias_from_tiles_kernel(const float* __restrict__ part, int ntiles, float* __restrict__ db) {
@@ -290,6 +356,21 @@ __global__ void bias_from_tiles_kernel(const float* __restrict__ part, int ntile
         __syncthreads();
     }
     if (threadIdx.x == 0) db[o] = red[0];
+}
+
+static wskpn_status launch_grad_mask_nhwc(void* g, const void* mask, int B, int C, int cp, size_t HW,
+                                          float* bias_part, float* db, cudaStream_t st, std::string& err) {
+    if (C > 64 || cp > 64 || cp % 16 || B > WSKPN_MAX_BATCH) {
+        err = "gradient mask: at most 64 channels and 16 frames";
+        return WSKPN_EUNSUPPORTED;
+    }
+    const unsigned tiles = (unsigned)((HW + GP_TILE - 1) / GP_TILE);
+    grad_mask_nhwc_kernel<<<dim3(tiles, B), 256, 0, st>>>(static_cast<uint4*>(g), static_cast<const uint4*>(mask), C,
+                                                          cp, HW, bias_part);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    bias_from_tiles_kernel<<<C, 256, 0, st>>>(bias_part, (int)tiles * B, db);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    return WSKPN_OK;
 }
 
 // Packs (and with a mask, masks) the gradient of a layer with C output
@@ -516,6 +597,7 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
     std::vector<float*> gx(batch);
     for (int b = 0; b < batch; ++b) gy[b] = dz + (size_t)b * 2 * M * HW;
     float* gbuf[2] = {t->gA, t->gB};
+    void* gcur = t->gpack;  // tensor cores: gy of the current layer, NHWC hi/lo
     if (tc_bwd) {
         // Transposed weight images first: the input-gradient conv is launched
         // as a programmatic dependent of the kernel before it and loads its
@@ -535,21 +617,20 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         const Layer& Ly = ctx->layers[l];
         if (tc_bwd) {
             const int gcp = cpad(Ly.cout), xcp = cpad(Ly.cin);
-            s = launch_wgrad_tc(xn(l), 2 * xcp, t->gpack, 2 * gcp, batch, h, w, Ly.cin, Ly.cout, KS, t->wg_part,
+            s = launch_wgrad_tc(xn(l), 2 * xcp, gcur, 2 * gcp, batch, h, w, Ly.cin, Ly.cout, KS, t->wg_part,
                                 t->wg_part_floats, dweights + Ly.woff, ctx->d_status, ctx->device, st, ctx->err);
             if (s) return s;
             if (l == 0) break;
-            float* dst = gbuf[l % 2];
-            for (int b = 0; b < batch; ++b) gx[b] = dst + (size_t)b * Ly.cin * HW;
+            // input gradient straight to NHWC hi/lo, then the ReLU mask of x_l in place
+            void* gnext = gcur == t->gpack ? t->gpack2 : t->gpack;
             Layer& Lt = t->lt[l];
-            s = tc_layer_run(Lt, KS, t->gpack, dst, Lt.cout_p, 0, 1, 0, batch, h, w, ctx->d_status, ctx->device, st,
+            s = tc_layer_run(Lt, KS, gcur, gnext, Lt.cout_p, 0, 0, 0, batch, h, w, ctx->d_status, ctx->device, st,
                              ctx->err);
             if (s) return s;
-            // ReLU mask of x_l in place; NHWC hi/lo for the next layer's gradients
-            s = launch_grad_mask_pack(gx.data(), xn(l), xcp, batch, Ly.cin, xcp, HW, t->gpack, t->bias_part,
+            s = launch_grad_mask_nhwc(gnext, xn(l), batch, Ly.cin, xcp, HW, t->bias_part,
                                       dweights + ctx->layers[l - 1].boff, st, ctx->err);
             if (s) return s;
-            for (int b = 0; b < batch; ++b) gy[b] = gx[b];
+            gcur = gnext;
             continue;
         }
         for (int b = 0; b < batch; ++b) xs[b] = act(l, b);
