@@ -134,7 +134,17 @@ def conv_flops(l, h=H, w=W):
     return 2.0 * WIDTHS[l] * WIDTHS[l + 1] * KS * KS * h * w
 
 
-def stage_rooflines(stage_ms, precision, pk, h=H, w=W):
+def tensor_peak(pk, clocks):
+    """The BF16 tensor peak a timed region is compared with: the sustained
+    figure of MEASURED_PEAKS.json (matmul back to back for seconds, under the
+    power cap) when the region itself ran under the power cap or lasted a
+    second or more, else the burst figure.  Returns (TFLOP/s, which)."""
+    sustained = bool(clocks) and ("sw_power_cap" in clocks.get("reasons", [])
+                                  or (clocks.get("window_ms") or 0.0) >= 1000.0)
+    return (pk["bf16_tflops_sustained"], "sustained") if sustained else (pk["bf16_tflops"], "burst")
+
+
+def stage_rooflines(stage_ms, precision, pk, h=H, w=W, tpeak=None):
     """Achieved throughput and fraction of the measured peak for every stage
     (algorithmic FLOPs for the convolutions, algorithmic bytes for the
     streaming kernels), from the stage times of one denoise."""
@@ -155,7 +165,8 @@ def stage_rooflines(stage_ms, precision, pk, h=H, w=W):
             if precision == "fp32":
                 peak, bound = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12, "alu"
             else:
-                peak, bound = pk["bf16_tflops"] * (2.0 if precision == "fp8" else 1.0), "tensor"
+                peak = (tpeak if tpeak is not None else pk["bf16_tflops"]) * (2.0 if precision == "fp8" else 1.0)
+                bound = "tensor"
             kname = f"conv{i} ({WIDTHS[i - 1]}->{WIDTHS[i]})"
             out[f"conv{i}"] = {"bound": bound, "achieved": tf, "unit": "TFLOP/s", "frac": tf / peak,
                                "traffic": TRAFFIC.get((precision, kname)) if (h, w) == (H, W) else None}
@@ -620,11 +631,14 @@ def main():
             peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
             bound, psrc = "alu", "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz"
         else:
-            peak = pk["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
-            bound, psrc = "tensor", f"{pk['source']} bf16 burst" + (" x2 (fp8 nominal ratio)" if args.precision == "fp8" else "")
+            tp, which = tensor_peak(pk, clocks)
+            peak = tp * (2.0 if args.precision == "fp8" else 1.0)
+            bound, psrc = "tensor", f"{pk['source']} bf16 {which}" + (" x2 (fp8 nominal ratio)" if args.precision == "fp8" else "")
         kname = f"conv{l + 1} ({WIDTHS[l]}->{WIDTHS[l + 1]})"
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC.get((args.precision, kname)), "kernel": kname, "peak_source": psrc}
+        if args.precision != "fp32":
+            roof["frac_of_burst"] = achieved / (pk["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0))
     else:
         name = "prep" if dom == 0 else "decode_fuse_fwd"
         byts = (40 + {"fp32": 40, "bf16": 64, "fp8": 64}[args.precision]) * H * W if dom == 0 \
@@ -678,7 +692,8 @@ def main():
             "p99_step_ms": sorted(main_res["per"])[min(len(main_res["per"]) - 1,
                                                       int(round(0.99 * (len(main_res["per"]) - 1))))],
             "roofline": roof,
-            "stage_rooflines": stage_rooflines(main_res["stage_ms"], args.precision, pk),
+            "stage_rooflines": stage_rooflines(main_res["stage_ms"], args.precision, pk,
+                                               tpeak=tensor_peak(pk, clocks)[0]),
             "gpu_launches": args.steps * (L + 2),
             "clocks": clocks,
         }
