@@ -219,10 +219,18 @@ wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int 
 /* Backward pass: from dout = dL/d(out) [batch][3][h][w] and z_saved,
  * writes dL/dweights (device, wskpn_n_weights floats, blob layout) and,
  * if dz_out is not NULL, dL/dz [batch][2M][h][w].  The activations are
- * recomputed from the frames in FP32 and the convolution gradients run in
- * FP32; the ReLU derivative at 0 is 0.  The first training call on a
- * context allocates its training workspaces.  batch <= 16.  Errors: EINVAL,
- * ENOMEM, ECUDA. */
+ * recomputed from the frames (not kept from the forward).  BF16 context
+ * (default WSKPN_TUNE_TRAIN_RECOMPUTE = 1): recomputed with the context's
+ * own tensor-core convolutions, as its forward computes them; the input
+ * gradient of each layer is a tensor-core convolution of the gradient (BF16
+ * hi/lo pairs) with the transposed, flipped BF16 weights, the weight
+ * gradient a tensor-core GEMM over the pixels (BF16 operands), both with
+ * FP32 accumulation and a fixed summation order (the result does not
+ * depend on scheduling).  FP32 and FP8 contexts, and the other tuning
+ * values: FP32 recompute and FP32 gradient kernels.  The ReLU derivative
+ * at 0 is 0.  The first training call on a context allocates its training
+ * workspaces (of the order of 1.5 KB per pixel of max_batch x max_h x
+ * max_w).  batch <= 16.  Errors: EINVAL, ENOMEM, ECUDA. */
 wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
                             const float* z_saved, const float* dout, float* dz_out, float* dweights,
                             void* stream);

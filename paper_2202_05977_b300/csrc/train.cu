@@ -48,8 +48,9 @@ struct TrainWs {
     size_t px = 0;
     float* acts = nullptr;      // x_0 .. x_{L-1}, planar FP32, layer after layer
     size_t act_off[WSKPN_MAX_LAYERS] = {};
-    float* gA = nullptr;        // gradient ping-pong [B][maxw][H][W]
+    float* gA = nullptr;        // gradient ping-pong [B][maxw][H][W] (FP32 gradient paths, on first use)
     float* gB = nullptr;
+    size_t g_floats = 0;
     float* dz = nullptr;        // [B][2M][H][W]
     float* dscratch = nullptr;  // reconstruction-backward scratch [B][5M+3][H][W]
     float* part = nullptr;      // wgrad partial sums
@@ -131,8 +132,7 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
     for (int l = 1; l <= L; ++l) maxw = std::max(maxw, c.widths[l]);
     for (int l = 0; l < L; ++l) maxcin = std::max(maxcin, c.widths[l]);
     t->acts_floats = off;  // allocated by the first backward that needs planar activations
-    WSKPN_TRY_ALLOC(t->gA, (size_t)maxw * t->px * sizeof(float));
-    WSKPN_TRY_ALLOC(t->gB, (size_t)maxw * t->px * sizeof(float));
+    t->g_floats = (size_t)maxw * t->px;
     WSKPN_TRY_ALLOC(t->dz, (size_t)2 * M * t->px * sizeof(float));
     WSKPN_TRY_ALLOC(t->dscratch, (size_t)(5 * M + 3) * t->px * sizeof(float));
     WSKPN_TRY_ALLOC(t->part, wgrad_part_floats(maxcin, KS, kWgradGroups) * sizeof(float));
@@ -596,6 +596,10 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
     std::vector<const float*> gy(batch), xs(batch), mask(batch);
     std::vector<float*> gx(batch);
     for (int b = 0; b < batch; ++b) gy[b] = dz + (size_t)b * 2 * M * HW;
+    if (!tc_bwd && !t->gA) {
+        WSKPN_TRY_ALLOC(t->gA, t->g_floats * sizeof(float));
+        WSKPN_TRY_ALLOC(t->gB, t->g_floats * sizeof(float));
+    }
     float* gbuf[2] = {t->gA, t->gB};
     void* gcur = t->gpack;  // tensor cores: gy of the current layer, NHWC hi/lo
     if (tc_bwd) {
