@@ -182,17 +182,15 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
     return WSKPN_OK;
 }
 
-// Gradient planes g (planar FP32 [C][HW] per frame, C <= 64), one block per
-// tile of 64 pixels of one frame, transposed through shared memory so that
-// both layouts are read and written in whole runs.  With a mask (the layer's
-// input activation as NHWC BF16 hi/lo pairs [B][HW][hi(mcp) | lo(mcp)], mcp a
-// multiple of 16 and >= C, x = hi + lo) g is multiplied in place by the ReLU
-// derivative (x > 0).  The planes are written channels-last as BF16 hi/lo
-// pairs nhwc [B][HW][hi(cp) | lo(cp)] (channels C .. cp - 1 zero,
-// lo = bf16(g - bf16(g))): the input of a tensor-core input-gradient
-// convolution, whose hi half also feeds the weight gradient.  bias_part
-// [tiles][64] receives each tile's per-channel sum of the (masked) gradient
-// (pixels in a fixed order), from which the bias gradient is added up.
+// Gradient planes g (planar FP32 [C][HW] per frame, C <= CMAX) written
+// channels-last as BF16 hi/lo pairs nhwc [B][HW][hi(cp) | lo(cp)] (channels
+// C .. cp - 1 zero, lo = bf16(g - bf16(g))): the input of a tensor-core
+// input-gradient convolution, whose hi half also feeds the weight gradient.
+// One block per tile of 4096 / CMAX pixels of one frame, transposed through
+// shared memory so that both layouts are read and written in whole runs
+// (every thread issues its 16 loads before storing any).  bias_part
+// [tiles][64] receives each tile's per-channel sum (pixels in a fixed order),
+// from which the bias gradient is added up.
 __device__ __forceinline__ void bf16x8_to_float(const uint4& u, float f[8]) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
@@ -202,79 +200,58 @@ __device__ __forceinline__ void bf16x8_to_float(const uint4& u, float f[8]) {
         f[2 * j + 1] = t.y;
     }
 }
-__global__ void __launch_bounds__(256) grad_mask_pack_kernel(PtrBatch<float*> g, const uint4* __restrict__ mask,
-                                                             int mcp, int C, int cp, size_t HW,
-                                                             uint4* __restrict__ nhwc, float* __restrict__ bias_part) {
-    __shared__ float sg[64][GP_TILE + 1];
+template <int CMAX>
+__global__ void __launch_bounds__(256) grad_pack_kernel(PtrBatch<const float*> g, int C, int cp, size_t HW,
+                                                        uint4* __restrict__ nhwc, float* __restrict__ bias_part) {
+    constexpr int TILE = 4096 / CMAX;  // pixels per block
+    constexpr int TPC = 256 / CMAX;    // threads per channel in the tile sums
+    __shared__ float sg[CMAX][TILE + 1];
     const int b = blockIdx.y, tid = threadIdx.x;
-    const size_t p0 = (size_t)blockIdx.x * GP_TILE;
-    float* __restrict__ gb = g.p[b];
-    // 1. planar -> shared (channel rows of 64 pixels); all of a thread's
-    //    loads are issued before any is stored
+    const size_t p0 = (size_t)blockIdx.x * TILE;
+    const float* __restrict__ gb = g.p[b];
     {
-        float v[64 * GP_TILE / 256];
+        float v[16];
 #pragma unroll
-        for (int u = 0; u < 64 * GP_TILE / 256; ++u) {
-            const int k = tid + 256 * u, c = k / GP_TILE, i = k % GP_TILE;
+        for (int u = 0; u < 16; ++u) {
+            const int k = tid + 256 * u, c = k / TILE, i = k % TILE;
             v[u] = c < C && p0 + i < HW ? gb[(size_t)c * HW + p0 + i] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 64 * GP_TILE / 256; ++u) {
+        for (int u = 0; u < 16; ++u) {
             const int k = tid + 256 * u;
-            sg[k / GP_TILE][k % GP_TILE] = v[u];
+            sg[k / TILE][k % TILE] = v[u];
         }
     }
     __syncthreads();
-    // 2. per (pixel, 8-channel chunk): mask, then the hi/lo pair as two 16-byte stores
+    // per (pixel, 8-channel chunk): the hi/lo pair as two 16-byte stores
     const int nq = cp / 8;
 #pragma unroll
-    for (int u = 0; u < 8 * GP_TILE / 256; ++u) {
+    for (int u = 0; u < 2; ++u) {
         const int k = tid + 256 * u;
-        if (k >= GP_TILE * nq) break;
+        if (k >= TILE * nq) break;
         const int i = k / nq, q = k % nq;
         const size_t p = p0 + i;
         if (p >= HW) continue;
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = sg[q * 8 + j][i];
-        if (mask && q * 8 < C) {
-            const uint4* mpx = mask + ((size_t)b * HW + p) * (size_t)(mcp / 4);  // 2 mcp BF16
-            float mh[8], ml[8];
-            bf16x8_to_float(mpx[q], mh);
-            bf16x8_to_float(mpx[mcp / 8 + q], ml);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (!(mh[j] + ml[j] > 0.f)) v[j] = 0.f;
-                sg[q * 8 + j][i] = v[j];
-            }
-        }
         __nv_bfloat162 h[4], l[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            const float a = sg[q * 8 + 2 * j][i], c = sg[q * 8 + 2 * j + 1][i];
+            h[j] = __floats2bfloat162_rn(a, c);
             const float2 hf = __bfloat1622float2(h[j]);
-            l[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+            l[j] = __floats2bfloat162_rn(a - hf.x, c - hf.y);
         }
         uint4* dst = nhwc + ((size_t)b * HW + p) * (size_t)(cp / 4);  // 2 cp BF16 = cp / 4 uint4
         dst[q] = *reinterpret_cast<const uint4*>(h);
         dst[cp / 8 + q] = *reinterpret_cast<const uint4*>(l);
     }
-    __syncthreads();
-    // 3. masked planes back (planar, whole runs) and per-channel tile sums:
-    //    4 threads per channel, 16 pixels each in order, then 2 shuffle steps
-    if (mask)
-#pragma unroll
-        for (int u = 0; u < 64 * GP_TILE / 256; ++u) {
-            const int k = tid + 256 * u, c = k / GP_TILE, i = k % GP_TILE;
-            if (c < C && p0 + i < HW) gb[(size_t)c * HW + p0 + i] = sg[c][i];
-        }
+    // per-channel tile sums: TPC threads per channel, 16 pixels each in order
     {
-        const int c = tid / 4, part = tid % 4;
+        const int c = tid / TPC, part = tid % TPC;
         float s = 0.f;
 #pragma unroll
-        for (int i = 0; i < GP_TILE / 4; ++i) s += sg[c][part * (GP_TILE / 4) + i];
-        s += __shfl_down_sync(0xffffffffu, s, 1);
-        s += __shfl_down_sync(0xffffffffu, s, 2);
+        for (int i = 0; i < 16; ++i) s += sg[c][part * 16 + i];
+#pragma unroll
+        for (int o = 1; o < TPC; o <<= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (part == 0 && c < C) bias_part[((size_t)b * gridDim.x + blockIdx.x) * 64 + c] = s;
     }
 }
@@ -373,20 +350,22 @@ static wskpn_status launch_grad_mask_nhwc(void* g, const void* mask, int B, int 
     return WSKPN_OK;
 }
 
-// Packs (and with a mask, masks) the gradient of a layer with C output
-// channels, then writes its bias gradient db.
-static wskpn_status launch_grad_mask_pack(float* const* g, const void* mask, int mcp, int B, int C, int cp,
-                                          size_t HW, void* nhwc, float* bias_part, float* db, cudaStream_t st,
-                                          std::string& err) {
-    if (C > 64 || cp > 64 || B > WSKPN_MAX_BATCH) {
+// Packs the gradient of a layer with C output channels (planar FP32) as
+// NHWC BF16 hi/lo pairs with cp channels, then writes its bias gradient db.
+static wskpn_status launch_grad_pack(const float* const* g, int B, int C, int cp, size_t HW, void* nhwc,
+                                     float* bias_part, float* db, cudaStream_t st, std::string& err) {
+    if (C > cp || cp > 64 || cp % 16 || B > WSKPN_MAX_BATCH) {
         err = "gradient pack: at most 64 channels and 16 frames";
         return WSKPN_EUNSUPPORTED;
     }
-    PtrBatch<float*> gp{};
+    PtrBatch<const float*> gp{};
     for (int b = 0; b < B; ++b) gp.p[b] = g[b];
-    const unsigned tiles = (unsigned)((HW + GP_TILE - 1) / GP_TILE);
-    grad_mask_pack_kernel<<<dim3(tiles, B), 256, 0, st>>>(gp, static_cast<const uint4*>(mask), mcp, C, cp, HW,
-                                                          static_cast<uint4*>(nhwc), bias_part);
+    const int tile = cp <= 16 ? 256 : 64;
+    const unsigned tiles = (unsigned)((HW + tile - 1) / tile);
+    if (cp <= 16)
+        grad_pack_kernel<16><<<dim3(tiles, B), 256, 0, st>>>(gp, C, cp, HW, static_cast<uint4*>(nhwc), bias_part);
+    else
+        grad_pack_kernel<64><<<dim3(tiles, B), 256, 0, st>>>(gp, C, cp, HW, static_cast<uint4*>(nhwc), bias_part);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     bias_from_tiles_kernel<<<C, 256, 0, st>>>(bias_part, (int)tiles * B, db);
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
@@ -613,8 +592,8 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
             if (s) return s;
         }
         // dz -> NHWC hi/lo
-        s = launch_grad_mask_pack(const_cast<float* const*>(gy.data()), nullptr, 0, batch, 2 * M, cpad(2 * M), HW,
-                                  t->gpack, t->bias_part, dweights + ctx->layers[L - 1].boff, st, ctx->err);
+        s = launch_grad_pack(gy.data(), batch, 2 * M, cpad(2 * M), HW, t->gpack, t->bias_part,
+                             dweights + ctx->layers[L - 1].boff, st, ctx->err);
         if (s) return s;
     }
     for (int l = L - 1; l >= 0; --l) {
