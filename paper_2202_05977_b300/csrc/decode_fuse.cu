@@ -605,8 +605,10 @@ wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r
 //            footprint's minimum LSE, then
 //            dz_i(q) = exp(I_i(q) - s) (sum_c y_c(q) S_c(q) - S_B(q)).
 // Footprints whose LSE range exceeds 80 take an exact per-window loop.
-// Scratch layout per frame: planes [LSE_0..M-1, alpha_0..M-1,
-// R_{0,0..2}, ..., R_{M-1,0..2}, g_0..2] = 5M + 3 planes of H x W.
+// Scratch layout per frame: planes [LSE_0..M-1, hR_0..M-1,
+// h_{0,0..2}, ..., h_{M-1,0..2}, (3 unused)] = 5M + 3 planes of H x W, with
+// h_ic = alpha_i g_c and hR_i = sum_c h_ic R_ic: kernel 2 reads four
+// planes per footprint pixel besides LSE.
 // ======================================================================
 
 struct DecodeBwdArgs {
@@ -667,13 +669,6 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd1_kernel(Decode
         for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) alpha[j][i] = in ? alpha[j][i] / s : 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) gc[j][c] = in ? (a[c * HW + g] + eps) * G[c * HW + g] : 0.f;
-        if (in) {
-#pragma unroll
-            for (int i = 0; i < WSKPN_MAX_KERNELS; ++i)
-                if (i < M) sc[(size_t)(M + i) * HW + g] = alpha[j][i];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sc[(size_t)(5 * M + c) * HW + g] = gc[j][c];
-        }
     }
 
     for (int i = 0; i < M; ++i) {
@@ -707,9 +702,19 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd1_kernel(Decode
                 L = mw + logf(Dw);
                 if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
             }
-            sc[(size_t)i * HW + g] = L;
+            float al = 0.f;  // alpha_i of this pixel (registers indexed by constants only)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sc[(size_t)(2 * M + 3 * i + c) * HW + g] = R[c];
+            for (int q = 0; q < WSKPN_MAX_KERNELS; ++q)
+                if (q == i) al = alpha[j][q];
+            sc[(size_t)i * HW + g] = L;
+            float hR = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float hc = al * gc[j][c];
+                sc[(size_t)(2 * M + 3 * i + c) * HW + g] = hc;
+                hR += hc * R[c];
+            }
+            sc[(size_t)(M + i) * HW + g] = hR;
             const float d = gc[j][0] * R[0] + gc[j][1] * R[1] + gc[j][2] * R[2];
 #pragma unroll
             for (int q = 0; q < WSKPN_MAX_KERNELS; ++q)
@@ -769,17 +774,22 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd2_kernel(Decode
         const int h = k / 2;
         const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
         const float* __restrict__ Li = sc + (size_t)i * HW;
-        const float* __restrict__ Ai = sc + (size_t)(M + i) * HW;
-        const float* __restrict__ Ri = sc + (size_t)(2 * M + 3 * i) * HW;
-        const float* __restrict__ gcp = sc + (size_t)(5 * M) * HW;
-        // footprint minimum and maximum of LSE
+        const float* __restrict__ HRi = sc + (size_t)(M + i) * HW;
+        const float* __restrict__ Hi = sc + (size_t)(2 * M + 3 * i) * HW;
+        // footprint minimum and maximum of LSE; the footprint's LSE values
+        // stay in registers for the plane pass (all loads issued first)
+        constexpr int FPER = ((df::TH + 2 * df::HALO) * (df::TW + 2 * df::HALO) + df::THREADS - 1) / df::THREADS;
+        float lv[FPER];
         float mn = INFINITY, mx = -INFINITY;
-        for (int t = tid; t < nr * nc; t += df::THREADS) {
+#pragma unroll
+        for (int u = 0; u < FPER; ++u) {
+            const int t = tid + u * df::THREADS;
             const int gy = ty0 - h + t / nc, gx = tx0 - h + t % nc;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                const float v = Li[(size_t)gy * W + gx];
-                mn = fminf(mn, v);
-                mx = fmaxf(mx, v);
+            const bool in = t < nr * nc && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            lv[u] = in ? Li[(size_t)gy * W + gx] : 0.f;
+            if (in) {
+                mn = fminf(mn, lv[u]);
+                mx = fmaxf(mx, lv[u]);
             }
         }
 #pragma unroll
@@ -801,19 +811,21 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd2_kernel(Decode
         }
         const bool exact = mx - mn > 80.f;  // block-uniform
         if (!exact) {
-            for (int t = tid; t < nr * nc; t += df::THREADS) {
+#pragma unroll
+            for (int u = 0; u < FPER; ++u) {
+                const int t = tid + u * df::THREADS;
+                if (t >= nr * nc) break;
                 const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
                 const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
                 const int o = ry * df::RP + rx;
                 float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
                 if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
                     const size_t g = (size_t)gy * W + gx;
-                    const float u = expf(mn - Li[g]) * Ai[g];
-                    const float h0 = u * gcp[g], h1 = u * gcp[HW + g], h2 = u * gcp[2 * HW + g];
-                    v0 = h0;
-                    v1 = h1;
-                    v2 = h2;
-                    v3 = h0 * Ri[g] + h1 * Ri[HW + g] + h2 * Ri[2 * HW + g];
+                    const float e = expf(mn - lv[u]);
+                    v0 = e * Hi[g];
+                    v1 = e * Hi[HW + g];
+                    v2 = e * Hi[2 * HW + g];
+                    v3 = e * HRi[g];
                 }
                 sE[o] = v0;
                 sE[df::RH * df::RP + o] = v1;
@@ -850,10 +862,9 @@ __global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd2_kernel(Decode
                 for (int py = max(gy - h, 0); py <= min(gy + h, H - 1); ++py)
                     for (int px = max(gx - h, 0); px <= min(gx + h, W - 1); ++px) {
                         const size_t gp = (size_t)py * W + px;
-                        const float al = Ai[gp];
-                        float t = 0.f;
+                        float t = -HRi[gp];
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) t += gcp[c * HW + gp] * al * (yq[j][c] - Ri[c * HW + gp]);
+                        for (int c = 0; c < 3; ++c) t += Hi[c * HW + gp] * yq[j][c];
                         v += expf(zq - Li[gp]) * t;
                     }
                 if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
