@@ -102,6 +102,26 @@ def test_bf16_1080p_sampled_matches_oracle(wk):
     assert fmx < TOL_BF16
 
 
+@pytest.mark.parametrize("H,W,seed", [(720, 1280, 1), (1440, 2560, 3)])
+def test_bf16_other_resolutions_match_oracle(wk, H, W, seed):
+    """The resolution sweep's other frames (720p seed 1, 1440p seed 3, the
+    weights of the 1080p frame): 24 sampled pixels against the oracle and
+    every pixel against the FP32 path, both within the BF16 bar (a CPU
+    emulation of the BF16 weight rounding put the 1440p frame at 9.1e-3)."""
+    f = synth.make_frame(H, W, seed)
+    wb = synth.make_weights(seed=2)
+    dev = to_dev(stack_frames([f]))
+    out = _den(wk, wb, max_hw=(H, W)).denoise(*args(dev)).cpu().numpy()[0]
+    pix = sample_pixels(H, W, 24, seed=seed)
+    ref = oracle.denoise_pixels(f, wb, pix)
+    mx, mean = rel_err(np.stack([out[:, y, x] for x, y in pix]), ref)
+    full = wk.Denoiser(wb, precision="fp32", max_hw=(H, W)).denoise(*args(dev)).cpu().numpy()[0]
+    fmx, fmean = rel_err(out, full)
+    print(f"bf16 {W}x{H}: sampled vs oracle max {mx:.3e} mean {mean:.3e}; all px vs fp32 max {fmx:.3e} "
+          f"mean {fmean:.3e}")
+    assert np.isfinite(out).all() and mx < TOL_BF16 and fmx < TOL_BF16
+
+
 def test_bf16_batch_invariance(wk):
     frames = [synth.make_frame(48, 80, 60 + b) for b in range(3)]
     wb = synth.make_weights(seed=7)

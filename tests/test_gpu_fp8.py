@@ -74,3 +74,25 @@ def test_fp8_1080p_error(wk):
     print(f"fp8 1080p: sampled vs oracle max {mx:.3e} mean {mean:.3e}; all px vs fp32 max {fmx:.3e} mean {fmean:.3e}")
     # the FP32 path is within 2e-6 of the oracle (tests/test_gpu_fp32.py)
     assert np.isfinite(out).all() and mx < TOL_FP8 and fmx < TOL_FP8
+
+
+@pytest.mark.parametrize("H,W,seed", [(720, 1280, 1), (1440, 2560, 3)])
+def test_fp8_other_resolutions_error(wk, H, W, seed):
+    """The resolution sweep's other frames (720p seed 1, 1440p seed 3),
+    calibrated on a different frame of the same size (seed + 10): 24 sampled
+    pixels against the oracle and every pixel against the FP32 path."""
+    f = synth.make_frame(H, W, seed)
+    wb = synth.make_weights(seed=2)
+    dev = to_dev(stack_frames([f]))
+    cal = to_dev(stack_frames([synth.make_frame(H, W, seed + 10)]))
+    d = wk.Denoiser(wb, precision="fp8", max_hw=(H, W))
+    d.calibrate(*args(cal))
+    out = d.denoise(*args(dev)).cpu().numpy()[0]
+    pix = sample_pixels(H, W, 24, seed=seed)
+    ref = oracle.denoise_pixels(f, wb, pix)
+    mx, mean = rel_err(np.stack([out[:, y, x] for x, y in pix]), ref)
+    full = wk.Denoiser(wb, precision="fp32", max_hw=(H, W)).denoise(*args(dev)).cpu().numpy()[0]
+    fmx, fmean = rel_err(out, full)
+    print(f"fp8 {W}x{H}: sampled vs oracle max {mx:.3e} mean {mean:.3e}; all px vs fp32 max {fmx:.3e} "
+          f"mean {fmean:.3e}")
+    assert np.isfinite(out).all() and mx < TOL_FP8 and fmx < TOL_FP8
