@@ -464,6 +464,11 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     hi/lo pair (x = hi + lo, both BF16) and run the K loop over both
  *     halves against the same BF16 weights, which removes the activation
  *     rounding error at twice the MMA work (default); 0 = one BF16 value.
+ *   WSKPN_TUNE_TC_SPLIT_LAYERS (BF16 only, with TC_SPLIT = 1): bit l set =
+ *     the input of layer l is stored as a hi/lo pair, clear = as one BF16
+ *     value (half the MMA work of that layer, its input rounded to BF16);
+ *     default all bits set.  The training backward on the tensor cores
+ *     needs every bit set (otherwise it recomputes in FP32).
  *   WSKPN_TUNE_TRAIN_RECOMPUTE (BF16 only): how wskpn_backward recomputes
  *     the activations and forms the input gradients: 1 = activations with
  *     the context's own tensor-core convolutions, as the forward computed
@@ -495,6 +500,7 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
 #define WSKPN_TUNE_HOST_BANDS 5
 #define WSKPN_TUNE_HOST_FIRST_BAND 6
 #define WSKPN_TUNE_HOST_LAST_BAND 7
+#define WSKPN_TUNE_TC_SPLIT_LAYERS 8
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
 
 /* Reads and clears the context's device status word after synchronising

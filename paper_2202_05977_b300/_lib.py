@@ -16,6 +16,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EBUSY", "ETI
 FP32, BF16, FP8 = 0, 1, 2
 TUNE_TC_SPLIT = 2
 TUNE_TRAIN_RECOMPUTE = 3
+TUNE_TC_SPLIT_LAYERS = 8
 TUNE_FP8_SPLIT = 4
 TUNE_HOST_BANDS = 5
 TUNE_HOST_FIRST_BAND = 6

@@ -575,6 +575,10 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
         ctx->tc_split = value;
         return WSKPN_OK;
     }
+    if (key == WSKPN_TUNE_TC_SPLIT_LAYERS && value >= 0) {
+        ctx->tc_split_layers = (unsigned)value;
+        return WSKPN_OK;
+    }
     if (key == WSKPN_TUNE_TRAIN_RECOMPUTE && value >= 0 && value <= 2) {
         ctx->train_tc_recompute = value;
         return WSKPN_OK;

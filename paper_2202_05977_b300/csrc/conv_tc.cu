@@ -1069,6 +1069,15 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     return WSKPN_OK;
 }
 
+int tc_split_of(const wskpn_ctx* ctx, int l) {
+    return ctx->tc_split && ((ctx->tc_split_layers >> l) & 1u) ? 1 : 0;
+}
+bool tc_split_all(const wskpn_ctx* ctx) {
+    for (int l = 0; l < ctx->cfg.n_layers; ++l)
+        if (!tc_split_of(ctx, l)) return false;
+    return true;
+}
+
 // One layer of a context's ImportanceNet.
 static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st) {
     const wskpn_config& c = ctx->cfg;
@@ -1077,7 +1086,12 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     r.L = &ctx->layers[l];
     r.KS = c.conv_ks;
     r.fp8 = fp8;
-    r.split_in = r.split_out = fp8 ? ctx->fp8_split : ctx->tc_split;
+    if (fp8) {
+        r.split_in = r.split_out = ctx->fp8_split;
+    } else {
+        r.split_in = tc_split_of(ctx, l);
+        r.split_out = l + 1 < c.n_layers ? tc_split_of(ctx, l + 1) : 0;
+    }
     r.last = l == c.n_layers - 1;
     r.relu = !r.last;
     r.out_cp = r.last ? ctx->layers[l].cout_p : ctx->layers[l + 1].cin_p;  // stored channels per pixel
@@ -1227,7 +1241,7 @@ wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, 
     uint8_t* A = static_cast<uint8_t*>(ctx->d_tcA);
     uint8_t* Bf = static_cast<uint8_t*>(ctx->d_tcB);
     std::vector<void*> x0(B);
-    const int split = ctx->tc_split;
+    const int split = tc_split_of(ctx, 0);
     const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * (split ? 2 : 1) * HW;
     for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * x0_bytes;
     wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), split ? 2 : 1, st,
@@ -1269,7 +1283,7 @@ wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B,
     const size_t HW = (size_t)H * W;
     uint8_t* A = static_cast<uint8_t*>(ctx->d_tcA);
     uint8_t* Bf = static_cast<uint8_t*>(ctx->d_tcB);
-    const int split = ctx->tc_split;
+    const int split = tc_split_all(ctx) ? 1 : 0;
     std::vector<void*> x0(B);
     const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * (split ? 2 : 1) * HW;
     for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * x0_bytes;
@@ -1300,7 +1314,7 @@ wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B,
 wskpn_status tc_recompute_nhwc(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
                                const std::vector<void*>& xs, cudaStream_t st) {
     const wskpn_config& c = ctx->cfg;
-    if (c.prec != WSKPN_BF16 || !ctx->tc_split || B > WSKPN_MAX_BATCH) {
+    if (c.prec != WSKPN_BF16 || !tc_split_all(ctx) || B > WSKPN_MAX_BATCH) {
         ctx->err = "tc_recompute_nhwc: BF16 contexts with hi/lo activations only, at most 16 frames";
         return WSKPN_EUNSUPPORTED;
     }

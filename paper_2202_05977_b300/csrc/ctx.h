@@ -60,6 +60,7 @@ struct wskpn_ctx {
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
     bool fp8_calibrated = false;
     int tc_split = 1;  // BF16 activations as hi/lo pairs (WSKPN_TUNE_TC_SPLIT)
+    unsigned tc_split_layers = 0xFFFFFFFFu;  // of those, the layer inputs split (bit l; WSKPN_TUNE_TC_SPLIT_LAYERS)
     int fp8_split = 1;  // e4m3 activations and weights as hi/lo pairs (WSKPN_TUNE_FP8_SPLIT)
     int train_tc_recompute = 1;  // backward on the tensor cores: 1 recompute + input gradients, 2 recompute only (WSKPN_TUNE_TRAIN_RECOMPUTE)
     int host_bands = 0;         // bands of the host-buffer pipeline, 0 = automatic (WSKPN_TUNE_HOST_BANDS)
@@ -91,6 +92,10 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st);
 wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                        cudaStream_t st);
 wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string& err);
+// BF16: whether the input of layer l is stored as hi/lo pairs, and whether
+// every layer input is (the training recompute needs all of them split).
+int tc_split_of(const wskpn_ctx* ctx, int l);
+bool tc_split_all(const wskpn_ctx* ctx);
 wskpn_status tc_recompute_nhwc(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
                                const std::vector<void*>& xs, cudaStream_t st);
 wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,

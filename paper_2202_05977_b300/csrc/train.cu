@@ -529,7 +529,7 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
     //    (tensor cores, hi/lo activations, as the forward), else FP32.  With
     //    every gradient on the tensor cores they stay NHWC hi/lo; otherwise
     //    planar FP32 for the SIMT gradient kernels.
-    const bool on_tc = c.prec == WSKPN_BF16 && ctx->tc_split && ctx->train_tc_recompute && batch <= WSKPN_MAX_BATCH;
+    const bool on_tc = c.prec == WSKPN_BF16 && tc_split_all(ctx) && ctx->train_tc_recompute && batch <= WSKPN_MAX_BATCH;
     const bool tc_bwd = on_tc && ctx->train_tc_recompute == 1 && t->all_tc;
     auto xn = [&](int l) { return static_cast<void*>(static_cast<uint8_t*>(t->xnhwc) + t->x_off[l]); };
     auto act = [&](int l, int b) { return t->acts + t->act_off[l] + (size_t)b * c.widths[l] * HW; };
