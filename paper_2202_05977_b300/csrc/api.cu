@@ -402,14 +402,14 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
             wskpn_frame f{};
             const float** dst[4] = {&f.radiance, &f.albedo, &f.normal, &f.depth};
             float* p = base;
+            // one 2D copy per input buffer: its ch[q] plane bands (HW apart in the
+            // host buffer) land ePX apart in the band buffer
             for (int q = 0; q < 4; ++q) {
                 *dst[q] = p;
-                for (int c = 0; c < ch[q]; ++c) {
-                    WSKPN_CUDA_TRY(cudaMemcpyAsync(p, src[q] + c * HW + (size_t)e0 * w, ePX * sizeof(float),
-                                                   cudaMemcpyHostToDevice, ctx->up_stream),
-                                   ctx->err);
-                    p += ePX;
-                }
+                WSKPN_CUDA_TRY(cudaMemcpy2DAsync(p, ePX * sizeof(float), src[q] + (size_t)e0 * w, HW * sizeof(float),
+                                                 ePX * sizeof(float), ch[q], cudaMemcpyHostToDevice, ctx->up_stream),
+                               ctx->err);
+                p += (size_t)ch[q] * ePX;
             }
             float* dout = p;
             WSKPN_CUDA_TRY(cudaEventRecord(ev[slot], ctx->up_stream), ctx->err);
@@ -427,12 +427,11 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
             WSKPN_CUDA_TRY(cudaEventRecord(ev[2 + slot], cs), ctx->err);
             // download the central rows
             WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->down_stream, ev[2 + slot], 0), ctx->err);
-            for (int c = 0; c < 3; ++c)
-                WSKPN_CUDA_TRY(cudaMemcpyAsync(host_out + ((size_t)b * 3 + c) * HW + (size_t)y0 * w,
-                                               dout + c * ePX + (size_t)(y0 - e0) * w,
-                                               (size_t)(y1 - y0) * w * sizeof(float), cudaMemcpyDeviceToHost,
-                                               ctx->down_stream),
-                               ctx->err);
+            WSKPN_CUDA_TRY(cudaMemcpy2DAsync(host_out + (size_t)b * 3 * HW + (size_t)y0 * w, HW * sizeof(float),
+                                             dout + (size_t)(y0 - e0) * w, ePX * sizeof(float),
+                                             (size_t)(y1 - y0) * w * sizeof(float), 3, cudaMemcpyDeviceToHost,
+                                             ctx->down_stream),
+                           ctx->err);
             WSKPN_CUDA_TRY(cudaEventRecord(ev[4 + slot], ctx->down_stream), ctx->err);
         }
     }
