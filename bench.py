@@ -92,10 +92,10 @@ def peaks():
 
 def host_upload_bytes(h: int, w: int, n_layers: int = len(WIDTHS) - 1, ks: int = KS,
                       kmax: int = max(KSIZES)) -> int:
-    """Bytes wskpn_denoise_host uploads for one frame: frames of 480+ rows go
-    in bands of ceil(h / nb) rows (nb = min(8, h // 240)), each with a halo
+    """Bytes wskpn_denoise_host uploads for one frame: frames of 432+ rows go
+    in bands of ceil(h / nb) rows (nb = min(8, h // 216)), each with a halo
     of n_layers * ks // 2 + kmax // 2 rows, so the halo rows travel twice."""
-    nb = min(8, h // 240)
+    nb = min(8, h // 216)
     if nb < 2:
         return 40 * h * w
     halo = n_layers * (ks // 2) + kmax // 2

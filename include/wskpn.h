@@ -143,8 +143,8 @@ wskpn_status wskpn_denoise(wskpn_ctx* ctx, const wskpn_frame* frames, int batch,
 /* wskpn_denoise from HOST buffers, synchronous: copies each frame's inputs
  * (host float32 planar, pinned memory recommended) into context-owned
  * device staging buffers, denoises, copies the result to host_out
- * ([batch][3][h][w] float32) and waits before returning.  Frames of 480
- * rows or more are processed as horizontal bands of about 240 rows, each
+ * ([batch][3][h][w] float32) and waits before returning.  Frames of 432
+ * rows or more are processed as horizontal bands of about 216 rows, each
  * with the receptive-field halo (conv_ks / 2 rows per layer plus the largest
  * window's half) recomputed, on `stream`, while two context-owned copy
  * streams upload the next band and download the previous one; the result
@@ -487,7 +487,7 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     Eq. 3); 0 = one e4m3 value per operand.  Changing it re-packs the
  *     weights (synchronises the device).
  *   WSKPN_TUNE_HOST_BANDS: bands of the wskpn_denoise_host pipeline; 0 =
- *     automatic (one per ~240 rows, at most 8, none below 480 rows), 1 = no
+ *     automatic (one per ~216 rows, at most 8, none below 432 rows), 1 = no
  *     banding, n = n bands.
  *   WSKPN_TUNE_HOST_FIRST_BAND, WSKPN_TUNE_HOST_LAST_BAND: height of the
  *     pipeline's first / last band in % of the others (10 .. 100; defaults

@@ -450,10 +450,10 @@ wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, 
         ctx->err = "host_out is NULL";
         return WSKPN_EINVAL;
     }
-    // Frames of at least 480 rows go through the banded pipeline (one band
-    // per ~240 rows, at most 8): the recomputed halos cost less than the
+    // Frames of at least 432 rows go through the banded pipeline (one band
+    // per ~216 rows, at most 8): the recomputed halos cost less than the
     // copies they let overlap.  Smaller frames: one upload, denoise, download.
-    const int nb = ctx->host_bands > 0 ? std::min(ctx->host_bands, h) : std::min(8, h / 240);
+    const int nb = ctx->host_bands > 0 ? std::min(ctx->host_bands, h) : std::min(8, h / 216);
     if (nb >= 2) return denoise_host_banded(ctx, host_frames, batch, h, w, host_out, nb, (cudaStream_t)stream);
     if (!ctx->d_stage) {
         cudaError_t e = cudaMalloc((void**)&ctx->d_stage, ctx->ws_pixels * 13 * sizeof(float));

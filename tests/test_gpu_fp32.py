@@ -174,7 +174,7 @@ def test_denoise_host_matches_device_call(torch, wk):
 
 @pytest.mark.parametrize("prec,B,H,W", [("fp32", 2, 600, 200), ("bf16", 1, 1080, 256), ("fp32", 1, 517, 130)])
 def test_banded_host_call_matches_device_call(torch, wk, prec, B, H, W):
-    """Frames of 480+ rows go through the banded host pipeline (halo rows
+    """Frames of 432+ rows go through the banded host pipeline (halo rows
     recomputed per band, copies overlapped with compute); the kept rows equal
     the whole-frame device call up to the per-tile exponent shift of the
     reconstruction (FP32 rounding)."""
