@@ -66,7 +66,9 @@ def test_six_blocks_1080p_bf16_sampled(wk):
     assert mx < 1e-2
 
 
-def test_six_blocks_fp8_runs(wk):
+def test_six_blocks_fp8_matches_oracle(wk):
+    """FP8 form of the 6-block network: e4m3 hi/lo operands, every pixel
+    held to the 3e-2 per-pixel bar of the FP8 form."""
     f = synth.make_frame(64, 96, 73)
     wb = synth.make_weights(WIDTHS6, seed=73)
     dev = to_dev(stack_frames([f]))
@@ -76,4 +78,4 @@ def test_six_blocks_fp8_runs(wk):
     assert np.all(np.isfinite(out)) and d.device_status() == 0
     mx, mean = rel_err(out, oracle.denoise(f, wb, widths=WIDTHS6))
     print(f"6-block fp8 64x96: max rel {mx:.3e} mean {mean:.3e}")
-    assert mean < 3e-2
+    assert mx < 3e-2
