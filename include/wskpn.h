@@ -519,8 +519,10 @@ wskpn_status wskpn_device_status(wskpn_ctx* ctx, uint32_t* bits);
  * network output) lives in one static device array of 64 MiB that each GPU
  * loading this library holds until the process exits.  No cudaMalloc,
  * cudaFree or allocating library call is made.
- *   cfg      configuration as for wskpn_create; prec must be WSKPN_FP32
- *            (else EUNSUPPORTED); max_batch/max_h/max_w are ignored;
+ *   cfg      configuration as for wskpn_create, validated the same way
+ *            (max_batch/max_h/max_w must hold valid values although they
+ *            do not limit this call); prec must be WSKPN_FP32 (else
+ *            EUNSUPPORTED);
  *   weights  DEVICE float32 blob in the wskpn_create layout;
  *   frames   host array of `batch` wskpn_frame (device pointers);
  *   out      device float32 [batch][3][h][w].
@@ -529,8 +531,13 @@ wskpn_status wskpn_device_status(wskpn_ctx* ctx, uint32_t* bits);
  * batch x h x w; at the default widths about 134,000 pixels, e.g. one
  * 512 x 256 frame); larger requests return EINVAL with the size needed.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and it keeps the
+ * (cudaGetSymbolAddress) with that device current.  With lazy module
+ * loading (the CUDA default) that lookup is also when the driver loads the
+ * module and commits the 64 MiB on that device, so the first call can fail
+ * with ECUDA (out of memory) where memory is short: make it at start-up,
+ * before any stream capture.  The address is cached per device for the
+ * life of the process; cudaDeviceReset invalidates it and is not supported
+ * between calls.  All calls share the array and it keeps the
  * last call's contents: calls whose work overlaps on the GPU (different
  * streams or devices' threads racing on one device) corrupt each other, so
  * serialise them.  Asynchronous on `stream` like wskpn_denoise. */

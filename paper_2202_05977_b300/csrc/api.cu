@@ -310,7 +310,11 @@ static int band_halo(const wskpn_config& c) {
 // The network's workspaces (activations, logits) for a call of `px` pixels,
 // moved to the second half of the context's buffers while the object lives:
 // two band calls of at most ws_pixels / 2 pixels each can then be in flight
-// on two streams (kernels take the buffer addresses at launch).
+// on two streams (kernels take the buffer addresses at launch).  The
+// context's device status word and fallback counter are NOT shifted: both
+// band streams accumulate into the same two words, which are meant to be
+// read only after the call's final synchronisation (a timeout bit or a
+// fallback count then covers the whole frame, not one band).
 struct WorkspaceShift {
     wskpn_ctx* c;
     void *ta, *tb;
