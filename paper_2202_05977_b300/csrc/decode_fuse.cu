@@ -124,7 +124,7 @@ __device__ __forceinline__ void box_sums(const float* sE, float* sH, float* sV, 
 }
 
 // Exact per-window evaluation of Eq. 3-4 for one pixel (slow path).
-__device__ __noinline__ void window_exact(const float* __restrict__ z, const float* __restrict__ r,
+__device__ __forceinline__ void window_exact_inl(const float* __restrict__ z, const float* __restrict__ r,
                              const float* __restrict__ a, int H, int W, int k, float eps, int px,
                              int py, float R[3]) {
     const int h = k / 2;
@@ -147,6 +147,12 @@ __device__ __noinline__ void window_exact(const float* __restrict__ z, const flo
     R[0] = N0 / D;
     R[1] = N1 / D;
     R[2] = N2 / D;
+}
+
+__device__ __noinline__ void window_exact(const float* __restrict__ z, const float* __restrict__ r,
+                                          const float* __restrict__ a, int H, int W, int k, float eps, int px, int py,
+                                          float R[3]) {
+    window_exact_inl(z, r, a, H, W, k, eps, px, py, R);
 }
 
 // Every load of a thread is issued before any is used (one memory latency
@@ -240,336 +246,560 @@ __device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float*
 // With a NULL albedo the kernel takes r as the irradiance itself and writes
 // the fused filtered irradiance (no demodulation, no re-modulation): the
 // per-level filtering of the multi-resolution variant.
-// The forward kernel uses 64 x 32 output tiles (6-pixel halo, 512 threads,
-// one CTA per SM: the halo overhead of a tile is 1.6x its area for the
-// largest window instead of 2.1x with 64 x 16) and organises each size's
-// work for instruction economy:
-//  * the horizontal pass forms E and E*y on the fly from the E and y planes
-//    and handles the four planes as two packed pairs (D, N0) and (N1, N2)
-//    with paired FP32 adds;
-//  * a K-wide window sum is built from sums of 2, 4 and 8 neighbours taken
-//    once per row segment and combined by the binary digits of K (all
-//    terms positive, so no cancellation);
-//  * the vertical pass of one column produces D and N directly for the
-//    thread's own 4 pixels, which accumulate alpha_i R_i in registers;
-//  * alpha (Eq. 5) is computed once per pixel into shared memory.
-namespace dfw {
+//
+// Organisation (64 x 32 output tiles, 512 threads, two CTAs per SM):
+//  * set-up: the demodulated irradiance y of the tile's 44 x 80 footprint
+//    (rows -6..37, columns -8..71 around the tile, 0 outside the image) is
+//    formed once into shared memory as a y0 plane and a (y1, y2) plane;
+//    per output pixel, the maximum c of its fusion logits (the shift of
+//    Eq. 5's softmax) goes to shared memory too;
+//  * per window size K (two block barriers):
+//      - the importance map I_i of the footprint has been staged in shared
+//        memory by cp.async during the previous size's horizontal pass, and
+//        its maximum m_i (the exponent shift, over the whole staged block)
+//        reduced at the same time; the tile's fusion logits l_i are staged
+//        during the vertical pass;
+//      - vertical pass, one task per (footprint column, half tile, pair):
+//        the thread walks 16 + K - 1 rows, forms E = exp(I - m_i) and
+//        either (E, E y0) or (E y1, E y2), and keeps their K-row window
+//        sums as streaming binary-digit partial sums in registers;
+//      - horizontal pass, one task per (row, 8 pixels, pair): K-column
+//        window sums of the pair; the (E y1, E y2) thread takes D from its
+//        (E, E y0) partner lane (lane ^ 16) by a warp shuffle; each forms
+//        w = exp(l_i - c) / D_i and accumulates w N for its channels, and
+//        the (E, E y0) thread also sum_i exp(l_i - c);
+//  * out = (a + eps) acc / sum_i exp(l_i - c), with the tile's albedo staged
+//    by cp.async into the y planes during the last horizontal pass.
+// The exponent shift cancels in N/D for every window; a pixel whose D_i
+// falls below 1e-30 is recomputed exactly (window_exact) and counted.
+namespace dfv {
 constexpr int TW = 64;                  // tile width (output pixels)
 constexpr int TH = 32;                  // tile height
 constexpr int HALO = 6;                 // largest half window (k = 13)
-constexpr int RW = TW + 2 * HALO;       // 76: region pitch in floats (76 / 4 odd: row-strided 16-byte accesses are conflict-free)
-constexpr int RH = TH + 2 * HALO;       // 44
-constexpr int SEG = 8;                  // horizontal-pass outputs per item
-constexpr int NSEG = TW / SEG;          // 8
-constexpr int HP2 = TW + 2;             // pitch of the packed horizontal-sum rows in float2 (132 floats, 132 / 4 odd)
+constexpr int XOFF = 8;                 // staged columns start 8 left of the tile (16-byte aligned)
+constexpr int FW = TW + 2 * XOFF;       // 80 staged columns
+constexpr int FH = TH + 2 * HALO;       // 44 staged rows
+constexpr int NCH = FH * FW / 4;        // 880 four-column chunks
 constexpr int THREADS = 512;
-constexpr int RPT = TH * TW / THREADS;  // 4 output pixels per thread, one column
-static_assert(THREADS / TW * RPT == TH, "vertical-pass mapping");
-static_assert(RH * NSEG <= THREADS, "one horizontal item per thread");
-constexpr int MAXK = WSKPN_MAX_KERNELS;
-// shared memory in floats: y [3][RH][RW] | E [RH][RW] | hsum [2][RH][HP2] float2 | alpha [MAXK][TH][TW] |
-// acc [RPT * 3][THREADS]
-constexpr int OFF_Y = 0;
-constexpr int OFF_E = OFF_Y + 3 * RH * RW;
-constexpr int OFF_H = OFF_E + RH * RW;
-constexpr int OFF_A = OFF_H + 2 * RH * HP2 * 2;
-constexpr int OFF_ACC = OFF_A + MAXK * TH * TW;
-constexpr int SMEM_FLOATS = OFF_ACC + RPT * 3 * THREADS;
-constexpr size_t SMEM_BYTES = SMEM_FLOATS * sizeof(float);
-static_assert(OFF_E % 4 == 0 && OFF_H % 4 == 0 && OFF_A % 4 == 0, "16-byte aligned planes");
-}  // namespace dfw
+constexpr int NWARP = THREADS / 32;
+constexpr int RV = TH / 2;              // vertical-pass output rows per task
+constexpr int SEG = 8;                  // horizontal-pass output pixels per task
+constexpr int VP = TW + 2 * HALO + 1;   // 77: pitch of the window-sum planes in float2 (odd: conflict-free columns)
+constexpr int LP = TW + 4;              // 68: pitch of the per-pixel planes (16-byte aligned rows)
+constexpr int CPT = (NCH + THREADS - 1) / THREADS;  // chunks per thread (2)
+static_assert(TH == 32 && TW / SEG * 2 == NWARP, "horizontal pass: (row half, segment) per warp");
+static_assert(4 * (TW + 2 * HALO) <= THREADS, "vertical pass: one task per thread");
+static_assert(TH * TW / 4 == THREADS, "one fusion-logit chunk per thread");
+constexpr size_t OFF_Y12 = 0;                                     // float2 [FH][FW]: (y1, y2)
+constexpr size_t OFF_Y0 = OFF_Y12 + sizeof(float2) * FH * FW;    // float  [FH][FW]
+constexpr size_t OFF_Z = OFF_Y0 + sizeof(float) * FH * FW;       // float  [FH][FW]
+constexpr size_t OFF_V = OFF_Z + sizeof(float) * FH * FW;        // float2 [2][TH][VP]: (D, N0) | (N1, N2)
+constexpr size_t OFF_C = OFF_V + sizeof(float2) * 2 * TH * VP;   // float [TH][LP]: c log2(e)
+constexpr size_t OFF_L = OFF_C + sizeof(float) * TH * LP;        // float [TH][LP]: fusion logits l_i
+constexpr size_t OFF_R = OFF_L + sizeof(float) * TH * LP;        // int [2][NWARP]
+constexpr size_t SMEM_BYTES = OFF_R + sizeof(int) * 2 * NWARP;
+static_assert(OFF_V % 16 == 0 && OFF_C % 16 == 0 && OFF_L % 16 == 0, "16-byte aligned planes");
+static_assert(3 * TH * LP * sizeof(float) <= OFF_Y0 - OFF_Y12, "staged albedo fits the (y1, y2) plane");
+static_assert(2 * (SMEM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
+constexpr float LOG2E = 1.4426950408889634f;
+}  // namespace dfv
 
-// s[x] = sum_{d < K} w[x + d], x < NOUT, for two planes at once.  Sums of 2,
-// 4 and 8 consecutive inputs are formed once and the window is assembled
-// from the binary digits of K (K <= 15); values no output needs are never
-// computed (the arrays are fully unrolled).
-template <int K, int NOUT>
-__device__ __forceinline__ void box_sum2(const float2 (&w)[NOUT + K - 1], float2 (&s)[NOUT]) {
+// 2^x with the SFU's approximate exponential (flushes subnormal results to
+// 0).  exp(t) is formed as 2^(t log2 e); the caller folds the constant
+// shift into one FMA, so only the product's final rounding enters.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Order-preserving map between float and int (so integer max reductions
+// give the float maximum; -inf maps below every finite value).
+__device__ __forceinline__ int f2ord(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(__cvta_generic_to_global(gsrc))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(__cvta_generic_to_global(gsrc))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Window sums s[y] = sum_{d < K} w[y + d] of a float pair, y < NOUT,
+// streamed in input order: in(j) yields input j, out(y, s) takes output y
+// as soon as its last input has arrived.  Sums of 2, 4 and 8 consecutive
+// inputs are formed once; a window is assembled from the binary digits of
+// K (all terms of one sign: no cancellation).  Every array index is a
+// compile-time constant, so the arrays live in registers and entries no
+// output needs are never computed; at step j only the partial sums later
+// outputs still need are live (about 16 pairs for K = 13).
+template <int K, int NOUT, typename In, typename Out>
+__device__ __forceinline__ void box_stream(In in, Out out) {
     constexpr int N1 = NOUT + K - 1;
     constexpr int B8 = K & 8, B4 = K & 4, B2 = K & 2, B1 = K & 1;
     constexpr int O4 = B8, O2 = B8 + B4, O1 = B8 + B4 + B2;
     static_assert(K >= 1 && K <= 15, "window");
-    float2 p2[N1 > 1 ? N1 - 1 : 1], p4[N1 > 3 ? N1 - 3 : 1], p8[N1 > 7 ? N1 - 7 : 1];
+    float2 w[N1], p2[N1], p4[N1], p8[N1];
 #pragma unroll
-    for (int j = 0; j + 1 < N1; ++j) p2[j] = __fadd2_rn(w[j], w[j + 1]);
-#pragma unroll
-    for (int j = 0; j + 3 < N1; ++j) p4[j] = __fadd2_rn(p2[j], p2[j + 2]);
-#pragma unroll
-    for (int j = 0; j + 7 < N1; ++j) p8[j] = __fadd2_rn(p4[j], p4[j + 4]);
-#pragma unroll
-    for (int x = 0; x < NOUT; ++x) {
-        float2 t = make_float2(0.f, 0.f);
-        if constexpr (B8 != 0) t = p8[x];
-        if constexpr (B4 != 0) {
-            if constexpr (O4 != 0) t = __fadd2_rn(t, p4[x + O4]);
-            else t = p4[x];
+    for (int j = 0; j < N1; ++j) {
+        w[j] = in(j);
+        if (j >= 1) p2[j - 1] = __fadd2_rn(w[j - 1], w[j]);
+        if (j >= 3) p4[j - 3] = __fadd2_rn(p2[j - 3], p2[j - 1]);
+        if (j >= 7) p8[j - 7] = __fadd2_rn(p4[j - 7], p4[j - 3]);
+        const int y = j - (K - 1);
+        if (y >= 0) {
+            float2 t = make_float2(0.f, 0.f);
+            bool set = false;
+            if constexpr (B8 != 0) {
+                t = p8[y];
+                set = true;
+            }
+            if constexpr (B4 != 0) {
+                t = set ? __fadd2_rn(t, p4[y + O4]) : p4[y + O4];
+                set = true;
+            }
+            if constexpr (B2 != 0) {
+                t = set ? __fadd2_rn(t, p2[y + O2]) : p2[y + O2];
+                set = true;
+            }
+            if constexpr (B1 != 0) t = set ? __fadd2_rn(t, w[y + O1]) : w[y + O1];
+            out(y, t);
         }
-        if constexpr (B2 != 0) {
-            if constexpr (O2 != 0) t = __fadd2_rn(t, p2[x + O2]);
-            else t = p2[x];
-        }
-        if constexpr (B1 != 0) {
-            if constexpr (O1 != 0) t = __fadd2_rn(t, w[x + O1]);
-            else t = w[x];
-        }
-        s[x] = t;
     }
 }
 
-// Horizontal window sums of (E, E y0) and (E y1, E y2) for the NR footprint
-// rows of size K: one thread per (row, 8-pixel segment).  Inputs are read
-// as 16-byte vectors from the aligned column at or before the footprint's
-// first column; rows of consecutive threads are one region pitch apart.
-template <int K>
-__device__ __forceinline__ void fwd_hpass(const float* __restrict__ sE, const float* __restrict__ sY,
-                                          float2* __restrict__ sH, int tid) {
-    constexpr int h = K / 2, NR = dfw::TH + 2 * h;
-    constexpr int C0 = dfw::HALO - h;
-    constexpr int A0 = C0 & ~3;
-    constexpr int OFF = C0 - A0;
-    constexpr int NIN = dfw::SEG + K - 1;
-    constexpr int NV = (OFF + NIN + 3) / 4;
-    static_assert(A0 + (dfw::NSEG - 1) * dfw::SEG + 4 * NV <= dfw::RW, "aligned row reads stay in the region");
-    if (tid >= NR * dfw::NSEG) return;
-    const int row = tid % NR, seg = tid / NR;
-    const int base = (dfw::HALO - h + row) * dfw::RW + seg * dfw::SEG + A0;
-    float e[4 * NV], y[4 * NV];
+// Stage one logit plane's footprint block [FH][FW] into sZ (cp.async;
+// -inf outside the image) and return the maximum of what this thread
+// staged once its copies have landed (call finish_stage for that).
+template <bool VEC>
+__device__ __forceinline__ void stage_plane(float* __restrict__ sZ, const float* __restrict__ zi, int H, int W,
+                                            int tx0, int ty0, int tid) {
+    if constexpr (VEC) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const float4 t = *reinterpret_cast<const float4*>(sE + base + 4 * v);
-        e[4 * v] = t.x; e[4 * v + 1] = t.y; e[4 * v + 2] = t.z; e[4 * v + 3] = t.w;
+        for (int u = 0; u < dfv::CPT; ++u) {
+            const int c = tid + u * dfv::THREADS;
+            if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
+            const int row = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
+            const int gy = ty0 - dfv::HALO + row, gx = tx0 - dfv::XOFF + 4 * c4;
+            float* dst = sZ + row * dfv::FW + 4 * c4;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)  // W % 4 == 0: a chunk is wholly in or out
+                cp_async16(dst, zi + (size_t)gy * W + gx);
+            else
+                *reinterpret_cast<float4*>(dst) = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+        }
+    } else {
+        for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) {
+            const int row = e / dfv::FW, col = e % dfv::FW;
+            const int gy = ty0 - dfv::HALO + row, gx = tx0 - dfv::XOFF + col;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                cp_async4(sZ + e, zi + (size_t)gy * W + gx);
+            else
+                sZ[e] = -INFINITY;
+        }
     }
-    float2 w[NIN], s01[dfw::SEG], s23[dfw::SEG];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const float4 t = *reinterpret_cast<const float4*>(sY + base + 4 * v);
-        y[4 * v] = t.x; y[4 * v + 1] = t.y; y[4 * v + 2] = t.z; y[4 * v + 3] = t.w;
-    }
-#pragma unroll
-    for (int j = 0; j < NIN; ++j) w[j] = make_float2(e[OFF + j], e[OFF + j] * y[OFF + j]);
-    box_sum2<K, dfw::SEG>(w, s01);
-    float y2[4 * NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const float4 t = *reinterpret_cast<const float4*>(sY + dfw::RH * dfw::RW + base + 4 * v);
-        const float4 u = *reinterpret_cast<const float4*>(sY + 2 * dfw::RH * dfw::RW + base + 4 * v);
-        y[4 * v] = t.x; y[4 * v + 1] = t.y; y[4 * v + 2] = t.z; y[4 * v + 3] = t.w;
-        y2[4 * v] = u.x; y2[4 * v + 1] = u.y; y2[4 * v + 2] = u.z; y2[4 * v + 3] = u.w;
-    }
-#pragma unroll
-    for (int j = 0; j < NIN; ++j)
-        w[j] = __fmul2_rn(make_float2(e[OFF + j], e[OFF + j]), make_float2(y[OFF + j], y2[OFF + j]));
-    box_sum2<K, dfw::SEG>(w, s23);
-    float2* d01 = sH + row * dfw::HP2 + seg * dfw::SEG;
-    float2* d23 = d01 + dfw::RH * dfw::HP2;
-#pragma unroll
-    for (int x = 0; x < dfw::SEG; x += 2) {
-        *reinterpret_cast<float4*>(d01 + x) = make_float4(s01[x].x, s01[x].y, s01[x + 1].x, s01[x + 1].y);
-        *reinterpret_cast<float4*>(d23 + x) = make_float4(s23[x].x, s23[x].y, s23[x + 1].x, s23[x + 1].y);
-    }
+    cp_async_commit();
 }
 
-// One window size K: footprint logits and their maximum, E = exp(I_i - m)
-// (0 outside the image), horizontal then vertical window sums, and
-// acc += alpha_i R_i for the thread's own pixels (column x, rows
-// RPT * rg ...), kept in shared memory [RPT * 3][THREADS] so that each size
-// is a separate function with its own register allocation.  Three block
-// barriers; the next size's first barrier orders this size's reads of E and
-// the sums before they are overwritten.
-template <int K>
-__device__ __noinline__ void fwd_size(float* __restrict__ sE, float2* __restrict__ sH,
-                                         const float* __restrict__ sY, const float* __restrict__ sAl,
-                                         float* __restrict__ red, const float* __restrict__ zi,
-                                         const float* __restrict__ r, const float* __restrict__ a, int H, int W,
-                                         int tx0, int ty0, int tid, float eps, unsigned int* fallbacks,
-                                         float* __restrict__ sAcc) {
-    constexpr int h = K / 2, NR = dfw::TH + 2 * h, NC = dfw::TW + 2 * h, NT = NR * NC;
-    constexpr int PER = (NT + dfw::THREADS - 1) / dfw::THREADS;
-    float v[PER];
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int t = tid + j * dfw::THREADS;
-        const int gy = ty0 - h + t / NC, gx = tx0 - h + t % NC;
-        const bool in = t < NT && gy >= 0 && gy < H && gx >= 0 && gx < W;
-        v[j] = in ? __ldg(zi + (size_t)gy * W + gx) : -INFINITY;
-    }
+// Wait for this thread's copies, take the maximum of the elements it
+// staged and publish the warp's maximum in red[warp].
+template <bool VEC>
+__device__ __forceinline__ void finish_stage(const float* __restrict__ sZ, int* __restrict__ red, int tid) {
+    cp_async_wait_all();
     float m = -INFINITY;
+    if constexpr (VEC) {
 #pragma unroll
-    for (int j = 0; j < PER; ++j) m = fmaxf(m, v[j]);
-    m = warp_max(m);
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    m = red[0];
-#pragma unroll
-    for (int w = 1; w < dfw::THREADS / 32; ++w) m = fmaxf(m, red[w]);
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int t = tid + j * dfw::THREADS;
-        if (PER * dfw::THREADS > NT && t >= NT) continue;
-        sE[(dfw::HALO - h + t / NC) * dfw::RW + (dfw::HALO - h + t % NC)] = expf(v[j] - m);
+        for (int u = 0; u < dfv::CPT; ++u) {
+            const int c = tid + u * dfv::THREADS;
+            if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
+            const float4 v = reinterpret_cast<const float4*>(sZ)[c];
+            m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        }
+    } else {
+        for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) m = fmaxf(m, sZ[e]);
     }
-    __syncthreads();
-    fwd_hpass<K>(sE, sY, sH, tid);
-    __syncthreads();
+    const int w = __reduce_max_sync(0xffffffffu, f2ord(m));
+    if ((tid & 31) == 0) red[tid >> 5] = w;
+}
 
-    const int x = tid % dfw::TW, rg = tid / dfw::TW;
-    constexpr int NIN = dfw::RPT + K - 1;
-    float2 c[NIN], s01[dfw::RPT], s23[dfw::RPT];
+// The fusion logits of one row's 8 consecutive pixels (0 outside the image).
+template <bool VEC>
+__device__ __forceinline__ void load_fusion_logits(float (&l)[dfv::SEG], const float* __restrict__ zl, int H, int W,
+                                                   int gy, int gx0) {
+    if (VEC && gy < H && gx0 + dfv::SEG <= W) {
+        const float4* p = reinterpret_cast<const float4*>(zl + (size_t)gy * W + gx0);
+        const float4 u = __ldg(p), v = __ldg(p + 1);
+        l[0] = u.x, l[1] = u.y, l[2] = u.z, l[3] = u.w, l[4] = v.x, l[5] = v.y, l[6] = v.z, l[7] = v.w;
+    } else {
 #pragma unroll
-    for (int j = 0; j < NIN; ++j) c[j] = sH[(rg * dfw::RPT + j) * dfw::HP2 + x];
-    box_sum2<K, dfw::RPT>(c, s01);
-#pragma unroll
-    for (int j = 0; j < NIN; ++j) c[j] = sH[(dfw::RH + rg * dfw::RPT + j) * dfw::HP2 + x];
-    box_sum2<K, dfw::RPT>(c, s23);
-    const int gx = tx0 + x;
-#pragma unroll
-    for (int j = 0; j < dfw::RPT; ++j) {
-        const int ly = rg * dfw::RPT + j, gy = ty0 + ly;
-        if (gy >= H || gx >= W) continue;
-        float R[3];
-        const float D = s01[j].x;
-        if (D >= df::DMIN) {
-            const float invD = 1.f / D;
-            R[0] = s01[j].y * invD;
-            R[1] = s23[j].x * invD;
-            R[2] = s23[j].y * invD;
-        } else {
-            window_exact(zi, r, a, H, W, K, eps, gx, gy, R);
-            if (fallbacks) atomicAdd(fallbacks, 1u);
-        }
-        const float al = sAl[ly * dfw::TW + x];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float* p = sAcc + (j * 3 + ch) * dfw::THREADS + tid;
-            *p = fmaf(al, R[ch], *p);
-        }
+        for (int x = 0; x < dfv::SEG; ++x)
+            l[x] = (gy < H && gx0 + x < W) ? __ldg(zl + (size_t)gy * W + gx0 + x) : 0.f;
     }
 }
 
-template <bool DEMOD>
-__global__ void __launch_bounds__(dfw::THREADS, 1) decode_fuse_fwd_kernel(DecodeArgs args) {
+// Stage the tile's fusion logits l_i [TH][TW] into sL (one 16-byte chunk per
+// thread; rows or chunks outside the image are left as they are and never
+// used).
+template <bool VEC>
+__device__ __forceinline__ void stage_logits(float* __restrict__ sL, const float* __restrict__ zl, int H, int W,
+                                             int tx0, int ty0, int tid) {
+    const int row = tid >> 4, c4 = tid & 15;
+    const int gy = ty0 + row, gx = tx0 + 4 * c4;
+    float* dst = sL + row * dfv::LP + 4 * c4;
+    if constexpr (VEC) {
+        if (gy < H && gx < W) cp_async16(dst, zl + (size_t)gy * W + gx);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (gy < H && gx + e < W) cp_async4(dst + e, zl + (size_t)gy * W + gx + e);
+    }
+    cp_async_commit();
+}
+
+// Vertical pass of size K: task (pair, half, col) walks footprint column col
+// (image column tx0 - h + col) over rows 16 half - h .. 16 half + 15 + h of
+// the tile and writes the 16 K-row sums of (E, E y0) (pair 0) or
+// (E y1, E y2) (pair 1) to sV[pair][16 half + r][col].
+template <int K>
+__device__ __forceinline__ void fwd_vpass(const float* __restrict__ sZ, const float* __restrict__ sY0,
+                                          const float2* __restrict__ sY12, float2* __restrict__ sV, float ml2e,
+                                          int tid) {
+    constexpr int h = K / 2, NCOL = dfv::TW + 2 * h;
+    if (tid >= 4 * NCOL) return;
+    const int pair = tid >= 2 * NCOL ? 1 : 0;
+    const int t = tid - pair * 2 * NCOL;
+    const int half = t >= NCOL ? 1 : 0;
+    const int col = t - half * NCOL;
+    const int o = (dfv::HALO + dfv::RV * half - h) * dfv::FW + dfv::XOFF - h + col;
+    const float* zc = sZ + o;
+    float2* vc = sV + (pair * dfv::TH + dfv::RV * half) * dfv::VP + col;
+    if (pair == 0)
+        box_stream<K, dfv::RV>(
+            [&](int j) {
+                const float e = ex2_approx(fmaf(zc[j * dfv::FW], dfv::LOG2E, -ml2e));
+                return make_float2(e, e * sY0[o + j * dfv::FW]);
+            },
+            [&](int y, float2 s) { vc[y * dfv::VP] = s; });
+    else
+        box_stream<K, dfv::RV>(
+            [&](int j) {
+                const float e = ex2_approx(fmaf(zc[j * dfv::FW], dfv::LOG2E, -ml2e));
+                return __fmul2_rn(make_float2(e, e), sY12[o + j * dfv::FW]);
+            },
+            [&](int y, float2 s) { vc[y * dfv::VP] = s; });
+}
+
+// Per-thread accumulators of the horizontal-pass task: pair 0 keeps
+// acc0 = sum_i w_i N0 (u[0]) and sum_i exp(l_i - c) (u[1]); pair 1 keeps
+// sum_i w_i N1 (u[0]) and sum_i w_i N2 (u[1]).
+struct HState {
+    float u[2][dfv::SEG];
+};
+
+// Horizontal pass of size K for the thread's (row, 8-pixel segment, pair).
+// Returns the mask of pixels whose D underflowed (their exact evaluation
+// is deferred to the end of the kernel, out of the unrolled code).
+template <int K>
+__device__ __forceinline__ unsigned fwd_hpass(const float2* __restrict__ sV, const float* __restrict__ sC,
+                                              const float* __restrict__ sL, HState& st, int row, int seg, int pair) {
+    const float2* vr = sV + (pair * dfv::TH + row) * dfv::VP + seg * dfv::SEG;
+    const float* cr = sC + row * dfv::LP + seg * dfv::SEG;
+    const float* lr = sL + row * dfv::LP + seg * dfv::SEG;
+    unsigned exact = 0;
+    box_stream<K, dfv::SEG>([&](int j) { return vr[j]; },
+                            [&](int x, float2 s) {
+                                // D from the pair-0 lane (lane ^ 16); pair-0 lanes keep their own
+                                const float Dp = __shfl_xor_sync(0xffffffffu, s.x, 16);
+                                const float D = pair ? Dp : s.x;
+                                const float e = ex2_approx(fmaf(lr[x], dfv::LOG2E, -cr[x]));
+                                float w = 0.f;
+                                if (D >= df::DMIN) w = e * __fdividef(1.f, D);
+                                else exact |= 1u << x;
+                                st.u[0][x] = fmaf(w, pair ? s.x : s.y, st.u[0][x]);
+                                st.u[1][x] = pair ? fmaf(w, s.y, st.u[1][x]) : st.u[1][x] + e;
+                            });
+    return exact;
+}
+
+// The tile's albedo [3][TH][TW] into sA (cp.async, 16-byte chunks; chunks
+// outside the image are not copied and never used).
+__device__ __forceinline__ void stage_albedo(float* __restrict__ sA, const float* __restrict__ a, int H, int W,
+                                             int tx0, int ty0, int tid) {
+    const size_t HW = (size_t)H * W;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const int row = tid >> 4, c4 = tid & 15;
+        const int gy = ty0 + row, gx = tx0 + 4 * c4;
+        if (gy < H && gx < W) cp_async16(sA + (ch * dfv::TH + row) * dfv::LP + 4 * c4, a + ch * HW + (size_t)gy * W + gx);
+    }
+    cp_async_commit();
+}
+
+template <int K, bool VEC>
+__device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZ, const float* __restrict__ sY0,
+                                             const float2* __restrict__ sY12, float2* __restrict__ sV,
+                                             const float* __restrict__ sC, float* __restrict__ sL,
+                                             int* __restrict__ red, int* __restrict__ red_next, HState& st,
+                                             const float* __restrict__ znext, const float* __restrict__ zl,
+                                             const float* __restrict__ a_stage, int H, int W, int tx0, int ty0,
+                                             int tid) {
+    stage_logits<VEC>(sL, zl, H, W, tx0, ty0, tid);
+    int mo = red[0];
+#pragma unroll
+    for (int w = 1; w < dfv::NWARP; ++w) mo = max(mo, red[w]);
+    const float ml2e = ord2f(mo) * dfv::LOG2E;
+    fwd_vpass<K>(sZ, sY0, sY12, sV, ml2e, tid);
+    cp_async_wait_all();
+    __syncthreads();
+    if (znext) stage_plane<VEC>(const_cast<float*>(sZ), znext, H, W, tx0, ty0, tid);
+    // after the last vertical pass the y planes are free: the albedo of the
+    // re-modulation is staged there while the horizontal pass runs
+    if (a_stage) stage_albedo(reinterpret_cast<float*>(const_cast<float2*>(sY12)), a_stage, H, W, tx0, ty0, tid);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int pair = lane >> 4, row = (lane & 15) + 16 * (warp & 1), seg = warp >> 1;
+    const unsigned exact = fwd_hpass<K>(sV, sC, sL, st, row, seg, pair);
+    if (znext) finish_stage<VEC>(sZ, red_next, tid);
+    if (a_stage) cp_async_wait_all();
+    __syncthreads();
+    return exact;
+}
+
+template <bool DEMOD, bool VEC>
+__global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const __grid_constant__ DecodeArgs args) {
     extern __shared__ float4 dsm4[];
-    float* smem = reinterpret_cast<float*>(dsm4);
-    float* sY = smem + dfw::OFF_Y;
-    float* sE = smem + dfw::OFF_E;
-    float2* sH = reinterpret_cast<float2*>(smem + dfw::OFF_H);
-    float* sAl = smem + dfw::OFF_A;
-    float* sAcc = smem + dfw::OFF_ACC;
-    __shared__ float red[dfw::THREADS / 32];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(dsm4);
+    float2* sY12 = reinterpret_cast<float2*>(smem + dfv::OFF_Y12);
+    float* sY0 = reinterpret_cast<float*>(smem + dfv::OFF_Y0);
+    float* sZ = reinterpret_cast<float*>(smem + dfv::OFF_Z);
+    float2* sV = reinterpret_cast<float2*>(smem + dfv::OFF_V);
+    float* sC = reinterpret_cast<float*>(smem + dfv::OFF_C);
+    float* sL = reinterpret_cast<float*>(smem + dfv::OFF_L);
+    int* red = reinterpret_cast<int*>(smem + dfv::OFF_R);
 
     const int tid = threadIdx.x;
     const int b = blockIdx.z;
     const int H = args.H, W = args.W, M = args.M;
     const size_t HW = (size_t)H * W;
-    const int tx0 = blockIdx.x * dfw::TW, ty0 = blockIdx.y * dfw::TH;
+    const int tx0 = blockIdx.x * dfv::TW, ty0 = blockIdx.y * dfv::TH;
     const float* __restrict__ z = args.z.p[b];
     const float* __restrict__ r = args.r.p[b];
     const float* __restrict__ a = DEMOD ? args.a.p[b] : nullptr;
     const float eps = args.eps;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int pair = lane >> 4, row = (lane & 15) + 16 * (warp & 1), seg = warp >> 1;
+    const int gy = ty0 + row, gx0 = tx0 + seg * dfv::SEG;
 
-    // Demodulated irradiance y = r / (a + eps) on tile + halo (0 outside the image);
-    // every load of the phase is issued before any is used.
+    // the first importance map's footprint is in flight during the set-up
+    stage_plane<VEC>(sZ, z, H, W, tx0, ty0, tid);
+
+    // Shift of the fusion softmax per own pixel (Eq. 5): c = max_i l_i.  The
+    // two threads of a (row, segment) load alternate planes (all loads
+    // issued at once), combine their maxima by a shuffle, and the pair-0
+    // thread stores c log2(e).
     {
-        constexpr int NREG = dfw::RH * dfw::RW;
-        constexpr int PER = (NREG + dfw::THREADS - 1) / dfw::THREADS;
-        float rv[PER][3], av[PER][3];
+        constexpr int HALF = (WSKPN_MAX_KERNELS + 1) / 2;
+        float l[HALF][dfv::SEG];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int t = tid + j * dfw::THREADS;
-            const int gy = ty0 - dfw::HALO + t / dfw::RW, gx = tx0 - dfw::HALO + t % dfw::RW;
-            const bool in = t < NREG && gy >= 0 && gy < H && gx >= 0 && gx < W;
-            const size_t g = in ? (size_t)gy * W + gx : 0;
+        for (int q = 0; q < HALF; ++q)
+            if (2 * q + pair < M) load_fusion_logits<VEC>(l[q], z + (size_t)(M + 2 * q + pair) * HW, H, W, gy, gx0);
+        float c[dfv::SEG];
+#pragma unroll
+        for (int x = 0; x < dfv::SEG; ++x) {
+            c[x] = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < HALF; ++q)
+                if (2 * q + pair < M) c[x] = fmaxf(c[x], l[q][x]);
+            c[x] = fmaxf(c[x], __shfl_xor_sync(0xffffffffu, c[x], 16)) * dfv::LOG2E;
+        }
+        if (pair == 0) {
+            float4* pc = reinterpret_cast<float4*>(sC + row * dfv::LP + seg * dfv::SEG);
+            pc[0] = make_float4(c[0], c[1], c[2], c[3]);
+            pc[1] = make_float4(c[4], c[5], c[6], c[7]);
+        }
+    }
+
+    // Demodulated irradiance y = r / (a + eps) on the footprint (0 outside
+    // the image); all loads of a pass are issued before any is used.
+    if constexpr (VEC) {
+        float4 rv[dfv::CPT][3], av[dfv::CPT][3];
+#pragma unroll
+        for (int q = 0; q < dfv::CPT; ++q) {
+            const int c = tid + q * dfv::THREADS;
+            const int cr = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
+            const int yy = ty0 - dfv::HALO + cr, xx = tx0 - dfv::XOFF + 4 * c4;
+            const bool in = c < dfv::NCH && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t g = in ? (size_t)yy * W + xx : 0;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                rv[j][ch] = in ? __ldg(r + ch * HW + g) : 0.f;
-                av[j][ch] = in && DEMOD ? __ldg(a + ch * HW + g) : 1.f - eps;
+                rv[q][ch] = in ? __ldg(reinterpret_cast<const float4*>(r + ch * HW + g)) : make_float4(0, 0, 0, 0);
+                av[q][ch] = (DEMOD && in) ? __ldg(reinterpret_cast<const float4*>(a + ch * HW + g))
+                                          : make_float4(0, 0, 0, 0);
             }
         }
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int t = tid + j * dfw::THREADS;
-            if (PER * dfw::THREADS > NREG && t >= NREG) continue;
+        for (int q = 0; q < dfv::CPT; ++q) {
+            const int c = tid + q * dfv::THREADS;
+            if (c >= dfv::NCH) continue;
+            float y[3][4];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) sY[ch * NREG + t] = DEMOD ? rv[j][ch] / (av[j][ch] + eps) : rv[j][ch];
+            for (int ch = 0; ch < 3; ++ch) {
+                const float rr[4] = {rv[q][ch].x, rv[q][ch].y, rv[q][ch].z, rv[q][ch].w};
+                const float aa[4] = {av[q][ch].x, av[q][ch].y, av[q][ch].z, av[q][ch].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) y[ch][e] = DEMOD ? __fdividef(rr[e], aa[e] + eps) : rr[e];
+            }
+            reinterpret_cast<float4*>(sY0)[c] = make_float4(y[0][0], y[0][1], y[0][2], y[0][3]);
+            float4* p12 = reinterpret_cast<float4*>(sY12 + 4 * c);
+            p12[0] = make_float4(y[1][0], y[2][0], y[1][1], y[2][1]);
+            p12[1] = make_float4(y[1][2], y[2][2], y[1][3], y[2][3]);
+        }
+    } else {
+        for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) {
+            const int er = e / dfv::FW, ec = e % dfv::FW;
+            const int yy = ty0 - dfv::HALO + er, xx = tx0 - dfv::XOFF + ec;
+            float y[3] = {0.f, 0.f, 0.f};
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const size_t g = (size_t)yy * W + xx;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    y[ch] = DEMOD ? __fdividef(__ldg(r + ch * HW + g), __ldg(a + ch * HW + g) + eps)
+                                  : __ldg(r + ch * HW + g);
+            }
+            sY0[e] = y[0];
+            sY12[e] = make_float2(y[1], y[2]);
         }
     }
 
-    // Fusion weights alpha_i(p) = softmax_i of the M fusion logits (Eq. 5),
-    // once per own pixel, into shared memory [i][TH][TW].
-    const int x = tid % dfw::TW, rg = tid / dfw::TW;
-    const int gx = tx0 + x;
+    HState st;
 #pragma unroll
-    for (int j = 0; j < dfw::RPT; ++j) {
-        const int ly = rg * dfw::RPT + j, gy = ty0 + ly;
-        if (gy >= H || gx >= W) continue;
-        const size_t g = (size_t)gy * W + gx;
-        float l[dfw::MAXK];
-        float m = -INFINITY;
-#pragma unroll
-        for (int i = 0; i < dfw::MAXK; ++i) {
-            l[i] = i < M ? __ldg(z + (size_t)(M + i) * HW + g) : -INFINITY;
-            m = fmaxf(m, l[i]);
-        }
-        float sum = 0.f;
-#pragma unroll
-        for (int i = 0; i < dfw::MAXK; ++i) {
-            l[i] = i < M ? expf(l[i] - m) : 0.f;
-            sum += l[i];
-        }
-        const float inv = 1.f / sum;
-#pragma unroll
-        for (int i = 0; i < dfw::MAXK; ++i)
-            if (i < M) sAl[(i * dfw::TH + ly) * dfw::TW + x] = l[i] * inv;
-    }
-#pragma unroll
-    for (int j = 0; j < dfw::RPT * 3; ++j) sAcc[j * dfw::THREADS + tid] = 0.f;
+    for (int x = 0; x < dfv::SEG; ++x) st.u[0][x] = st.u[1][x] = 0.f;
+    finish_stage<VEC>(sZ, red, tid);
     __syncthreads();
 
+    unsigned long long exact = 0;  // bit 8 i + x: pixel x's D_i underflowed
     for (int i = 0; i < M; ++i) {
-        const float* __restrict__ zi = z + (size_t)i * HW;
-        const float* __restrict__ al = sAl + i * dfw::TH * dfw::TW;
-#define WSKPN_FWD_SIZE(K_) \
-    case K_: fwd_size<K_>(sE, sH, sY, al, red, zi, r, a, H, W, tx0, ty0, tid, eps, args.fallbacks, sAcc); break;
+        const float* znext = i + 1 < M ? z + (size_t)(i + 1) * HW : nullptr;
+        const float* zl = z + (size_t)(M + i) * HW;
+        int* rd = red + (i & 1) * dfv::NWARP;
+        int* rn = red + ((i + 1) & 1) * dfv::NWARP;
+        const float* astage = DEMOD && VEC && i + 1 == M ? a : nullptr;
+        unsigned ex = 0;
+#define WSKPN_FWD_SIZE(K_)                                                                                  \
+    case K_:                                                                                                \
+        ex = fwd_size<K_, VEC>(sZ, sY0, sY12, sV, sC, sL, rd, rn, st, znext, zl, astage, H, W, tx0, ty0, tid); \
+        break;
         switch (args.ks[i]) {
             WSKPN_FWD_SIZE(1) WSKPN_FWD_SIZE(3) WSKPN_FWD_SIZE(5) WSKPN_FWD_SIZE(7) WSKPN_FWD_SIZE(9)
-            WSKPN_FWD_SIZE(11)
-            default: fwd_size<13>(sE, sH, sY, al, red, zi, r, a, H, W, tx0, ty0, tid, eps, args.fallbacks, sAcc);
+            WSKPN_FWD_SIZE(11) WSKPN_FWD_SIZE(13)
         }
 #undef WSKPN_FWD_SIZE
+        exact |= (unsigned long long)ex << (8 * i);
     }
 
-    // Re-modulation and store.
+    // Pixels whose window sum underflowed for some size: exact per-window
+    // evaluation (rare), then the same accumulation as the fast path.
+    if (exact) {
+        const float* cr = sC + row * dfv::LP + seg * dfv::SEG;
+#pragma unroll 1
+        for (int i = 0; i < M; ++i) {
+#pragma unroll 1
+            for (int x = 0; x < dfv::SEG; ++x) {
+                if (!((exact >> (8 * i + x)) & 1ull) || gy >= H || gx0 + x >= W) continue;  // outside: never stored
+                float R[3];
+                window_exact_inl(z + (size_t)i * HW, r, a, H, W, args.ks[i], eps, gx0 + x, gy, R);
+                if (args.fallbacks && pair == 0) atomicAdd(args.fallbacks, 1u);
+                const float l = __ldg(z + (size_t)(M + i) * HW + (size_t)gy * W + gx0 + x);
+                const float e = ex2_approx(fmaf(l, dfv::LOG2E, -cr[x]));
+#pragma unroll
+                for (int q = 0; q < dfv::SEG; ++q)
+                    if (q == x) {
+                        st.u[0][q] = fmaf(e, pair ? R[1] : R[0], st.u[0][q]);
+                        if (pair) st.u[1][q] = fmaf(e, R[2], st.u[1][q]);
+                    }
+            }
+        }
+    }
+
+    // Re-modulation and store: out = (a + eps) acc / sum_i exp(l_i - c);
+    // the pair-0 thread writes channel 0, the pair-1 thread channels 1, 2.
     float* __restrict__ out = args.out.p[b];
+    float inv[dfv::SEG];
 #pragma unroll
-    for (int j = 0; j < dfw::RPT; ++j) {
-        const int gy = ty0 + rg * dfw::RPT + j;
-        if (gy >= H || gx >= W) continue;
-        const size_t g = (size_t)gy * W + gx;
+    for (int x = 0; x < dfv::SEG; ++x) {
+        const float s = __shfl_xor_sync(0xffffffffu, st.u[1][x], 16);  // pair 1 reads pair 0's sum
+        inv[x] = __fdividef(1.f, pair ? s : st.u[1][x]);
+    }
+    if (gy >= H) return;
+    const size_t g0 = (size_t)gy * W + gx0;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch)
-            out[ch * HW + g] = (DEMOD ? __ldg(a + ch * HW + g) + eps : 1.f) * sAcc[(j * 3 + ch) * dfw::THREADS + tid];
+    for (int q = 0; q < 2; ++q) {
+        if (pair == 0 && q == 1) break;
+        const int ch = pair + q;
+        float o[dfv::SEG];
+#pragma unroll
+        for (int x = 0; x < dfv::SEG; ++x) o[x] = st.u[q][x] * inv[x];
+        if (VEC && gx0 + dfv::SEG <= W) {
+            if constexpr (DEMOD) {
+                const float4* pa = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(sY12) +
+                                                                   (ch * dfv::TH + row) * dfv::LP + seg * dfv::SEG);
+                const float4 u = pa[0], v = pa[1];
+                const float m[dfv::SEG] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int x = 0; x < dfv::SEG; ++x) o[x] *= m[x] + eps;
+            }
+            float4* po = reinterpret_cast<float4*>(out + ch * HW + g0);
+            po[0] = make_float4(o[0], o[1], o[2], o[3]);
+            po[1] = make_float4(o[4], o[5], o[6], o[7]);
+        } else {
+#pragma unroll
+            for (int x = 0; x < dfv::SEG; ++x) {
+                if (gx0 + x >= W) break;
+                out[ch * HW + g0 + x] = (DEMOD ? __ldg(a + ch * HW + g0 + x) + eps : 1.f) * o[x];
+            }
+        }
     }
 }
 
-// Host launcher: z/r/a/out given per frame.
+template <bool DEMOD, bool VEC>
+static wskpn_status launch_fwd_variant(const DecodeArgs& args, int nb, cudaStream_t st, std::string& err) {
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel<DEMOD, VEC>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dfv::SMEM_BYTES),
+                   err);
+    dim3 grid(cdiv(args.W, dfv::TW), cdiv(args.H, dfv::TH), nb);
+    decode_fuse_fwd_kernel<DEMOD, VEC><<<grid, dfv::THREADS, dfv::SMEM_BYTES, st>>>(args);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    return WSKPN_OK;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Host launcher: z/r/a/out given per frame.  The vectorised variant (16-byte
+// loads, stores and copies) runs when W is a multiple of 4 and every plane
+// pointer is 16-byte aligned, so that each 4-pixel chunk of a row lies
+// wholly inside or outside the image.
 wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r,
                                     const float* const* a, float* const* out, int B, int H, int W,
                                     int M, const int* ks, float eps, unsigned int* fallbacks,
                                     cudaStream_t st, std::string& err) {
-    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)dfw::SMEM_BYTES),
-                   err);
-    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)dfw::SMEM_BYTES),
-                   err);
     for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
         const int nb = B - b0 < WSKPN_MAX_BATCH ? B - b0 : WSKPN_MAX_BATCH;
         DecodeArgs args{};
+        bool vec = W % 4 == 0;
         for (int j = 0; j < nb; ++j) {
             args.z.p[j] = z[b0 + j];
             args.r.p[j] = r[b0 + j];
             args.a.p[j] = a[b0 + j];
             args.out.p[j] = out[b0 + j];
+            vec = vec && aligned16(z[b0 + j]) && aligned16(r[b0 + j]) && aligned16(out[b0 + j]) &&
+                  (!a[b0 + j] || aligned16(a[b0 + j]));
         }
         args.H = H;
         args.W = W;
@@ -577,12 +807,13 @@ wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r
         for (int i = 0; i < M; ++i) args.ks[i] = ks[i];
         args.eps = eps;
         args.fallbacks = fallbacks;
-        dim3 grid(cdiv(W, dfw::TW), cdiv(H, dfw::TH), nb);
+        wskpn_status s;
         if (a[b0])  // every frame of a call either has an albedo or none
-            decode_fuse_fwd_kernel<true><<<grid, dfw::THREADS, dfw::SMEM_BYTES, st>>>(args);
+            s = vec ? launch_fwd_variant<true, true>(args, nb, st, err) : launch_fwd_variant<true, false>(args, nb, st, err);
         else
-            decode_fuse_fwd_kernel<false><<<grid, dfw::THREADS, dfw::SMEM_BYTES, st>>>(args);
-        WSKPN_CUDA_TRY(cudaGetLastError(), err);
+            s = vec ? launch_fwd_variant<false, true>(args, nb, st, err)
+                    : launch_fwd_variant<false, false>(args, nb, st, err);
+        if (s) return s;
     }
     return WSKPN_OK;
 }
