@@ -247,29 +247,28 @@ __device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float*
 // the fused filtered irradiance (no demodulation, no re-modulation): the
 // per-level filtering of the multi-resolution variant.
 //
-// Organisation (64 x 32 output tiles, 512 threads, two CTAs per SM):
+// Organisation (64 x 32 output tiles, 256 threads, two CTAs per SM):
 //  * set-up: the demodulated irradiance y of the tile's 44 x 80 footprint
 //    (rows -6..37, columns -8..71 around the tile, 0 outside the image) is
 //    formed once into shared memory as a y0 plane and a (y1, y2) plane;
-//    per output pixel, the maximum c of its fusion logits (the shift of
-//    Eq. 5's softmax) goes to shared memory too;
+//    each horizontal-pass thread keeps, for its 8 pixels, the maximum c of
+//    their fusion logits (the shift of Eq. 5's softmax) in registers;
 //  * per window size K (two block barriers):
-//      - the importance map I_i of the footprint has been staged in shared
-//        memory by cp.async during the previous size's horizontal pass, and
-//        its maximum m_i (the exponent shift, over the whole staged block)
-//        reduced at the same time; the tile's fusion logits l_i are staged
-//        during the vertical pass;
-//      - vertical pass, one task per (footprint column, half tile, pair):
-//        the thread walks 16 + K - 1 rows, forms E = exp(I - m_i) and
-//        either (E, E y0) or (E y1, E y2), and keeps their K-row window
+//      - the importance map I_i of the footprint was staged in shared
+//        memory by cp.async during the previous size's phase (two buffers),
+//        and its maximum m_i (the exponent shift, over the whole staged
+//        block) reduced at the end of that phase;
+//      - vertical pass, one task per (footprint column, half tile): the
+//        thread walks 16 + K - 1 rows, forms E = exp(I - m_i) once per
+//        element, (E y0, E) and (E y1, E y2), and keeps their K-row window
 //        sums as streaming binary-digit partial sums in registers;
-//      - horizontal pass, one task per (row, 8 pixels, pair): K-column
-//        window sums of the pair; the (E y1, E y2) thread takes D from its
-//        (E, E y0) partner lane (lane ^ 16) by a warp shuffle; each forms
-//        w = exp(l_i - c) / D_i and accumulates w N for its channels, and
-//        the (E, E y0) thread also sum_i exp(l_i - c);
-//  * out = (a + eps) acc / sum_i exp(l_i - c), with the tile's albedo staged
-//    by cp.async into the y planes during the last horizontal pass.
+//      - horizontal pass, one task per (row, 8 pixels): K-column sums of
+//        (E y0, E), giving w = exp(l_i - c) / D_i (the fusion logits l_i
+//        were loaded into registers one phase ahead), acc0 += w N0 and
+//        S += w D (= exp(l_i - c)); then of (E y1, E y2): acc1 += w N1,
+//        acc2 += w N2;
+//  * out = (a + eps) acc / S, with the tile's albedo staged by cp.async
+//    into the y planes during the last horizontal pass.
 // The exponent shift cancels in N/D for every window; a pixel whose D_i
 // falls below 1e-30 is recomputed exactly (window_exact) and counted.
 namespace dfv {
@@ -280,25 +279,22 @@ constexpr int XOFF = 8;                 // staged columns start 8 left of the ti
 constexpr int FW = TW + 2 * XOFF;       // 80 staged columns
 constexpr int FH = TH + 2 * HALO;       // 44 staged rows
 constexpr int NCH = FH * FW / 4;        // 880 four-column chunks
-constexpr int THREADS = 512;
+constexpr int THREADS = 256;
 constexpr int NWARP = THREADS / 32;
 constexpr int RV = TH / 2;              // vertical-pass output rows per task
 constexpr int SEG = 8;                  // horizontal-pass output pixels per task
-constexpr int VP = TW + 2 * HALO + 1;   // 77: pitch of the window-sum planes in float2 (odd: conflict-free columns)
+constexpr int VP = TW + 2 * HALO + 1;   // 77: pitch of the window-sum planes in float2 (odd: conflict-free)
 constexpr int LP = TW + 4;              // 68: pitch of the per-pixel planes (16-byte aligned rows)
-constexpr int CPT = (NCH + THREADS - 1) / THREADS;  // chunks per thread (2)
-static_assert(TH == 32 && TW / SEG * 2 == NWARP, "horizontal pass: (row half, segment) per warp");
-static_assert(4 * (TW + 2 * HALO) <= THREADS, "vertical pass: one task per thread");
-static_assert(TH * TW / 4 == THREADS, "one fusion-logit chunk per thread");
+constexpr int CPT = (NCH + THREADS - 1) / THREADS;  // chunks per thread (4)
+static_assert(TH == 32 && TW / SEG == NWARP, "horizontal pass: lane = row, warp = segment");
+static_assert(2 * (TW + 2 * HALO) < THREADS, "vertical pass: one task per thread, some threads idle");
 constexpr size_t OFF_Y12 = 0;                                     // float2 [FH][FW]: (y1, y2)
 constexpr size_t OFF_Y0 = OFF_Y12 + sizeof(float2) * FH * FW;    // float  [FH][FW]
-constexpr size_t OFF_Z = OFF_Y0 + sizeof(float) * FH * FW;       // float  [FH][FW]
-constexpr size_t OFF_V = OFF_Z + sizeof(float) * FH * FW;        // float2 [2][TH][VP]: (D, N0) | (N1, N2)
-constexpr size_t OFF_C = OFF_V + sizeof(float2) * 2 * TH * VP;   // float [TH][LP]: c log2(e)
-constexpr size_t OFF_L = OFF_C + sizeof(float) * TH * LP;        // float [TH][LP]: fusion logits l_i
-constexpr size_t OFF_R = OFF_L + sizeof(float) * TH * LP;        // int [2][NWARP]
-constexpr size_t SMEM_BYTES = OFF_R + sizeof(int) * 2 * NWARP;
-static_assert(OFF_V % 16 == 0 && OFF_C % 16 == 0 && OFF_L % 16 == 0, "16-byte aligned planes");
+constexpr size_t OFF_Z = OFF_Y0 + sizeof(float) * FH * FW;       // float  [2][FH][FW]: I_i, I_{i+1}
+constexpr size_t OFF_V = OFF_Z + sizeof(float) * 2 * FH * FW;    // float2 [2][TH][VP]: (N0, D) | (N1, N2)
+constexpr size_t OFF_R = OFF_V + sizeof(float2) * 2 * TH * VP;   // int [2]: shifts of sizes i, i + 1
+constexpr size_t SMEM_BYTES = OFF_R + sizeof(int) * 4;
+static_assert(OFF_V % 16 == 0 && OFF_Z % 16 == 0, "16-byte aligned planes");
 static_assert(3 * TH * LP * sizeof(float) <= OFF_Y0 - OFF_Y12, "staged albedo fits the (y1, y2) plane");
 static_assert(2 * (SMEM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
 constexpr float LOG2E = 1.4426950408889634f;
@@ -334,44 +330,51 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Window sums s[y] = sum_{d < K} w[y + d] of a float pair, y < NOUT,
-// streamed in input order: in(j) yields input j, out(y, s) takes output y
-// as soon as its last input has arrived.  Sums of 2, 4 and 8 consecutive
-// inputs are formed once; a window is assembled from the binary digits of
-// K (all terms of one sign: no cancellation).  Every array index is a
-// compile-time constant, so the arrays live in registers and entries no
-// output needs are never computed; at step j only the partial sums later
-// outputs still need are live (about 16 pairs for K = 13).
-template <int K, int NOUT, typename In, typename Out>
+// Window sums s[y] = sum_{d < K} w[y + d] of NP float pairs, y < NOUT,
+// streamed in input order: in(j, w) yields input j of every pair,
+// out(y, s) takes output y as soon as its last input has arrived.  Sums of
+// 2, 4 and 8 consecutive inputs are formed once; a window is assembled
+// from the binary digits of K (all terms of one sign: no cancellation).
+// Every array index is a compile-time constant, so the arrays live in
+// registers and entries no output needs are never computed; at step j only
+// the partial sums later outputs still need are live (about 16 pairs per
+// plane pair for K = 13).
+template <int K, int NOUT, int NP, typename In, typename Out>
 __device__ __forceinline__ void box_stream(In in, Out out) {
     constexpr int N1 = NOUT + K - 1;
     constexpr int B8 = K & 8, B4 = K & 4, B2 = K & 2, B1 = K & 1;
     constexpr int O4 = B8, O2 = B8 + B4, O1 = B8 + B4 + B2;
     static_assert(K >= 1 && K <= 15, "window");
-    float2 w[N1], p2[N1], p4[N1], p8[N1];
+    float2 w[N1][NP], p2[N1][NP], p4[N1][NP], p8[N1][NP];
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
-        w[j] = in(j);
-        if (j >= 1) p2[j - 1] = __fadd2_rn(w[j - 1], w[j]);
-        if (j >= 3) p4[j - 3] = __fadd2_rn(p2[j - 3], p2[j - 1]);
-        if (j >= 7) p8[j - 7] = __fadd2_rn(p4[j - 7], p4[j - 3]);
+        in(j, w[j]);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            if (j >= 1) p2[j - 1][q] = __fadd2_rn(w[j - 1][q], w[j][q]);
+            if (j >= 3) p4[j - 3][q] = __fadd2_rn(p2[j - 3][q], p2[j - 1][q]);
+            if (j >= 7) p8[j - 7][q] = __fadd2_rn(p4[j - 7][q], p4[j - 3][q]);
+        }
         const int y = j - (K - 1);
         if (y >= 0) {
-            float2 t = make_float2(0.f, 0.f);
-            bool set = false;
-            if constexpr (B8 != 0) {
-                t = p8[y];
-                set = true;
+            float2 t[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                bool set = false;
+                if constexpr (B8 != 0) {
+                    t[q] = p8[y][q];
+                    set = true;
+                }
+                if constexpr (B4 != 0) {
+                    t[q] = set ? __fadd2_rn(t[q], p4[y + O4][q]) : p4[y + O4][q];
+                    set = true;
+                }
+                if constexpr (B2 != 0) {
+                    t[q] = set ? __fadd2_rn(t[q], p2[y + O2][q]) : p2[y + O2][q];
+                    set = true;
+                }
+                if constexpr (B1 != 0) t[q] = set ? __fadd2_rn(t[q], w[y + O1][q]) : w[y + O1][q];
             }
-            if constexpr (B4 != 0) {
-                t = set ? __fadd2_rn(t, p4[y + O4]) : p4[y + O4];
-                set = true;
-            }
-            if constexpr (B2 != 0) {
-                t = set ? __fadd2_rn(t, p2[y + O2]) : p2[y + O2];
-                set = true;
-            }
-            if constexpr (B1 != 0) t = set ? __fadd2_rn(t, w[y + O1]) : w[y + O1];
             out(y, t);
         }
     }
@@ -410,7 +413,7 @@ __device__ __forceinline__ void stage_plane(float* __restrict__ sZ, const float*
 }
 
 // Wait for this thread's copies, take the maximum of the elements it
-// staged and publish the warp's maximum in red[warp].
+// staged and fold the warp's maximum into *red (order-preserving int).
 template <bool VEC>
 __device__ __forceinline__ void finish_stage(const float* __restrict__ sZ, int* __restrict__ red, int tid) {
     cp_async_wait_all();
@@ -427,7 +430,7 @@ __device__ __forceinline__ void finish_stage(const float* __restrict__ sZ, int* 
         for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) m = fmaxf(m, sZ[e]);
     }
     const int w = __reduce_max_sync(0xffffffffu, f2ord(m));
-    if ((tid & 31) == 0) red[tid >> 5] = w;
+    if ((tid & 31) == 0) atomicMax(red, w);
 }
 
 // The fusion logits of one row's 8 consecutive pixels (0 outside the image).
@@ -444,129 +447,121 @@ __device__ __forceinline__ void load_fusion_logits(float (&l)[dfv::SEG], const f
             l[x] = (gy < H && gx0 + x < W) ? __ldg(zl + (size_t)gy * W + gx0 + x) : 0.f;
     }
 }
-
-// Stage the tile's fusion logits l_i [TH][TW] into sL (one 16-byte chunk per
-// thread; rows or chunks outside the image are left as they are and never
-// used).
-template <bool VEC>
-__device__ __forceinline__ void stage_logits(float* __restrict__ sL, const float* __restrict__ zl, int H, int W,
-                                             int tx0, int ty0, int tid) {
-    const int row = tid >> 4, c4 = tid & 15;
-    const int gy = ty0 + row, gx = tx0 + 4 * c4;
-    float* dst = sL + row * dfv::LP + 4 * c4;
-    if constexpr (VEC) {
-        if (gy < H && gx < W) cp_async16(dst, zl + (size_t)gy * W + gx);
-    } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            if (gy < H && gx + e < W) cp_async4(dst + e, zl + (size_t)gy * W + gx + e);
-    }
-    cp_async_commit();
-}
-
-// Vertical pass of size K: task (pair, half, col) walks footprint column col
-// (image column tx0 - h + col) over rows 16 half - h .. 16 half + 15 + h of
-// the tile and writes the 16 K-row sums of (E, E y0) (pair 0) or
-// (E y1, E y2) (pair 1) to sV[pair][16 half + r][col].
+// Vertical pass of size K: task (half, col), t < 2 (64 + K - 1), walks
+// footprint column col (image column tx0 - h + col) over rows
+// 16 half - h .. 16 half + 15 + h of the tile, forming E once per element,
+// and writes the 16 K-row sums of (E y0, E) to sVA and of (E y1, E y2) to
+// sVB at [16 half + r][col].
 template <int K>
 __device__ __forceinline__ void fwd_vpass(const float* __restrict__ sZ, const float* __restrict__ sY0,
-                                          const float2* __restrict__ sY12, float2* __restrict__ sV, float ml2e,
-                                          int tid) {
+                                          const float2* __restrict__ sY12, float2* __restrict__ sVA,
+                                          float2* __restrict__ sVB, float ml2e, int t) {
     constexpr int h = K / 2, NCOL = dfv::TW + 2 * h;
-    if (tid >= 4 * NCOL) return;
-    const int pair = tid >= 2 * NCOL ? 1 : 0;
-    const int t = tid - pair * 2 * NCOL;
     const int half = t >= NCOL ? 1 : 0;
     const int col = t - half * NCOL;
     const int o = (dfv::HALO + dfv::RV * half - h) * dfv::FW + dfv::XOFF - h + col;
-    const float* zc = sZ + o;
-    float2* vc = sV + (pair * dfv::TH + dfv::RV * half) * dfv::VP + col;
-    if (pair == 0)
-        box_stream<K, dfv::RV>(
-            [&](int j) {
-                const float e = ex2_approx(fmaf(zc[j * dfv::FW], dfv::LOG2E, -ml2e));
-                return make_float2(e, e * sY0[o + j * dfv::FW]);
-            },
-            [&](int y, float2 s) { vc[y * dfv::VP] = s; });
-    else
-        box_stream<K, dfv::RV>(
-            [&](int j) {
-                const float e = ex2_approx(fmaf(zc[j * dfv::FW], dfv::LOG2E, -ml2e));
-                return __fmul2_rn(make_float2(e, e), sY12[o + j * dfv::FW]);
-            },
-            [&](int y, float2 s) { vc[y * dfv::VP] = s; });
+    const int v = dfv::RV * half * dfv::VP + col;
+    box_stream<K, dfv::RV, 2>(
+        [&](int j, float2(&w)[2]) {
+            const float e = ex2_approx(fmaf(sZ[o + j * dfv::FW], dfv::LOG2E, -ml2e));
+            w[0] = make_float2(e * sY0[o + j * dfv::FW], e);
+            w[1] = __fmul2_rn(make_float2(e, e), sY12[o + j * dfv::FW]);
+        },
+        [&](int y, const float2(&s)[2]) {
+            sVA[v + y * dfv::VP] = s[0];
+            sVB[v + y * dfv::VP] = s[1];
+        });
 }
 
-// Per-thread accumulators of the horizontal-pass task: pair 0 keeps
-// acc0 = sum_i w_i N0 (u[0]) and sum_i exp(l_i - c) (u[1]); pair 1 keeps
-// sum_i w_i N1 (u[0]) and sum_i w_i N2 (u[1]).
+// Per-thread state of the horizontal-pass task (row, 8 pixels) across the
+// sizes i: acc_c = sum_i w_i N_ic and S = sum_i w_i D_i = sum_i exp(l_i - c)
+// with w_i = exp(l_i - c) / D_i; cl = c log2(e) (c = max_i l_i) and l, the
+// fusion logits of the size being processed (loaded one phase ahead).
 struct HState {
-    float u[2][dfv::SEG];
+    float acc[dfv::SEG][3];
+    float S[dfv::SEG];
+    float cl[dfv::SEG];
+    float l[dfv::SEG];
 };
 
-// Horizontal pass of size K for the thread's (row, 8-pixel segment, pair).
+// Horizontal pass of size K for the thread's row and 8-pixel segment.
 // Returns the mask of pixels whose D underflowed (their exact evaluation
 // is deferred to the end of the kernel, out of the unrolled code).
 template <int K>
-__device__ __forceinline__ unsigned fwd_hpass(const float2* __restrict__ sV, const float* __restrict__ sC,
-                                              const float* __restrict__ sL, HState& st, int row, int seg, int pair) {
-    const float2* vr = sV + (pair * dfv::TH + row) * dfv::VP + seg * dfv::SEG;
-    const float* cr = sC + row * dfv::LP + seg * dfv::SEG;
-    const float* lr = sL + row * dfv::LP + seg * dfv::SEG;
+__device__ __forceinline__ unsigned fwd_hpass(const float2* __restrict__ sVA, const float2* __restrict__ sVB,
+                                              HState& st, int row, int seg) {
+    const int v = row * dfv::VP + seg * dfv::SEG;
+    float w[dfv::SEG];
+    bool bad = false;
+    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVA[v + j]; },
+                               [&](int x, const float2(&t)[1]) {
+                                   const float D = t[0].y;
+                                   const bool ok = D >= df::DMIN;
+                                   bad |= !ok;
+                                   const float e = ex2_approx(fmaf(st.l[x], dfv::LOG2E, -st.cl[x]));
+                                   w[x] = ok ? e * __fdividef(1.f, D) : 0.f;
+                                   st.acc[x][0] = fmaf(w[x], t[0].x, st.acc[x][0]);
+                                   st.S[x] = fmaf(w[x], D, st.S[x]);
+                               });
+    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVB[v + j]; },
+                               [&](int x, const float2(&t)[1]) {
+                                   st.acc[x][1] = fmaf(w[x], t[0].x, st.acc[x][1]);
+                                   st.acc[x][2] = fmaf(w[x], t[0].y, st.acc[x][2]);
+                               });
     unsigned exact = 0;
-    box_stream<K, dfv::SEG>([&](int j) { return vr[j]; },
-                            [&](int x, float2 s) {
-                                // D from the pair-0 lane (lane ^ 16); pair-0 lanes keep their own
-                                const float Dp = __shfl_xor_sync(0xffffffffu, s.x, 16);
-                                const float D = pair ? Dp : s.x;
-                                const float e = ex2_approx(fmaf(lr[x], dfv::LOG2E, -cr[x]));
-                                float w = 0.f;
-                                if (D >= df::DMIN) w = e * __fdividef(1.f, D);
-                                else exact |= 1u << x;
-                                st.u[0][x] = fmaf(w, pair ? s.x : s.y, st.u[0][x]);
-                                st.u[1][x] = pair ? fmaf(w, s.y, st.u[1][x]) : st.u[1][x] + e;
-                            });
+    if (bad) {  // rare: find the pixels again
+#pragma unroll 1
+        for (int x = 0; x < dfv::SEG; ++x) {
+            float D = 0.f;
+#pragma unroll 1
+            for (int j = 0; j < K; ++j) D += sVA[v + x + j].y;
+            if (!(D >= df::DMIN)) exact |= 1u << x;
+        }
+    }
     return exact;
 }
 
-// The tile's albedo [3][TH][TW] into sA (cp.async, 16-byte chunks; chunks
-// outside the image are not copied and never used).
+// The tile's albedo [3][TH][TW] into sA [3][TH][LP] (cp.async, 16-byte
+// chunks; chunks outside the image are not copied and never used).
 __device__ __forceinline__ void stage_albedo(float* __restrict__ sA, const float* __restrict__ a, int H, int W,
                                              int tx0, int ty0, int tid) {
     const size_t HW = (size_t)H * W;
+    constexpr int NC = 3 * dfv::TH * (dfv::TW / 4);
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        const int row = tid >> 4, c4 = tid & 15;
+    for (int c = tid; c < NC; c += dfv::THREADS) {
+        const int ch = c / (dfv::TH * dfv::TW / 4), rc = c % (dfv::TH * dfv::TW / 4);
+        const int row = rc / (dfv::TW / 4), c4 = rc % (dfv::TW / 4);
         const int gy = ty0 + row, gx = tx0 + 4 * c4;
         if (gy < H && gx < W) cp_async16(sA + (ch * dfv::TH + row) * dfv::LP + 4 * c4, a + ch * HW + (size_t)gy * W + gx);
     }
     cp_async_commit();
 }
 
+// One window size K.  Phase layout: I_{i+1} is staged into the other z
+// buffer at the start (it has the whole phase to land); the vertical pass
+// reads I_i; after the barrier the horizontal pass consumes this size's
+// fusion logits, the next size's are loaded, and the next shift is reduced.
 template <int K, bool VEC>
-__device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZ, const float* __restrict__ sY0,
-                                             const float2* __restrict__ sY12, float2* __restrict__ sV,
-                                             const float* __restrict__ sC, float* __restrict__ sL,
+__device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZcur, float* __restrict__ sZnext,
+                                             const float* __restrict__ sY0, const float2* __restrict__ sY12,
+                                             float2* __restrict__ sVA, float2* __restrict__ sVB,
                                              int* __restrict__ red, int* __restrict__ red_next, HState& st,
-                                             const float* __restrict__ znext, const float* __restrict__ zl,
+                                             const float* __restrict__ znext, const float* __restrict__ zlnext,
                                              const float* __restrict__ a_stage, int H, int W, int tx0, int ty0,
                                              int tid) {
-    stage_logits<VEC>(sL, zl, H, W, tx0, ty0, tid);
-    int mo = red[0];
-#pragma unroll
-    for (int w = 1; w < dfv::NWARP; ++w) mo = max(mo, red[w]);
-    const float ml2e = ord2f(mo) * dfv::LOG2E;
-    fwd_vpass<K>(sZ, sY0, sY12, sV, ml2e, tid);
-    cp_async_wait_all();
+    constexpr int NCOL = dfv::TW + 2 * (K / 2);
+    const float ml2e = ord2f(*red) * dfv::LOG2E;
+    if (tid == 0) *red_next = INT_MIN;  // its last reader finished before the previous barrier
+    if (znext) stage_plane<VEC>(sZnext, znext, H, W, tx0, ty0, tid);
+    if (tid < 2 * NCOL) fwd_vpass<K>(sZcur, sY0, sY12, sVA, sVB, ml2e, tid);
     __syncthreads();
-    if (znext) stage_plane<VEC>(const_cast<float*>(sZ), znext, H, W, tx0, ty0, tid);
     // after the last vertical pass the y planes are free: the albedo of the
     // re-modulation is staged there while the horizontal pass runs
     if (a_stage) stage_albedo(reinterpret_cast<float*>(const_cast<float2*>(sY12)), a_stage, H, W, tx0, ty0, tid);
-    const int lane = tid & 31, warp = tid >> 5;
-    const int pair = lane >> 4, row = (lane & 15) + 16 * (warp & 1), seg = warp >> 1;
-    const unsigned exact = fwd_hpass<K>(sV, sC, sL, st, row, seg, pair);
-    if (znext) finish_stage<VEC>(sZ, red_next, tid);
+    const int row = tid & 31, seg = tid >> 5;
+    const unsigned exact = fwd_hpass<K>(sVA, sVB, st, row, seg);
+    if (zlnext) load_fusion_logits<VEC>(st.l, zlnext, H, W, ty0 + row, tx0 + seg * dfv::SEG);
+    if (znext) finish_stage<VEC>(sZnext, red_next, tid);
     if (a_stage) cp_async_wait_all();
     __syncthreads();
     return exact;
@@ -579,9 +574,8 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     float2* sY12 = reinterpret_cast<float2*>(smem + dfv::OFF_Y12);
     float* sY0 = reinterpret_cast<float*>(smem + dfv::OFF_Y0);
     float* sZ = reinterpret_cast<float*>(smem + dfv::OFF_Z);
-    float2* sV = reinterpret_cast<float2*>(smem + dfv::OFF_V);
-    float* sC = reinterpret_cast<float*>(smem + dfv::OFF_C);
-    float* sL = reinterpret_cast<float*>(smem + dfv::OFF_L);
+    float2* sVA = reinterpret_cast<float2*>(smem + dfv::OFF_V);
+    float2* sVB = sVA + dfv::TH * dfv::VP;
     int* red = reinterpret_cast<int*>(smem + dfv::OFF_R);
 
     const int tid = threadIdx.x;
@@ -593,73 +587,71 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     const float* __restrict__ r = args.r.p[b];
     const float* __restrict__ a = DEMOD ? args.a.p[b] : nullptr;
     const float eps = args.eps;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int pair = lane >> 4, row = (lane & 15) + 16 * (warp & 1), seg = warp >> 1;
+    const int row = tid & 31, seg = tid >> 5;
     const int gy = ty0 + row, gx0 = tx0 + seg * dfv::SEG;
 
     // the first importance map's footprint is in flight during the set-up
+    if (tid == 0) red[0] = INT_MIN;
     stage_plane<VEC>(sZ, z, H, W, tx0, ty0, tid);
+    __syncthreads();  // red[0] initialised before any thread folds its maximum in
 
-    // Shift of the fusion softmax per own pixel (Eq. 5): c = max_i l_i.  The
-    // two threads of a (row, segment) load alternate planes (all loads
-    // issued at once), combine their maxima by a shuffle, and the pair-0
-    // thread stores c log2(e).
+    // Shift of the fusion softmax per own pixel (Eq. 5): c = max_i l_i (all
+    // loads issued at once); the first size's logits stay in st.l.
+    HState st;
     {
-        constexpr int HALF = (WSKPN_MAX_KERNELS + 1) / 2;
-        float l[HALF][dfv::SEG];
+        float l[WSKPN_MAX_KERNELS][dfv::SEG];
 #pragma unroll
-        for (int q = 0; q < HALF; ++q)
-            if (2 * q + pair < M) load_fusion_logits<VEC>(l[q], z + (size_t)(M + 2 * q + pair) * HW, H, W, gy, gx0);
-        float c[dfv::SEG];
+        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i)
+            if (i < M) load_fusion_logits<VEC>(l[i], z + (size_t)(M + i) * HW, H, W, gy, gx0);
 #pragma unroll
         for (int x = 0; x < dfv::SEG; ++x) {
-            c[x] = -INFINITY;
+            float c = l[0][x];
 #pragma unroll
-            for (int q = 0; q < HALF; ++q)
-                if (2 * q + pair < M) c[x] = fmaxf(c[x], l[q][x]);
-            c[x] = fmaxf(c[x], __shfl_xor_sync(0xffffffffu, c[x], 16)) * dfv::LOG2E;
-        }
-        if (pair == 0) {
-            float4* pc = reinterpret_cast<float4*>(sC + row * dfv::LP + seg * dfv::SEG);
-            pc[0] = make_float4(c[0], c[1], c[2], c[3]);
-            pc[1] = make_float4(c[4], c[5], c[6], c[7]);
+            for (int i = 1; i < WSKPN_MAX_KERNELS; ++i)
+                if (i < M) c = fmaxf(c, l[i][x]);
+            st.cl[x] = c * dfv::LOG2E;
+            st.l[x] = l[0][x];
+            st.acc[x][0] = st.acc[x][1] = st.acc[x][2] = st.S[x] = 0.f;
         }
     }
 
     // Demodulated irradiance y = r / (a + eps) on the footprint (0 outside
-    // the image); all loads of a pass are issued before any is used.
+    // the image); the loads of two chunks are issued before any is used.
     if constexpr (VEC) {
-        float4 rv[dfv::CPT][3], av[dfv::CPT][3];
 #pragma unroll
-        for (int q = 0; q < dfv::CPT; ++q) {
-            const int c = tid + q * dfv::THREADS;
-            const int cr = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
-            const int yy = ty0 - dfv::HALO + cr, xx = tx0 - dfv::XOFF + 4 * c4;
-            const bool in = c < dfv::NCH && yy >= 0 && yy < H && xx >= 0 && xx < W;
-            const size_t g = in ? (size_t)yy * W + xx : 0;
+        for (int u0 = 0; u0 < dfv::CPT; u0 += 2) {
+            float4 rv[2][3], av[2][3];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                rv[q][ch] = in ? __ldg(reinterpret_cast<const float4*>(r + ch * HW + g)) : make_float4(0, 0, 0, 0);
-                av[q][ch] = (DEMOD && in) ? __ldg(reinterpret_cast<const float4*>(a + ch * HW + g))
-                                          : make_float4(0, 0, 0, 0);
+            for (int q = 0; q < 2; ++q) {
+                const int c = tid + (u0 + q) * dfv::THREADS;
+                const int cr = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
+                const int yy = ty0 - dfv::HALO + cr, xx = tx0 - dfv::XOFF + 4 * c4;
+                const bool in = c < dfv::NCH && yy >= 0 && yy < H && xx >= 0 && xx < W;
+                const size_t g = in ? (size_t)yy * W + xx : 0;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    rv[q][ch] = in ? __ldg(reinterpret_cast<const float4*>(r + ch * HW + g)) : make_float4(0, 0, 0, 0);
+                    av[q][ch] = (DEMOD && in) ? __ldg(reinterpret_cast<const float4*>(a + ch * HW + g))
+                                              : make_float4(0, 0, 0, 0);
+                }
             }
-        }
 #pragma unroll
-        for (int q = 0; q < dfv::CPT; ++q) {
-            const int c = tid + q * dfv::THREADS;
-            if (c >= dfv::NCH) continue;
-            float y[3][4];
+            for (int q = 0; q < 2; ++q) {
+                const int c = tid + (u0 + q) * dfv::THREADS;
+                if (c >= dfv::NCH) continue;
+                float y[3][4];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const float rr[4] = {rv[q][ch].x, rv[q][ch].y, rv[q][ch].z, rv[q][ch].w};
-                const float aa[4] = {av[q][ch].x, av[q][ch].y, av[q][ch].z, av[q][ch].w};
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float rr[4] = {rv[q][ch].x, rv[q][ch].y, rv[q][ch].z, rv[q][ch].w};
+                    const float aa[4] = {av[q][ch].x, av[q][ch].y, av[q][ch].z, av[q][ch].w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) y[ch][e] = DEMOD ? __fdividef(rr[e], aa[e] + eps) : rr[e];
+                    for (int e = 0; e < 4; ++e) y[ch][e] = DEMOD ? __fdividef(rr[e], aa[e] + eps) : rr[e];
+                }
+                reinterpret_cast<float4*>(sY0)[c] = make_float4(y[0][0], y[0][1], y[0][2], y[0][3]);
+                float4* p12 = reinterpret_cast<float4*>(sY12 + 4 * c);
+                p12[0] = make_float4(y[1][0], y[2][0], y[1][1], y[2][1]);
+                p12[1] = make_float4(y[1][2], y[2][2], y[1][3], y[2][3]);
             }
-            reinterpret_cast<float4*>(sY0)[c] = make_float4(y[0][0], y[0][1], y[0][2], y[0][3]);
-            float4* p12 = reinterpret_cast<float4*>(sY12 + 4 * c);
-            p12[0] = make_float4(y[1][0], y[2][0], y[1][1], y[2][1]);
-            p12[1] = make_float4(y[1][2], y[2][2], y[1][3], y[2][3]);
         }
     } else {
         for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) {
@@ -678,23 +670,24 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
         }
     }
 
-    HState st;
-#pragma unroll
-    for (int x = 0; x < dfv::SEG; ++x) st.u[0][x] = st.u[1][x] = 0.f;
     finish_stage<VEC>(sZ, red, tid);
     __syncthreads();
 
     unsigned long long exact = 0;  // bit 8 i + x: pixel x's D_i underflowed
     for (int i = 0; i < M; ++i) {
-        const float* znext = i + 1 < M ? z + (size_t)(i + 1) * HW : nullptr;
-        const float* zl = z + (size_t)(M + i) * HW;
-        int* rd = red + (i & 1) * dfv::NWARP;
-        int* rn = red + ((i + 1) & 1) * dfv::NWARP;
+        const bool more = i + 1 < M;
+        const float* znext = more ? z + (size_t)(i + 1) * HW : nullptr;
+        const float* zlnext = more ? z + (size_t)(M + i + 1) * HW : nullptr;
+        float* zc = sZ + (i & 1) * dfv::FH * dfv::FW;
+        float* zn = sZ + ((i + 1) & 1) * dfv::FH * dfv::FW;
+        int* rd = red + (i & 1);
+        int* rn = red + ((i + 1) & 1);
         const float* astage = DEMOD && VEC && i + 1 == M ? a : nullptr;
         unsigned ex = 0;
-#define WSKPN_FWD_SIZE(K_)                                                                                  \
-    case K_:                                                                                                \
-        ex = fwd_size<K_, VEC>(sZ, sY0, sY12, sV, sC, sL, rd, rn, st, znext, zl, astage, H, W, tx0, ty0, tid); \
+#define WSKPN_FWD_SIZE(K_)                                                                                      \
+    case K_:                                                                                                    \
+        ex = fwd_size<K_, VEC>(zc, zn, sY0, sY12, sVA, sVB, rd, rn, st, znext, zlnext, astage, H, W, tx0, ty0, \
+                               tid);                                                                            \
         break;
         switch (args.ks[i]) {
             WSKPN_FWD_SIZE(1) WSKPN_FWD_SIZE(3) WSKPN_FWD_SIZE(5) WSKPN_FWD_SIZE(7) WSKPN_FWD_SIZE(9)
@@ -705,9 +698,8 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     }
 
     // Pixels whose window sum underflowed for some size: exact per-window
-    // evaluation (rare), then the same accumulation as the fast path.
+    // evaluation (rare); that size contributed nothing on the fast path.
     if (exact) {
-        const float* cr = sC + row * dfv::LP + seg * dfv::SEG;
 #pragma unroll 1
         for (int i = 0; i < M; ++i) {
 #pragma unroll 1
@@ -715,37 +707,33 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
                 if (!((exact >> (8 * i + x)) & 1ull) || gy >= H || gx0 + x >= W) continue;  // outside: never stored
                 float R[3];
                 window_exact_inl(z + (size_t)i * HW, r, a, H, W, args.ks[i], eps, gx0 + x, gy, R);
-                if (args.fallbacks && pair == 0) atomicAdd(args.fallbacks, 1u);
+                if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
                 const float l = __ldg(z + (size_t)(M + i) * HW + (size_t)gy * W + gx0 + x);
-                const float e = ex2_approx(fmaf(l, dfv::LOG2E, -cr[x]));
 #pragma unroll
                 for (int q = 0; q < dfv::SEG; ++q)
                     if (q == x) {
-                        st.u[0][q] = fmaf(e, pair ? R[1] : R[0], st.u[0][q]);
-                        if (pair) st.u[1][q] = fmaf(e, R[2], st.u[1][q]);
+                        const float e = ex2_approx(fmaf(l, dfv::LOG2E, -st.cl[q]));
+                        st.acc[q][0] = fmaf(e, R[0], st.acc[q][0]);
+                        st.acc[q][1] = fmaf(e, R[1], st.acc[q][1]);
+                        st.acc[q][2] = fmaf(e, R[2], st.acc[q][2]);
+                        st.S[q] += e;
                     }
             }
         }
     }
 
-    // Re-modulation and store: out = (a + eps) acc / sum_i exp(l_i - c);
-    // the pair-0 thread writes channel 0, the pair-1 thread channels 1, 2.
+    // Re-modulation and store: out = (a + eps) acc / S.
     float* __restrict__ out = args.out.p[b];
+    if (gy >= H) return;
     float inv[dfv::SEG];
 #pragma unroll
-    for (int x = 0; x < dfv::SEG; ++x) {
-        const float s = __shfl_xor_sync(0xffffffffu, st.u[1][x], 16);  // pair 1 reads pair 0's sum
-        inv[x] = __fdividef(1.f, pair ? s : st.u[1][x]);
-    }
-    if (gy >= H) return;
+    for (int x = 0; x < dfv::SEG; ++x) inv[x] = __fdividef(1.f, st.S[x]);
     const size_t g0 = (size_t)gy * W + gx0;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        if (pair == 0 && q == 1) break;
-        const int ch = pair + q;
+    for (int ch = 0; ch < 3; ++ch) {
         float o[dfv::SEG];
 #pragma unroll
-        for (int x = 0; x < dfv::SEG; ++x) o[x] = st.u[q][x] * inv[x];
+        for (int x = 0; x < dfv::SEG; ++x) o[x] = st.acc[x][ch] * inv[x];
         if (VEC && gx0 + dfv::SEG <= W) {
             if constexpr (DEMOD) {
                 const float4* pa = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(sY12) +
