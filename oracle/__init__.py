@@ -19,6 +19,10 @@ What it computes (paper sections / equations):
   * ``reconstruct_bwd`` / ``conv2d_bwd`` / ``train_grads``: the chain rule of
                         the above for one training step (Eq. 1), with the L1
                         loss or SMAPE (Eq. 6).
+  * ``round_bf16`` / ``bf16_weights``: the weight rounding of the BF16
+                        convolutions (round to nearest even), so that the
+                        BF16 training form can be compared with the exact
+                        gradient of the network it actually computes.
   * ``temporal.accumulate`` Sec. 4.3 temporal accumulation before denoising
                         (reprojection, geometry consistency, blend); numpy.
   * ``multires``        the multi-resolution variant: U-Net logits at 3
@@ -216,6 +220,34 @@ def split_weights(blob, widths=DEFAULT_WIDTHS, ks: int = 5):
         out.append((blob[off:off + nw].reshape(cout, cin, ks, ks), blob[off + nw:off + nw + cout]))
         off += nw + cout
     assert off == blob.size, (off, blob.size)
+    return out
+
+
+def round_bf16(x):
+    """Round float32 values to bfloat16 (8-bit significand), round to nearest
+    with ties to even, returned as float64: the BF16 tensor-core form keeps
+    its convolution weights this way (reading A12).  Written from the
+    definition: keep the top 16 bits of the IEEE binary32 pattern and add
+    one unit in the kept last place when the dropped 16 bits exceed half a
+    unit, or equal half a unit and the kept last bit is odd.  Finite inputs
+    only (the weights are finite)."""
+    bits = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    kept, dropped = bits >> 16, bits & 0xFFFF
+    up = (dropped > 0x8000) | ((dropped == 0x8000) & ((kept & 1) == 1))
+    kept = kept + up.astype(np.uint64)
+    return (kept << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_weights(blob, widths=DEFAULT_WIDTHS, ks: int = 5):
+    """The flat weight blob as the BF16 convolutions use it: every
+    convolution weight rounded by ``round_bf16``, the biases unchanged
+    (they are added in FP32 in the convolution epilogue)."""
+    out = _d(blob).copy()
+    off = 0
+    for l in range(len(widths) - 1):
+        nw = widths[l + 1] * widths[l] * ks * ks
+        out[off:off + nw] = round_bf16(np.asarray(blob, np.float32)[off:off + nw])
+        off += nw + widths[l + 1]
     return out
 
 

@@ -12,6 +12,7 @@ from tests._util import KSIZES, args, stack_frames, to_dev
 pytestmark = pytest.mark.gpu
 
 TOL_GRAD = 2e-4
+TOL_BF16_TRAIN = 2e-2  # measured 2.7e-3 .. 1.03e-2 per layer on the case below
 
 
 @pytest.fixture(scope="module")
@@ -105,11 +106,16 @@ def test_training_backward_matches_oracle(torch, wk, prec):
 
 
 def test_training_backward_bf16_tensor_core_recompute(torch, wk):
-    """BF16 convolutions with recomputed activations (the default): the
-    activations come from the BF16-weight network, so a few ReLU masks
-    differ from the FP64 network's; the gradient keeps its direction
-    (cosine > 0.99 per layer) and stays within 15 % in L2 (measured 6-10 %
-    for the first three layers, 0.4-0.7 % for the last)."""
+    """The default BF16 training form (convolutions on the tensor cores,
+    activations recomputed) against the oracle gradient of the network it
+    computes: the same weights rounded to bfloat16 (oracle.bf16_weights,
+    biases unchanged).  Per layer, every gradient element is within
+    TOL_BF16_TRAIN of that layer's largest oracle gradient; the remaining
+    error is the weight-gradient GEMMs' BF16 operands (one rounding of the
+    activation and of the pre-activation gradient per product, 2^-9
+    relative each) and ReLU masks flipped by the activations' hi/lo
+    rounding (measured per layer, 10-32 / 32-48 / 48-64 / 64-12: 2.7e-3,
+    4.1e-3, 8.6e-3, 1.03e-2 of the layer maximum; 0.26-0.55 % in L2)."""
     B, H, W = 2, 64, 96
     frames = [synth.make_frame(H, W, 310 + b) for b in range(B)]
     wb = synth.make_weights(seed=10)
@@ -118,20 +124,21 @@ def test_training_backward_bf16_tensor_core_recompute(torch, wk):
     out, z = d.forward_train(*args(dev))
     G = np.random.default_rng(10).standard_normal((B, 3, H, W)).astype(np.float32)
     dw, _ = d.backward(*args(dev), z, torch.from_numpy(G).cuda())
+    wr = oracle.bf16_weights(wb)
     ref = np.zeros(wb.size)
     for b in range(B):
-        o, acts = oracle.forward_train(frames[b], wb)
-        gb, _ = oracle.backward_train(frames[b], wb, acts, G[b])
+        o, acts = oracle.forward_train(frames[b], wr)
+        gb, _ = oracle.backward_train(frames[b], wr, acts, G[b])
         ref += gb
     dw = dw.cpu().numpy().astype(np.float64)
     off = 0
     for (ws, bs) in synth.weight_shapes():
         n = int(np.prod(ws)) + bs[0]
         a, r = dw[off:off + n], ref[off:off + n]
+        mx = np.abs(a - r).max() / np.abs(r).max()
         rel = np.linalg.norm(a - r) / np.linalg.norm(r)
-        cos = a @ r / np.linalg.norm(a) / np.linalg.norm(r)
-        print(f"bf16 tc recompute {ws}: L2 rel {rel:.3e} cos {cos:.6f}")
-        assert rel < 0.15 and cos > 0.99, ws
+        print(f"bf16 tc recompute {ws}: max rel (of layer max) {mx:.3e}, L2 rel {rel:.3e}")
+        assert mx < TOL_BF16_TRAIN, (ws, mx)
         off += n
     assert d.device_status() == 0
 

@@ -283,6 +283,50 @@ def test_training_gradient_matches_finite_differences():
         np.testing.assert_allclose(grad[idx], _fd(fun, wb, idx), rtol=5e-5, atol=1e-7)
 
 
+def test_round_bf16_definition():
+    """Hand values of round-to-nearest-even at 8 significand bits, and the
+    library conversion (torch's float32 -> bfloat16) on random values."""
+    u = 2.0 ** -7  # one unit in the last place of bfloat16 at [1, 2)
+    cases = [(1.0, 1.0), (1.0 + u / 2, 1.0),                 # tie, kept last bit even: down
+             (1.0 + 3 * u / 2, 1.0 + 2 * u),                   # tie, kept last bit odd: up
+             (1.0 + u / 2 + 2.0 ** -20, 1.0 + u),              # above the tie: up
+             (1.0 + u / 2 - 2.0 ** -20, 1.0),                  # below the tie: down
+             (-(1.0 + 3 * u / 2), -(1.0 + 2 * u)),            # sign symmetric
+             (2.0 - u / 4, 2.0), (0.0, 0.0), (3.0e-3, 0.0030059814453125)]
+    for x, want in cases:
+        assert oracle.round_bf16(np.float32(x)) == want, (x, oracle.round_bf16(np.float32(x)), want)
+    x = _rng(31).standard_normal(10000).astype(np.float32) * 0.3
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(oracle.round_bf16(x), ref)
+    wb = synth.make_weights(seed=31)
+    r = oracle.bf16_weights(wb)
+    for (ws, bs), (wr, br), (w0, b0) in zip(synth.weight_shapes(), oracle.split_weights(r), oracle.split_weights(wb)):
+        np.testing.assert_array_equal(br, b0)  # biases stay FP32
+        np.testing.assert_array_equal(wr, oracle.round_bf16(w0.astype(np.float32)))
+
+
+def test_training_gradient_matches_fd_at_training_crop_size():
+    """Config-5 size pin: a 32 x 32 crop through the default network
+    (widths 10-32-48-64-12, 5 x 5 convs, sizes 3..13); central differences
+    on weights sampled from every layer (kernel entries and biases) against
+    the oracle gradient of a random-cotangent objective."""
+    g = _rng(32)
+    f = synth.make_frame(32, 32, 32)
+    wb = synth.make_weights(seed=32).astype(np.float64)
+    G = g.standard_normal((3, 32, 32))
+    out, acts = oracle.forward_train(f, wb)
+    grad, _ = oracle.backward_train(f, wb, acts, G)
+    fun = lambda ww: float((oracle.forward_train(f, ww)[0] * G).sum())
+    idx, off = [], 0
+    for (ws, bs) in synth.weight_shapes():
+        nw = int(np.prod(ws))
+        idx += [off + int(i) for i in g.choice(nw, 3, replace=False)] + [off + nw + int(g.integers(bs[0]))]
+        off += nw + bs[0]
+    scale = np.abs(grad).max()
+    for i in idx:
+        np.testing.assert_allclose(grad[i], _fd(fun, wb, i, h=1e-5), rtol=1e-4, atol=1e-7 * scale)
+
+
 def test_losses_and_gradients():
     g = _rng(24)
     out = g.lognormal(0, 1, (2, 3, 4, 5))
