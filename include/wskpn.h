@@ -478,7 +478,8 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     gradients in FP32 SIMT with the FP32 weights; 0 = everything in FP32
  *     with the FP32 weights (the ReLU masks are then those of the FP32
  *     network, which brings the gradient closer to the FP32/FP64 one).
- *     Weight gradients are FP32 SIMT in every mode.
+ *     Weight gradients: tensor-core GEMMs over the pixels in mode 1, FP32
+ *     SIMT in modes 0 and 2.
  *   WSKPN_TUNE_FP8_SPLIT (FP8 only): 1 = every e4m3 activation and weight
  *     is a hi/lo pair in one scale (x / s = hi + lo, lo = e4m3 of the
  *     residual) and each convolution sums A_hi W_hi + A_lo W_hi + A_hi W_lo,
@@ -493,6 +494,17 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     pipeline's first / last band in % of the others (10 .. 100; defaults
  *     100 and 70: a shorter last band leaves less work after the last
  *     upload).
+ *   WSKPN_TUNE_WAIT_LIMIT_US: limit, in microseconds, of every shared-memory
+ *     barrier wait of the context's tensor-core convolutions (0 = the
+ *     default, 2 s).  An expired wait sets a bit of the device status word
+ *     (wskpn_device_status) and the kernel winds down: every role stops,
+ *     waits (for at most 2 s, whatever this limit) for the copies and MMAs
+ *     it has issued, and the CTA frees its tensor memory and returns; the
+ *     launch's output is then invalid.
+ *   WSKPN_TUNE_WAIT_PROBE (BF16 / FP8 only): test hook for that path.  1 =
+ *     in the next tensor-core convolution launch of the context (one launch;
+ *     the key then reads 0 again), each epilogue warp first waits on a
+ *     barrier that nothing signals, so that its wait limit expires.
  * Errors: EINVAL for an unknown key or value. */
 #define WSKPN_TUNE_TC_SPLIT 2
 #define WSKPN_TUNE_TRAIN_RECOMPUTE 3
@@ -501,6 +513,8 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
 #define WSKPN_TUNE_HOST_FIRST_BAND 6
 #define WSKPN_TUNE_HOST_LAST_BAND 7
 #define WSKPN_TUNE_TC_SPLIT_LAYERS 8
+#define WSKPN_TUNE_WAIT_LIMIT_US 9
+#define WSKPN_TUNE_WAIT_PROBE 10
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
 
 /* Reads and clears the context's device status word after synchronising

@@ -21,6 +21,8 @@ TUNE_FP8_SPLIT = 4
 TUNE_HOST_BANDS = 5
 TUNE_HOST_FIRST_BAND = 6
 TUNE_HOST_LAST_BAND = 7
+TUNE_WAIT_LIMIT_US = 9
+TUNE_WAIT_PROBE = 10
 
 
 class Config(ctypes.Structure):

@@ -611,6 +611,14 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
         WSKPN_CUDA_TRY(cudaDeviceSynchronize(), ctx->err);
         return WSKPN_OK;
     }
+    if (key == WSKPN_TUNE_WAIT_LIMIT_US && value >= 0) {
+        ctx->wait_ns = value == 0 ? 2000000000ull : (uint64_t)value * 1000ull;
+        return WSKPN_OK;
+    }
+    if (key == WSKPN_TUNE_WAIT_PROBE && (value == 0 || value == 1) && ctx->cfg.prec != WSKPN_FP32) {
+        ctx->wait_probe = value;
+        return WSKPN_OK;
+    }
     ctx->err = "wskpn_set_tuning: unknown key or value";
     return WSKPN_EINVAL;
 }

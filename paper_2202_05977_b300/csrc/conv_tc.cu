@@ -87,6 +87,8 @@ struct TcArgs {
     uint32_t stage_bytes;
     int tiles_x, tiles_y, ntiles;
     unsigned int* status;
+    uint64_t wait_ns;        // limit of every wait but the drains
+    int probe;               // test hook: the epilogue first waits on a barrier nothing signals
 };
 
 // ------------------------------------------------------------- primitives
@@ -355,10 +357,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     uint64_t* acce = accf + 2;
     uint64_t* wbar = acce + 2;
     uint64_t* fin = wbar + 1;
-    volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(fin + 1);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(fin + 1) + 1;
-    // [COUT_P], 16-byte aligned for vector loads (the barriers end 8 bytes past a 16-byte boundary)
-    float* s_scale = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(fin + 2) + 15) & ~uintptr_t(15));
+    uint64_t* dead = fin + 1;  // never signalled: the bounded-wait test hook (a.probe)
+    volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(dead + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(dead + 1) + 1;
+    // [COUT_P], 16-byte aligned for vector loads
+    float* s_scale = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dead + 2) + 15) & ~uintptr_t(15));
     float* s_bias = s_scale + COUT_P;                     // [COUT_P]
     // XF: edge partial sums and the epilogue warps' tile flags, after the 2 x 64 floats
     float* const sEdge = reinterpret_cast<float*>(
@@ -385,6 +388,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
         mbar_init(smem_u32(wbar), 1);
         mbar_init(smem_u32(fin), 1);
+        mbar_init(smem_u32(dead), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         // accumulators start at zero: every MMA accumulates
         const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll 1
-        for (int c = 0; c < 2 * R * COUT_P; c += 16) tmem_zero16(tmem + lb + (uint32_t)c);
+        for (int c = 0; c < 2 * R * NCB; c += 16) tmem_zero16(tmem + lb + (uint32_t)c);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
     }
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const int x0 = tx * TPX, y0 = ty * R;
                 for (int r0 = 0; r0 < ROWS_IN; r0 += RPI, ++it) {
                     const int s = it % S;
-                    if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -449,17 +453,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 atomicOr(a.status, tc::ST_TIMEOUT_PRODUCER);
                 *abort_flag = 1;
             }
-            // Drain: every issued stage's load must have landed before exit.
+            // Drain: every issued stage's load must have landed before exit
+            // (also after an abort: these waits ignore the abort flag).
             const uint32_t n_in_flight = it < (uint32_t)S ? it : (uint32_t)S;
             for (uint32_t k = 0; k < n_in_flight; ++k) {
                 const uint32_t j = it - 1 - k;
-                mbar_wait(smem_u32(&full[j % S]), (j / S) & 1u, abort_flag);
+                mbar_wait_drain(smem_u32(&full[j % S]), (j / S) & 1u);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag);
+            bool ok = mbar_wait(smem_u32(wbar), 0, abort_flag, a.wait_ns);
             // Descriptors are linear in the start address (16-byte units in
             // the low bits): stages, chunks and taps are offsets from two bases.
             const uint64_t wdesc0 = sdesc_sw32(smem_u32(sW));
@@ -471,7 +476,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             int lt = 0;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
                 const int buf = lt & 1;
-                if (!mbar_wait(smem_u32(&acce[buf]), ((lt >> 1) & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait(smem_u32(&acce[buf]), ((lt >> 1) & 1) ^ 1, abort_flag, a.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const uint32_t dbase = tmem + (uint32_t)(buf * R * NCB);
                 for (int r0 = 0; r0 < ROWS_IN; r0 += RPI, ++it) {
                     const int s = it % S;
-                    if (!mbar_wait(smem_u32(&full[s]), (it / S) & 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&full[s]), (it / S) & 1u, abort_flag, a.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -496,9 +501,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 atomicOr(a.status, tc::ST_TIMEOUT_MMA);
                 *abort_flag = 1;
             }
-            // Every issued MMA must complete before TMEM is released.
+            // Every issued MMA must complete before TMEM is released (also
+            // after an abort: the drain wait ignores the abort flag).
             mma_commit(smem_u32(fin));
-            mbar_wait(smem_u32(fin), 0, abort_flag);
+            mbar_wait_drain(smem_u32(fin), 0);
         }
     } else {
         // ------------------------------------------------ epilogue warps 2..5
@@ -509,7 +515,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
             const int buf = lt & 1;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag);
+            if (lane == 0) {
+                // test hook: a wait that nothing completes, so the limit expires
+                if (a.probe && lt == 0) ok = mbar_wait(smem_u32(dead), 0, abort_flag, a.wait_ns);
+                if (ok) ok = mbar_wait(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag, a.wait_ns);
+            }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if constexpr (XF) {
                 // the rows below hold barriers of the 4 epilogue warps: all of
@@ -977,6 +987,8 @@ struct TcRun {
     float out_qscale;
     unsigned int* status;
     int device;
+    uint64_t wait_ns = MBAR_WAIT_NS;
+    int probe = 0;
 };
 
 static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int H, int W, cudaStream_t st,
@@ -1044,6 +1056,8 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     a.tiles_y = cdiv(H, xf ? xf_rows_per_tile(KS) : tc::rows_per_tile(cg));
     a.ntiles = a.tiles_x * a.tiles_y * B;
     a.status = r.status;
+    a.wait_ns = r.wait_ns;
+    a.probe = r.probe;
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, r.device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
@@ -1104,6 +1118,9 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     r.out_qscale = fp8 && !r.last ? 1.f / ctx->act_scale[l + 1] : 1.f;
     r.status = ctx->d_status;
     r.device = ctx->device;
+    r.wait_ns = ctx->wait_ns;
+    r.probe = ctx->wait_probe;
+    ctx->wait_probe = 0;  // the test hook applies to one launch
     return tc_run(r, in, out, B, H, W, st, ctx->err);
 }
 

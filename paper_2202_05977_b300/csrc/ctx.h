@@ -60,6 +60,8 @@ struct wskpn_ctx {
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
     bool fp8_calibrated = false;
     int tc_split = 1;  // BF16 activations as hi/lo pairs (WSKPN_TUNE_TC_SPLIT)
+    uint64_t wait_ns = 2000000000ull;  // limit of the convolutions' barrier waits (WSKPN_TUNE_WAIT_LIMIT_US)
+    int wait_probe = 0;                 // test hook for the next convolution launch (WSKPN_TUNE_WAIT_PROBE)
     unsigned tc_split_layers = 0xFFFFFFFFu;  // of those, the layer inputs split (bit l; WSKPN_TUNE_TC_SPLIT_LAYERS)
     int fp8_split = 1;  // e4m3 activations and weights as hi/lo pairs (WSKPN_TUNE_FP8_SPLIT)
     int train_tc_recompute = 1;  // backward on the tensor cores: 1 recompute + input gradients, 2 recompute only (WSKPN_TUNE_TRAIN_RECOMPUTE)

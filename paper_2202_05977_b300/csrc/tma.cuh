@@ -11,8 +11,10 @@
 
 namespace wskpn {
 
-// Limit of every mbarrier wait: a wait that has not completed after this
-// long returns false (the caller records a status and winds down).
+// Default limit of every mbarrier wait: a wait that has not completed after
+// this long returns false (the caller records a status and winds down).  A
+// context may shorten the limit of its convolutions' waits
+// (WSKPN_TUNE_WAIT_LIMIT_US); drains always use this one.
 constexpr uint64_t MBAR_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -43,8 +45,9 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait: false when the limit expired or another role aborted.
-static __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int* abort_flag) {
+// Bounded wait: false when limit_ns expired or another role aborted.
+static __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, const volatile int* abort_flag,
+                                              uint64_t limit_ns = MBAR_WAIT_NS) {
     if (mbar_try_wait(a, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
@@ -52,6 +55,19 @@ static __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, const
         for (int i = 0; i < 8; ++i)
             if (mbar_try_wait(a, parity)) return true;
         if (*abort_flag) return false;
+        if (gtimer() - t0 > limit_ns) return false;
+    }
+}
+// Drain wait for a role's own copies or MMAs in flight before it exits or
+// frees TMEM: bounded by the default limit only, not cut short by the
+// abort flag (aborting roles must still let their issued work land).
+static __device__ __noinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
+    if (mbar_try_wait(a, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+#pragma unroll 1
+        for (int i = 0; i < 8; ++i)
+            if (mbar_try_wait(a, parity)) return true;
         if (gtimer() - t0 > MBAR_WAIT_NS) return false;
     }
 }

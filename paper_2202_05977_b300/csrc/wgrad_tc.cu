@@ -238,11 +238,12 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
                 atomicOr(a.status, ST_TIMEOUT);
                 *abort_flag = 1;
             }
-            // Drain: every issued stage's load must have landed before exit.
+            // Drain: every issued stage's load must have landed before exit
+            // (also after an abort: these waits ignore the abort flag).
             const uint32_t n_in_flight = it < (uint32_t)S ? it : (uint32_t)S;
             for (uint32_t k = 0; k < n_in_flight; ++k) {
                 const uint32_t j = it - 1 - k;
-                mbar_wait(smem_u32(&full[j % S]), (j / S) & 1u, abort_flag);
+                mbar_wait_drain(smem_u32(&full[j % S]), (j / S) & 1u);
             }
         }
     } else if (warp == 1) {
@@ -288,8 +289,10 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
                 atomicOr(a.status, ST_TIMEOUT);
                 *abort_flag = 1;
             }
-            // arrives when every issued MMA has completed
+            // arrives when every issued MMA has completed; TMEM is released
+            // only after that, whether or not the writers aborted
             commit(smem_u32(done));
+            mbar_wait_drain(smem_u32(done), 0);
         }
     } else {
         // ------------------------------------------------ partial-sum writers, warps 2..5

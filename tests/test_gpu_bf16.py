@@ -173,3 +173,37 @@ def test_bf16_denoises_1080p_faster_than_fp32(wk):
     t16, t32 = ms("bf16"), ms("fp32")
     print(f"1080p: bf16 {t16:.3f} ms, fp32 {t32:.3f} ms")
     assert t16 * 3 < t32
+
+
+def test_bounded_wait_expires_and_context_recovers(wk):
+    """Failure path of the tensor-core convolution without a GPU fault: with
+    a 1 ms wait limit and the test hook that makes each epilogue warp wait
+    once on a barrier nothing signals, the wait expires; the kernel winds
+    down (its roles drain their issued copies and MMAs, TMEM is freed) and
+    the C ABI reports WSKPN_ETIMEOUT with the epilogue's status bit.  With
+    the default limit restored, the same context denoises the next frame
+    to the oracle's values."""
+    import ctypes
+
+    from paper_2202_05977_b300 import _lib
+
+    lib = _lib.load()
+    H, W = 64, 96
+    f = synth.make_frame(H, W, 5)
+    wb = synth.make_weights(seed=5)
+    d = _den(wk, wb, max_hw=(H, W))
+    dev = to_dev(stack_frames([f]))
+    d.denoise(*args(dev))
+    assert d.device_status() == 0
+    d.set_tuning(_lib.TUNE_WAIT_LIMIT_US, 1000)
+    d.set_tuning(_lib.TUNE_WAIT_PROBE, 1)
+    d.denoise(*args(dev))
+    bits = ctypes.c_uint32()
+    assert lib.wskpn_device_status(d._h, ctypes.byref(bits)) == _lib.ETIMEOUT
+    assert bits.value & 4, bits.value  # bit 2: the epilogue role's wait expired
+    d.set_tuning(_lib.TUNE_WAIT_LIMIT_US, 0)
+    out = d.denoise(*args(dev)).cpu().numpy()[0]
+    assert lib.wskpn_device_status(d._h, ctypes.byref(bits)) == _lib.OK and bits.value == 0
+    mx, mean = rel_err(out, oracle.denoise(f, wb))
+    print(f"after the expired wait: max rel {mx:.3e} mean {mean:.3e}")
+    assert mx < TOL_BF16
