@@ -73,6 +73,9 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=4096)
     p.add_argument("--serve-rate", type=float, default=240.0)
     p.add_argument("--serve-workers", type=int, default=2, help="serving workers (streams with their own context)")
+    p.add_argument("--serve-sweep", type=float, nargs="*", default=[480.0, 960.0, 1920.0],
+                   help="further offered rates (req/s) for the load sweep")
+    p.add_argument("--serve-sweep-requests", type=int, default=2048)
     p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
     return p.parse_args()
 
@@ -292,36 +295,44 @@ def config_block(precision):
             "kernel_sizes": list(KSIZES), "l2": "flushed between timed steps (256 MiB write)"}
 
 
-def serving_run(wk_serving, synth, torch, np, n_req, rate, wb, dev, n_workers=2):
+def _pct(v, p):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
+
+
+def serving_run(wk_serving, synth, torch, np, n_req, rate, wb, dev, n_workers=2, warm=True):
     """Serving form: n_req requests, Poisson arrivals at `rate`/s from 8
-    client streams, sizes uniform over 720p / 1080p / 1440p, BF16."""
+    client streams, sizes uniform over 720p / 1080p / 1440p, BF16.  Each
+    request's timeline comes back with its delivery (wskpn_serve_wait_info):
+    latency percentiles per resolution, batch sizes, and how long batches of
+    the two workers were in flight at the same time."""
     sizes = [(720, 1280), (1080, 1920), (1440, 2560)]
     keys = ("radiance", "albedo", "normal", "depth")
     frames = []
     for i, (h, w) in enumerate(sizes):
         f = synth.make_frame(h, w, 11 + i)
         frames.append([torch.from_numpy(np.ascontiguousarray(f[k][None])).to(dev) for k in keys])
-    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=n_workers, max_batch=4, mem_budget=8 << 30,
-                            batch_window_us=0)
+    mk = lambda: wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=n_workers, max_batch=4,
+                                   mem_budget=8 << 30, batch_window_us=0)
     n_streams = 8
     outs = {(s, r): torch.empty((1, 3, *sizes[r]), device=dev) for s in range(n_streams) for r in range(3)}
     busy = {}
     g = np.random.default_rng(240)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
     res = g.integers(0, 3, n_req)
-    # warm the graphs of every size once
-    for r in range(3):
-        t = srv.submit(0, *frames[r], outs[(0, r)])
-        srv.wait(t, 60000)
-    srv.stop()
-    srv = wk_serving.Server(wb, "bf16", max_hw=(1440, 2560), n_workers=n_workers, max_batch=4, mem_budget=8 << 30,
-                            batch_window_us=0)
+    if warm:  # load every kernel once in a throw-away server
+        srv = mk()
+        for r in range(3):
+            t = srv.submit(0, *frames[r], outs[(0, r)])
+            srv.wait(t, 60000)
+        srv.stop()
+    srv = mk()
     for r in range(3):  # capture outside the measured stream
         t = srv.submit(0, *frames[r], outs[(0, r)])
         srv.wait(t, 60000)
     stats0 = srv.stats()
+    infos = []
     t0 = time.perf_counter()
-    tickets = []
     late = 0
     for i in range(n_req):
         now = time.perf_counter() - t0
@@ -329,25 +340,53 @@ def serving_run(wk_serving, synth, torch, np, n_req, rate, wb, dev, n_workers=2)
             time.sleep(arrivals[i] - now)
         sid, r = i % n_streams, int(res[i])
         prev = busy.get((sid, r))
-        if prev is not None and srv.wait(prev, 0) != 0:
-            late += 1
-            srv.wait(prev, -1)
-        t = srv.submit(sid, *frames[r], outs[(sid, r)])
-        busy[(sid, r)] = t
-        tickets.append(t)
+        if prev is not None:
+            s_, info = srv.wait_info(prev, 0)
+            if info is None:
+                late += 1
+                s_, info = srv.wait_info(prev, -1)
+            infos.append(info)
+        busy[(sid, r)] = srv.submit(sid, *frames[r], outs[(sid, r)])
     for t in busy.values():
-        srv.wait(t, -1)
+        infos.append(srv.wait_info(t, -1)[1])
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.stop()
     done = st["completed"] - stats0["completed"]
+    per_res = {}
+    for (h, w) in sizes:
+        lat = [x["done_ms"] - x["submit_ms"] for x in infos if x and (x["h"], x["w"]) == (h, w)]
+        per_res[f"{w}x{h}"] = {"n": len(lat), "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99)}
+    lat_all = [x["done_ms"] - x["submit_ms"] for x in infos if x]
+    # time during which batches of different workers were in flight together
+    spans = {}
+    for x in infos:
+        if x and x["worker"] >= 0:
+            spans.setdefault(x["worker"], set()).add((x["dispatch_ms"], x["done_ms"]))
+    overlap = 0.0
+    ws = sorted(spans)
+    if len(ws) >= 2:
+        ev = []
+        for k in ws:
+            for (a, b) in spans[k]:
+                ev += [(a, 1, k), (b, -1, k)]
+        ev.sort()
+        live = {k: 0 for k in ws}
+        last = None
+        for tms, d, k in ev:
+            if last is not None and sum(1 for v in live.values() if v > 0) >= 2:
+                overlap += tms - last
+            live[k] += d
+            last = tms
     return {"requests": n_req, "rate_per_s": rate, "streams": n_streams, "workers": n_workers,
             "sizes": ["1280x720", "1920x1080", "2560x1440"], "precision": "bf16",
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "p50_ms": _pct(lat_all, 0.5), "p99_ms": _pct(lat_all, 0.99), "mean_ms": st["mean_ms"],
+            "max_ms": st["max_ms"], "per_resolution": per_res,
             "fps": done / wall, "mean_batch": st["mean_batch"], "batches": st["batches"],
             "graph_launches": st["graph_launches"], "rejected": st["rejected"], "failed": st["failed"],
+            "workers_in_flight_together_ms": overlap, "wall_s": wall,
             "mem_peak_gib": st["mem_peak"] / 2 ** 30, "client_waits_for_own_buffer": late,
-            "note": "latency submit->delivery incl. the warm-up requests of each size (3 of the total)"}
+            "note": "latency submit->delivery of the measured requests (the warm-up request of each size excluded)"}
 
 
 def cpu_baseline():
@@ -731,6 +770,15 @@ def main():
             import paper_2202_05977_b300.serving as wk_serving
             line["serving"] = serving_run(wk_serving, synth, torch, np, args.serve_requests, args.serve_rate, wb, dev,
                                           args.serve_workers)
+            # offered load beyond the configured 240 req/s: where frames/s stops rising
+            sweep = []
+            for rate in args.serve_sweep:
+                r_ = serving_run(wk_serving, synth, torch, np, args.serve_sweep_requests, rate, wb, dev,
+                                 args.serve_workers, warm=False)
+                sweep.append({k: r_[k] for k in ("rate_per_s", "requests", "fps", "mean_batch", "p50_ms", "p99_ms",
+                                                 "per_resolution", "workers_in_flight_together_ms", "wall_s",
+                                                 "rejected", "failed")})
+            line["serving_sweep"] = sweep
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], ref = cpu_baseline()
             # every pixel of the precision forms against the FP64 oracle

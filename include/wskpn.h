@@ -430,6 +430,20 @@ wskpn_status wskpn_serve_submit_temporal(wskpn_server* srv, int stream_id, const
  * ticket, or the request's own failure status. */
 wskpn_status wskpn_serve_wait(wskpn_server* srv, uint64_t ticket, int timeout_ms);
 
+/* Timeline of one delivered request, in milliseconds of the host's
+ * steady clock since wskpn_serve_start: when it was submitted, when its
+ * batch was handed to a worker (dispatch_ms; -1 if it never ran), and when
+ * the scheduler saw that batch complete (done_ms, polled every ~20 us);
+ * the worker index, the frames in its batch and its size. */
+typedef struct {
+    int h, w, worker, batch;
+    double submit_ms, dispatch_ms, done_ms;
+} wskpn_serve_ticket_info;
+
+/* As wskpn_serve_wait; on delivery also fills *info (NULL is ignored). */
+wskpn_status wskpn_serve_wait_info(wskpn_server* srv, uint64_t ticket, int timeout_ms,
+                                   wskpn_serve_ticket_info* info);
+
 /* Pauses (1) or resumes (0) admission of queued requests (batches already
  * on the GPU finish).  Used to drain or to build a queue deterministically. */
 wskpn_status wskpn_serve_pause(wskpn_server* srv, int paused);

@@ -75,6 +75,11 @@ class ServeStats(ctypes.Structure):
                 ("temporal_bytes", ctypes.c_size_t)]
 
 
+class ServeTicketInfo(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_int), ("w", ctypes.c_int), ("worker", ctypes.c_int), ("batch", ctypes.c_int),
+                ("submit_ms", ctypes.c_double), ("dispatch_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _F = ctypes.c_float
@@ -123,6 +128,7 @@ SIGNATURES = {
     "wskpn_serve_submit": ([_P, _I, _FR, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wskpn_serve_submit_temporal": ([_P, _I, _FR, _P, _P, _I, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
     "wskpn_serve_wait": ([_P, ctypes.c_uint64, _I], _I),
+    "wskpn_serve_wait_info": ([_P, ctypes.c_uint64, _I, ctypes.POINTER(ServeTicketInfo)], _I),
     "wskpn_serve_pause": ([_P, _I], _I),
     "wskpn_serve_stats_get": ([_P, ctypes.POINTER(ServeStats)], _I),
     "wskpn_serve_stop": ([_P], None),

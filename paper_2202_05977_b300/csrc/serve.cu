@@ -44,7 +44,8 @@ struct Request {
     const float* motion = nullptr;    // and motion [2][h][w]
     int temporal = 0, reset = 0;
     size_t footprint = 0;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_dispatch, t_done;
+    int worker = -1, batch = 0;  // worker that ran it and frames in its batch
     int state = 0;  // 0 queued, 1 running, 2 complete, 3 delivered
     wskpn_status status = WSKPN_OK;
 };
@@ -91,7 +92,7 @@ struct wskpn_server {
              graph_captures = 0, batched_frames = 0, temporal_frames = 0;
     std::vector<double> lat_ms;
     bool any_submit = false;
-    wskpn::Clock::time_point t_first, t_last;
+    wskpn::Clock::time_point t_start, t_first, t_last;
     std::string err;
 };
 
@@ -260,7 +261,8 @@ static void scheduler(wskpn_server* s) {
         // 2. admission and dispatch
         bool dispatched = false;
         if (!s->paused) {
-            for (auto& wk : s->workers) {
+            for (size_t wi = 0; wi < s->workers.size(); ++wi) {
+                Worker& wk = s->workers[wi];
                 if (wk.busy || s->queue.empty()) continue;
                 // the oldest request that may run now: a temporal stream runs one
                 // frame at a time, in submission order
@@ -304,8 +306,13 @@ static void scheduler(wskpn_server* s) {
                 }
                 s->mem_in_use = mem;
                 s->mem_peak = std::max(s->mem_peak, mem);
-                for (Request* r : wk.batch)
+                const auto t_disp = Clock::now();
+                for (Request* r : wk.batch) {
                     if (r->temporal) s->tstreams[r->stream_id].running = true;
+                    r->worker = (int)wi;
+                    r->batch = (int)wk.batch.size();
+                    r->t_dispatch = t_disp;
+                }
                 const wskpn_status st = dispatch(s, wk);
                 ++s->batches;
                 s->batched_frames += wk.batch.size();
@@ -396,6 +403,7 @@ wskpn_status wskpn_serve_start(const wskpn_config* cfg, const float* host_weight
             return st;
         }
     }
+    s->t_start = Clock::now();
     s->sched = std::thread(scheduler, s);
     *out = s;
     return WSKPN_OK;
@@ -461,6 +469,10 @@ wskpn_status wskpn_serve_submit_temporal(wskpn_server* s, int stream_id, const w
 }
 
 wskpn_status wskpn_serve_wait(wskpn_server* s, uint64_t ticket, int timeout_ms) {
+    return wskpn_serve_wait_info(s, ticket, timeout_ms, nullptr);
+}
+
+wskpn_status wskpn_serve_wait_info(wskpn_server* s, uint64_t ticket, int timeout_ms, wskpn_serve_ticket_info* info) {
     if (!s) return WSKPN_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(ticket);
@@ -475,6 +487,16 @@ wskpn_status wskpn_serve_wait(wskpn_server* s, uint64_t ticket, int timeout_ms) 
     else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
         return WSKPN_ETIMEOUT;
     const wskpn_status st = r->status;
+    if (info) {
+        auto ms = [&](Clock::time_point t) { return std::chrono::duration<double, std::milli>(t - s->t_start).count(); };
+        info->h = r->h;
+        info->w = r->w;
+        info->worker = r->worker;
+        info->batch = r->batch;
+        info->submit_ms = ms(r->t_submit);
+        info->dispatch_ms = r->worker >= 0 ? ms(r->t_dispatch) : -1.0;
+        info->done_ms = ms(r->t_done);
+    }
     s->reqs.erase(it);
     delete r;
     return st;

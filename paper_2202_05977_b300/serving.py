@@ -73,6 +73,16 @@ class Server:
         """Status of the ticket (OK, ETIMEOUT, ...)."""
         return self._lib.wskpn_serve_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms))
 
+    def wait_info(self, ticket, timeout_ms=-1):
+        """(status, timeline dict) of the ticket: h, w, worker, batch and
+        submit / dispatch / done times in ms since the server started (the
+        dict is None unless delivered)."""
+        info = _lib.ServeTicketInfo()
+        s = self._lib.wskpn_serve_wait_info(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(info))
+        if s in (_lib.ETIMEOUT, _lib.EINVAL):
+            return s, None
+        return s, {f: getattr(info, f) for f, _ in _lib.ServeTicketInfo._fields_}
+
     def pause(self, paused=True):
         _lib.check(self._lib.wskpn_serve_pause(self._h, int(paused)))
 

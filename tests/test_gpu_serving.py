@@ -177,3 +177,47 @@ def test_temporal_stream_restarts_when_its_size_changes(torch):
         for o, f in zip(part, frames):
             acc = ta.step(f["radiance"], f["position"], f["normal"], f["motion"])
             assert torch.equal(o, d.denoise(acc[None], f["albedo"][None], f["normal"][None], f["depth"][None]))
+
+
+def test_saturating_burst_batches_overlaps_and_matches_solo(torch):
+    """Saturating load: 60 requests of three sizes queued at once (admission
+    paused while they arrive, then resumed) on two workers.  The scheduler
+    forms batches of several frames, the two workers' batches are in flight
+    on the GPU at the same time (their dispatch-to-done intervals overlap),
+    and every result is bit-identical to the same frame denoised alone."""
+    import paper_2202_05977_b300 as wk
+    from paper_2202_05977_b300.serving import Server
+    wb = synth.make_weights(seed=14)
+    shapes = [(96, 160), (72, 128), (120, 200)]
+    sizes = [shapes[i % 3] for i in range(60)]
+    frames = _frames(sizes, 800)
+    srv = Server(wb, "bf16", max_hw=(120, 200), n_workers=2, max_batch=4, batch_window_us=0)
+    # graphs captured before the measured burst
+    warm = [torch.empty((1, 3, h, w), device="cuda") for (h, w) in shapes]
+    for (h, w), o, f in zip(shapes, warm, frames[:3]):
+        assert srv.wait(srv.submit(0, *args(f), o), 20000) == OK
+    srv.pause(True)
+    outs = [torch.full((1, 3, h, w), float("nan"), device="cuda") for (h, w) in sizes]
+    tickets = [srv.submit(i % 6, *args(frames[i]), outs[i]) for i in range(len(sizes))]
+    srv.pause(False)
+    infos = []
+    for t in tickets:
+        s, info = srv.wait_info(t, 30000)
+        assert s == OK
+        infos.append(info)
+    st = srv.stats()
+    srv.stop()
+    assert st["failed"] == 0
+    batches = [x["batch"] for x in infos]
+    assert max(batches) > 1 and sum(batches) / len(batches) > 1.5, batches
+    by_worker = {}
+    for x in infos:
+        by_worker.setdefault(x["worker"], set()).add((x["dispatch_ms"], x["done_ms"]))
+    assert set(by_worker) == {0, 1}, by_worker.keys()
+    overlap = any(a0 < b1 and a1 < b0 for (a0, b0) in by_worker[0] for (a1, b1) in by_worker[1])
+    assert overlap, by_worker
+    solo = {}
+    for i, (h, w) in enumerate(sizes):
+        if (h, w) not in solo:
+            solo[(h, w)] = wk.Denoiser(wb, "bf16", max_hw=(h, w))
+        assert torch.equal(outs[i], solo[(h, w)].denoise(*args(frames[i]))), i
