@@ -93,22 +93,11 @@ def peaks():
                 "source": "fallback"}
 
 
-def host_upload_bytes(h: int, w: int, n_layers: int = len(WIDTHS) - 1, ks: int = KS,
-                      kmax: int = max(KSIZES)) -> int:
-    """Bytes wskpn_denoise_host uploads for one frame: frames of 432+ rows go
-    in bands of ceil(h / nb) rows (nb = min(8, h // 216)), each with a halo
-    of n_layers * ks // 2 + kmax // 2 rows, so the halo rows travel twice."""
-    nb = min(8, h // 216)
-    if nb < 2:
-        return 40 * h * w
-    halo = n_layers * (ks // 2) + kmax // 2
-    bh = -(-h // nb)
-    rows = 0
-    for k in range(nb):
-        y0, y1 = k * bh, min(h, (k + 1) * bh)
-        if y0 < y1:
-            rows += min(h, y1 + halo) - max(0, y0 - halo)
-    return 40 * rows * w
+def host_upload_bytes(h: int, w: int) -> int:
+    """Bytes wskpn_denoise_host uploads for one frame: every input row
+    (10 float32 channels) crosses the host link once; the halo rows a band
+    shares with the previous band are copied on the device."""
+    return 40 * h * w
 
 
 # ------------------------------------------------------- replicas (N > 1)

@@ -363,7 +363,8 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
     if (!ctx->up_stream) {
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking), ctx->err);
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking), ctx->err);
-        ctx->band_events.resize(6);
+        WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->halo_stream, cudaStreamNonBlocking), ctx->err);
+        ctx->band_events.resize(8);
         for (auto& e : ctx->band_events)
             WSKPN_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), ctx->err);
     }
@@ -387,13 +388,15 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
         WSKPN_CUDA_TRY(cudaMalloc(&ctx->d_band[1], need * sizeof(float)), ctx->err);
         ctx->band_floats = need;
     }
-    // events per slot: [0..1] uploaded, [2..3] computed, [4..5] downloaded
+    // events per slot: [0..1] uploaded, [2..3] computed, [4..5] downloaded,
+    // [6..7] halo rows copied from the other slot
     cudaEvent_t* ev = ctx->band_events.data();
     const int ch[4] = {3, 3, 3, 1};
     const size_t HW = (size_t)h * w;
     int job = 0;
     for (int b = 0; b < batch; ++b) {
         const float* src[4] = {hf[b].radiance, hf[b].albedo, hf[b].normal, hf[b].depth};
+        int pe0 = 0, pe1 = 0;  // extended rows of this frame's previous band (in the other slot)
         for (int k = 0; k < nb; ++k, ++job) {
             const int slot = job & 1;
             const int y0 = yb[k], y1 = yb[k + 1];
@@ -401,27 +404,56 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
             const int e0 = std::max(0, y0 - halo), e1 = std::min(h, y1 + halo), eh = e1 - e0;
             const size_t ePX = (size_t)eh * w;
             float* base = ctx->d_band[slot];
-            // the slot's previous band must be computed before its inputs are replaced
+            // the slot's previous band must be computed before its inputs are
+            // replaced, and the other slot's band must have copied its halo rows
+            // out of this slot
             if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, ev[2 + slot], 0), ctx->err);
+            if (job >= 1) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, ev[6 + (slot ^ 1)], 0), ctx->err);
             wskpn_frame f{};
             const float** dst[4] = {&f.radiance, &f.albedo, &f.normal, &f.depth};
+            // rows [e0, kept) are already on the device in the previous band's
+            // slot (its halo overlaps this band's): copied there device to device
+            // on a stream of their own, concurrently with this band's upload;
+            // only rows [kept, e1) cross the host link, so each input row is
+            // uploaded once per frame
+            const int kept = k > 0 ? std::max(e0, std::min(e1, pe1)) : e0;
+            const size_t pPX = (size_t)(pe1 - pe0) * w;
+            const float* prev = ctx->d_band[slot ^ 1];
+            if (kept > e0) {  // after the previous band's upload and this slot's previous compute
+                WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->halo_stream, ev[slot ^ 1], 0), ctx->err);
+                if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->halo_stream, ev[2 + slot], 0), ctx->err);
+            }
             float* p = base;
-            // one 2D copy per input buffer: its ch[q] plane bands (HW apart in the
-            // host buffer) land ePX apart in the band buffer
             for (int q = 0; q < 4; ++q) {
                 *dst[q] = p;
-                WSKPN_CUDA_TRY(cudaMemcpy2DAsync(p, ePX * sizeof(float), src[q] + (size_t)e0 * w, HW * sizeof(float),
-                                                 ePX * sizeof(float), ch[q], cudaMemcpyHostToDevice, ctx->up_stream),
-                               ctx->err);
+                if (kept > e0)  // ch[q] planes, pPX apart in the previous slot, ePX apart here
+                    WSKPN_CUDA_TRY(cudaMemcpy2DAsync(p, ePX * sizeof(float), prev + (size_t)(e0 - pe0) * w,
+                                                     pPX * sizeof(float), (size_t)(kept - e0) * w * sizeof(float),
+                                                     ch[q], cudaMemcpyDeviceToDevice, ctx->halo_stream),
+                                   ctx->err);
+                if (e1 > kept)  // one 2D copy per input buffer: ch[q] planes HW apart in the host buffer
+                    WSKPN_CUDA_TRY(cudaMemcpy2DAsync(p + (size_t)(kept - e0) * w, ePX * sizeof(float),
+                                                     src[q] + (size_t)kept * w, HW * sizeof(float),
+                                                     (size_t)(e1 - kept) * w * sizeof(float), ch[q],
+                                                     cudaMemcpyHostToDevice, ctx->up_stream),
+                                   ctx->err);
                 p += (size_t)ch[q] * ePX;
+                prev += (size_t)ch[q] * pPX;
             }
-            float* dout = p;
+            WSKPN_CUDA_TRY(cudaEventRecord(ev[6 + slot], ctx->halo_stream), ctx->err);
+            pe0 = e0;
+            pe1 = e1;
+            // the output region sits past the inputs of the tallest band, so a
+            // later, taller band's upload into this slot cannot reach the rows
+            // of this band still waiting for download
+            float* dout = base + (size_t)10 * ext * w;
             WSKPN_CUDA_TRY(cudaEventRecord(ev[slot], ctx->up_stream), ctx->err);
             // compute after the upload, and after the slot's previous download;
             // with two compute streams, slot 1's jobs use the second stream and
             // the second half of the workspaces
             cudaStream_t cs = two && slot ? ctx->band_stream : st;
             WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[slot], 0), ctx->err);
+            WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[6 + slot], 0), ctx->err);
             if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[4 + slot], 0), ctx->err);
             {
                 WorkspaceShift shift(ctx, two && slot, band_px);

@@ -99,6 +99,7 @@ void ctx_free(wskpn_ctx* ctx) {
     if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
     if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
     if (ctx->band_stream) cudaStreamDestroy(ctx->band_stream);
+    if (ctx->halo_stream) cudaStreamDestroy(ctx->halo_stream);
     cudaFree(ctx->d_fallbacks);
     for (auto& set : ctx->prof_sets)
         for (auto e : set) cudaEventDestroy(e);

@@ -52,9 +52,10 @@ struct wskpn_ctx {
     // of two bands in flight
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
     cudaStream_t band_stream = nullptr;  // second compute stream of the host-buffer pipeline
+    cudaStream_t halo_stream = nullptr;  // device copies of the halo rows bands share
     float* d_band[2] = {nullptr, nullptr};  // [10 + 3][band_rows][max_w]
     size_t band_floats = 0;
-    std::vector<cudaEvent_t> band_events;   // 4 per band slot ring (uploaded, computed, downloaded)
+    std::vector<cudaEvent_t> band_events;   // per band slot: uploaded, computed, downloaded, halo copied
     unsigned int* d_fallbacks = nullptr;
     unsigned int* d_status = nullptr;  // device status word of the tensor-core kernels
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales
