@@ -40,17 +40,18 @@ KSIZES = (3, 5, 7, 9, 11, 13)
 DECODE_BYTES_PER_PX = 84
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 148, 2032.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# of the current kernels at 1920x1080 (profiles/conv_tc_bf16_1080p.md and
-# profiles/decode_fuse_fwd_1080p.md); a kernel absent here has no capture of
-# its current version
+# of the current kernels at 1920x1080 (profiles/traffic_bf16_1080p.md); the
+# reconstruction kernel reads the same bytes whatever the network's precision;
+# a kernel absent here has no capture of its current version
 TRAFFIC = {
-    ("bf16", "conv1 (10->32)"): 344.9e6,
-    ("bf16", "conv2 (32->48)"): 610.0e6,
-    ("bf16", "conv3 (48->64)"): 875.7e6,
-    ("bf16", "conv4 (64->12)"): 620.4e6,
-    ("bf16", "decode_fuse_fwd"): 165.4e6,
-    ("fp32", "decode_fuse_fwd"): 165.4e6,
-    ("fp8", "decode_fuse_fwd"): 165.4e6,
+    ("bf16", "prep"): 159.7e6,
+    ("bf16", "conv1 (10->32)"): 341.3e6,
+    ("bf16", "conv2 (32->48)"): 606.7e6,
+    ("bf16", "conv3 (48->64)"): 873.2e6,
+    ("bf16", "conv4 (64->12)"): 616.7e6,
+    ("bf16", "decode_fuse_fwd"): 161.1e6,
+    ("fp32", "decode_fuse_fwd"): 161.1e6,
+    ("fp8", "decode_fuse_fwd"): 161.1e6,
 }
 
 
@@ -152,7 +153,8 @@ def stage_rooflines(stage_ms, precision, pk, h=H, w=W, tpeak=None):
             gbs = byts / (ms * 1e-3) / 1e9
             out["prep" if i == 0 else "reconstruct"] = {
                 "bound": "hbm", "achieved": gbs, "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
-                "traffic": TRAFFIC.get((precision, "decode_fuse_fwd")) if i == L + 1 and (h, w) == (H, W) else None}
+                "traffic": TRAFFIC.get((precision, "prep" if i == 0 else "decode_fuse_fwd")) if (h, w) == (H, W)
+                else None}
         else:
             tf = conv_flops(i - 1, h, w) / (ms * 1e-3) / 1e12
             if precision == "fp32":
