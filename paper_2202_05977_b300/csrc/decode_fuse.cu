@@ -248,9 +248,10 @@ __device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float*
 // per-level filtering of the multi-resolution variant.
 //
 // Organisation (64 x 32 output tiles, 256 threads, two CTAs per SM):
-//  * set-up: the demodulated irradiance y of the tile's 44 x 80 footprint
-//    (rows -6..37, columns -8..71 around the tile, 0 outside the image) is
-//    formed once into shared memory as a y0 plane and a (y1, y2) plane;
+//  * set-up: the radiance and albedo of the tile's 44 x 80 footprint (rows
+//    -6..37, columns -8..71 around the tile) are staged by cp.async while
+//    the fusion logits load, and the demodulated irradiance y = r / (a + eps)
+//    (0 outside the image) is formed in place as three planes;
 //    each horizontal-pass thread keeps, for its 8 pixels, the maximum c of
 //    their fusion logits (the shift of Eq. 5's softmax) in registers;
 //  * per window size K (two block barriers):
@@ -288,14 +289,19 @@ constexpr int LP = TW + 4;              // 68: pitch of the per-pixel planes (16
 constexpr int CPT = (NCH + THREADS - 1) / THREADS;  // chunks per thread (4)
 static_assert(TH == 32 && TW / SEG == NWARP, "horizontal pass: lane = row, warp = segment");
 static_assert(2 * (TW + 2 * HALO) < THREADS, "vertical pass: one task per thread, some threads idle");
-constexpr size_t OFF_Y12 = 0;                                     // float2 [FH][FW]: (y1, y2)
-constexpr size_t OFF_Y0 = OFF_Y12 + sizeof(float2) * FH * FW;    // float  [FH][FW]
-constexpr size_t OFF_Z = OFF_Y0 + sizeof(float) * FH * FW;       // float  [2][FH][FW]: I_i, I_{i+1}
-constexpr size_t OFF_V = OFF_Z + sizeof(float) * 2 * FH * FW;    // float2 [2][TH][VP]: (N0, D) | (N1, N2)
+constexpr size_t PLANE = sizeof(float) * FH * FW;                // one staged [FH][FW] plane (14,080 B)
+constexpr size_t OFF_Y = 0;                                       // float [3][FH][FW]: y0, y1, y2
+constexpr size_t OFF_Z = OFF_Y + 3 * PLANE;                      // float [2][FH][FW]: I_i, I_{i+1}
+constexpr size_t OFF_V = OFF_Z + 2 * PLANE;                      // float2 [2][TH][VP]: (N0, D) | (N1, N2)
 constexpr size_t OFF_R = OFF_V + sizeof(float2) * 2 * TH * VP;   // int [2]: shifts of sizes i, i + 1
 constexpr size_t SMEM_BYTES = OFF_R + sizeof(int) * 4;
-static_assert(OFF_V % 16 == 0 && OFF_Z % 16 == 0, "16-byte aligned planes");
-static_assert(3 * TH * LP * sizeof(float) <= OFF_Y0 - OFF_Y12, "staged albedo fits the (y1, y2) plane");
+// set-up: the radiance footprint is staged in the second z buffer and the
+// window-sum planes (idle until the first size), the albedo footprint in
+// the y planes, where y = r / (a + eps) then replaces it element by element
+constexpr size_t OFF_RSTAGE = OFF_Z + PLANE;
+static_assert(OFF_RSTAGE + 3 * PLANE <= OFF_R, "staged radiance fits before the shifts");
+static_assert(OFF_V % 16 == 0 && OFF_Z % 16 == 0 && PLANE % 16 == 0, "16-byte aligned planes");
+static_assert(3 * TH * LP * sizeof(float) <= 2 * PLANE, "staged albedo fits the y1, y2 planes");
 static_assert(2 * (SMEM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
 constexpr float LOG2E = 1.4426950408889634f;
 }  // namespace dfv
@@ -451,21 +457,22 @@ __device__ __forceinline__ void load_fusion_logits(float (&l)[dfv::SEG], const f
 // footprint column col (image column tx0 - h + col) over rows
 // 16 half - h .. 16 half + 15 + h of the tile, forming E once per element,
 // and writes the 16 K-row sums of (E y0, E) to sVA and of (E y1, E y2) to
-// sVB at [16 half + r][col].
+// sVB at [16 half + r][col].  sY holds the planes y0, y1, y2.
 template <int K>
-__device__ __forceinline__ void fwd_vpass(const float* __restrict__ sZ, const float* __restrict__ sY0,
-                                          const float2* __restrict__ sY12, float2* __restrict__ sVA,
-                                          float2* __restrict__ sVB, float ml2e, int t) {
+__device__ __forceinline__ void fwd_vpass(const float* __restrict__ sZ, const float* __restrict__ sY,
+                                          float2* __restrict__ sVA, float2* __restrict__ sVB, float ml2e, int t) {
     constexpr int h = K / 2, NCOL = dfv::TW + 2 * h;
+    constexpr int PL = dfv::FH * dfv::FW;
     const int half = t >= NCOL ? 1 : 0;
     const int col = t - half * NCOL;
     const int o = (dfv::HALO + dfv::RV * half - h) * dfv::FW + dfv::XOFF - h + col;
     const int v = dfv::RV * half * dfv::VP + col;
     box_stream<K, dfv::RV, 2>(
         [&](int j, float2(&w)[2]) {
-            const float e = ex2_approx(fmaf(sZ[o + j * dfv::FW], dfv::LOG2E, -ml2e));
-            w[0] = make_float2(e * sY0[o + j * dfv::FW], e);
-            w[1] = __fmul2_rn(make_float2(e, e), sY12[o + j * dfv::FW]);
+            const int q = o + j * dfv::FW;
+            const float e = ex2_approx(fmaf(sZ[q], dfv::LOG2E, -ml2e));
+            w[0] = make_float2(e * sY[q], e);
+            w[1] = __fmul2_rn(make_float2(e, e), make_float2(sY[PL + q], sY[2 * PL + q]));
         },
         [&](int y, const float2(&s)[2]) {
             sVA[v + y * dfv::VP] = s[0];
@@ -543,8 +550,8 @@ __device__ __forceinline__ void stage_albedo(float* __restrict__ sA, const float
 // fusion logits, the next size's are loaded, and the next shift is reduced.
 template <int K, bool VEC>
 __device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZcur, float* __restrict__ sZnext,
-                                             const float* __restrict__ sY0, const float2* __restrict__ sY12,
-                                             float2* __restrict__ sVA, float2* __restrict__ sVB,
+                                             float* __restrict__ sY, float2* __restrict__ sVA,
+                                             float2* __restrict__ sVB,
                                              int* __restrict__ red, int* __restrict__ red_next, HState& st,
                                              const float* __restrict__ znext, const float* __restrict__ zlnext,
                                              const float* __restrict__ a_stage, int H, int W, int tx0, int ty0,
@@ -553,11 +560,11 @@ __device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZcur, fl
     const float ml2e = ord2f(*red) * dfv::LOG2E;
     if (tid == 0) *red_next = INT_MIN;  // its last reader finished before the previous barrier
     if (znext) stage_plane<VEC>(sZnext, znext, H, W, tx0, ty0, tid);
-    if (tid < 2 * NCOL) fwd_vpass<K>(sZcur, sY0, sY12, sVA, sVB, ml2e, tid);
+    if (tid < 2 * NCOL) fwd_vpass<K>(sZcur, sY, sVA, sVB, ml2e, tid);
     __syncthreads();
     // after the last vertical pass the y planes are free: the albedo of the
-    // re-modulation is staged there while the horizontal pass runs
-    if (a_stage) stage_albedo(reinterpret_cast<float*>(const_cast<float2*>(sY12)), a_stage, H, W, tx0, ty0, tid);
+    // re-modulation is staged in the y1, y2 planes while the horizontal pass runs
+    if (a_stage) stage_albedo(sY + dfv::FH * dfv::FW, a_stage, H, W, tx0, ty0, tid);
     const int row = tid & 31, seg = tid >> 5;
     const unsigned exact = fwd_hpass<K>(sVA, sVB, st, row, seg);
     if (zlnext) load_fusion_logits<VEC>(st.l, zlnext, H, W, ty0 + row, tx0 + seg * dfv::SEG);
@@ -571,8 +578,8 @@ template <bool DEMOD, bool VEC>
 __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const __grid_constant__ DecodeArgs args) {
     extern __shared__ float4 dsm4[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(dsm4);
-    float2* sY12 = reinterpret_cast<float2*>(smem + dfv::OFF_Y12);
-    float* sY0 = reinterpret_cast<float*>(smem + dfv::OFF_Y0);
+    float* sY = reinterpret_cast<float*>(smem + dfv::OFF_Y);
+    float* sRst = reinterpret_cast<float*>(smem + dfv::OFF_RSTAGE);
     float* sZ = reinterpret_cast<float*>(smem + dfv::OFF_Z);
     float2* sVA = reinterpret_cast<float2*>(smem + dfv::OFF_V);
     float2* sVB = sVA + dfv::TH * dfv::VP;
@@ -590,13 +597,65 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     const int row = tid & 31, seg = tid >> 5;
     const int gy = ty0 + row, gx0 = tx0 + seg * dfv::SEG;
 
-    // the first importance map's footprint is in flight during the set-up
+    // Set-up, with every DRAM read in flight at once: the first importance
+    // map's footprint into sZ[0]; the radiance and albedo footprints by
+    // cp.async (the radiance into space idle until the first size, the
+    // albedo into the y planes); the fusion logits of the thread's own
+    // pixels into registers.
+    constexpr int PL = dfv::FH * dfv::FW;
     if (tid == 0) red[0] = INT_MIN;
     stage_plane<VEC>(sZ, z, H, W, tx0, ty0, tid);
+    {
+        // chunk (VEC: 4 columns, else 1 element) c of plane ch: image rows and
+        // columns outside the frame are written as 0 (y = 0 there)
+        float* rdst = DEMOD ? sRst : sY;
+        if constexpr (VEC) {
+#pragma unroll
+            for (int u = 0; u < dfv::CPT; ++u) {
+                const int c = tid + u * dfv::THREADS;
+                if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
+                const int cr = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
+                const int yy = ty0 - dfv::HALO + cr, xx = tx0 - dfv::XOFF + 4 * c4;
+                const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+                const size_t g = (size_t)yy * W + xx;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    float* dr = rdst + ch * PL + 4 * c;
+                    float* da = sY + ch * PL + 4 * c;
+                    if (in) {
+                        cp_async16(dr, r + ch * HW + g);
+                        if (DEMOD) cp_async16(da, a + ch * HW + g);
+                    } else {
+                        *reinterpret_cast<float4*>(dr) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (DEMOD) *reinterpret_cast<float4*>(da) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+        } else {
+            for (int e = tid; e < PL; e += dfv::THREADS) {
+                const int er = e / dfv::FW, ec = e % dfv::FW;
+                const int yy = ty0 - dfv::HALO + er, xx = tx0 - dfv::XOFF + ec;
+                const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+                const size_t g = (size_t)yy * W + xx;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    if (in) {
+                        cp_async4(rdst + ch * PL + e, r + ch * HW + g);
+                        if (DEMOD) cp_async4(sY + ch * PL + e, a + ch * HW + g);
+                    } else {
+                        rdst[ch * PL + e] = 0.f;
+                        if (DEMOD) sY[ch * PL + e] = 0.f;
+                    }
+                }
+            }
+        }
+        cp_async_commit();
+    }
     __syncthreads();  // red[0] initialised before any thread folds its maximum in
 
     // Shift of the fusion softmax per own pixel (Eq. 5): c = max_i l_i (all
-    // loads issued at once); the first size's logits stay in st.l.
+    // loads issued at once, while the copies above are in flight); the first
+    // size's logits stay in st.l.
     HState st;
     {
         float l[WSKPN_MAX_KERNELS][dfv::SEG];
@@ -615,58 +674,30 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
         }
     }
 
-    // Demodulated irradiance y = r / (a + eps) on the footprint (0 outside
-    // the image); the loads of two chunks are issued before any is used.
-    if constexpr (VEC) {
+    // Demodulated irradiance y = r / (a + eps), in place of the albedo: each
+    // thread converts exactly the elements it staged, after its own copies
+    // landed (outside the frame r = a = 0, so y = 0).
+    cp_async_wait_all();
+    if constexpr (DEMOD) {
+        if constexpr (VEC) {
 #pragma unroll
-        for (int u0 = 0; u0 < dfv::CPT; u0 += 2) {
-            float4 rv[2][3], av[2][3];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int c = tid + (u0 + q) * dfv::THREADS;
-                const int cr = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
-                const int yy = ty0 - dfv::HALO + cr, xx = tx0 - dfv::XOFF + 4 * c4;
-                const bool in = c < dfv::NCH && yy >= 0 && yy < H && xx >= 0 && xx < W;
-                const size_t g = in ? (size_t)yy * W + xx : 0;
+            for (int u = 0; u < dfv::CPT; ++u) {
+                const int c = tid + u * dfv::THREADS;
+                if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    rv[q][ch] = in ? __ldg(reinterpret_cast<const float4*>(r + ch * HW + g)) : make_float4(0, 0, 0, 0);
-                    av[q][ch] = (DEMOD && in) ? __ldg(reinterpret_cast<const float4*>(a + ch * HW + g))
-                                              : make_float4(0, 0, 0, 0);
+                    const float4 rv = reinterpret_cast<const float4*>(sRst + ch * PL)[c];
+                    float4& yv = reinterpret_cast<float4*>(sY + ch * PL)[c];
+                    const float4 av = yv;
+                    yv = make_float4(__fdividef(rv.x, av.x + eps), __fdividef(rv.y, av.y + eps),
+                                     __fdividef(rv.z, av.z + eps), __fdividef(rv.w, av.w + eps));
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int c = tid + (u0 + q) * dfv::THREADS;
-                if (c >= dfv::NCH) continue;
-                float y[3][4];
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    const float rr[4] = {rv[q][ch].x, rv[q][ch].y, rv[q][ch].z, rv[q][ch].w};
-                    const float aa[4] = {av[q][ch].x, av[q][ch].y, av[q][ch].z, av[q][ch].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) y[ch][e] = DEMOD ? __fdividef(rr[e], aa[e] + eps) : rr[e];
-                }
-                reinterpret_cast<float4*>(sY0)[c] = make_float4(y[0][0], y[0][1], y[0][2], y[0][3]);
-                float4* p12 = reinterpret_cast<float4*>(sY12 + 4 * c);
-                p12[0] = make_float4(y[1][0], y[2][0], y[1][1], y[2][1]);
-                p12[1] = make_float4(y[1][2], y[2][2], y[1][3], y[2][3]);
-            }
-        }
-    } else {
-        for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) {
-            const int er = e / dfv::FW, ec = e % dfv::FW;
-            const int yy = ty0 - dfv::HALO + er, xx = tx0 - dfv::XOFF + ec;
-            float y[3] = {0.f, 0.f, 0.f};
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-                const size_t g = (size_t)yy * W + xx;
+        } else {
+            for (int e = tid; e < PL; e += dfv::THREADS)
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch)
-                    y[ch] = DEMOD ? __fdividef(__ldg(r + ch * HW + g), __ldg(a + ch * HW + g) + eps)
-                                  : __ldg(r + ch * HW + g);
-            }
-            sY0[e] = y[0];
-            sY12[e] = make_float2(y[1], y[2]);
+                    sY[ch * PL + e] = __fdividef(sRst[ch * PL + e], sY[ch * PL + e] + eps);
         }
     }
 
@@ -686,8 +717,7 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
         unsigned ex = 0;
 #define WSKPN_FWD_SIZE(K_)                                                                                      \
     case K_:                                                                                                    \
-        ex = fwd_size<K_, VEC>(zc, zn, sY0, sY12, sVA, sVB, rd, rn, st, znext, zlnext, astage, H, W, tx0, ty0, \
-                               tid);                                                                            \
+        ex = fwd_size<K_, VEC>(zc, zn, sY, sVA, sVB, rd, rn, st, znext, zlnext, astage, H, W, tx0, ty0, tid); \
         break;
         switch (args.ks[i]) {
             WSKPN_FWD_SIZE(1) WSKPN_FWD_SIZE(3) WSKPN_FWD_SIZE(5) WSKPN_FWD_SIZE(7) WSKPN_FWD_SIZE(9)
@@ -736,8 +766,8 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
         for (int x = 0; x < dfv::SEG; ++x) o[x] = st.acc[x][ch] * inv[x];
         if (VEC && gx0 + dfv::SEG <= W) {
             if constexpr (DEMOD) {
-                const float4* pa = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(sY12) +
-                                                                   (ch * dfv::TH + row) * dfv::LP + seg * dfv::SEG);
+                const float4* pa = reinterpret_cast<const float4*>(sY + PL + (ch * dfv::TH + row) * dfv::LP +
+                                                                   seg * dfv::SEG);
                 const float4 u = pa[0], v = pa[1];
                 const float m[dfv::SEG] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
 #pragma unroll
