@@ -89,6 +89,12 @@ struct TcArgs {
     unsigned int* status;
     uint64_t wait_ns;        // limit of every wait but the drains
     int probe;               // test hook: the epilogue first waits on a barrier nothing signals
+    // GM kernels (input gradients of the training step): the ReLU derivative
+    // of the layer input, NHWC BF16 hi/lo laid out like out (x = hi + lo > 0
+    // keeps a gradient value), and per-warp bias-gradient sums
+    // bias_part [gridDim.x * 4][64] of the masked values
+    const void* gmask;
+    float* bias_part;
 };
 
 // ------------------------------------------------------------- primitives
@@ -328,7 +334,7 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
 }
 
 // ----------------------------------------------------------------- kernel
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF, bool GM>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr int PAD = KS / 2;
@@ -336,6 +342,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     constexpr int NCB = XF ? KS * COUT_P : COUT_P;        // TMEM columns of one output row's accumulators
     constexpr int TPX = XF ? tc::BM - (KS - 1) : tc::BM;  // output pixels per tile row
     static_assert(!XF || COUT_P == 16, "folded taps: 16 output channels");
+    static_assert(!GM || (!XF && !FP8 && COUT_P <= 64), "gradient mask: BF16 hi/lo, at most 64 channels");
     constexpr uint32_t NCOL = tmem_cols<NCB, R>();
     constexpr int ROWS_IN = R + KS - 1;
     constexpr int CPB = chunks_per_box(NCC_IN);
@@ -512,6 +519,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int p = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         int lt = 0, rowc = 0;
+        // GM: this thread's sums of its masked gradient values per channel,
+        // over its pixels in tile and row order
+        float bsum[GM ? COUT_P : 1];
+#pragma unroll
+        for (int c = 0; c < (GM ? COUT_P : 1); ++c) bsum[c] = 0.f;
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
             const int buf = lt & 1;
             int ok = 1;
@@ -606,6 +618,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const size_t pix = ((size_t)b * a.H + y) * a.W + x;
                 // this group's first channel of the pixel (hi half for BF16)
                 uint8_t* const pbase = static_cast<uint8_t*>(a.out) + pix * pix_bytes + (size_t)a.out_c0 * (FP8 ? 1 : 2);
+                // GM: hi halves of the layer input at this pixel, loaded before
+                // the accumulators are read.  The layer input is a ReLU output
+                // (x >= 0) stored as hi + lo with hi = bf16(x), so x > 0 exactly
+                // when hi is positive: bits in [0x0001, 0x7F80]
+                uint4 mk[GM ? COUT_P / 8 : 1];
+                if constexpr (GM) {
+                    const uint4* mh = reinterpret_cast<const uint4*>(
+                        static_cast<const uint8_t*>(a.gmask) + pix * pix_bytes + (size_t)a.out_c0 * 2);
+#pragma unroll
+                    for (int k = 0; k < COUT_P / 8; ++k) mk[k] = valid ? mh[k] : make_uint4(0u, 0u, 0u, 0u);
+                }
 #pragma unroll
                 for (int c16 = 0; c16 < COUT_P / 16; ++c16) {
                     float v[16];
@@ -633,6 +656,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         if (a.relu)
 #pragma unroll
                             for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+                    }
+                    if constexpr (GM) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const uint32_t m = j & 1 ? (j & 2 ? mk[2 * c16 + j / 4].w : mk[2 * c16 + j / 4].y)
+                                                     : (j & 2 ? mk[2 * c16 + j / 4].z : mk[2 * c16 + j / 4].x);
+                            if ((m & 0xFFFFu) - 1u >= 0x7F80u) v[2 * j] = 0.f;
+                            if ((m >> 16) - 1u >= 0x7F80u) v[2 * j + 1] = 0.f;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) bsum[c16 * 16 + j] += v[j];
                     }
                     if (a.last) {
                         const size_t HW = (size_t)a.H * a.W;
@@ -686,6 +720,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
+        }
+        if constexpr (GM) {
+            // the warp's per-channel sums (a fixed butterfly over its lanes);
+            // lane c % 32 stores channel c
+            __syncwarp();
+            float* const dst = a.bias_part + ((size_t)blockIdx.x * 4 + q) * 64 + a.out_c0;
+#pragma unroll
+            for (int c = 0; c < COUT_P; ++c) {
+                float s = bsum[c];
+#pragma unroll
+                for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+                if (lane == (c & 31)) dst[c] = s;
+            }
         }
     }
     __syncthreads();
@@ -890,11 +937,11 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     return WSKPN_OK;
 }
 
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF, bool GM = false>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
     auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, XF ? xf_rows_per_tile(KS) : tc::rows_per_tile(COUT_P),
-                               WM, XF>;
+                               WM, XF, GM>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     // programmatic dependent launch: set-up overlaps the previous kernel's
     // tail; the TMA producer waits for that kernel before reading activations
@@ -917,22 +964,25 @@ using TcLaunch = wskpn_status (*)(const CUtensorMap&, const TcArgs&, size_t, int
 // The kernel instantiation for a layer shape: KS, output channels of one
 // group, input chunks per row (hi/lo included), weight-image chunks,
 // precision, e4m3 weight mode, folded taps.  nullptr when none is built.
-static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8, int wm, bool xf) {
+static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8, int wm, bool xf, bool gm = false) {
     TcLaunch launch = nullptr;
 #define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
-    if (!launch && !xf && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
+    if (!launch && !xf && !gm && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
         launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_, false>;
+#define WSKPN_TC_GM(ks_, n_, nin_, nw_)                                                                    \
+    if (!launch && gm && !xf && !fp8 && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_)             \
+        launch = launch_tc_t<ks_, n_, nin_, nw_, false, 0, false, true>;
     // the BF16 last layer 64 -> 16 with folded horizontal taps
     // (hi/lo activations, or single BF16 values when the split is tuned off)
-    if (xf && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
-    if (xf && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
-    if (xf && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
-    if (xf && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
+    if (xf && !gm && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
+    if (xf && !gm && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
+    if (xf && !gm && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
+    if (xf && !gm && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
     // e4m3 hi/lo (three products per chunk) and single-term
-    if (xf && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
-    if (xf && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
-    if (xf && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
-    if (xf && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
+    if (xf && !gm && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
+    if (xf && !gm && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
+    if (xf && !gm && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
+    if (xf && !gm && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
 #define WSKPN_TC_BF16(ks_)                                                                                 \
     WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
     WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
@@ -949,11 +999,10 @@ static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8
     WSKPN_TC_CASE(ks_, 64, 4, 3, true, 2) WSKPN_TC_CASE(ks_, 16, 4, 4, true, 1)                            \
     WSKPN_TC_CASE(ks_, 32, 4, 4, true, 1) WSKPN_TC_CASE(ks_, 64, 4, 4, true, 1)
 // input gradients of the training step (hi/lo gradients, weights transposed
-// and flipped): 12 -> 64, 64 -> 48, 48 -> 32 (64 -> 64 runs as two 32-channel
-// groups, a forward case above)
+// and flipped, the ReLU mask and bias sums in the epilogue): 12 -> 64,
+// 64 -> 48, 48 -> 32, and 64 -> 64 as two 32-channel groups
 #define WSKPN_TC_DGRAD(ks_)                                                                                \
-    WSKPN_TC_CASE(ks_, 64, 2, 1, false, 0) WSKPN_TC_CASE(ks_, 48, 8, 4, false, 0)                          \
-    WSKPN_TC_CASE(ks_, 32, 6, 3, false, 0)
+    WSKPN_TC_GM(ks_, 64, 2, 1) WSKPN_TC_GM(ks_, 48, 8, 4) WSKPN_TC_GM(ks_, 32, 6, 3) WSKPN_TC_GM(ks_, 32, 8, 4)
 // the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
 // 112-48, 80-32 and the heads 48-5, 32-5
 #define WSKPN_TC_UNET                                                                                      \
@@ -964,6 +1013,7 @@ static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8
     WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3) WSKPN_TC_UNET
     WSKPN_TC_DGRAD(5) WSKPN_TC_DGRAD(3)
 #undef WSKPN_TC_DGRAD
+#undef WSKPN_TC_GM
 #undef WSKPN_TC_UNET
 #undef WSKPN_TC_FP8
 #undef WSKPN_TC_BF16
@@ -989,6 +1039,9 @@ struct TcRun {
     int device;
     uint64_t wait_ns = MBAR_WAIT_NS;
     int probe = 0;
+    const void* gmask = nullptr;  // input gradient: ReLU mask and bias sums in the epilogue (TcArgs)
+    float* bias_part = nullptr;
+    int* grid_out = nullptr;      // receives the grid size (bias_part holds 4 rows per CTA)
 };
 
 static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int H, int W, cudaStream_t st,
@@ -1058,10 +1111,18 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     a.status = r.status;
     a.wait_ns = r.wait_ns;
     a.probe = r.probe;
+    a.gmask = r.gmask;
+    a.bias_part = r.bias_part;
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, r.device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
-    const TcLaunch launch = select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf);
+    if (r.grid_out) *r.grid_out = grid;
+    const bool gm = r.gmask != nullptr;
+    if (gm && (fp8 || xf || !r.split_out || r.last || r.relu || !r.bias_part)) {
+        err = "conv_tc: the gradient mask needs a BF16 hi/lo input-gradient layer";
+        return WSKPN_EINVAL;
+    }
+    const TcLaunch launch = select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf, gm);
     if (!launch) {
         err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M, "
               "64-64 and the multi-resolution U-Net are built";
@@ -1171,7 +1232,7 @@ wskpn_status tc_dgrad_layer_alloc(Layer& Lt, int KS, int cin, int cout, std::str
     const wskpn_status s = tc_layer_alloc(Lt, KS, false, false, err);
     if (s) return s;
     const int ncc = Lt.cin_p / 16;
-    if (!select_tc_kernel(KS, Lt.cout_p / Lt.groups, 2 * ncc, ncc, false, 0, false)) {
+    if (!select_tc_kernel(KS, Lt.cout_p / Lt.groups, 2 * ncc, ncc, false, 0, false, true)) {
         err = "tensor-core input gradient: no kernel for this layer shape";
         return WSKPN_EUNSUPPORTED;
     }
@@ -1216,6 +1277,30 @@ wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int
     r.status = status;
     r.device = device;
     return tc_run(r, in, out, B, H, W, st, err);
+}
+
+wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, const void* x, float* bias_part,
+                          int* nparts, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
+                          std::string& err) {
+    TcRun r{};
+    r.L = &Lt;
+    r.KS = KS;
+    r.fp8 = false;
+    r.split_in = r.split_out = 1;
+    r.last = 0;
+    r.relu = 0;
+    r.out_cp = Lt.cout_p;
+    r.out_c0 = 0;
+    r.out_qscale = 1.f;
+    r.status = status;
+    r.device = device;
+    r.gmask = x;
+    r.bias_part = bias_part;
+    int grid = 0;
+    r.grid_out = &grid;
+    const wskpn_status s = tc_run(r, g, gx, B, H, W, st, err);
+    *nparts = 4 * grid;
+    return s;
 }
 
 wskpn_status launch_prep(const wskpn_frame* frames, int B, int H, int W, float gamma, float dnear, float dfar,

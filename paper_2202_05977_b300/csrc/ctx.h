@@ -112,6 +112,13 @@ wskpn_status tc_dgrad_layer_pack(Layer& Lt, int KS, const float* w, float* wt, c
 wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int out_cp, int out_c0, int last,
                           int relu, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
                           std::string& err);
+// The input gradient gx (NHWC hi/lo, Lt.cout_p channels) of a layer from its
+// output gradient g through Lt, times the ReLU derivative of the layer input
+// x (NHWC hi/lo like gx), with per-warp bias sums of the result in
+// bias_part [*nparts][64] (channels of gx).
+wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, const void* x, float* bias_part,
+                          int* nparts, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
+                          std::string& err);
 }  // namespace wskpn
 
 // Temporal accumulation history of one stream (temporal.cu): planes

@@ -174,9 +174,11 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
             WSKPN_TRY_ALLOC(t->gpack, gcp * 2 * sizeof(uint16_t) * t->px);
             WSKPN_TRY_ALLOC(t->gpack2, gcp * 2 * sizeof(uint16_t) * t->px);
             WSKPN_TRY_ALLOC(t->wg_part, t->wg_part_floats * sizeof(float));
-            // tiles of GP_TILE pixels per frame, for every frame of a call
+            // rows of bias sums: tiles of GP_TILE pixels per frame for every
+            // frame of a call (gradient packing), 4 per CTA of an
+            // input-gradient convolution (at most one CTA per SM)
             const size_t tiles = (size_t)c.max_batch * (((size_t)c.max_h * c.max_w + GP_TILE - 1) / GP_TILE);
-            WSKPN_TRY_ALLOC(t->bias_part, tiles * 64 * sizeof(float));
+            WSKPN_TRY_ALLOC(t->bias_part, std::max(tiles, (size_t)4 * nsm) * 64 * sizeof(float));
         }
     }
     return WSKPN_OK;
@@ -256,69 +258,6 @@ __global__ void __launch_bounds__(256) grad_pack_kernel(PtrBatch<const float*> g
     }
 }
 
-// The input gradient of a layer, written by its tensor-core convolution as
-// NHWC BF16 hi/lo pairs g [B][HW][hi(cp) | lo(cp)], times the ReLU derivative
-// of the layer input (mask, NHWC hi/lo with the same cp: x = hi + lo > 0),
-// in place; channels C .. cp - 1 are set to zero.  One block per 64 pixels
-// of one frame; threads walk (pixel, 8-channel chunk) pairs, so every load
-// and store is a whole 16-byte piece of consecutive runs.  bias_part
-// [tiles][64] receives each tile's per-channel sum of the masked gradient
-// (pixels in a fixed order).
-__global__ void __launch_bounds__(256) grad_mask_nhwc_kernel(uint4* __restrict__ g, const uint4* __restrict__ mask,
-                                                             int C, int cp, size_t HW, float* __restrict__ bias_part) {
-    __shared__ float sg[64][GP_TILE + 1];
-    const int b = blockIdx.y, tid = threadIdx.x;
-    const size_t p0 = (size_t)blockIdx.x * GP_TILE;
-    const int nq = cp / 8;
-#pragma unroll
-    for (int u = 0; u < 8 * GP_TILE / 256; ++u) {
-        const int k = tid + 256 * u;
-        if (k >= GP_TILE * nq) break;
-        const int i = k / nq, q = k % nq;
-        const size_t p = p0 + i;
-        float v[8];
-        if (p < HW) {
-            const size_t px = ((size_t)b * HW + p) * (size_t)(cp / 4);  // 2 cp BF16 = cp / 4 uint4
-            uint4 gh = g[px + q], gl = g[px + cp / 8 + q];
-            const uint4 mh = mask[px + q], ml = mask[px + cp / 8 + q];
-            float fgh[8], fgl[8], fmh[8], fml[8];
-            bf16x8_to_float(gh, fgh);
-            bf16x8_to_float(gl, fgl);
-            bf16x8_to_float(mh, fmh);
-            bf16x8_to_float(ml, fml);
-            __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&gh);
-            __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&gl);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const bool keep = q * 8 + j < C && fmh[j] + fml[j] > 0.f;
-                v[j] = keep ? fgh[j] + fgl[j] : 0.f;
-                if (!keep) {
-                    hh[j] = __float2bfloat16_rn(0.f);
-                    ll[j] = __float2bfloat16_rn(0.f);
-                }
-            }
-            g[px + q] = gh;
-            g[px + cp / 8 + q] = gl;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) sg[q * 8 + j][i] = v[j];
-    }
-    __syncthreads();
-    {
-        const int c = tid / 4, part = tid % 4;
-        float s = 0.f;
-        if (c < cp)
-#pragma unroll
-            for (int i = 0; i < GP_TILE / 4; ++i) s += sg[c][part * (GP_TILE / 4) + i];
-        s += __shfl_down_sync(0xffffffffu, s, 1);
-        s += __shfl_down_sync(0xffffffffu, s, 2);
-        if (part == 0 && c < C) bias_part[((size_t)b * gridDim.x + blockIdx.x) * 64 + c] = s;
-    }
-}
-
 // db[o] = sum over the tiles (fixed order: thread t adds tiles t, t + 256,
 // ..., then a fixed tree) of bias_part[tile][o]; one block per channel.
 __global__ void bias_from_tiles_kernel(const float* __restrict__ part, int ntiles, float* __restrict__ db) {
@@ -335,20 +274,6 @@ __global__ void bias_from_tiles_kernel(const float* __restrict__ part, int ntile
     if (threadIdx.x == 0) db[o] = red[0];
 }
 
-static wskpn_status launch_grad_mask_nhwc(void* g, const void* mask, int B, int C, int cp, size_t HW,
-                                          float* bias_part, float* db, cudaStream_t st, std::string& err) {
-    if (C > 64 || cp > 64 || cp % 16 || B > WSKPN_MAX_BATCH) {
-        err = "gradient mask: at most 64 channels and 16 frames";
-        return WSKPN_EUNSUPPORTED;
-    }
-    const unsigned tiles = (unsigned)((HW + GP_TILE - 1) / GP_TILE);
-    grad_mask_nhwc_kernel<<<dim3(tiles, B), 256, 0, st>>>(static_cast<uint4*>(g), static_cast<const uint4*>(mask), C,
-                                                          cp, HW, bias_part);
-    WSKPN_CUDA_TRY(cudaGetLastError(), err);
-    bias_from_tiles_kernel<<<C, 256, 0, st>>>(bias_part, (int)tiles * B, db);
-    WSKPN_CUDA_TRY(cudaGetLastError(), err);
-    return WSKPN_OK;
-}
 
 // Packs the gradient of a layer with C output channels (planar FP32) as
 // NHWC BF16 hi/lo pairs with cp channels, then writes its bias gradient db.
@@ -604,15 +529,16 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
                                 t->wg_part_floats, dweights + Ly.woff, ctx->d_status, ctx->device, st, ctx->err);
             if (s) return s;
             if (l == 0) break;
-            // input gradient straight to NHWC hi/lo, then the ReLU mask of x_l in place
+            // input gradient straight to NHWC hi/lo, times the ReLU mask of
+            // x_l, with the bias sums of layer l - 1, in the conv's epilogue
             void* gnext = gcur == t->gpack ? t->gpack2 : t->gpack;
             Layer& Lt = t->lt[l];
-            s = tc_layer_run(Lt, KS, gcur, gnext, Lt.cout_p, 0, 0, 0, batch, h, w, ctx->d_status, ctx->device, st,
-                             ctx->err);
+            int nparts = 0;
+            s = tc_dgrad_run(Lt, KS, gcur, gnext, xn(l), t->bias_part, &nparts, batch, h, w, ctx->d_status,
+                             ctx->device, st, ctx->err);
             if (s) return s;
-            s = launch_grad_mask_nhwc(gnext, xn(l), batch, Ly.cin, xcp, HW, t->bias_part,
-                                      dweights + ctx->layers[l - 1].boff, st, ctx->err);
-            if (s) return s;
+            bias_from_tiles_kernel<<<Ly.cin, 256, 0, st>>>(t->bias_part, nparts, dweights + ctx->layers[l - 1].boff);
+            WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
             gcur = gnext;
             continue;
         }
