@@ -7,7 +7,7 @@
 //   R_i(p) = sum_q exp(I_i(q)) y(q) / sum_q exp(I_i(q)),  y = r / (a + eps)
 // i.e. Eq. 3-4 written as the ratio of two window sums N_i / D_i.  The sums
 // are separable box sums, evaluated from a shared-memory tile with a 6-pixel
-// halo.  The exponent is shifted by the maximum of I_i over the tile's
+// halo (64 x 32 output pixels per tile).  The exponent is shifted by the maximum of I_i over the tile's
 // window footprint; the shift cancels in N/D for every pixel.  A pixel whose
 // D_i falls below 1e-30 (the footprint's logit range exceeds ~69) is
 // recomputed exactly with its own window maximum and counted.
@@ -16,18 +16,7 @@
 namespace wskpn {
 
 namespace df {
-constexpr int TW = 64;              // tile width (output pixels)
-constexpr int TH = 16;              // tile height
-constexpr int HALO = 6;             // largest half window (k = 13)
-constexpr int RW = TW + 2 * HALO;   // 76
-constexpr int RH = TH + 2 * HALO;   // 28
-constexpr int RP = RW + 1;          // odd row pitch: column-walking lanes hit distinct banks
-constexpr int HP = TW + 1;          // pitch of the horizontal-sum rows
-constexpr int THREADS = 256;
-constexpr int PPT = TW * TH / THREADS;  // output pixels per thread (4)
-constexpr int SMEM_FLOATS = 3 * RH * RP + 4 * RH * RP + 4 * RH * HP;
-constexpr size_t SMEM_BYTES = SMEM_FLOATS * sizeof(float);
-constexpr float DMIN = 1e-30f;
+constexpr float DMIN = 1e-30f;  // smallest window sum D_i the fast paths divide by
 }  // namespace df
 
 struct DecodeArgs {
@@ -38,90 +27,6 @@ struct DecodeArgs {
     float eps;
     unsigned int* fallbacks;
 };
-
-// s[x] = sum_{d < K} w[x + d], x < NOUT (K <= 15): sums of 2, 4 and 8
-// consecutive inputs are formed once and each window is assembled from the
-// binary digits of K (all terms of one sign, so no cancellation); values no
-// output needs are never computed (the arrays are fully unrolled).
-template <int K, int NOUT>
-__device__ __forceinline__ void box_sum1(const float (&w)[NOUT + K - 1], float (&s)[NOUT]) {
-    constexpr int N1 = NOUT + K - 1;
-    constexpr int B8 = K & 8, B4 = K & 4, B2 = K & 2, B1 = K & 1;
-    constexpr int O4 = B8, O2 = B8 + B4, O1 = B8 + B4 + B2;
-    static_assert(K >= 1 && K <= 15, "window");
-    float p2[N1 > 1 ? N1 - 1 : 1], p4[N1 > 3 ? N1 - 3 : 1], p8[N1 > 7 ? N1 - 7 : 1];
-#pragma unroll
-    for (int j = 0; j + 1 < N1; ++j) p2[j] = w[j] + w[j + 1];
-#pragma unroll
-    for (int j = 0; j + 3 < N1; ++j) p4[j] = p2[j] + p2[j + 2];
-#pragma unroll
-    for (int j = 0; j + 7 < N1; ++j) p8[j] = p4[j] + p4[j + 4];
-#pragma unroll
-    for (int x = 0; x < NOUT; ++x) {
-        float t = 0.f;
-        if constexpr (B8 != 0) t = p8[x];
-        if constexpr (B4 != 0) {
-            if constexpr (O4 != 0) t += p4[x + O4];
-            else t = p4[x];
-        }
-        if constexpr (B2 != 0) {
-            if constexpr (O2 != 0) t += p2[x + O2];
-            else t = p2[x];
-        }
-        if constexpr (B1 != 0) {
-            if constexpr (O1 != 0) t += w[x + O1];
-            else t = w[x];
-        }
-        s[x] = t;
-    }
-}
-
-// Horizontal window sums of the 4 planes (E, E*y0, E*y1, E*y2) for the rows
-// the vertical pass needs.  One thread walks one (plane, row, 16-pixel
-// segment) and keeps the 16 + K - 1 inputs in registers.
-template <int K>
-__device__ __forceinline__ void hpass(const float* __restrict__ sE, float* __restrict__ sH, int tid) {
-    constexpr int h = K / 2;
-    constexpr int NR = df::TH + 2 * h;
-    constexpr int SEG = 16;                 // outputs per item
-    constexpr int NSEG = df::TW / SEG;      // 4
-    for (int it = tid; it < 4 * NSEG * NR; it += df::THREADS) {
-        const int row = it % NR;
-        const int seg = (it / NR) % NSEG;
-        const int ch = it / (NSEG * NR);
-        const int ry = df::HALO - h + row;
-        const float* src = sE + (ch * df::RH + ry) * df::RP + (df::HALO - h) + seg * SEG;
-        float* dst = sH + (ch * df::RH + ry) * df::HP + seg * SEG;
-        float win[SEG + K - 1], out[SEG];
-#pragma unroll
-        for (int j = 0; j < SEG + K - 1; ++j) win[j] = src[j];
-        box_sum1<K, SEG>(win, out);
-#pragma unroll
-        for (int x = 0; x < SEG; ++x) dst[x] = out[x];
-    }
-}
-
-// Vertical window sums of the horizontal sums -> sV[4][TH][TW].
-template <int K>
-__device__ __forceinline__ void vpass(const float* __restrict__ sH, float* __restrict__ sV, int tid) {
-    constexpr int h = K / 2;
-    const int x = tid % df::TW;
-    const int ch = tid / df::TW;  // THREADS == 4 * TW
-    const float* src = sH + (ch * df::RH + (df::HALO - h)) * df::HP + x;
-    float col[df::TH + K - 1], out[df::TH];
-#pragma unroll
-    for (int j = 0; j < df::TH + K - 1; ++j) col[j] = src[j * df::HP];
-    box_sum1<K, df::TH>(col, out);
-#pragma unroll
-    for (int y = 0; y < df::TH; ++y) sV[(ch * df::TH + y) * df::TW + x] = out[y];
-}
-
-template <int K>
-__device__ __forceinline__ void box_sums(const float* sE, float* sH, float* sV, int tid) {
-    hpass<K>(sE, sH, tid);
-    __syncthreads();
-    vpass<K>(sH, sV, tid);
-}
 
 // Exact per-window evaluation of Eq. 3-4 for one pixel (slow path).
 __device__ __forceinline__ void window_exact_inl(const float* __restrict__ z, const float* __restrict__ r,
@@ -147,99 +52,6 @@ __device__ __forceinline__ void window_exact_inl(const float* __restrict__ z, co
     R[0] = N0 / D;
     R[1] = N1 / D;
     R[2] = N2 / D;
-}
-
-__device__ __noinline__ void window_exact(const float* __restrict__ z, const float* __restrict__ r,
-                                          const float* __restrict__ a, int H, int W, int k, float eps, int px, int py,
-                                          float R[3]) {
-    window_exact_inl(z, r, a, H, W, k, eps, px, py, R);
-}
-
-// Every load of a thread is issued before any is used (one memory latency
-// per phase instead of one per loop iteration).
-constexpr int REGION_PER_THREAD = (df::RH * df::RW + df::THREADS - 1) / df::THREADS;  // 9
-
-__device__ __forceinline__ void load_irradiance(float* __restrict__ sY, const float* __restrict__ r,
-                                                const float* __restrict__ a, int H, int W, int tx0, int ty0,
-                                                float eps, int tid) {
-    const size_t HW = (size_t)H * W;
-    float rv[REGION_PER_THREAD][3], av[REGION_PER_THREAD][3];
-#pragma unroll
-    for (int j = 0; j < REGION_PER_THREAD; ++j) {
-        const int i = tid + j * df::THREADS;
-        const int ry = i / df::RW, rx = i % df::RW;
-        const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
-        const bool in = i < df::RH * df::RW && gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const size_t g = in ? (size_t)gy * W + gx : 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            rv[j][c] = in ? __ldg(r + c * HW + g) : 0.f;
-            av[j][c] = in ? __ldg(a + c * HW + g) : 0.f;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < REGION_PER_THREAD; ++j) {
-        const int i = tid + j * df::THREADS;
-        if (i >= df::RH * df::RW) continue;
-        const int ry = i / df::RW, rx = i % df::RW;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) sY[(c * df::RH + ry) * df::RP + rx] = rv[j][c] / (av[j][c] + eps);
-    }
-}
-
-// For one window size K (compile-time, so all index arithmetic divides by
-// constants): load I_i on the footprint of the tile's windows, shift by its
-// maximum m, form E = exp(I - m) and E*y in smem (E = 0 outside the image)
-// and take the K x K window sums into sV.  Returns m.
-template <int K>
-__device__ __noinline__ float size_sums(float* __restrict__ sE, float* __restrict__ sH, float* __restrict__ sV,
-                                           const float* __restrict__ sY, float* __restrict__ red,
-                                           const float* __restrict__ zi, int H, int W, int tx0, int ty0, int tid) {
-    constexpr int h = K / 2, NR = df::TH + 2 * h, NC = df::TW + 2 * h, NT = NR * NC;
-    constexpr int PER = (NT + df::THREADS - 1) / df::THREADS;
-    float v[PER];
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int t = tid + j * df::THREADS;
-        const int gy = ty0 - h + t / NC, gx = tx0 - h + t % NC;
-        const bool in = t < NT && gy >= 0 && gy < H && gx >= 0 && gx < W;
-        v[j] = in ? __ldg(zi + (size_t)gy * W + gx) : -INFINITY;
-    }
-    float m = -INFINITY;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) m = fmaxf(m, v[j]);
-    m = warp_max(m);
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    m = red[0];
-#pragma unroll
-    for (int w = 1; w < df::THREADS / 32; ++w) m = fmaxf(m, red[w]);
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int t = tid + j * df::THREADS;
-        if (PER * df::THREADS > NT && t >= NT) continue;
-        const int o = (df::HALO - h + t / NC) * df::RP + (df::HALO - h + t % NC);
-        const float e = expf(v[j] - m);
-        sE[o] = e;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) sE[(1 + c) * df::RH * df::RP + o] = e * sY[c * df::RH * df::RP + o];
-    }
-    __syncthreads();
-    box_sums<K>(sE, sH, sV, tid);
-    return m;
-}
-
-__device__ __forceinline__ float size_sums_k(int k, float* sE, float* sH, float* sV, const float* sY, float* red,
-                                             const float* zi, int H, int W, int tx0, int ty0, int tid) {
-    switch (k) {
-        case 1: return size_sums<1>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        case 3: return size_sums<3>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        case 5: return size_sums<5>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        case 7: return size_sums<7>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        case 9: return size_sums<9>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        case 11: return size_sums<11>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        default: return size_sums<13>(sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-    }
 }
 
 // ---------------------------------------------------------------- forward
@@ -386,12 +198,12 @@ __device__ __forceinline__ void box_stream(In in, Out out) {
     }
 }
 
-// Stage one logit plane's footprint block [FH][FW] into sZ (cp.async;
-// -inf outside the image) and return the maximum of what this thread
-// staged once its copies have landed (call finish_stage for that).
+// Stage one plane's footprint block [FH][FW] into sZ (cp.async; `fill`
+// outside the image, -inf for logits); finish_stage (or, in the backward,
+// finish_minmax) waits for the copies and reduces what landed.
 template <bool VEC>
 __device__ __forceinline__ void stage_plane(float* __restrict__ sZ, const float* __restrict__ zi, int H, int W,
-                                            int tx0, int ty0, int tid) {
+                                            int tx0, int ty0, int tid, float fill) {
     if constexpr (VEC) {
 #pragma unroll
         for (int u = 0; u < dfv::CPT; ++u) {
@@ -403,7 +215,7 @@ __device__ __forceinline__ void stage_plane(float* __restrict__ sZ, const float*
             if (gy >= 0 && gy < H && gx >= 0 && gx < W)  // W % 4 == 0: a chunk is wholly in or out
                 cp_async16(dst, zi + (size_t)gy * W + gx);
             else
-                *reinterpret_cast<float4*>(dst) = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+                *reinterpret_cast<float4*>(dst) = make_float4(fill, fill, fill, fill);
         }
     } else {
         for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) {
@@ -412,7 +224,7 @@ __device__ __forceinline__ void stage_plane(float* __restrict__ sZ, const float*
             if (gy >= 0 && gy < H && gx >= 0 && gx < W)
                 cp_async4(sZ + e, zi + (size_t)gy * W + gx);
             else
-                sZ[e] = -INFINITY;
+                sZ[e] = fill;
         }
     }
     cp_async_commit();
@@ -439,10 +251,11 @@ __device__ __forceinline__ void finish_stage(const float* __restrict__ sZ, int* 
     if ((tid & 31) == 0) atomicMax(red, w);
 }
 
-// The fusion logits of one row's 8 consecutive pixels (0 outside the image).
+// 8 consecutive pixels of one row of a plane (0 outside the image): the
+// fusion logits of a horizontal-pass task, its radiance, albedo, ...
 template <bool VEC>
-__device__ __forceinline__ void load_fusion_logits(float (&l)[dfv::SEG], const float* __restrict__ zl, int H, int W,
-                                                   int gy, int gx0) {
+__device__ __forceinline__ void load_row8(float (&l)[dfv::SEG], const float* __restrict__ zl, int H, int W, int gy,
+                                          int gx0) {
     if (VEC && gy < H && gx0 + dfv::SEG <= W) {
         const float4* p = reinterpret_cast<const float4*>(zl + (size_t)gy * W + gx0);
         const float4 u = __ldg(p), v = __ldg(p + 1);
@@ -478,6 +291,89 @@ __device__ __forceinline__ void fwd_vpass(const float* __restrict__ sZ, const fl
             sVA[v + y * dfv::VP] = s[0];
             sVB[v + y * dfv::VP] = s[1];
         });
+}
+
+// Radiance and albedo of the footprint block [3][FH][FW] by cp.async: the
+// radiance into sR, the albedo into sY (DEMOD; without an albedo the
+// radiance goes straight into sY as the irradiance).  Chunks (VEC: 4
+// columns, else 1 element) outside the frame are written as 0, so y = 0
+// there.
+template <bool DEMOD, bool VEC>
+__device__ __forceinline__ void stage_irradiance(float* __restrict__ sY, float* __restrict__ sR,
+                                                 const float* __restrict__ r, const float* __restrict__ a, int H,
+                                                 int W, int tx0, int ty0, int tid) {
+    constexpr int PL = dfv::FH * dfv::FW;
+    const size_t HW = (size_t)H * W;
+    float* rdst = DEMOD ? sR : sY;
+    if constexpr (VEC) {
+#pragma unroll
+        for (int u = 0; u < dfv::CPT; ++u) {
+            const int c = tid + u * dfv::THREADS;
+            if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
+            const int cr = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
+            const int yy = ty0 - dfv::HALO + cr, xx = tx0 - dfv::XOFF + 4 * c4;
+            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t g = (size_t)yy * W + xx;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float* dr = rdst + ch * PL + 4 * c;
+                float* da = sY + ch * PL + 4 * c;
+                if (in) {
+                    cp_async16(dr, r + ch * HW + g);
+                    if (DEMOD) cp_async16(da, a + ch * HW + g);
+                } else {
+                    *reinterpret_cast<float4*>(dr) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (DEMOD) *reinterpret_cast<float4*>(da) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+    } else {
+        for (int e = tid; e < PL; e += dfv::THREADS) {
+            const int er = e / dfv::FW, ec = e % dfv::FW;
+            const int yy = ty0 - dfv::HALO + er, xx = tx0 - dfv::XOFF + ec;
+            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t g = (size_t)yy * W + xx;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                if (in) {
+                    cp_async4(rdst + ch * PL + e, r + ch * HW + g);
+                    if (DEMOD) cp_async4(sY + ch * PL + e, a + ch * HW + g);
+                } else {
+                    rdst[ch * PL + e] = 0.f;
+                    if (DEMOD) sY[ch * PL + e] = 0.f;
+                }
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+// Demodulated irradiance y = r / (a + eps) in place of the staged albedo:
+// each thread converts exactly the elements it staged, once its own copies
+// have landed (outside the frame r = a = 0, so y = 0).
+template <bool VEC>
+__device__ __forceinline__ void form_irradiance(float* __restrict__ sY, const float* __restrict__ sR, float eps,
+                                                int tid) {
+    constexpr int PL = dfv::FH * dfv::FW;
+    if constexpr (VEC) {
+#pragma unroll
+        for (int u = 0; u < dfv::CPT; ++u) {
+            const int c = tid + u * dfv::THREADS;
+            if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float4 rv = reinterpret_cast<const float4*>(sR + ch * PL)[c];
+                float4& yv = reinterpret_cast<float4*>(sY + ch * PL)[c];
+                const float4 av = yv;
+                yv = make_float4(__fdividef(rv.x, av.x + eps), __fdividef(rv.y, av.y + eps),
+                                 __fdividef(rv.z, av.z + eps), __fdividef(rv.w, av.w + eps));
+            }
+        }
+    } else {
+        for (int e = tid; e < PL; e += dfv::THREADS)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) sY[ch * PL + e] = __fdividef(sR[ch * PL + e], sY[ch * PL + e] + eps);
+    }
 }
 
 // Per-thread state of the horizontal-pass task (row, 8 pixels) across the
@@ -559,7 +455,7 @@ __device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZcur, fl
     constexpr int NCOL = dfv::TW + 2 * (K / 2);
     const float ml2e = ord2f(*red) * dfv::LOG2E;
     if (tid == 0) *red_next = INT_MIN;  // its last reader finished before the previous barrier
-    if (znext) stage_plane<VEC>(sZnext, znext, H, W, tx0, ty0, tid);
+    if (znext) stage_plane<VEC>(sZnext, znext, H, W, tx0, ty0, tid, -INFINITY);
     if (tid < 2 * NCOL) fwd_vpass<K>(sZcur, sY, sVA, sVB, ml2e, tid);
     __syncthreads();
     // after the last vertical pass the y planes are free: the albedo of the
@@ -567,7 +463,7 @@ __device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZcur, fl
     if (a_stage) stage_albedo(sY + dfv::FH * dfv::FW, a_stage, H, W, tx0, ty0, tid);
     const int row = tid & 31, seg = tid >> 5;
     const unsigned exact = fwd_hpass<K>(sVA, sVB, st, row, seg);
-    if (zlnext) load_fusion_logits<VEC>(st.l, zlnext, H, W, ty0 + row, tx0 + seg * dfv::SEG);
+    if (zlnext) load_row8<VEC>(st.l, zlnext, H, W, ty0 + row, tx0 + seg * dfv::SEG);
     if (znext) finish_stage<VEC>(sZnext, red_next, tid);
     if (a_stage) cp_async_wait_all();
     __syncthreads();
@@ -604,53 +500,8 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     // pixels into registers.
     constexpr int PL = dfv::FH * dfv::FW;
     if (tid == 0) red[0] = INT_MIN;
-    stage_plane<VEC>(sZ, z, H, W, tx0, ty0, tid);
-    {
-        // chunk (VEC: 4 columns, else 1 element) c of plane ch: image rows and
-        // columns outside the frame are written as 0 (y = 0 there)
-        float* rdst = DEMOD ? sRst : sY;
-        if constexpr (VEC) {
-#pragma unroll
-            for (int u = 0; u < dfv::CPT; ++u) {
-                const int c = tid + u * dfv::THREADS;
-                if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
-                const int cr = c / (dfv::FW / 4), c4 = c % (dfv::FW / 4);
-                const int yy = ty0 - dfv::HALO + cr, xx = tx0 - dfv::XOFF + 4 * c4;
-                const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-                const size_t g = (size_t)yy * W + xx;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    float* dr = rdst + ch * PL + 4 * c;
-                    float* da = sY + ch * PL + 4 * c;
-                    if (in) {
-                        cp_async16(dr, r + ch * HW + g);
-                        if (DEMOD) cp_async16(da, a + ch * HW + g);
-                    } else {
-                        *reinterpret_cast<float4*>(dr) = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (DEMOD) *reinterpret_cast<float4*>(da) = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-            }
-        } else {
-            for (int e = tid; e < PL; e += dfv::THREADS) {
-                const int er = e / dfv::FW, ec = e % dfv::FW;
-                const int yy = ty0 - dfv::HALO + er, xx = tx0 - dfv::XOFF + ec;
-                const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-                const size_t g = (size_t)yy * W + xx;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    if (in) {
-                        cp_async4(rdst + ch * PL + e, r + ch * HW + g);
-                        if (DEMOD) cp_async4(sY + ch * PL + e, a + ch * HW + g);
-                    } else {
-                        rdst[ch * PL + e] = 0.f;
-                        if (DEMOD) sY[ch * PL + e] = 0.f;
-                    }
-                }
-            }
-        }
-        cp_async_commit();
-    }
+    stage_plane<VEC>(sZ, z, H, W, tx0, ty0, tid, -INFINITY);
+    stage_irradiance<DEMOD, VEC>(sY, sRst, r, a, H, W, tx0, ty0, tid);
     __syncthreads();  // red[0] initialised before any thread folds its maximum in
 
     // Shift of the fusion softmax per own pixel (Eq. 5): c = max_i l_i (all
@@ -661,7 +512,7 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
         float l[WSKPN_MAX_KERNELS][dfv::SEG];
 #pragma unroll
         for (int i = 0; i < WSKPN_MAX_KERNELS; ++i)
-            if (i < M) load_fusion_logits<VEC>(l[i], z + (size_t)(M + i) * HW, H, W, gy, gx0);
+            if (i < M) load_row8<VEC>(l[i], z + (size_t)(M + i) * HW, H, W, gy, gx0);
 #pragma unroll
         for (int x = 0; x < dfv::SEG; ++x) {
             float c = l[0][x];
@@ -678,29 +529,7 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     // thread converts exactly the elements it staged, after its own copies
     // landed (outside the frame r = a = 0, so y = 0).
     cp_async_wait_all();
-    if constexpr (DEMOD) {
-        if constexpr (VEC) {
-#pragma unroll
-            for (int u = 0; u < dfv::CPT; ++u) {
-                const int c = tid + u * dfv::THREADS;
-                if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    const float4 rv = reinterpret_cast<const float4*>(sRst + ch * PL)[c];
-                    float4& yv = reinterpret_cast<float4*>(sY + ch * PL)[c];
-                    const float4 av = yv;
-                    yv = make_float4(__fdividef(rv.x, av.x + eps), __fdividef(rv.y, av.y + eps),
-                                     __fdividef(rv.z, av.z + eps), __fdividef(rv.w, av.w + eps));
-                }
-            }
-        } else {
-            for (int e = tid; e < PL; e += dfv::THREADS)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch)
-                    sY[ch * PL + e] = __fdividef(sRst[ch * PL + e], sY[ch * PL + e] + eps);
-        }
-    }
-
+    if constexpr (DEMOD) form_irradiance<VEC>(sY, sRst, eps, tid);
     finish_stage<VEC>(sZ, red, tid);
     __syncthreads();
 
@@ -840,24 +669,24 @@ wskpn_status launch_decode_fuse_fwd(const float* const* z, const float* const* r
 // ======================================================================
 // Backward of the reconstruction (chain rule through Eq. 3-5).
 //
-// With g_c = (a_c + eps) dL/dout_c, h_ic = g_c alpha_i, E_i = exp(I_i),
-// D_i(p) = sum_{Omega_i(p)} E_i and R_ic = N_ic / D_i:
-//   dL/dalpha-logit_i(p) = alpha_i (da_i - sum_j alpha_j da_j),  da_i = sum_c g_c R_ic
-//   dL/dI_i(q) = sum_{p in Omega_i(q)} exp(I_i(q) - LSE_i(p)) sum_c h_ic(p) (y_c(q) - R_ic(p))
-// (windows are symmetric: q in Omega(p) <=> p in Omega(q)), where
-// LSE_i(p) = log D_i(p) is carried exactly, so the two kernels need no
-// common exponent shift.
-//   kernel 1 (per pixel p): R_ic, LSE_i, alpha_i, g_c -> scratch; the
-//            fusion-logit gradients -> dz;
-//   kernel 2 (per pixel q): window sums over p of u(p) h_ic(p) and
-//            u(p) sum_c h_ic(p) R_ic(p) with u = exp(s - LSE), s the
-//            footprint's minimum LSE, then
-//            dz_i(q) = exp(I_i(q) - s) (sum_c y_c(q) S_c(q) - S_B(q)).
-// Footprints whose LSE range exceeds 80 take an exact per-window loop.
-// Scratch layout per frame: planes [LSE_0..M-1, hR_0..M-1,
-// h_{0,0..2}, ..., h_{M-1,0..2}, (3 unused)] = 5M + 3 planes of H x W, with
-// h_ic = alpha_i g_c and hR_i = sum_c h_ic R_ic: kernel 2 reads four
-// planes per footprint pixel besides LSE.
+// With g_c = (a_c + eps) dL/dout_c, E_i = exp(I_i), D_i(p) = sum over
+// Omega_i(p) of E_i, R_ic = N_ic / D_i, LSE_i = log D_i, fusion weights
+// alpha_i and d_i = sum_c g_c R_ic:
+//   dL/dl_i(p) = alpha_i (d_i - sum_j alpha_j d_j)              (fusion logits)
+//   dL/dI_i(q) = sum over p in Omega_i(q) of
+//                alpha_i(p) exp(I_i(q) - LSE_i(p)) (sum_c g_c(p) y_c(q) - d_i(p))
+// (windows are symmetric: q in Omega(p) <=> p in Omega(q)).  With
+// Lp_i = LSE_i - ln alpha_i the second is exp(I_i(q) - s) times the window
+// sums over p of e(p) g_c(p) and e(p) d_i(p), e = exp(s - Lp_i(p)), for any
+// shift s; s is the minimum of Lp_i over the tile's staged block.
+//   kernel 1 (the forward's tiles and window sums): Lp_i, d_i and g_c ->
+//            scratch, the fusion-logit gradients -> dz;
+//   kernel 2 (the same tiles): per size, the window sums of
+//            (e g0, e g1 | e g2, e d) -> dz_i.
+// Scratch per frame: planes [Lp_0..M-1 | d_0..M-1 | g_0 g_1 g_2] of H x W.
+// A pixel whose D_i underflows takes an exact window loop in kernel 1; a
+// tile whose staged Lp_i spans more than 80 takes one in kernel 2 (there the
+// factors exp(I - s) and exp(s - Lp) stay inside the FP32 range).
 // ======================================================================
 
 struct DecodeBwdArgs {
@@ -869,276 +698,510 @@ struct DecodeBwdArgs {
     unsigned int* fallbacks;
 };
 
-__global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd1_kernel(DecodeBwdArgs args) {
-    extern __shared__ float smem[];
-    float* sY = smem;
-    float* sE = sY + 3 * df::RH * df::RP;
-    float* sH = sE + 4 * df::RH * df::RP;
-    float* sV = sE;
-    __shared__ float red[df::THREADS / 32];
+namespace dfv {
+constexpr float LN2 = 0.6931471805599453f;
+constexpr float RANGE = 80.f;  // widest staged Lp range of kernel 2's window-sum path
+}  // namespace dfv
+
+// 8 results of a horizontal-pass task into one row of a plane.
+template <bool VEC>
+__device__ __forceinline__ void store_row8(float* __restrict__ p, int H, int W, int gy, int gx0,
+                                           const float (&v)[dfv::SEG]) {
+    if (gy >= H) return;
+    if (VEC && gx0 + dfv::SEG <= W) {
+        float4* q = reinterpret_cast<float4*>(p + (size_t)gy * W + gx0);
+        q[0] = make_float4(v[0], v[1], v[2], v[3]);
+        q[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int x = 0; x < dfv::SEG; ++x)
+            if (gx0 + x < W) p[(size_t)gy * W + gx0 + x] = v[x];
+    }
+}
+
+// log-sum-exp of I over the window of size k around (px, py), clipped to
+// the image (exact, shifted by the window's own maximum).
+__device__ __noinline__ float window_lse(const float* __restrict__ zi, int H, int W, int k, int px, int py) {
+    const int h = k / 2;
+    const int y0 = max(py - h, 0), y1 = min(py + h, H - 1), x0 = max(px - h, 0), x1 = min(px + h, W - 1);
+    float m = -INFINITY, D = 0.f;
+    for (int qy = y0; qy <= y1; ++qy)
+        for (int qx = x0; qx <= x1; ++qx) m = fmaxf(m, zi[(size_t)qy * W + qx]);
+    for (int qy = y0; qy <= y1; ++qy)
+        for (int qx = x0; qx <= x1; ++qx) D += expf(zi[(size_t)qy * W + qx] - m);
+    return m + logf(D);
+}
+
+// Kernel-1 state of a horizontal-pass task across the sizes.
+struct BState {
+    float g[dfv::SEG][3];  // g_c = (a_c + eps) dL/dout_c
+    float Sd[dfv::SEG];    // sum over the sizes so far of alpha_i d_i
+    float cl[dfv::SEG];    // (c + ln S) log2 e, so that alpha_i = 2^(l_i log2 e - cl)
+    float l[dfv::SEG];     // fusion logits of the size being processed
+};
+
+// Kernel 1, horizontal pass of size K: from the window sums (N0, D) and
+// (N1, N2), d = sum_c g_c N_c / D and Lp = LSE - ln alpha (LSE = m + ln D,
+// m the size's exponent shift, ml2e = m log2 e); Sd += alpha d.  Returns the
+// mask of pixels whose D underflowed (their d, Lp are redone exactly).
+template <int K>
+__device__ __forceinline__ unsigned bwd1_hpass(const float2* __restrict__ sVA, const float2* __restrict__ sVB,
+                                               BState& st, float ml2e, int row, int seg, float (&Lp)[dfv::SEG],
+                                               float (&d)[dfv::SEG]) {
+    const int v = row * dfv::VP + seg * dfv::SEG;
+    float inv[dfv::SEG];
+    bool bad = false;
+    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVA[v + j]; },
+                               [&](int x, const float2(&t)[1]) {
+                                   const float D = t[0].y;
+                                   const bool ok = D >= df::DMIN;
+                                   bad |= !ok;
+                                   inv[x] = ok ? __fdividef(1.f, D) : 0.f;
+                                   d[x] = st.g[x][0] * t[0].x;
+                                   // log2 alpha = l log2 e - cl
+                                   Lp[x] = (ml2e + __log2f(D) - fmaf(st.l[x], dfv::LOG2E, -st.cl[x])) * dfv::LN2;
+                               });
+    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVB[v + j]; },
+                               [&](int x, const float2(&t)[1]) {
+                                   d[x] = (d[x] + fmaf(st.g[x][1], t[0].x, st.g[x][2] * t[0].y)) * inv[x];
+                               });
+#pragma unroll
+    for (int x = 0; x < dfv::SEG; ++x)
+        st.Sd[x] = fmaf(ex2_approx(fmaf(st.l[x], dfv::LOG2E, -st.cl[x])), d[x], st.Sd[x]);
+    unsigned exact = 0;
+    if (bad) {  // rare: find the pixels again
+#pragma unroll 1
+        for (int x = 0; x < dfv::SEG; ++x) {
+            float D = 0.f;
+#pragma unroll 1
+            for (int j = 0; j < K; ++j) D += sVA[v + x + j].y;
+            if (!(D >= df::DMIN)) exact |= 1u << x;
+        }
+    }
+    return exact;
+}
+
+// Kernel 1, one window size K: the forward's phase (I_{i+1} staged during
+// this size's vertical pass, the next fusion logits and shift after the
+// horizontal pass), storing Lp_i and d_i of the task's 8 pixels.
+template <int K, bool VEC>
+__device__ __forceinline__ unsigned bwd1_size(const float* __restrict__ sZcur, float* __restrict__ sZnext,
+                                              const float* __restrict__ sY, float2* __restrict__ sVA,
+                                              float2* __restrict__ sVB, int* __restrict__ red,
+                                              int* __restrict__ red_next, BState& st,
+                                              const float* __restrict__ znext, const float* __restrict__ zlnext,
+                                              float* __restrict__ Lp_out, float* __restrict__ d_out, int H, int W,
+                                              int tx0, int ty0, int tid) {
+    constexpr int NCOL = dfv::TW + 2 * (K / 2);
+    const float ml2e = ord2f(*red) * dfv::LOG2E;
+    if (tid == 0) *red_next = INT_MIN;  // its last reader finished before the previous barrier
+    if (znext) stage_plane<VEC>(sZnext, znext, H, W, tx0, ty0, tid, -INFINITY);
+    if (tid < 2 * NCOL) fwd_vpass<K>(sZcur, sY, sVA, sVB, ml2e, tid);
+    __syncthreads();
+    const int row = tid & 31, seg = tid >> 5;
+    float Lp[dfv::SEG], d[dfv::SEG];
+    const unsigned exact = bwd1_hpass<K>(sVA, sVB, st, ml2e, row, seg, Lp, d);
+    store_row8<VEC>(Lp_out, H, W, ty0 + row, tx0 + seg * dfv::SEG, Lp);
+    store_row8<VEC>(d_out, H, W, ty0 + row, tx0 + seg * dfv::SEG, d);
+    if (zlnext) load_row8<VEC>(st.l, zlnext, H, W, ty0 + row, tx0 + seg * dfv::SEG);
+    if (znext) finish_stage<VEC>(sZnext, red_next, tid);
+    __syncthreads();
+    return exact;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_bwd1_kernel(const __grid_constant__ DecodeBwdArgs args) {
+    extern __shared__ float4 dsm4[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(dsm4);
+    float* sY = reinterpret_cast<float*>(smem + dfv::OFF_Y);
+    float* sRst = reinterpret_cast<float*>(smem + dfv::OFF_RSTAGE);
+    float* sZ = reinterpret_cast<float*>(smem + dfv::OFF_Z);
+    float2* sVA = reinterpret_cast<float2*>(smem + dfv::OFF_V);
+    float2* sVB = sVA + dfv::TH * dfv::VP;
+    int* red = reinterpret_cast<int*>(smem + dfv::OFF_R);
 
     const int tid = threadIdx.x;
     const int b = blockIdx.z;
     const int H = args.H, W = args.W, M = args.M;
     const size_t HW = (size_t)H * W;
-    const int tx0 = blockIdx.x * df::TW, ty0 = blockIdx.y * df::TH;
+    const int tx0 = blockIdx.x * dfv::TW, ty0 = blockIdx.y * dfv::TH;
     const float* __restrict__ z = args.z.p[b];
     const float* __restrict__ r = args.r.p[b];
     const float* __restrict__ a = args.a.p[b];
     const float* __restrict__ G = args.G.p[b];
-    float* __restrict__ sc = args.scratch.p[b];
+    float* const sc = args.scratch.p[b];  // written here and read back by the same threads
     float* __restrict__ dz = args.dz.p[b];
     const float eps = args.eps;
+    const int row = tid & 31, seg = tid >> 5;
+    const int gy = ty0 + row, gx0 = tx0 + seg * dfv::SEG;
 
-    load_irradiance(sY, r, a, H, W, tx0, ty0, eps, tid);
-
-    float alpha[df::PPT][WSKPN_MAX_KERNELS];
-    float dal[df::PPT][WSKPN_MAX_KERNELS];
-    float gc[df::PPT][3];
-#pragma unroll
-    for (int j = 0; j < df::PPT; ++j) {
-        const int p = tid + j * df::THREADS;
-        const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
-        const bool in = gy < H && gx < W;
-        const size_t g = (size_t)gy * W + gx;
-        float m = -INFINITY;
-#pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) {
-            alpha[j][i] = (i < M && in) ? z[(size_t)(M + i) * HW + g] : -INFINITY;
-            m = fmaxf(m, alpha[j][i]);
-            dal[j][i] = 0.f;
-        }
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) {
-            alpha[j][i] = (i < M && in) ? expf(alpha[j][i] - m) : 0.f;
-            s += alpha[j][i];
-        }
-#pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) alpha[j][i] = in ? alpha[j][i] / s : 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gc[j][c] = in ? (a[c * HW + g] + eps) * G[c * HW + g] : 0.f;
-    }
-
-    for (int i = 0; i < M; ++i) {
-        const int k = args.ks[i];
-        const int h = k / 2;
-        const float* __restrict__ zi = z + (size_t)i * HW;
-        const float m = size_sums_k(k, sE, sH, sV, sY, red, zi, H, W, tx0, ty0, tid);
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < df::PPT; ++j) {
-            const int p = tid + j * df::THREADS;
-            const int ly = p / df::TW, lx = p % df::TW;
-            const int gy = ty0 + ly, gx = tx0 + lx;
-            if (gy >= H || gx >= W) continue;
-            const size_t g = (size_t)gy * W + gx;
-            const float D = sV[ly * df::TW + lx];
-            float R[3], L;
-            if (D >= df::DMIN) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) R[c] = sV[((1 + c) * df::TH + ly) * df::TW + lx] / D;
-                L = m + logf(D);
-            } else {
-                window_exact(zi, r, a, H, W, k, eps, gx, gy, R);
-                // exact log-sum-exp of the window
-                const int y0 = max(gy - h, 0), y1 = min(gy + h, H - 1), x0 = max(gx - h, 0), x1 = min(gx + h, W - 1);
-                float mw = -INFINITY, Dw = 0.f;
-                for (int qy = y0; qy <= y1; ++qy)
-                    for (int qx = x0; qx <= x1; ++qx) mw = fmaxf(mw, zi[(size_t)qy * W + qx]);
-                for (int qy = y0; qy <= y1; ++qy)
-                    for (int qx = x0; qx <= x1; ++qx) Dw += expf(zi[(size_t)qy * W + qx] - mw);
-                L = mw + logf(Dw);
-                if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
-            }
-            float al = 0.f;  // alpha_i of this pixel (registers indexed by constants only)
-#pragma unroll
-            for (int q = 0; q < WSKPN_MAX_KERNELS; ++q)
-                if (q == i) al = alpha[j][q];
-            sc[(size_t)i * HW + g] = L;
-            float hR = 0.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float hc = al * gc[j][c];
-                sc[(size_t)(2 * M + 3 * i + c) * HW + g] = hc;
-                hR += hc * R[c];
-            }
-            sc[(size_t)(M + i) * HW + g] = hR;
-            const float d = gc[j][0] * R[0] + gc[j][1] * R[1] + gc[j][2] * R[2];
-#pragma unroll
-            for (int q = 0; q < WSKPN_MAX_KERNELS; ++q)
-                if (q == i) dal[j][q] = d;
-        }
-        __syncthreads();
-    }
-
-    // fusion-logit gradients
-#pragma unroll
-    for (int j = 0; j < df::PPT; ++j) {
-        const int p = tid + j * df::THREADS;
-        const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
-        if (gy >= H || gx >= W) continue;
-        const size_t g = (size_t)gy * W + gx;
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i) s += alpha[j][i] * dal[j][i];
+    // Set-up as the forward's; besides the fusion softmax's shift each task
+    // keeps the shift that also normalises it, and g_c of its pixels.
+    if (tid == 0) red[0] = INT_MIN;
+    stage_plane<VEC>(sZ, z, H, W, tx0, ty0, tid, -INFINITY);
+    stage_irradiance<true, VEC>(sY, sRst, r, a, H, W, tx0, ty0, tid);
+    __syncthreads();  // red[0] initialised before any thread folds its maximum in
+    BState st;
+    {
+        float l[WSKPN_MAX_KERNELS][dfv::SEG];
 #pragma unroll
         for (int i = 0; i < WSKPN_MAX_KERNELS; ++i)
-            if (i < M) dz[(size_t)(M + i) * HW + g] = alpha[j][i] * (dal[j][i] - s);
+            if (i < M) load_row8<VEC>(l[i], z + (size_t)(M + i) * HW, H, W, gy, gx0);
+#pragma unroll
+        for (int x = 0; x < dfv::SEG; ++x) {
+            float c = l[0][x];
+#pragma unroll
+            for (int i = 1; i < WSKPN_MAX_KERNELS; ++i)
+                if (i < M) c = fmaxf(c, l[i][x]);
+            const float c2 = c * dfv::LOG2E;
+            float S = 0.f;  // >= 1: the largest term is 2^0
+#pragma unroll
+            for (int i = 0; i < WSKPN_MAX_KERNELS; ++i)
+                if (i < M) S += ex2_approx(fmaf(l[i][x], dfv::LOG2E, -c2));
+            st.cl[x] = c2 + __log2f(S);
+            st.l[x] = l[0][x];
+            st.Sd[x] = 0.f;
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float av[dfv::SEG], gv[dfv::SEG];
+            load_row8<VEC>(av, a + ch * HW, H, W, gy, gx0);
+            load_row8<VEC>(gv, G + ch * HW, H, W, gy, gx0);
+#pragma unroll
+            for (int x = 0; x < dfv::SEG; ++x) st.g[x][ch] = (av[x] + eps) * gv[x];
+        }
+    }
+    cp_async_wait_all();
+    form_irradiance<VEC>(sY, sRst, eps, tid);
+    finish_stage<VEC>(sZ, red, tid);
+    __syncthreads();
+
+    unsigned long long exact = 0;  // bit 8 i + x: pixel x's D_i underflowed
+    for (int i = 0; i < M; ++i) {
+        const bool more = i + 1 < M;
+        const float* znext = more ? z + (size_t)(i + 1) * HW : nullptr;
+        const float* zlnext = more ? z + (size_t)(M + i + 1) * HW : nullptr;
+        float* zc = sZ + (i & 1) * dfv::FH * dfv::FW;
+        float* zn = sZ + ((i + 1) & 1) * dfv::FH * dfv::FW;
+        int* rd = red + (i & 1);
+        int* rn = red + ((i + 1) & 1);
+        float* Lp_out = sc + (size_t)i * HW;
+        float* d_out = sc + (size_t)(M + i) * HW;
+        unsigned ex = 0;
+#define WSKPN_BWD1_SIZE(K_)                                                                                  \
+    case K_:                                                                                                 \
+        ex = bwd1_size<K_, VEC>(zc, zn, sY, sVA, sVB, rd, rn, st, znext, zlnext, Lp_out, d_out, H, W, tx0, ty0, \
+                                tid);                                                                        \
+        break;
+        switch (args.ks[i]) {
+            WSKPN_BWD1_SIZE(1) WSKPN_BWD1_SIZE(3) WSKPN_BWD1_SIZE(5) WSKPN_BWD1_SIZE(7) WSKPN_BWD1_SIZE(9)
+            WSKPN_BWD1_SIZE(11) WSKPN_BWD1_SIZE(13)
+        }
+#undef WSKPN_BWD1_SIZE
+        exact |= (unsigned long long)ex << (8 * i);
+    }
+    if (gy >= H) return;
+
+    // Pixels whose D_i underflowed: exact R and LSE of the window (rare); the
+    // fast path left d = 0 out of Sd and stored values replaced here.
+    if (exact) {
+#pragma unroll 1
+        for (int i = 0; i < M; ++i) {
+#pragma unroll 1
+            for (int x = 0; x < dfv::SEG; ++x) {
+                const int px = gx0 + x;
+                if (!((exact >> (8 * i + x)) & 1ull) || px >= W) continue;
+                const float* zi = z + (size_t)i * HW;
+                float R[3];
+                window_exact_inl(zi, r, a, H, W, args.ks[i], eps, px, gy, R);
+                const float L = window_lse(zi, H, W, args.ks[i], px, gy);
+                if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
+                const size_t g = (size_t)gy * W + px;
+                const float l = __ldg(z + (size_t)(M + i) * HW + g);
+#pragma unroll
+                for (int q = 0; q < dfv::SEG; ++q)
+                    if (q == x) {
+                        const float la2 = fmaf(l, dfv::LOG2E, -st.cl[q]);  // log2 alpha_i
+                        const float dv = st.g[q][0] * R[0] + st.g[q][1] * R[1] + st.g[q][2] * R[2];
+                        sc[(size_t)i * HW + g] = L - la2 * dfv::LN2;
+                        sc[(size_t)(M + i) * HW + g] = dv;
+                        st.Sd[q] = fmaf(ex2_approx(la2), dv, st.Sd[q]);
+                    }
+            }
+        }
+    }
+
+    // g_c for kernel 2, and the fusion-logit gradients alpha_i (d_i - Sd)
+    // (d_i read back from this thread's own stores).
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float gv[dfv::SEG];
+#pragma unroll
+        for (int x = 0; x < dfv::SEG; ++x) gv[x] = st.g[x][ch];
+        store_row8<VEC>(sc + (size_t)(2 * M + ch) * HW, H, W, gy, gx0, gv);
+    }
+    for (int i = 0; i < M; ++i) {
+        float l[dfv::SEG], o[dfv::SEG];
+        load_row8<VEC>(l, z + (size_t)(M + i) * HW, H, W, gy, gx0);
+        const float* dp = sc + (size_t)(M + i) * HW + (size_t)gy * W + gx0;
+#pragma unroll
+        for (int x = 0; x < dfv::SEG; ++x) {
+            const float dv = gx0 + x < W ? dp[x] : 0.f;
+            o[x] = ex2_approx(fmaf(l[x], dfv::LOG2E, -st.cl[x])) * (dv - st.Sd[x]);
+        }
+        store_row8<VEC>(dz + (size_t)(M + i) * HW, H, W, gy, gx0, o);
     }
 }
 
-__global__ void __launch_bounds__(df::THREADS, 2) decode_fuse_bwd2_kernel(DecodeBwdArgs args) {
-    extern __shared__ float smem[];
-    float* sE = smem;                       // [4][RH][RP]: u h_0, u h_1, u h_2, u sum_c h_c R_c
-    float* sH = sE + 4 * df::RH * df::RP;   // [4][RH][HP]
-    float* sV = sE;
-    __shared__ float red[2][df::THREADS / 32];
+// Kernel 2: wait for this thread's copies of the staged Lp block, and fold
+// the warp's minimum and largest finite value into red[0], red[1]
+// (order-preserving ints; outside the image Lp is +inf).
+template <bool VEC>
+__device__ __forceinline__ void finish_minmax(const float* __restrict__ sL, int* __restrict__ red, int tid) {
+    cp_async_wait_all();
+    float mn = INFINITY, mx = -INFINITY;
+    auto take = [&](float v) {
+        mn = fminf(mn, v);
+        if (v < INFINITY) mx = fmaxf(mx, v);
+    };
+    if constexpr (VEC) {
+#pragma unroll
+        for (int u = 0; u < dfv::CPT; ++u) {
+            const int c = tid + u * dfv::THREADS;
+            if (dfv::CPT * dfv::THREADS > dfv::NCH && c >= dfv::NCH) break;
+            const float4 v = reinterpret_cast<const float4*>(sL)[c];
+            take(v.x), take(v.y), take(v.z), take(v.w);
+        }
+    } else {
+        for (int e = tid; e < dfv::FH * dfv::FW; e += dfv::THREADS) take(sL[e]);
+    }
+    const int wmn = __reduce_min_sync(0xffffffffu, f2ord(mn));
+    const int wmx = __reduce_max_sync(0xffffffffu, f2ord(mx));
+    if ((tid & 31) == 0) {
+        atomicMin(red, wmn);
+        atomicMax(red + 1, wmx);
+    }
+}
+
+// Kernel 2, vertical pass of size K (tasks as the forward's): e =
+// exp(s - Lp) once per element (s = mn2 / log2 e), and the K-row sums of
+// (e g0, e g1) into sVA and of (e g2, e d) into sVB.  sS holds the Lp and d
+// blocks, sG the g blocks.
+template <int K>
+__device__ __forceinline__ void bwd2_vpass(const float* __restrict__ sS, const float* __restrict__ sG,
+                                           float2* __restrict__ sVA, float2* __restrict__ sVB, float mn2, int t) {
+    constexpr int h = K / 2, NCOL = dfv::TW + 2 * h;
+    constexpr int PL = dfv::FH * dfv::FW;
+    const int half = t >= NCOL ? 1 : 0;
+    const int col = t - half * NCOL;
+    const int o = (dfv::HALO + dfv::RV * half - h) * dfv::FW + dfv::XOFF - h + col;
+    const int v = dfv::RV * half * dfv::VP + col;
+    box_stream<K, dfv::RV, 2>(
+        [&](int j, float2(&w)[2]) {
+            const int q = o + j * dfv::FW;
+            const float e = ex2_approx(fmaf(sS[q], -dfv::LOG2E, mn2));
+            w[0] = __fmul2_rn(make_float2(e, e), make_float2(sG[q], sG[PL + q]));
+            w[1] = __fmul2_rn(make_float2(e, e), make_float2(sG[2 * PL + q], sS[PL + q]));
+        },
+        [&](int y, const float2(&s)[2]) {
+            sVA[v + y * dfv::VP] = s[0];
+            sVB[v + y * dfv::VP] = s[1];
+        });
+}
+
+// Kernel 2, horizontal pass of size K: the window sums S_c (of e g_c) and
+// S_d (of e d) of the task's 8 pixels q give
+// dL/dI(q) = exp(I(q) - s) (sum_c y_c(q) S_c - S_d).
+template <int K>
+__device__ __forceinline__ void bwd2_hpass(const float2* __restrict__ sVA, const float2* __restrict__ sVB,
+                                           const float (&y)[dfv::SEG][3], const float (&zq)[dfv::SEG], float mn2,
+                                           int row, int seg, float (&o)[dfv::SEG]) {
+    const int v = row * dfv::VP + seg * dfv::SEG;
+    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVA[v + j]; },
+                               [&](int x, const float2(&t)[1]) { o[x] = fmaf(y[x][0], t[0].x, y[x][1] * t[0].y); });
+    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVB[v + j]; },
+                               [&](int x, const float2(&t)[1]) {
+                                   const float f = ex2_approx(fmaf(zq[x], dfv::LOG2E, -mn2));
+                                   o[x] = f * (fmaf(y[x][2], t[0].x, o[x]) - t[0].y);
+                               });
+}
+
+// Kernel 2's exact path for one pixel q (a tile whose staged Lp range is too
+// wide): the window loop over p of exp(I(q) - Lp(p)) (sum_c g_c(p) y_c(q) - d(p)).
+__device__ __noinline__ float bwd2_exact(const float* __restrict__ sc, int M, int i, int H, int W, int k, float zq,
+                                         float y0, float y1, float y2, int px, int py) {
+    const size_t HW = (size_t)H * W;
+    const float* Lp = sc + (size_t)i * HW;
+    const float* d = sc + (size_t)(M + i) * HW;
+    const float* g = sc + (size_t)(2 * M) * HW;
+    const int h = k / 2;
+    float v = 0.f;
+    for (int qy = max(py - h, 0); qy <= min(py + h, H - 1); ++qy)
+        for (int qx = max(px - h, 0); qx <= min(px + h, W - 1); ++qx) {
+            const size_t p = (size_t)qy * W + qx;
+            const float t = fmaf(__ldg(g + p), y0, fmaf(__ldg(g + HW + p), y1, __ldg(g + 2 * HW + p) * y2)) - __ldg(d + p);
+            v += expf(zq - __ldg(Lp + p)) * t;
+        }
+    return v;
+}
+
+// Kernel 2, one window size K.  Phase: the vertical pass reads the staged
+// Lp_i, d_i blocks; after the barrier Lp_{i+1}, d_{i+1} are staged into the
+// same buffer while the horizontal pass runs, then their range is reduced.
+// Returns true (block-uniform) when the staged range is too wide for the
+// window sums: the size's gradients are then left to the exact loop.
+template <int K, bool VEC>
+__device__ __forceinline__ bool bwd2_size(float* __restrict__ sS, const float* __restrict__ sG,
+                                          float2* __restrict__ sVA, float2* __restrict__ sVB, int* __restrict__ red,
+                                          int* __restrict__ red_next, const float (&y)[dfv::SEG][3],
+                                          float (&zq)[dfv::SEG], const float* __restrict__ sc, int M, int i,
+                                          const float* __restrict__ zi_next, float* __restrict__ dzi, int H, int W,
+                                          int tx0, int ty0, int tid) {
+    constexpr int NCOL = dfv::TW + 2 * (K / 2);
+    constexpr int PL = dfv::FH * dfv::FW;
+    const float mn = ord2f(red[0]), mx = ord2f(red[1]);
+    const float mn2 = mn * dfv::LOG2E;
+    const bool wide = !(mx - mn <= dfv::RANGE);  // block-uniform
+    if (tid == 0) {  // their last readers finished before the previous barrier
+        red_next[0] = INT_MAX;
+        red_next[1] = INT_MIN;
+    }
+    if (!wide && tid < 2 * NCOL) bwd2_vpass<K>(sS, sG, sVA, sVB, mn2, tid);
+    __syncthreads();
+    const bool more = zi_next != nullptr;
+    const size_t HW = (size_t)H * W;
+    if (more) {
+        stage_plane<VEC>(sS, sc + (size_t)(i + 1) * HW, H, W, tx0, ty0, tid, INFINITY);
+        stage_plane<VEC>(sS + PL, sc + (size_t)(M + i + 1) * HW, H, W, tx0, ty0, tid, 0.f);
+    }
+    const int row = tid & 31, seg = tid >> 5;
+    const int gy = ty0 + row, gx0 = tx0 + seg * dfv::SEG;
+    if (!wide) {
+        float o[dfv::SEG];
+        bwd2_hpass<K>(sVA, sVB, y, zq, mn2, row, seg, o);
+        store_row8<VEC>(dzi, H, W, gy, gx0, o);
+    }
+    if (more) load_row8<VEC>(zq, zi_next, H, W, gy, gx0);
+    if (more) finish_minmax<VEC>(sS, red_next, tid);
+    __syncthreads();
+    return wide;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_bwd2_kernel(const __grid_constant__ DecodeBwdArgs args) {
+    extern __shared__ float4 dsm4[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(dsm4);
+    float* sG = reinterpret_cast<float*>(smem + dfv::OFF_Y);  // [3][FH][FW]: g0, g1, g2
+    float* sS = reinterpret_cast<float*>(smem + dfv::OFF_Z);  // [2][FH][FW]: Lp_i, d_i
+    float2* sVA = reinterpret_cast<float2*>(smem + dfv::OFF_V);
+    float2* sVB = sVA + dfv::TH * dfv::VP;
+    int* red = reinterpret_cast<int*>(smem + dfv::OFF_R);  // [2][min, max]
+    constexpr int PL = dfv::FH * dfv::FW;
 
     const int tid = threadIdx.x;
     const int b = blockIdx.z;
     const int H = args.H, W = args.W, M = args.M;
     const size_t HW = (size_t)H * W;
-    const int tx0 = blockIdx.x * df::TW, ty0 = blockIdx.y * df::TH;
+    const int tx0 = blockIdx.x * dfv::TW, ty0 = blockIdx.y * dfv::TH;
     const float* __restrict__ z = args.z.p[b];
     const float* __restrict__ r = args.r.p[b];
     const float* __restrict__ a = args.a.p[b];
     const float* __restrict__ sc = args.scratch.p[b];
     float* __restrict__ dz = args.dz.p[b];
     const float eps = args.eps;
+    const int row = tid & 31, seg = tid >> 5;
+    const int gy = ty0 + row, gx0 = tx0 + seg * dfv::SEG;
 
-    float yq[df::PPT][3];
+    // Set-up: the g blocks and the first size's Lp, d blocks by cp.async;
+    // y and I_0 of the task's own pixels into registers.
+    if (tid == 0) {
+        red[0] = INT_MAX;
+        red[1] = INT_MIN;
+    }
 #pragma unroll
-    for (int j = 0; j < df::PPT; ++j) {
-        const int p = tid + j * df::THREADS;
-        const int gy = ty0 + p / df::TW, gx = tx0 + p % df::TW;
-        const bool in = gy < H && gx < W;
-        const size_t g = (size_t)gy * W + gx;
+    for (int ch = 0; ch < 3; ++ch) stage_plane<VEC>(sG + ch * PL, sc + (size_t)(2 * M + ch) * HW, H, W, tx0, ty0, tid, 0.f);
+    stage_plane<VEC>(sS, sc, H, W, tx0, ty0, tid, INFINITY);
+    stage_plane<VEC>(sS + PL, sc + (size_t)M * HW, H, W, tx0, ty0, tid, 0.f);
+    float y[dfv::SEG][3], zq[dfv::SEG];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) yq[j][c] = in ? r[c * HW + g] / (a[c * HW + g] + eps) : 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+        float rv[dfv::SEG], av[dfv::SEG];
+        load_row8<VEC>(rv, r + ch * HW, H, W, gy, gx0);
+        load_row8<VEC>(av, a + ch * HW, H, W, gy, gx0);
+#pragma unroll
+        for (int x = 0; x < dfv::SEG; ++x) y[x][ch] = __fdividef(rv[x], av[x] + eps);
+    }
+    load_row8<VEC>(zq, z, H, W, gy, gx0);
+    __syncthreads();  // red initialised before any thread folds its range in
+    finish_minmax<VEC>(sS, red, tid);
+    __syncthreads();
+
+    unsigned wide = 0;  // bit i: size i's staged Lp range was too wide
+    for (int i = 0; i < M; ++i) {
+        int* rd = red + 2 * (i & 1);
+        int* rn = red + 2 * ((i + 1) & 1);
+        const float* zi_next = i + 1 < M ? z + (size_t)(i + 1) * HW : nullptr;
+        float* dzi = dz + (size_t)i * HW;
+        bool wi = false;
+#define WSKPN_BWD2_SIZE(K_)                                                                                   \
+    case K_:                                                                                                  \
+        wi = bwd2_size<K_, VEC>(sS, sG, sVA, sVB, rd, rn, y, zq, sc, M, i, zi_next, dzi, H, W, tx0, ty0, tid); \
+        break;
+        switch (args.ks[i]) {
+            WSKPN_BWD2_SIZE(1) WSKPN_BWD2_SIZE(3) WSKPN_BWD2_SIZE(5) WSKPN_BWD2_SIZE(7) WSKPN_BWD2_SIZE(9)
+            WSKPN_BWD2_SIZE(11) WSKPN_BWD2_SIZE(13)
+        }
+#undef WSKPN_BWD2_SIZE
+        wide |= (unsigned)wi << i;
     }
 
-    for (int i = 0; i < M; ++i) {
-        const int k = args.ks[i];
-        const int h = k / 2;
-        const int nr = df::TH + 2 * h, nc = df::TW + 2 * h;
-        const float* __restrict__ Li = sc + (size_t)i * HW;
-        const float* __restrict__ HRi = sc + (size_t)(M + i) * HW;
-        const float* __restrict__ Hi = sc + (size_t)(2 * M + 3 * i) * HW;
-        // footprint minimum and maximum of LSE; the footprint's LSE values
-        // stay in registers for the plane pass (all loads issued first)
-        constexpr int FPER = ((df::TH + 2 * df::HALO) * (df::TW + 2 * df::HALO) + df::THREADS - 1) / df::THREADS;
-        float lv[FPER];
-        float mn = INFINITY, mx = -INFINITY;
+    // Sizes whose range was too wide: the exact window loop per own pixel
+    // (rare; y and I reloaded, out of the unrolled code above).
+    if (wide && gy < H) {
+#pragma unroll 1
+        for (int i = 0; i < M; ++i) {
+            if (!((wide >> i) & 1u)) continue;
+#pragma unroll 1
+            for (int x = 0; x < dfv::SEG; ++x) {
+                if (gx0 + x >= W) break;
+                const size_t g = (size_t)gy * W + gx0 + x;
+                float yc[3];
 #pragma unroll
-        for (int u = 0; u < FPER; ++u) {
-            const int t = tid + u * df::THREADS;
-            const int gy = ty0 - h + t / nc, gx = tx0 - h + t % nc;
-            const bool in = t < nr * nc && gy >= 0 && gy < H && gx >= 0 && gx < W;
-            lv[u] = in ? Li[(size_t)gy * W + gx] : 0.f;
-            if (in) {
-                mn = fminf(mn, lv[u]);
-                mx = fmaxf(mx, lv[u]);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if ((tid & 31) == 0) {
-            red[0][tid >> 5] = mn;
-            red[1][tid >> 5] = mx;
-        }
-        __syncthreads();
-        mn = red[0][0];
-        mx = red[1][0];
-#pragma unroll
-        for (int w = 1; w < df::THREADS / 32; ++w) {
-            mn = fminf(mn, red[0][w]);
-            mx = fmaxf(mx, red[1][w]);
-        }
-        const bool exact = mx - mn > 80.f;  // block-uniform
-        if (!exact) {
-#pragma unroll
-            for (int u = 0; u < FPER; ++u) {
-                const int t = tid + u * df::THREADS;
-                if (t >= nr * nc) break;
-                const int ry = df::HALO - h + t / nc, rx = df::HALO - h + t % nc;
-                const int gy = ty0 - df::HALO + ry, gx = tx0 - df::HALO + rx;
-                const int o = ry * df::RP + rx;
-                float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                    const size_t g = (size_t)gy * W + gx;
-                    const float e = expf(mn - lv[u]);
-                    v0 = e * Hi[g];
-                    v1 = e * Hi[HW + g];
-                    v2 = e * Hi[2 * HW + g];
-                    v3 = e * HRi[g];
-                }
-                sE[o] = v0;
-                sE[df::RH * df::RP + o] = v1;
-                sE[2 * df::RH * df::RP + o] = v2;
-                sE[3 * df::RH * df::RP + o] = v3;
-            }
-            __syncthreads();
-            switch (k) {
-                case 1: box_sums<1>(sE, sH, sV, tid); break;
-                case 3: box_sums<3>(sE, sH, sV, tid); break;
-                case 5: box_sums<5>(sE, sH, sV, tid); break;
-                case 7: box_sums<7>(sE, sH, sV, tid); break;
-                case 9: box_sums<9>(sE, sH, sV, tid); break;
-                case 11: box_sums<11>(sE, sH, sV, tid); break;
-                default: box_sums<13>(sE, sH, sV, tid); break;
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int j = 0; j < df::PPT; ++j) {
-            const int p = tid + j * df::THREADS;
-            const int ly = p / df::TW, lx = p % df::TW;
-            const int gy = ty0 + ly, gx = tx0 + lx;
-            if (gy >= H || gx >= W) continue;
-            const size_t g = (size_t)gy * W + gx;
-            const float zq = z[(size_t)i * HW + g];
-            float v;
-            if (!exact) {
-                const float S0 = sV[ly * df::TW + lx], S1 = sV[(df::TH + ly) * df::TW + lx];
-                const float S2 = sV[(2 * df::TH + ly) * df::TW + lx], SB = sV[(3 * df::TH + ly) * df::TW + lx];
-                v = expf(zq - mn) * (yq[j][0] * S0 + yq[j][1] * S1 + yq[j][2] * S2 - SB);
-            } else {
-                v = 0.f;
-                for (int py = max(gy - h, 0); py <= min(gy + h, H - 1); ++py)
-                    for (int px = max(gx - h, 0); px <= min(gx + h, W - 1); ++px) {
-                        const size_t gp = (size_t)py * W + px;
-                        float t = -HRi[gp];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) t += Hi[c * HW + gp] * yq[j][c];
-                        v += expf(zq - Li[gp]) * t;
-                    }
+                for (int c = 0; c < 3; ++c) yc[c] = __fdividef(__ldg(r + c * HW + g), __ldg(a + c * HW + g) + eps);
+                dz[(size_t)i * HW + g] = bwd2_exact(sc, M, i, H, W, args.ks[i], __ldg(z + (size_t)i * HW + g), yc[0],
+                                                    yc[1], yc[2], gx0 + x, gy);
                 if (args.fallbacks) atomicAdd(args.fallbacks, 1u);
             }
-            dz[(size_t)i * HW + g] = v;
         }
-        __syncthreads();
     }
 }
 
-constexpr size_t DF_BWD2_SMEM = (4 * df::RH * df::RP + 4 * df::RH * df::HP) * sizeof(float);
+template <bool VEC>
+static wskpn_status launch_bwd_variant(const DecodeBwdArgs& args, int nb, cudaStream_t st, std::string& err) {
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_bwd1_kernel<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)dfv::SMEM_BYTES),
+                   err);
+    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_bwd2_kernel<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)dfv::SMEM_BYTES),
+                   err);
+    dim3 grid(cdiv(args.W, dfv::TW), cdiv(args.H, dfv::TH), nb);
+    decode_fuse_bwd1_kernel<VEC><<<grid, dfv::THREADS, dfv::SMEM_BYTES, st>>>(args);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    decode_fuse_bwd2_kernel<VEC><<<grid, dfv::THREADS, dfv::SMEM_BYTES, st>>>(args);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
+    return WSKPN_OK;
+}
 
+// Host launcher; the vectorised variant under the forward's condition (W a
+// multiple of 4, every plane pointer 16-byte aligned).
 wskpn_status launch_decode_fuse_bwd(const float* const* z, const float* const* r, const float* const* a,
                                     const float* const* G, float* const* dz, float* const* scratch, int B, int H,
                                     int W, int M, const int* ks, float eps, unsigned int* fallbacks,
                                     cudaStream_t st, std::string& err) {
-    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_bwd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)df::SMEM_BYTES),
-                   err);
-    WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_bwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)DF_BWD2_SMEM),
-                   err);
     for (int b0 = 0; b0 < B; b0 += WSKPN_MAX_BATCH) {
         const int nb = B - b0 < WSKPN_MAX_BATCH ? B - b0 : WSKPN_MAX_BATCH;
         DecodeBwdArgs args{};
+        bool vec = W % 4 == 0;
         for (int j = 0; j < nb; ++j) {
             args.z.p[j] = z[b0 + j];
             args.r.p[j] = r[b0 + j];
@@ -1146,6 +1209,8 @@ wskpn_status launch_decode_fuse_bwd(const float* const* z, const float* const* r
             args.G.p[j] = G[b0 + j];
             args.dz.p[j] = dz[b0 + j];
             args.scratch.p[j] = scratch[b0 + j];
+            vec = vec && aligned16(z[b0 + j]) && aligned16(r[b0 + j]) && aligned16(a[b0 + j]) &&
+                  aligned16(G[b0 + j]) && aligned16(dz[b0 + j]) && aligned16(scratch[b0 + j]);
         }
         args.H = H;
         args.W = W;
@@ -1153,11 +1218,8 @@ wskpn_status launch_decode_fuse_bwd(const float* const* z, const float* const* r
         for (int i = 0; i < M; ++i) args.ks[i] = ks[i];
         args.eps = eps;
         args.fallbacks = fallbacks;
-        dim3 grid(cdiv(W, df::TW), cdiv(H, df::TH), nb);
-        decode_fuse_bwd1_kernel<<<grid, df::THREADS, df::SMEM_BYTES, st>>>(args);
-        WSKPN_CUDA_TRY(cudaGetLastError(), err);
-        decode_fuse_bwd2_kernel<<<grid, df::THREADS, DF_BWD2_SMEM, st>>>(args);
-        WSKPN_CUDA_TRY(cudaGetLastError(), err);
+        const wskpn_status s = vec ? launch_bwd_variant<true>(args, nb, st, err) : launch_bwd_variant<false>(args, nb, st, err);
+        if (s) return s;
     }
     return WSKPN_OK;
 }

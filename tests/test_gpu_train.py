@@ -36,7 +36,8 @@ def _close(gpu, ref, tol=TOL_GRAD, scale=None):
     return float(np.abs(gpu - ref).max() / den) < tol
 
 
-@pytest.mark.parametrize("B,H,W", [(1, 45, 67), (2, 33, 90), (1, 1, 1), (1, 14, 200), (1, 70, 20)])
+@pytest.mark.parametrize("B,H,W", [(1, 45, 67), (2, 33, 90), (1, 1, 1), (1, 14, 200), (1, 70, 20),
+                                   (2, 100, 196), (1, 97, 131)])
 def test_decode_fuse_bwd_matches_oracle(torch, wk, B, H, W):
     g = np.random.default_rng(B * 100 + H)
     frames = [synth.make_frame(H, W, 200 + b) for b in range(B)]
