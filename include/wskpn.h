@@ -194,7 +194,7 @@ wskpn_status wskpn_calibrate(wskpn_ctx* ctx, const wskpn_frame* frames, int batc
 
 /* ---- Differentiation (one training step of Eq. 1) ------------------ */
 
-/* Floats of scratch that wskpn_decode_fuse_bwd needs: (5M + 3) x batch x h
+/* Floats of scratch that wskpn_decode_fuse_bwd needs: (2M + 3) x batch x h
  * x w (0 for invalid sizes). */
 size_t wskpn_decode_fuse_bwd_scratch_floats(int batch, int h, int w, int M);
 

@@ -52,7 +52,7 @@ struct TrainWs {
     float* gB = nullptr;
     size_t g_floats = 0;
     float* dz = nullptr;        // [B][2M][H][W]
-    float* dscratch = nullptr;  // reconstruction-backward scratch [B][5M+3][H][W]
+    float* dscratch = nullptr;  // reconstruction-backward scratch [B][2M+3][H][W]
     float* part = nullptr;      // wgrad partial sums
     float* wT[WSKPN_MAX_LAYERS] = {};  // transposed + flipped packed weights
     float* bT[WSKPN_MAX_LAYERS] = {};
@@ -134,7 +134,7 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
     t->acts_floats = off;  // allocated by the first backward that needs planar activations
     t->g_floats = (size_t)maxw * t->px;
     WSKPN_TRY_ALLOC(t->dz, (size_t)2 * M * t->px * sizeof(float));
-    WSKPN_TRY_ALLOC(t->dscratch, (size_t)(5 * M + 3) * t->px * sizeof(float));
+    WSKPN_TRY_ALLOC(t->dscratch, (size_t)(2 * M + 3) * t->px * sizeof(float));
     WSKPN_TRY_ALLOC(t->part, wgrad_part_floats(maxcin, KS, kWgradGroups) * sizeof(float));
     for (int l = 1; l < L; ++l) {  // layer 0 needs no input gradient
         const int cin = c.widths[l], cout = c.widths[l + 1];
@@ -356,7 +356,7 @@ extern "C" {
 
 size_t wskpn_decode_fuse_bwd_scratch_floats(int batch, int h, int w, int M) {
     if (batch < 1 || h < 1 || w < 1 || M < 1 || M > WSKPN_MAX_KERNELS) return 0;
-    return (size_t)(5 * M + 3) * batch * h * w;
+    return (size_t)(2 * M + 3) * batch * h * w;
 }
 
 wskpn_status wskpn_decode_fuse_bwd(const float* z, const float* radiance, const float* albedo, const float* dout,
@@ -381,7 +381,7 @@ wskpn_status wskpn_decode_fuse_bwd(const float* z, const float* radiance, const 
         aa[b] = albedo + (size_t)b * 3 * HW;
         gg[b] = dout + (size_t)b * 3 * HW;
         dd[b] = dz + (size_t)b * 2 * M * HW;
-        ss[b] = scratch + (size_t)b * (5 * M + 3) * HW;
+        ss[b] = scratch + (size_t)b * (2 * M + 3) * HW;
     }
     std::string err;
     wskpn_status s = launch_decode_fuse_bwd(zz.data(), rr.data(), aa.data(), gg.data(), dd.data(), ss.data(), batch,
@@ -444,7 +444,7 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
             aa[b] = frames[b].albedo;
             gg[b] = dout + (size_t)b * 3 * HW;
             dd[b] = dz + (size_t)b * 2 * M * HW;
-            ss[b] = t->dscratch + (size_t)b * (5 * M + 3) * HW;
+            ss[b] = t->dscratch + (size_t)b * (2 * M + 3) * HW;
         }
         s = launch_decode_fuse_bwd(zz.data(), rr.data(), aa.data(), gg.data(), dd.data(), ss.data(), batch, h, w, M,
                                    c.ksizes, c.albedo_eps, ctx->d_fallbacks, st, ctx->err);

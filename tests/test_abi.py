@@ -65,6 +65,15 @@ def test_even_kernel_size_rejected():
     assert b"odd" in lib.wskpn_last_error(None)
 
 
+def test_backward_scratch_size():
+    # planes per frame: Lp_i and d_i of every size, then g_0, g_1, g_2
+    lib = _lib.load()
+    assert lib.wskpn_decode_fuse_bwd_scratch_floats(2, 3, 5, 6) == (2 * 6 + 3) * 2 * 3 * 5
+    assert lib.wskpn_decode_fuse_bwd_scratch_floats(1, 1, 1, 1) == 5
+    assert lib.wskpn_decode_fuse_bwd_scratch_floats(1, 4, 4, 0) == 0
+    assert lib.wskpn_decode_fuse_bwd_scratch_floats(1, 4, 4, 9) == 0
+
+
 def test_null_arguments_rejected():
     lib = _lib.load()
     assert lib.wskpn_denoise(None, None, 1, 4, 4, None, None) == _lib.EINVAL
