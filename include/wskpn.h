@@ -212,16 +212,21 @@ wskpn_status wskpn_decode_fuse_bwd(const float* z, const float* radiance, const 
 
 /* Forward pass for training: out [batch][3][h][w] as wskpn_denoise, and the
  * network output z_saved [batch][2M][h][w] (device, caller-owned) that
- * wskpn_backward needs.  No activation is kept. */
+ * wskpn_backward needs.  BF16 context on the tensor-core training path
+ * (default tuning, batch <= 16): the layer inputs are written to the
+ * context's training workspace (allocated by the first training call) and
+ * kept for a wskpn_backward over the same frame buffers (pointers), batch
+ * and size; the values are those of wskpn_logits.  The frame buffers must
+ * not change in between.  Other contexts keep no activation. */
 wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
                                  float* out, float* z_saved, void* stream);
 
 /* Backward pass: from dout = dL/d(out) [batch][3][h][w] and z_saved,
  * writes dL/dweights (device, wskpn_n_weights floats, blob layout) and,
  * if dz_out is not NULL, dL/dz [batch][2M][h][w].  The activations are
- * recomputed from the frames (not kept from the forward).  BF16 context
- * (default WSKPN_TUNE_TRAIN_RECOMPUTE = 1): recomputed with the context's
- * own tensor-core convolutions, as its forward computes them; the input
+ * those kept by wskpn_forward_train (see there), else recomputed from the
+ * frames.  BF16 context (default WSKPN_TUNE_TRAIN_RECOMPUTE = 1): kept or
+ * recomputed with the context's own tensor-core convolutions; the input
  * gradient of each layer is a tensor-core convolution of the gradient (BF16
  * hi/lo pairs) with the transposed, flipped BF16 weights, the weight
  * gradient a tensor-core GEMM over the pixels (BF16 operands), both with

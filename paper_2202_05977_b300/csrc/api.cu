@@ -94,7 +94,7 @@ wskpn_status ctx_repack(wskpn_ctx* ctx, cudaStream_t st) {
     return WSKPN_OK;
 }
 
-static wskpn_status check_frames(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w) {
+wskpn_status check_frames(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w) {
     if (!frames) {
         ctx->err = "frames is NULL";
         return WSKPN_EINVAL;

@@ -1185,6 +1185,10 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     return tc_run(r, in, out, B, H, W, st, ctx->err);
 }
 
+wskpn_status tc_conv_layer(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st) {
+    return conv_tc(ctx, l, in, out, B, H, W, st);
+}
+
 // A BF16 layer (hi/lo activations) outside a context: weight image, groups,
 // epilogue bias; w [cout][cin][KS][KS] and b [cout] on the device.
 wskpn_status tc_layer_create(Layer& L, int KS, const float* w, const float* b, cudaStream_t st, std::string& err) {

@@ -92,6 +92,11 @@ wskpn_status ctx_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H,
 size_t tc_act_bytes_per_pixel(const wskpn_config& c, int which /*0 = A, 1 = B*/);
 wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l);
 wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st);
+// Argument checks shared by the calls that take frames (EINVAL with a message).
+wskpn_status check_frames(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w);
+// Layer l of the context's ImportanceNet on the tensor cores (BF16 / FP8
+// activations in the context's layout; the last layer writes planar z).
+wskpn_status tc_conv_layer(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st);
 wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                        cudaStream_t st);
 wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string& err);

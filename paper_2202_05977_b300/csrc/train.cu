@@ -75,7 +75,17 @@ struct TrainWs {
     float* wg_part = nullptr;           // tensor-core weight-gradient partial sums
     size_t wg_part_floats = 0;
     size_t acts_floats = 0;             // planar acts (FP32 gradient paths), allocated on first use
+    // xnhwc as written by the last wskpn_forward_train on the tensor-core
+    // path: the layer inputs of that forward, reused by a backward over the
+    // same frames (buffer pointers), batch and size instead of recomputed
+    bool kept = false;
+    int kept_batch = 0, kept_h = 0, kept_w = 0;
+    wskpn_frame kept_frames[WSKPN_MAX_BATCH] = {};
 };
+
+static bool same_frames(const wskpn_frame& x, const wskpn_frame& y) {
+    return x.radiance == y.radiance && x.albedo == y.albedo && x.normal == y.normal && x.depth == y.depth;
+}
 
 static void free_train(TrainWs* t) {
     if (!t) return;
@@ -397,9 +407,42 @@ wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int 
         ctx->err = "wskpn_forward_train: out or z_saved is NULL";
         return WSKPN_EINVAL;
     }
-    wskpn_status s = wskpn_logits(ctx, frames, batch, h, w, z_saved, stream);
-    if (s) return s;
     const wskpn_config& c = ctx->cfg;
+    cudaStream_t st = (cudaStream_t)stream;
+    // BF16 with the tensor-core backward: the layer inputs x_0 .. x_{L-1} go
+    // to the training workspace (NHWC hi/lo, where the backward reads them)
+    // instead of the inference ping-pong buffers; same kernels, same values.
+    const bool keep = c.prec == WSKPN_BF16 && tc_split_all(ctx) && ctx->train_tc_recompute == 1 &&
+                      batch >= 1 && batch <= WSKPN_MAX_BATCH;
+    wskpn_status s = WSKPN_OK;
+    TrainWs* t = nullptr;
+    if (keep) {
+        s = check_frames(ctx, frames, batch, h, w);
+        if (!s) s = ensure_train(ctx);
+        if (s) return s;
+        t = static_cast<TrainWs*>(ctx->train);
+        t->kept = false;
+        if (!t->all_tc) t = nullptr;
+    } else if (ctx->train) {
+        static_cast<TrainWs*>(ctx->train)->kept = false;
+    }
+    if (t) {
+        if (!t->xnhwc) WSKPN_TRY_ALLOC(t->xnhwc, t->x_bytes);
+        const int L = c.n_layers;
+        std::vector<void*> xs(L);
+        for (int l = 0; l < L; ++l) xs[l] = static_cast<uint8_t*>(t->xnhwc) + t->x_off[l];
+        s = tc_recompute_nhwc(ctx, frames, batch, h, w, xs, st);
+        if (!s) s = tc_conv_layer(ctx, L - 1, xs[L - 1], z_saved, batch, h, w, st);
+        if (s) return s;
+        t->kept = true;
+        t->kept_batch = batch;
+        t->kept_h = h;
+        t->kept_w = w;
+        for (int b = 0; b < batch; ++b) t->kept_frames[b] = frames[b];
+    } else {
+        s = wskpn_logits(ctx, frames, batch, h, w, z_saved, stream);
+        if (s) return s;
+    }
     const size_t HW = (size_t)h * w;
     std::vector<const float*> z(batch), r(batch), a(batch);
     std::vector<float*> o(batch);
@@ -410,7 +453,7 @@ wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int 
         o[b] = out + (size_t)b * 3 * HW;
     }
     return launch_decode_fuse_fwd(z.data(), r.data(), a.data(), o.data(), batch, h, w, c.n_kernels, c.ksizes,
-                                  c.albedo_eps, ctx->d_fallbacks, (cudaStream_t)stream, ctx->err);
+                                  c.albedo_eps, ctx->d_fallbacks, st, ctx->err);
 }
 
 wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
@@ -450,21 +493,25 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
                                    c.ksizes, c.albedo_eps, ctx->d_fallbacks, st, ctx->err);
         if (s) return s;
     }
-    // 2. recompute x_0 .. x_{L-1}: with the context's own convolutions for BF16
-    //    (tensor cores, hi/lo activations, as the forward), else FP32.  With
-    //    every gradient on the tensor cores they stay NHWC hi/lo; otherwise
-    //    planar FP32 for the SIMT gradient kernels.
+    // 2. the layer inputs x_0 .. x_{L-1}: kept by wskpn_forward_train over the
+    //    same frames, or recomputed with the context's own convolutions for
+    //    BF16 (tensor cores, hi/lo activations, as the forward), else FP32.
+    //    With every gradient on the tensor cores they stay NHWC hi/lo;
+    //    otherwise planar FP32 for the SIMT gradient kernels.
     const bool on_tc = c.prec == WSKPN_BF16 && tc_split_all(ctx) && ctx->train_tc_recompute && batch <= WSKPN_MAX_BATCH;
     const bool tc_bwd = on_tc && ctx->train_tc_recompute == 1 && t->all_tc;
     auto xn = [&](int l) { return static_cast<void*>(static_cast<uint8_t*>(t->xnhwc) + t->x_off[l]); };
     auto act = [&](int l, int b) { return t->acts + t->act_off[l] + (size_t)b * c.widths[l] * HW; };
-    if (tc_bwd) {
+    bool kept = tc_bwd && t->kept && t->kept_batch == batch && t->kept_h == h && t->kept_w == w;
+    for (int b = 0; kept && b < batch; ++b) kept = same_frames(t->kept_frames[b], frames[b]);
+    if (tc_bwd && !kept) {
         if (!t->xnhwc) WSKPN_TRY_ALLOC(t->xnhwc, t->x_bytes);
         std::vector<void*> xs(L);
         for (int l = 0; l < L; ++l) xs[l] = xn(l);
+        t->kept = false;  // overwritten with this call's frames
         s = tc_recompute_nhwc(ctx, frames, batch, h, w, xs, st);
         if (s) return s;
-    } else {
+    } else if (!tc_bwd) {
         if (!t->acts) WSKPN_TRY_ALLOC(t->acts, t->acts_floats * sizeof(float));
         std::vector<void*> x0(batch);
         for (int b = 0; b < batch; ++b) x0[b] = act(0, b);

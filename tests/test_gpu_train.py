@@ -144,6 +144,31 @@ def test_training_backward_bf16_tensor_core_recompute(torch, wk):
     assert d.device_status() == 0
 
 
+def test_backward_reuses_kept_activations_only_for_the_same_frames(torch, wk):
+    """wskpn_forward_train keeps the layer inputs of the BF16 tensor-core
+    path; wskpn_backward reuses them for the same frame buffers and
+    recomputes otherwise.  The two give bit-identical gradients (the same
+    kernels on the same values), the kept forward's z equals wskpn_logits',
+    and a backward over other frames does not see the kept activations."""
+    B, H, W = 2, 48, 80
+    wb = synth.make_weights(seed=13)
+    d = wk.Denoiser(wb, precision="bf16", max_batch=B, max_hw=(H, W))
+    devA = to_dev(stack_frames([synth.make_frame(H, W, 340 + b) for b in range(B)]))
+    devB = to_dev(stack_frames([synth.make_frame(H, W, 350 + b) for b in range(B)]))
+    clone = lambda dev: {k: v.clone() for k, v in dev.items()}
+    G = torch.from_numpy(np.random.default_rng(13).standard_normal((B, 3, H, W)).astype(np.float32)).cuda()
+    out, z = d.forward_train(*args(devA))
+    assert torch.equal(z, d.logits(*args(devA)))
+    dw_kept, dz_kept = d.backward(*args(devA), z, G, want_dz=True)     # kept activations
+    dw_re, dz_re = d.backward(*args(clone(devA)), z, G, want_dz=True)  # other pointers: recomputed
+    assert torch.equal(dw_kept, dw_re) and torch.equal(dz_kept, dz_re)
+    d.forward_train(*args(devA))
+    dw_b = d.backward(*args(devB), z, G)[0]  # other frames: recomputed from B
+    dw_b2 = d.backward(*args(clone(devB)), z, G)[0]
+    assert torch.equal(dw_b, dw_b2) and not torch.equal(dw_b, dw_kept)
+    assert d.device_status() == 0
+
+
 @pytest.mark.parametrize("KS,six", [(5, False), (3, False), (5, True)])
 def test_tensor_core_gradients_match_fp32(torch, wk, KS, six):
     """Input and weight gradients on the tensor cores (default) against the
