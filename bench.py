@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the 720p / 1440p runs")
     p.add_argument("--no-variants", action="store_true", help="skip the 6-block network timing")
+    p.add_argument("--train-keep", action="store_true",
+                   help="with --train-only: also time the step with the activations kept")
     p.add_argument("--train-only", action="store_true",
                    help="time only the training step (16 crops of 256 x 256) and print its line")
     p.add_argument("--serve-requests", type=int, default=4096)
@@ -435,14 +437,18 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     pk = peaks()
 
-    def time_training(steps, warmup):
+    def time_training(steps, warmup, keep=False):
         """The differentiation form: one training step on 16 crops of 256 x
         256 (BF16 forward, L1 loss against the mean of 256 noise draws,
-        hand-written backward with the activations recomputed, Adam)."""
+        hand-written backward with the activations recomputed, Adam).  With
+        keep, the forward keeps the layer inputs for the backward instead
+        (WSKPN_TUNE_TRAIN_KEEP = 1)."""
         tb = synth.make_batch(16, 256, 256, seed=5)
         ttg = torch.from_numpy(synth.make_target(tb["clean"], seed=5, draws=256)).to(dev)
         tx = [torch.from_numpy(np.ascontiguousarray(tb[k])).to(dev) for k in keys]
         dt = wk.Denoiser(wb, precision="bf16", max_batch=16, max_hw=(256, 256))
+        if keep:
+            dt.set_tuning(11, 1)
         t_it = 1
 
         def train_step():
@@ -464,15 +470,20 @@ def main():
         torch.cuda.synchronize()
         ms_t = e0.elapsed_time(e1) / steps
         dt.close()
-        return {"precision": "bf16", "ms_per_step": ms_t, "crops_per_s": 16e3 / ms_t}
+        return {"precision": "bf16", "activations": "kept" if keep else "recomputed", "ms_per_step": ms_t,
+                "crops_per_s": 16e3 / ms_t}
 
     if args.train_only:
         # the differentiation form alone (for profiling its launches)
         r = time_training(args.steps, args.warmup)
+        rk = time_training(args.steps, args.warmup, keep=True) if args.train_keep else None
         if rank == 0:
-            print(json.dumps({"metric": "training step ms (16 crops of 256 x 256, BF16)", "value": r["ms_per_step"],
-                              "unit": "ms/step", "steps": args.steps, "warmup": args.warmup,
-                              "higher_is_better": False, "crops_per_s": r["crops_per_s"], "data": "synthetic"}))
+            line = {"metric": "training step ms (16 crops of 256 x 256, BF16, activations recomputed)",
+                    "value": r["ms_per_step"], "unit": "ms/step", "steps": args.steps, "warmup": args.warmup,
+                    "higher_is_better": False, "crops_per_s": r["crops_per_s"], "data": "synthetic"}
+            if rk:
+                line["kept_activations"] = rk
+            print(json.dumps(line))
         return
 
     def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS, clk=None):
@@ -600,6 +611,7 @@ def main():
             del r
         variants["conv3x3_1920x1080"] = c3
         variants["training_step_16x256x256"] = time_training(max(5, args.steps // 4), 3)
+        variants["training_step_16x256x256_kept_activations"] = time_training(max(5, args.steps // 4), 3, keep=True)
     if not args.no_variants:
         # the multi-resolution variant (U-Net, 3 levels, kernels 3 and 5, Eq. 7), FP32
         from paper_2202_05977_b300.multires import MultiResDenoiser

@@ -212,12 +212,13 @@ wskpn_status wskpn_decode_fuse_bwd(const float* z, const float* radiance, const 
 
 /* Forward pass for training: out [batch][3][h][w] as wskpn_denoise, and the
  * network output z_saved [batch][2M][h][w] (device, caller-owned) that
- * wskpn_backward needs.  BF16 context on the tensor-core training path
- * (default tuning, batch <= 16): the layer inputs are written to the
- * context's training workspace (allocated by the first training call) and
- * kept for a wskpn_backward over the same frame buffers (pointers), batch
- * and size; the values are those of wskpn_logits.  The frame buffers must
- * not change in between.  Other contexts keep no activation. */
+ * wskpn_backward needs.  With WSKPN_TUNE_TRAIN_KEEP = 1 (BF16 context on
+ * the tensor-core training path, batch <= 16) the layer inputs are written
+ * to the context's training workspace (allocated by the first training
+ * call) and kept for a wskpn_backward over the same frame buffers
+ * (pointers), batch and size; the values are those of wskpn_logits, and the
+ * frame buffers must not change in between.  Otherwise (default) no
+ * activation is kept. */
 wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, int h, int w,
                                  float* out, float* z_saved, void* stream);
 
@@ -227,8 +228,9 @@ wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int 
  * those kept by wskpn_forward_train (see there), else recomputed from the
  * frames.  BF16 context (default WSKPN_TUNE_TRAIN_RECOMPUTE = 1): kept or
  * recomputed with the context's own tensor-core convolutions; the input
- * gradient of each layer is a tensor-core convolution of the gradient (BF16
- * hi/lo pairs) with the transposed, flipped BF16 weights, the weight
+ * gradient of each layer is a tensor-core convolution of the gradient
+ * (carried between layers as BF16) with the transposed, flipped BF16
+ * weights, the weight
  * gradient a tensor-core GEMM over the pixels (BF16 operands), both with
  * FP32 accumulation and a fixed summation order (the result does not
  * depend on scheduling).  FP32 and FP8 contexts, and the other tuning
@@ -492,7 +494,7 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     the activations and forms the input gradients: 1 = activations with
  *     the context's own tensor-core convolutions, as the forward computed
  *     them, and each layer's input gradient as a tensor-core convolution of
- *     the gradient (BF16 hi/lo pairs) with the transposed, flipped BF16
+ *     the gradient (BF16 values) with the transposed, flipped BF16
  *     weights (default; needs TC_SPLIT = 1); 2 = the same activations, input
  *     gradients in FP32 SIMT with the FP32 weights; 0 = everything in FP32
  *     with the FP32 weights (the ReLU masks are then those of the FP32
@@ -524,6 +526,10 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     in the next tensor-core convolution launch of the context (one launch;
  *     the key then reads 0 again), each epilogue warp first waits on a
  *     barrier that nothing signals, so that its wait limit expires.
+ *   WSKPN_TUNE_TRAIN_KEEP (BF16 only, with TRAIN_RECOMPUTE = 1): 0 = the
+ *     backward recomputes the layer inputs (default); 1 = wskpn_forward_train
+ *     keeps them for the backward (see there), at 4 bytes per channel of
+ *     every layer input per pixel (0.64 GB for 16 crops of 256 x 256).
  * Errors: EINVAL for an unknown key or value. */
 #define WSKPN_TUNE_TC_SPLIT 2
 #define WSKPN_TUNE_TRAIN_RECOMPUTE 3
@@ -534,6 +540,7 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
 #define WSKPN_TUNE_TC_SPLIT_LAYERS 8
 #define WSKPN_TUNE_WAIT_LIMIT_US 9
 #define WSKPN_TUNE_WAIT_PROBE 10
+#define WSKPN_TUNE_TRAIN_KEEP 11
 wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value);
 
 /* Reads and clears the context's device status word after synchronising

@@ -23,6 +23,7 @@ TUNE_HOST_FIRST_BAND = 6
 TUNE_HOST_LAST_BAND = 7
 TUNE_WAIT_LIMIT_US = 9
 TUNE_WAIT_PROBE = 10
+TUNE_TRAIN_KEEP = 11
 
 
 class Config(ctypes.Structure):

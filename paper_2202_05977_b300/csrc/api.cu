@@ -79,18 +79,30 @@ size_t n_weights_of(const wskpn_config* c) {
     return n;
 }
 
+// Weight images from the master weights: the configured precision's now;
+// the FP32 SIMT images of a BF16 / FP8 context (used only by its FP32
+// training and calibration paths) when one of those next needs them.
 wskpn_status ctx_repack(wskpn_ctx* ctx, cudaStream_t st) {
+    const wskpn_config& c = ctx->cfg;
+    ctx->simt_stale = true;
+    if (c.prec == WSKPN_FP32) return ctx_simt_weights(ctx, st);
+    for (int l = 0; l < c.n_layers; ++l) {
+        const wskpn_status s = tc_pack_layer(ctx, l, st);
+        if (s) return s;
+    }
+    return WSKPN_OK;
+}
+
+wskpn_status ctx_simt_weights(wskpn_ctx* ctx, cudaStream_t st) {
+    if (!ctx->simt_stale) return WSKPN_OK;
     const wskpn_config& c = ctx->cfg;
     for (int l = 0; l < c.n_layers; ++l) {
         Layer& L = ctx->layers[l];
-        wskpn_status s = launch_pack_simt(ctx->d_master + L.woff, ctx->d_master + L.boff, L.cin, L.cout,
-                                          c.conv_ks, L.w32, L.b32, st, ctx->err);
+        const wskpn_status s = launch_pack_simt(ctx->d_master + L.woff, ctx->d_master + L.boff, L.cin, L.cout,
+                                                c.conv_ks, L.w32, L.b32, st, ctx->err);
         if (s) return s;
-        if (c.prec != WSKPN_FP32) {
-            s = tc_pack_layer(ctx, l, st);
-            if (s) return s;
-        }
     }
+    ctx->simt_stale = false;
     return WSKPN_OK;
 }
 
@@ -125,6 +137,8 @@ static wskpn_status logits_fp32(wskpn_ctx* ctx, const wskpn_frame* frames, int B
     wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), 0, st, ctx->err);
     if (s) return s;
     prof_mark(ctx, 1, st);
+    s = ctx_simt_weights(ctx, st);
+    if (s) return s;
     std::vector<const float*> in(B);
     std::vector<float*> out(B);
     for (int l = 1; l <= c.n_layers; ++l) {
@@ -649,6 +663,10 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
     }
     if (key == WSKPN_TUNE_WAIT_PROBE && (value == 0 || value == 1) && ctx->cfg.prec != WSKPN_FP32) {
         ctx->wait_probe = value;
+        return WSKPN_OK;
+    }
+    if (key == WSKPN_TUNE_TRAIN_KEEP && (value == 0 || value == 1)) {
+        ctx->train_keep = value;
         return WSKPN_OK;
     }
     ctx->err = "wskpn_set_tuning: unknown key or value";

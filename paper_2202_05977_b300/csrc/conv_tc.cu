@@ -90,11 +90,17 @@ struct TcArgs {
     uint64_t wait_ns;        // limit of every wait but the drains
     int probe;               // test hook: the epilogue first waits on a barrier nothing signals
     // GM kernels (input gradients of the training step): the ReLU derivative
-    // of the layer input, NHWC BF16 hi/lo laid out like out (x = hi + lo > 0
-    // keeps a gradient value), and per-warp bias-gradient sums
-    // bias_part [gridDim.x * 4][64] of the masked values
-    const void* gmask;
+    // of the layer input as bits, two words per pixel (bit c set: channel c
+    // positive, as written through relu_bits by the layer that produced it),
+    // and per-warp bias-gradient sums bias_part [gridDim.x * 4][64] of the
+    // masked values
+    const uint32_t* gbits;
     float* bias_part;
+    // BF16 ReLU layers, optional: two words per pixel, bit out_c0 + c set
+    // when the stored hi half of output channel c is positive (then x = hi +
+    // lo > 0, and only then); this launch writes the words its channels
+    // occupy
+    uint32_t* relu_bits;
 };
 
 // ------------------------------------------------------------- primitives
@@ -618,17 +624,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const size_t pix = ((size_t)b * a.H + y) * a.W + x;
                 // this group's first channel of the pixel (hi half for BF16)
                 uint8_t* const pbase = static_cast<uint8_t*>(a.out) + pix * pix_bytes + (size_t)a.out_c0 * (FP8 ? 1 : 2);
-                // GM: hi halves of the layer input at this pixel, loaded before
-                // the accumulators are read.  The layer input is a ReLU output
-                // (x >= 0) stored as hi + lo with hi = bf16(x), so x > 0 exactly
-                // when hi is positive: bits in [0x0001, 0x7F80]
-                uint4 mk[GM ? COUT_P / 8 : 1];
+                // GM: the layer input's positive channels at this pixel, loaded
+                // before the accumulators are read
+                uint64_t mbits = 0;
                 if constexpr (GM) {
-                    const uint4* mh = reinterpret_cast<const uint4*>(
-                        static_cast<const uint8_t*>(a.gmask) + pix * pix_bytes + (size_t)a.out_c0 * 2);
-#pragma unroll
-                    for (int k = 0; k < COUT_P / 8; ++k) mk[k] = valid ? mh[k] : make_uint4(0u, 0u, 0u, 0u);
+                    if (valid) {
+                        const uint2 m = reinterpret_cast<const uint2*>(a.gbits)[pix];
+                        mbits = (((uint64_t)m.y << 32) | m.x) >> a.out_c0;
+                    }
                 }
+                uint64_t rbits = 0;  // relu_bits of this pixel (channels of this launch)
 #pragma unroll
                 for (int c16 = 0; c16 < COUT_P / 16; ++c16) {
                     float v[16];
@@ -659,12 +664,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     }
                     if constexpr (GM) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const uint32_t m = j & 1 ? (j & 2 ? mk[2 * c16 + j / 4].w : mk[2 * c16 + j / 4].y)
-                                                     : (j & 2 ? mk[2 * c16 + j / 4].z : mk[2 * c16 + j / 4].x);
-                            if ((m & 0xFFFFu) - 1u >= 0x7F80u) v[2 * j] = 0.f;
-                            if ((m >> 16) - 1u >= 0x7F80u) v[2 * j + 1] = 0.f;
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            if (!((mbits >> (c16 * 16 + j)) & 1ull)) v[j] = 0.f;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) bsum[c16 * 16 + j] += v[j];
                     }
@@ -691,6 +692,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         const uint4* src = reinterpret_cast<const uint4*>(h2);
                         dst[0] = src[0];
                         dst[1] = src[1];
+                        if (a.relu_bits) {
+                            // a positive finite BF16 has bits in [0x0001, 0x7F80]
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const uint32_t hw = reinterpret_cast<const uint32_t*>(h2)[j];
+                                if ((hw & 0xFFFFu) - 1u < 0x7F80u) rbits |= 1ull << (c16 * 16 + 2 * j);
+                                if ((hw >> 16) - 1u < 0x7F80u) rbits |= 1ull << (c16 * 16 + 2 * j + 1);
+                            }
+                        }
                         if (a.split_out) {
                             // residual v - bf16(v), itself rounded to BF16
                             __nv_bfloat162 l2[8];
@@ -704,6 +714,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             dlo[0] = slo[0];
                             dlo[1] = slo[1];
                         }
+                    }
+                }
+                if constexpr (!FP8) {
+                    if (a.relu_bits && valid) {
+                        uint32_t* rb = a.relu_bits + pix * 2 + (a.out_c0 >> 5);
+                        rb[0] = (uint32_t)rbits;
+                        if (COUT_P > 32) rb[1] = (uint32_t)(rbits >> 32);
                     }
                 }
                 if (a.zero_n && valid) {  // storage padding past the layer's channels
@@ -998,11 +1015,11 @@ static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8
     WSKPN_TC_CASE(ks_, 32, 2, 1, true, 2) WSKPN_TC_CASE(ks_, 48, 2, 2, true, 1)                            \
     WSKPN_TC_CASE(ks_, 64, 4, 3, true, 2) WSKPN_TC_CASE(ks_, 16, 4, 4, true, 1)                            \
     WSKPN_TC_CASE(ks_, 32, 4, 4, true, 1) WSKPN_TC_CASE(ks_, 64, 4, 4, true, 1)
-// input gradients of the training step (hi/lo gradients, weights transposed
+// input gradients of the training step (BF16 gradients, weights transposed
 // and flipped, the ReLU mask and bias sums in the epilogue): 12 -> 64,
 // 64 -> 48, 48 -> 32, and 64 -> 64 as two 32-channel groups
 #define WSKPN_TC_DGRAD(ks_)                                                                                \
-    WSKPN_TC_GM(ks_, 64, 2, 1) WSKPN_TC_GM(ks_, 48, 8, 4) WSKPN_TC_GM(ks_, 32, 6, 3) WSKPN_TC_GM(ks_, 32, 8, 4)
+    WSKPN_TC_GM(ks_, 64, 1, 1) WSKPN_TC_GM(ks_, 48, 4, 4) WSKPN_TC_GM(ks_, 32, 3, 3) WSKPN_TC_GM(ks_, 32, 4, 4)
 // the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
 // 112-48, 80-32 and the heads 48-5, 32-5
 #define WSKPN_TC_UNET                                                                                      \
@@ -1039,8 +1056,9 @@ struct TcRun {
     int device;
     uint64_t wait_ns = MBAR_WAIT_NS;
     int probe = 0;
-    const void* gmask = nullptr;  // input gradient: ReLU mask and bias sums in the epilogue (TcArgs)
+    const uint32_t* gbits = nullptr;  // input gradient: ReLU mask and bias sums in the epilogue (TcArgs)
     float* bias_part = nullptr;
+    uint32_t* relu_bits = nullptr;    // ReLU layer: positive-channel bits of the output (TcArgs)
     int* grid_out = nullptr;      // receives the grid size (bias_part holds 4 rows per CTA)
 };
 
@@ -1111,15 +1129,20 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     a.status = r.status;
     a.wait_ns = r.wait_ns;
     a.probe = r.probe;
-    a.gmask = r.gmask;
+    a.gbits = r.gbits;
     a.bias_part = r.bias_part;
+    a.relu_bits = r.relu_bits;
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, r.device);
     const int grid = a.ntiles < nsm ? a.ntiles : nsm;
     if (r.grid_out) *r.grid_out = grid;
-    const bool gm = r.gmask != nullptr;
-    if (gm && (fp8 || xf || !r.split_out || r.last || r.relu || !r.bias_part)) {
-        err = "conv_tc: the gradient mask needs a BF16 hi/lo input-gradient layer";
+    const bool gm = r.gbits != nullptr;
+    if (r.relu_bits && (fp8 || xf || r.last || !r.relu || r.out_cp > 64 || r.out_c0 % 32 || (G > 1 && cg != 32))) {
+        err = "conv_tc: ReLU bits need a BF16 ReLU layer of at most 64 channels in 32-channel groups";
+        return WSKPN_EINVAL;
+    }
+    if (gm && (fp8 || xf || r.split_in || r.split_out || r.last || r.relu || !r.bias_part)) {
+        err = "conv_tc: the gradient mask needs a single-BF16 input-gradient layer";
         return WSKPN_EINVAL;
     }
     const TcLaunch launch = select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf, gm);
@@ -1153,8 +1176,9 @@ bool tc_split_all(const wskpn_ctx* ctx) {
     return true;
 }
 
-// One layer of a context's ImportanceNet.
-static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st) {
+// One layer of a context's ImportanceNet (relu_bits: see TcArgs; BF16 only).
+static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st,
+                            uint32_t* relu_bits = nullptr) {
     const wskpn_config& c = ctx->cfg;
     const bool fp8 = c.prec == WSKPN_FP8;
     TcRun r{};
@@ -1182,6 +1206,7 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     r.wait_ns = ctx->wait_ns;
     r.probe = ctx->wait_probe;
     ctx->wait_probe = 0;  // the test hook applies to one launch
+    r.relu_bits = relu_bits;
     return tc_run(r, in, out, B, H, W, st, ctx->err);
 }
 
@@ -1219,7 +1244,7 @@ __global__ void transpose_flip_kernel(const float* __restrict__ w, int Cin, int 
     }
 }
 
-// The tensor-core layer (BF16, hi/lo inputs) of the input gradient of a
+// The tensor-core layer (single BF16 values in and out) of the input gradient of a
 // forward layer with cin -> cout channels: Lt.cin = cout, Lt.cout = cin.
 // EUNSUPPORTED when no kernel is built for its shape (the caller then takes
 // the FP32 path).
@@ -1236,7 +1261,7 @@ wskpn_status tc_dgrad_layer_alloc(Layer& Lt, int KS, int cin, int cout, std::str
     const wskpn_status s = tc_layer_alloc(Lt, KS, false, false, err);
     if (s) return s;
     const int ncc = Lt.cin_p / 16;
-    if (!select_tc_kernel(KS, Lt.cout_p / Lt.groups, 2 * ncc, ncc, false, 0, false, true)) {
+    if (!select_tc_kernel(KS, Lt.cout_p / Lt.groups, ncc, ncc, false, 0, false, true)) {
         err = "tensor-core input gradient: no kernel for this layer shape";
         return WSKPN_EUNSUPPORTED;
     }
@@ -1283,14 +1308,14 @@ wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int
     return tc_run(r, in, out, B, H, W, st, err);
 }
 
-wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, const void* x, float* bias_part,
+wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, const uint32_t* x_bits, float* bias_part,
                           int* nparts, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
                           std::string& err) {
     TcRun r{};
     r.L = &Lt;
     r.KS = KS;
     r.fp8 = false;
-    r.split_in = r.split_out = 1;
+    r.split_in = r.split_out = 0;  // gradients as single BF16 values
     r.last = 0;
     r.relu = 0;
     r.out_cp = Lt.cout_p;
@@ -1298,7 +1323,7 @@ wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, cons
     r.out_qscale = 1.f;
     r.status = status;
     r.device = device;
-    r.gmask = x;
+    r.gbits = x_bits;
     r.bias_part = bias_part;
     int grid = 0;
     r.grid_out = &grid;
@@ -1418,7 +1443,7 @@ wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B,
 // recomputed on the tensor cores exactly as its forward computes them, kept
 // channels-last: xs[l] = NHWC [B][H][W][hi(cin_p) | lo(cin_p)] of layer l.
 wskpn_status tc_recompute_nhwc(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
-                               const std::vector<void*>& xs, cudaStream_t st) {
+                               const std::vector<void*>& xs, cudaStream_t st, const std::vector<uint32_t*>* bits) {
     const wskpn_config& c = ctx->cfg;
     if (c.prec != WSKPN_BF16 || !tc_split_all(ctx) || B > WSKPN_MAX_BATCH) {
         ctx->err = "tc_recompute_nhwc: BF16 contexts with hi/lo activations only, at most 16 frames";
@@ -1429,7 +1454,8 @@ wskpn_status tc_recompute_nhwc(wskpn_ctx* ctx, const wskpn_frame* frames, int B,
     const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * 2 * HW;
     for (int b = 0; b < B; ++b) x0[b] = static_cast<uint8_t*>(xs[0]) + (size_t)b * x0_bytes;
     wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), 2, st, ctx->err);
-    for (int l = 0; !s && l + 1 < c.n_layers; ++l) s = conv_tc(ctx, l, xs[l], xs[l + 1], B, H, W, st);
+    for (int l = 0; !s && l + 1 < c.n_layers; ++l)
+        s = conv_tc(ctx, l, xs[l], xs[l + 1], B, H, W, st, bits ? (*bits)[l + 1] : nullptr);
     return s;
 }
 
@@ -1486,6 +1512,7 @@ extern "C" wskpn_status wskpn_calibrate(wskpn_ctx* ctx, const wskpn_frame* frame
     std::vector<void*> x0(batch);
     for (int b = 0; b < batch; ++b) x0[b] = buf[0] + (size_t)b * c.widths[0] * HW;
     s = launch_prep(frames, batch, h, w, c.gamma, c.depth_near, c.depth_far, x0.data(), 0, st, ctx->err);
+    if (!s) s = ctx_simt_weights(ctx, st);
     std::vector<const float*> in(batch);
     std::vector<float*> out(batch);
     for (int l = 0; l < c.n_layers && !s; ++l) {

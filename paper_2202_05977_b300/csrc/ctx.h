@@ -65,6 +65,8 @@ struct wskpn_ctx {
     int wait_probe = 0;                 // test hook for the next convolution launch (WSKPN_TUNE_WAIT_PROBE)
     unsigned tc_split_layers = 0xFFFFFFFFu;  // of those, the layer inputs split (bit l; WSKPN_TUNE_TC_SPLIT_LAYERS)
     int fp8_split = 1;  // e4m3 activations and weights as hi/lo pairs (WSKPN_TUNE_FP8_SPLIT)
+    bool simt_stale = true;      // FP32 SIMT weight images older than the master weights
+    int train_keep = 0;          // wskpn_forward_train keeps the layer inputs for the backward (WSKPN_TUNE_TRAIN_KEEP)
     int train_tc_recompute = 1;  // backward on the tensor cores: 1 recompute + input gradients, 2 recompute only (WSKPN_TUNE_TRAIN_RECOMPUTE)
     int host_bands = 0;         // bands of the host-buffer pipeline, 0 = automatic (WSKPN_TUNE_HOST_BANDS)
     int host_first_pct = 100;   // first band's height in % of the others (WSKPN_TUNE_HOST_FIRST_BAND)
@@ -82,6 +84,8 @@ wskpn_status ctx_init(wskpn_ctx* ctx, const float* host_weights);
 void ctx_free(wskpn_ctx* ctx);
 void ctx_free_train(wskpn_ctx* ctx);
 wskpn_status ctx_repack(wskpn_ctx* ctx, cudaStream_t st);
+// Packs the FP32 SIMT weight images if the master weights changed since.
+wskpn_status ctx_simt_weights(wskpn_ctx* ctx, cudaStream_t st);
 // stage profiling hooks (no-ops unless profiling is enabled)
 void prof_begin(wskpn_ctx* ctx, cudaStream_t st);
 void prof_mark(wskpn_ctx* ctx, int boundary, cudaStream_t st);  // boundary 1..n_layers+2
@@ -104,8 +108,11 @@ wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string
 // every layer input is (the training recompute needs all of them split).
 int tc_split_of(const wskpn_ctx* ctx, int l);
 bool tc_split_all(const wskpn_ctx* ctx);
+// x_0 .. x_{L-1} as NHWC hi/lo into xs[l]; with bits, also the positive-
+// channel bits of x_1 .. x_{L-1} into (*bits)[l] (two words per pixel).
 wskpn_status tc_recompute_nhwc(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
-                               const std::vector<void*>& xs, cudaStream_t st);
+                               const std::vector<void*>& xs, cudaStream_t st,
+                               const std::vector<uint32_t*>* bits = nullptr);
 wskpn_status tc_recompute_acts(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,
                                const std::vector<std::vector<float*>>& acts, cudaStream_t st);
 // BF16 tensor-core layers outside a context (hi/lo activations in and out)
@@ -117,11 +124,11 @@ wskpn_status tc_dgrad_layer_pack(Layer& Lt, int KS, const float* w, float* wt, c
 wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int out_cp, int out_c0, int last,
                           int relu, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
                           std::string& err);
-// The input gradient gx (NHWC hi/lo, Lt.cout_p channels) of a layer from its
-// output gradient g through Lt, times the ReLU derivative of the layer input
-// x (NHWC hi/lo like gx), with per-warp bias sums of the result in
-// bias_part [*nparts][64] (channels of gx).
-wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, const void* x, float* bias_part,
+// The input gradient gx (NHWC BF16, Lt.cout_p channels) of a layer from its
+// output gradient g (NHWC BF16) through Lt, times the ReLU derivative of the layer input
+// (x_bits: its positive-channel bits, two words per pixel), with per-warp
+// bias sums of the result in bias_part [*nparts][64] (channels of gx).
+wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, const uint32_t* x_bits, float* bias_part,
                           int* nparts, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
                           std::string& err);
 }  // namespace wskpn

@@ -940,16 +940,33 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_bwd1_kernel(const
         for (int x = 0; x < dfv::SEG; ++x) gv[x] = st.g[x][ch];
         store_row8<VEC>(sc + (size_t)(2 * M + ch) * HW, H, W, gy, gx0, gv);
     }
-    for (int i = 0; i < M; ++i) {
-        float l[dfv::SEG], o[dfv::SEG];
-        load_row8<VEC>(l, z + (size_t)(M + i) * HW, H, W, gy, gx0);
-        const float* dp = sc + (size_t)(M + i) * HW + (size_t)gy * W + gx0;
+    // three sizes per round, every load of a round issued before any use
+    constexpr int GRP = 3;
+    for (int i0 = 0; i0 < M; i0 += GRP) {
+        float l[GRP][dfv::SEG], dv[GRP][dfv::SEG];
 #pragma unroll
-        for (int x = 0; x < dfv::SEG; ++x) {
-            const float dv = gx0 + x < W ? dp[x] : 0.f;
-            o[x] = ex2_approx(fmaf(l[x], dfv::LOG2E, -st.cl[x])) * (dv - st.Sd[x]);
+        for (int j = 0; j < GRP; ++j) {
+            if (i0 + j >= M) break;
+            load_row8<VEC>(l[j], z + (size_t)(M + i0 + j) * HW, H, W, gy, gx0);
+            const float* dp = sc + (size_t)(M + i0 + j) * HW + (size_t)gy * W + gx0;
+            if (VEC && gx0 + dfv::SEG <= W) {
+                const float4 u = reinterpret_cast<const float4*>(dp)[0], v = reinterpret_cast<const float4*>(dp)[1];
+                dv[j][0] = u.x, dv[j][1] = u.y, dv[j][2] = u.z, dv[j][3] = u.w;
+                dv[j][4] = v.x, dv[j][5] = v.y, dv[j][6] = v.z, dv[j][7] = v.w;
+            } else {
+#pragma unroll
+                for (int x = 0; x < dfv::SEG; ++x) dv[j][x] = gx0 + x < W ? dp[x] : 0.f;
+            }
         }
-        store_row8<VEC>(dz + (size_t)(M + i) * HW, H, W, gy, gx0, o);
+#pragma unroll
+        for (int j = 0; j < GRP; ++j) {
+            if (i0 + j >= M) break;
+            float o[dfv::SEG];
+#pragma unroll
+            for (int x = 0; x < dfv::SEG; ++x)
+                o[x] = ex2_approx(fmaf(l[j][x], dfv::LOG2E, -st.cl[x])) * (dv[j][x] - st.Sd[x]);
+            store_row8<VEC>(dz + (size_t)(M + i0 + j) * HW, H, W, gy, gx0, o);
+        }
     }
 }
 

@@ -65,9 +65,10 @@ struct TrainWs {
     bool wg_ok[WSKPN_MAX_LAYERS] = {};  // layer l's weight gradient has a tensor-core kernel
     float* wt = nullptr;                // transposed weights of one layer (packing scratch)
     float* zero_bias = nullptr;         // [64] zeros
-    void* gpack = nullptr;              // gradient as NHWC BF16 hi/lo [B][H][W][2 cp], two buffers
+    void* gpack = nullptr;              // gradient as NHWC BF16 [B][H][W][cp], two buffers
     void* gpack2 = nullptr;
     void* xnhwc = nullptr;              // layer inputs x_0 .. x_{L-1}, NHWC BF16 hi/lo, layer after layer
+    uint32_t* xbits = nullptr;          // their positive-channel bits [L][px][2] (x_1 .. x_{L-1} used)
     size_t x_off[WSKPN_MAX_LAYERS] = {};  // byte offsets in xnhwc
     size_t x_bytes = 0;
     bool all_tc = false;                // every layer has its tensor-core gradient kernels
@@ -107,6 +108,7 @@ static void free_train(TrainWs* t) {
     cudaFree(t->zero_bias);
     cudaFree(t->gpack);
     cudaFree(t->xnhwc);
+    cudaFree(t->xbits);
     cudaFree(t->gpack2);
     cudaFree(t->bias_part);
     cudaFree(t->wg_part);
@@ -195,9 +197,9 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
 }
 
 // Gradient planes g (planar FP32 [C][HW] per frame, C <= CMAX) written
-// channels-last as BF16 hi/lo pairs nhwc [B][HW][hi(cp) | lo(cp)] (channels
-// C .. cp - 1 zero, lo = bf16(g - bf16(g))): the input of a tensor-core
-// input-gradient convolution, whose hi half also feeds the weight gradient.
+// channels-last as BF16 nhwc [B][HW][cp] (channels C .. cp - 1 zero): the
+// input of a tensor-core input-gradient convolution and of the weight
+// gradient.
 // One block per tile of 4096 / CMAX pixels of one frame, transposed through
 // shared memory so that both layouts are read and written in whole runs
 // (every thread issues its 16 loads before storing any).  bias_part
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(256) grad_pack_kernel(PtrBatch<const float*> g
         }
     }
     __syncthreads();
-    // per (pixel, 8-channel chunk): the hi/lo pair as two 16-byte stores
+    // per (pixel, 8-channel chunk): one 16-byte store of BF16 values
     const int nq = cp / 8;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -244,17 +246,11 @@ __global__ void __launch_bounds__(256) grad_pack_kernel(PtrBatch<const float*> g
         const int i = k / nq, q = k % nq;
         const size_t p = p0 + i;
         if (p >= HW) continue;
-        __nv_bfloat162 h[4], l[4];
+        __nv_bfloat162 h[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float a = sg[q * 8 + 2 * j][i], c = sg[q * 8 + 2 * j + 1][i];
-            h[j] = __floats2bfloat162_rn(a, c);
-            const float2 hf = __bfloat1622float2(h[j]);
-            l[j] = __floats2bfloat162_rn(a - hf.x, c - hf.y);
-        }
-        uint4* dst = nhwc + ((size_t)b * HW + p) * (size_t)(cp / 4);  // 2 cp BF16 = cp / 4 uint4
+        for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(sg[q * 8 + 2 * j][i], sg[q * 8 + 2 * j + 1][i]);
+        uint4* dst = nhwc + ((size_t)b * HW + p) * (size_t)(cp / 8);  // cp BF16 = cp / 8 uint4
         dst[q] = *reinterpret_cast<const uint4*>(h);
-        dst[cp / 8 + q] = *reinterpret_cast<const uint4*>(l);
     }
     // per-channel tile sums: TPC threads per channel, 16 pixels each in order
     {
@@ -286,7 +282,8 @@ __global__ void bias_from_tiles_kernel(const float* __restrict__ part, int ntile
 
 
 // Packs the gradient of a layer with C output channels (planar FP32) as
-// NHWC BF16 hi/lo pairs with cp channels, then writes its bias gradient db.
+// NHWC BF16 with cp channels, then writes its bias gradient db (from the
+// FP32 values).
 static wskpn_status launch_grad_pack(const float* const* g, int B, int C, int cp, size_t HW, void* nhwc,
                                      float* bias_part, float* db, cudaStream_t st, std::string& err) {
     if (C > cp || cp > 64 || cp % 16 || B > WSKPN_MAX_BATCH) {
@@ -409,11 +406,12 @@ wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int 
     }
     const wskpn_config& c = ctx->cfg;
     cudaStream_t st = (cudaStream_t)stream;
-    // BF16 with the tensor-core backward: the layer inputs x_0 .. x_{L-1} go
-    // to the training workspace (NHWC hi/lo, where the backward reads them)
-    // instead of the inference ping-pong buffers; same kernels, same values.
-    const bool keep = c.prec == WSKPN_BF16 && tc_split_all(ctx) && ctx->train_tc_recompute == 1 &&
-                      batch >= 1 && batch <= WSKPN_MAX_BATCH;
+    // Kept activations (BF16, tensor-core backward): the layer inputs x_0 ..
+    // x_{L-1} go to the training workspace (NHWC hi/lo, where the backward
+    // reads them) instead of the inference ping-pong buffers; same kernels,
+    // same values.
+    const bool keep = ctx->train_keep && c.prec == WSKPN_BF16 && tc_split_all(ctx) &&
+                      ctx->train_tc_recompute == 1 && batch >= 1 && batch <= WSKPN_MAX_BATCH;
     wskpn_status s = WSKPN_OK;
     TrainWs* t = nullptr;
     if (keep) {
@@ -428,10 +426,15 @@ wskpn_status wskpn_forward_train(wskpn_ctx* ctx, const wskpn_frame* frames, int 
     }
     if (t) {
         if (!t->xnhwc) WSKPN_TRY_ALLOC(t->xnhwc, t->x_bytes);
+        if (!t->xbits) WSKPN_TRY_ALLOC(t->xbits, (size_t)c.n_layers * t->px * 2 * sizeof(uint32_t));
         const int L = c.n_layers;
         std::vector<void*> xs(L);
-        for (int l = 0; l < L; ++l) xs[l] = static_cast<uint8_t*>(t->xnhwc) + t->x_off[l];
-        s = tc_recompute_nhwc(ctx, frames, batch, h, w, xs, st);
+        std::vector<uint32_t*> bits(L);
+        for (int l = 0; l < L; ++l) {
+            xs[l] = static_cast<uint8_t*>(t->xnhwc) + t->x_off[l];
+            bits[l] = t->xbits + (size_t)l * t->px * 2;
+        }
+        s = tc_recompute_nhwc(ctx, frames, batch, h, w, xs, st, &bits);
         if (!s) s = tc_conv_layer(ctx, L - 1, xs[L - 1], z_saved, batch, h, w, st);
         if (s) return s;
         t->kept = true;
@@ -506,10 +509,15 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
     for (int b = 0; kept && b < batch; ++b) kept = same_frames(t->kept_frames[b], frames[b]);
     if (tc_bwd && !kept) {
         if (!t->xnhwc) WSKPN_TRY_ALLOC(t->xnhwc, t->x_bytes);
+        if (!t->xbits) WSKPN_TRY_ALLOC(t->xbits, (size_t)L * t->px * 2 * sizeof(uint32_t));
         std::vector<void*> xs(L);
-        for (int l = 0; l < L; ++l) xs[l] = xn(l);
+        std::vector<uint32_t*> bits(L);
+        for (int l = 0; l < L; ++l) {
+            xs[l] = xn(l);
+            bits[l] = t->xbits + (size_t)l * t->px * 2;
+        }
         t->kept = false;  // overwritten with this call's frames
-        s = tc_recompute_nhwc(ctx, frames, batch, h, w, xs, st);
+        s = tc_recompute_nhwc(ctx, frames, batch, h, w, xs, st, &bits);
         if (s) return s;
     } else if (!tc_bwd) {
         if (!t->acts) WSKPN_TRY_ALLOC(t->acts, t->acts_floats * sizeof(float));
@@ -526,6 +534,10 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
             s = tc_recompute_acts(ctx, frames, batch, h, w, acts, st);
             if (s) return s;
         }
+        if (!on_tc) {
+            s = ctx_simt_weights(ctx, st);
+            if (s) return s;
+        }
         for (int l = 1; l < L && !on_tc; ++l) {
             for (int b = 0; b < batch; ++b) {
                 in[b] = act(l - 1, b);
@@ -538,11 +550,13 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         }
     }
     // 3. layer by layer: weight gradient, then the masked input gradient.
-    //    Tensor cores: the gradient is packed as NHWC BF16 hi/lo pairs; the
-    //    weight gradient is a GEMM over the pixels of the hi halves of layer
-    //    input and gradient, the input gradient a convolution with the
-    //    transposed, flipped BF16 weights, then the ReLU mask (from the NHWC
-    //    layer input).  Otherwise FP32 SIMT (mask fused into the conv).
+    //    Tensor cores: the gradient is packed as NHWC BF16 (one value per
+    //    channel: the GEMMs take BF16 operands, FP32 sums); the weight
+    //    gradient is a GEMM over the pixels of the layer input's hi half and
+    //    the gradient, the input gradient a convolution with the transposed,
+    //    flipped BF16 weights whose epilogue applies the ReLU mask (from the
+    //    layer input's bits) and forms the bias sums.  Otherwise FP32 SIMT
+    //    (mask fused into the conv).
     auto cpad = [&](int ch) { return (ch + 15) / 16 * 16; };
     std::vector<const float*> gy(batch), xs(batch), mask(batch);
     std::vector<float*> gx(batch);
@@ -552,7 +566,7 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         WSKPN_TRY_ALLOC(t->gB, t->g_floats * sizeof(float));
     }
     float* gbuf[2] = {t->gA, t->gB};
-    void* gcur = t->gpack;  // tensor cores: gy of the current layer, NHWC hi/lo
+    void* gcur = t->gpack;  // tensor cores: gy of the current layer, NHWC BF16
     if (tc_bwd) {
         // Transposed weight images first: the input-gradient conv is launched
         // as a programmatic dependent of the kernel before it and loads its
@@ -563,7 +577,7 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
                                     ctx->err);
             if (s) return s;
         }
-        // dz -> NHWC hi/lo
+        // dz -> NHWC BF16
         s = launch_grad_pack(gy.data(), batch, 2 * M, cpad(2 * M), HW, t->gpack, t->bias_part,
                              dweights + ctx->layers[L - 1].boff, st, ctx->err);
         if (s) return s;
@@ -572,17 +586,17 @@ wskpn_status wskpn_backward(wskpn_ctx* ctx, const wskpn_frame* frames, int batch
         const Layer& Ly = ctx->layers[l];
         if (tc_bwd) {
             const int gcp = cpad(Ly.cout), xcp = cpad(Ly.cin);
-            s = launch_wgrad_tc(xn(l), 2 * xcp, gcur, 2 * gcp, batch, h, w, Ly.cin, Ly.cout, KS, t->wg_part,
+            s = launch_wgrad_tc(xn(l), 2 * xcp, gcur, gcp, batch, h, w, Ly.cin, Ly.cout, KS, t->wg_part,
                                 t->wg_part_floats, dweights + Ly.woff, ctx->d_status, ctx->device, st, ctx->err);
             if (s) return s;
             if (l == 0) break;
-            // input gradient straight to NHWC hi/lo, times the ReLU mask of
+            // input gradient straight to NHWC BF16, times the ReLU mask of
             // x_l, with the bias sums of layer l - 1, in the conv's epilogue
             void* gnext = gcur == t->gpack ? t->gpack2 : t->gpack;
             Layer& Lt = t->lt[l];
             int nparts = 0;
-            s = tc_dgrad_run(Lt, KS, gcur, gnext, xn(l), t->bias_part, &nparts, batch, h, w, ctx->d_status,
-                             ctx->device, st, ctx->err);
+            s = tc_dgrad_run(Lt, KS, gcur, gnext, t->xbits + (size_t)l * t->px * 2, t->bias_part, &nparts, batch, h,
+                             w, ctx->d_status, ctx->device, st, ctx->err);
             if (s) return s;
             bias_from_tiles_kernel<<<Ly.cin, 256, 0, st>>>(t->bias_part, nparts, dweights + ctx->layers[l - 1].boff);
             WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);

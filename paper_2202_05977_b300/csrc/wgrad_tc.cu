@@ -31,6 +31,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -328,27 +329,44 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
     }
 }
 
-// dW[o][c][dy][dx] = sum over the split-K CTAs g (fixed order) of partial
+// dW[o][c][dy][dx] = sum over the split-K CTAs g of partial
 // [group][g][k][o][dx * 16 + c % 16], chunk c / 16 = group * NCC + ci and
 // accumulator k = dy * NCC + ci, or ci * KS + dy with folded vertical taps.
-// Threads walk the partials in their own order (consecutive TMEM lanes), so
-// every read of a CTA's partials is coalesced; the few sums are scattered to
-// dW, and lanes of shifts >= KS or padding channels are skipped.
-__global__ void wgrad_tc_reduce_kernel(const float* __restrict__ part, int Gk, int groups, int KS, int NCC, int CPG,
-                                       int fold, int Cin, int Cout, float* __restrict__ dw) {
+// A block takes 32 consecutive partial entries (one warp-wide coalesced
+// read per CTA g); warp w sums the CTAs g = w, w + 8, ... in that order and
+// the 8 warp sums are added in warp order, so the result does not depend on
+// scheduling.  Entries of shifts >= KS or padding channels are skipped.
+constexpr int WG_RED_SLICES = 8;
+__global__ void __launch_bounds__(32 * WG_RED_SLICES) wgrad_tc_reduce_kernel(const float* __restrict__ part, int Gk,
+                                                                             int groups, int KS, int NCC, int CPG,
+                                                                             int fold, int Cin, int Cout,
+                                                                             float* __restrict__ dw) {
+    __shared__ float red[WG_RED_SLICES][33];
     const size_t blk = (size_t)KS * NCC * CPG * 128;  // floats of one CTA's partials
     const size_t n = (size_t)groups * blk;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int row = (int)(i % 128), o = (int)((i / 128) % CPG), k = (int)((i / (128 * (size_t)CPG)) % (KS * NCC));
-        const int grp = (int)(i / blk);
-        const int dx = row / 16, c16 = row % 16;
-        const int dy = fold ? k % KS : k / NCC, ci = fold ? k / KS : k % NCC;
-        const int c = (grp * NCC + ci) * 16 + c16;
-        if (dx >= KS || c >= Cin || o >= Cout) continue;
-        const float* p = part + (size_t)grp * Gk * blk + (i % blk);
+    const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    for (size_t base = (size_t)blockIdx.x * 32; base < n; base += (size_t)gridDim.x * 32) {
+        const size_t i = base + lane;
         float s = 0.f;
-        for (int g = 0; g < Gk; ++g) s += p[(size_t)g * blk];
-        dw[(((size_t)o * Cin + c) * KS + dy) * KS + dx] = s;
+        if (i < n) {
+            const float* p = part + (i / blk) * Gk * blk + (i % blk);
+#pragma unroll 4
+            for (int g = sl; g < Gk; g += WG_RED_SLICES) s += p[(size_t)g * blk];
+        }
+        red[sl][lane] = s;
+        __syncthreads();
+        if (sl == 0 && i < n) {
+            float t = red[0][lane];
+#pragma unroll
+            for (int k = 1; k < WG_RED_SLICES; ++k) t += red[k][lane];
+            const int row = (int)(i % 128), o = (int)((i / 128) % CPG), k = (int)((i / (128 * (size_t)CPG)) % (KS * NCC));
+            const int grp = (int)(i / blk);
+            const int dx = row / 16, c16 = row % 16;
+            const int dy = fold ? k % KS : k / NCC, ci = fold ? k / KS : k % NCC;
+            const int c = (grp * NCC + ci) * 16 + c16;
+            if (dx < KS && c < Cin && o < Cout) dw[(((size_t)o * Cin + c) * KS + dy) * KS + dx] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -489,8 +507,12 @@ wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gc
     a.status = status;
     const WgLaunch launch = select_wg(KS, p.cpg, p.ncc);
     WSKPN_CUDA_TRY(launch(xm, gm, a, dim3(p.gk, p.groups), p.smem, st), err);
-    wgrad_tc_reduce_kernel<<<148 * 4, 256, 0, st>>>(part, p.gk, p.groups, KS, p.ncc, p.cpg,
-                                                    wg_fold(KS, p.cpg) ? 1 : 0, Cin, Cout, dw);
+    {
+        const size_t n = (size_t)p.groups * KS * p.ncc * p.cpg * 128;
+        const unsigned blocks = (unsigned)std::min<size_t>((n + 31) / 32, 148 * 16);
+        wgrad_tc_reduce_kernel<<<blocks, 32 * WG_RED_SLICES, 0, st>>>(part, p.gk, p.groups, KS, p.ncc, p.cpg,
+                                                                      wg_fold(KS, p.cpg) ? 1 : 0, Cin, Cout, dw);
+    }
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
