@@ -340,15 +340,19 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
 }
 
 // ----------------------------------------------------------------- kernel
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF, bool GM>
+// EPI: 0 plain epilogue; 1 (GM) input gradient with the ReLU mask of the
+// layer input and bias sums; 2 (RB) also writes the output's ReLU bits.
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF, int EPI>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
+    constexpr bool GM = EPI == 1, RB = EPI == 2;
     constexpr int PAD = KS / 2;
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
     constexpr int NCB = XF ? KS * COUT_P : COUT_P;        // TMEM columns of one output row's accumulators
     constexpr int TPX = XF ? tc::BM - (KS - 1) : tc::BM;  // output pixels per tile row
     static_assert(!XF || COUT_P == 16, "folded taps: 16 output channels");
-    static_assert(!GM || (!XF && !FP8 && COUT_P <= 64), "gradient mask: BF16 hi/lo, at most 64 channels");
+    static_assert(!GM || (!XF && !FP8 && COUT_P <= 64), "gradient mask: BF16, at most 64 channels");
+    static_assert(!RB || (!XF && !FP8 && COUT_P <= 64), "ReLU bits: BF16, at most 64 channels");
     constexpr uint32_t NCOL = tmem_cols<NCB, R>();
     constexpr int ROWS_IN = R + KS - 1;
     constexpr int CPB = chunks_per_box(NCC_IN);
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         const uint4* src = reinterpret_cast<const uint4*>(h2);
                         dst[0] = src[0];
                         dst[1] = src[1];
-                        if (a.relu_bits) {
+                        if constexpr (RB) {
                             // a positive finite BF16 has bits in [0x0001, 0x7F80]
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
@@ -716,8 +720,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         }
                     }
                 }
-                if constexpr (!FP8) {
-                    if (a.relu_bits && valid) {
+                if constexpr (RB) {
+                    if (valid) {
                         uint32_t* rb = a.relu_bits + pix * 2 + (a.out_c0 >> 5);
                         rb[0] = (uint32_t)rbits;
                         if (COUT_P > 32) rb[1] = (uint32_t)(rbits >> 32);
@@ -954,11 +958,11 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     return WSKPN_OK;
 }
 
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF, bool GM = false>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF, int EPI = 0>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
     auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, XF ? xf_rows_per_tile(KS) : tc::rows_per_tile(COUT_P),
-                               WM, XF, GM>;
+                               WM, XF, EPI>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     // programmatic dependent launch: set-up overlaps the previous kernel's
     // tail; the TMA producer waits for that kernel before reading activations
@@ -981,25 +985,29 @@ using TcLaunch = wskpn_status (*)(const CUtensorMap&, const TcArgs&, size_t, int
 // The kernel instantiation for a layer shape: KS, output channels of one
 // group, input chunks per row (hi/lo included), weight-image chunks,
 // precision, e4m3 weight mode, folded taps.  nullptr when none is built.
-static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8, int wm, bool xf, bool gm = false) {
+static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8, int wm, bool xf, bool gm = false,
+                                 bool rb = false) {
     TcLaunch launch = nullptr;
 #define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
-    if (!launch && !xf && !gm && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
+    if (!launch && !xf && !gm && !rb && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
         launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_, false>;
 #define WSKPN_TC_GM(ks_, n_, nin_, nw_)                                                                    \
     if (!launch && gm && !xf && !fp8 && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_)             \
-        launch = launch_tc_t<ks_, n_, nin_, nw_, false, 0, false, true>;
+        launch = launch_tc_t<ks_, n_, nin_, nw_, false, 0, false, 1>;
+#define WSKPN_TC_RB(ks_, n_, nin_, nw_)                                                                    \
+    if (!launch && rb && !gm && !xf && !fp8 && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_)      \
+        launch = launch_tc_t<ks_, n_, nin_, nw_, false, 0, false, 2>;
     // the BF16 last layer 64 -> 16 with folded horizontal taps
     // (hi/lo activations, or single BF16 values when the split is tuned off)
-    if (xf && !gm && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
-    if (xf && !gm && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
-    if (xf && !gm && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
-    if (xf && !gm && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
+    if (xf && !gm && !rb && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
+    if (xf && !gm && !rb && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
+    if (xf && !gm && !rb && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
+    if (xf && !gm && !rb && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
     // e4m3 hi/lo (three products per chunk) and single-term
-    if (xf && !gm && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
-    if (xf && !gm && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
-    if (xf && !gm && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
-    if (xf && !gm && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
+    if (xf && !gm && !rb && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
+    if (xf && !gm && !rb && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
+    if (xf && !gm && !rb && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
+    if (xf && !gm && !rb && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
 #define WSKPN_TC_BF16(ks_)                                                                                 \
     WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
     WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
@@ -1020,6 +1028,11 @@ static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8
 // 64 -> 48, 48 -> 32, and 64 -> 64 as two 32-channel groups
 #define WSKPN_TC_DGRAD(ks_)                                                                                \
     WSKPN_TC_GM(ks_, 64, 1, 1) WSKPN_TC_GM(ks_, 48, 4, 4) WSKPN_TC_GM(ks_, 32, 3, 3) WSKPN_TC_GM(ks_, 32, 4, 4)
+// the training forward's ReLU layers with positive-channel bits (hi/lo
+// activations): 10 -> 32, 32 -> 48, 48 -> 64 and 64 -> 64 as two 32-channel
+// groups
+#define WSKPN_TC_RELU_BITS(ks_) \
+    WSKPN_TC_RB(ks_, 32, 2, 1) WSKPN_TC_RB(ks_, 48, 4, 2) WSKPN_TC_RB(ks_, 64, 6, 3) WSKPN_TC_RB(ks_, 32, 8, 4)
 // the multi-resolution U-Net (3x3, hi/lo activations): 32-32, 48-48, 64-64,
 // 112-48, 80-32 and the heads 48-5, 32-5
 #define WSKPN_TC_UNET                                                                                      \
@@ -1028,9 +1041,11 @@ static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8
     WSKPN_TC_CASE(3, 32, 10, 5, false, 0) WSKPN_TC_CASE(3, 16, 6, 3, false, 0)                             \
     WSKPN_TC_CASE(3, 16, 4, 2, false, 0)
     WSKPN_TC_BF16(5) WSKPN_TC_BF16(3) WSKPN_TC_FP8(5) WSKPN_TC_FP8(3) WSKPN_TC_UNET
-    WSKPN_TC_DGRAD(5) WSKPN_TC_DGRAD(3)
+    WSKPN_TC_DGRAD(5) WSKPN_TC_DGRAD(3) WSKPN_TC_RELU_BITS(5) WSKPN_TC_RELU_BITS(3)
 #undef WSKPN_TC_DGRAD
 #undef WSKPN_TC_GM
+#undef WSKPN_TC_RB
+#undef WSKPN_TC_RELU_BITS
 #undef WSKPN_TC_UNET
 #undef WSKPN_TC_FP8
 #undef WSKPN_TC_BF16
@@ -1145,7 +1160,7 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
         err = "conv_tc: the gradient mask needs a single-BF16 input-gradient layer";
         return WSKPN_EINVAL;
     }
-    const TcLaunch launch = select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf, gm);
+    const TcLaunch launch = select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf, gm, r.relu_bits != nullptr);
     if (!launch) {
         err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M, "
               "64-64 and the multi-resolution U-Net are built";
@@ -1208,6 +1223,14 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     ctx->wait_probe = 0;  // the test hook applies to one launch
     r.relu_bits = relu_bits;
     return tc_run(r, in, out, B, H, W, st, ctx->err);
+}
+
+bool tc_relu_bits_supported(const wskpn_ctx* ctx, int l) {
+    const Layer& L = ctx->layers[l];
+    if (ctx->cfg.prec != WSKPN_BF16 || L.xfold || L.cout_p > 64 || (L.groups > 1 && L.cout_p / L.groups != 32))
+        return false;
+    const int ncc = L.cin_p / 16;
+    return select_tc_kernel(ctx->cfg.conv_ks, L.cout_p / L.groups, 2 * ncc, ncc, false, 0, false, false, true) != nullptr;
 }
 
 wskpn_status tc_conv_layer(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st) {

@@ -101,6 +101,9 @@ wskpn_status check_frames(wskpn_ctx* ctx, const wskpn_frame* frames, int batch, 
 // Layer l of the context's ImportanceNet on the tensor cores (BF16 / FP8
 // activations in the context's layout; the last layer writes planar z).
 wskpn_status tc_conv_layer(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st);
+// Whether layer l (BF16, hi/lo input) has a kernel that also writes its
+// output's ReLU bits (the training backward's input-gradient masks).
+bool tc_relu_bits_supported(const wskpn_ctx* ctx, int l);
 wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W, float* z,
                        cudaStream_t st);
 wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string& err);

@@ -170,6 +170,7 @@ static wskpn_status ensure_train(wskpn_ctx* ctx) {
             gcp = std::max(gcp, (size_t)(cout + 15) / 16 * 16);
             t->x_off[l] = t->x_bytes;
             t->x_bytes += (size_t)(cin + 15) / 16 * 16 * 2 * sizeof(uint16_t) * t->px;
+            if (l + 1 < L) t->all_tc = t->all_tc && tc_relu_bits_supported(ctx, l);
             if (l == 0) continue;
             std::string e;
             t->lt_ok[l] = tc_dgrad_layer_alloc(t->lt[l], KS, cin, cout, e) == WSKPN_OK;
