@@ -97,15 +97,17 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
         : "memory");
 }
 
-// Shared-memory bytes of one stage: the gy boxes (one row, or with folded
-// vertical taps the KS rows an x row meets), then the x boxes (KS rows of NCC
-// chunks, or one row of NCC chunks with folded taps).
-__host__ __device__ constexpr uint32_t gy_part_bytes(int KS, int CPG, bool FOLD) {
-    return (uint32_t)((FOLD ? KS : 1) * (CPG / 16)) * GY_BOX;
+// Shared-memory bytes of one stage: the gy boxes (GR rows, or with folded
+// vertical taps the KS rows an x row meets), then the x boxes (the GR + KS - 1
+// rows those gy rows meet, NCC chunks each, or one row with folded taps).
+__host__ __device__ constexpr uint32_t gy_part_bytes(int KS, int CPG, bool FOLD, int GR = 1) {
+    return (uint32_t)((FOLD ? KS : GR) * (CPG / 16)) * GY_BOX;
 }
-__host__ __device__ constexpr int x_boxes(int KS, int NCC, bool FOLD) { return FOLD ? NCC : KS * NCC; }
-__host__ __device__ constexpr uint32_t stage_bytes(int KS, int CPG, int NCC, bool FOLD) {
-    return gy_part_bytes(KS, CPG, FOLD) + (uint32_t)x_boxes(KS, NCC, FOLD) * X_SLOT;
+__host__ __device__ constexpr int x_boxes(int KS, int NCC, bool FOLD, int GR = 1) {
+    return FOLD ? NCC : (GR + KS - 1) * NCC;
+}
+__host__ __device__ constexpr uint32_t stage_bytes(int KS, int CPG, int NCC, bool FOLD, int GR = 1) {
+    return gy_part_bytes(KS, CPG, FOLD, GR) + (uint32_t)x_boxes(KS, NCC, FOLD, GR) * X_SLOT;
 }
 __host__ __device__ constexpr uint32_t tmem_alloc_cols(int cols) {
     return cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
@@ -115,7 +117,7 @@ __host__ __device__ constexpr uint32_t tmem_alloc_cols(int cols) {
 struct WgTcArgs {
     float* part;          // [gridDim.y][gridDim.x][KS * NCC][CPG][128] partial sums
     int H, W;
-    int tiles_x, nitems;  // work items: (frame, row, 128-pixel segment)
+    int tiles_x, nitems;  // work items: (frame, row or group of GR rows, 128-pixel segment)
     int stages;
     unsigned int* status;
 };
@@ -129,18 +131,28 @@ struct WgTcArgs {
 // (N = KS x CPG, the boxes one LBO apart), so one MMA per (chunk, K step)
 // covers every vertical tap and reads its A tile once; accumulators ordered
 // (chunk, dy).  Every (x row, gy row) pair is met exactly once either way.
-template <int KS, int CPG, int NCC, bool FOLD>
+// With GR > 1 (unfolded) a work item is GR consecutive gy rows y0 .. y0 + GR
+// - 1 and the GR + KS - 1 x rows they meet: x row xr (image row y0 - pad +
+// xr) meets gy rows g in [xr - KS + 1, xr] (dy = xr - g), whose boxes sit in
+// shared memory in descending g, one LBO apart, so one MMA per (x row,
+// chunk, K step) takes them all (N = count x CPG <= 256) into the adjacent
+// accumulators of dy = xr - g_hi .. xr - g_lo; accumulators ordered (chunk,
+// dy) as with FOLD.  Each x tile is read once per item instead of once per
+// gy row.
+template <int KS, int CPG, int NCC, bool FOLD, int GR = 1>
 __global__ void __launch_bounds__(wgtc::THREADS, 1)
     wgrad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap gmap,
                     const WgTcArgs a) {
     using namespace wgtc;
+    static_assert(GR >= 1 && !(FOLD && GR > 1), "row groups: unfolded form only");
+    static_assert(GR == 1 || (GR < KS ? GR : KS) * CPG <= 256, "row groups: MMA N");
     constexpr int PAD = KS / 2;
     constexpr int NACC = KS * NCC;              // accumulators (dy, chunk)
     constexpr int NCOL = NACC * CPG;            // TMEM columns used
     constexpr uint32_t ALLOC = tmem_alloc_cols(NCOL);
-    constexpr uint32_t SB = stage_bytes(KS, CPG, NCC, FOLD);
-    constexpr uint32_t GYB = gy_part_bytes(KS, CPG, FOLD);  // gy part of a stage
-    constexpr int NXB = x_boxes(KS, NCC, FOLD);
+    constexpr uint32_t SB = stage_bytes(KS, CPG, NCC, FOLD, GR);
+    constexpr uint32_t GYB = gy_part_bytes(KS, CPG, FOLD, GR);  // gy part of a stage
+    constexpr int NXB = x_boxes(KS, NCC, FOLD, GR);
     constexpr uint32_t TX = GYB + (uint32_t)NXB * X_BOX;    // bytes a stage's loads deliver
     // folded: DYP vertical taps per MMA (N = DYP x CPG <= 256), the last MMA
     // of a K step takes the remaining DYL taps
@@ -208,7 +220,8 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
                     ok = false;
                     break;
                 }
-                const int xt = w % a.tiles_x, y = (w / a.tiles_x) % a.H, b = w / (a.tiles_x * a.H);
+                const int HG = (a.H + GR - 1) / GR;  // row groups per frame
+                const int xt = w % a.tiles_x, y = (w / a.tiles_x) % HG * GR, b = w / (a.tiles_x * HG);
                 const int x0 = xt * TPX;
                 const uint32_t fb = smem_u32(&full[s]);
                 const uint32_t dst = smem_u32(sm + (size_t)s * SB);
@@ -225,14 +238,20 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
                     for (int ci = 0; ci < NCC; ++ci)
                         tma_load_4d(dst + GYB + ci * X_SLOT, &xmap, (chunk0 + ci) * 16, x0 - PAD, y, b, fb);
                 } else {
+                    // gy rows y .. y + GR - 1 in descending order (rows past the
+                    // image read as zeros), then the x rows they meet
 #pragma unroll
-                    for (int j = 0; j < CPG / 16; ++j) tma_load_4d(dst + j * GY_BOX, &gmap, 16 * j, x0, y, b, fb);
+                    for (int g = 0; g < GR; ++g)
 #pragma unroll
-                    for (int dy = 0; dy < KS; ++dy)
+                        for (int j = 0; j < CPG / 16; ++j)
+                            tma_load_4d(dst + ((GR - 1 - g) * (CPG / 16) + j) * GY_BOX, &gmap, 16 * j, x0, y + g, b,
+                                        fb);
+#pragma unroll
+                    for (int xr = 0; xr < GR + KS - 1; ++xr)
 #pragma unroll
                         for (int ci = 0; ci < NCC; ++ci)
-                            tma_load_4d(dst + GYB + (dy * NCC + ci) * X_SLOT, &xmap, (chunk0 + ci) * 16, x0 - PAD,
-                                        y + dy - PAD, b, fb);
+                            tma_load_4d(dst + GYB + (xr * NCC + ci) * X_SLOT, &xmap, (chunk0 + ci) * 16, x0 - PAD,
+                                        y + xr - PAD, b, fb);
                 }
             }
             if (!ok) {
@@ -276,13 +295,27 @@ __global__ void __launch_bounds__(wgtc::THREADS, 1)
                                          as + (uint64_t)(ci * (X_SLOT >> 4) + j * 32),
                                          bs + (uint64_t)(pt * DYP * (CPG / 16) * (GY_BOX >> 4) + j * 32),
                                          pt == NPART - 1 ? IDESC_L : IDESC);
-                } else {
+                } else if constexpr (GR == 1) {
 #pragma unroll
                     for (int k = 0; k < NACC; ++k)
 #pragma unroll
                         for (int j = 0; j < TPX / 16; ++j)
                             mma_bf16(tmem + (uint32_t)(k * CPG), as + (uint64_t)(k * (X_SLOT >> 4) + j * 32),
                                      bs + (uint64_t)(j * 32), IDESC);
+                } else {
+#pragma unroll
+                    for (int xr = 0; xr < GR + KS - 1; ++xr) {
+                        const int g_lo = xr - KS + 1 > 0 ? xr - KS + 1 : 0;
+                        const int g_hi = xr < GR - 1 ? xr : GR - 1;
+                        const uint32_t idesc = IDESC0 | ((uint32_t)(((g_hi - g_lo + 1) * CPG) >> 3) << 17);
+#pragma unroll
+                        for (int ci = 0; ci < NCC; ++ci)
+#pragma unroll
+                            for (int j = 0; j < TPX / 16; ++j)
+                                mma_bf16(tmem + (uint32_t)((ci * KS + xr - g_hi) * CPG),
+                                         as + (uint64_t)((xr * NCC + ci) * (X_SLOT >> 4) + j * 32),
+                                         bs + (uint64_t)((GR - 1 - g_hi) * (CPG / 16) * (GY_BOX >> 4) + j * 32), idesc);
+                    }
                 }
                 commit(smem_u32(&empty[s]));  // frees the stage when these MMAs finish
             }
@@ -381,25 +414,31 @@ static int wgrad_tc_ncc(int KS, int nchunks, int cpg) {
 using WgLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const WgTcArgs&, dim3, size_t,
                                  cudaStream_t);
 
-template <int KS, int CPG, int NCC, bool FOLD>
+template <int KS, int CPG, int NCC, bool FOLD, int GR>
 static cudaError_t launch_wg(const CUtensorMap& xm, const CUtensorMap& gm, const WgTcArgs& a, dim3 grid, size_t smem,
                              cudaStream_t st) {
-    const cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<KS, CPG, NCC, FOLD>,
+    const cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<KS, CPG, NCC, FOLD, GR>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    wgrad_tc_kernel<KS, CPG, NCC, FOLD><<<grid, wgtc::THREADS, smem, st>>>(xm, gm, a);
+    wgrad_tc_kernel<KS, CPG, NCC, FOLD, GR><<<grid, wgtc::THREADS, smem, st>>>(xm, gm, a);
     return cudaGetLastError();
 }
 
 // Vertical taps folded into N where KS x CPG fits one MMA (<= 256).  For
 // wider layers (5 x 64) the fold with two MMAs per K step (4 + 1 taps)
 // measured no faster than the unfolded form (278 vs 271 us for 48 -> 64 at
-// 16 x 256^2): each gradient row is then fetched KS times from L2.
+// 16 x 256^2): each gradient row is then fetched KS times from L2.  Those
+// layers take groups of WG_ROWS gy rows per work item instead (see the
+// kernel), up to 256 / CPG rows meeting one x row per MMA.
+constexpr int WG_ROWS = 4;
 static constexpr bool wg_fold(int KS, int cpg) { return KS * cpg <= 256; }
+static constexpr int wg_rows(int KS, int cpg) {
+    return wg_fold(KS, cpg) ? 1 : (256 / cpg < WG_ROWS ? 256 / cpg : WG_ROWS);
+}
 
 static WgLaunch select_wg(int KS, int cpg, int ncc) {
 #define WSKPN_WG_CASE(ks_, n_, c_) \
-    if (KS == ks_ && cpg == n_ && ncc == c_) return launch_wg<ks_, n_, c_, wg_fold(ks_, n_)>;
+    if (KS == ks_ && cpg == n_ && ncc == c_) return launch_wg<ks_, n_, c_, wg_fold(ks_, n_), wg_rows(ks_, n_)>;
     // widths 10-32-48-64-12 and 64-64: (output channels, x chunks per CTA)
     WSKPN_WG_CASE(5, 32, 1) WSKPN_WG_CASE(5, 48, 2) WSKPN_WG_CASE(5, 64, 1) WSKPN_WG_CASE(5, 16, 4)
     WSKPN_WG_CASE(3, 32, 1) WSKPN_WG_CASE(3, 48, 2) WSKPN_WG_CASE(3, 64, 1) WSKPN_WG_CASE(3, 16, 4)
@@ -410,7 +449,7 @@ static WgLaunch select_wg(int KS, int cpg, int ncc) {
 
 // Geometry of one layer's tensor-core weight gradient.
 struct WgPlan {
-    int cpx, cpg, nchunks, ncc, groups, gk, stages;
+    int cpx, cpg, nchunks, ncc, groups, gk, stages, rows;  // rows: gy rows per work item
     size_t smem, part_floats;
 };
 
@@ -421,11 +460,12 @@ static bool wgrad_tc_plan(int KS, int Cin, int Cout, int B, int H, int W, int ns
     p.ncc = wgrad_tc_ncc(KS, p.nchunks, p.cpg);
     if (!p.ncc || !select_wg(KS, p.cpg, p.ncc)) return false;
     p.groups = p.nchunks / p.ncc;
-    const int nitems = cdiv(W, wgtc::TPX) * H * B;
+    p.rows = wg_rows(KS, p.cpg);
+    const int nitems = cdiv(W, wgtc::TPX) * cdiv(H, p.rows) * B;
     p.gk = nsm / p.groups;
     if (p.gk < 1) p.gk = 1;
     if (p.gk > nitems) p.gk = nitems;
-    const uint32_t sb = wgtc::stage_bytes(KS, p.cpg, p.ncc, wg_fold(KS, p.cpg));
+    const uint32_t sb = wgtc::stage_bytes(KS, p.cpg, p.ncc, wg_fold(KS, p.cpg), p.rows);
     const uint32_t fixed = 1024 + 256;  // alignment slack, barriers
     const int s = (int)((wgtc::SMEM_MAX - fixed) / sb);
     if (s < 2) return false;
@@ -502,7 +542,7 @@ wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gc
     a.H = H;
     a.W = W;
     a.tiles_x = cdiv(W, wgtc::TPX);
-    a.nitems = a.tiles_x * H * B;
+    a.nitems = a.tiles_x * cdiv(H, p.rows) * B;
     a.stages = p.stages;
     a.status = status;
     const WgLaunch launch = select_wg(KS, p.cpg, p.ncc);
@@ -511,7 +551,8 @@ wskpn_status launch_wgrad_tc(const void* x, int xcp, const void* gy_nhwc, int gc
         const size_t n = (size_t)p.groups * KS * p.ncc * p.cpg * 128;
         const unsigned blocks = (unsigned)std::min<size_t>((n + 31) / 32, 148 * 16);
         wgrad_tc_reduce_kernel<<<blocks, 32 * WG_RED_SLICES, 0, st>>>(part, p.gk, p.groups, KS, p.ncc, p.cpg,
-                                                                      wg_fold(KS, p.cpg) ? 1 : 0, Cin, Cout, dw);
+                                                                      wg_fold(KS, p.cpg) || p.rows > 1 ? 1 : 0, Cin,
+                                                                      Cout, dw);
     }
     WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
