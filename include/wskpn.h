@@ -509,12 +509,11 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     Eq. 3); 0 = one e4m3 value per operand.  Changing it re-packs the
  *     weights (synchronises the device).
  *   WSKPN_TUNE_HOST_BANDS: bands of the wskpn_denoise_host pipeline; 0 =
- *     automatic (one per ~216 rows, at most 8, none below 432 rows), 1 = no
- *     banding, n = n bands.
+ *     automatic (one per ~160 rows, at most 12, none below 432 rows), 1 =
+ *     no banding, n = n bands.
  *   WSKPN_TUNE_HOST_FIRST_BAND, WSKPN_TUNE_HOST_LAST_BAND: height of the
  *     pipeline's first / last band in % of the others (10 .. 100; defaults
- *     100 and 70: a shorter last band leaves less work after the last
- *     upload).
+ *     100 and 100).
  *   WSKPN_TUNE_WAIT_LIMIT_US: limit, in microseconds, of every shared-memory
  *     barrier wait of the context's tensor-core convolutions (0 = the
  *     default, 2 s).  An expired wait sets a bit of the device status word

@@ -378,7 +378,7 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking), ctx->err);
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking), ctx->err);
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->halo_stream, cudaStreamNonBlocking), ctx->err);
-        ctx->band_events.resize(8);
+        ctx->band_events.resize(4 * wskpn_ctx::BAND_SLOTS);
         for (auto& e : ctx->band_events)
             WSKPN_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), ctx->err);
     }
@@ -393,18 +393,25 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
         WSKPN_CUDA_TRY(cudaEventRecord(ctx->band_events[0], st), ctx->err);
         WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->band_stream, ctx->band_events[0], 0), ctx->err);
     }
+    constexpr int NS = wskpn_ctx::BAND_SLOTS;
     if (ctx->band_floats < need) {
-        cudaFree(ctx->d_band[0]);
-        cudaFree(ctx->d_band[1]);
-        ctx->d_band[0] = ctx->d_band[1] = nullptr;
+        for (float*& p : ctx->d_band) {
+            cudaFree(p);
+            p = nullptr;
+        }
         ctx->band_floats = 0;
-        WSKPN_CUDA_TRY(cudaMalloc(&ctx->d_band[0], need * sizeof(float)), ctx->err);
-        WSKPN_CUDA_TRY(cudaMalloc(&ctx->d_band[1], need * sizeof(float)), ctx->err);
+        for (float*& p : ctx->d_band) WSKPN_CUDA_TRY(cudaMalloc(&p, need * sizeof(float)), ctx->err);
         ctx->band_floats = need;
     }
-    // events per slot: [0..1] uploaded, [2..3] computed, [4..5] downloaded,
-    // [6..7] halo rows copied from the other slot
-    cudaEvent_t* ev = ctx->band_events.data();
+    // events per slot s: uploaded, computed, downloaded, halo rows copied in
+    // from the previous band's slot.  With three slots the upload of band j
+    // waits only for band j - 3's compute, so the uploads (the host link is
+    // the bottleneck) run back to back while bands compute.
+    cudaEvent_t* evs = ctx->band_events.data();
+    auto EV_UP = [&](int s) { return evs[s]; };
+    auto EV_COMP = [&](int s) { return evs[NS + s]; };
+    auto EV_DOWN = [&](int s) { return evs[2 * NS + s]; };
+    auto EV_HALO = [&](int s) { return evs[3 * NS + s]; };
     const int ch[4] = {3, 3, 3, 1};
     const size_t HW = (size_t)h * w;
     int job = 0;
@@ -412,17 +419,18 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
         const float* src[4] = {hf[b].radiance, hf[b].albedo, hf[b].normal, hf[b].depth};
         int pe0 = 0, pe1 = 0;  // extended rows of this frame's previous band (in the other slot)
         for (int k = 0; k < nb; ++k, ++job) {
-            const int slot = job & 1;
+            const int slot = job % NS, pslot = (job + NS - 1) % NS;
             const int y0 = yb[k], y1 = yb[k + 1];
             if (y0 >= y1) break;
             const int e0 = std::max(0, y0 - halo), e1 = std::min(h, y1 + halo), eh = e1 - e0;
             const size_t ePX = (size_t)eh * w;
             float* base = ctx->d_band[slot];
-            // the slot's previous band must be computed before its inputs are
-            // replaced, and the other slot's band must have copied its halo rows
-            // out of this slot
-            if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, ev[2 + slot], 0), ctx->err);
-            if (job >= 1) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, ev[6 + (slot ^ 1)], 0), ctx->err);
+            // the slot's previous band (job - NS) must be computed before its
+            // inputs are replaced, and band job - NS + 1 must have copied its
+            // halo rows out of this slot
+            if (job >= NS) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, EV_COMP(slot), 0), ctx->err);
+            if (job >= NS - 1)
+                WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, EV_HALO((job - NS + 1) % NS), 0), ctx->err);
             wskpn_frame f{};
             const float** dst[4] = {&f.radiance, &f.albedo, &f.normal, &f.depth};
             // rows [e0, kept) are already on the device in the previous band's
@@ -432,10 +440,10 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
             // uploaded once per frame
             const int kept = k > 0 ? std::max(e0, std::min(e1, pe1)) : e0;
             const size_t pPX = (size_t)(pe1 - pe0) * w;
-            const float* prev = ctx->d_band[slot ^ 1];
+            const float* prev = ctx->d_band[pslot];
             if (kept > e0) {  // after the previous band's upload and this slot's previous compute
-                WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->halo_stream, ev[slot ^ 1], 0), ctx->err);
-                if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->halo_stream, ev[2 + slot], 0), ctx->err);
+                WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->halo_stream, EV_UP(pslot), 0), ctx->err);
+                if (job >= NS) WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->halo_stream, EV_COMP(slot), 0), ctx->err);
             }
             float* p = base;
             for (int q = 0; q < 4; ++q) {
@@ -454,35 +462,37 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
                 p += (size_t)ch[q] * ePX;
                 prev += (size_t)ch[q] * pPX;
             }
-            WSKPN_CUDA_TRY(cudaEventRecord(ev[6 + slot], ctx->halo_stream), ctx->err);
+            WSKPN_CUDA_TRY(cudaEventRecord(EV_HALO(slot), ctx->halo_stream), ctx->err);
             pe0 = e0;
             pe1 = e1;
             // the output region sits past the inputs of the tallest band, so a
             // later, taller band's upload into this slot cannot reach the rows
             // of this band still waiting for download
             float* dout = base + (size_t)10 * ext * w;
-            WSKPN_CUDA_TRY(cudaEventRecord(ev[slot], ctx->up_stream), ctx->err);
-            // compute after the upload, and after the slot's previous download;
-            // with two compute streams, slot 1's jobs use the second stream and
-            // the second half of the workspaces
-            cudaStream_t cs = two && slot ? ctx->band_stream : st;
-            WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[slot], 0), ctx->err);
-            WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[6 + slot], 0), ctx->err);
-            if (job >= 2) WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, ev[4 + slot], 0), ctx->err);
+            WSKPN_CUDA_TRY(cudaEventRecord(EV_UP(slot), ctx->up_stream), ctx->err);
+            // compute after the upload and the halo copy, and after the slot's
+            // previous download; with two compute streams, odd jobs use the
+            // second stream and the second half of the workspaces (jobs on
+            // one stream run in order, so a workspace half is never shared)
+            const bool odd = job & 1;
+            cudaStream_t cs = two && odd ? ctx->band_stream : st;
+            WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, EV_UP(slot), 0), ctx->err);
+            WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, EV_HALO(slot), 0), ctx->err);
+            if (job >= NS) WSKPN_CUDA_TRY(cudaStreamWaitEvent(cs, EV_DOWN(slot), 0), ctx->err);
             {
-                WorkspaceShift shift(ctx, two && slot, band_px);
+                WorkspaceShift shift(ctx, two && odd, band_px);
                 wskpn_status s = wskpn_denoise(ctx, &f, 1, eh, w, dout, cs);
                 if (s) return s;
             }
-            WSKPN_CUDA_TRY(cudaEventRecord(ev[2 + slot], cs), ctx->err);
+            WSKPN_CUDA_TRY(cudaEventRecord(EV_COMP(slot), cs), ctx->err);
             // download the central rows
-            WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->down_stream, ev[2 + slot], 0), ctx->err);
+            WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->down_stream, EV_COMP(slot), 0), ctx->err);
             WSKPN_CUDA_TRY(cudaMemcpy2DAsync(host_out + (size_t)b * 3 * HW + (size_t)y0 * w, HW * sizeof(float),
                                              dout + (size_t)(y0 - e0) * w, ePX * sizeof(float),
                                              (size_t)(y1 - y0) * w * sizeof(float), 3, cudaMemcpyDeviceToHost,
                                              ctx->down_stream),
                            ctx->err);
-            WSKPN_CUDA_TRY(cudaEventRecord(ev[4 + slot], ctx->down_stream), ctx->err);
+            WSKPN_CUDA_TRY(cudaEventRecord(EV_DOWN(slot), ctx->down_stream), ctx->err);
         }
     }
     WSKPN_CUDA_TRY(cudaStreamSynchronize(ctx->down_stream), ctx->err);
@@ -501,9 +511,11 @@ wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, 
         return WSKPN_EINVAL;
     }
     // Frames of at least 432 rows go through the banded pipeline (one band
-    // per ~216 rows, at most 8): the recomputed halos cost less than the
-    // copies they let overlap.  Smaller frames: one upload, denoise, download.
-    const int nb = ctx->host_bands > 0 ? std::min(ctx->host_bands, h) : std::min(8, h / 216);
+    // per ~160 rows, at most 12; measured best or within 2 % of the best
+    // count at 720p, 1080p and 1440p): the recomputed halos cost less than
+    // the copies they let overlap.  Smaller frames: one upload, denoise,
+    // download.
+    const int nb = ctx->host_bands > 0 ? std::min(ctx->host_bands, h) : h < 432 ? 1 : std::min(12, h / 160);
     if (nb >= 2) return denoise_host_banded(ctx, host_frames, batch, h, w, host_out, nb, (cudaStream_t)stream);
     if (!ctx->d_stage) {
         cudaError_t e = cudaMalloc((void**)&ctx->d_stage, ctx->ws_pixels * 13 * sizeof(float));

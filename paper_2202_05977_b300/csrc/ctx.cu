@@ -93,8 +93,7 @@ void ctx_free(wskpn_ctx* ctx) {
     cudaFree(ctx->d_tcB);
     cudaFree(ctx->d_z);
     cudaFree(ctx->d_stage);
-    cudaFree(ctx->d_band[0]);
-    cudaFree(ctx->d_band[1]);
+    for (float* p : ctx->d_band) cudaFree(p);
     for (cudaEvent_t e : ctx->band_events) cudaEventDestroy(e);
     if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
     if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);

@@ -53,7 +53,8 @@ struct wskpn_ctx {
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
     cudaStream_t band_stream = nullptr;  // second compute stream of the host-buffer pipeline
     cudaStream_t halo_stream = nullptr;  // device copies of the halo rows bands share
-    float* d_band[2] = {nullptr, nullptr};  // [10 + 3][band_rows][max_w]
+    static constexpr int BAND_SLOTS = 3;       // band buffers of the host pipeline
+    float* d_band[BAND_SLOTS] = {};            // [10 + 3][band_rows][max_w] each
     size_t band_floats = 0;
     std::vector<cudaEvent_t> band_events;   // per band slot: uploaded, computed, downloaded, halo copied
     unsigned int* d_fallbacks = nullptr;
@@ -70,7 +71,7 @@ struct wskpn_ctx {
     int train_tc_recompute = 1;  // backward on the tensor cores: 1 recompute + input gradients, 2 recompute only (WSKPN_TUNE_TRAIN_RECOMPUTE)
     int host_bands = 0;         // bands of the host-buffer pipeline, 0 = automatic (WSKPN_TUNE_HOST_BANDS)
     int host_first_pct = 100;   // first band's height in % of the others (WSKPN_TUNE_HOST_FIRST_BAND)
-    int host_last_pct = 70;     // last band's height in % of the others (WSKPN_TUNE_HOST_LAST_BAND)
+    int host_last_pct = 100;    // last band's height in % of the others (WSKPN_TUNE_HOST_LAST_BAND)
     void* train = nullptr;  // training workspaces (train.cu), allocated by the first training call
     // stage profiling: one event set (n_layers + 3 events) per recorded call
     bool prof = false;
