@@ -80,6 +80,8 @@ def parse():
                    help="further offered rates (req/s) for the load sweep")
     p.add_argument("--serve-sweep-requests", type=int, default=2048)
     p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
+    p.add_argument("--fused-prep", type=int, default=None,
+                   help="BF16: the first convolution assembles its input (1, default) or a separate kernel stores it (0)")
     return p.parse_args()
 
 
@@ -140,15 +142,16 @@ def tensor_peak(pk, clocks):
     return (pk["bf16_tflops_sustained"], "sustained") if sustained else (pk["bf16_tflops"], "burst")
 
 
-def stage_rooflines(stage_ms, precision, pk, h=H, w=W, tpeak=None):
+def stage_rooflines(stage_ms, precision, pk, h=H, w=W, tpeak=None, fused_prep=False):
     """Achieved throughput and fraction of the measured peak for every stage
     (algorithmic FLOPs for the convolutions, algorithmic bytes for the
-    streaming kernels), from the stage times of one denoise."""
+    streaming kernels), from the stage times of one denoise.  fused_prep: the
+    input assembly ran inside conv1 (stage 0 holds no kernel)."""
     L = len(WIDTHS) - 1
     out = {}
     prep_bytes = (40 + {"fp32": 40, "bf16": 64, "fp8": 64}[precision]) * h * w
     for i, ms in enumerate(stage_ms):
-        if ms <= 0:
+        if ms <= 0 or (i == 0 and fused_prep):  # no assembly launch: it runs inside conv1
             continue
         if i == 0 or i == L + 1:
             byts = prep_bytes if i == 0 else DECODE_BYTES_PER_PX * h * w
@@ -486,13 +489,20 @@ def main():
             print(json.dumps(line))
         return
 
-    def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS, clk=None):
+    # the first layer assembles its input inside its own kernel (no prep launch)
+    fused_prep_on = args.precision == "bf16" and args.fused_prep != 0 and args.tc_split != 0
+
+    def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS, clk=None,
+                  fused_prep=None):
         h, w = hw
         xs = xin if frame is None else frame
         d = wk.Denoiser(wb if weights is None else weights, precision=precision, max_hw=(h, w), widths=widths,
                         conv_ks=ks)
         if args.tc_split is not None and precision == "bf16":
             d.set_tuning(2, args.tc_split)
+        fp = fused_prep if fused_prep is not None else args.fused_prep
+        if fp is not None and precision == "bf16":
+            d.set_tuning(12, fp)  # WSKPN_TUNE_FUSED_PREP
         if precision == "fp8":  # static activation scales from a different frame (seed 3)
             cal = synth.make_frame(h, w, SEED + 1)
             d.calibrate(*[torch.from_numpy(np.ascontiguousarray(cal[k][None])).to(dev) for k in keys])
@@ -578,7 +588,8 @@ def main():
             xs = [torch.from_numpy(np.ascontiguousarray(fr[k][None])).to(dev) for k in keys]
             r = time_path(args.precision, max(5, args.steps // 2), 3, (h, w), xs)
             sweep[f"{w}x{h}"] = {"ms_per_frame": r["ms_step"], "fps": 1e3 / r["ms_step"],
-                                 "stage_rooflines": stage_rooflines(r["stage_ms"], args.precision, pk, h, w)}
+                                 "stage_rooflines": stage_rooflines(r["stage_ms"], args.precision, pk, h, w,
+                                                                    fused_prep=fused_prep_on)}
             del r
 
     # the paper's 6-block quality variant of ImportanceNet (Sec. 4.1), widths
@@ -610,6 +621,15 @@ def main():
             c3[f"{prec}_ms_per_frame"] = r["ms_step"]
             del r
         variants["conv3x3_1920x1080"] = c3
+        if args.precision == "bf16":
+            # the input assembly as its own kernel, its output stored in HBM
+            # and read back by conv1 (the default runs it inside conv1)
+            r = time_path("bf16", max(5, args.steps // 2), 3, fused_prep=0)
+            variants["separate_input_assembly_1920x1080"] = {
+                "ms_per_frame": r["ms_step"],
+                "stages_ms": dict(zip(["prep"] + [f"conv{i + 1}" for i in range(len(WIDTHS) - 1)] + ["reconstruct"],
+                                      r["stage_ms"]))}
+            del r
         variants["training_step_16x256x256"] = time_training(max(5, args.steps // 4), 3)
         variants["training_step_16x256x256_kept_activations"] = time_training(max(5, args.steps // 4), 3, keep=True)
     if not args.no_variants:
@@ -739,7 +759,7 @@ def main():
             "data": "synthetic",
             "config": config_block(args.precision),
             "fps": job_metrics(main_res["ms_step"], world)["fps"],
-            "stages_ms": dict(zip(stage_names, main_res["stage_ms"])),
+            "stages_ms": {k: v for k, v in zip(stage_names, main_res["stage_ms"]) if not (k == "prep" and fused_prep_on)},
             "prediction_ms": sum(main_res["stage_ms"][:L + 1]),
             "reconstruction_ms": main_res["stage_ms"][L + 1],
             "p50_step_ms": statistics.median(main_res["per"]),
@@ -747,8 +767,9 @@ def main():
                                                       int(round(0.99 * (len(main_res["per"]) - 1))))],
             "roofline": roof,
             "stage_rooflines": stage_rooflines(main_res["stage_ms"], args.precision, pk,
-                                               tpeak=tensor_peak(pk, clocks)[0]),
-            "gpu_launches": args.steps * (L + 2),
+                                               tpeak=tensor_peak(pk, clocks)[0], fused_prep=fused_prep_on),
+            "input_assembly": "inside conv1 (its producer warps)" if fused_prep_on else "separate kernel",
+            "gpu_launches": args.steps * (L + (1 if fused_prep_on else 2)),
             "clocks": clocks,
         }
         if sweep:

@@ -24,6 +24,7 @@ TUNE_HOST_LAST_BAND = 7
 TUNE_WAIT_LIMIT_US = 9
 TUNE_WAIT_PROBE = 10
 TUNE_TRAIN_KEEP = 11
+TUNE_FUSED_PREP = 12
 
 
 class Config(ctypes.Structure):

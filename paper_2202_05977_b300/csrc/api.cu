@@ -681,6 +681,10 @@ wskpn_status wskpn_set_tuning(wskpn_ctx* ctx, int key, int value) {
         ctx->train_keep = value;
         return WSKPN_OK;
     }
+    if (key == WSKPN_TUNE_FUSED_PREP && (value == 0 || value == 1)) {
+        ctx->fused_prep = value;
+        return WSKPN_OK;
+    }
     ctx->err = "wskpn_set_tuning: unknown key or value";
     return WSKPN_EINVAL;
 }

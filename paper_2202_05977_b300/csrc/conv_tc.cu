@@ -45,6 +45,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "prep.cuh"
 #include "quant.cuh"
 #include "tma.cuh"
 
@@ -60,6 +61,8 @@ __host__ __device__ constexpr int rows_per_tile(int cout_p) {
     return cout_p <= 16 ? 16 : cout_p <= 32 ? 8 : cout_p <= 48 ? 5 : 4;
 }
 constexpr int THREADS = 192;
+// PIN kernels add four warps that assemble the input tiles (Sec. 5.1)
+constexpr int THREADS_PIN = THREADS + 128;
 constexpr int ROWB = 32;           // bytes of one pixel row of one K chunk
 constexpr uint32_t SMEM_MAX = 232448;  // also the limit tc_rows_per_item tests against
 constexpr unsigned ST_TIMEOUT_PRODUCER = 1u, ST_TIMEOUT_MMA = 2u, ST_TIMEOUT_EPILOGUE = 4u;
@@ -101,6 +104,11 @@ struct TcArgs {
     // lo > 0, and only then); this launch writes the words its channels
     // occupy
     uint32_t* relu_bits;
+    // PIN (the first layer assembling its own input, Sec. 5.1): the FP32
+    // planar frame buffers of this launch's B frames and the assembly
+    // constants; the layer input is then never stored
+    FrameBatch frames;
+    PrepConst prep;
 };
 
 // ------------------------------------------------------------- primitives
@@ -342,10 +350,12 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
 // ----------------------------------------------------------------- kernel
 // EPI: 0 plain epilogue; 1 (GM) input gradient with the ReLU mask of the
 // layer input and bias sums; 2 (RB) also writes the output's ReLU bits.
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF, int EPI>
-__global__ void __launch_bounds__(tc::THREADS, 1)
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bool XF, int EPI, bool PIN = false>
+__global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr bool GM = EPI == 1, RB = EPI == 2;
+    static_assert(!PIN || (!FP8 && !XF && EPI == 0 && NCC_IN == 2 && NCC_W == 1),
+                  "input assembly in the producer: the first BF16 layer with hi/lo input pairs");
     constexpr int PAD = KS / 2;
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
     constexpr int NCB = XF ? KS * COUT_P : COUT_P;        // TMEM columns of one output row's accumulators
@@ -396,7 +406,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&full[s]), PIN ? 4 : 1);  // PIN: one arrival per assembling warp
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -419,7 +429,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
-    if (warp >= 2) {
+    if (warp >= 2 && warp < 6) {
         // accumulators start at zero: every MMA accumulates
         const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll 1
@@ -439,43 +449,49 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const uint32_t n = a.wbytes - off < 32768u ? a.wbytes - off : 32768u;
                 bulk_load(smem_u32(sW + off), static_cast<const uint8_t*>(a.wimg) + off, n, wb);
             }
-            // the activations are the previous kernel's output: wait for that
-            // grid to complete (returns at once without a programmatic
-            // dependency).  Everything else this CTA reads or writes in global
-            // memory follows from these loads.
-            asm volatile("griddepcontrol.wait;" ::: "memory");
-            uint32_t it = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-                const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
-                const int x0 = tx * TPX, y0 = ty * R;
-                for (int r0 = 0; r0 < ROWS_IN; r0 += RPI, ++it) {
-                    const int s = it % S;
-                    if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
-                        ok = false;
-                        break;
+            if constexpr (PIN) {
+                // the assembling warps stage the activations: only the weight
+                // copy is this warp's to see land before exit
+                mbar_wait_drain(wb, 0);
+            } else {
+                // the activations are the previous kernel's output: wait for that
+                // grid to complete (returns at once without a programmatic
+                // dependency).  Everything else this CTA reads or writes in global
+                // memory follows from these loads.
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                uint32_t it = 0;
+                bool ok = true;
+                for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+                    const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
+                    const int x0 = tx * TPX, y0 = ty * R;
+                    for (int r0 = 0; r0 < ROWS_IN; r0 += RPI, ++it) {
+                        const int s = it % S;
+                        if (!mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = smem_u32(&full[s]);
+                        const uint32_t dst = smem_u32(sA + (size_t)s * a.stage_bytes);
+                        mbar_expect_tx(fb, (uint32_t)RPI * NBOX * BOX_BYTES);
+#pragma unroll
+                        for (int j = 0; j < RPI; ++j)  // rows past the tile read as zeros
+#pragma unroll
+                            for (int bx = 0; bx < NBOX; ++bx)
+                                tma_load_4d(dst + j * a.row_bytes + bx * a.box_stride, &tmap, bx * CPB * CH, x0 - PAD,
+                                            y0 - PAD + r0 + j, b, fb);
                     }
-                    const uint32_t fb = smem_u32(&full[s]);
-                    const uint32_t dst = smem_u32(sA + (size_t)s * a.stage_bytes);
-                    mbar_expect_tx(fb, (uint32_t)RPI * NBOX * BOX_BYTES);
-#pragma unroll
-                    for (int j = 0; j < RPI; ++j)  // rows past the tile read as zeros
-#pragma unroll
-                        for (int bx = 0; bx < NBOX; ++bx)
-                            tma_load_4d(dst + j * a.row_bytes + bx * a.box_stride, &tmap, bx * CPB * CH, x0 - PAD,
-                                        y0 - PAD + r0 + j, b, fb);
                 }
-            }
-            if (!ok) {
-                atomicOr(a.status, tc::ST_TIMEOUT_PRODUCER);
-                *abort_flag = 1;
-            }
-            // Drain: every issued stage's load must have landed before exit
-            // (also after an abort: these waits ignore the abort flag).
-            const uint32_t n_in_flight = it < (uint32_t)S ? it : (uint32_t)S;
-            for (uint32_t k = 0; k < n_in_flight; ++k) {
-                const uint32_t j = it - 1 - k;
-                mbar_wait_drain(smem_u32(&full[j % S]), (j / S) & 1u);
+                if (!ok) {
+                    atomicOr(a.status, tc::ST_TIMEOUT_PRODUCER);
+                    *abort_flag = 1;
+                }
+                // Drain: every issued stage's load must have landed before exit
+                // (also after an abort: these waits ignore the abort flag).
+                const uint32_t n_in_flight = it < (uint32_t)S ? it : (uint32_t)S;
+                for (uint32_t k = 0; k < n_in_flight; ++k) {
+                    const uint32_t j = it - 1 - k;
+                    mbar_wait_drain(smem_u32(&full[j % S]), (j / S) & 1u);
+                }
             }
         }
     } else if (warp == 1) {
@@ -522,6 +538,81 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             // after an abort: the drain wait ignores the abort flag).
             mma_commit(smem_u32(fin));
             mbar_wait_drain(smem_u32(fin), 0);
+        }
+    } else if (PIN && warp >= 6) {
+        // ------------------------------------------------ input assembly (PIN), warps 6..9
+        // The first layer's input tiles straight from the FP32 frame buffers
+        // (Sec. 5.1 assembly, the same functions and bits as the separate
+        // assembly kernel): each stage row holds the 128 + KS - 1 input pixels
+        // of one tile row as 64-byte rows [hi(16) | lo(16)] in the 64-byte
+        // swizzle (16-byte unit u of a row at unit u ^ (address bits 7-8)),
+        // which is what the TMA writes from the stored NHWC input, so the MMA
+        // side is unchanged.  Pixels outside the image are the convolution's
+        // zero padding.  All raw loads of a stage are issued before any is used.
+        if constexpr (PIN) {
+            constexpr int NPX = tc::BM + KS - 1;
+            constexpr int NPT = (RPI * NPX + 127) / 128;  // pixels per thread per stage
+            const int ct = tid - tc::THREADS;              // 0..127
+            const size_t HW = (size_t)a.H * a.W;
+            // the frames may be the previous kernel's output
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+                const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, b = t / (a.tiles_x * a.tiles_y);
+                const int x0 = tx * TPX, y0 = ty * R;
+                const float* const fr = a.frames.r.p[b];
+                const float* const fa = a.frames.a.p[b];
+                const float* const fn = a.frames.n.p[b];
+                const float* const fd = a.frames.d.p[b];
+                for (int r0 = 0; r0 < ROWS_IN; r0 += RPI, ++it) {
+                    const int s = it % S;
+                    int w = 1;
+                    if (lane == 0) w = mbar_wait(smem_u32(&empty[s]), ((it / S) & 1u) ^ 1u, abort_flag, a.wait_ns);
+                    if (!__shfl_sync(0xffffffffu, w, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* const stg = sA + (size_t)s * a.stage_bytes;
+                    float raw[NPT][10];
+                    bool inside[NPT];
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
+                        const int i = ct + 128 * k;
+                        const int j = i / NPX, px = i - j * NPX;
+                        const int yy = y0 - PAD + r0 + j, xx = x0 - PAD + px;
+                        inside[k] = i < RPI * NPX && r0 + j < ROWS_IN && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                        if (inside[k]) prep_load_raw(fr, fa, fn, fd, (size_t)yy * a.W + xx, HW, raw[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < NPT; ++k) {
+                        const int i = ct + 128 * k;
+                        const int j = i / NPX, px = i - j * NPX;
+                        if (i >= RPI * NPX || r0 + j >= ROWS_IN) continue;  // rows no MMA reads
+                        uint4 qv[4] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u),
+                                       make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+                        if (inside[k]) {
+                            float v[16];
+                            prep_from_raw<true>(raw[k], a.prep, v);
+#pragma unroll
+                            for (int c = 10; c < 16; ++c) v[c] = 0.f;
+                            bf16_hilo16(v, qv);
+                        }
+                        uint8_t* const row = stg + (size_t)j * a.row_bytes + (size_t)px * 64;
+                        const int sw = (px >> 1) & 3;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) *reinterpret_cast<uint4*>(row + ((u ^ sw) << 4)) = qv[u];
+                    }
+                    // generic-proxy writes made visible to the tensor core's reads
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+                }
+            }
+            if (!ok && lane == 0) {
+                atomicOr(a.status, tc::ST_TIMEOUT_PRODUCER);
+                *abort_flag = 1;
+            }
         }
     } else {
         // ------------------------------------------------ epilogue warps 2..5
@@ -958,17 +1049,17 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     return WSKPN_OK;
 }
 
-template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF, int EPI = 0>
+template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF, int EPI = 0, bool PIN = false>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
     auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, XF ? xf_rows_per_tile(KS) : tc::rows_per_tile(COUT_P),
-                               WM, XF, EPI>;
+                               WM, XF, EPI, PIN>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     // programmatic dependent launch: set-up overlaps the previous kernel's
     // tail; the TMA producer waits for that kernel before reading activations
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(tc::THREADS);
+    cfg.blockDim = dim3(PIN ? tc::THREADS_PIN : tc::THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -986,8 +1077,16 @@ using TcLaunch = wskpn_status (*)(const CUtensorMap&, const TcArgs&, size_t, int
 // group, input chunks per row (hi/lo included), weight-image chunks,
 // precision, e4m3 weight mode, folded taps.  nullptr when none is built.
 static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8, int wm, bool xf, bool gm = false,
-                                 bool rb = false) {
+                                 bool rb = false, bool pin = false) {
     TcLaunch launch = nullptr;
+    // the first layer assembling its own input (BF16 hi/lo, 10 -> 32)
+    if (pin) {
+        if (!xf && !gm && !rb && !fp8 && wm == 0 && cg == 32 && ncc_in == 2 && ncc_w == 1) {
+            if (KS == 5) launch = launch_tc_t<5, 32, 2, 1, false, 0, false, 0, true>;
+            if (KS == 3) launch = launch_tc_t<3, 32, 2, 1, false, 0, false, 0, true>;
+        }
+        return launch;
+    }
 #define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
     if (!launch && !xf && !gm && !rb && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_ && fp8 == f8_ && wm == wm_) \
         launch = launch_tc_t<ks_, n_, nin_, nw_, f8_, wm_, false>;
@@ -1075,6 +1174,10 @@ struct TcRun {
     float* bias_part = nullptr;
     uint32_t* relu_bits = nullptr;    // ReLU layer: positive-channel bits of the output (TcArgs)
     int* grid_out = nullptr;      // receives the grid size (bias_part holds 4 rows per CTA)
+    // the first layer assembling its input from these B FP32 frames (the
+    // PIN kernels) instead of reading a stored input; in is then unused
+    const wskpn_frame* frames = nullptr;
+    PrepConst prep{};
 };
 
 static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int H, int W, cudaStream_t st,
@@ -1084,26 +1187,37 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     const int KS = r.KS;
     const int eb = fp8 ? 1 : 2;
     const int ch = fp8 ? 32 : 16;
-    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder(err);
-    if (!encode) return WSKPN_EUNSUPPORTED;
+    const bool pin = r.frames != nullptr;
     const int split = r.split_in;                   // hi/lo activations (BF16 or e4m3)
     const int wm = fp8 && split ? fp8_weight_mode(L.cin) : 0;  // e4m3 hi/lo weights with hi/lo activations
     const int cin_row = L.cin_p * (split ? 2 : 1);  // stored channels per input pixel
-    CUtensorMap map;
-    cuuint64_t gdim[4] = {(cuuint64_t)cin_row, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
-    cuuint64_t gstr[3] = {(cuuint64_t)cin_row * eb, (cuuint64_t)W * cin_row * eb, (cuuint64_t)H * W * cin_row * eb};
     const int ncc_in = L.cin_p / ch * (split ? 2 : 1);
     const int ncc_w = wm == 1 ? ncc_in : wm == 2 ? ncc_in - 1 : L.cin_p / ch;  // weight-image chunks
     const int cpb = chunks_per_box(ncc_in);
-    cuuint32_t box[4] = {(cuuint32_t)(ch * cpb), (cuuint32_t)(tc::BM + KS - 1), 1, 1};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult cr = encode(&map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
-                         const_cast<void*>(in), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         cpb == 4 ? CU_TENSOR_MAP_SWIZZLE_128B : (cpb == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) {
-        err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
-        return WSKPN_ECUDA;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));  // unused by the PIN kernels
+    if (pin) {
+        if (fp8 || !split || r.last || !r.relu || r.gbits || r.relu_bits || L.xfold) {
+            err = "conv_tc: input assembly in the first layer needs a BF16 ReLU layer with hi/lo input";
+            return WSKPN_EINVAL;
+        }
+    } else {
+        PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder(err);
+        if (!encode) return WSKPN_EUNSUPPORTED;
+        cuuint64_t gdim[4] = {(cuuint64_t)cin_row, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        cuuint64_t gstr[3] = {(cuuint64_t)cin_row * eb, (cuuint64_t)W * cin_row * eb,
+                              (cuuint64_t)H * W * cin_row * eb};
+        cuuint32_t box[4] = {(cuuint32_t)(ch * cpb), (cuuint32_t)(tc::BM + KS - 1), 1, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        CUresult cr = encode(&map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                             const_cast<void*>(in), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             cpb == 4 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                      : (cpb == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) {
+            err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")";
+            return WSKPN_ECUDA;
+        }
     }
     const int G = L.groups, cg = L.cout_p / G;
     const size_t group_bytes = L.wtc_bytes / G;
@@ -1160,24 +1274,47 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
         err = "conv_tc: the gradient mask needs a single-BF16 input-gradient layer";
         return WSKPN_EINVAL;
     }
-    const TcLaunch launch = select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf, gm, r.relu_bits != nullptr);
+    const TcLaunch launch =
+        select_tc_kernel(KS, cg, ncc_in, ncc_w, fp8, wm, xf, gm, r.relu_bits != nullptr, pin);
     if (!launch) {
-        err = "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M, "
-              "64-64 and the multi-resolution U-Net are built";
+        err = pin ? "conv_tc: no input-assembling kernel for this first layer (BF16 hi/lo 10 -> 32 is built)"
+                  : "conv_tc: no kernel for this (KS, padded Cin, padded Cout, precision); widths 10-32-48-64-2M, "
+                    "64-64 and the multi-resolution U-Net are built";
         return WSKPN_EUNSUPPORTED;
     }
-    for (int g = 0; g < G; ++g) {  // each group reads the whole input and writes its channels
-        a.wimg = static_cast<const uint8_t*>(L.wtc) + g * group_bytes;
-        a.ep_scale = L.ep_scale + g * cg;
-        a.ep_bias = L.ep_bias + g * cg;
-        a.out_c0 = r.out_c0 + g * cg;
-        const int end = r.out_c0 + L.cout_p;
-        a.zero_c0 = end;
-        a.zero_n = r.zero_pad && g == G - 1 && r.out_cp > end ? r.out_cp - end : 0;
-        a.dup_src = r.dup_src;
-        a.dup_dst = r.dup_dst;
-        const wskpn_status s = launch(map, a, smem, grid, st, err);
-        if (s) return s;
+    // PIN kernels take the frame pointers as a parameter table: at most
+    // WSKPN_MAX_BATCH frames per launch
+    const size_t out_pix_bytes = (size_t)r.out_cp * (fp8 ? 1 : 2) * (a.split_out ? 2 : 1);
+    const int bstep = pin ? WSKPN_MAX_BATCH : B;
+    for (int b0 = 0; b0 < B; b0 += bstep) {
+        int gridc = grid;
+        if (pin) {
+            const int nb = B - b0 < bstep ? B - b0 : bstep;
+            a.B = nb;
+            a.ntiles = a.tiles_x * a.tiles_y * nb;
+            gridc = a.ntiles < nsm ? a.ntiles : nsm;
+            a.out = static_cast<uint8_t*>(out) + (size_t)b0 * H * W * out_pix_bytes;
+            for (int j = 0; j < nb; ++j) {
+                a.frames.r.p[j] = r.frames[b0 + j].radiance;
+                a.frames.a.p[j] = r.frames[b0 + j].albedo;
+                a.frames.n.p[j] = r.frames[b0 + j].normal;
+                a.frames.d.p[j] = r.frames[b0 + j].depth;
+            }
+            a.prep = r.prep;
+        }
+        for (int g = 0; g < G; ++g) {  // each group reads the whole input and writes its channels
+            a.wimg = static_cast<const uint8_t*>(L.wtc) + g * group_bytes;
+            a.ep_scale = L.ep_scale + g * cg;
+            a.ep_bias = L.ep_bias + g * cg;
+            a.out_c0 = r.out_c0 + g * cg;
+            const int end = r.out_c0 + L.cout_p;
+            a.zero_c0 = end;
+            a.zero_n = r.zero_pad && g == G - 1 && r.out_cp > end ? r.out_cp - end : 0;
+            a.dup_src = r.dup_src;
+            a.dup_dst = r.dup_dst;
+            const wskpn_status s = launch(map, a, smem, gridc, st, err);
+            if (s) return s;
+        }
     }
     return WSKPN_OK;
 }
@@ -1193,7 +1330,7 @@ bool tc_split_all(const wskpn_ctx* ctx) {
 
 // One layer of a context's ImportanceNet (relu_bits: see TcArgs; BF16 only).
 static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, int B, int H, int W, cudaStream_t st,
-                            uint32_t* relu_bits = nullptr) {
+                            uint32_t* relu_bits = nullptr, const wskpn_frame* frames = nullptr) {
     const wskpn_config& c = ctx->cfg;
     const bool fp8 = c.prec == WSKPN_FP8;
     TcRun r{};
@@ -1222,7 +1359,24 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
     r.probe = ctx->wait_probe;
     ctx->wait_probe = 0;  // the test hook applies to one launch
     r.relu_bits = relu_bits;
+    if (frames) {  // the first layer assembles its input (same constants as the assembly kernel)
+        r.frames = frames;
+        r.prep.inv_gamma = (float)(1.0 / (double)c.gamma);
+        r.prep.dnear = c.depth_near;
+        r.prep.dscale = (float)(1.0 / ((double)c.depth_far - (double)c.depth_near));
+    }
     return tc_run(r, in, out, B, H, W, st, ctx->err);
+}
+
+// The context's first layer can assemble its own input (BF16 context,
+// hi/lo input pairs, a kernel built for the layer's shape).
+bool tc_fused_prep_supported(const wskpn_ctx* ctx) {
+    const wskpn_config& c = ctx->cfg;
+    if (c.prec != WSKPN_BF16 || c.n_layers < 2 || !tc_split_of(ctx, 0)) return false;
+    const Layer& L = ctx->layers[0];
+    if (L.xfold || L.groups != 1) return false;
+    return select_tc_kernel(c.conv_ks, L.cout_p, 2 * (L.cin_p / 16), L.cin_p / 16, false, 0, false, false, false,
+                            true) != nullptr;
 }
 
 bool tc_relu_bits_supported(const wskpn_ctx* ctx, int l) {
@@ -1398,14 +1552,20 @@ wskpn_status tc_logits(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, 
     const int split = tc_split_of(ctx, 0);
     const size_t x0_bytes = (size_t)ctx->layers[0].cin_p * 2 * (split ? 2 : 1) * HW;
     for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * x0_bytes;
-    wskpn_status s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), split ? 2 : 1, st,
-                                 ctx->err);
-    if (s) return s;
+    // the first layer assembles its input tiles itself (Sec. 5.1 inside its
+    // producer) unless tuned off; otherwise the assembly kernel stores them
+    const bool fused = ctx->fused_prep && tc_fused_prep_supported(ctx);
+    wskpn_status s = WSKPN_OK;
+    if (!fused) {
+        s = launch_prep(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), split ? 2 : 1, st,
+                        ctx->err);
+        if (s) return s;
+    }
     prof_mark(ctx, 1, st);
     for (int l = 0; l < c.n_layers; ++l) {
         const void* in = l % 2 == 0 ? (const void*)A : (const void*)Bf;
         void* out = l == c.n_layers - 1 ? (void*)z : ((l + 1) % 2 == 0 ? (void*)A : (void*)Bf);
-        s = conv_tc(ctx, l, in, out, B, H, W, st);
+        s = conv_tc(ctx, l, in, out, B, H, W, st, nullptr, l == 0 && fused ? frames : nullptr);
         if (s) return s;
         prof_mark(ctx, 2 + l, st);
     }

@@ -68,6 +68,7 @@ struct wskpn_ctx {
     int fp8_split = 1;  // e4m3 activations and weights as hi/lo pairs (WSKPN_TUNE_FP8_SPLIT)
     bool simt_stale = true;      // FP32 SIMT weight images older than the master weights
     int train_keep = 0;          // wskpn_forward_train keeps the layer inputs for the backward (WSKPN_TUNE_TRAIN_KEEP)
+    int fused_prep = 1;          // BF16 inference: the first layer assembles its input (WSKPN_TUNE_FUSED_PREP)
     int train_tc_recompute = 1;  // backward on the tensor cores: 1 recompute + input gradients, 2 recompute only (WSKPN_TUNE_TRAIN_RECOMPUTE)
     int host_bands = 0;         // bands of the host-buffer pipeline, 0 = automatic (WSKPN_TUNE_HOST_BANDS)
     int host_first_pct = 100;   // first band's height in % of the others (WSKPN_TUNE_HOST_FIRST_BAND)
@@ -112,6 +113,7 @@ wskpn_status tc_layer_alloc(Layer& L, int KS, bool fp8, bool fp8_lo, std::string
 // every layer input is (the training recompute needs all of them split).
 int tc_split_of(const wskpn_ctx* ctx, int l);
 bool tc_split_all(const wskpn_ctx* ctx);
+bool tc_fused_prep_supported(const wskpn_ctx* ctx);
 // x_0 .. x_{L-1} as NHWC hi/lo into xs[l]; with bits, also the positive-
 // channel bits of x_1 .. x_{L-1} into (*bits)[l] (two words per pixel).
 wskpn_status tc_recompute_nhwc(wskpn_ctx* ctx, const wskpn_frame* frames, int B, int H, int W,

@@ -6,15 +6,10 @@
 #include <cuda_fp8.h>
 
 #include "common.cuh"
+#include "prep.cuh"
 #include "quant.cuh"
 
 namespace wskpn {
-
-__device__ __forceinline__ float exp2f_fast(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 struct PrepArgs {
     FrameBatch f;
@@ -24,24 +19,12 @@ struct PrepArgs {
     float qscale;                    // e4m3 layout: 1 / activation scale
 };
 
-// FAST (layouts stored as BF16 or e4m3, whose rounding is 2^-9 or coarser):
-// t^(1/gamma) as 2^(log2(t) / gamma) with the hardware's approximate log2
-// and exp2 (relative error near 2^-21 for t in (0, 1]; t = 0 gives 0);
-// the FP32 layout keeps powf.
+// The 10 input channels of pixel g of frame b (prep.cuh).
 template <bool FAST = false>
 __device__ __forceinline__ void prep_pixel(const PrepArgs& a, int b, size_t g, size_t HW, float* v) {
-    const float* r = a.f.r.p[b];
-    const float* al = a.f.a.p[b];
-    const float* n = a.f.n.p[b];
-    const float* d = a.f.d.p[b];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float t = fminf(fmaxf(r[c * HW + g], 0.f), 1.f);
-        v[c] = FAST ? exp2f_fast(__log2f(t) * a.inv_gamma) : powf(t, a.inv_gamma);
-        v[3 + c] = al[c * HW + g];
-        v[6 + c] = 0.5f * n[c * HW + g] + 0.5f;
-    }
-    v[9] = (d[g] - a.dnear) * a.dscale;
+    float raw[10];
+    prep_load_raw(a.f.r.p[b], a.f.a.p[b], a.f.n.p[b], a.f.d.p[b], g, HW, raw);
+    prep_from_raw<FAST>(raw, PrepConst{a.inv_gamma, a.dnear, a.dscale}, v);
 }
 
 // Planar FP32 output [10][H][W] (the FP32 path's layout).
@@ -88,19 +71,12 @@ __global__ void prep_nhwc16_bf16x2_kernel(PrepArgs a) {
         prep_pixel<true>(a, b, g, HW, v);
 #pragma unroll
         for (int j = 10; j < 16; ++j) v[j] = 0.f;
-        __nv_bfloat162 h[8], l[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-            const float2 hf = __bfloat1622float2(h[j]);
-            l[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
-        }
-        const uint4* hv = reinterpret_cast<const uint4*>(h);
-        const uint4* lv = reinterpret_cast<const uint4*>(l);
-        out[4 * g] = hv[0];
-        out[4 * g + 1] = hv[1];
-        out[4 * g + 2] = lv[0];
-        out[4 * g + 3] = lv[1];
+        uint4 q[4];
+        bf16_hilo16(v, q);
+        out[4 * g] = q[0];
+        out[4 * g + 1] = q[1];
+        out[4 * g + 2] = q[2];
+        out[4 * g + 3] = q[3];
     }
 }
 
