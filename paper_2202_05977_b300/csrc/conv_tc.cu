@@ -170,11 +170,25 @@ __host__ __device__ constexpr int xf_rows_per_tile(int KS) { return 256 / (KS * 
 // stages fit (one barrier wait and one commit per stage instead of per row:
 // conv1 0.158 -> 0.130, conv2 0.269 -> 0.232, conv4 0.381 -> 0.341 ms at
 // 1080p), else one.
-__host__ __device__ constexpr int tc_rows_per_item(int KS, int cout_g, int ncc_in, int ncc_w) {
-    return tc_fixed_bytes(KS, cout_g, ncc_w) + 8 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448   ? 4
-           : tc_fixed_bytes(KS, cout_g, ncc_w) + 6 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 3
-           : tc_fixed_bytes(KS, cout_g, ncc_w) + 4 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 2
-                                                                                                  : 1;
+// extra: further fixed bytes of the kernel (the epilogue staging, below).
+__host__ __device__ constexpr int tc_rows_per_item(int KS, int cout_g, int ncc_in, int ncc_w, size_t extra = 0) {
+    return tc_fixed_bytes(KS, cout_g, ncc_w) + extra + 8 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448   ? 4
+           : tc_fixed_bytes(KS, cout_g, ncc_w) + extra + 6 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 3
+           : tc_fixed_bytes(KS, cout_g, ncc_w) + extra + 4 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 2
+                                                                                                          : 1;
+}
+// Epilogue staging (STG): each epilogue warp writes a row's 32 output
+// pixels of BF16 hi/lo pairs (4 x cout bytes each) into shared memory at a
+// pitch of an odd number of 16-byte units (conflict-free per lane), then
+// stores them back as 512-byte contiguous pieces per warp instruction,
+// instead of one 16-byte piece per lane 4 x cout bytes apart (a partial
+// sector per lane).  Built for BF16 layers of at most 48 output channels
+// whose weights, staging and two input stages fit in shared memory.
+__host__ __device__ constexpr size_t tc_stg_pitch(int cout_g) { return (size_t)4 * cout_g + 16; }
+__host__ __device__ constexpr size_t tc_stg_bytes(int cout_g) { return 4 * 32 * tc_stg_pitch(cout_g) + 16; }
+__host__ __device__ constexpr bool tc_stg_fits(int KS, int cout_g, int ncc_in, int ncc_w) {
+    return cout_g <= 48 &&
+           tc_fixed_bytes(KS, cout_g, ncc_w) + tc_stg_bytes(cout_g) + 2 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448;
 }
 // The accumulate flag is a compile-time constant: a predicate computed at
 // run time costs about twice the issue time of the MMA itself.
@@ -368,7 +382,8 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
     constexpr int CPB = chunks_per_box(NCC_IN);
     constexpr int NBOX = NCC_IN / CPB;
     constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB * CPB;
-    constexpr int RPI = tc_rows_per_item(KS, COUT_P, NCC_IN, NCC_W);
+    constexpr bool STG = !FP8 && !XF && EPI == 0 && tc_stg_fits(KS, COUT_P, NCC_IN, NCC_W);
+    constexpr int RPI = tc_rows_per_item(KS, COUT_P, NCC_IN, NCC_W, STG ? tc_stg_bytes(COUT_P) : 0);
     static_assert(COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256, "MMA N");
     static_assert(2 * R * NCB <= 512, "TMEM columns");
 
@@ -394,6 +409,8 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
     float* const sEdge = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(s_scale) + 2 * 64 * sizeof(float) + 15) & ~uintptr_t(15));
     volatile int* const sOk = reinterpret_cast<volatile int*>(sEdge + 2 * 4 * (KS - 1) * (KS - 1) * 17);
+    // STG: the epilogue warps' staging rows, after the 2 x 64 floats
+    uint8_t* const sStg = reinterpret_cast<uint8_t*>(sEdge);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // Every CTA of this persistent grid is resident from the start, so the
@@ -620,6 +637,11 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
         const int p = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         int lt = 0, rowc = 0;
+        // STG: the whole stored pixel is this launch's (one group, no padding
+        // channels, BF16 hi/lo output of a hidden layer)
+        const bool coal = STG && !a.last && a.split_out && a.out_c0 == 0 && a.out_cp == COUT_P && a.zero_n == 0 &&
+                          a.dup_src < 0;
+        (void)coal;
         // GM: this thread's sums of its masked gradient values per channel,
         // over its pixels in tile and row order
         float bsum[GM ? COUT_P : 1];
@@ -710,7 +732,78 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                         }
                     }
                 }
-            } else
+            } else {
+            bool staged = false;
+            if constexpr (STG) {
+                if (coal) {
+                    staged = true;
+                    constexpr int NU = COUT_P / 4;  // 16-byte units of a stored pixel: hi then lo
+                    constexpr uint32_t PITCH = (uint32_t)tc_stg_pitch(COUT_P);
+                    uint8_t* const stw = sStg + (size_t)q * 32 * PITCH;  // this warp's 32 pixel slots
+                    uint8_t* const slot = stw + (size_t)lane * PITCH;
+                    const int xw = tx * TPX + q * 32;  // the warp's first pixel
+#pragma unroll 1
+                    for (int r = 0; r < R; ++r) {
+                        const int y = ty * R + r;
+                        const uint32_t col = (uint32_t)(buf * R * NCB + (R - 1 - r) * NCB);
+                        uint32_t u[COUT_P / 16][16];
+#pragma unroll
+                        for (int c16 = 0; c16 < COUT_P / 16; ++c16)
+                            tmem_ld16_async(tmem + lane_base + col + c16 * 16, u[c16]);
+#pragma unroll
+                        for (int c16 = 0; c16 < COUT_P / 16; ++c16) tmem_wait16(u[c16]);
+#pragma unroll
+                        for (int c16 = 0; c16 < COUT_P / 16; ++c16)
+                            tmem_zero16(tmem + lane_base + col + c16 * 16);  // ready for the buffer's next tile
+                        if (y >= a.H) continue;  // warp-uniform
+#pragma unroll
+                        for (int c16 = 0; c16 < COUT_P / 16; ++c16) {
+                            float v[16];
+                            const float4* b4 = reinterpret_cast<const float4*>(s_bias + c16 * 16);
+#pragma unroll
+                            for (int j4 = 0; j4 < 4; ++j4) {
+                                const float4 bb = b4[j4];
+                                v[4 * j4] = __uint_as_float(u[c16][4 * j4]) + bb.x;
+                                v[4 * j4 + 1] = __uint_as_float(u[c16][4 * j4 + 1]) + bb.y;
+                                v[4 * j4 + 2] = __uint_as_float(u[c16][4 * j4 + 2]) + bb.z;
+                                v[4 * j4 + 3] = __uint_as_float(u[c16][4 * j4 + 3]) + bb.w;
+                            }
+                            if (a.relu)
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+                            __nv_bfloat162 h2[8], l2[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                                const float2 hf = __bfloat1622float2(h2[j]);
+                                l2[j] = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+                            }
+                            const uint4* hs = reinterpret_cast<const uint4*>(h2);
+                            const uint4* ls = reinterpret_cast<const uint4*>(l2);
+                            uint4* const sh = reinterpret_cast<uint4*>(slot) + 2 * c16;
+                            uint4* const sl = reinterpret_cast<uint4*>(slot) + NU / 2 + 2 * c16;
+                            sh[0] = hs[0];
+                            sh[1] = hs[1];
+                            sl[0] = ls[0];
+                            sl[1] = ls[1];
+                        }
+                        __syncwarp();
+                        // the warp's pixels are contiguous in the NHWC output:
+                        // unit g of the run is pixel g / NU, unit g % NU
+                        uint8_t* const orow =
+                            static_cast<uint8_t*>(a.out) + (((size_t)b * a.H + y) * a.W + xw) * (size_t)(4 * COUT_P);
+#pragma unroll
+                        for (int k = 0; k < NU; ++k) {
+                            const int g = k * 32 + lane;
+                            const int pp = g / NU, uu = g - pp * NU;
+                            const uint4 val = *reinterpret_cast<const uint4*>(stw + (size_t)pp * PITCH + uu * 16);
+                            if (xw + pp < a.W) *reinterpret_cast<uint4*>(orow + (size_t)g * 16) = val;
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+            if (!staged)
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const int y = ty * R + r;
@@ -827,6 +920,7 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                         if (a.split_out) *reinterpret_cast<uint4*>(zb + (size_t)a.out_cp * EB + zc) = zero;
                     }
                 }
+            }
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
@@ -1241,8 +1335,11 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
         err = "conv_tc: folded-tap weights outside the last layer";
         return WSKPN_EINVAL;
     }
-    const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w) + (xf ? tc_xf_bytes(KS) : 0);
-    a.stage_bytes = tc_rows_per_item(KS, cg, ncc_in, ncc_w) * a.row_bytes;  // the kernel's own RPI
+    const bool gm0 = r.gbits != nullptr, rb0 = r.relu_bits != nullptr;
+    // the kernel's epilogue staging (its STG): as the kernel decides it
+    const size_t stg = !fp8 && !xf && !gm0 && !rb0 && tc_stg_fits(KS, cg, ncc_in, ncc_w) ? tc_stg_bytes(cg) : 0;
+    const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w) + (xf ? tc_xf_bytes(KS) : 0) + stg;
+    a.stage_bytes = tc_rows_per_item(KS, cg, ncc_in, ncc_w, stg) * a.row_bytes;  // the kernel's own RPI
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
         err = "conv_tc: layer weights and two input stages do not fit in shared memory";
         return WSKPN_EUNSUPPORTED;
