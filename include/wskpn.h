@@ -529,14 +529,14 @@ wskpn_status wskpn_profile_read(wskpn_ctx* ctx, float* ms, int cap, int* n_stage
  *     backward recomputes the layer inputs (default); 1 = wskpn_forward_train
  *     keeps them for the backward (see there), at 4 bytes per channel of
  *     every layer input per pixel (0.64 GB for 16 crops of 256 x 256).
- *   WSKPN_TUNE_FUSED_PREP (BF16 inference): 1 = the first convolution
- *     assembles its own input tiles from the FP32 frame buffers (the
- *     Sec. 5.1 tone map and scalings, split into BF16 hi/lo pairs, written
- *     to shared memory by four extra warps of that kernel) and the
- *     assembled input is never stored (default; applies when the first
- *     layer's input is a hi/lo pair and a kernel is built for its shape,
- *     10 -> 32); 0 = a separate assembly kernel stores the input in HBM and
- *     the first convolution reads it back.  Both give the same bits.
+ *   WSKPN_TUNE_FUSED_PREP (BF16 / FP8 inference): 1 = the first
+ *     convolution assembles its own input tiles from the FP32 frame buffers
+ *     (the Sec. 5.1 tone map and scalings, split into BF16 or e4m3 hi/lo
+ *     pairs, written to shared memory by four extra warps of that kernel)
+ *     and the assembled input is never stored (default; applies when the
+ *     first layer's input is a hi/lo pair and a kernel is built for its
+ *     shape, 10 -> 32); 0 = a separate assembly kernel stores the input in
+ *     HBM and the first convolution reads it back.  Both give the same bits.
  * Errors: EINVAL for an unknown key or value. */
 #define WSKPN_TUNE_TC_SPLIT 2
 #define WSKPN_TUNE_TRAIN_RECOMPUTE 3

@@ -109,6 +109,7 @@ struct TcArgs {
     // constants; the layer input is then never stored
     FrameBatch frames;
     PrepConst prep;
+    float in_qscale;  // PIN, e4m3 input: 1 / the input's activation scale
 };
 
 // ------------------------------------------------------------- primitives
@@ -368,8 +369,9 @@ template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int R, int WM, bo
 __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
     constexpr bool GM = EPI == 1, RB = EPI == 2;
-    static_assert(!PIN || (!FP8 && !XF && EPI == 0 && NCC_IN == 2 && NCC_W == 1),
-                  "input assembly in the producer: the first BF16 layer with hi/lo input pairs");
+    static_assert(!PIN || (!XF && EPI == 0 && NCC_IN == 2 && NCC_W == 1 && (!FP8 || WM == 2)),
+                  "input assembly in the producer: the first layer with hi/lo input pairs (BF16, or e4m3 with "
+                  "the trailing half chunk)");
     constexpr int PAD = KS / 2;
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
     constexpr int NCB = XF ? KS * COUT_P : COUT_P;        // TMEM columns of one output row's accumulators
@@ -561,7 +563,8 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
         // The first layer's input tiles straight from the FP32 frame buffers
         // (Sec. 5.1 assembly, the same functions and bits as the separate
         // assembly kernel): each stage row holds the 128 + KS - 1 input pixels
-        // of one tile row as 64-byte rows [hi(16) | lo(16)] in the 64-byte
+        // of one tile row as 64-byte rows, [hi(16) | lo(16)] BF16 or
+        // [hi(16) | hi(16) | lo(16) | 0(16)] e4m3, in the 64-byte
         // swizzle (16-byte unit u of a row at unit u ^ (address bits 7-8)),
         // which is what the TMA writes from the stored NHWC input, so the MMA
         // side is unchanged.  Pixels outside the image are the convolution's
@@ -613,7 +616,14 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                             prep_from_raw<true>(raw[k], a.prep, v);
 #pragma unroll
                             for (int c = 10; c < 16; ++c) v[c] = 0.f;
-                            bf16_hilo16(v, qv);
+                            if constexpr (FP8) {
+                                // e4m3 hi/lo of v / scale: [hi | hi | lo | 0], the
+                                // layer's trailing half chunk (as the assembly kernel)
+                                fp8_pack16(v, a.in_qscale, qv[0], &qv[2]);
+                                qv[1] = qv[0];
+                            } else {
+                                bf16_hilo16(v, qv);
+                            }
                         }
                         uint8_t* const row = stg + (size_t)j * a.row_bytes + (size_t)px * 64;
                         const int sw = (px >> 1) & 3;
@@ -1179,6 +1189,10 @@ static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8
             if (KS == 5) launch = launch_tc_t<5, 32, 2, 1, false, 0, false, 0, true>;
             if (KS == 3) launch = launch_tc_t<3, 32, 2, 1, false, 0, false, 0, true>;
         }
+        if (!xf && !gm && !rb && fp8 && wm == 2 && cg == 32 && ncc_in == 2 && ncc_w == 1) {
+            if (KS == 5) launch = launch_tc_t<5, 32, 2, 1, true, 2, false, 0, true>;
+            if (KS == 3) launch = launch_tc_t<3, 32, 2, 1, true, 2, false, 0, true>;
+        }
         return launch;
     }
 #define WSKPN_TC_CASE(ks_, n_, nin_, nw_, f8_, wm_)                                                    \
@@ -1272,6 +1286,7 @@ struct TcRun {
     // PIN kernels) instead of reading a stored input; in is then unused
     const wskpn_frame* frames = nullptr;
     PrepConst prep{};
+    float in_qscale = 1.f;  // e4m3 input: 1 / its activation scale
 };
 
 static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int H, int W, cudaStream_t st,
@@ -1291,8 +1306,8 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));  // unused by the PIN kernels
     if (pin) {
-        if (fp8 || !split || r.last || !r.relu || r.gbits || r.relu_bits || L.xfold) {
-            err = "conv_tc: input assembly in the first layer needs a BF16 ReLU layer with hi/lo input";
+        if (!split || r.last || !r.relu || r.gbits || r.relu_bits || L.xfold) {
+            err = "conv_tc: input assembly in the first layer needs a ReLU layer with hi/lo input";
             return WSKPN_EINVAL;
         }
     } else {
@@ -1398,6 +1413,7 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
                 a.frames.d.p[j] = r.frames[b0 + j].depth;
             }
             a.prep = r.prep;
+            a.in_qscale = r.in_qscale;
         }
         for (int g = 0; g < G; ++g) {  // each group reads the whole input and writes its channels
             a.wimg = static_cast<const uint8_t*>(L.wtc) + g * group_bytes;
@@ -1461,19 +1477,30 @@ static wskpn_status conv_tc(wskpn_ctx* ctx, int l, const void* in, void* out, in
         r.prep.inv_gamma = (float)(1.0 / (double)c.gamma);
         r.prep.dnear = c.depth_near;
         r.prep.dscale = (float)(1.0 / ((double)c.depth_far - (double)c.depth_near));
+        if (fp8) r.in_qscale = 1.f / ctx->act_scale[0];
     }
     return tc_run(r, in, out, B, H, W, st, ctx->err);
 }
 
-// The context's first layer can assemble its own input (BF16 context,
-// hi/lo input pairs, a kernel built for the layer's shape).
+// The context's first layer can assemble its own input (hi/lo input pairs,
+// BF16 or e4m3, and a kernel built for the layer's shape).
 bool tc_fused_prep_supported(const wskpn_ctx* ctx) {
     const wskpn_config& c = ctx->cfg;
-    if (c.prec != WSKPN_BF16 || c.n_layers < 2 || !tc_split_of(ctx, 0)) return false;
+    if (c.n_layers < 2) return false;
     const Layer& L = ctx->layers[0];
     if (L.xfold || L.groups != 1) return false;
-    return select_tc_kernel(c.conv_ks, L.cout_p, 2 * (L.cin_p / 16), L.cin_p / 16, false, 0, false, false, false,
-                            true) != nullptr;
+    if (c.prec == WSKPN_BF16) {
+        if (!tc_split_of(ctx, 0)) return false;
+        return select_tc_kernel(c.conv_ks, L.cout_p, 2 * (L.cin_p / 16), L.cin_p / 16, false, 0, false, false,
+                                false, true) != nullptr;
+    }
+    if (c.prec == WSKPN_FP8) {
+        if (!ctx->fp8_split || fp8_weight_mode(L.cin) != 2) return false;
+        const int ncc_in = 2 * (L.cin_p / 32);
+        return select_tc_kernel(c.conv_ks, L.cout_p, ncc_in, ncc_in - 1, true, 2, false, false, false, true) !=
+               nullptr;
+    }
+    return false;
 }
 
 bool tc_relu_bits_supported(const wskpn_ctx* ctx, int l) {
@@ -1625,14 +1652,19 @@ static wskpn_status tc_logits_fp8(wskpn_ctx* ctx, const wskpn_frame* frames, int
     std::vector<void*> x0(B);
     const int split = ctx->fp8_split;
     for (int b = 0; b < B; ++b) x0[b] = A + (size_t)b * ctx->layers[0].cin_p * (split ? 2 : 1) * HW;
-    wskpn_status s = launch_prep_fp8(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(),
-                                     ctx->act_scale[0], split, st, ctx->err);
-    if (s) return s;
+    // the first layer assembles its input tiles itself unless tuned off
+    const bool fused = ctx->fused_prep && tc_fused_prep_supported(ctx);
+    wskpn_status s = WSKPN_OK;
+    if (!fused) {
+        s = launch_prep_fp8(frames, B, H, W, c.gamma, c.depth_near, c.depth_far, x0.data(), ctx->act_scale[0],
+                            split, st, ctx->err);
+        if (s) return s;
+    }
     prof_mark(ctx, 1, st);
     for (int l = 0; l < c.n_layers; ++l) {
         const void* in = l % 2 == 0 ? (const void*)A : (const void*)Bf;
         void* out = l == c.n_layers - 1 ? (void*)z : ((l + 1) % 2 == 0 ? (void*)A : (void*)Bf);
-        s = conv_tc(ctx, l, in, out, B, H, W, st);
+        s = conv_tc(ctx, l, in, out, B, H, W, st, nullptr, l == 0 && fused ? frames : nullptr);
         if (s) return s;
         prof_mark(ctx, 2 + l, st);
     }

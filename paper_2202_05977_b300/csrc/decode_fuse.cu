@@ -485,7 +485,9 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     const int b = blockIdx.z;
     const int H = args.H, W = args.W, M = args.M;
     const size_t HW = (size_t)H * W;
-    const int tx0 = blockIdx.x * dfv::TW, ty0 = blockIdx.y * dfv::TH;
+    // tiles bottom row first: the logits the convolution wrote last (the
+    // bottom of the frame) are the ones still in L2 when this kernel starts
+    const int tx0 = blockIdx.x * dfv::TW, ty0 = (gridDim.y - 1 - blockIdx.y) * dfv::TH;
     const float* __restrict__ z = args.z.p[b];
     const float* __restrict__ r = args.r.p[b];
     const float* __restrict__ a = DEMOD ? args.a.p[b] : nullptr;

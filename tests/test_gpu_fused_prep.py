@@ -1,4 +1,4 @@
-"""GPU: the first BF16 convolution assembling its own input tiles (Sec. 5.1
+"""GPU: the first BF16 / FP8 convolution assembling its own input tiles (Sec. 5.1
 tone map and scalings inside the kernel's producer, WSKPN_TUNE_FUSED_PREP =
 1, the default) against the separate assembly kernel followed by the
 convolution reading the stored input (= 0).  Both run the same per-pixel
@@ -23,12 +23,15 @@ def wk():
     return wk
 
 
-def _logits_both(wk, wb, frames, **kw):
+def _logits_both(wk, wb, frames, precision="bf16", **kw):
     H, W = frames[0]["radiance"].shape[-2:]
     dev = to_dev(stack_frames(frames))
     outs = []
     for fused in (1, 0):
-        d = wk.Denoiser(wb, precision="bf16", max_hw=(H, W), max_batch=len(frames), **kw)
+        d = wk.Denoiser(wb, precision=precision, max_hw=(H, W), max_batch=len(frames), **kw)
+        if precision == "fp8":  # static activation scales from another frame
+            cal = to_dev(stack_frames([synth.make_frame(H, W, 999)]))
+            d.calibrate(*args(cal))
         d.set_tuning(FUSED_PREP, fused)
         outs.append(d.logits(*args(dev)).cpu().numpy())
         assert d.device_status() == 0
@@ -42,6 +45,15 @@ def test_fused_prep_bit_identical(wk, B, H, W):
     frames = [synth.make_frame(H, W, 70 + b) for b in range(B)]
     wb = synth.make_weights(seed=7)
     fused, plain = _logits_both(wk, wb, frames)
+    assert np.array_equal(fused, plain)
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 64, 64), (2, 45, 67), (1, 14, 200), (1, 130, 257)])
+def test_fused_prep_fp8_bit_identical(wk, B, H, W):
+    # e4m3 hi/lo input assembled inside the first layer ([hi | hi | lo | 0])
+    frames = [synth.make_frame(H, W, 80 + b) for b in range(B)]
+    wb = synth.make_weights(seed=11)
+    fused, plain = _logits_both(wk, wb, frames, precision="fp8")
     assert np.array_equal(fused, plain)
 
 
