@@ -155,8 +155,16 @@ __host__ __device__ constexpr uint32_t tc_row_bytes(int KS, int ncc_in) {
     return (uint32_t)(ncc_in / chunks_per_box(ncc_in)) *
            (uint32_t)(((128 + KS - 1) * 32 * chunks_per_box(ncc_in) + 1023) / 1024 * 1024);
 }
-__host__ __device__ constexpr size_t tc_fixed_bytes(int KS, int cout_g, int ncc_w) {
-    return 1024 + ((size_t)KS * KS * ncc_w * cout_g * 32 + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
+// Folded horizontal taps (XF, the last layer): TMEM columns and weight-image
+// rows of one output row's accumulators, the KS horizontal taps of cr
+// output channels each (cr = 12 or 16), padded to a multiple of 16.
+__host__ __device__ constexpr int xf_ncb(int KS, int cr) { return (KS * cr + 15) / 16 * 16; }
+// Weight-image bytes of one output-channel group (xf_cr: folded, cr channels per tap block; 0: not folded).
+__host__ __device__ constexpr size_t tc_wimg_bytes(int KS, int cout_g, int ncc_w, int xf_cr = 0) {
+    return xf_cr ? (size_t)KS * ncc_w * xf_ncb(KS, xf_cr) * 32 : (size_t)KS * KS * ncc_w * cout_g * 32;
+}
+__host__ __device__ constexpr size_t tc_fixed_bytes(int KS, int cout_g, int ncc_w, int xf_cr = 0) {
+    return 1024 + (tc_wimg_bytes(KS, cout_g, ncc_w, xf_cr) + 1023) / 1024 * 1024 + 256 + 2 * 64 * sizeof(float);
 }
 // Folded horizontal taps (XF, the last layer with 16 output channels): the
 // epilogue warps exchange the partial sums of their edge pixels through
@@ -165,18 +173,20 @@ __host__ __device__ constexpr size_t tc_fixed_bytes(int KS, int cout_g, int ncc_
 __host__ __device__ constexpr size_t tc_xf_bytes(int KS) {
     return (size_t)2 * 4 * (KS - 1) * (KS - 1) * 17 * sizeof(float) + 64;
 }
-// Output rows per tile of the folded form: N = (vertical taps) x KS x 16 <= 256.
-__host__ __device__ constexpr int xf_rows_per_tile(int KS) { return 256 / (KS * 16); }
+// Output rows per tile of the folded form: N = (vertical taps) x xf_ncb <= 256
+// (and two buffers of that many accumulator slots fill at most 512 columns).
+__host__ __device__ constexpr int xf_rows_per_tile(int KS, int cr = 16) { return 256 / xf_ncb(KS, cr); }
 // Input rows per pipeline stage: the most of 4, 3, 2 for which two such
 // stages fit (one barrier wait and one commit per stage instead of per row:
 // conv1 0.158 -> 0.130, conv2 0.269 -> 0.232, conv4 0.381 -> 0.341 ms at
 // 1080p), else one.
 // extra: further fixed bytes of the kernel (the epilogue staging, below).
-__host__ __device__ constexpr int tc_rows_per_item(int KS, int cout_g, int ncc_in, int ncc_w, size_t extra = 0) {
-    return tc_fixed_bytes(KS, cout_g, ncc_w) + extra + 8 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448   ? 4
-           : tc_fixed_bytes(KS, cout_g, ncc_w) + extra + 6 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 3
-           : tc_fixed_bytes(KS, cout_g, ncc_w) + extra + 4 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 2
-                                                                                                          : 1;
+__host__ __device__ constexpr int tc_rows_per_item(int KS, int cout_g, int ncc_in, int ncc_w, size_t extra = 0,
+                                                   int xf_cr = 0) {
+    return tc_fixed_bytes(KS, cout_g, ncc_w, xf_cr) + extra + 8 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448   ? 4
+           : tc_fixed_bytes(KS, cout_g, ncc_w, xf_cr) + extra + 6 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 3
+           : tc_fixed_bytes(KS, cout_g, ncc_w, xf_cr) + extra + 4 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448 ? 2
+                                                                                                                : 1;
 }
 // Epilogue staging (STG): each epilogue warp writes a row's 32 output
 // pixels of BF16 hi/lo pairs (4 x cout bytes each) into shared memory at a
@@ -275,11 +285,12 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
     if constexpr (XF) {
         // Folded horizontal taps: one MMA per (activation chunk, weight chunk)
         // product covers the input row's vertical taps dy0..dy1 and all KS
-        // horizontal taps, N = nb x KS x COUT_P columns ordered (dy, dx,
-        // channel); accumulator row slots hold KS x COUT_P columns, and the
+        // horizontal taps, N = nb x NCB columns ordered (dy, dx, channel),
+        // NCB = KS x COUT_P rounded up to 16 (COUT_P = 12 or 16 channels per
+        // tap block); accumulator row slots hold NCB columns, and the
         // epilogue adds the dx-shifted partial sums.  The A operand is the
         // unshifted row window (input pixels x0 - PAD ..).  Products as below.
-        constexpr int NCB = KS * COUT_P;
+        constexpr int NCB = xf_ncb(KS, COUT_P);
         static_assert(NCB * (R < KS ? R : KS) <= 256, "MMA N");
         const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
         const int dy1 = ri < KS - 1 ? ri : KS - 1;
@@ -288,7 +299,7 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
         constexpr uint32_t IDESC0 =
             (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(tc::BM >> 4) << 24);
         const uint32_t idesc = IDESC0 | ((uint32_t)((nb * NCB) >> 3) << 17);
-        constexpr uint32_t b_blk = (COUT_P * tc::ROWB) >> 4;  // one (dy, dx) block of a chunk, 16-byte units
+        constexpr uint32_t b_blk = (NCB * tc::ROWB) >> 4;  // one dy block (all dx) of a chunk, 16-byte units
         constexpr int CPB = chunks_per_box(NCC_IN);
         const uint32_t d = dbase + (uint32_t)((R - 1 - (ri - dy0)) * NCB);
         constexpr int nA = NCC_IN / 2;
@@ -309,11 +320,11 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
                 cw = 2 * NF;
             }
             const uint64_t a = ad + (uint64_t)((ca / CPB) * box_step + (ca % CPB) * (tc::ROWB >> 4));
-            const uint64_t b = bd + (uint64_t)((cw * KS + dy0) * KS * b_blk);
+            const uint64_t b = bd + (uint64_t)((cw * KS + dy0) * b_blk);
             mma<FP8, true>(d, a, b, idesc);
         }
         return;
-    }
+    } else {
     static_assert(COUT_P % 16 == 0 && COUT_P * (R < KS ? R : KS) <= 256, "MMA N");
     const int dy0 = ri - (R - 1) > 0 ? ri - (R - 1) : 0;
     const int dy1 = ri < KS - 1 ? ri : KS - 1;
@@ -360,6 +371,7 @@ __device__ __forceinline__ void issue_item(int ri, uint32_t dbase, uint64_t ad, 
             mma<FP8, true>(d, a, b, idesc);
         }
     }
+    }
 }
 
 // ----------------------------------------------------------------- kernel
@@ -374,9 +386,9 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                   "the trailing half chunk)");
     constexpr int PAD = KS / 2;
     constexpr int CH = FP8 ? 32 : 16;  // channels per K chunk
-    constexpr int NCB = XF ? KS * COUT_P : COUT_P;        // TMEM columns of one output row's accumulators
+    constexpr int NCB = XF ? xf_ncb(KS, COUT_P) : COUT_P;  // TMEM columns of one output row's accumulators
     constexpr int TPX = XF ? tc::BM - (KS - 1) : tc::BM;  // output pixels per tile row
-    static_assert(!XF || COUT_P == 16, "folded taps: 16 output channels");
+    static_assert(!XF || COUT_P == 16 || COUT_P == 12, "folded taps: 12 or 16 output channels per tap block");
     static_assert(!GM || (!XF && !FP8 && COUT_P <= 64), "gradient mask: BF16, at most 64 channels");
     static_assert(!RB || (!XF && !FP8 && COUT_P <= 64), "ReLU bits: BF16, at most 64 channels");
     constexpr uint32_t NCOL = tmem_cols<NCB, R>();
@@ -385,8 +397,8 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
     constexpr int NBOX = NCC_IN / CPB;
     constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB * CPB;
     constexpr bool STG = !FP8 && !XF && EPI == 0 && tc_stg_fits(KS, COUT_P, NCC_IN, NCC_W);
-    constexpr int RPI = tc_rows_per_item(KS, COUT_P, NCC_IN, NCC_W, STG ? tc_stg_bytes(COUT_P) : 0);
-    static_assert(COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256, "MMA N");
+    constexpr int RPI = tc_rows_per_item(KS, COUT_P, NCC_IN, NCC_W, STG ? tc_stg_bytes(COUT_P) : 0, XF ? COUT_P : 0);
+    static_assert(XF || (COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256), "MMA N");
     static_assert(2 * R * NCB <= 512, "TMEM columns");
 
     extern __shared__ __align__(1024) uint8_t dsmem[];
@@ -693,35 +705,38 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                 for (int r = 0; r < R; ++r, ++rowc) {
                     const int y = ty * R + r;
                     const uint32_t col = (uint32_t)(buf * R * NCB + (R - 1 - r) * NCB);
-                    uint32_t u[KS][16];
+                    // the slot's NCB columns: tap dx's channel o at column dx COUT_P + o
+                    constexpr int NL = NCB / 16;
+                    uint32_t u[NL][16];
 #pragma unroll
-                    for (int dx = 0; dx < KS; ++dx) tmem_ld16_async(tmem + lane_base + col + dx * 16, u[dx]);
+                    for (int c = 0; c < NL; ++c) tmem_ld16_async(tmem + lane_base + col + c * 16, u[c]);
 #pragma unroll
-                    for (int dx = 0; dx < KS; ++dx) tmem_wait16(u[dx]);
+                    for (int c = 0; c < NL; ++c) tmem_wait16(u[c]);
 #pragma unroll
-                    for (int dx = 0; dx < KS; ++dx) tmem_zero16(tmem + lane_base + col + dx * 16);
-                    float v[KS][16];
+                    for (int c = 0; c < NL; ++c) tmem_zero16(tmem + lane_base + col + c * 16);
+                    float v[KS][COUT_P];
 #pragma unroll
                     for (int dx = 0; dx < KS; ++dx)
 #pragma unroll
-                        for (int o = 0; o < 16; ++o) v[dx][o] = __uint_as_float(u[dx][o]);
+                        for (int o = 0; o < COUT_P; ++o)
+                            v[dx][o] = __uint_as_float(u[(dx * COUT_P + o) / 16][(dx * COUT_P + o) % 16]);
                     float* const eb = sEdge + (rowc & 1) * (4 * (KS - 1) * (KS - 1) * 17);
                     if (lane < KS - 1) {
 #pragma unroll
                         for (int dx = 1; dx < KS; ++dx)
 #pragma unroll
-                            for (int o = 0; o < 16; ++o)
+                            for (int o = 0; o < COUT_P; ++o)
                                 eb[((q * (KS - 1) + lane) * (KS - 1) + dx - 1) * 17 + o] = v[dx][o];
                     }
                     asm volatile("bar.sync 1, 128;" ::: "memory");
-                    float acc[16];
+                    float acc[COUT_P];
 #pragma unroll
-                    for (int o = 0; o < 16; ++o) acc[o] = v[0][o];
+                    for (int o = 0; o < COUT_P; ++o) acc[o] = v[0][o];
 #pragma unroll
                     for (int dx = 1; dx < KS; ++dx) {
                         const int src = lane + dx - 32;  // >= 0: lane src of the next warp
 #pragma unroll
-                        for (int o = 0; o < 16; ++o) {
+                        for (int o = 0; o < COUT_P; ++o) {
                             float sv = __shfl_down_sync(0xffffffffu, v[dx][o], dx);
                             if (src >= 0) sv = q < 3 ? eb[(((q + 1) * (KS - 1) + src) * (KS - 1) + dx - 1) * 17 + o] : 0.f;
                             acc[o] += sv;
@@ -730,16 +745,9 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                     if (p < TPX && x < a.W && y < a.H) {
                         const size_t HW = (size_t)a.H * a.W;
                         float* z = static_cast<float*>(a.out) + (size_t)b * a.cout * HW + (size_t)y * a.W + x;
-                        const float4* s4 = reinterpret_cast<const float4*>(s_scale);
-                        const float4* b4 = reinterpret_cast<const float4*>(s_bias);
 #pragma unroll
-                        for (int j4 = 0; j4 < 4; ++j4) {
-                            const float4 ss = s4[j4], bb = b4[j4];
-                            const float sj[4] = {ss.x, ss.y, ss.z, ss.w}, bj[4] = {bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                if (4 * j4 + k < a.cout) z[(size_t)(4 * j4 + k) * HW] = fmaf(acc[4 * j4 + k], sj[k], bj[k]);
-                        }
+                        for (int o = 0; o < COUT_P; ++o)
+                            if (o < a.cout) z[(size_t)o * HW] = fmaf(acc[o], s_scale[o], s_bias[o]);
                     }
                 }
             } else {
@@ -1054,8 +1062,10 @@ wskpn_status tc_alloc_layer(wskpn_ctx* ctx, int l) {
 // (K-major) of tap (dy, dx) and channel chunk cc, so the KS vertical taps of
 // one (dx, cc) pair are consecutive N blocks.  32-byte swizzled like the TMA
 // writes A: byte o of a block goes to o ^ (((o >> 7) & 1) << 4).  With xf
-// (folded horizontal taps) the blocks of a chunk are ordered (dy, dx)
-// instead: block ((cc * KS + dy) * KS + dx).  e4m3
+// (folded horizontal taps, xf = channels per tap block, 12 or 16) the rows
+// of a chunk are ordered (dy, dx, channel) instead: row ((cc * KS + dy) *
+// xf_ncb + dx * xf + n), rows past KS * xf of each dy block zero (the image
+// is cleared first).  e4m3
 // weight modes (lo = e4m3(w / s - e4m3(w / s)), s the channel's scale):
 // wm 1: chunks nf .. 2 nf - 1 hold the lo halves of chunks 0 .. nf - 1;
 // wm 2: the same for nf = (ncc - 1) / 2 full chunks, then one chunk with
@@ -1079,6 +1089,7 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restr
         const int dy = xf ? (chunk / KS) % KS : chunk % KS;
         const int cc = xf ? chunk / (KS * KS) : (chunk / KS) % ncc;
         const int dx = xf ? chunk % KS : chunk / (KS * ncc);
+        if (xf && nl >= xf) continue;  // channels past the tap block: not stored
         bool lo;
         int cin;
         if (wm == 2 && cc == 2 * nf) {  // trailing half chunk: hi | lo
@@ -1090,7 +1101,11 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, const float* __restr
         }
         const float v = (n < Cout && cin < Cin) ? w[((size_t)n * Cin + cin) * KS * KS + dy * KS + dx] : 0.f;
         const uint32_t o = (uint32_t)(nl * 32 + k * (fp8 ? 1 : 2));
-        const size_t phys = g * group_bytes + (size_t)chunk * cg * 32 + (o ^ (((o >> 7) & 1u) << 4));
+        size_t phys = g * group_bytes + (size_t)chunk * cg * 32 + (o ^ (((o >> 7) & 1u) << 4));
+        if (xf) {  // one group; swizzle on the absolute byte offset (the image is 1024-aligned)
+            const size_t oa = ((size_t)(cc * KS + dy) * xf_ncb(KS, xf) + dx * xf + nl) * 32 + k * (fp8 ? 1 : 2);
+            phys = oa ^ (((oa >> 7) & 1u) << 4);
+        }
         if (fp8) {
             const float q = v / wscale[n];
             const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
@@ -1142,11 +1157,15 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
     // runs with folded horizontal taps (fewer, wider MMAs; see issue_item)
     L.xfold = l == c.n_layers - 1 && L.cin_p == 64 && L.cout_p == 16 && L.groups == 1 &&
               (c.conv_ks == 5 || c.conv_ks == 3);
+    // tap blocks of 12 channels when the layer has at most 12 outputs (the
+    // 2M = 12 logits): 5 x 12 = 60 -> 64 columns per output row instead of 80
+    L.xf_cr = L.xfold ? (L.cout <= 12 ? 12 : 16) : 0;
+    if (L.xfold) WSKPN_CUDA_TRY(cudaMemsetAsync(L.wtc, 0, L.wtc_bytes, st), ctx->err);
     if (fp8) {
         wscale_kernel<<<L.cout_p, 128, 0, st>>>(w, L.cin, L.cout, c.conv_ks, L.cout_p, L.wscale);
         WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
     }
-    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, wm, L.xfold,
+    pack_tc_kernel<<<148, 256, 0, st>>>(w, b, L.cin, L.cout, c.conv_ks, L.cout_p, L.groups, ncc, fp8, wm, L.xf_cr,
                                         L.wscale, ctx->act_scale[l], static_cast<uint8_t*>(L.wtc), L.ep_scale,
                                         L.ep_bias);
     WSKPN_CUDA_TRY(cudaGetLastError(), ctx->err);
@@ -1156,7 +1175,7 @@ wskpn_status tc_pack_layer(wskpn_ctx* ctx, int l, cudaStream_t st) {
 template <int KS, int COUT_P, int NCC_IN, int NCC_W, bool FP8, int WM, bool XF, int EPI = 0, bool PIN = false>
 static wskpn_status launch_tc_t(const CUtensorMap& map, const TcArgs& a, size_t smem, int grid, cudaStream_t st,
                                 std::string& err) {
-    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, XF ? xf_rows_per_tile(KS) : tc::rows_per_tile(COUT_P),
+    auto kern = conv_tc_kernel<KS, COUT_P, NCC_IN, NCC_W, FP8, XF ? xf_rows_per_tile(KS, COUT_P) : tc::rows_per_tile(COUT_P),
                                WM, XF, EPI, PIN>;
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), err);
     // programmatic dependent launch: set-up overlaps the previous kernel's
@@ -1204,17 +1223,21 @@ static TcLaunch select_tc_kernel(int KS, int cg, int ncc_in, int ncc_w, bool fp8
 #define WSKPN_TC_RB(ks_, n_, nin_, nw_)                                                                    \
     if (!launch && rb && !gm && !xf && !fp8 && KS == ks_ && cg == n_ && ncc_in == nin_ && ncc_w == nw_)      \
         launch = launch_tc_t<ks_, n_, nin_, nw_, false, 0, false, 2>;
-    // the BF16 last layer 64 -> 16 with folded horizontal taps
-    // (hi/lo activations, or single BF16 values when the split is tuned off)
-    if (xf && !gm && !rb && !fp8 && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, 16, 8, 4, false, 0, true>;
-    if (xf && !gm && !rb && !fp8 && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, 16, 8, 4, false, 0, true>;
-    if (xf && !gm && !rb && !fp8 && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, false, 0, true>;
-    if (xf && !gm && !rb && !fp8 && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, false, 0, true>;
-    // e4m3 hi/lo (three products per chunk) and single-term
-    if (xf && !gm && !rb && fp8 && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, 16, 4, 4, true, 1, true>;
-    if (xf && !gm && !rb && fp8 && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, 16, 4, 4, true, 1, true>;
-    if (xf && !gm && !rb && fp8 && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, 16, 2, 2, true, 0, true>;
-    if (xf && !gm && !rb && fp8 && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, 16, 2, 2, true, 0, true>;
+    // the last layer 64 -> 12 or 16 with folded horizontal taps (tap blocks
+    // of cg = 12 or 16 channels), BF16 (hi/lo activations, or single BF16
+    // values when the split is tuned off) and e4m3 (hi/lo: three products per
+    // chunk, or single-term)
+#define WSKPN_TC_XF(n_)                                                                                          \
+    if (xf && !gm && !rb && !fp8 && cg == n_ && KS == 5 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<5, n_, 8, 4, false, 0, true>; \
+    if (xf && !gm && !rb && !fp8 && cg == n_ && KS == 3 && ncc_in == 8 && ncc_w == 4) launch = launch_tc_t<3, n_, 8, 4, false, 0, true>; \
+    if (xf && !gm && !rb && !fp8 && cg == n_ && KS == 5 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, n_, 4, 4, false, 0, true>; \
+    if (xf && !gm && !rb && !fp8 && cg == n_ && KS == 3 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, n_, 4, 4, false, 0, true>; \
+    if (xf && !gm && !rb && fp8 && cg == n_ && KS == 5 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<5, n_, 4, 4, true, 1, true>; \
+    if (xf && !gm && !rb && fp8 && cg == n_ && KS == 3 && wm == 1 && ncc_in == 4 && ncc_w == 4) launch = launch_tc_t<3, n_, 4, 4, true, 1, true>; \
+    if (xf && !gm && !rb && fp8 && cg == n_ && KS == 5 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<5, n_, 2, 2, true, 0, true>; \
+    if (xf && !gm && !rb && fp8 && cg == n_ && KS == 3 && wm == 0 && ncc_in == 2 && ncc_w == 2) launch = launch_tc_t<3, n_, 2, 2, true, 0, true>;
+    WSKPN_TC_XF(16) WSKPN_TC_XF(12)
+#undef WSKPN_TC_XF
 #define WSKPN_TC_BF16(ks_)                                                                                 \
     WSKPN_TC_CASE(ks_, 32, 1, 1, false, 0) WSKPN_TC_CASE(ks_, 32, 2, 1, false, 0)                          \
     WSKPN_TC_CASE(ks_, 48, 2, 2, false, 0) WSKPN_TC_CASE(ks_, 48, 4, 2, false, 0)                          \
@@ -1328,10 +1351,13 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
             return WSKPN_ECUDA;
         }
     }
-    const int G = L.groups, cg = L.cout_p / G;
+    const int G = L.groups, cg0 = L.cout_p / G;
+    const bool xf = L.xfold != 0;  // folded horizontal taps (the image was packed for them)
+    // the kernel's channel parameter: channels per tap block when folded
+    const int cg = xf ? L.xf_cr : cg0;
     const size_t group_bytes = L.wtc_bytes / G;
     TcArgs a{};
-    a.wbytes = (uint32_t)group_bytes;
+    a.wbytes = (uint32_t)(xf ? tc_wimg_bytes(KS, cg, ncc_w, cg) : group_bytes);
     a.out = out;
     a.B = B;
     a.H = H;
@@ -1345,16 +1371,15 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     // boxes of 128 + KS - 1 rows of cpb x 32 B, each 1024-byte aligned (128B-swizzle atom)
     a.box_stride = (uint32_t)(((tc::BM + KS - 1) * tc::ROWB * cpb + 1023) / 1024 * 1024);
     a.row_bytes = tc_row_bytes(KS, ncc_in);
-    const bool xf = L.xfold != 0;  // folded horizontal taps (the image was packed for them)
-    if (xf && !(r.last && cg == 16)) {
+    if (xf && !(r.last && cg0 == 16)) {
         err = "conv_tc: folded-tap weights outside the last layer";
         return WSKPN_EINVAL;
     }
     const bool gm0 = r.gbits != nullptr, rb0 = r.relu_bits != nullptr;
     // the kernel's epilogue staging (its STG): as the kernel decides it
     const size_t stg = !fp8 && !xf && !gm0 && !rb0 && tc_stg_fits(KS, cg, ncc_in, ncc_w) ? tc_stg_bytes(cg) : 0;
-    const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w) + (xf ? tc_xf_bytes(KS) : 0) + stg;
-    a.stage_bytes = tc_rows_per_item(KS, cg, ncc_in, ncc_w, stg) * a.row_bytes;  // the kernel's own RPI
+    const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w, xf ? cg : 0) + (xf ? tc_xf_bytes(KS) : 0) + stg;
+    a.stage_bytes = tc_rows_per_item(KS, cg, ncc_in, ncc_w, stg, xf ? cg : 0) * a.row_bytes;  // the kernel's own RPI
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
         err = "conv_tc: layer weights and two input stages do not fit in shared memory";
         return WSKPN_EUNSUPPORTED;
@@ -1365,7 +1390,7 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     size_t smem = fixed + (size_t)a.stages * a.stage_bytes;
     if (smem < 120 * 1024) smem = 120 * 1024;
     a.tiles_x = cdiv(W, xf ? tc::BM - (KS - 1) : tc::BM);
-    a.tiles_y = cdiv(H, xf ? xf_rows_per_tile(KS) : tc::rows_per_tile(cg));
+    a.tiles_y = cdiv(H, xf ? xf_rows_per_tile(KS, cg) : tc::rows_per_tile(cg));
     a.ntiles = a.tiles_x * a.tiles_y * B;
     a.status = r.status;
     a.wait_ns = r.wait_ns;

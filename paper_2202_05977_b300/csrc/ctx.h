@@ -27,6 +27,7 @@ struct Layer {
     int cin_p = 0, cout_p = 0;  // padded channel counts of the tensor-core layout
     int groups = 1;             // output-channel groups run as separate passes (weights too large for one)
     int xfold = 0;              // image packed for folded horizontal taps (BF16 last layer, 16 outputs)
+    int xf_cr = 0;              // folded: output channels per tap block (12 or 16)
 };
 
 std::string validate_config(const wskpn_config* c);
