@@ -481,12 +481,6 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     float2* sVB = sVA + dfv::TH * dfv::VP;
     int* red = reinterpret_cast<int*>(smem + dfv::OFF_R);
 
-    // Programmatic dependent launch: this grid may start while the kernel
-    // that wrote the logits drains, and lets the next kernel on the stream
-    // start its own set-up as this grid's last CTAs run; nothing global is
-    // read or written before the previous grid has completed.
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int tid = threadIdx.x;
     const int b = blockIdx.z;
     const int H = args.H, W = args.W, M = args.M;
@@ -628,17 +622,9 @@ static wskpn_status launch_fwd_variant(const DecodeArgs& args, int nb, cudaStrea
     WSKPN_CUDA_TRY(cudaFuncSetAttribute(decode_fuse_fwd_kernel<DEMOD, VEC>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dfv::SMEM_BYTES),
                    err);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cdiv(args.W, dfv::TW), cdiv(args.H, dfv::TH), nb);
-    cfg.blockDim = dim3(dfv::THREADS);
-    cfg.dynamicSmemBytes = dfv::SMEM_BYTES;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    WSKPN_CUDA_TRY(cudaLaunchKernelEx(&cfg, decode_fuse_fwd_kernel<DEMOD, VEC>, args), err);
+    dim3 grid(cdiv(args.W, dfv::TW), cdiv(args.H, dfv::TH), nb);
+    decode_fuse_fwd_kernel<DEMOD, VEC><<<grid, dfv::THREADS, dfv::SMEM_BYTES, st>>>(args);
+    WSKPN_CUDA_TRY(cudaGetLastError(), err);
     return WSKPN_OK;
 }
 
