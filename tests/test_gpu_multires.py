@@ -87,6 +87,31 @@ def test_multires_bf16_denoise_close_to_oracle(H, W, seed):
     assert mx < 1e-2 and mean_rel < 1e-3
 
 
+@pytest.fixture(scope="module")
+def mr1080():
+    """1920x1080 seed-2 frame, weights and the oracle's output and Eq. 7
+    term scale over every pixel (computed once: about 10 s on 16 cores)."""
+    f = synth.make_frame(1080, 1920, 2)
+    wb = synth.make_weights_for(omr.weight_shapes(), seed=2)
+    zs = omr.logits(f, wb)
+    ref = omr.reconstruct(zs, f["radiance"], f["albedo"])
+    scale = np.maximum(np.abs(ref), omr.term_scale(zs, f["radiance"], f["albedo"]))
+    return f, wb, ref, scale
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 1e-2)])
+def test_multires_1080p_every_pixel_matches_oracle(mr1080, precision, tol):
+    from paper_2202_05977_b300.multires import MultiResDenoiser
+    f, wb, ref, scale = mr1080
+    d = MultiResDenoiser(wb, max_hw=(1080, 1920), precision=precision)
+    out = d.denoise(*args(to_dev(stack_frames([f])))).cpu().numpy()[0]
+    e = np.abs(out - ref) / scale
+    mean_rel = rel_err(out, ref)[1]
+    print(f"multires {precision} 1080p: max err / term scale {e.max():.3e}, mean {e.mean():.3e}; "
+          f"mean rel {mean_rel:.3e}")
+    assert e.max() < tol and mean_rel < (1e-5 if precision == "fp32" else 1e-3)
+
+
 def test_multires_bf16_1080p_agrees_with_fp32_path():
     from paper_2202_05977_b300.multires import MultiResDenoiser
     f = synth.make_frame(1080, 1920, 2)
