@@ -81,7 +81,7 @@ def parse():
     p.add_argument("--serve-sweep-requests", type=int, default=2048)
     p.add_argument("--tc-split", type=int, default=None, help="BF16 activations as hi/lo pairs (1, default) or single (0)")
     p.add_argument("--fused-prep", type=int, default=None,
-                   help="BF16: the first convolution assembles its input (1, default) or a separate kernel stores it (0)")
+                   help="BF16/FP8: the first convolution assembles its input (1, default) or a separate kernel stores it (0)")
     return p.parse_args()
 
 
@@ -490,7 +490,8 @@ def main():
         return
 
     # the first layer assembles its input inside its own kernel (no prep launch)
-    fused_prep_on = args.precision == "bf16" and args.fused_prep != 0 and args.tc_split != 0
+    fused_prep_on = args.fused_prep != 0 and (args.precision == "fp8" or (args.precision == "bf16"
+                                                                          and args.tc_split != 0))
 
     def time_path(precision, steps, warmup, hw=(H, W), frame=None, widths=WIDTHS, weights=None, ks=KS, clk=None,
                   fused_prep=None):
@@ -501,7 +502,7 @@ def main():
         if args.tc_split is not None and precision == "bf16":
             d.set_tuning(2, args.tc_split)
         fp = fused_prep if fused_prep is not None else args.fused_prep
-        if fp is not None and precision == "bf16":
+        if fp is not None and precision in ("bf16", "fp8"):
             d.set_tuning(12, fp)  # WSKPN_TUNE_FUSED_PREP
         if precision == "fp8":  # static activation scales from a different frame (seed 3)
             cal = synth.make_frame(h, w, SEED + 1)
@@ -573,8 +574,9 @@ def main():
             r8 = time_path("fp8", max(5, args.steps // 2), 3)
             precision_form["fp8"] = {"ms_per_frame": r8["ms_step"], "form": "e4m3 hi/lo activations and weights",
                                      "calibration": f"static scales from the seed-{SEED + 1} frame",
-                                     "stages_ms": dict(zip(["prep"] + [f"conv{i + 1}" for i in range(len(WIDTHS) - 1)]
-                                                           + ["reconstruct"], r8["stage_ms"])),
+                                     "stages_ms": {k: v for k, v in zip(["prep"] + [f"conv{i + 1}" for i in range(len(WIDTHS) - 1)]
+                                                                       + ["reconstruct"], r8["stage_ms"])
+                                                   if not (k == "prep" and args.fused_prep != 0)},
                                      **err_vs_fp32(r8["out"])}
             form_out["fp8"] = r8["out"].cpu().numpy()[0]
             del r8

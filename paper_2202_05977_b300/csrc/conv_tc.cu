@@ -189,17 +189,23 @@ __host__ __device__ constexpr int tc_rows_per_item(int KS, int cout_g, int ncc_i
                                                                                                                 : 1;
 }
 // Epilogue staging (STG): each epilogue warp writes a row's 32 output
-// pixels of BF16 hi/lo pairs (4 x cout bytes each) into shared memory at a
-// pitch of an odd number of 16-byte units (conflict-free per lane), then
-// stores them back as 512-byte contiguous pieces per warp instruction,
-// instead of one 16-byte piece per lane 4 x cout bytes apart (a partial
-// sector per lane).  Built for BF16 layers of at most 48 output channels
-// whose weights, staging and two input stages fit in shared memory.
-__host__ __device__ constexpr size_t tc_stg_pitch(int cout_g) { return (size_t)4 * cout_g + 16; }
-__host__ __device__ constexpr size_t tc_stg_bytes(int cout_g) { return 4 * 32 * tc_stg_pitch(cout_g) + 16; }
-__host__ __device__ constexpr bool tc_stg_fits(int KS, int cout_g, int ncc_in, int ncc_w) {
-    return cout_g <= 48 &&
-           tc_fixed_bytes(KS, cout_g, ncc_w) + tc_stg_bytes(cout_g) + 2 * (size_t)tc_row_bytes(KS, ncc_in) <= 232448;
+// pixels of hi/lo pairs (4 x cout bytes each for BF16, 2 x cout for e4m3)
+// into shared memory at a pitch of an odd number of 16-byte units
+// (conflict-free per lane), then stores them back as 512-byte contiguous
+// pieces per warp instruction, instead of one 16-byte piece per lane a
+// pixel apart (a partial sector per lane).  Built for BF16 layers of at
+// most 48 output channels and e4m3 layers of 32 whose weights, staging and
+// two input stages fit in shared memory.
+__host__ __device__ constexpr size_t tc_stg_pitch(int cout_g, bool fp8 = false) {
+    return (size_t)(fp8 ? 2 : 4) * cout_g + 16;
+}
+__host__ __device__ constexpr size_t tc_stg_bytes(int cout_g, bool fp8 = false) {
+    return 4 * 32 * tc_stg_pitch(cout_g, fp8) + 16;
+}
+__host__ __device__ constexpr bool tc_stg_fits(int KS, int cout_g, int ncc_in, int ncc_w, bool fp8 = false) {
+    return (fp8 ? cout_g == 32 : cout_g <= 48) &&
+           tc_fixed_bytes(KS, cout_g, ncc_w) + tc_stg_bytes(cout_g, fp8) + 2 * (size_t)tc_row_bytes(KS, ncc_in) <=
+               232448;
 }
 // The accumulate flag is a compile-time constant: a predicate computed at
 // run time costs about twice the issue time of the MMA itself.
@@ -396,8 +402,9 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
     constexpr int CPB = chunks_per_box(NCC_IN);
     constexpr int NBOX = NCC_IN / CPB;
     constexpr uint32_t BOX_BYTES = (tc::BM + KS - 1) * tc::ROWB * CPB;
-    constexpr bool STG = !FP8 && !XF && EPI == 0 && tc_stg_fits(KS, COUT_P, NCC_IN, NCC_W);
-    constexpr int RPI = tc_rows_per_item(KS, COUT_P, NCC_IN, NCC_W, STG ? tc_stg_bytes(COUT_P) : 0, XF ? COUT_P : 0);
+    constexpr bool STG = !XF && EPI == 0 && tc_stg_fits(KS, COUT_P, NCC_IN, NCC_W, FP8);
+    constexpr int RPI =
+        tc_rows_per_item(KS, COUT_P, NCC_IN, NCC_W, STG ? tc_stg_bytes(COUT_P, FP8) : 0, XF ? COUT_P : 0);
     static_assert(XF || (COUT_P % 16 == 0 && COUT_P >= 16 && COUT_P <= 256), "MMA N");
     static_assert(2 * R * NCB <= 512, "TMEM columns");
 
@@ -755,8 +762,9 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
             if constexpr (STG) {
                 if (coal) {
                     staged = true;
-                    constexpr int NU = COUT_P / 4;  // 16-byte units of a stored pixel: hi then lo
-                    constexpr uint32_t PITCH = (uint32_t)tc_stg_pitch(COUT_P);
+                    constexpr int PB = (FP8 ? 2 : 4) * COUT_P;  // bytes of a stored pixel: hi then lo
+                    constexpr int NU = PB / 16;                 // its 16-byte units
+                    constexpr uint32_t PITCH = (uint32_t)tc_stg_pitch(COUT_P, FP8);
                     uint8_t* const stw = sStg + (size_t)q * 32 * PITCH;  // this warp's 32 pixel slots
                     uint8_t* const slot = stw + (size_t)lane * PITCH;
                     const int xw = tx * TPX + q * 32;  // the warp's first pixel
@@ -778,17 +786,35 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                         for (int c16 = 0; c16 < COUT_P / 16; ++c16) {
                             float v[16];
                             const float4* b4 = reinterpret_cast<const float4*>(s_bias + c16 * 16);
+                            const float4* s4 = reinterpret_cast<const float4*>(s_scale + c16 * 16);
 #pragma unroll
                             for (int j4 = 0; j4 < 4; ++j4) {
                                 const float4 bb = b4[j4];
-                                v[4 * j4] = __uint_as_float(u[c16][4 * j4]) + bb.x;
-                                v[4 * j4 + 1] = __uint_as_float(u[c16][4 * j4 + 1]) + bb.y;
-                                v[4 * j4 + 2] = __uint_as_float(u[c16][4 * j4 + 2]) + bb.z;
-                                v[4 * j4 + 3] = __uint_as_float(u[c16][4 * j4 + 3]) + bb.w;
+                                if constexpr (FP8) {  // e4m3 accumulators carry the weight and input scales
+                                    const float4 ss = s4[j4];
+                                    v[4 * j4] = fmaf(__uint_as_float(u[c16][4 * j4]), ss.x, bb.x);
+                                    v[4 * j4 + 1] = fmaf(__uint_as_float(u[c16][4 * j4 + 1]), ss.y, bb.y);
+                                    v[4 * j4 + 2] = fmaf(__uint_as_float(u[c16][4 * j4 + 2]), ss.z, bb.z);
+                                    v[4 * j4 + 3] = fmaf(__uint_as_float(u[c16][4 * j4 + 3]), ss.w, bb.w);
+                                } else {
+                                    v[4 * j4] = __uint_as_float(u[c16][4 * j4]) + bb.x;
+                                    v[4 * j4 + 1] = __uint_as_float(u[c16][4 * j4 + 1]) + bb.y;
+                                    v[4 * j4 + 2] = __uint_as_float(u[c16][4 * j4 + 2]) + bb.z;
+                                    v[4 * j4 + 3] = __uint_as_float(u[c16][4 * j4 + 3]) + bb.w;
+                                }
                             }
+                            (void)s4;
                             if (a.relu)
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+                            if constexpr (FP8) {
+                                // [hi(cout) | lo(cout)] e4m3 of v / the output's scale
+                                uint4 hq, lq;
+                                fp8_pack16(v, a.out_qscale, hq, &lq);
+                                reinterpret_cast<uint4*>(slot)[c16] = hq;
+                                reinterpret_cast<uint4*>(slot)[NU / 2 + c16] = lq;
+                                continue;
+                            }
                             __nv_bfloat162 h2[8], l2[8];
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
@@ -809,7 +835,7 @@ __global__ void __launch_bounds__(PIN ? tc::THREADS_PIN : tc::THREADS, 1)
                         // the warp's pixels are contiguous in the NHWC output:
                         // unit g of the run is pixel g / NU, unit g % NU
                         uint8_t* const orow =
-                            static_cast<uint8_t*>(a.out) + (((size_t)b * a.H + y) * a.W + xw) * (size_t)(4 * COUT_P);
+                            static_cast<uint8_t*>(a.out) + (((size_t)b * a.H + y) * a.W + xw) * (size_t)PB;
 #pragma unroll
                         for (int k = 0; k < NU; ++k) {
                             const int g = k * 32 + lane;
@@ -1377,7 +1403,8 @@ static wskpn_status tc_run(const TcRun& r, const void* in, void* out, int B, int
     }
     const bool gm0 = r.gbits != nullptr, rb0 = r.relu_bits != nullptr;
     // the kernel's epilogue staging (its STG): as the kernel decides it
-    const size_t stg = !fp8 && !xf && !gm0 && !rb0 && tc_stg_fits(KS, cg, ncc_in, ncc_w) ? tc_stg_bytes(cg) : 0;
+    const size_t stg =
+        !xf && !gm0 && !rb0 && tc_stg_fits(KS, cg, ncc_in, ncc_w, fp8) ? tc_stg_bytes(cg, fp8) : 0;
     const size_t fixed = tc_fixed_bytes(KS, cg, ncc_w, xf ? cg : 0) + (xf ? tc_xf_bytes(KS) : 0) + stg;
     a.stage_bytes = tc_rows_per_item(KS, cg, ncc_in, ncc_w, stg, xf ? cg : 0) * a.row_bytes;  // the kernel's own RPI
     if (fixed + 2 * a.stage_bytes > tc::SMEM_MAX) {
