@@ -266,21 +266,29 @@ __device__ __forceinline__ void load_row8(float (&l)[dfv::SEG], const float* __r
             l[x] = (gy < H && gx0 + x < W) ? __ldg(zl + (size_t)gy * W + gx0 + x) : 0.f;
     }
 }
-// Vertical pass of size K: task (half, col), t < 2 (64 + K - 1), walks
-// footprint column col (image column tx0 - h + col) over rows
-// 16 half - h .. 16 half + 15 + h of the tile, forming E once per element,
-// and writes the 16 K-row sums of (E y0, E) to sVA and of (E y1, E y2) to
-// sVB at [16 half + r][col].  sY holds the planes y0, y1, y2.
+// Vertical pass of size K: task (segment, col), t < 3 (64 + K - 1), walks
+// footprint column col (image column tx0 - h + col) over the rows r0 - h ..
+// r0 + 10 + h of the tile, r0 = 0, 11, 21 for segments 0, 1, 2 (three
+// segments of 11 rows keep 3 (64 + K - 1) of the 256 threads busy, each
+// walking 11 + K - 1 rows), forming E once per element, and writes the 11
+// K-row sums of (E y0, E) to sVA and of (E y1, E y2) to sVB at
+// [r0 + r][col] (row 21, the last of segment 1, is written by segment 1
+// only).  sY holds the planes y0, y1, y2.
 template <int K>
 __device__ __forceinline__ void fwd_vpass(const float* __restrict__ sZ, const float* __restrict__ sY,
                                           float2* __restrict__ sVA, float2* __restrict__ sVB, float ml2e, int t) {
     constexpr int h = K / 2, NCOL = dfv::TW + 2 * h;
     constexpr int PL = dfv::FH * dfv::FW;
-    const int half = t >= NCOL ? 1 : 0;
-    const int col = t - half * NCOL;
-    const int o = (dfv::HALO + dfv::RV * half - h) * dfv::FW + dfv::XOFF - h + col;
-    const int v = dfv::RV * half * dfv::VP + col;
-    box_stream<K, dfv::RV, 2>(
+    constexpr int RS = 11;  // output rows per segment
+    static_assert(2 * RS <= dfv::TH && dfv::TH - RS <= 2 * RS && 3 * (dfv::TW + 12) <= dfv::THREADS,
+                  "three segments cover the tile rows; every task has a thread");
+    const int seg = t >= 2 * NCOL ? 2 : t >= NCOL ? 1 : 0;
+    const int col = t - seg * NCOL;
+    const int r0 = seg == 2 ? dfv::TH - RS : seg * RS;
+    const int o = (dfv::HALO + r0 - h) * dfv::FW + dfv::XOFF - h + col;
+    const int v = r0 * dfv::VP + col;
+    const int y_first = seg == 2 ? 2 * RS - r0 : 0;  // rows before it belong to segment 1
+    box_stream<K, RS, 2>(
         [&](int j, float2(&w)[2]) {
             const int q = o + j * dfv::FW;
             const float e = ex2_approx(fmaf(sZ[q], dfv::LOG2E, -ml2e));
@@ -288,8 +296,10 @@ __device__ __forceinline__ void fwd_vpass(const float* __restrict__ sZ, const fl
             w[1] = __fmul2_rn(make_float2(e, e), make_float2(sY[PL + q], sY[2 * PL + q]));
         },
         [&](int y, const float2(&s)[2]) {
-            sVA[v + y * dfv::VP] = s[0];
-            sVB[v + y * dfv::VP] = s[1];
+            if (y >= y_first) {
+                sVA[v + y * dfv::VP] = s[0];
+                sVB[v + y * dfv::VP] = s[1];
+            }
         });
 }
 
@@ -456,7 +466,7 @@ __device__ __forceinline__ unsigned fwd_size(const float* __restrict__ sZcur, fl
     const float ml2e = ord2f(*red) * dfv::LOG2E;
     if (tid == 0) *red_next = INT_MIN;  // its last reader finished before the previous barrier
     if (znext) stage_plane<VEC>(sZnext, znext, H, W, tx0, ty0, tid, -INFINITY);
-    if (tid < 2 * NCOL) fwd_vpass<K>(sZcur, sY, sVA, sVB, ml2e, tid);
+    if (tid < 3 * NCOL) fwd_vpass<K>(sZcur, sY, sVA, sVB, ml2e, tid);
     __syncthreads();
     // after the last vertical pass the y planes are free: the albedo of the
     // re-modulation is staged in the y1, y2 planes while the horizontal pass runs
@@ -798,7 +808,7 @@ __device__ __forceinline__ unsigned bwd1_size(const float* __restrict__ sZcur, f
     const float ml2e = ord2f(*red) * dfv::LOG2E;
     if (tid == 0) *red_next = INT_MIN;  // its last reader finished before the previous barrier
     if (znext) stage_plane<VEC>(sZnext, znext, H, W, tx0, ty0, tid, -INFINITY);
-    if (tid < 2 * NCOL) fwd_vpass<K>(sZcur, sY, sVA, sVB, ml2e, tid);
+    if (tid < 3 * NCOL) fwd_vpass<K>(sZcur, sY, sVA, sVB, ml2e, tid);
     __syncthreads();
     const int row = tid & 31, seg = tid >> 5;
     float Lp[dfv::SEG], d[dfv::SEG];
