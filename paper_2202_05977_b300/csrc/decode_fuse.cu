@@ -96,7 +96,10 @@ constexpr int THREADS = 256;
 constexpr int NWARP = THREADS / 32;
 constexpr int RV = TH / 2;              // vertical-pass output rows per task
 constexpr int SEG = 8;                  // horizontal-pass output pixels per task
-constexpr int VP = TW + 2 * HALO + 1;   // 77: pitch of the window-sum planes in float2 (odd: conflict-free)
+// 78: pitch of the window-sum planes in float2; even, so that a horizontal-
+// pass row starts on 16 bytes and its inputs load in pairs; the lanes of a
+// warp (rows, 624 bytes apart) then hit 8 distinct 16-byte bank groups
+constexpr int VP = TW + 2 * HALO + 2;
 constexpr int LP = TW + 4;              // 68: pitch of the per-pixel planes (16-byte aligned rows)
 constexpr int CPT = (NCH + THREADS - 1) / THREADS;  // chunks per thread (4)
 static_assert(TH == 32 && TW / SEG == NWARP, "horizontal pass: lane = row, warp = segment");
@@ -113,6 +116,7 @@ constexpr size_t SMEM_BYTES = OFF_R + sizeof(int) * 4;
 constexpr size_t OFF_RSTAGE = OFF_Z + PLANE;
 static_assert(OFF_RSTAGE + 3 * PLANE <= OFF_R, "staged radiance fits before the shifts");
 static_assert(OFF_V % 16 == 0 && OFF_Z % 16 == 0 && PLANE % 16 == 0, "16-byte aligned planes");
+static_assert(VP % 2 == 0 && SEG % 2 == 0 && (TH * VP) % 2 == 0, "paired loads of the window-sum planes");
 static_assert(3 * TH * LP * sizeof(float) <= 2 * PLANE, "staged albedo fits the y1, y2 planes");
 static_assert(2 * (SMEM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
 constexpr float LOG2E = 1.4426950408889634f;
@@ -157,6 +161,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // registers and entries no output needs are never computed; at step j only
 // the partial sums later outputs still need are live (about 16 pairs per
 // plane pair for K = 13).
+template <int K, int NOUT, int NP, typename In, typename Out>
+__device__ __forceinline__ void box_stream(In in, Out out);
+
+// Input of a horizontal pass: element j of a plane row starting at p (16-
+// byte aligned), for j = 0, 1, 2, ... in order, two per 16-byte load.
+struct PairLoader {
+    const float2* p;
+    float2 nxt;
+    __device__ __forceinline__ void operator()(int j, float2 (&in)[1]) {
+        if ((j & 1) == 0) {
+            const float4 q = *reinterpret_cast<const float4*>(p + j);
+            in[0] = make_float2(q.x, q.y);
+            nxt = make_float2(q.z, q.w);
+        } else {
+            in[0] = nxt;
+        }
+    }
+};
+
 template <int K, int NOUT, int NP, typename In, typename Out>
 __device__ __forceinline__ void box_stream(In in, Out out) {
     constexpr int N1 = NOUT + K - 1;
@@ -406,7 +429,7 @@ __device__ __forceinline__ unsigned fwd_hpass(const float2* __restrict__ sVA, co
     const int v = row * dfv::VP + seg * dfv::SEG;
     float w[dfv::SEG];
     bool bad = false;
-    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVA[v + j]; },
+    box_stream<K, dfv::SEG, 1>(PairLoader{sVA + v, {}},
                                [&](int x, const float2(&t)[1]) {
                                    const float D = t[0].y;
                                    const bool ok = D >= df::DMIN;
@@ -416,7 +439,7 @@ __device__ __forceinline__ unsigned fwd_hpass(const float2* __restrict__ sVA, co
                                    st.acc[x][0] = fmaf(w[x], t[0].x, st.acc[x][0]);
                                    st.S[x] = fmaf(w[x], D, st.S[x]);
                                });
-    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVB[v + j]; },
+    box_stream<K, dfv::SEG, 1>(PairLoader{sVB + v, {}},
                                [&](int x, const float2(&t)[1]) {
                                    st.acc[x][1] = fmaf(w[x], t[0].x, st.acc[x][1]);
                                    st.acc[x][2] = fmaf(w[x], t[0].y, st.acc[x][2]);
@@ -763,7 +786,7 @@ __device__ __forceinline__ unsigned bwd1_hpass(const float2* __restrict__ sVA, c
     const int v = row * dfv::VP + seg * dfv::SEG;
     float inv[dfv::SEG];
     bool bad = false;
-    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVA[v + j]; },
+    box_stream<K, dfv::SEG, 1>(PairLoader{sVA + v, {}},
                                [&](int x, const float2(&t)[1]) {
                                    const float D = t[0].y;
                                    const bool ok = D >= df::DMIN;
@@ -773,7 +796,7 @@ __device__ __forceinline__ unsigned bwd1_hpass(const float2* __restrict__ sVA, c
                                    // log2 alpha = l log2 e - cl
                                    Lp[x] = (ml2e + __log2f(D) - fmaf(st.l[x], dfv::LOG2E, -st.cl[x])) * dfv::LN2;
                                });
-    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVB[v + j]; },
+    box_stream<K, dfv::SEG, 1>(PairLoader{sVB + v, {}},
                                [&](int x, const float2(&t)[1]) {
                                    d[x] = (d[x] + fmaf(st.g[x][1], t[0].x, st.g[x][2] * t[0].y)) * inv[x];
                                });
@@ -1046,9 +1069,9 @@ __device__ __forceinline__ void bwd2_hpass(const float2* __restrict__ sVA, const
                                            const float (&y)[dfv::SEG][3], const float (&zq)[dfv::SEG], float mn2,
                                            int row, int seg, float (&o)[dfv::SEG]) {
     const int v = row * dfv::VP + seg * dfv::SEG;
-    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVA[v + j]; },
+    box_stream<K, dfv::SEG, 1>(PairLoader{sVA + v, {}},
                                [&](int x, const float2(&t)[1]) { o[x] = fmaf(y[x][0], t[0].x, y[x][1] * t[0].y); });
-    box_stream<K, dfv::SEG, 1>([&](int j, float2(&in)[1]) { in[0] = sVB[v + j]; },
+    box_stream<K, dfv::SEG, 1>(PairLoader{sVB + v, {}},
                                [&](int x, const float2(&t)[1]) {
                                    const float f = ex2_approx(fmaf(zq[x], dfv::LOG2E, -mn2));
                                    o[x] = f * (fmaf(y[x][2], t[0].x, o[x]) - t[0].y);
