@@ -207,3 +207,19 @@ def test_bounded_wait_expires_and_context_recovers(wk):
     mx, mean = rel_err(out, oracle.denoise(f, wb))
     print(f"after the expired wait: max rel {mx:.3e} mean {mean:.3e}")
     assert mx < TOL_BF16
+
+
+@pytest.mark.parametrize("ksizes", [(7,), (3, 9, 13), (1, 3, 5, 7, 9, 11, 13), (3, 3, 5, 5, 7, 9, 11, 13)])
+def test_bf16_other_kernel_counts_match_oracle(wk, ksizes):
+    # M != 6: the last layer's folded taps in 12-channel blocks (2M <= 12)
+    # or 16-channel blocks (2M = 14, 16)
+    M = len(ksizes)
+    widths = (10, 32, 48, 64, 2 * M)
+    f = synth.make_frame(70, 150, 60 + M)
+    wb = synth.make_weights(widths, 5, seed=60 + M)
+    d = _den(wk, wb, max_hw=(70, 150), widths=widths, ksizes=ksizes)
+    out = d.denoise(*args(to_dev(stack_frames([f])))).cpu().numpy()[0]
+    assert d.device_status() == 0
+    mx, mean = rel_err(out, oracle.denoise(f, wb, widths=widths, ksizes=ksizes))
+    print(f"bf16 M={M}: max rel {mx:.3e} mean {mean:.3e}")
+    assert mx < TOL_BF16
