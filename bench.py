@@ -49,9 +49,9 @@ TRAFFIC = {
     ("bf16", "conv2 (32->48)"): 604.0e6,
     ("bf16", "conv3 (48->64)"): 872.7e6,
     ("bf16", "conv4 (64->12)"): 614.7e6,
-    ("bf16", "decode_fuse_fwd"): 161.5e6,
-    ("fp32", "decode_fuse_fwd"): 161.5e6,
-    ("fp8", "decode_fuse_fwd"): 161.5e6,
+    ("bf16", "decode_fuse_fwd"): 161.8e6,
+    ("fp32", "decode_fuse_fwd"): 161.8e6,
+    ("fp8", "decode_fuse_fwd"): 161.8e6,
 }
 
 
