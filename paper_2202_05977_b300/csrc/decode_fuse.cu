@@ -411,8 +411,11 @@ __device__ __forceinline__ void form_irradiance(float* __restrict__ sY, const fl
 
 // Per-thread state of the horizontal-pass task (row, 8 pixels) across the
 // sizes i: acc_c = sum_i w_i N_ic and S = sum_i w_i D_i = sum_i exp(l_i - c)
-// with w_i = exp(l_i - c) / D_i; cl = c log2(e) (c = max_i l_i) and l, the
-// fusion logits of the size being processed (loaded one phase ahead).
+// with w_i = exp(l_i - c) / D_i; cl = c log2(e), c the largest fusion logit
+// of the sizes so far (a running maximum: when a size raises it, acc and S
+// are rescaled by exp(c_old - c_new) first, so every size's exponential is
+// at most 1), and l, the fusion logits of the size being processed (loaded
+// one phase ahead).
 struct HState {
     float acc[dfv::SEG][3];
     float S[dfv::SEG];
@@ -434,7 +437,17 @@ __device__ __forceinline__ unsigned fwd_hpass(const float2* __restrict__ sVA, co
                                    const float D = t[0].y;
                                    const bool ok = D >= df::DMIN;
                                    bad |= !ok;
-                                   const float e = ex2_approx(fmaf(st.l[x], dfv::LOG2E, -st.cl[x]));
+                                   // running softmax shift (Eq. 5): rescale what the
+                                   // earlier sizes accumulated when this one raises it
+                                   const float lx = st.l[x] * dfv::LOG2E;
+                                   const float cn = fmaxf(st.cl[x], lx);
+                                   const float sc = ex2_approx(st.cl[x] - cn);
+                                   st.cl[x] = cn;
+                                   st.acc[x][0] *= sc;
+                                   st.acc[x][1] *= sc;
+                                   st.acc[x][2] *= sc;
+                                   st.S[x] *= sc;
+                                   const float e = ex2_approx(lx - cn);
                                    w[x] = ok ? e * __fdividef(1.f, D) : 0.f;
                                    st.acc[x][0] = fmaf(w[x], t[0].x, st.acc[x][0]);
                                    st.S[x] = fmaf(w[x], D, st.S[x]);
@@ -539,25 +552,16 @@ __global__ void __launch_bounds__(dfv::THREADS, 2) decode_fuse_fwd_kernel(const 
     stage_irradiance<DEMOD, VEC>(sY, sRst, r, a, H, W, tx0, ty0, tid);
     __syncthreads();  // red[0] initialised before any thread folds its maximum in
 
-    // Shift of the fusion softmax per own pixel (Eq. 5): c = max_i l_i (all
-    // loads issued at once, while the copies above are in flight); the first
-    // size's logits stay in st.l.
+    // The first size's fusion logits (loaded while the copies above are in
+    // flight); the softmax shift of Eq. 5 is a running maximum over the
+    // sizes (HState), so the other sizes' logits are read once, one size
+    // ahead of their horizontal pass.
     HState st;
-    {
-        float l[WSKPN_MAX_KERNELS][dfv::SEG];
+    load_row8<VEC>(st.l, z + (size_t)M * HW, H, W, gy, gx0);
 #pragma unroll
-        for (int i = 0; i < WSKPN_MAX_KERNELS; ++i)
-            if (i < M) load_row8<VEC>(l[i], z + (size_t)(M + i) * HW, H, W, gy, gx0);
-#pragma unroll
-        for (int x = 0; x < dfv::SEG; ++x) {
-            float c = l[0][x];
-#pragma unroll
-            for (int i = 1; i < WSKPN_MAX_KERNELS; ++i)
-                if (i < M) c = fmaxf(c, l[i][x]);
-            st.cl[x] = c * dfv::LOG2E;
-            st.l[x] = l[0][x];
-            st.acc[x][0] = st.acc[x][1] = st.acc[x][2] = st.S[x] = 0.f;
-        }
+    for (int x = 0; x < dfv::SEG; ++x) {
+        st.cl[x] = -INFINITY;
+        st.acc[x][0] = st.acc[x][1] = st.acc[x][2] = st.S[x] = 0.f;
     }
 
     // Demodulated irradiance y = r / (a + eps), in place of the albedo: each
