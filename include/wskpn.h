@@ -144,17 +144,33 @@ wskpn_status wskpn_denoise(wskpn_ctx* ctx, const wskpn_frame* frames, int batch,
  * (host float32 planar, pinned memory recommended) into context-owned
  * device staging buffers, denoises, copies the result to host_out
  * ([batch][3][h][w] float32) and waits before returning.  Frames of 432
- * rows or more are processed as horizontal bands of about 216 rows, each
- * with the receptive-field halo (conv_ks / 2 rows per layer plus the largest
- * window's half) recomputed, on `stream`, while two context-owned copy
- * streams upload the next band and download the previous one; the result
- * equals wskpn_denoise up to the reconstruction's per-tile exponent shift
- * (float32 rounding).  Staging (52 bytes per pixel of max_batch x max_h x
- * max_w for unbanded calls, 13 floats per pixel of two extended bands for
- * banded ones) is allocated on first use.  Errors as wskpn_denoise, plus
- * ENOMEM. */
+ * rows or more are processed as horizontal bands of about 160 rows (at
+ * most 12; WSKPN_TUNE_HOST_BANDS), each with the receptive-field halo
+ * (conv_ks / 2 rows per layer plus the largest window's half) recomputed:
+ * three context-owned band buffers rotate so that a band uploads while
+ * earlier bands compute (on `stream` and, when two band workspaces fit, a
+ * second context-owned stream) and download; each input row crosses the
+ * host link once (the halo rows a band shares with the previous one are
+ * copied on the device).  The result equals wskpn_denoise up to the
+ * reconstruction's per-tile exponent shift (float32 rounding).  Staging
+ * (52 bytes per pixel of max_batch x max_h x max_w for unbanded calls, 13
+ * floats per pixel of an extended band per buffer for banded ones) is
+ * allocated on first use.  Errors as wskpn_denoise, plus ENOMEM. */
 wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h,
                                 int w, float* host_out, void* stream);
+
+/* wskpn_denoise_host without the final wait: queues the same copies and
+ * kernels and returns; `stream` is ordered after the last copy into
+ * host_out, so the result may be read once `stream` has reached that point
+ * (cudaStreamSynchronize, or an event recorded on it after the call).  The
+ * host input and output buffers must stay valid and unmodified until then.
+ * Successive calls on one context overlap: a call's uploads wait only for
+ * the band buffers they reuse, so the next frame's first bands cross the
+ * host link while the previous frame's last bands compute and download.
+ * Calls of one context are issued from one thread, on one stream.  Errors
+ * as wskpn_denoise_host (argument errors before anything is queued). */
+wskpn_status wskpn_denoise_host_async(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h,
+                                      int w, float* host_out, void* stream);
 
 /* ImportanceNet only (Sec. 5.1 + Sec. 4.1): writes the network output
  * z [batch][2M][h][w] (channels 0..M-1 importance maps for ksizes[0..M-1],

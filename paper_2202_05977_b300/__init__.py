@@ -115,15 +115,18 @@ class Denoiser:
         self._check(self._lib.wskpn_denoise(self._h, fr, B, H, W, _dev_f32(out, "out"), _stream(stream)))
         return out
 
-    def denoise_host(self, radiance, albedo, normal, depth, out, stream=None):
-        """Synchronous denoise of HOST float32 tensors [B, C, H, W] (pinned
-        recommended) into host tensor `out` [B, 3, H, W]; the library copies
-        the inputs in and the result back."""
+    def denoise_host(self, radiance, albedo, normal, depth, out, stream=None, wait=True):
+        """Denoise of HOST float32 tensors [B, C, H, W] (pinned recommended)
+        into host tensor `out` [B, 3, H, W]; the library copies the inputs in
+        and the result back.  wait=False returns once the work is queued:
+        `out` holds the result when `stream` (the current stream if None) has
+        reached the point after the call, and the host tensors must be kept
+        alive and unmodified until then."""
         fr, B, H, W = _frames(radiance, albedo, normal, depth, device=False)
         if out.is_cuda or not out.is_contiguous() or tuple(out.shape) != (B, 3, H, W):
             raise TypeError("out must be a contiguous host tensor [B, 3, H, W]")
-        self._check(self._lib.wskpn_denoise_host(self._h, fr, B, H, W, ctypes.c_void_p(out.data_ptr()),
-                                                 _stream(stream)))
+        fn = self._lib.wskpn_denoise_host if wait else self._lib.wskpn_denoise_host_async
+        self._check(fn(self._h, fr, B, H, W, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
 
     def logits(self, radiance, albedo, normal, depth, out=None, stream=None):

@@ -100,6 +100,7 @@ SIGNATURES = {
     "wskpn_get_weights": ([_P, _P, _SZ, _P], _I),
     "wskpn_denoise": ([_P, _FR, _I, _I, _I, _P, _P], _I),
     "wskpn_denoise_host": ([_P, _FR, _I, _I, _I, _P, _P], _I),
+    "wskpn_denoise_host_async": ([_P, _FR, _I, _I, _I, _P, _P], _I),
     "wskpn_logits": ([_P, _FR, _I, _I, _I, _P, _P], _I),
     "wskpn_prep": ([_FR, _I, _I, _I, _F, _F, _F, _P, _P], _I),
     "wskpn_decode_fuse_fwd": ([_P, _P, _P, _I, _I, _I, _I, ctypes.POINTER(_I), _F, _P, _P, _P], _I),

@@ -349,8 +349,11 @@ struct WorkspaceShift {
     ~WorkspaceShift() { c->d_tcA = ta, c->d_tcB = tb, c->d_actA = fa, c->d_actB = fb, c->d_z = z; }
 };
 
+// wait: return after the results are in host_out; else return once the
+// work is queued, with `st` ordered after the last download (a later call's
+// bands then wait, through the slot events, only for the slots they reuse).
 static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, int batch, int h, int w,
-                                        float* host_out, int nb, cudaStream_t st) {
+                                        float* host_out, int nb, cudaStream_t st, bool wait) {
     const int halo = band_halo(ctx->cfg);
     // band k covers rows [yb[k], yb[k + 1]); the first may be shorter (the
     // first computation starts sooner) and the last (less work after the
@@ -378,7 +381,7 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking), ctx->err);
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking), ctx->err);
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->halo_stream, cudaStreamNonBlocking), ctx->err);
-        ctx->band_events.resize(4 * wskpn_ctx::BAND_SLOTS);
+        ctx->band_events.resize(4 * wskpn_ctx::BAND_SLOTS + 2);
         for (auto& e : ctx->band_events)
             WSKPN_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), ctx->err);
     }
@@ -389,12 +392,27 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
     const bool two = !ctx->prof && 2 * (band_px + 256) <= ctx->ws_pixels;
     if (two && !ctx->band_stream)
         WSKPN_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->band_stream, cudaStreamNonBlocking), ctx->err);
+    cudaEvent_t ev_start = ctx->band_events[4 * wskpn_ctx::BAND_SLOTS];
+    cudaEvent_t ev_end = ctx->band_events[4 * wskpn_ctx::BAND_SLOTS + 1];
+    // A band buffer holds its inputs from the start and its output past the
+    // inputs of the call's tallest band.  A call with another layout (frame
+    // width or band height) could write inputs over an output an earlier
+    // call has not downloaded yet: its copies into the buffers wait for
+    // that call's last download first.  Calls of one size overlap freely.
+    if (ctx->band_job > 0 && (ext != ctx->band_ext || w != ctx->band_w)) {
+        WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream, ev_end, 0), ctx->err);
+        WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->halo_stream, ev_end, 0), ctx->err);
+    }
+    ctx->band_ext = ext;
+    ctx->band_w = w;
     if (two) {  // the second stream starts after what the caller queued before
-        WSKPN_CUDA_TRY(cudaEventRecord(ctx->band_events[0], st), ctx->err);
-        WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->band_stream, ctx->band_events[0], 0), ctx->err);
+        WSKPN_CUDA_TRY(cudaEventRecord(ev_start, st), ctx->err);
+        WSKPN_CUDA_TRY(cudaStreamWaitEvent(ctx->band_stream, ev_start, 0), ctx->err);
     }
     constexpr int NS = wskpn_ctx::BAND_SLOTS;
     if (ctx->band_floats < need) {
+        // earlier calls that returned without waiting may still use the slots
+        WSKPN_CUDA_TRY(cudaDeviceSynchronize(), ctx->err);
         for (float*& p : ctx->d_band) {
             cudaFree(p);
             p = nullptr;
@@ -414,12 +432,15 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
     auto EV_HALO = [&](int s) { return evs[3 * NS + s]; };
     const int ch[4] = {3, 3, 3, 1};
     const size_t HW = (size_t)h * w;
-    int job = 0;
+    // the job count runs on across calls, so that a call's first bands wait
+    // for the slots' previous uses (also those of an earlier call that
+    // returned without waiting)
+    uint64_t job = ctx->band_job;
     for (int b = 0; b < batch; ++b) {
         const float* src[4] = {hf[b].radiance, hf[b].albedo, hf[b].normal, hf[b].depth};
         int pe0 = 0, pe1 = 0;  // extended rows of this frame's previous band (in the other slot)
         for (int k = 0; k < nb; ++k, ++job) {
-            const int slot = job % NS, pslot = (job + NS - 1) % NS;
+            const int slot = (int)(job % NS), pslot = (int)((job + NS - 1) % NS);
             const int y0 = yb[k], y1 = yb[k + 1];
             if (y0 >= y1) break;
             const int e0 = std::max(0, y0 - halo), e1 = std::min(h, y1 + halo), eh = e1 - e0;
@@ -495,14 +516,21 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
             WSKPN_CUDA_TRY(cudaEventRecord(EV_DOWN(slot), ctx->down_stream), ctx->err);
         }
     }
+    ctx->band_job = job;
+    // every download is ordered after its band's compute
+    WSKPN_CUDA_TRY(cudaEventRecord(ev_end, ctx->down_stream), ctx->err);
+    if (!wait) {
+        WSKPN_CUDA_TRY(cudaStreamWaitEvent(st, ev_end, 0), ctx->err);
+        return WSKPN_OK;
+    }
     WSKPN_CUDA_TRY(cudaStreamSynchronize(ctx->down_stream), ctx->err);
     WSKPN_CUDA_TRY(cudaStreamSynchronize(st), ctx->err);
     if (two) WSKPN_CUDA_TRY(cudaStreamSynchronize(ctx->band_stream), ctx->err);
     return WSKPN_OK;
 }
 
-wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h, int w,
-                                float* host_out, void* stream) {
+static wskpn_status denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h, int w,
+                                 float* host_out, void* stream, bool wait) {
     if (!ctx) return WSKPN_EINVAL;
     wskpn_status s = check_frames(ctx, host_frames, batch, h, w);
     if (s) return s;
@@ -516,7 +544,7 @@ wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, 
     // the copies they let overlap.  Smaller frames: one upload, denoise,
     // download.
     const int nb = ctx->host_bands > 0 ? std::min(ctx->host_bands, h) : h < 432 ? 1 : std::min(12, h / 160);
-    if (nb >= 2) return denoise_host_banded(ctx, host_frames, batch, h, w, host_out, nb, (cudaStream_t)stream);
+    if (nb >= 2) return denoise_host_banded(ctx, host_frames, batch, h, w, host_out, nb, (cudaStream_t)stream, wait);
     if (!ctx->d_stage) {
         cudaError_t e = cudaMalloc((void**)&ctx->d_stage, ctx->ws_pixels * 13 * sizeof(float));
         if (e != cudaSuccess) {
@@ -547,8 +575,18 @@ wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, 
     WSKPN_CUDA_TRY(cudaMemcpyAsync(host_out, dout, (size_t)batch * 3 * HW * sizeof(float), cudaMemcpyDeviceToHost,
                                    st),
                    ctx->err);
-    WSKPN_CUDA_TRY(cudaStreamSynchronize(st), ctx->err);
+    if (wait) WSKPN_CUDA_TRY(cudaStreamSynchronize(st), ctx->err);
     return WSKPN_OK;
+}
+
+wskpn_status wskpn_denoise_host(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h, int w,
+                                float* host_out, void* stream) {
+    return denoise_host(ctx, host_frames, batch, h, w, host_out, stream, true);
+}
+
+wskpn_status wskpn_denoise_host_async(wskpn_ctx* ctx, const wskpn_frame* host_frames, int batch, int h, int w,
+                                      float* host_out, void* stream) {
+    return denoise_host(ctx, host_frames, batch, h, w, host_out, stream, false);
 }
 
 wskpn_status wskpn_prep(const wskpn_frame* frames, int batch, int h, int w, float gamma, float depth_near,

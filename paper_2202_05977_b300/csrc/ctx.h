@@ -57,7 +57,10 @@ struct wskpn_ctx {
     static constexpr int BAND_SLOTS = 3;       // band buffers of the host pipeline
     float* d_band[BAND_SLOTS] = {};            // [10 + 3][band_rows][max_w] each
     size_t band_floats = 0;
-    std::vector<cudaEvent_t> band_events;   // per band slot: uploaded, computed, downloaded, halo copied
+    std::vector<cudaEvent_t> band_events;   // per band slot: uploaded, computed, downloaded, halo copied;
+                                            // then the call's start and end
+    uint64_t band_job = 0;                  // bands issued so far (slot = job % BAND_SLOTS, across calls)
+    int band_ext = -1, band_w = -1;         // band buffer layout of the last call (extended rows, width)
     unsigned int* d_fallbacks = nullptr;
     unsigned int* d_status = nullptr;  // device status word of the tensor-core kernels
     float act_scale[WSKPN_MAX_LAYERS + 1] = {};  // FP8 per-layer activation scales

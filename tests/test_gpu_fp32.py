@@ -210,3 +210,33 @@ def test_banded_host_call_with_tuned_bands(torch, wk, bands, first):
     assert mx < 1e-5, mx
     with pytest.raises(wk.WskpnError):
         d.set_tuning(_lib.TUNE_HOST_FIRST_BAND, 5)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_async_host_calls_overlap_and_match_sync_calls(torch, wk, prec):
+    """wskpn_denoise_host_async: several frames of different sizes queued
+    back to back on one context (banded and unbanded, each into its own host
+    buffer), one synchronisation at the end; every result equals the
+    synchronous call's, bit for bit (same bands, same kernels)."""
+    sizes = [(600, 200), (460, 130), (600, 200), (40, 72), (1080, 256)]
+    wb = synth.make_weights(seed=5)
+    d = wk.Denoiser(wb, precision=prec, max_hw=(1080, 256))
+    hosts, outs, refs = [], [], []
+    for i, (H, W) in enumerate(sizes):
+        st = stack_frames([synth.make_frame(H, W, 50 + i)])
+        host = [torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in ("radiance", "albedo", "normal", "depth")]
+        ref = torch.empty((1, 3, H, W), dtype=torch.float32).pin_memory()
+        d.denoise_host(*host, ref)
+        hosts.append(host)
+        refs.append(ref)
+        outs.append(torch.full((1, 3, H, W), float("nan"), dtype=torch.float32).pin_memory())
+    s = torch.cuda.Stream()
+    for _ in range(2):  # twice: the second round reuses band buffers the first still holds in flight
+        for host, out in zip(hosts, outs):
+            d.denoise_host(*host, out, stream=s, wait=False)
+        s.synchronize()
+        for out, ref in zip(outs, refs):
+            assert torch.equal(out, ref)
+        for out in outs:
+            out.fill_(float("nan"))
+    assert d.device_status() == 0
