@@ -514,9 +514,9 @@ static wskpn_status denoise_host_banded(wskpn_ctx* ctx, const wskpn_frame* hf, i
                                              ctx->down_stream),
                            ctx->err);
             WSKPN_CUDA_TRY(cudaEventRecord(EV_DOWN(slot), ctx->down_stream), ctx->err);
+            ctx->band_job = job + 1;  // issued: a later call (even after an error here) waits for it
         }
     }
-    ctx->band_job = job;
     // every download is ordered after its band's compute
     WSKPN_CUDA_TRY(cudaEventRecord(ev_end, ctx->down_stream), ctx->err);
     if (!wait) {
