@@ -554,8 +554,16 @@ def main():
     clocks = clk.stop()
 
     fp32 = None
+    fp32_720 = None
     if not args.no_fp32 and args.precision != "fp32":
         fp32 = time_path("fp32", max(3, args.steps // 4), 3)
+        # the plain FP32 path on the 1280x720 seed-1 frame (its oracle is
+        # timed with the CPU baseline below)
+        f720p = synth.make_frame(720, 1280, replica_seed(1, rank))
+        x720p = [torch.from_numpy(np.ascontiguousarray(f720p[k][None])).to(dev) for k in keys]
+        r720 = time_path("fp32", max(3, args.steps // 4), 3, (720, 1280), x720p)
+        fp32_720 = {"ms": r720["ms_step"], "out": r720["out"].cpu().numpy()[0], "frame": f720p}
+        del r720
 
     # the precision form: the same frame through the BF16 and FP8 forms, each
     # output against the FP32 path's and (after the CPU baseline has run the
@@ -826,6 +834,18 @@ def main():
             line["serving_sweep"] = sweep
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], ref = cpu_baseline()
+            if fp32_720 is not None:
+                # the plain FP32 path at 1280x720 against the FP64 oracle on the
+                # host cores: time per frame of each, error over every pixel
+                import oracle
+                wb720 = synth.make_weights(WIDTHS, KS, seed=SEED)
+                t0 = time.perf_counter()
+                ref720 = oracle.denoise(fp32_720["frame"], wb720, widths=WIDTHS, ks=KS, ksizes=KSIZES)
+                el = time.perf_counter() - t0
+                line["plain_fp32_720p"] = {"ms_per_frame": fp32_720["ms"], "oracle_ms_per_frame": el * 1e3,
+                                           "oracle_cores": oracle.num_threads(),
+                                           "speedup_vs_oracle": el * 1e3 / fp32_720["ms"],
+                                           **oracle_errors(fp32_720["out"], ref720)}
             # every pixel of the precision forms against the FP64 oracle
             if precision_form is not None:
                 for prec, o in form_out.items():
