@@ -108,3 +108,19 @@ def test_multires_arguments_rejected_without_touching_the_gpu():
     assert lib.wskpn_mr_create(ctypes.byref(cfg), w.ctypes.data, w.size, ctypes.byref(out)) == _lib.EINVAL
     assert lib.wskpn_mr_n_weights() == 188_878
     lib.wskpn_mr_destroy(None)
+
+
+def test_header_compiles_as_c(tmp_path):
+    """include/wskpn.h is a plain C header: a C99 translation unit that
+    includes it compiles without warnings (no C++ or CUDA types in the
+    signatures)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "wskpn.h"\nint main(void) { return 0; }\n')
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
