@@ -1661,6 +1661,30 @@ wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int
     return tc_run(r, in, out, B, H, W, st, err);
 }
 
+// tc_layer_run of a first layer that assembles its input from one frame's
+// FP32 buffers (Sec. 5.1; the input-assembling kernel, BF16 hi/lo).
+wskpn_status tc_layer_run_pin(const Layer& L, int KS, const wskpn_frame* frame, float gamma, float dnear, float dfar,
+                              void* out, int out_cp, int relu, int H, int W, unsigned int* status, int device,
+                              cudaStream_t st, std::string& err) {
+    TcRun r{};
+    r.L = &L;
+    r.KS = KS;
+    r.fp8 = false;
+    r.split_in = r.split_out = 1;
+    r.last = 0;
+    r.relu = relu;
+    r.out_cp = out_cp;
+    r.out_c0 = 0;
+    r.out_qscale = 1.f;
+    r.status = status;
+    r.device = device;
+    r.frames = frame;
+    r.prep.inv_gamma = (float)(1.0 / (double)gamma);
+    r.prep.dnear = dnear;
+    r.prep.dscale = (float)(1.0 / ((double)dfar - (double)dnear));
+    return tc_run(r, nullptr, out, 1, H, W, st, err);
+}
+
 wskpn_status tc_dgrad_run(const Layer& Lt, int KS, const void* g, void* gx, const uint32_t* x_bits, float* bias_part,
                           int* nparts, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
                           std::string& err) {

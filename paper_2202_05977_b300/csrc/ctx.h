@@ -134,6 +134,9 @@ wskpn_status tc_dgrad_layer_pack(Layer& Lt, int KS, const float* w, float* wt, c
 wskpn_status tc_layer_run(const Layer& L, int KS, const void* in, void* out, int out_cp, int out_c0, int last,
                           int relu, int B, int H, int W, unsigned int* status, int device, cudaStream_t st,
                           std::string& err);
+wskpn_status tc_layer_run_pin(const Layer& L, int KS, const wskpn_frame* frame, float gamma, float dnear, float dfar,
+                              void* out, int out_cp, int relu, int H, int W, unsigned int* status, int device,
+                              cudaStream_t st, std::string& err);
 // The input gradient gx (NHWC BF16, Lt.cout_p channels) of a layer from its
 // output gradient g (NHWC BF16) through Lt, times the ReLU derivative of the layer input
 // (x_bits: its positive-channel bits, two words per pixel), with per-warp

@@ -176,9 +176,9 @@ struct wskpn_mr {
     float* w32[mr::NL] = {};    // SIMT packing per layer (FP32)
     float* b32[mr::NL] = {};
     wskpn::Layer tcL[mr::NL];   // tensor-core layers (BF16)
-    // BF16 activations, hi/lo NHWC: x0 [16], t0 [32], c0 [48 + 32], p1 [32],
-    // t1 [48], c1 [64 + 48], p2 [48], t2 [64], e2 [64]
-    __nv_bfloat16 *bx0 = nullptr, *bt0 = nullptr, *bc0 = nullptr, *bp1 = nullptr, *bt1 = nullptr,
+    // BF16 activations, hi/lo NHWC: t0 [32], c0 [48 + 32], p1 [32], t1 [48],
+    // c1 [64 + 48], p2 [48], t2 [64], e2 [64] (E0 assembles its own input)
+    __nv_bfloat16 *bt0 = nullptr, *bc0 = nullptr, *bp1 = nullptr, *bt1 = nullptr,
                   *bc1 = nullptr, *bp2 = nullptr, *bt2 = nullptr, *be2 = nullptr;
     unsigned int* d_status = nullptr;
     // workspaces, sized for max_h x max_w (levels: l1 = ceil halves, l2 = ceil quarters)
@@ -224,7 +224,7 @@ extern "C" void wskpn_mr_destroy(wskpn_mr* m) {
     float* bufs[] = {m->x0, m->t0, m->c0, m->z0, m->p1, m->t1, m->c1, m->z1, m->p2, m->t2, m->e2, m->z2,
                      m->y[0], m->y[1], m->y[2], m->iv[0], m->iv[1], m->iv[2], m->o1};
     for (float* b : bufs) cudaFree(b);
-    __nv_bfloat16* hbufs[] = {m->bx0, m->bt0, m->bc0, m->bp1, m->bt1, m->bc1, m->bp2, m->bt2, m->be2};
+    __nv_bfloat16* hbufs[] = {m->bt0, m->bc0, m->bp1, m->bt1, m->bc1, m->bp2, m->bt2, m->be2};
     for (auto* b : hbufs) cudaFree(b);
     for (auto& L : m->tcL) tc_layer_free(L);
     cudaFree(m->d_fallbacks);
@@ -273,7 +273,7 @@ extern "C" wskpn_status wskpn_mr_create(const wskpn_mr_config* cfg_in, const flo
              alloc(&m->t1, 48 * P1) && alloc(&m->c1, 112 * P1) && alloc(&m->p2, 48 * P2) && alloc(&m->t2, 64 * P2) &&
              alloc(&m->e2, 64 * P2);
     if (ok && bf16)
-        ok = halloc(&m->bx0, 16, P0) && halloc(&m->bt0, 32, P0) && halloc(&m->bc0, 80, P0) &&
+        ok = halloc(&m->bt0, 32, P0) && halloc(&m->bc0, 80, P0) &&
              halloc(&m->bp1, 32, P1) && halloc(&m->bt1, 48, P1) && halloc(&m->bc1, 112, P1) &&
              halloc(&m->bp2, 48, P2) && halloc(&m->bt2, 64, P2) && halloc(&m->be2, 64, P2);
     size_t off = 0;
@@ -334,9 +334,10 @@ wskpn_status mr_tc(wskpn_mr* m, int l, const void* in, void* out, int out_cp, in
 wskpn_status mr_forward_bf16(wskpn_mr* m, const wskpn_frame* f, int h, int w, cudaStream_t st) {
     const int h1 = (h + 1) / 2, w1 = (w + 1) / 2, h2 = (h1 + 1) / 2, w2 = (w1 + 1) / 2;
     const size_t P0 = (size_t)h * w, P1 = (size_t)h1 * w1, P2 = (size_t)h2 * w2;
-    void* x0 = m->bx0;
-    wskpn_status s = launch_prep(f, 1, h, w, m->cfg.gamma, m->cfg.depth_near, m->cfg.depth_far, &x0, 2, st, m->err);
-    if (!s) s = mr_tc(m, mr::E0, m->bx0, m->bt0, 32, 0, h, w, st);
+    // E0 assembles its input tiles from the frame (Sec. 5.1) inside its own
+    // kernel; the assembled input is never stored
+    wskpn_status s = tc_layer_run_pin(m->tcL[mr::E0], mr::KS, f, m->cfg.gamma, m->cfg.depth_near, m->cfg.depth_far,
+                                      m->bt0, 32, mr::LAYERS[mr::E0].relu, h, w, m->d_status, m->device, st, m->err);
     if (!s) s = mr_tc(m, mr::E0B, m->bt0, m->bc0, 80, 48, h, w, st);  // skip into channels 48..79
     if (!s) {
         mr::pool_nhwc_kernel<<<mr::grid_for(32 * P1), 256, 0, st>>>(m->bc0, 80, 48, 32, h, w, m->bp1);
