@@ -79,3 +79,17 @@ def test_fp8_1080p_every_pixel_matches_oracle(wk, frame_1080p):
     mx, mean = rel_err(out, ref)
     print(f"fp8 1920x1080 every pixel vs oracle: max {mx:.3e} mean {mean:.3e}")
     assert np.isfinite(out).all() and mx < TOL["fp8"]
+
+
+def test_bf16_fp8_1440p_every_pixel_matches_oracle(wk):
+    """The resolution sweep's largest frame (2560x1440, frame and weights of
+    seed 3) over every pixel, BF16 and FP8 (scales calibrated on the seed-4
+    frame); about 28 s of oracle time on 16 host cores."""
+    f = synth.make_frame(1440, 2560, 3)
+    wb = synth.make_weights(seed=3)
+    ref = oracle.denoise(f, wb)
+    for prec, cal in (("bf16", None), ("fp8", synth.make_frame(1440, 2560, 4))):
+        out = _run(wk, f, wb, prec, cal=cal)
+        mx, mean = rel_err(out, ref)
+        print(f"{prec} 2560x1440 every pixel vs oracle: max {mx:.3e} mean {mean:.3e}")
+        assert np.isfinite(out).all() and mx < TOL[prec]
